@@ -1,0 +1,263 @@
+"""Python handle on the plain FP64 C oracle (``amr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path (the
+CUDA library and its binding) never imports this package.
+
+The oracle follows the paper's own structure for one level step (Sec. 3):
+gather a 6x6x6 stencil of ``uold`` per oct, convert to primitives, limited
+slopes, Hancock predictor, HLLC on every face of the oct's cells, update.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "amr_oracle.c")
+HDR = os.path.join(HERE, "amr_oracle.h")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
+
+NV = 5
+ERRORS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EGRADING", 4: "EDUP"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what}: {ERRORS.get(code, code)}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-ffp-contract=off: source-order IEEE)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest:
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Params(C.Structure):
+    _fields_ = [("levelmin", C.c_int), ("levelmax", C.c_int),
+                ("gamma", C.c_double), ("cfl", C.c_double),
+                ("smallr", C.c_double), ("smallc", C.c_double),
+                ("reflux", C.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P, I64, U64, D, I = C.c_void_p, C.c_int64, C.c_uint64, C.c_double, C.c_int
+            sig = {
+                "orc_pack_key": (U64, [I, C.c_uint32, C.c_uint32, C.c_uint32]),
+                "orc_fnv1a64_bytes": (U64, [P, C.c_size_t]),
+                "orc_fnv1a64_key": (U64, [U64]),
+                "orc_hilbert3": (U64, [C.c_uint32, C.c_uint32, C.c_uint32, I]),
+                "orc_create": (I, [C.POINTER(_Params), I64, P, P, P, P, P, C.POINTER(P)]),
+                "orc_destroy": (None, [P]),
+                "orc_num_octs": (I64, [P, I]),
+                "orc_level_offset": (I64, [P, I]),
+                "orc_num_cache": (I64, [P, I]),
+                "orc_lookup": (I64, [P, U64]),
+                "orc_read": (I, [P, I, P, P]),
+                "orc_read_R": (I, [P, I, P]),
+                "orc_read_split": (I, [P, I, P]),
+                "orc_read_nbr": (I, [P, I, P]),
+                "orc_read_cache": (I, [P, I, P]),
+                "orc_ghost": (I, [P, I, P]),
+                "orc_write": (I, [P, I, P]),
+                "orc_totals": (None, [P, P]),
+                "orc_cfl_dt": (D, [P]),
+                "orc_step_level": (I, [P, I, D]),
+                "orc_step_sample": (I, [P, I, D, I64, P, P]),
+                "orc_advance": (I, [P, I, C.POINTER(D)]),
+                "orc_uniform_step": (I, [I, P, D, D, D, D]),
+                "orc_uniform_cfl_dt": (D, [I, P, D, D, D, D]),
+                "orc_1d_step": (I, [I, P, D, D, D, D]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def pack_key(level, i, j, k) -> int:
+    return int(lib().orc_pack_key(int(level), int(i), int(j), int(k)))
+
+
+def fnv1a64_bytes(b: bytes) -> int:
+    buf = np.frombuffer(b, dtype=np.uint8).copy() if b else np.zeros(1, np.uint8)
+    return int(lib().orc_fnv1a64_bytes(_ptr(buf), len(b)))
+
+
+def fnv1a64_key(key: int) -> int:
+    return int(lib().orc_fnv1a64_key(int(key)))
+
+
+def hilbert3(x, y, z, bits) -> int:
+    return int(lib().orc_hilbert3(int(x), int(y), int(z), int(bits)))
+
+
+class Mesh:
+    """An oracle mesh built from an oct list (same inputs as ``amr_create``)."""
+
+    def __init__(self, level, i, j, k, U, *, levelmin, levelmax, gamma, cfl=0.8,
+                 smallr=1e-10, smallc=1e-10, reflux=True):
+        self.params = _Params(levelmin, levelmax, gamma, cfl, smallr, smallc, int(reflux))
+        level = np.ascontiguousarray(level, dtype=np.uint8)
+        i = np.ascontiguousarray(i, dtype=np.uint32)
+        j = np.ascontiguousarray(j, dtype=np.uint32)
+        k = np.ascontiguousarray(k, dtype=np.uint32)
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        n = level.shape[0]
+        assert U.shape == (NV, 8 * n), U.shape
+        h = C.c_void_p()
+        rc = lib().orc_create(C.byref(self.params), n, _ptr(level), _ptr(i), _ptr(j),
+                              _ptr(k), _ptr(U), C.byref(h))
+        if rc:
+            raise OracleError(rc, "create")
+        self._h = h
+        self.levelmin, self.levelmax = levelmin, levelmax
+        self.gamma = gamma
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_destroy(h)
+            self._h = None
+
+    # -- introspection -----------------------------------------------------
+    def num_octs(self, level: int) -> int:
+        return int(lib().orc_num_octs(self._h, level))
+
+    def level_offset(self, level: int) -> int:
+        return int(lib().orc_level_offset(self._h, level))
+
+    def num_cache(self, level: int) -> int:
+        return int(lib().orc_num_cache(self._h, level))
+
+    def lookup(self, key: int) -> int:
+        return int(lib().orc_lookup(self._h, int(key)))
+
+    def read(self, level: int):
+        n = self.num_octs(level)
+        keys = np.zeros(max(n, 1), np.uint64)
+        U = np.zeros((NV, 8 * max(n, 1)), np.float64)
+        lib().orc_read(self._h, level, _ptr(keys), _ptr(U))
+        return keys[:n], U[:, :8 * n]
+
+    def read_R(self, level: int):
+        n = self.num_octs(level)
+        R = np.zeros((NV, 8 * max(n, 1)), np.float64)
+        lib().orc_read_R(self._h, level, _ptr(R))
+        return R[:, :8 * n]
+
+    def read_split(self, level: int):
+        n = self.num_octs(level)
+        s = np.zeros(8 * max(n, 1), np.uint8)
+        lib().orc_read_split(self._h, level, _ptr(s))
+        return s[:8 * n]
+
+    def read_nbr(self, level: int):
+        n = self.num_octs(level)
+        nb = np.zeros((max(n, 1), 27), np.int64)
+        lib().orc_read_nbr(self._h, level, _ptr(nb))
+        return nb[:n]
+
+    def read_cache(self, level: int):
+        n = self.num_cache(level)
+        keys = np.zeros(max(n, 1), np.uint64)
+        lib().orc_read_cache(self._h, level, _ptr(keys))
+        return keys[:n]
+
+    def ghost(self, level: int):
+        n = self.num_cache(level)
+        Ug = np.zeros((NV, 8 * max(n, 1)), np.float64)
+        rc = lib().orc_ghost(self._h, level, _ptr(Ug))
+        if rc:
+            raise OracleError(rc, "ghost")
+        return Ug[:, :8 * n]
+
+    def write(self, level: int, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        assert U.shape == (NV, 8 * self.num_octs(level))
+        lib().orc_write(self._h, level, _ptr(U))
+
+    def totals(self):
+        t = np.zeros(NV, np.float64)
+        lib().orc_totals(self._h, _ptr(t))
+        return t
+
+    # -- stepping ------------------------------------------------------------
+    def cfl_dt(self) -> float:
+        return float(lib().orc_cfl_dt(self._h))
+
+    def step_level(self, level: int, dt: float):
+        rc = lib().orc_step_level(self._h, level, float(dt))
+        if rc:
+            raise OracleError(rc, "step_level")
+
+    def step_sample(self, level: int, dt: float, octs):
+        octs = np.ascontiguousarray(octs, dtype=np.int64)
+        ns = octs.shape[0]
+        out = np.zeros((NV, 8 * max(ns, 1)), np.float64)
+        rc = lib().orc_step_sample(self._h, level, float(dt), ns, _ptr(octs), _ptr(out))
+        if rc:
+            raise OracleError(rc, "step_sample")
+        return out[:, :8 * ns]
+
+    def advance(self, nsteps: int = 1) -> float:
+        dt = C.c_double(0.0)
+        rc = lib().orc_advance(self._h, int(nsteps), C.byref(dt))
+        if rc:
+            raise OracleError(rc, "advance")
+        return dt.value
+
+    def levels(self):
+        return [l for l in range(self.levelmin, self.levelmax + 1) if self.num_octs(l) > 0]
+
+
+def uniform_step(U, gamma, dt, smallr=1e-10, smallc=1e-10):
+    """One step of the independent uniform periodic 3-D solver; U is [5][n^3]."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    n = round(U.shape[1] ** (1.0 / 3.0))
+    assert n ** 3 == U.shape[1]
+    rc = lib().orc_uniform_step(n, _ptr(U), gamma, dt, smallr, smallc)
+    if rc:
+        raise OracleError(rc, "uniform_step")
+    return U
+
+
+def uniform_cfl_dt(U, gamma, cfl, smallr=1e-10, smallc=1e-10):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    n = round(U.shape[1] ** (1.0 / 3.0))
+    return float(lib().orc_uniform_cfl_dt(n, _ptr(U), gamma, cfl, smallr, smallc))
+
+
+def step_1d(U, gamma, dt, smallr=1e-10, smallc=1e-10):
+    """One step of the 1-D restriction of the scheme; U is [5][n], periodic."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    rc = lib().orc_1d_step(U.shape[1], _ptr(U), gamma, dt, smallr, smallc)
+    if rc:
+        raise OracleError(rc, "1d_step")
+    return U

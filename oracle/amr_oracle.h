@@ -1,0 +1,93 @@
+/*
+ * amr_oracle.h -- plain, slow FP64 CPU oracle of one AMR level step of
+ * compressible Euler on a cell-by-cell octree (RAMSES-GPU, arXiv 2607.20704).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; the two are compared
+ * element by element on the same seeded inputs.
+ *
+ * Conventions (paper Sec. 2, "Adaptive Mesh Refinement on the GPU"):
+ *   - an oct is a 2x2x2 block of cells; an oct of level l has integer
+ *     coordinates (i,j,k) in [0, 2^(l-1))^3 and cell size dx_l = 2^-l in the
+ *     unit box; cell c = cx + 2cy + 4cz inside the oct;
+ *   - nvar = 5 conservative variables U = (rho, rho u, rho v, rho w, E);
+ *   - state arrays are structure-of-arrays: U[v*8n + 8*oct + c];
+ *   - octs are held sorted by (level, Hilbert key, input index) (Sec. 2.2).
+ *
+ * Parity unpinned (any choice is "correct", one is fixed here and mirrored in
+ * the CUDA path): the HLLC wave-speed estimate, the floor constants smallr /
+ * smallc, the Hilbert orientation, the hash-table slot layout.
+ */
+#ifndef AMR_ORACLE_H
+#define AMR_ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NV 5
+#define ORC_MAXLEV 15
+
+enum {
+  ORC_OK = 0,
+  ORC_EINVAL = 1,
+  ORC_ENOMEM = 2,
+  ORC_EGRADING = 3,
+  ORC_EDUP = 4
+};
+
+typedef struct {
+  int levelmin, levelmax;
+  double gamma, cfl;
+  double smallr, smallc; /* floors: rho >= smallr, p >= rho*smallc^2/gamma */
+  int reflux;            /* 1: reflux at coarse-fine faces; 0: negative control */
+} orc_params;
+
+typedef struct orc_mesh orc_mesh;
+
+/* --- keys, hash function, Hilbert key (Sec. 2.1, 2.2, Sec. 5) ------------ */
+uint64_t orc_pack_key(int level, uint32_t i, uint32_t j, uint32_t k);
+uint64_t orc_fnv1a64_bytes(const uint8_t *bytes, size_t len);
+uint64_t orc_fnv1a64_key(uint64_t key);
+uint64_t orc_hilbert3(uint32_t x, uint32_t y, uint32_t z, int bits);
+
+/* --- mesh ------------------------------------------------------------------ */
+int orc_create(const orc_params *p, int64_t n, const uint8_t *lvl,
+               const uint32_t *i, const uint32_t *j, const uint32_t *k,
+               const double *U, orc_mesh **out);
+void orc_destroy(orc_mesh *m);
+int64_t orc_num_octs(const orc_mesh *m, int level);
+int64_t orc_level_offset(const orc_mesh *m, int level);
+int64_t orc_num_cache(const orc_mesh *m, int level);
+int64_t orc_lookup(const orc_mesh *m, uint64_t key);
+int orc_read(const orc_mesh *m, int level, uint64_t *keys, double *U);
+int orc_read_R(const orc_mesh *m, int level, double *R);
+int orc_read_split(const orc_mesh *m, int level, uint8_t *split);
+int orc_read_nbr(const orc_mesh *m, int level, int64_t *nbr);
+int orc_read_cache(const orc_mesh *m, int level, uint64_t *keys);
+int orc_ghost(orc_mesh *m, int level, double *Ug);
+int orc_write(orc_mesh *m, int level, const double *U);
+void orc_totals(const orc_mesh *m, double tot[ORC_NV]);
+
+/* --- time stepping (Sec. 3; stage order of Table 1) ------------------------ */
+double orc_cfl_dt(const orc_mesh *m);
+int orc_step_level(orc_mesh *m, int level, double dt);
+int orc_step_sample(orc_mesh *m, int level, double dt, int64_t ns,
+                    const int64_t *octs, double *Unew);
+int orc_advance(orc_mesh *m, int nsteps, double *dt_last);
+
+/* --- independent cross-check solvers ----------------------------------------- */
+int orc_uniform_step(int n, double *U, double gamma, double dt, double smallr,
+                     double smallc);
+double orc_uniform_cfl_dt(int n, const double *U, double gamma, double cfl,
+                          double smallr, double smallc);
+int orc_1d_step(int n, double *U, double gamma, double dt, double smallr,
+                double smallc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
