@@ -1,0 +1,228 @@
+/*
+ * amr.h -- C ABI of the GB300 level-advance library for compressible Euler on
+ * a cell-by-cell octree (the AMR hydro method of RAMSES-GPU, arXiv 2607.20704).
+ *
+ * One handle owns one graded octree resident in device memory: the oct list
+ * (sorted by level, then Hilbert key, Sec. 2.2), an FNV-1a 64 hash table with
+ * linear probing keyed by (i,j,k,l) (Sec. 2.1, Sec. 5), the father/neighbour
+ * index arrays and the ghost-oct cache (Sec. 2.3), the conservative state
+ * U = (rho, rho u, rho v, rho w, E) of every cell and the pending reflux of
+ * every coarse cell.  All computation runs in the library's CUDA kernels on
+ * the handle's stream; nothing falls back to the CPU.
+ *
+ * Conventions.  An oct of level l (levelmin <= l <= levelmax <= 15) has
+ * integer coordinates (i,j,k) in [0, 2^(l-1))^3 of the periodic unit box and
+ * cell size dx_l = 2^-l; its cells are c = cx + 2cy + 4cz.  The father cell
+ * of oct (i,j,k,l) is cell (i,j,k) of level l-1, i.e. cell
+ * (i&1)+2(j&1)+4(k&1) of oct (i/2,j/2,k/2,l-1) (Sec. 2.1).  Host state
+ * arrays are structure-of-arrays: U[v * 8n + 8*oct + c], v = 0..4.  The base
+ * level must be complete and the tree graded: every oct of level l > levelmin
+ * needs the 27 level-(l-1) cells around its father cell.
+ *
+ * Errors.  Every call returns an amr_status and never aborts the process.
+ * CUDA failures map to AMR_ECUDA.  The text of the last error of the calling
+ * thread is returned by amr_last_error().  Asynchronous calls
+ * (amr_step_level, amr_advance) report device-side faults at the next
+ * synchronising call (amr_cfl_dt, amr_read, amr_sync).
+ *
+ * Threads.  A handle is not thread-safe; different handles may be used from
+ * different threads.
+ */
+#ifndef AMR_H
+#define AMR_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amr_mesh *amr_handle;
+
+typedef enum {
+  AMR_OK = 0,
+  AMR_EINVAL = 1,   /* bad argument, level, coordinate or size */
+  AMR_ENOMEM = 2,   /* allocation refused or over the handle's HBM budget */
+  AMR_EGRADING = 3, /* incomplete base level or 2:1 grading violated */
+  AMR_EDUP = 4,     /* the same oct listed twice */
+  AMR_ECUDA = 5,    /* a CUDA runtime error */
+  AMR_ETIMEOUT = 6, /* a bounded device-side wait gave up */
+  AMR_ENAN = 7      /* non-finite state met by the time-step reduction */
+} amr_status;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns a device pointer aligned to 256 bytes or NULL; free receives
+ * the pointer and the size that alloc returned it for.  Both are called with
+ * the handle's stream. */
+typedef void *(*amr_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*amr_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct {
+  int levelmin, levelmax;   /* 1 <= levelmin <= levelmax <= 15 */
+  double gamma;             /* ratio of specific heats, > 1 */
+  double cfl;               /* Courant number of amr_cfl_dt */
+  double smallr, smallc;    /* floors: rho >= smallr, p >= rho smallc^2 / gamma */
+  /* refinement thresholds of the regrid stage; stored, not used while the
+   * mesh is static */
+  double refine_grad_rho, refine_grad_p, refine_mass;
+  int precision;            /* 8: FP64 state and arithmetic; 4: FP32 state and
+                               arithmetic, FP64 time-step reduction */
+  int reflux;               /* 1: reflux at coarse-fine faces (default);
+                               0: off (a negative control for tests) */
+  int reindex_every_step;   /* 1: amr_advance rebuilds the hash table and the
+                               neighbour/cache index at the start of every
+                               coarse step, as after a regrid (default) */
+  int use_graphs;           /* 1: amr_advance replays a captured CUDA graph of
+                               one coarse step (default) */
+  size_t hbm_budget_bytes;  /* 0: no limit; else AMR_ENOMEM beyond it */
+  void *stream;             /* cudaStream_t; NULL: the legacy default stream */
+  amr_alloc_fn alloc;       /* NULL: cudaMallocAsync on the stream */
+  amr_free_fn free;
+  void *alloc_user;
+} amr_params;
+
+/* Fills p with the defaults: levelmin = levelmax = 1, gamma = 1.4, cfl = 0.8,
+ * smallr = smallc = 1e-10, precision 8, reflux 1, reindex_every_step 1,
+ * use_graphs 1, no budget, NULL stream and allocator. */
+void amr_params_default(amr_params *p);
+
+/*
+ * amr_create -- build a mesh from a host oct list (Sec. 2: oct array;
+ * Sec. 2.2: level bucket sort with prefix sums, Hilbert radix sort;
+ * Sec. 2.1: FNV-1a 64 hash with linear probing; Sec. 2.3: father/neighbour
+ * arrays and ghost cache).
+ *   n_oct          number of octs, >= 1 (the base level at least)
+ *   level,i,j,k    host arrays of n_oct entries, any order
+ *   hilbert_key    optional host array of n_oct sort keys within a level;
+ *                  NULL: the library computes the 3-D Hilbert index of
+ *                  (i,j,k) with l-1 bits per axis, x most significant
+ *   U              host array [5][8*n_oct] in the input order; values of
+ *                  split cells are ignored (replaced by the mean of their
+ *                  children)
+ *   out            receives the handle
+ * The inputs are copied; the caller keeps ownership of its buffers.  The call
+ * synchronises the stream.  Errors: AMR_EINVAL (arguments, levels,
+ * coordinates), AMR_EDUP, AMR_EGRADING, AMR_ENOMEM, AMR_ECUDA.
+ */
+amr_status amr_create(const amr_params *p, int64_t n_oct, const uint8_t *level,
+                      const uint32_t *i, const uint32_t *j, const uint32_t *k,
+                      const uint64_t *hilbert_key, const double *U, amr_handle *out);
+
+/* Frees every device buffer of the handle (after synchronising its stream). */
+amr_status amr_destroy(amr_handle h);
+
+/*
+ * amr_cfl_dt -- coarse time step (stage "compute dt" of Table 1):
+ * dt_l = cfl dx_l / max over leaf cells of level l of sum_d (|u_d| + c),
+ * dt = min over levels of dt_l 2^(l - levelmin).  FP64 warp-shuffle max
+ * reduction on the device; the result is copied to *dt_out (synchronous).
+ * Errors: AMR_ENAN if a leaf state is not finite.
+ */
+amr_status amr_cfl_dt(amr_handle h, double *dt_out);
+
+/*
+ * amr_step_level -- advance every oct of one level by dt (Sec. 3; stages
+ * godunov, set uold and upload of Table 1): ghost octs by minmod-limited
+ * prolongation from level-1, MUSCL-Hancock predictor, HLLC flux on every
+ * face, conservative update of leaf cells plus the pending reflux of the
+ * level (which is then cleared), reflux of coarse-fine face fluxes onto the
+ * level-1 cells (fixed-order segmented sum, no floating-point atomics), and
+ * restriction of the level onto its father cells.  Asynchronous on the
+ * handle's stream.  The caller runs levels in the W-cycle order: a level
+ * l < finest takes its step after the two half steps of level l+1.
+ * Errors: AMR_EINVAL for a level outside [levelmin, levelmax] or dt <= 0.
+ */
+amr_status amr_step_level(amr_handle h, int level, double dt);
+
+/*
+ * amr_advance -- n coarse steps of the level-by-level W-cycle: per coarse
+ * step (optionally) rebuild the index, dt = amr_cfl_dt computed on the device,
+ * then advance(levelmin, dt), where advance(l, dt) runs advance(l+1, dt/2)
+ * twice when level l+1 holds octs and then amr_step_level(l, dt).  No host
+ * synchronisation inside; with use_graphs the coarse step is one graph
+ * launch.  If dt_last is not NULL the call synchronises and stores the last
+ * coarse dt there.
+ */
+amr_status amr_advance(amr_handle h, int n_coarse_steps, double *dt_last);
+
+/* Rebuild the hash table, father/son flags, 27-neighbour array and ghost
+ * cache from the oct list (what a regrid triggers, Sec. 2.3).  Async. */
+amr_status amr_reindex(amr_handle h);
+
+/*
+ * amr_read -- copy out the octs of one level in the mesh order: packed keys
+ * key = (l << 60) | (i << 40) | (j << 20) | k, and U [5][8*n] as doubles.
+ * *n_oct_out receives the level's oct count; keys and U may be NULL; when not
+ * NULL they must hold cap octs (AMR_EINVAL if cap is smaller).  Synchronous.
+ */
+amr_status amr_read(amr_handle h, int level, int64_t *n_oct_out, uint64_t *keys,
+                    double *U, int64_t cap);
+
+/* Same as amr_read for the pending reflux R [5][8*n] of a level. */
+amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_t cap);
+
+/*
+ * amr_write -- replace the state of one level from a host array [5][8*n] in
+ * the mesh order of amr_read (for restarts and end-to-end runs).  Values of
+ * split cells are taken as given.  Pinned host memory makes the copy
+ * asynchronous; the host buffer must stay valid until the stream passes it.
+ */
+amr_status amr_write(amr_handle h, int level, const double *U, int64_t n);
+
+/* ---- index introspection (parity tests; not on the hot path) -------------- */
+
+/* hash_get of Sec. 2.1 for n host keys: idx_out[t] = mesh index of the oct
+ * (0-based, mesh order) or -1.  Synchronous. */
+amr_status amr_lookup(amr_handle h, int64_t n, const uint64_t *keys, int64_t *idx_out);
+
+/* The 27-entry neighbour array of a level, [n][27] in (dz,dy,dx) order
+ * (13 = self): >= 0 mesh index of a same-level oct, else -(1 + s) for ghost
+ * oct s of the cache; split flags [8n] (1 if the cell has a child oct).
+ * Either pointer may be NULL.  Synchronous. */
+amr_status amr_read_index(amr_handle h, int level, int64_t *nbr, uint8_t *split,
+                          int64_t cap);
+
+/* Ghost (cache) octs of a level: *n_out count, keys (sorted ascending),
+ * ghost values Ug [5][8*n] as last filled by a level step or amr_fill_ghosts.
+ * cache slot s of the neighbour array counts across levels; the first slot of
+ * a level is *first_out.  Synchronous. */
+amr_status amr_read_cache(amr_handle h, int level, int64_t *n_out, int64_t *first_out,
+                          uint64_t *keys, double *Ug, int64_t cap);
+
+/* Fill the ghost octs of a level from the current coarser levels (the first
+ * stage of amr_step_level), asynchronously. */
+amr_status amr_fill_ghosts(amr_handle h, int level);
+
+typedef struct {
+  int64_t n_oct, n_cache, n_leaf_cells;
+  int64_t level_octs[16], level_cache[16], level_leaf_cells[16];
+  int64_t device_bytes;       /* bytes held on the device */
+  int64_t kernel_launches;    /* kernels launched by the handle so far */
+  int64_t graph_launches;     /* CUDA graph launches so far */
+  int64_t hash_capacity;
+  int precision;
+} amr_info;
+
+/* Counts of the mesh and of the work done so far. */
+amr_status amr_get_info(amr_handle h, amr_info *info);
+
+/* Per-kernel device time.  amr_set_timing(h, 1) brackets every later kernel
+ * launch (also inside captured graphs) with CUDA events on the handle's
+ * stream; amr_read_timing synchronises and, for kernel id t < n, returns the
+ * total milliseconds and launch count since timing was enabled.
+ * amr_kernel_name(t) names kernel id t (NULL past the last). */
+amr_status amr_set_timing(amr_handle h, int on);
+amr_status amr_read_timing(amr_handle h, int n, double *ms, int64_t *launches);
+const char *amr_kernel_name(int t);
+
+/* Wait for the handle's stream and report any pending device-side error. */
+amr_status amr_sync(amr_handle h);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *amr_last_error(void);
+const char *amr_status_string(amr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

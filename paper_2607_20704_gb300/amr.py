@@ -1,0 +1,358 @@
+"""Python binding of the C ABI in ``include/amr.h`` (argument marshalling only).
+
+Every step of the mesh build, index and level step runs in the CUDA kernels
+of ``_build/libamr.so``.  There is no CPU fallback: if the library has not
+been built (``python -m paper_2607_20704_gb300.build`` or
+``__graft_entry__.build()``) or no GPU is visible, loading raises.
+
+PyTorch provides the stream the library runs on and, by default, its device
+memory (through the caching allocator, handed to the library as a callback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB
+
+NV = 5
+
+AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_EGRADING, AMR_EDUP, AMR_ECUDA, AMR_ETIMEOUT, AMR_ENAN = range(8)
+STATUS = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_EGRADING", 4: "AMR_EDUP",
+          5: "AMR_ECUDA", 6: "AMR_ETIMEOUT", 7: "AMR_ENAN"}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class amr_params(C.Structure):
+    _fields_ = [("levelmin", C.c_int), ("levelmax", C.c_int),
+                ("gamma", C.c_double), ("cfl", C.c_double),
+                ("smallr", C.c_double), ("smallc", C.c_double),
+                ("refine_grad_rho", C.c_double), ("refine_grad_p", C.c_double),
+                ("refine_mass", C.c_double),
+                ("precision", C.c_int), ("reflux", C.c_int),
+                ("reindex_every_step", C.c_int), ("use_graphs", C.c_int),
+                ("hbm_budget_bytes", C.c_size_t), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class amr_info(C.Structure):
+    _fields_ = [("n_oct", C.c_int64), ("n_cache", C.c_int64), ("n_leaf_cells", C.c_int64),
+                ("level_octs", C.c_int64 * 16), ("level_cache", C.c_int64 * 16),
+                ("level_leaf_cells", C.c_int64 * 16),
+                ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
+                ("graph_launches", C.c_int64), ("hash_capacity", C.c_int64),
+                ("precision", C.c_int)]
+
+
+class AmrError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+# exported symbols of the C ABI (checked by the CPU tests against amr.h)
+SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr_step_level",
+           "amr_advance", "amr_reindex", "amr_read", "amr_read_reflux", "amr_write",
+           "amr_lookup", "amr_read_index", "amr_read_cache", "amr_fill_ghosts", "amr_get_info",
+           "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
+           "amr_status_string"]
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run paper_2607_20704_gb300.build.build())")
+        L = C.CDLL(path)
+        P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "amr_params_default": (None, [C.POINTER(amr_params)]),
+            "amr_create": (I, [C.POINTER(amr_params), I64, P, P, P, P, P, P, C.POINTER(P)]),
+            "amr_destroy": (I, [P]),
+            "amr_cfl_dt": (I, [P, C.POINTER(D)]),
+            "amr_step_level": (I, [P, I, D]),
+            "amr_advance": (I, [P, I, P]),
+            "amr_reindex": (I, [P]),
+            "amr_read": (I, [P, I, C.POINTER(I64), P, P, I64]),
+            "amr_read_reflux": (I, [P, I, P, I64]),
+            "amr_write": (I, [P, I, P, I64]),
+            "amr_lookup": (I, [P, I64, P, P]),
+            "amr_read_index": (I, [P, I, P, P, I64]),
+            "amr_read_cache": (I, [P, I, C.POINTER(I64), C.POINTER(I64), P, P, I64]),
+            "amr_fill_ghosts": (I, [P, I]),
+            "amr_get_info": (I, [P, C.POINTER(amr_info)]),
+            "amr_set_timing": (I, [P, I]),
+            "amr_read_timing": (I, [P, I, P, P]),
+            "amr_kernel_name": (C.c_char_p, [I]),
+            "amr_sync": (I, [P]),
+            "amr_last_error": (C.c_char_p, []),
+            "amr_status_string": (C.c_char_p, [I]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(rc: int, where: str):
+    if rc != AMR_OK:
+        raise AmrError(rc, where, load().amr_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# -- PyTorch plumbing: streams and the caching allocator ----------------------
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device visible: the AMR library has no CPU path")
+    return torch
+
+
+@ALLOC_FN
+def _torch_alloc(nbytes, stream, user):
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:
+        return None
+
+
+@FREE_FN
+def _torch_free(ptr, nbytes, stream, user):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+def kernel_names():
+    L = load()
+    out = []
+    t = 0
+    while True:
+        n = L.amr_kernel_name(t)
+        if n is None:
+            return out
+        out.append(n.decode())
+        t += 1
+
+
+class Mesh:
+    """One resident octree (wraps an ``amr_handle``)."""
+
+    def __init__(self, level, i, j, k, U, *, levelmin, levelmax, gamma, cfl=0.8,
+                 smallr=1e-10, smallc=1e-10, precision=8, reflux=True,
+                 reindex_every_step=True, use_graphs=True, hbm_budget_bytes=0,
+                 hilbert_key=None, allocator="torch", stream=None):
+        torch = _torch()
+        L = load()
+        p = amr_params()
+        L.amr_params_default(C.byref(p))
+        p.levelmin, p.levelmax = int(levelmin), int(levelmax)
+        p.gamma, p.cfl, p.smallr, p.smallc = float(gamma), float(cfl), float(smallr), float(smallc)
+        p.precision = int(precision)
+        p.reflux = int(bool(reflux))
+        p.reindex_every_step = int(bool(reindex_every_step))
+        p.use_graphs = int(bool(use_graphs))
+        p.hbm_budget_bytes = int(hbm_budget_bytes)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        p.stream = C.c_void_p(self.stream.cuda_stream)
+        if allocator == "torch":
+            p.alloc, p.free = _torch_alloc, _torch_free
+        self.params = p
+        level = np.ascontiguousarray(level, dtype=np.uint8)
+        i = np.ascontiguousarray(i, dtype=np.uint32)
+        j = np.ascontiguousarray(j, dtype=np.uint32)
+        k = np.ascontiguousarray(k, dtype=np.uint32)
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        n = level.shape[0]
+        if U.shape != (NV, 8 * n):
+            raise ValueError(f"U must have shape (5, {8 * n}), got {U.shape}")
+        hk = None if hilbert_key is None else np.ascontiguousarray(hilbert_key, dtype=np.uint64)
+        h = C.c_void_p()
+        rc = L.amr_create(C.byref(p), n, _ptr(level), _ptr(i), _ptr(j), _ptr(k), _ptr(hk),
+                          _ptr(U), C.byref(h))
+        _check(rc, "amr_create")
+        self._h = h
+        self.levelmin, self.levelmax, self.gamma = int(levelmin), int(levelmax), float(gamma)
+        self.precision = int(precision)
+
+    # -- lifetime ----------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().amr_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- stepping ------------------------------------------------------------------
+    def cfl_dt(self) -> float:
+        dt = C.c_double()
+        _check(load().amr_cfl_dt(self._h, C.byref(dt)), "amr_cfl_dt")
+        return dt.value
+
+    def step_level(self, level: int, dt: float):
+        _check(load().amr_step_level(self._h, int(level), float(dt)), "amr_step_level")
+
+    def advance(self, n: int = 1, sync: bool = False):
+        if sync:
+            dt = C.c_double()
+            _check(load().amr_advance(self._h, int(n), C.byref(dt)), "amr_advance")
+            return dt.value
+        _check(load().amr_advance(self._h, int(n), None), "amr_advance")
+        return None
+
+    def reindex(self):
+        _check(load().amr_reindex(self._h), "amr_reindex")
+
+    def fill_ghosts(self, level: int):
+        _check(load().amr_fill_ghosts(self._h, int(level)), "amr_fill_ghosts")
+
+    def sync(self):
+        _check(load().amr_sync(self._h), "amr_sync")
+
+    # -- state -----------------------------------------------------------------------
+    def num_octs(self, level: int) -> int:
+        n = C.c_int64()
+        _check(load().amr_read(self._h, int(level), C.byref(n), None, None, 0), "amr_read")
+        return n.value
+
+    def read(self, level: int, out_U=None, keys=True):
+        n = self.num_octs(level)
+        kk = np.zeros(max(n, 1), np.uint64) if keys else None
+        U = out_U if out_U is not None else np.zeros((NV, 8 * max(n, 1)), np.float64)
+        cnt = C.c_int64()
+        _check(load().amr_read(self._h, int(level), C.byref(cnt), _ptr(kk), _ptr(U), max(n, 1)),
+               "amr_read")
+        return (kk[:n] if keys else None), U[:, :8 * n]
+
+    def read_reflux(self, level: int):
+        n = self.num_octs(level)
+        R = np.zeros((NV, 8 * max(n, 1)), np.float64)
+        _check(load().amr_read_reflux(self._h, int(level), _ptr(R), max(n, 1)), "amr_read_reflux")
+        return R[:, :8 * n]
+
+    def write(self, level: int, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        n = U.shape[1] // 8
+        _check(load().amr_write(self._h, int(level), _ptr(U), n), "amr_write")
+
+    # -- index introspection ---------------------------------------------------------
+    def lookup(self, keys):
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        out = np.zeros(max(len(keys), 1), np.int64)
+        _check(load().amr_lookup(self._h, len(keys), _ptr(keys), _ptr(out)), "amr_lookup")
+        return out[:len(keys)]
+
+    def read_index(self, level: int):
+        n = self.num_octs(level)
+        nb = np.zeros((max(n, 1), 27), np.int64)
+        sp = np.zeros(8 * max(n, 1), np.uint8)
+        _check(load().amr_read_index(self._h, int(level), _ptr(nb), _ptr(sp), max(n, 1)),
+               "amr_read_index")
+        return nb[:n], sp[:8 * n]
+
+    def read_cache(self, level: int):
+        n, first = C.c_int64(), C.c_int64()
+        L = load()
+        _check(L.amr_read_cache(self._h, int(level), C.byref(n), C.byref(first), None, None, 0),
+               "amr_read_cache")
+        nc = n.value
+        keys = np.zeros(max(nc, 1), np.uint64)
+        Ug = np.zeros((NV, 8 * max(nc, 1)), np.float64)
+        _check(L.amr_read_cache(self._h, int(level), C.byref(n), C.byref(first), _ptr(keys),
+                                _ptr(Ug), max(nc, 1)), "amr_read_cache")
+        return keys[:nc], Ug[:, :8 * nc], first.value
+
+    def info(self) -> dict:
+        inf = amr_info()
+        _check(load().amr_get_info(self._h, C.byref(inf)), "amr_get_info")
+        return {
+            "n_oct": inf.n_oct, "n_cache": inf.n_cache, "n_leaf_cells": inf.n_leaf_cells,
+            "level_octs": list(inf.level_octs), "level_cache": list(inf.level_cache),
+            "level_leaf_cells": list(inf.level_leaf_cells), "device_bytes": inf.device_bytes,
+            "kernel_launches": inf.kernel_launches, "graph_launches": inf.graph_launches,
+            "hash_capacity": inf.hash_capacity, "precision": inf.precision,
+        }
+
+    def set_timing(self, on: bool):
+        _check(load().amr_set_timing(self._h, int(bool(on))), "amr_set_timing")
+
+    def read_timing(self) -> dict:
+        names = kernel_names()
+        ms = np.zeros(len(names), np.float64)
+        n = np.zeros(len(names), np.int64)
+        _check(load().amr_read_timing(self._h, len(names), _ptr(ms), _ptr(n)), "amr_read_timing")
+        return {nm: (float(ms[t]), int(n[t])) for t, nm in enumerate(names) if n[t]}
+
+    def levels(self):
+        return [l for l in range(self.levelmin, self.levelmax + 1) if self.num_octs(l) > 0]
+
+
+# -- the C names, one thin wrapper each ---------------------------------------------
+def amr_create(prob_or_args, **kw) -> Mesh:
+    """``amr_create`` from an ``inputs.Problem`` or a (level, i, j, k, U) tuple."""
+    if hasattr(prob_or_args, "mesh_args"):
+        args = prob_or_args.mesh_args()
+        params = dict(prob_or_args.params())
+        params.update(kw)
+        return Mesh(*args, **params)
+    return Mesh(*prob_or_args, **kw)
+
+
+def amr_destroy(m: Mesh):
+    m.close()
+
+
+def amr_cfl_dt(m: Mesh) -> float:
+    return m.cfl_dt()
+
+
+def amr_step_level(m: Mesh, level: int, dt: float):
+    m.step_level(level, dt)
+
+
+def amr_advance(m: Mesh, n: int = 1, sync: bool = False):
+    return m.advance(n, sync=sync)
+
+
+def amr_read(m: Mesh, level: int):
+    return m.read(level)
+
+
+def amr_write(m: Mesh, level: int, U):
+    m.write(level, U)

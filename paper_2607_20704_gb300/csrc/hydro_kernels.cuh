@@ -1,0 +1,404 @@
+// hydro_kernels.cuh -- one AMR level step of compressible Euler (paper Sec. 3:
+// MUSCL-Hancock predictor-corrector with an HLLC Riemann solver and two
+// ghost cells per side; Sec. 2.3 ghost octs; Table 1 stages godunov /
+// set uold / upload), as non-redundant per-cell passes:
+//
+//   k_prolong   ghost octs of the level from their father cell (minmod)
+//   k_prim      primitive variables of every real and ghost cell
+//   k_predict   limited slopes and the Hancock half-step, once per cell
+//   k_flux      one HLLC flux per face (owned by the cell on its minus side)
+//   k_update    conservative update of leaf cells + pending reflux
+//   k_reflux    fixed-order sum of coarse-fine fluxes onto level l-1 cells
+//   k_restrict  father cell = mean of its 8 children
+//
+// The paper's kernels gather a 6x6x6 stencil per oct and recompute the
+// slopes and predictor of its ghost ring (8x work per cell at nsubgrid=1).
+// On GB300 the FP64 rate is far below the memory rate, so each cell's
+// predictor and each face's Riemann solve is computed exactly once and the
+// intermediate states go through L2/HBM instead.
+#pragma once
+#include "hydro_args.cuh"
+
+namespace amr {
+
+// ---------------------------------------------------------------------------
+// arithmetic helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double minmod(double a, double b) {
+  // 0 for opposite signs or a zero argument, else the argument of smaller
+  // magnitude; decided on the bit patterns (integer pipes, no FP64 issue)
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const long long ma = ia & 0x7FFFFFFFFFFFFFFFll, mb = ib & 0x7FFFFFFFFFFFFFFFll;
+  if (((ia ^ ib) < 0) | (ma == 0) | (mb == 0)) return 0.0;
+  return ma < mb ? a : b;
+}
+__device__ __forceinline__ float minmod(float a, float b) {
+  const int ia = __float_as_int(a), ib = __float_as_int(b);
+  const int ma = ia & 0x7FFFFFFF, mb = ib & 0x7FFFFFFF;
+  if (((ia ^ ib) < 0) | (ma == 0) | (mb == 0)) return 0.0f;
+  return ma < mb ? a : b;
+}
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
+
+template <class T>
+__device__ __forceinline__ double level_dt(const LevelArgs<T> &a) {
+  return a.dt_dev ? __ldg(a.dt_dev) * a.dt_scale : a.dt_host;
+}
+
+// extended oct index of local oct index q, and back
+template <class T>
+__device__ __forceinline__ int64_t ext_of_local(const LevelArgs<T> &a, int64_t q) {
+  return q < a.nl ? a.lo + q : a.N + a.clo + (q - a.nl);
+}
+template <class T>
+__device__ __forceinline__ int64_t local_of_ext(const LevelArgs<T> &a, int64_t e) {
+  return e < a.N ? e - a.lo : e - a.N - a.clo + a.nl;
+}
+
+// local index of the face neighbour of local cell t (extended oct e, cell c)
+// along axis d on side `plus`; -1 when the neighbouring oct does not exist
+template <class T>
+__device__ __forceinline__ int64_t nbr_local(const LevelArgs<T> &a, int64_t t, int64_t e, int c,
+                                             int d, int plus) {
+  const int bit = 1 << d;
+  if (((c >> d) & 1) != plus) return t ^ bit;
+  const int32_t ne = __ldg(a.fnb + (2 * d + plus) * a.NE + e);
+  if (ne < 0) return -1;
+  return 8 * local_of_ext(a, int64_t(ne)) + (c ^ bit);
+}
+
+template <class T>
+__device__ __forceinline__ bool cell_is_split(const LevelArgs<T> &a, int64_t t) {
+  const int64_t q = t >> 3;
+  if (q >= a.nl) return false;  // ghost cells are leaves
+  return (__ldg(a.son + a.lo + q) >> (t & 7)) & 1u;
+}
+
+// ---------------------------------------------------------------------------
+// ghost octs: child = U_C + sum_d (+-1/4) minmod(U(C+e_d)-U(C), U(C)-U(C-e_d))
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_prolong(LevelArgs<T> a) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 5 * a.ncl) return;
+  const int v = int(q / a.ncl);
+  const int64_t s = q % a.ncl;
+  const int64_t cs = a.clo + s;
+  const T *Uv = a.U + v * a.S;
+  T src[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) src[k] = Uv[__ldg(a.csrc + k * a.NC + cs)];
+  const T uc = src[0];
+  const T sx = minmod(src[2] - uc, uc - src[1]);
+  const T sy = minmod(src[4] - uc, uc - src[3]);
+  const T sz = minmod(src[6] - uc, uc - src[5]);
+  T *dst = a.U + v * a.S + 8 * (a.N + cs);
+  const T h = T(0.25);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const T hx = (c & 1) ? h : -h, hy = (c & 2) ? h : -h, hz = (c & 4) ? h : -h;
+    dst[c] = ((uc + hx * sx) + hy * sy) + hz * sz;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// primitives of every real and ghost cell of the level
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_prim(LevelArgs<T> a) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.LS) return;
+  const int64_t g = 8 * ext_of_local(a, t >> 3) + (t & 7);
+  const T u0 = a.U[g], u1 = a.U[a.S + g], u2 = a.U[2 * a.S + g], u3 = a.U[3 * a.S + g],
+          u4 = a.U[4 * a.S + g];
+  const T r = vmax(u0, a.smallr);
+  const T ir = T(1) / r;
+  const T vx = u1 * ir, vy = u2 * ir, vz = u3 * ir;
+  const T ek = T(0.5) * r * ((vx * vx + vy * vy) + vz * vz);
+  const T p = vmax((a.gamma - T(1)) * (u4 - ek), r * a.smallp);
+  a.W[t] = r;
+  a.W[a.LS + t] = vx;
+  a.W[2 * a.LS + t] = vy;
+  a.W[3 * a.LS + t] = vz;
+  a.W[4 * a.LS + t] = p;
+}
+
+// ---------------------------------------------------------------------------
+// limited slopes and Hancock predictor W* = W + dt/(2dx) S(W, dW)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_predict(LevelArgs<T> a) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.LS) return;
+  const int64_t e = ext_of_local(a, t >> 3);
+  const int c = int(t & 7);
+  T w[5], dw[3][5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) w[v] = a.W[v * a.LS + t];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t tm = nbr_local(a, t, e, c, d, 0);
+    const int64_t tp = nbr_local(a, t, e, c, d, 1);
+    if (tm < 0 || tp < 0) {  // outer ring of a ghost oct: never used
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
+      continue;
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const T wm = a.W[v * a.LS + tm], wp = a.W[v * a.LS + tp];
+      dw[d][v] = minmod(wp - w[v], w[v] - wm);
+    }
+  }
+  const T r = w[0], p = w[4], g = a.gamma;
+  const T ir = T(1) / r;
+  const T gp = g * p;
+  T s[5];
+  s[0] = -(((w[1] * dw[0][0] + r * dw[0][1]) + (w[2] * dw[1][0] + r * dw[1][2])) +
+           (w[3] * dw[2][0] + r * dw[2][3]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    s[1 + k] = -((w[1] * dw[0][1 + k] + w[2] * dw[1][1 + k]) + w[3] * dw[2][1 + k]) - dw[k][4] * ir;
+  s[4] = -(((w[1] * dw[0][4] + gp * dw[0][1]) + (w[2] * dw[1][4] + gp * dw[1][2])) +
+           (w[3] * dw[2][4] + gp * dw[2][3]));
+  const T hdt = T(0.5 * level_dt(a) * a.inv_dx);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) a.Q[v * a.LS + t] = w[v] + hdt * s[v];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) a.Q[(5 + 5 * d + v) * a.LS + t] = dw[d][v];
+}
+
+// ---------------------------------------------------------------------------
+// HLLC flux normal to axis d from face states qL, qR (rho, u, v, w, p):
+// S_L = min(u) - max(c), S_R = max(u) + max(c); star speed and pressure from
+// the two-wave HLL jump conditions; physical flux of the state sampled at
+// x/t = 0 (Toro's HLLC); transverse velocities from the upwind side.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void hllc(const T *qL, const T *qR, int d, T g, T *F) {
+  const int in = 1 + d;
+  const T rl = qL[0], ul = qL[in], pl = qL[4];
+  const T rr = qR[0], ur = qR[in], pr = qR[4];
+  const T igm1 = T(1) / (g - T(1));
+  const T el = pl * igm1 + T(0.5) * rl * ((qL[1] * qL[1] + qL[2] * qL[2]) + qL[3] * qL[3]);
+  const T er = pr * igm1 + T(0.5) * rr * ((qR[1] * qR[1] + qR[2] * qR[2]) + qR[3] * qR[3]);
+  const T cl = vsqrt(g * pl / rl), cr = vsqrt(g * pr / rr);
+  const T cmax = vmax(cl, cr);
+  const T sl = vmin(ul, ur) - cmax;
+  const T sr = vmax(ul, ur) + cmax;
+  const T rcl = rl * (ul - sl), rcr = rr * (sr - ur);
+  const T irc = T(1) / (rcl + rcr);
+  const T us = ((rcr * ur + rcl * ul) + (pl - pr)) * irc;
+  const T ps = ((rcr * pl + rcl * pr) + rcl * rcr * (ul - ur)) * irc;
+  T ro, uo, po, eo;
+  const T *qt;
+  if (sl > T(0)) {
+    ro = rl; uo = ul; po = pl; eo = el; qt = qL;
+  } else if (us > T(0)) {
+    const T id = T(1) / (sl - us);
+    ro = rl * (sl - ul) * id;
+    eo = ((sl - ul) * el - pl * ul + ps * us) * id;
+    uo = us; po = ps; qt = qL;
+  } else if (sr > T(0)) {
+    const T id = T(1) / (sr - us);
+    ro = rr * (sr - ur) * id;
+    eo = ((sr - ur) * er - pr * ur + ps * us) * id;
+    uo = us; po = ps; qt = qR;
+  } else {
+    ro = rr; uo = ur; po = pr; eo = er; qt = qR;
+  }
+  const T mf = ro * uo;
+  F[0] = mf;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) F[k] = (k == in) ? mf * uo + po : mf * qt[k];
+  F[4] = (eo + po) * uo;
+}
+
+// One thread per real or ghost cell: the fluxes of its three plus faces.
+// A face is needed when at least one side is a real cell and neither side
+// is split; other faces carry zero.  A needed face with a ghost on one side
+// is a coarse-fine face: its flux, times sigma dt/dx / 8, goes to slot
+// (direction seen from the coarse cell, fine face a,b) of the ghost oct.
+template <class T>
+__global__ void k_flux(LevelArgs<T> a) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.LS) return;
+  const int64_t q = t >> 3;
+  const int64_t e = ext_of_local(a, q);
+  const int c = int(t & 7);
+  const bool real = q < a.nl;
+  const bool split = cell_is_split(a, t);
+  const T dtdx = T(level_dt(a) * a.inv_dx);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T F[5] = {T(0), T(0), T(0), T(0), T(0)};
+    const int64_t tn = nbr_local(a, t, e, c, d, 1);
+    bool need = false, nreal = false;
+    if (tn >= 0) {
+      nreal = (tn >> 3) < a.nl;
+      need = (real || nreal) && !split && !cell_is_split(a, tn);
+    }
+    if (need) {
+      T qL[5], qR[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const T half_l = T(0.5) * a.Q[(5 + 5 * d + v) * a.LS + t];
+        const T half_r = T(0.5) * a.Q[(5 + 5 * d + v) * a.LS + tn];
+        qL[v] = a.Q[v * a.LS + t] + half_l;
+        qR[v] = a.Q[v * a.LS + tn] - half_r;
+      }
+      qL[0] = vmax(qL[0], a.smallr);
+      qR[0] = vmax(qR[0], a.smallr);
+      qL[4] = vmax(qL[4], qL[0] * a.smallp);
+      qR[4] = vmax(qR[4], qR[0] * a.smallp);
+      hllc(qL, qR, d, a.gamma, F);
+      if (a.reflux && (real != nreal)) {
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        const int ab = (((c >> d1) & 1) << 1) | ((c >> d2) & 1);
+        int64_t gslot;
+        T sg;
+        if (real) {  // ghost on the plus side: the face is the coarse cell's minus face
+          gslot = (a.clo + (tn >> 3) - a.nl) * 24 + (2 * d) * 4 + ab;
+          sg = T(1);
+        } else {     // ghost on the minus side: the coarse cell's plus face
+          gslot = (a.clo + q - a.nl) * 24 + (2 * d + 1) * 4 + ab;
+          sg = T(-1);
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (sg * dtdx) * F[v] / T(8);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) a.F[(5 * d + v) * a.LS + t] = F[v];
+  }
+}
+
+// U <- U + dt/dx sum_d (F_d- - F_d+) + R on leaf cells; R <- 0
+template <class T>
+__global__ void k_update(LevelArgs<T> a) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= 8 * a.nl) return;
+  if (cell_is_split(a, t)) return;
+  const int64_t e = a.lo + (t >> 3);
+  const int c = int(t & 7);
+  int64_t tm[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) tm[d] = nbr_local(a, t, e, c, d, 0);
+  const T dtdx = T(level_dt(a) * a.inv_dx);
+  const int64_t g = 8 * e + c;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const T dx = a.F[(0 + v) * a.LS + tm[0]] - a.F[(0 + v) * a.LS + t];
+    const T dy = a.F[(5 + v) * a.LS + tm[1]] - a.F[(5 + v) * a.LS + t];
+    const T dz = a.F[(10 + v) * a.LS + tm[2]] - a.F[(10 + v) * a.LS + t];
+    const T du = (dx + dy) + dz;
+    T *Ug = a.U + v * a.S + g;
+    T *Rg = a.R + v * a.RS + g;
+    *Ug = (*Ug + dtdx * du) + *Rg;
+    *Rg = T(0);
+  }
+}
+
+// R_{l-1}[X] += sum of the 24 slots of the ghost oct whose father is X,
+// in slot order (direction -x,+x,-y,+y,-z,+z seen from X, then fine face)
+template <class T>
+__global__ void k_reflux(LevelArgs<T> a) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 5 * a.ncl) return;
+  const int v = int(q / a.ncl);
+  const int64_t s = q % a.ncl;
+  const int64_t X = __ldg(a.csrc + a.clo + s);
+  const T *cv = a.C + v * a.CS + 24 * (a.clo + s);
+  T acc = a.R[v * a.RS + X];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) acc += cv[k];
+  a.R[v * a.RS + X] = acc;
+}
+
+// father cell = (sum of the 8 children in child order) / 8
+template <class T>
+__global__ void k_restrict(LevelArgs<T> a) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 5 * a.nl) return;
+  const int v = int(q / a.nl);
+  const int64_t o = a.lo + q % a.nl;
+  const uint64_t k = __ldg(a.key + o);
+  const int fc = int((key_x(k) & 1) | ((key_y(k) & 1) << 1) | ((key_z(k) & 1) << 2));
+  const int64_t f = __ldg(a.father + o);
+  const T *src = a.U + v * a.S + 8 * o;
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += src[c];
+  a.U[v * a.S + 8 * f + fc] = s * T(0.125);
+}
+
+// ---------------------------------------------------------------------------
+// CFL time step: per-level FP64 max of sum_d (|u_d| + c) over leaf cells,
+// warp-shuffle reduction, one integer atomicMax per warp on the bit pattern
+// (non-negative doubles order like their bits), then dt on one thread.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_cfl(CflArgs a, const T *U) {
+  const int l = a.lmin + blockIdx.y;
+  const int64_t lo = a.lo[l], n8 = 8 * (a.lo[l + 1] - lo);
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  double s = 0.0;
+  if (t < n8 && !((__ldg(a.son + lo + (t >> 3)) >> (t & 7)) & 1u)) {
+    const int64_t g = 8 * lo + t;
+    const double u0 = double(U[g]), u1 = double(U[a.S + g]), u2 = double(U[2 * a.S + g]),
+                 u3 = double(U[3 * a.S + g]), u4 = double(U[4 * a.S + g]);
+    const double r = fmax(u0, a.smallr);
+    const double vx = u1 / r, vy = u2 / r, vz = u3 / r;
+    const double ek = 0.5 * r * ((vx * vx + vy * vy) + vz * vz);
+    const double p = fmax((a.gamma - 1.0) * (u4 - ek), r * a.smallp);
+    const double cs = sqrt(a.gamma * p / r);
+    s = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
+    if (!isfinite(s) || !isfinite(u0 + u1 + u2 + u3 + u4)) {
+      atomicOr(a.err, kErrNaN);
+      s = 0.0;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+  if ((threadIdx.x & 31) == 0 && s > 0.0)
+    atomicMax(a.smax + l, (unsigned long long)__double_as_longlong(s));
+}
+
+__global__ void k_dt(CflArgs a) {
+  double dt = __longlong_as_double(0x7FF0000000000000ll);  // +inf
+  for (int l = a.lmin; l <= a.lmax; ++l) {
+    const unsigned long long b = a.smax[l];
+    a.smax[l] = 0ull;
+    if (b == 0ull) continue;
+    const double smax = __longlong_as_double((long long)b);
+    const double dtl = a.cfl * ldexp(1.0, -l) / smax;
+    const double dtc = dtl * ldexp(1.0, l - a.lmin);
+    dt = fmin(dt, dtc);
+  }
+  *a.dt_dev = dt;
+}
+
+template <class T>
+__global__ void k_to_double(const T *src, int64_t src_stride, int64_t count, double *dst) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 5 * count) return;
+  const int v = int(q / count);
+  dst[q] = double(src[v * src_stride + q % count]);
+}
+template <class T>
+__global__ void k_from_double(const double *src, int64_t count, T *dst, int64_t dst_stride) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 5 * count) return;
+  const int v = int(q / count);
+  dst[v * dst_stride + q % count] = T(src[q]);
+}
+
+
+}  // namespace amr

@@ -1,0 +1,377 @@
+// index_kernels.cuh -- create-time and re-index kernels: oct ordering (level
+// bucket sort with prefix sums after a Hilbert-key LSD radix sort, Sec. 2.2),
+// the FNV-1a 64 linear-probing hash table (Sec. 2.1), father/son flags,
+// the 27-entry neighbour array and the ghost-oct cache (Sec. 2.3).
+#pragma once
+#include "amr_internal.cuh"
+
+namespace amr {
+
+// ---------------------------------------------------------------------------
+// input validation and sort keys
+// ---------------------------------------------------------------------------
+__global__ void k_make_sort_keys(const uint8_t *__restrict__ lvl, const uint32_t *__restrict__ ci,
+                                 const uint32_t *__restrict__ cj, const uint32_t *__restrict__ ck,
+                                 const uint64_t *__restrict__ hkey_in, int64_t n, int lmin, int lmax,
+                                 uint64_t *__restrict__ comp, uint32_t *__restrict__ perm,
+                                 int *__restrict__ err) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const int l = lvl[t];
+  uint64_t h = 0;
+  if (l < lmin || l > lmax) {
+    atomicOr(err, kErrRange);
+  } else {
+    const uint32_t side = 1u << (l - 1);
+    if (ci[t] >= side || cj[t] >= side || ck[t] >= side) atomicOr(err, kErrRange);
+    h = hkey_in ? hkey_in[t] : hilbert_index(ci[t], cj[t], ck[t], l - 1);
+    if (h >> 58) atomicOr(err, kErrRange);
+  }
+  comp[t] = (uint64_t(l & 15) << 58) | (h & ((1ull << 58) - 1));
+  perm[t] = uint32_t(t);
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (u64 key, u32 value) pairs, one item per thread,
+// 256-item tiles: tile histograms -> exclusive scan (digit-major) -> scatter
+// with warp-level ranks (__match_any_sync) and a warp-ordered prefix.
+// ---------------------------------------------------------------------------
+constexpr int kRadixTile = 256;
+constexpr int kTile = kRadixTile;
+
+__global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, int nbits,
+                             uint32_t *__restrict__ table, int64_t ntiles) {
+  __shared__ uint32_t hist[256];
+  const int ndig = 1 << nbits;
+  for (int d = threadIdx.x; d < ndig; d += blockDim.x) hist[d] = 0;
+  __syncthreads();
+  const int64_t t = blockIdx.x * int64_t(kTile) + threadIdx.x;
+  if (t < n) atomicAdd(&hist[(keys[t] >> shift) & uint64_t(ndig - 1)], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < ndig; d += blockDim.x) table[int64_t(d) * ntiles + blockIdx.x] = hist[d];
+}
+
+__global__ void k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
+                                int shift, int nbits, const uint32_t *__restrict__ offs,
+                                int64_t ntiles) {
+  __shared__ uint32_t wcnt[kTile / 32][256];
+  const int ndig = 1 << nbits;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = threadIdx.x; q < (kTile / 32) * 256; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+  __syncthreads();
+  const int64_t t = blockIdx.x * int64_t(kTile) + threadIdx.x;
+  const bool valid = t < n;
+  const uint64_t k = valid ? kin[t] : 0;
+  const uint32_t v = valid ? vin[t] : 0;
+  const unsigned dig = valid ? unsigned((k >> shift) & uint64_t(ndig - 1)) : 0xFFFFFFFFu;
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
+  const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+  if (valid && rank == 0) wcnt[warp][dig] = __popc(peers);
+  __syncthreads();
+  for (int d = threadIdx.x; d < ndig; d += blockDim.x) {
+    uint32_t run = 0;
+    for (int w = 0; w < kTile / 32; ++w) {
+      const uint32_t c = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    const uint32_t dst = offs[int64_t(dig) * ntiles + blockIdx.x] + wcnt[warp][dig] + rank;
+    kout[dst] = k;
+    vout[dst] = v;
+  }
+}
+
+// exclusive scan of u32, 1024 items per block
+constexpr int kScanItems = 1024;
+constexpr int kScanBlock = kScanItems;
+
+__global__ void k_scan_block(uint32_t *__restrict__ data, int64_t n, uint32_t *__restrict__ sums) {
+  __shared__ uint32_t s[kScanBlock];
+  const int64_t base = blockIdx.x * int64_t(kScanBlock);
+  for (int q = threadIdx.x; q < kScanBlock; q += blockDim.x) {
+    const int64_t t = base + q;
+    s[q] = t < n ? data[t] : 0u;
+  }
+  __syncthreads();
+  // Hillis-Steele on 1024 items with 256 threads: each thread owns 4 items
+  const int q0 = threadIdx.x * 4;
+  uint32_t a0 = s[q0], a1 = s[q0 + 1], a2 = s[q0 + 2], a3 = s[q0 + 3];
+  const uint32_t tot = a0 + a1 + a2 + a3;
+  __shared__ uint32_t part[256];
+  part[threadIdx.x] = tot;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const uint32_t x = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += x;
+    __syncthreads();
+  }
+  const uint32_t excl = part[threadIdx.x] - tot;
+  s[q0] = excl;
+  s[q0 + 1] = excl + a0;
+  s[q0 + 2] = excl + a0 + a1;
+  s[q0 + 3] = excl + a0 + a1 + a2;
+  if (threadIdx.x == 255) sums[blockIdx.x] = part[255];
+  __syncthreads();
+  for (int q = threadIdx.x; q < kScanBlock; q += blockDim.x) {
+    const int64_t t = base + q;
+    if (t < n) data[t] = s[q];
+  }
+}
+
+__global__ void k_scan_add(uint32_t *__restrict__ data, int64_t n, const uint32_t *__restrict__ sums) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < n) data[t] += sums[t / kScanBlock];
+}
+
+// ---------------------------------------------------------------------------
+// gather octs and state into mesh order
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_gather_octs(const uint32_t *__restrict__ perm, const uint8_t *__restrict__ lvl,
+                              const uint32_t *__restrict__ ci, const uint32_t *__restrict__ cj,
+                              const uint32_t *__restrict__ ck, const double *__restrict__ Uin,
+                              int64_t n, uint64_t *__restrict__ key, T *__restrict__ U, int64_t S,
+                              uint32_t *__restrict__ level_count) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t s = perm[t];
+  key[t] = key_pack(lvl[s], ci[s], cj[s], ck[s]);
+  if (level_count) atomicAdd(level_count + lvl[s], 1u);
+  if (!U) return;
+  for (int v = 0; v < kNV; ++v)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) U[v * S + 8 * t + c] = T(Uin[v * 8 * n + 8 * int64_t(s) + c]);
+}
+
+// ---------------------------------------------------------------------------
+// hash table build, father/son, grading
+// ---------------------------------------------------------------------------
+__global__ void k_hash_insert(HashView h, const uint64_t *__restrict__ key, int64_t n, int *err) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  bool ins = false;
+  const uint64_t s = hash_insert(h, key[t], &ins, err);
+  if (s == ~0ull) return;
+  if (!ins) {
+    atomicOr(err, kErrDup);
+    return;
+  }
+  h.val[s] = int32_t(t + 1);
+}
+
+__global__ void k_father_son(HashView h, const uint64_t *__restrict__ key, int64_t first, int64_t n,
+                             int32_t *__restrict__ father, uint32_t *__restrict__ son, int *err) {
+  const int64_t t = first + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const uint64_t k = key[t];
+  const int l = key_lev(k);
+  const uint32_t x = key_x(k), y = key_y(k), z = key_z(k);
+  const int32_t v = hash_probe1(h, key_pack(l - 1, x >> 1, y >> 1, z >> 1));
+  if (v <= 0) {
+    atomicOr(err, kErrGrading);
+    father[t] = -1;
+    return;
+  }
+  father[t] = v - 1;
+  atomicOr(son + (v - 1), 1u << ((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)));
+}
+
+// 27 level-(l-1) cells around the father cell of each oct above levelmin
+__global__ void k_grading(HashView h, const uint64_t *__restrict__ key, int64_t first, int64_t n,
+                          int *err) {
+  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 3;
+  const int64_t t = first + q / 27;
+  if (t >= n) return;
+  const int e = int(q % 27);
+  const uint64_t k = key[t];
+  const int l = key_lev(k);
+  const int64_t cells = int64_t(1) << (l - 1);
+  const uint32_t x = wrapc(int64_t(key_x(k)) + (e % 3) - 1, cells);
+  const uint32_t y = wrapc(int64_t(key_y(k)) + (e / 3 % 3) - 1, cells);
+  const uint32_t z = wrapc(int64_t(key_z(k)) + (e / 9) - 1, cells);
+  const int32_t v = hash_probe8(h, key_pack(l - 1, x >> 1, y >> 1, z >> 1));
+  if (v <= 0 && (threadIdx.x & 7) == 0) atomicOr(err, kErrGrading);
+}
+
+// ---------------------------------------------------------------------------
+// 27-neighbour array; missing neighbours are claimed as ghost keys
+// ---------------------------------------------------------------------------
+__global__ void k_neighbours(HashView h, const uint64_t *__restrict__ key, int64_t n,
+                             int32_t *__restrict__ nbr27, uint64_t *__restrict__ claim,
+                             uint32_t *__restrict__ claim_count, int64_t claim_cap, int *err) {
+  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 3;
+  const int64_t t = q / 27;
+  if (t >= n) return;
+  const int e = int(q % 27);
+  const bool leader = (threadIdx.x & 7) == 0;
+  if (e == 13) {
+    if (leader) nbr27[13 * n + t] = int32_t(t);
+    return;
+  }
+  const uint64_t k = key[t];
+  const int l = key_lev(k);
+  const int64_t side = int64_t(1) << (l - 1);
+  const uint64_t nk = key_pack(l, wrapc(int64_t(key_x(k)) + (e % 3) - 1, side),
+                               wrapc(int64_t(key_y(k)) + (e / 3 % 3) - 1, side),
+                               wrapc(int64_t(key_z(k)) + (e / 9) - 1, side));
+  const int32_t v = hash_probe8(h, nk);
+  if (!leader) return;
+  if (v >= 1 && int64_t(v) <= n) {
+    nbr27[int64_t(e) * n + t] = v - 1;
+    return;
+  }
+  nbr27[int64_t(e) * n + t] = -1;
+  bool ins = false;
+  const uint64_t s = hash_insert(h, nk, &ins, err);
+  if (ins && s != ~0ull) {
+    h.val[s] = kPending;
+    const uint32_t slot = atomicAdd(claim_count, 1u);
+    if (int64_t(slot) < claim_cap)
+      claim[slot] = nk;
+    else
+      atomicOr(err, kErrClaimOverflow);
+  }
+}
+
+// compact sort key of a ghost key: (l, x, y, z) with B bits per coordinate
+__global__ void k_claim_to_comp(const uint64_t *__restrict__ claim, int64_t nc, int B,
+                                uint64_t *__restrict__ comp, uint32_t *__restrict__ val) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nc) return;
+  const uint64_t k = claim[t];
+  comp[t] = (uint64_t(key_lev(k)) << (3 * B)) | (uint64_t(key_x(k)) << (2 * B)) |
+            (uint64_t(key_y(k)) << B) | uint64_t(key_z(k));
+  val[t] = 0;
+}
+
+__global__ void k_cache_finalize(HashView h, const uint64_t *__restrict__ comp, int64_t nc, int B,
+                                 int64_t N, uint64_t *__restrict__ ckey,
+                                 uint32_t *__restrict__ level_count, int *err) {
+  const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (s >= nc) return;
+  const uint64_t c = comp[s];
+  const uint64_t m = (1ull << B) - 1;
+  const int l = int(c >> (3 * B));
+  const uint64_t k = key_pack(l, uint32_t((c >> (2 * B)) & m), uint32_t((c >> B) & m), uint32_t(c & m));
+  ckey[s] = k;
+  atomicAdd(level_count + l, 1u);
+  uint64_t p = fnv1a64(k) & h.mask;
+  for (uint64_t r = 0; r <= h.mask; ++r) {
+    if (h.key[p] == k) {
+      h.val[p] = int32_t(N + s + 1);
+      return;
+    }
+    p = (p + 1) & h.mask;
+  }
+  atomicOr(err, kErrCacheMismatch);
+}
+
+__global__ void k_neighbours_fix(HashView h, const uint64_t *__restrict__ key, int64_t n,
+                                 int32_t *__restrict__ nbr27, int *err) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 27 * n) return;
+  if (nbr27[q] >= 0) return;
+  const int64_t t = q % n;
+  const int e = int(q / n);
+  const uint64_t k = key[t];
+  const int l = key_lev(k);
+  const int64_t side = int64_t(1) << (l - 1);
+  const uint64_t nk = key_pack(l, wrapc(int64_t(key_x(k)) + (e % 3) - 1, side),
+                               wrapc(int64_t(key_y(k)) + (e / 3 % 3) - 1, side),
+                               wrapc(int64_t(key_z(k)) + (e / 9) - 1, side));
+  const int32_t v = hash_probe1(h, nk);
+  if (v <= n || v == kPending) {
+    atomicOr(err, kErrCacheMismatch);
+    return;
+  }
+  nbr27[q] = v - 1;
+}
+
+// face-neighbour table of the extended oct range (real octs, then ghosts)
+__global__ void k_faces_real(const int32_t *__restrict__ nbr27, int64_t n, int64_t next,
+                             int32_t *__restrict__ fnb) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 6 * n) return;
+  const int f = int(q / n);
+  const int64_t t = q % n;
+  fnb[int64_t(f) * next + t] = nbr27[int64_t(face_to_nbr27(f)) * n + t];
+}
+
+__global__ void k_faces_cache(HashView h, const uint64_t *__restrict__ ckey, int64_t nc, int64_t N,
+                              int64_t next, int32_t *__restrict__ fnb) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 6 * nc) return;
+  const int f = int(q / nc);
+  const int64_t s = q % nc;
+  const uint64_t k = ckey[s];
+  const int l = key_lev(k);
+  const int64_t side = int64_t(1) << (l - 1);
+  const int d = f >> 1, sg = (f & 1) ? 1 : -1;
+  const uint64_t nk = key_pack(l, wrapc(int64_t(key_x(k)) + (d == 0 ? sg : 0), side),
+                               wrapc(int64_t(key_y(k)) + (d == 1 ? sg : 0), side),
+                               wrapc(int64_t(key_z(k)) + (d == 2 ? sg : 0), side));
+  const int32_t v = hash_probe1(h, nk);
+  fnb[int64_t(f) * next + N + s] = (v >= 1 && v != kPending) ? v - 1 : -1;
+}
+
+// cell of level L at cell coordinates (x,y,z), or the coarser cell covering
+// it when its oct is absent; -1 if none down to levelmin.
+__device__ int64_t cell_or_coarser(HashView h, int L, int64_t x, int64_t y, int64_t z, int lmin,
+                                   int64_t N, int *found_level) {
+  while (L >= lmin) {
+    const int64_t side = int64_t(1) << L;
+    const uint32_t X = wrapc(x, side), Y = wrapc(y, side), Z = wrapc(z, side);
+    const int32_t v = hash_probe1(h, key_pack(L, X >> 1, Y >> 1, Z >> 1));
+    if (v >= 1 && int64_t(v) <= N) {
+      *found_level = L;
+      return 8 * int64_t(v - 1) + ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2));
+    }
+    x = X >> 1;
+    y = Y >> 1;
+    z = Z >> 1;
+    --L;
+  }
+  return -1;
+}
+
+// prolongation sources of each ghost oct: its father cell C and C -/+ e_d
+// for d = x, y, z (order C, -x, +x, -y, +y, -z, +z); C is also the coarse
+// cell that receives the reflux of the ghost's faces.
+__global__ void k_cache_sources(HashView h, const uint64_t *__restrict__ ckey, int64_t nc, int64_t N,
+                                int lmin, int32_t *__restrict__ csrc, int *err) {
+  const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (s >= nc) return;
+  const uint64_t k = ckey[s];
+  const int l = key_lev(k);
+  const int64_t x = key_x(k), y = key_y(k), z = key_z(k);
+  for (int q = 0; q < 7; ++q) {
+    const int d = (q - 1) >> 1;
+    const int sg = (q & 1) ? -1 : 1;
+    const int64_t dx = (q > 0 && d == 0) ? sg : 0, dy = (q > 0 && d == 1) ? sg : 0,
+                  dz = (q > 0 && d == 2) ? sg : 0;
+    int fl = -1;
+    const int64_t c = cell_or_coarser(h, l - 1, x + dx, y + dy, z + dz, lmin, N, &fl);
+    if (c < 0 || (q == 0 && fl != l - 1)) {
+      atomicOr(err, kErrGrading);
+      csrc[int64_t(q) * nc + s] = 0;
+      continue;
+    }
+    csrc[int64_t(q) * nc + s] = int32_t(c);
+  }
+}
+
+// hash_get for a batch of keys (introspection)
+__global__ void k_lookup(HashView h, const uint64_t *__restrict__ keys, int64_t nq, int64_t N,
+                         int64_t *__restrict__ out) {
+  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 3;
+  if (q >= nq) return;
+  const int32_t v = hash_probe8(h, keys[q]);
+  if ((threadIdx.x & 7) == 0) out[q] = (v >= 1 && int64_t(v) <= N) ? int64_t(v - 1) : -1;
+}
+
+}  // namespace amr

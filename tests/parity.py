@@ -1,0 +1,48 @@
+"""Helpers of the GPU-vs-oracle parity tests.
+
+Tolerance (FP64 state, one step from identical inputs): per variable v,
+|gpu - oracle| <= rtol * max(|oracle|, s_v), s_v = max |U_v| over the
+level.  rtol = 1e-12 per level step; the W-cycle tests that chain many
+level steps from one initial state allow 1e-11 (round-off is re-amplified
+by the nonlinear limiter/Riemann steps that follow)."""
+import numpy as np
+
+from paper_2607_20704_gb300 import inputs
+
+
+def close(gpu, orc, rtol, what=""):
+    gpu = np.asarray(gpu)
+    orc = np.asarray(orc)
+    assert gpu.shape == orc.shape, (what, gpu.shape, orc.shape)
+    if orc.size == 0:
+        return 0.0
+    s = np.abs(orc).max(axis=1, keepdims=True)
+    scale = np.maximum(np.abs(orc), s)
+    scale[scale == 0] = 1.0
+    err = np.abs(gpu - orc) / scale
+    worst = float(err.max())
+    assert worst <= rtol, f"{what}: max scaled error {worst:.3e} > {rtol:.1e} at {np.unravel_index(err.argmax(), err.shape)}"
+    return worst
+
+
+def pair(prob, gpu_kw=None, orc_kw=None):
+    import oracle
+    from paper_2607_20704_gb300 import amr
+    g = amr.Mesh(*prob.mesh_args(), **prob.params(), **(gpu_kw or {}))
+    o = oracle.Mesh(*prob.mesh_args(), **prob.params(), **(orc_kw or {}))
+    return g, o
+
+
+def compare_all(g, o, rtol, levels=None, reflux=True):
+    worst = 0.0
+    for l in levels or o.levels():
+        kg, Ug = g.read(l)
+        ko, Uo = o.read(l)
+        assert np.array_equal(kg, ko), f"level {l} order differs"
+        worst = max(worst, close(Ug, Uo, rtol, f"U level {l}"))
+        if reflux:
+            Rg, Ro = g.read_reflux(l), o.read_R(l)
+            s = np.maximum(np.abs(Uo).max(axis=1, keepdims=True), 1e-300)
+            err = float((np.abs(Rg - Ro) / s).max()) if Ro.size else 0.0
+            assert err <= rtol, f"R level {l}: {err:.3e}"
+    return worst
