@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Throughput of the AMR level advance on GB300: leaf cell-updates/s.
+
+Workload: the Sedov blast on a static graded octree, levels 7-10 (128^3 base
+cells, nested refined balls of radius 0.12 / 0.06 / 0.03 around the centre,
+about 2.4 M leaf cells), gamma = 5/3, synthetic seeded input.  One step is
+one coarse time step of the level-by-level W-cycle through the C ABI
+(amr_advance): rebuild of the hash table, neighbour array and ghost cache,
+device CFL reduction, then every level step (ghosts, primitives, predictor,
+HLLC fluxes, update, reflux, restriction) with 2^(l-7) substeps per level.
+The unit of work is one leaf cell advanced by one level step.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "sedov_l7-10_static_nested_balls"
+L2_FLUSH_BYTES = 256 << 20
+WORD = {8: 8, 4: 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=8, choices=[4, 8],
+                    help="state precision of the headline value (the other is reported beside it)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--profile-level", type=int, default=0,
+                    help="profiling mode: build the mesh and run one eager level step of this "
+                         "level (one launch of each level-step kernel), then exit")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def work_per_step(info, levelmin):
+    """Leaf cell-updates of one coarse step: level l runs 2^(l-levelmin) times."""
+    return sum(info["level_leaf_cells"][l] * 2 ** (l - levelmin)
+               for l in range(levelmin, 16) if info["level_octs"][l])
+
+
+# -- clocks ----------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons, pw = [], [], set(), []
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(pw) if pw else None}
+
+
+# -- roofline bookkeeping -----------------------------------------------------------
+def kernel_traffic(info, levelmin, w):
+    """Algorithmic bytes of one coarse step per kernel: each kernel's inputs
+    read once and outputs written once (w = bytes per word).
+      prim     U in, W out                      10 w per real+ghost cell
+      predict  W in, (W*, dW) out               25 w per real+ghost cell
+      flux     (W*, dW) in, F out               35 w per real+ghost cell
+      update   F in, U and R in/out             35 w per real cell
+      prolong  7 source cells in, 8 ghosts out  75 w per ghost oct
+      reflux   24 slots in, R in/out           130 w per ghost oct
+      restrict 8 children in, father out        45 w per real oct (l > lmin)
+    """
+    out = {k: 0.0 for k in ("prim", "predict", "flux", "update", "prolong", "reflux", "restrict")}
+    for l in range(levelmin, 16):
+        n, nc = info["level_octs"][l], info["level_cache"][l]
+        if not n:
+            continue
+        reps = 2 ** (l - levelmin)
+        cells = 8 * (n + nc)
+        out["prim"] += reps * cells * 10 * w
+        out["predict"] += reps * cells * 25 * w
+        out["flux"] += reps * cells * 35 * w
+        out["update"] += reps * 8 * n * 35 * w
+        out["prolong"] += reps * nc * 75 * w
+        out["reflux"] += reps * nc * 130 * w
+        if l > levelmin:
+            out["restrict"] += reps * n * 45 * w
+    return out
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+# -- our arm ----------------------------------------------------------------------
+def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=True):
+    from paper_2607_20704_gb300 import amr
+    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision)
+    info = mesh.info()
+    upd = work_per_step(info, prob.levelmin)
+    st = mesh.stream
+    for _ in range(warmup):
+        mesh.advance(1)
+        with torch.cuda.stream(st):
+            flush_l2(flush)
+    torch.cuda.synchronize(device)
+    launches0 = mesh.info()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    wall0 = time.perf_counter()
+    for e0, e1 in ev:
+        e0.record(st)
+        mesh.advance(1)
+        e1.record(st)
+        with torch.cuda.stream(st):
+            flush_l2(flush)
+    torch.cuda.synchronize(device)
+    wall = time.perf_counter() - wall0
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    launches = mesh.info()["kernel_launches"] - launches0
+    res = {"ms": ms, "wall_s": wall, "updates_per_step": upd, "launches": launches, "info": info}
+    mesh.close()
+    if kernels:
+        # per-kernel device time: same K steps, each launch bracketed by CUDA
+        # events on the library's stream (eager launches, no graph)
+        m2 = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision)
+        for _ in range(warmup):
+            m2.advance(1)
+        m2.sync()
+        m2.set_timing(True)
+        for _ in range(steps):
+            m2.advance(1)
+            with torch.cuda.stream(m2.stream):
+                flush_l2(flush)
+        res["kernels"] = m2.read_timing()
+        m2.close()
+    return res
+
+
+def run_e2e(prob, precision, steps, torch):
+    """Same metric through the public API with host buffers: per step, upload
+    every level's state from pinned host memory, advance one coarse step,
+    read every level back (synchronous)."""
+    from paper_2607_20704_gb300 import amr
+    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision)
+    info = mesh.info()
+    upd = work_per_step(info, prob.levelmin)
+    levels = mesh.levels()
+    host = {}
+    for l in levels:
+        n = mesh.num_octs(l)
+        t = torch.empty((5, 8 * n), dtype=torch.float64, pin_memory=True)
+        host[l] = t.numpy()
+        mesh.read(l, out_U=host[l], keys=False)
+    nbytes = sum(h.nbytes for h in host.values())
+
+    def one():
+        for l in levels:
+            mesh.write(l, host[l])
+        mesh.advance(1)
+        for l in levels:
+            mesh.read(l, out_U=host[l], keys=False)
+
+    one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = time.perf_counter() - t0
+    mesh.close()
+    return {"value": upd * steps / dt, "unit": "leaf cell-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "ms_per_step": 1e3 * dt / steps}
+
+
+def cpu_baseline(prob, nsteps):
+    import oracle
+    m = oracle.Mesh(*prob.mesh_args(), **prob.params())
+    upd = 0
+    for l in m.levels():
+        leaf = int(np.count_nonzero(m.read_split(l) == 0))
+        upd += leaf * 2 ** (l - prob.levelmin)
+    t0 = time.perf_counter()
+    m.advance(nsteps)
+    dt = time.perf_counter() - t0
+    return {"value": upd * nsteps / dt, "unit": "leaf cell-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{nsteps} coarse W-cycle steps of the same Sedov mesh (levels 7-10, "
+                      f"{upd} cell-updates per step), single-threaded FP64 oracle, {dt:.1f} s"}
+
+
+def fp64_peak(torch, device):
+    """FP64 rate of cuBLAS DGEMM on this GPU (denominator of the ALU roofline)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=device)
+    b = torch.randn(n, n, dtype=torch.float64, device=device)
+    torch.matmul(a, b)
+    torch.cuda.synchronize(device)
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def roofline(res, prec, levelmin, peak_gbs, peak_src):
+    w = WORD[prec]
+    traffic = kernel_traffic(res["info"], levelmin, w)
+    kt = res.get("kernels", {})
+    if not kt:
+        return None, None
+    top = max(kt.items(), key=lambda kv: kv[1][0])
+    name, (ms_tot, n_launch) = top
+    if name not in traffic:
+        return None, None
+    steps = res["steps"]
+    bytes_per_launch = traffic[name] * steps / n_launch
+    avg_ms = ms_tot / n_launch
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    tot = sum(v[0] for v in kt.values())
+    table = {k: {"ms": round(v[0], 4), "launches": v[1], "share": round(v[0] / tot, 4)}
+             for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+    return ({"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs,
+             "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
+             "peak_source": peak_src, "avg_launch_us": round(1e3 * avg_ms, 3),
+             "algorithmic_bytes_per_launch": int(bytes_per_launch)}, table)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.warmup < 3:
+        args.warmup = 3
+    from paper_2607_20704_gb300 import inputs
+    prob = inputs.sedov()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        m = oracle.Mesh(*prob.mesh_args(), **prob.params())
+        upd = sum(int(np.count_nonzero(m.read_split(l) == 0)) * 2 ** (l - prob.levelmin)
+                  for l in m.levels())
+        m.advance(args.warmup)
+        t0 = time.perf_counter()
+        m.advance(args.steps)
+        dt = time.perf_counter() - t0
+        v = upd * args.steps / dt
+        line = {"impl": "reference", "metric": "leaf cell-updates/s", "value": v,
+                "unit": "leaf cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "levelmin": 7, "levelmax": 10, "n_oct": prob.n_oct,
+                           "cell_updates_per_step": upd},
+                "cpu_baseline": {"value": v, "unit": "leaf cell-updates/s", "cores": 1,
+                                 "kind": "oracle",
+                                 "sample": f"{args.steps} full coarse steps of the workload, "
+                                           "single-threaded FP64 oracle on the host"},
+                "e2e": {"value": v, "unit": "leaf cell-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if args.profile_level:
+        from paper_2607_20704_gb300 import amr
+        m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=args.precision)
+        dt = m.cfl_dt() * 0.5 ** (args.profile_level - prob.levelmin)
+        m.step_level(args.profile_level, dt)
+        m.sync()
+        print(json.dumps({"profile_level": args.profile_level, "precision": args.precision,
+                          "octs": m.num_octs(args.profile_level)}))
+        m.close()
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2607_20704_gb300 import amr, build
+    build.build()
+    amr.load()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    peak_gbs, peak_src = load_peaks()
+
+    prec_main = args.precision
+    prec_other = 4 if prec_main == 8 else 8
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        main_res = run_precision(prob, prec_main, args.steps, args.warmup, torch, device, flush)
+        main_res["steps"] = args.steps
+        other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
+        other["steps"] = args.steps
+        e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
+    clocks = clk.summary()
+
+    ms = main_res["ms"]
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = main_res["updates_per_step"]
+    value = upd * args.steps * world / (ms * 1e-3)
+    rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src)
+    rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src)
+    step_bytes = 2 * 5 * WORD[prec_main]
+    line = {
+        "metric": "leaf cell-updates/s",
+        "value": value,
+        "unit": "leaf cell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec_main == 8 else "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "levelmin": 7, "levelmax": 10, "gamma": 5.0 / 3.0,
+                   "n_oct": main_res["info"]["n_oct"], "n_ghost_oct": main_res["info"]["n_cache"],
+                   "leaf_cells": main_res["info"]["n_leaf_cells"],
+                   "cell_updates_per_step": upd, "step": "one coarse W-cycle step (reindex + CFL + "
+                   "15 level steps)", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": rl,
+        "step_roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak_gbs,
+                          "achieved": round(value / world * step_bytes / 1e9, 1),
+                          "frac": round(value / world * step_bytes / 1e9 / peak_gbs, 4),
+                          "bytes_per_cell_update": step_bytes},
+        "kernels": table,
+        "gpu_launches": main_res["launches"],
+        "clocks": clocks,
+        "e2e": e2e,
+        ("fp32" if prec_other == 4 else "fp64"): {
+            "value": upd * args.steps * world / (other["ms"] * 1e-3),
+            "ms_per_step": other["ms"] / args.steps,
+            "roofline": rl_o, "kernels": table_o, "gpu_launches": other["launches"],
+            "step_roofline_frac": round(upd * args.steps / (other["ms"] * 1e-3)
+                                        * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)},
+    }
+    try:
+        line["fp64_dgemm_tflops"] = round(fp64_peak(torch, device), 3)
+    except Exception:
+        line["fp64_dgemm_tflops"] = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_steps)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
