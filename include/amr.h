@@ -4,7 +4,7 @@
  *
  * One handle owns one graded octree resident in device memory: the oct list
  * (sorted by level, then Hilbert key, Sec. 2.2), an FNV-1a 64 hash table with
- * linear probing keyed by (i,j,k,l) (Sec. 2.1, Sec. 5), the father/neighbour
+ * linear probing keyed by (i,j,k,l) (Sec. 2.1, Sec. 6), the father/neighbour
  * index arrays and the ghost-oct cache (Sec. 2.3), the conservative state
  * U = (rho, rho u, rho v, rho w, E) of every cell and the pending reflux of
  * every coarse cell.  All computation runs in the library's CUDA kernels on

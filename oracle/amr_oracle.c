@@ -16,7 +16,7 @@
  *   Sec. 3   MUSCL-Hancock predictor-corrector, HLLC Riemann solver, two ghost
  *            cells per side: a 6x6x6 stencil of uold -> unew per oct
  *   Table 1  stage order: set unew / godunov / set uold / upload (restriction)
- *   Sec. 5   FNV-1a 64-bit hash
+ *   Sec. 6   FNV-1a 64-bit hash (named for the hash table)
  * The paper prints no formulas; each formula below is the cited textbook
  * method (Van Leer 1979 MUSCL-Hancock, Toro HLLC with min/max wave speeds,
  * Teyssier 2002 refluxing and restriction), in the reading documented with
@@ -38,7 +38,7 @@ uint64_t orc_pack_key(int level, uint32_t i, uint32_t j, uint32_t k) {
          (uint64_t)k;
 }
 
-/* FNV-1a 64 (Sec. 5): offset basis 0xcbf29ce484222325, prime 0x100000001b3. */
+/* FNV-1a 64 (Sec. 6): offset basis 0xcbf29ce484222325, prime 0x100000001b3. */
 uint64_t orc_fnv1a64_bytes(const uint8_t *bytes, size_t len) {
   uint64_t h = 0xcbf29ce484222325ULL;
   for (size_t t = 0; t < len; ++t) {

@@ -48,7 +48,7 @@ typedef struct {
 
 typedef struct orc_mesh orc_mesh;
 
-/* --- keys, hash function, Hilbert key (Sec. 2.1, 2.2, Sec. 5) ------------ */
+/* --- keys, hash function, Hilbert key (Sec. 2.1, 2.2, Sec. 6) ------------ */
 uint64_t orc_pack_key(int level, uint32_t i, uint32_t j, uint32_t k);
 uint64_t orc_fnv1a64_bytes(const uint8_t *bytes, size_t len);
 uint64_t orc_fnv1a64_key(uint64_t key);

@@ -36,7 +36,7 @@ __host__ __device__ __forceinline__ uint32_t key_x(uint64_t key) { return uint32
 __host__ __device__ __forceinline__ uint32_t key_y(uint64_t key) { return uint32_t(key >> 20) & 0xFFFFFu; }
 __host__ __device__ __forceinline__ uint32_t key_z(uint64_t key) { return uint32_t(key) & 0xFFFFFu; }
 
-// FNV-1a 64 over the key's 8 bytes, least significant byte first (Sec. 5).
+// FNV-1a 64 over the key's 8 bytes, least significant byte first (Sec. 6).
 __device__ __forceinline__ uint64_t fnv1a64(uint64_t key) {
   uint64_t h = 0xcbf29ce484222325ull;
 #pragma unroll

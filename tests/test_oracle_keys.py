@@ -1,5 +1,5 @@
 """Pins of the oracle's integer machinery: hash function, Hilbert key, key
-packing (paper Sec. 2.1 hash key (i,j,k,l); Sec. 2.2 Hilbert order; Sec. 5
+packing (paper Sec. 2.1 hash key (i,j,k,l); Sec. 2.2 Hilbert order; Sec. 6
 FNV-1a 64)."""
 import itertools
 import os
