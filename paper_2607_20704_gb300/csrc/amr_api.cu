@@ -390,7 +390,8 @@ static void cfl_device(amr_mesh *h) {
   int64_t maxcells = 0;
   for (int l = h->p.levelmin; l <= h->p.levelmax; ++l)
     maxcells = std::max<int64_t>(maxcells, 8 * (h->lo[l + 1] - h->lo[l]));
-  dim3 grid(nblocks(maxcells), unsigned(h->p.levelmax - h->p.levelmin + 1));
+  // a few waves of 256-thread blocks per level, grid-stride inside
+  dim3 grid(std::min<unsigned>(nblocks(maxcells), 152 * 4), unsigned(h->p.levelmax - h->p.levelmin + 1));
   if (h->p.precision == 4)
     launch(h, K_CFL, k_cfl<float>, grid, dim3(256), a, (const float *)h->U);
   else

@@ -348,9 +348,11 @@ template <class T>
 __global__ void k_cfl(CflArgs a, const T *U) {
   const int l = a.lmin + blockIdx.y;
   const int64_t lo = a.lo[l], n8 = 8 * (a.lo[l + 1] - lo);
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   double s = 0.0;
-  if (t < n8 && !((__ldg(a.son + lo + (t >> 3)) >> (t & 7)) & 1u)) {
+  bool bad = false;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n8;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    if ((__ldg(a.son + lo + (t >> 3)) >> (t & 7)) & 1u) continue;
     const int64_t g = 8 * lo + t;
     const double u0 = double(U[g]), u1 = double(U[a.S + g]), u2 = double(U[2 * a.S + g]),
                  u3 = double(U[3 * a.S + g]), u4 = double(U[4 * a.S + g]);
@@ -359,16 +361,26 @@ __global__ void k_cfl(CflArgs a, const T *U) {
     const double ek = 0.5 * r * ((vx * vx + vy * vy) + vz * vz);
     const double p = fmax((a.gamma - 1.0) * (u4 - ek), r * a.smallp);
     const double cs = sqrt(a.gamma * p / r);
-    s = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
-    if (!isfinite(s) || !isfinite(u0 + u1 + u2 + u3 + u4)) {
-      atomicOr(a.err, kErrNaN);
-      s = 0.0;
-    }
+    const double st = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
+    if (!isfinite(st) || !isfinite(u0 + u1 + u2 + u3 + u4))
+      bad = true;
+    else
+      s = fmax(s, st);
   }
+  if (bad) atomicOr(a.err, kErrNaN);
+  // warp shuffle, then one value per warp in shared memory, one atomic per block
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
-  if ((threadIdx.x & 31) == 0 && s > 0.0)
-    atomicMax(a.smax + l, (unsigned long long)__double_as_longlong(s));
+  __shared__ double wmax[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) wmax[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < int(blockDim.x >> 5) ? wmax[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+    if (lane == 0 && s > 0.0) atomicMax(a.smax + l, (unsigned long long)__double_as_longlong(s));
+  }
 }
 
 __global__ void k_dt(CflArgs a) {
