@@ -215,6 +215,34 @@ amr_status amr_set_timing(amr_handle h, int on);
 amr_status amr_read_timing(amr_handle h, int n, double *ms, int64_t *launches);
 const char *amr_kernel_name(int t);
 
+/*
+ * amr_cfl_dt_static -- the time-step reduction of amr_cfl_dt for one level of
+ * leaf cells held in caller device memory, with no device allocation at all.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (device memory pre-reserved by another
+ * runtime's pool, allocator-free real-time loops).  Its scratch is fixed
+ * device storage inside the library (512 KiB per GPU that loads it, held
+ * until the process exits), so n_cells is limited to
+ * AMR_CFL_STATIC_MAX_CELLS (AMR_EINVAL beyond it).
+ *   U        device array of doubles, variable v of cell t at U[v*stride + t]
+ *   n_cells  cells to reduce, all leaves of one level
+ *   level    the cells' level l: dx = 2^-l
+ *   gamma, cfl, smallr, smallc   as in amr_params
+ *   dt_out   device pointer; receives cfl dx / max_t sum_d (|u_d| + c), or
+ *            NaN if a cell is not finite
+ *   stream   cudaStream_t (NULL: legacy default stream); asynchronous
+ * The first call on a device looks up the scratch address (with that device
+ * current); make that first call before any stream capture.  Every call on a
+ * device shares the same scratch: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  The
+ * call clears the scratch counter it needs before its kernel runs.
+ * Errors: AMR_EINVAL (NULL pointer, sizes, parameters), AMR_ECUDA.
+ */
+#define AMR_CFL_STATIC_MAX_CELLS ((int64_t)65536 * 256)
+amr_status amr_cfl_dt_static(const double *U, int64_t n_cells, int64_t stride, int level,
+                             double gamma, double cfl, double smallr, double smallc,
+                             double *dt_out, void *stream);
+
 /* Wait for the handle's stream and report any pending device-side error. */
 amr_status amr_sync(amr_handle h);
 

@@ -63,7 +63,10 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_advance", "amr_reindex", "amr_read", "amr_read_reflux", "amr_write",
            "amr_lookup", "amr_read_index", "amr_read_cache", "amr_fill_ghosts", "amr_get_info",
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
-           "amr_status_string"]
+           "amr_status_string", "amr_cfl_dt_static"]
+
+# fixed scratch limit of amr_cfl_dt_static (AMR_CFL_STATIC_MAX_CELLS in amr.h)
+CFL_STATIC_MAX_CELLS = 65536 * 256
 
 
 def load(path: str | None = None):
@@ -100,6 +103,7 @@ def load(path: str | None = None):
             "amr_sync": (I, [P]),
             "amr_last_error": (C.c_char_p, []),
             "amr_status_string": (C.c_char_p, [I]),
+            "amr_cfl_dt_static": (I, [P, I64, I64, I, D, D, D, D, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -356,3 +360,16 @@ def amr_read(m: Mesh, level: int):
 
 def amr_write(m: Mesh, level: int, U):
     m.write(level, U)
+
+
+def amr_cfl_dt_static(U_ptr: int, n_cells: int, stride: int, level: int, gamma: float,
+                      cfl: float, smallr: float, smallc: float, dt_out_ptr: int,
+                      stream_ptr: int = 0):
+    """Time-step reduction on caller-owned device buffers, allocating nothing
+    on the device (for callers that cannot allocate: see include/amr.h).
+    U_ptr and dt_out_ptr are device addresses; asynchronous on stream_ptr."""
+    L = load()
+    _check(L.amr_cfl_dt_static(C.c_void_p(U_ptr), int(n_cells), int(stride), int(level),
+                               float(gamma), float(cfl), float(smallr), float(smallc),
+                               C.c_void_p(dt_out_ptr), C.c_void_p(stream_ptr or None)),
+           "amr_cfl_dt_static")

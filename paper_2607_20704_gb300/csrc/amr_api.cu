@@ -46,6 +46,9 @@ static amr_status fail(amr_status s, const char *fmt, ...) {
 
 extern "C" const char *amr_last_error(void) { return g_last_error.c_str(); }
 
+// lets other translation units of the library set the calling thread's text
+void amr_set_error_text(const char *text) { g_last_error = text ? text : ""; }
+
 extern "C" const char *amr_status_string(amr_status s) {
   switch (s) {
     case AMR_OK: return "AMR_OK";
