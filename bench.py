@@ -118,7 +118,7 @@ def kernel_traffic(info, levelmin, w):
       prim     U in, W out                      10 w per real+ghost cell
       predict  W in, (W*, dW) out               25 w per real+ghost cell
       flux     (W*, dW) in, F out               35 w per real+ghost cell
-      update   F in, U and R in/out             35 w per real cell
+      update   F in (15 w), U in/out, reflux slot  25 w + 4 B per real cell
       prolong  7 source cells in, 8 ghosts out  75 w per ghost oct
       reflux   24 slots in, R in/out           130 w per ghost oct
       restrict 8 children in, father out        45 w per real oct (l > lmin)
@@ -133,7 +133,7 @@ def kernel_traffic(info, levelmin, w):
         out["prim"] += reps * cells * 10 * w
         out["predict"] += reps * cells * 25 * w
         out["flux"] += reps * cells * 35 * w
-        out["update"] += reps * 8 * n * 35 * w
+        out["update"] += reps * 8 * n * (25 * w + 4)
         out["prolong"] += reps * nc * 75 * w
         out["reflux"] += reps * nc * 130 * w
         if l > levelmin:

@@ -124,10 +124,12 @@ struct amr_mesh {
   int64_t table_cap = 0, scan_cap = 0;
 
   // state and scratch
-  void *U = nullptr, *R = nullptr;
+  void *U = nullptr, *Rc = nullptr;  // Rc: pending reflux per ghost oct [5][NC]
+  int32_t *rslot = nullptr;          // [8N] ghost slot whose father is the cell
   void *W = nullptr, *Q = nullptr, *F = nullptr, *C = nullptr;
   int64_t max_ls = 0, max_cs = 0;
   double *dt_dev = nullptr;
+  float *dtf_dev = nullptr;
   unsigned long long *smax = nullptr;
   int *err = nullptr;
 
@@ -317,19 +319,19 @@ static LevelArgs<T> level_args(amr_mesh *h, int l, const double *dt_dev, double 
   LevelArgs<T> a{};
   a.l = l;
   a.lmin = h->p.levelmin;
-  a.lo = h->lo[l];
-  a.nl = h->lo[l + 1] - h->lo[l];
-  a.clo = h->clo[l];
-  a.ncl = h->clo[l + 1] - h->clo[l];
-  a.N = h->N;
-  a.NE = h->NE;
-  a.NC = h->NC;
+  a.lo = int(h->lo[l]);
+  a.nl = int(h->lo[l + 1] - h->lo[l]);
+  a.clo = int(h->clo[l]);
+  a.ncl = int(h->clo[l + 1] - h->clo[l]);
+  a.N = int(h->N);
+  a.NE = int(h->NE);
+  a.NC = int(h->NC);
   a.S = h->S;
-  a.RS = 8 * h->N;
   a.LS = 8 * (a.nl + a.ncl);
   a.CS = 24 * h->NC;
   a.U = static_cast<T *>(h->U);
-  a.R = static_cast<T *>(h->R);
+  a.Rc = static_cast<T *>(h->Rc);
+  a.rslot = h->rslot;
   a.fnb = h->fnb;
   a.son = h->son;
   a.father = h->father;
@@ -340,10 +342,11 @@ static LevelArgs<T> level_args(amr_mesh *h, int l, const double *dt_dev, double 
   a.F = static_cast<T *>(h->F);
   a.C = static_cast<T *>(h->C);
   a.dt_dev = dt_dev;
-  a.dt_scale = scale;
-  a.dt_host = dt;
-  a.inv_dx = ldexp(1.0, l);
+  a.dtf_dev = dt_dev ? h->dtf_dev : nullptr;
+  a.dtdx_scale = scale * ldexp(1.0, l);
+  a.dtdx_host = T(dt * ldexp(1.0, l));
   a.gamma = T(h->p.gamma);
+  a.igm1 = T(1.0 / (h->p.gamma - 1.0));
   a.smallr = T(h->p.smallr);
   a.smallp = T(h->p.smallc * h->p.smallc / h->p.gamma);
   a.reflux = h->p.reflux;
@@ -384,6 +387,7 @@ static CflArgs cfl_args(amr_mesh *h) {
   a.cfl = h->p.cfl;
   a.smax = h->smax;
   a.dt_dev = h->dt_dev;
+  a.dtf_dev = h->dtf_dev;
   a.err = h->err;
   return a;
 }
@@ -428,7 +432,7 @@ static amr_status build_index(amr_mesh *h, bool first) {
   if (first)
     launch(h, K_GRADING, k_grading, dim3(nblocks(8 * 27 * (N - first_fine))), dim3(256), h->hash,
            (const uint64_t *)h->key, first_fine, N, h->err);
-  launch(h, K_NEIGHBOURS, k_neighbours, dim3(nblocks(8 * 27 * N)), dim3(256), h->hash,
+  launch(h, K_NEIGHBOURS, k_neighbours, dim3(nblocks(27 * N)), dim3(256), h->hash,
          (const uint64_t *)h->key, N, h->nbr27, h->claim, h->counters, h->claim_cap, h->err);
   if (first) {  // create: stop after the claims; the caller sizes the ghost buffers
     AMR_TRY(check_device(h, "amr_create"));
@@ -459,8 +463,9 @@ static amr_status build_faces_and_sources(amr_mesh *h) {
   if (h->NC) {
     launch(h, K_FACES, k_faces_cache, dim3(nblocks(6 * h->NC)), dim3(256), h->hash,
            (const uint64_t *)h->ckey, h->NC, h->N, h->NE, h->fnb);
+    cudaMemsetAsync(h->rslot, 0xFF, sizeof(int32_t) * 8 * h->N, h->s);
     launch(h, K_CACHE_SOURCES, k_cache_sources, dim3(nblocks(h->NC)), dim3(256), h->hash,
-           (const uint64_t *)h->ckey, h->NC, h->N, h->p.levelmin, h->csrc, h->err);
+           (const uint64_t *)h->ckey, h->NC, h->N, h->p.levelmin, h->csrc, h->rslot, h->err);
   }
   return AMR_OK;
 }
@@ -648,15 +653,17 @@ static amr_status create_impl(amr_mesh *h, int64_t n, const uint8_t *level, cons
   h->S = 8 * h->NE;
   AMR_TRY(alloc_n(h, &h->fnb, 6 * h->NE));
   AMR_TRY(alloc_n(h, &h->csrc, 7 * (NC > 0 ? NC : 1)));
+  AMR_TRY(alloc_n(h, &h->rslot, 8 * n));
+  CUDA_TRY(cudaMemsetAsync(h->rslot, 0xFF, sizeof(int32_t) * 8 * n, h->s));
   AMR_TRY(build_faces_and_sources(h));
   AMR_TRY(check_device(h, "amr_create"));
 
   // state in mesh order
   const size_t es = h->elem();
   AMR_TRY(dev_alloc(h, &h->U, es * 5 * size_t(h->S)));
-  AMR_TRY(dev_alloc(h, &h->R, es * 5 * size_t(8 * n)));
+  AMR_TRY(dev_alloc(h, &h->Rc, es * 5 * size_t(NC > 0 ? NC : 1)));
   CUDA_TRY(cudaMemsetAsync(h->U, 0, es * 5 * size_t(h->S), h->s));
-  CUDA_TRY(cudaMemsetAsync(h->R, 0, es * 5 * size_t(8 * n), h->s));
+  CUDA_TRY(cudaMemsetAsync(h->Rc, 0, es * 5 * size_t(NC > 0 ? NC : 1), h->s));
   if (p.precision == 4)
     launch(h, K_GATHER, k_gather_octs<float>, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
            (const uint8_t *)d_lvl, (const uint32_t *)d_i, (const uint32_t *)d_j,
@@ -685,6 +692,7 @@ static amr_status create_impl(amr_mesh *h, int64_t n, const uint8_t *level, cons
   AMR_TRY(dev_alloc(h, &h->C, es * 5 * size_t(h->max_cs > 0 ? h->max_cs : 1)));
   if (h->max_cs) CUDA_TRY(cudaMemsetAsync(h->C, 0, es * 5 * size_t(h->max_cs), h->s));
   AMR_TRY(alloc_n(h, &h->dt_dev, 1));
+  AMR_TRY(alloc_n(h, &h->dtf_dev, 1));
   AMR_TRY(alloc_n(h, &h->smax, 16));
   CUDA_TRY(cudaMemsetAsync(h->smax, 0, sizeof(unsigned long long) * 16, h->s));
 
@@ -884,7 +892,17 @@ extern "C" amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_
   if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_read_reflux: bad level");
   const int64_t lo = h->lo[level], nl = h->lo[level + 1] - lo;
   if (cap < nl) return fail(AMR_EINVAL, "amr_read_reflux: cap too small");
-  AMR_TRY(rows_to_host(h, h->R, 8 * h->N, 8 * lo, 8 * nl, R));
+  const int64_t n8 = 8 * nl;
+  for (int64_t t = 0; t < 5 * n8; ++t) R[t] = 0.0;
+  if (nl == 0 || h->NC == 0) return check_device(h, "amr_read_reflux");
+  std::vector<int32_t> slot(n8);
+  std::vector<double> rc(5 * size_t(h->NC));
+  CUDA_TRY(cudaMemcpyAsync(slot.data(), h->rslot + 8 * lo, 4 * n8, cudaMemcpyDeviceToHost, h->s));
+  AMR_TRY(rows_to_host(h, h->Rc, h->NC, 0, h->NC, rc.data()));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  for (int64_t t = 0; t < n8; ++t)
+    if (slot[t] >= 0)
+      for (int v = 0; v < 5; ++v) R[v * n8 + t] = rc[v * size_t(h->NC) + slot[t]];
   return check_device(h, "amr_read_reflux");
 }
 

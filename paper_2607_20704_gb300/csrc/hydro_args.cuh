@@ -6,33 +6,37 @@ namespace amr {
 
 // Everything one level step needs, passed by value.  "Local" cell indices
 // t in [0, LS) number the level's real cells first (8*nl) and then the
-// cells of its ghost octs (8*ncl); scratch arrays are indexed by t.
+// cells of its ghost octs (8*ncl); scratch arrays are indexed by t.  Every
+// count fits in 32 bits (at most 2^26 real octs), so kernels index with int.
 template <class T>
 struct LevelArgs {
   int l, lmin;
-  int64_t lo, nl;    // real octs of the level: mesh indices [lo, lo+nl)
-  int64_t clo, ncl;  // ghost octs of the level: cache slots [clo, clo+ncl)
-  int64_t N, NE;     // real octs; real + ghost octs (extended index range)
-  int64_t S;         // stride of U (8*NE)
-  int64_t RS;        // stride of R (8*N)
-  int64_t LS;        // stride of the scratch arrays (8*(nl+ncl))
-  int64_t CS;        // stride of the reflux contribution slots (24*NC): every
-                     // ghost oct owns 24 slots, written only by its own level
-  T *U, *R;
+  int lo, nl;     // real octs of the level: mesh indices [lo, lo+nl)
+  int clo, ncl;   // ghost octs of the level: cache slots [clo, clo+ncl)
+  int N, NE, NC;  // real octs; real + ghost octs; ghost octs
+  int LS;         // stride of the scratch arrays (8*(nl+ncl))
+  int64_t S;      // stride of U (8*NE)
+  int64_t CS;     // stride of the reflux contribution slots (24*NC): every
+                  // ghost oct owns 24 slots, written only by its own level
+  T *U;
+  T *Rc;                  // [5][NC] pending reflux of the father of ghost oct s
+  const int32_t *rslot;   // [8N] ghost slot whose father is this cell, or -1
   const int32_t *fnb;     // [6][NE] face neighbours (extended index, -1 none)
   const uint32_t *son;    // [N] split mask
   const int32_t *father;  // [N] father oct (mesh index), -1 at levelmin
   const uint64_t *key;    // [N]
   const int32_t *csrc;    // [7][NC] prolongation sources (global cell indices)
-  int64_t NC;
   T *W, *Q, *F, *C;       // scratch: W[5][LS], Q[20][LS], F[15][LS]; C[5][CS]
-  const double *dt_dev;   // if not NULL: dt = *dt_dev * dt_scale
-  double dt_scale, dt_host;
-  double inv_dx;          // 2^l
-  T gamma, smallr, smallp;
+  // dt/dx of this level step: from the device dt of the coarse step
+  // (dt_dev, or its float copy dtf_dev) times dtdx_scale = 2^(l - k) for the
+  // k-th halving, or the host value dtdx_host when both pointers are NULL
+  const double *dt_dev;
+  const float *dtf_dev;
+  double dtdx_scale;
+  T dtdx_host;
+  T gamma, igm1, smallr, smallp;  // igm1 = 1/(gamma - 1)
   int reflux;
 };
-
 
 struct CflArgs {
   int lmin, lmax;
@@ -42,9 +46,8 @@ struct CflArgs {
   double gamma, smallr, smallp, cfl;
   unsigned long long *smax;  // [16] bit patterns of per-level maxima
   double *dt_dev;
+  float *dtf_dev;            // float copy of dt for the FP32 kernels
   int *err;
 };
-
-
 
 }  // namespace amr

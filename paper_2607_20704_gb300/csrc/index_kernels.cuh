@@ -204,13 +204,15 @@ __global__ void k_grading(HashView h, const uint64_t *__restrict__ key, int64_t 
 __global__ void k_neighbours(HashView h, const uint64_t *__restrict__ key, int64_t n,
                              int32_t *__restrict__ nbr27, uint64_t *__restrict__ claim,
                              uint32_t *__restrict__ claim_count, int64_t claim_cap, int *err) {
-  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 3;
-  const int64_t t = q / 27;
-  if (t >= n) return;
-  const int e = int(q % 27);
-  const bool leader = (threadIdx.x & 7) == 0;
+  // one thread per (direction, oct), direction-major: coalesced table writes;
+  // a query resolves in about one probe at this load factor, so each thread
+  // probes alone (hash_probe8 would read 8 slots for it)
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 27 * n) return;
+  const int e = int(q / n);
+  const int64_t t = q - int64_t(e) * n;
   if (e == 13) {
-    if (leader) nbr27[13 * n + t] = int32_t(t);
+    nbr27[q] = int32_t(t);
     return;
   }
   const uint64_t k = key[t];
@@ -219,13 +221,12 @@ __global__ void k_neighbours(HashView h, const uint64_t *__restrict__ key, int64
   const uint64_t nk = key_pack(l, wrapc(int64_t(key_x(k)) + (e % 3) - 1, side),
                                wrapc(int64_t(key_y(k)) + (e / 3 % 3) - 1, side),
                                wrapc(int64_t(key_z(k)) + (e / 9) - 1, side));
-  const int32_t v = hash_probe8(h, nk);
-  if (!leader) return;
+  const int32_t v = hash_probe1(h, nk);
   if (v >= 1 && int64_t(v) <= n) {
-    nbr27[int64_t(e) * n + t] = v - 1;
+    nbr27[q] = v - 1;
     return;
   }
-  nbr27[int64_t(e) * n + t] = -1;
+  nbr27[q] = -1;
   bool ins = false;
   const uint64_t s = hash_insert(h, nk, &ins, err);
   if (ins && s != ~0ull) {
@@ -343,7 +344,8 @@ __device__ int64_t cell_or_coarser(HashView h, int L, int64_t x, int64_t y, int6
 // for d = x, y, z (order C, -x, +x, -y, +y, -z, +z); C is also the coarse
 // cell that receives the reflux of the ghost's faces.
 __global__ void k_cache_sources(HashView h, const uint64_t *__restrict__ ckey, int64_t nc, int64_t N,
-                                int lmin, int32_t *__restrict__ csrc, int *err) {
+                                int lmin, int32_t *__restrict__ csrc, int32_t *__restrict__ rslot,
+                                int *err) {
   const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (s >= nc) return;
   const uint64_t k = ckey[s];
@@ -362,6 +364,9 @@ __global__ void k_cache_sources(HashView h, const uint64_t *__restrict__ ckey, i
       continue;
     }
     csrc[int64_t(q) * nc + s] = int32_t(c);
+    // the father cell is the coarse cell that receives this ghost's reflux;
+    // distinct ghost octs have distinct fathers
+    if (q == 0) rslot[c] = int32_t(s);
   }
 }
 
