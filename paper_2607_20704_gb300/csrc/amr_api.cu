@@ -358,13 +358,21 @@ static void run_level_step(amr_mesh *h, int l, const double *dt_dev, double scal
   LevelArgs<T> a = level_args<T>(h, l, dt_dev, scale, dt);
   if (a.nl == 0) return;
   if (a.ncl) launch(h, K_PROLONG, k_prolong<T>, dim3(nblocks(5 * a.ncl)), dim3(256), a);
-  launch(h, K_PRIM, k_prim<T>, dim3(nblocks(a.LS)), dim3(256), a);
-  launch(h, K_PREDICT, k_predict<T>, dim3(nblocks(a.LS)), dim3(256), a);
-  launch(h, K_FLUX, k_flux<T>, dim3(nblocks(a.LS)), dim3(256), a);
-  launch(h, K_UPDATE, k_update<T>, dim3(nblocks(8 * a.nl)), dim3(256), a);
-  if (a.ncl && h->p.reflux)
-    launch(h, K_REFLUX, k_reflux<T>, dim3(nblocks(5 * a.ncl)), dim3(256), a);
-  if (l > h->p.levelmin) launch(h, K_RESTRICT, k_restrict<T>, dim3(nblocks(5 * a.nl)), dim3(256), a);
+  if (sizeof(T) == 4) {
+    // FP32: primitives recomputed inside the predictor; each leaf cell solves
+    // its six faces and updates itself
+    launch(h, K_PREDICT, k_predict_u<T>, dim3(nblocks(a.LS)), dim3(256), a);
+    launch(h, K_FLUX, k_flux_update<T>, dim3(nblocks(8 * a.nl)), dim3(256), a);
+  } else {
+    // FP64: every predictor and every face solve exactly once
+    launch(h, K_PRIM, k_prim<T>, dim3(nblocks(a.LS)), dim3(256), a);
+    launch(h, K_PREDICT, k_predict<T>, dim3(nblocks(a.LS)), dim3(256), a);
+    launch(h, K_FLUX, k_flux<T>, dim3(nblocks(a.LS)), dim3(256), a);
+    launch(h, K_UPDATE, k_update<T>, dim3(nblocks(8 * a.nl)), dim3(256), a);
+  }
+  const int do_restrict = l > h->p.levelmin;
+  const int64_t nq = (h->p.reflux ? 5 * int64_t(a.ncl) : 0) + (do_restrict ? 5 * int64_t(a.nl) : 0);
+  if (nq) launch(h, K_RESTRICT, k_reflux_restrict<T>, dim3(nblocks(nq)), dim3(256), a, do_restrict);
 }
 
 static void level_step(amr_mesh *h, int l, const double *dt_dev, double scale, double dt) {

@@ -382,6 +382,160 @@ __global__ void k_restrict(LevelArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32 level step in fewer launches.  FP32 arithmetic is cheap on GB300, so
+// these kernels trade recomputation for memory round trips and launches:
+// k_predict_u derives the primitives of a cell and its six face neighbours
+// from U directly (no W array); k_flux_update solves all six faces of a
+// real leaf cell and updates it in place (each interior face is solved by
+// both of its cells, bit-identically, so the update matches the split
+// kernels); coarse-fine faces are owned by the real cell.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void prim_at(const LevelArgs<T> &a, int t, T (&w)[5]) {
+  const int g = 8 * ext_of_local(a, t >> 3) + (t & 7);
+  const T r = vmax(a.U[g], a.smallr);
+  const T ir = rcp(r);
+  const T vx = a.U[a.S + g] * ir, vy = a.U[2 * a.S + g] * ir, vz = a.U[3 * a.S + g] * ir;
+  const T ek = T(0.5) * r * ((vx * vx + vy * vy) + vz * vz);
+  w[0] = r;
+  w[1] = vx;
+  w[2] = vy;
+  w[3] = vz;
+  w[4] = vmax((a.gamma - T(1)) * (a.U[4 * a.S + g] - ek), r * a.smallp);
+}
+
+template <class T>
+__global__ void k_predict_u(LevelArgs<T> a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.LS) return;
+  const int e = ext_of_local(a, t >> 3);
+  const int c = t & 7;
+  T w[5], dw[3][5];
+  prim_at(a, t, w);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int tm = nbr_local(a, t, e, c, d, 0);
+    const int tp = nbr_local(a, t, e, c, d, 1);
+    if (tm < 0 || tp < 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
+      continue;
+    }
+    T wm[5], wp[5];
+    prim_at(a, tm, wm);
+    prim_at(a, tp, wp);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dw[d][v] = minmod(wp[v] - w[v], w[v] - wm[v]);
+  }
+  const T r = w[0], p = w[4], g = a.gamma;
+  const T ir = rcp(r);
+  const T gp = g * p;
+  T s[5];
+  s[0] = -(((w[1] * dw[0][0] + r * dw[0][1]) + (w[2] * dw[1][0] + r * dw[1][2])) +
+           (w[3] * dw[2][0] + r * dw[2][3]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    s[1 + k] = -((w[1] * dw[0][1 + k] + w[2] * dw[1][1 + k]) + w[3] * dw[2][1 + k]) - dw[k][4] * ir;
+  s[4] = -(((w[1] * dw[0][4] + gp * dw[0][1]) + (w[2] * dw[1][4] + gp * dw[1][2])) +
+           (w[3] * dw[2][4] + gp * dw[2][3]));
+  const T hdt = T(0.5) * level_dtdx(a);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) a.Q[v * a.LS + t] = w[v] + hdt * s[v];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) a.Q[(5 + 5 * d + v) * a.LS + t] = dw[d][v];
+}
+
+// the two faces of local cell t along axis D; du += F(minus) - F(plus)
+template <int D, class T>
+__device__ __forceinline__ void faces_dir(const LevelArgs<T> &a, int t, int e, int c, T dtdx,
+                                          T (&du)[5]) {
+  constexpr int d1 = D == 0 ? 1 : 0, d2 = D == 2 ? 1 : 2;
+  const int ab = (((c >> d1) & 1) << 1) | ((c >> d2) & 1);
+  T Fm[5] = {T(0), T(0), T(0), T(0), T(0)}, Fp[5] = {T(0), T(0), T(0), T(0), T(0)};
+  const int tm = nbr_local(a, t, e, c, D, 0);
+  if (!cell_is_split(a, tm)) {
+    face_flux<D>(a, tm, t, Fm);
+    if (a.reflux && (tm >> 3) >= a.nl) {  // ghost on the minus side
+      const int gslot = (a.clo + (tm >> 3) - a.nl) * 24 + (2 * D + 1) * 4 + ab;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(-1) * dtdx) * Fm[v] / T(8);
+    }
+  }
+  const int tp = nbr_local(a, t, e, c, D, 1);
+  if (!cell_is_split(a, tp)) {
+    face_flux<D>(a, t, tp, Fp);
+    if (a.reflux && (tp >> 3) >= a.nl) {  // ghost on the plus side
+      const int gslot = (a.clo + (tp >> 3) - a.nl) * 24 + (2 * D) * 4 + ab;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(1) * dtdx) * Fp[v] / T(8);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) du[v] = Fm[v] - Fp[v];
+}
+
+template <class T>
+__global__ void k_flux_update(LevelArgs<T> a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 8 * a.nl) return;
+  if (cell_is_split(a, t)) return;
+  const int e = a.lo + (t >> 3);
+  const int c = t & 7;
+  const T dtdx = level_dtdx(a);
+  T dx[5], dy[5], dz[5];
+  faces_dir<0>(a, t, e, c, dtdx, dx);
+  faces_dir<1>(a, t, e, c, dtdx, dy);
+  faces_dir<2>(a, t, e, c, dtdx, dz);
+  const int g = 8 * e + c;
+  const int rs = __ldg(a.rslot + g);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    T *Ug = a.U + v * a.S + g;
+    T u = *Ug + dtdx * ((dx[v] + dy[v]) + dz[v]);
+    if (rs >= 0) {
+      T *Rv = a.Rc + v * int64_t(a.NC) + rs;
+      u = u + *Rv;
+      *Rv = T(0);
+    }
+    *Ug = u;
+  }
+}
+
+// k_reflux and k_restrict in one launch: they touch disjoint data (reflux
+// sums go to the pending reflux of leaf cells of level l-1, restriction
+// writes split cells of level l-1)
+template <class T>
+__global__ void k_reflux_restrict(LevelArgs<T> a, int do_restrict) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nref = a.reflux ? 5 * a.ncl : 0;
+  if (q < nref) {
+    const int v = q / a.ncl;
+    const int s = a.clo + (q - v * a.ncl);
+    const T *cv = a.C + v * a.CS + 24 * int64_t(s);
+    T *Rv = a.Rc + v * int64_t(a.NC) + s;
+    T acc = *Rv;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc += cv[k];
+    *Rv = acc;
+    return;
+  }
+  const int r = q - nref;
+  if (!do_restrict || r >= 5 * a.nl) return;
+  const int v = r / a.nl;
+  const int o = a.lo + (r - v * a.nl);
+  const uint64_t k = __ldg(a.key + o);
+  const int fc = int((key_x(k) & 1) | ((key_y(k) & 1) << 1) | ((key_z(k) & 1) << 2));
+  const int f = __ldg(a.father + o);
+  const T *src = a.U + v * a.S + 8 * o;
+  T sum = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) sum += src[c];
+  a.U[v * a.S + 8 * f + fc] = sum * T(0.125);
+}
+
+// ---------------------------------------------------------------------------
 // CFL time step: per-level max of sum_d (|u_d| + c) over leaf cells (cell
 // speeds in the state's precision, the maximum and dt in FP64), warp-shuffle
 // then block reduction, one integer atomicMax per block on the bit pattern

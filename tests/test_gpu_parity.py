@@ -287,3 +287,37 @@ def test_full_size_lognormal_sampled_level_steps():
         cells = (8 * pick[:, None] + np.arange(8)[None, :]).ravel()
         close(Ug[:, cells], want, 1e-12, f"lognormal level {l}")
         g.close()
+
+
+@pytest.mark.parametrize("cfg", ["random", "sod", "sedov"])
+def test_fp32_l1_error_per_config(cfg):
+    """FP32 state path against the FP64 oracle, one coarse W-cycle step:
+    L1 relative error of rho and E per level (reported with -s)."""
+    import oracle
+    from paper_2607_20704_gb300 import amr
+    prob = {"random": lambda: _random(21, 3, 6), "sod": inputs.sod, "sedov": inputs.sedov}[cfg]()
+    g = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=4)
+    o = oracle.Mesh(*prob.mesh_args(), **prob.params())
+    o.advance(1)
+    g.advance(1, sync=True)
+    worst = 0.0
+    for l in o.levels():
+        _, Ug = g.read(l)
+        _, Uo = o.read(l)
+        l1 = np.abs(Ug - Uo).sum(axis=1) / np.maximum(np.abs(Uo).sum(axis=1), 1e-300)
+        print(f"FP32 L1 {cfg} level {l}: rho {l1[0]:.2e} E {l1[4]:.2e}")
+        worst = max(worst, l1[0], l1[4])
+    assert worst < 5e-6, worst
+
+
+def test_fp32_runs_repeat_bit_for_bit():
+    prob = _random(22, 3, 6)
+    from paper_2607_20704_gb300 import amr
+    outs = []
+    for _ in range(2):
+        g = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=4)
+        g.advance(3)
+        outs.append([g.read(l)[1] for l in g.levels()])
+        g.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
