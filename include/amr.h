@@ -108,6 +108,43 @@ amr_status amr_create(const amr_params *p, int64_t n_oct, const uint8_t *level,
                       const uint32_t *i, const uint32_t *j, const uint32_t *k,
                       const uint64_t *hilbert_key, const double *U, amr_handle *out);
 
+/* One member mesh of a batched handle: its own levels, gas, floors and oct
+ * list, with the same meaning and layout as the arguments of amr_create. */
+typedef struct {
+  int levelmin, levelmax;
+  double gamma, cfl, smallr, smallc;
+  int64_t n_oct;
+  const uint8_t *level;
+  const uint32_t *i, *j, *k;
+  const uint64_t *hilbert_key; /* NULL for every member, or given for every member */
+  const double *U;             /* [5][8*n_oct] */
+} amr_member;
+
+/*
+ * amr_create_batch -- one handle over n_members independent meshes (the
+ * batched serving of many small solves; the paper's method applies to each
+ * mesh unchanged).  Octs are ordered by (member, level, Hilbert key); every
+ * level-step launch covers all members (a flattened list of (member, level)
+ * tiles), and amr_advance moves each member by its own CFL time step through
+ * its own W-cycle, the W-cycles aligned phase by phase.  Results of a member
+ * are bit-identical to the same mesh in a handle of its own.  p supplies the
+ * shared settings (precision, reflux, reindex_every_step, use_graphs,
+ * hbm_budget_bytes, stream, allocator); its per-mesh fields are ignored.
+ * amr_create(p, ...) is amr_create_batch with one member built from p.
+ * At most 32768 members and 2^26 octs in total.
+ */
+amr_status amr_create_batch(const amr_params *p, int n_members, const amr_member *members,
+                            amr_handle *out);
+
+/* Selects the member that amr_read, amr_write, amr_read_reflux, amr_lookup,
+ * amr_read_index, amr_read_cache, amr_cfl_dt and the dt of amr_advance refer
+ * to (default 0). */
+amr_status amr_select_member(amr_handle h, int member);
+
+/* The last coarse time step of every member (from amr_cfl_dt or
+ * amr_advance), copied into dt_out[0..n_members) (synchronous). */
+amr_status amr_member_dt(amr_handle h, double *dt_out, int n);
+
 /* Frees every device buffer of the handle (after synchronising its stream). */
 amr_status amr_destroy(amr_handle h);
 
@@ -130,7 +167,8 @@ amr_status amr_cfl_dt(amr_handle h, double *dt_out);
  * restriction of the level onto its father cells.  Asynchronous on the
  * handle's stream.  The caller runs levels in the W-cycle order: a level
  * l < finest takes its step after the two half steps of level l+1.
- * Errors: AMR_EINVAL for a level outside [levelmin, levelmax] or dt <= 0.
+ * In a batched handle the call advances that level of every member with the
+ * same dt.  Errors: AMR_EINVAL for a level outside [1, levelmax] or dt <= 0.
  */
 amr_status amr_step_level(amr_handle h, int level, double dt);
 
@@ -194,13 +232,16 @@ amr_status amr_read_cache(amr_handle h, int level, int64_t *n_out, int64_t *firs
 amr_status amr_fill_ghosts(amr_handle h, int level);
 
 typedef struct {
-  int64_t n_oct, n_cache, n_leaf_cells;
-  int64_t level_octs[16], level_cache[16], level_leaf_cells[16];
+  int64_t n_oct, n_cache, n_leaf_cells;  /* all members */
+  int64_t level_octs[16], level_cache[16], level_leaf_cells[16]; /* selected member */
   int64_t device_bytes;       /* bytes held on the device */
   int64_t kernel_launches;    /* kernels launched by the handle so far */
   int64_t graph_launches;     /* CUDA graph launches so far */
   int64_t hash_capacity;
+  int64_t work_per_step;      /* leaf cell-updates of one coarse step, all members */
   int precision;
+  int n_members, member;      /* members of the handle; the selected one */
+  int phases;                 /* level-step phases of one coarse step */
 } amr_info;
 
 /* Counts of the mesh and of the work done so far. */

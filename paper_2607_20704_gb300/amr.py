@@ -46,7 +46,18 @@ class amr_info(C.Structure):
                 ("level_leaf_cells", C.c_int64 * 16),
                 ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
                 ("graph_launches", C.c_int64), ("hash_capacity", C.c_int64),
-                ("precision", C.c_int)]
+                ("work_per_step", C.c_int64),
+                ("precision", C.c_int), ("n_members", C.c_int), ("member", C.c_int),
+                ("phases", C.c_int)]
+
+
+class amr_member(C.Structure):
+    _fields_ = [("levelmin", C.c_int), ("levelmax", C.c_int),
+                ("gamma", C.c_double), ("cfl", C.c_double),
+                ("smallr", C.c_double), ("smallc", C.c_double),
+                ("n_oct", C.c_int64),
+                ("level", C.c_void_p), ("i", C.c_void_p), ("j", C.c_void_p), ("k", C.c_void_p),
+                ("hilbert_key", C.c_void_p), ("U", C.c_void_p)]
 
 
 class AmrError(RuntimeError):
@@ -63,7 +74,8 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_advance", "amr_reindex", "amr_read", "amr_read_reflux", "amr_write",
            "amr_lookup", "amr_read_index", "amr_read_cache", "amr_fill_ghosts", "amr_get_info",
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
-           "amr_status_string", "amr_cfl_dt_static"]
+           "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
+           "amr_member_dt"]
 
 # fixed scratch limit of amr_cfl_dt_static (AMR_CFL_STATIC_MAX_CELLS in amr.h)
 CFL_STATIC_MAX_CELLS = 65536 * 256
@@ -104,6 +116,9 @@ def load(path: str | None = None):
             "amr_last_error": (C.c_char_p, []),
             "amr_status_string": (C.c_char_p, [I]),
             "amr_cfl_dt_static": (I, [P, I64, I64, I, D, D, D, D, P, P]),
+            "amr_create_batch": (I, [C.POINTER(amr_params), I, C.POINTER(amr_member), C.POINTER(P)]),
+            "amr_select_member": (I, [P, I]),
+            "amr_member_dt": (I, [P, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -161,12 +176,13 @@ def kernel_names():
 
 
 class Mesh:
-    """One resident octree (wraps an ``amr_handle``)."""
+    """One resident handle (wraps an ``amr_handle``): a single mesh, or with
+    ``Mesh.batch`` many independent member meshes advanced together."""
 
-    def __init__(self, level, i, j, k, U, *, levelmin, levelmax, gamma, cfl=0.8,
-                 smallr=1e-10, smallc=1e-10, precision=8, reflux=True,
+    def __init__(self, level=None, i=None, j=None, k=None, U=None, *, levelmin=1, levelmax=1,
+                 gamma=1.4, cfl=0.8, smallr=1e-10, smallc=1e-10, precision=8, reflux=True,
                  reindex_every_step=True, use_graphs=True, hbm_budget_bytes=0,
-                 hilbert_key=None, allocator="torch", stream=None):
+                 hilbert_key=None, allocator="torch", stream=None, members=None):
         torch = _torch()
         L = load()
         p = amr_params()
@@ -183,22 +199,62 @@ class Mesh:
         if allocator == "torch":
             p.alloc, p.free = _torch_alloc, _torch_free
         self.params = p
-        level = np.ascontiguousarray(level, dtype=np.uint8)
-        i = np.ascontiguousarray(i, dtype=np.uint32)
-        j = np.ascontiguousarray(j, dtype=np.uint32)
-        k = np.ascontiguousarray(k, dtype=np.uint32)
-        U = np.ascontiguousarray(U, dtype=np.float64)
-        n = level.shape[0]
-        if U.shape != (NV, 8 * n):
-            raise ValueError(f"U must have shape (5, {8 * n}), got {U.shape}")
-        hk = None if hilbert_key is None else np.ascontiguousarray(hilbert_key, dtype=np.uint64)
+        if members is None:
+            members = [dict(level=level, i=i, j=j, k=k, U=U, levelmin=levelmin, levelmax=levelmax,
+                            gamma=gamma, cfl=cfl, smallr=smallr, smallc=smallc,
+                            hilbert_key=hilbert_key)]
+        keep = []
+        arr = (amr_member * len(members))()
+        for t, mb in enumerate(members):
+            lv = np.ascontiguousarray(mb["level"], dtype=np.uint8)
+            ii = np.ascontiguousarray(mb["i"], dtype=np.uint32)
+            jj = np.ascontiguousarray(mb["j"], dtype=np.uint32)
+            kk = np.ascontiguousarray(mb["k"], dtype=np.uint32)
+            uu = np.ascontiguousarray(mb["U"], dtype=np.float64)
+            n = lv.shape[0]
+            if uu.shape != (NV, 8 * n):
+                raise ValueError(f"U must have shape (5, {8 * n}), got {uu.shape}")
+            hk = mb.get("hilbert_key")
+            hk = None if hk is None else np.ascontiguousarray(hk, dtype=np.uint64)
+            keep += [lv, ii, jj, kk, uu, hk]
+            m = arr[t]
+            m.levelmin, m.levelmax = int(mb["levelmin"]), int(mb["levelmax"])
+            m.gamma, m.cfl = float(mb["gamma"]), float(mb.get("cfl", 0.8))
+            m.smallr, m.smallc = float(mb.get("smallr", 1e-10)), float(mb.get("smallc", 1e-10))
+            m.n_oct = n
+            m.level, m.i, m.j, m.k, m.U = (_ptr(lv), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(uu))
+            m.hilbert_key = _ptr(hk) if hk is not None else None
         h = C.c_void_p()
-        rc = L.amr_create(C.byref(p), n, _ptr(level), _ptr(i), _ptr(j), _ptr(k), _ptr(hk),
-                          _ptr(U), C.byref(h))
+        rc = L.amr_create_batch(C.byref(p), len(members), arr, C.byref(h))
         _check(rc, "amr_create")
         self._h = h
-        self.levelmin, self.levelmax, self.gamma = int(levelmin), int(levelmax), float(gamma)
+        self.n_members = len(members)
+        self.member_levels = [(int(mb["levelmin"]), int(mb["levelmax"])) for mb in members]
+        self.levelmin, self.levelmax = self.member_levels[0]
+        self.gamma = float(members[0]["gamma"])
         self.precision = int(precision)
+        self._member = 0
+
+    @classmethod
+    def batch(cls, problems, **kw):
+        """A handle over several ``inputs.Problem`` meshes (one member each)."""
+        members = []
+        for pr in problems:
+            lv, i, j, k, U = pr.mesh_args()
+            members.append(dict(level=lv, i=i, j=j, k=k, U=U, **pr.params()))
+        return cls(members=members, **kw)
+
+    def select(self, member: int):
+        """Member that read/write/lookup/index calls refer to."""
+        _check(load().amr_select_member(self._h, int(member)), "amr_select_member")
+        self._member = int(member)
+        self.levelmin, self.levelmax = self.member_levels[int(member)]
+        return self
+
+    def member_dt(self):
+        out = np.zeros(self.n_members, np.float64)
+        _check(load().amr_member_dt(self._h, _ptr(out), self.n_members), "amr_member_dt")
+        return out
 
     # -- lifetime ----------------------------------------------------------------
     def close(self):
@@ -311,6 +367,8 @@ class Mesh:
             "level_leaf_cells": list(inf.level_leaf_cells), "device_bytes": inf.device_bytes,
             "kernel_launches": inf.kernel_launches, "graph_launches": inf.graph_launches,
             "hash_capacity": inf.hash_capacity, "precision": inf.precision,
+            "work_per_step": inf.work_per_step, "n_members": inf.n_members,
+            "member": inf.member, "phases": inf.phases,
         }
 
     def set_timing(self, on: bool):

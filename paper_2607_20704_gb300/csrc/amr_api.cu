@@ -2,6 +2,14 @@
 // Host orchestration only: every step of the mesh build, index and level
 // step runs in the kernels of index_kernels.cuh and hydro_kernels.cuh,
 // compiled here as one translation unit.
+//
+// A handle holds one or more independent member meshes.  Octs are ordered
+// by (member, level, Hilbert key), so each (member, level) is a contiguous
+// segment; a level-step launch runs over a flattened list of tiles of many
+// segments.  A coarse step advances every member by its own CFL time step
+// through its own W-cycle; the members' W-cycles are aligned phase by phase
+// (phase k runs the k-th level step of every member in one launch per
+// kernel), and one coarse step is captured once as a CUDA graph.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -76,7 +84,7 @@ static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
     "father_son", "grading", "neighbours", "claim_comp", "cache_finalize", "neighbours_fix",
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
-    "reflux", "restrict", "cfl", "dt", "convert"};
+    "reflux", "reflux_restrict", "cfl", "dt", "convert"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -92,6 +100,27 @@ struct DevBuf {
   size_t bytes;
 };
 
+// level-step launch domains of a segment
+enum Dom { DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_COUNT = 4 };
+
+// a list of segments and, per domain, its flattened tiles
+struct SegList {
+  int seg0 = 0, nseg = 0;
+  int tile0[DOM_COUNT] = {0, 0, 0, 0}, ntile[DOM_COUNT] = {0, 0, 0, 0};
+  int ls = 0;  // scratch cells used
+};
+
+struct Member {
+  int lmin = 1, lmax = 1;
+  double gamma = 1.4, cfl = 0.8, smallr = 1e-10, smallc = 1e-10;
+  int64_t n_oct = 0;
+  int64_t oct_base = 0, cache_base = 0;  // first mesh index, first ghost slot
+  int64_t lo[kMaxLev + 2] = {0};         // member-local level offsets of real octs
+  int64_t clo[kMaxLev + 2] = {0};        // member-local level offsets of ghost octs
+  int64_t leaf[kMaxLev + 1] = {0};
+  std::vector<int> seq;                  // levels of its W-cycle, in order
+};
+
 // ---------------------------------------------------------------------------
 // the handle
 // ---------------------------------------------------------------------------
@@ -99,19 +128,19 @@ struct amr_mesh {
   amr_params p{};
   cudaStream_t s = nullptr;
   bool own_stream = false;
-  int device = 0;
+  int device = 0, sm_count = 152;
   size_t bytes = 0;
   std::vector<DevBuf> bufs;
 
+  int M = 1, sel = 0, lmax_all = 1;
+  std::vector<Member> mem;
   int64_t N = 0, NC = 0, NE = 0, S = 0;
-  int64_t lo[kMaxLev + 2] = {0};   // real octs of level l: [lo[l], lo[l+1])
-  int64_t clo[kMaxLev + 2] = {0};  // ghost octs of level l: [clo[l], clo[l+1])
-  int64_t leaf[kMaxLev + 1] = {0};
-  int B = 1;                       // bits per coordinate in ghost sort keys
+  int B = 1;  // bits per coordinate in ghost sort keys
 
   // index
   uint64_t *key = nullptr;
   int32_t *nbr27 = nullptr, *fnb = nullptr, *father = nullptr, *csrc = nullptr;
+  int32_t *rslot = nullptr;
   uint32_t *son = nullptr;
   uint64_t *ckey = nullptr;
   HashView hash{};
@@ -119,19 +148,33 @@ struct amr_mesh {
   uint64_t *claim = nullptr, *comp0 = nullptr, *comp1 = nullptr;
   uint32_t *val0 = nullptr, *val1 = nullptr;
   int64_t claim_cap = 0;
-  uint32_t *counters = nullptr;  // [0] claim count, [1..16] ghost level counts
+  uint32_t *counters = nullptr;    // [0] claim count
+  uint32_t *seg_count = nullptr;   // [16 M] octs / ghost octs per (member, level)
   uint32_t *table = nullptr, *scan_tmp = nullptr;
   int64_t table_cap = 0, scan_cap = 0;
 
-  // state and scratch
-  void *U = nullptr, *Rc = nullptr;  // Rc: pending reflux per ghost oct [5][NC]
-  int32_t *rslot = nullptr;          // [8N] ghost slot whose father is the cell
-  void *W = nullptr, *Q = nullptr, *F = nullptr, *C = nullptr;
-  int64_t max_ls = 0, max_cs = 0;
-  double *dt_dev = nullptr;
-  float *dtf_dev = nullptr;
+  // members on the device
+  int *mlmin = nullptr, *mlmax = nullptr;
+  double *mgamma_d = nullptr, *mcfl_d = nullptr, *msmallr_d = nullptr, *msmallp_d = nullptr;
+  void *mgamma_t = nullptr, *migm1_t = nullptr, *msmallr_t = nullptr, *msmallp_t = nullptr;
+  double *dt_dev = nullptr, *dtdx_dev = nullptr;
+  float *dtdxf_dev = nullptr;
   unsigned long long *smax = nullptr;
   int *err = nullptr;
+
+  // segments and tiles
+  std::vector<Seg> segs_h;
+  std::vector<Tile> tiles_h;
+  Seg *segs = nullptr;
+  Tile *tiles = nullptr;
+  std::vector<SegList> phases;
+  SegList level_list[kMaxLev + 1], restrict_list[kMaxLev + 1], cfl_list;
+  int tile_size = 256;
+
+  // state and scratch
+  void *U = nullptr, *Rc = nullptr;
+  void *W = nullptr, *Q = nullptr, *F = nullptr, *C = nullptr;
+  int64_t max_ls = 0, max_cs = 0;
 
   // work accounting
   int64_t launches = 0, graph_launches = 0;
@@ -194,6 +237,14 @@ static amr_status alloc_n(amr_mesh *h, P **out, int64_t n) {
   void *p = nullptr;
   AMR_TRY(dev_alloc(h, &p, sizeof(P) * size_t(n > 0 ? n : 1)));
   *out = static_cast<P *>(p);
+  return AMR_OK;
+}
+
+template <class P>
+static amr_status upload(amr_mesh *h, P **out, const std::vector<P> &v) {
+  AMR_TRY(alloc_n(h, out, int64_t(v.size())));
+  if (!v.empty())
+    CUDA_TRY(cudaMemcpyAsync(*out, v.data(), sizeof(P) * v.size(), cudaMemcpyHostToDevice, h->s));
   return AMR_OK;
 }
 
@@ -311,23 +362,113 @@ static std::vector<std::pair<int, int>> digits_for(int shift0, int bits) {
   return d;
 }
 
+static int bits_for(int64_t n) {  // bits to hold values 0..n-1
+  int b = 0;
+  while ((int64_t(1) << b) < n) ++b;
+  return b;
+}
+
 // ---------------------------------------------------------------------------
-// level-step arguments
+// segment lists
+// ---------------------------------------------------------------------------
+static int dom_size(const Seg &s, int dom) {
+  switch (dom) {
+    case DOM_CELLS: return 8 * (s.nl + s.ncl);
+    case DOM_REAL: return 8 * s.nl;
+    case DOM_GHOST5: return 5 * s.ncl;
+    default:
+      return ((s.flags & kSegReflux) ? 5 * s.ncl : 0) + ((s.flags & kSegRestrict) ? 5 * s.nl : 0);
+  }
+}
+
+// append the (member, level) segments of `ml` (flags from `mode`: 0 = level
+// step, 1 = restriction only) as one list
+static SegList make_list(amr_mesh *h, const std::vector<std::pair<int, int>> &ml, int mode) {
+  SegList L;
+  L.seg0 = int(h->segs_h.size());
+  int base = 0;
+  for (auto &pr : ml) {
+    const Member &m = h->mem[pr.first];
+    const int l = pr.second;
+    Seg s;
+    s.member = pr.first;
+    s.level = l;
+    s.lo = int(m.oct_base + m.lo[l]);
+    s.nl = int(m.lo[l + 1] - m.lo[l]);
+    s.clo = int(m.cache_base + m.clo[l]);
+    s.ncl = int(m.clo[l + 1] - m.clo[l]);
+    s.base = base;
+    if (mode == 1)
+      s.flags = l > m.lmin ? kSegRestrict : 0;
+    else
+      s.flags = (h->p.reflux && s.ncl ? kSegReflux : 0) | (l > m.lmin ? kSegRestrict : 0);
+    if (s.nl == 0) continue;
+    base += 8 * (s.nl + s.ncl);
+    h->segs_h.push_back(s);
+  }
+  L.nseg = int(h->segs_h.size()) - L.seg0;
+  L.ls = base;
+  for (int d = 0; d < DOM_COUNT; ++d) {
+    L.tile0[d] = int(h->tiles_h.size());
+    for (int q = 0; q < L.nseg; ++q) {
+      const int n = dom_size(h->segs_h[L.seg0 + q], d);
+      for (int st = 0; st < n; st += h->tile_size) h->tiles_h.push_back({L.seg0 + q, st});
+    }
+    L.ntile[d] = int(h->tiles_h.size()) - L.tile0[d];
+  }
+  return L;
+}
+
+static void w_cycle(const Member &m, int l, std::vector<int> &out) {
+  if (l + 1 <= kMaxLev && m.lo[l + 2] > m.lo[l + 1]) {
+    w_cycle(m, l + 1, out);
+    w_cycle(m, l + 1, out);
+  }
+  out.push_back(l);
+}
+
+static void build_lists(amr_mesh *h) {
+  h->segs_h.clear();
+  h->tiles_h.clear();
+  h->phases.clear();
+  size_t P = 0;
+  for (auto &m : h->mem) {
+    m.seq.clear();
+    w_cycle(m, m.lmin, m.seq);
+    P = std::max(P, m.seq.size());
+  }
+  for (size_t k = 0; k < P; ++k) {
+    std::vector<std::pair<int, int>> ml;
+    for (int q = 0; q < h->M; ++q)
+      if (k < h->mem[q].seq.size()) ml.push_back({q, h->mem[q].seq[k]});
+    h->phases.push_back(make_list(h, ml, 0));
+  }
+  for (int l = 0; l <= kMaxLev; ++l) {
+    std::vector<std::pair<int, int>> ml;
+    for (int q = 0; q < h->M; ++q) ml.push_back({q, l});
+    h->level_list[l] = make_list(h, ml, 0);
+    h->restrict_list[l] = make_list(h, ml, 1);
+  }
+  std::vector<std::pair<int, int>> all;
+  for (int q = 0; q < h->M; ++q)
+    for (int l = 0; l <= kMaxLev; ++l) all.push_back({q, l});
+  h->cfl_list = make_list(h, all, 0);
+  h->max_ls = 0;
+  for (auto &L : h->phases) h->max_ls = std::max<int64_t>(h->max_ls, L.ls);
+  for (int l = 0; l <= kMaxLev; ++l) h->max_ls = std::max<int64_t>(h->max_ls, h->level_list[l].ls);
+}
+
+// ---------------------------------------------------------------------------
+// level-step launches
 // ---------------------------------------------------------------------------
 template <class T>
-static LevelArgs<T> level_args(amr_mesh *h, int l, const double *dt_dev, double scale, double dt) {
-  LevelArgs<T> a{};
-  a.l = l;
-  a.lmin = h->p.levelmin;
-  a.lo = int(h->lo[l]);
-  a.nl = int(h->lo[l + 1] - h->lo[l]);
-  a.clo = int(h->clo[l]);
-  a.ncl = int(h->clo[l + 1] - h->clo[l]);
+static StepArgs<T> step_args(amr_mesh *h, bool device_dt, double dt) {
+  StepArgs<T> a{};
   a.N = int(h->N);
   a.NE = int(h->NE);
   a.NC = int(h->NC);
+  a.LS = int(h->max_ls);
   a.S = h->S;
-  a.LS = 8 * (a.nl + a.ncl);
   a.CS = 24 * h->NC;
   a.U = static_cast<T *>(h->U);
   a.Rc = static_cast<T *>(h->Rc);
@@ -341,85 +482,99 @@ static LevelArgs<T> level_args(amr_mesh *h, int l, const double *dt_dev, double 
   a.Q = static_cast<T *>(h->Q);
   a.F = static_cast<T *>(h->F);
   a.C = static_cast<T *>(h->C);
-  a.dt_dev = dt_dev;
-  a.dtf_dev = dt_dev ? h->dtf_dev : nullptr;
-  a.dtdx_scale = scale * ldexp(1.0, l);
-  a.dtdx_host = T(dt * ldexp(1.0, l));
-  a.gamma = T(h->p.gamma);
-  a.igm1 = T(1.0 / (h->p.gamma - 1.0));
-  a.smallr = T(h->p.smallr);
-  a.smallp = T(h->p.smallc * h->p.smallc / h->p.gamma);
+  a.segs = h->segs;
+  a.mgamma = static_cast<const T *>(h->mgamma_t);
+  a.migm1 = static_cast<const T *>(h->migm1_t);
+  a.msmallr = static_cast<const T *>(h->msmallr_t);
+  a.msmallp = static_cast<const T *>(h->msmallp_t);
+  a.dtdx_dev = device_dt ? h->dtdx_dev : nullptr;
+  a.dtdxf_dev = device_dt ? h->dtdxf_dev : nullptr;
+  a.dt_host = dt;
   a.reflux = h->p.reflux;
   return a;
 }
 
+// persistent grid: enough blocks to fill the GPU once, never more than tiles
 template <class T>
-static void run_level_step(amr_mesh *h, int l, const double *dt_dev, double scale, double dt) {
-  LevelArgs<T> a = level_args<T>(h, l, dt_dev, scale, dt);
-  if (a.nl == 0) return;
-  if (a.ncl) launch(h, K_PROLONG, k_prolong<T>, dim3(nblocks(5 * a.ncl)), dim3(256), a);
+static void run_list(amr_mesh *h, int kid, void (*kern)(StepArgs<T>), StepArgs<T> a,
+                     const SegList &L, int dom) {
+  if (L.ntile[dom] == 0) return;
+  a.tiles = h->tiles + L.tile0[dom];
+  a.ntiles = L.ntile[dom];
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, h->tile_size, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int grid = std::min(a.ntiles, per_sm * h->sm_count);
+  launch(h, kid, kern, dim3(unsigned(grid)), dim3(unsigned(h->tile_size)), a);
+}
+
+template <class T>
+static void run_segments(amr_mesh *h, const SegList &L, bool device_dt, double dt) {
+  if (L.nseg == 0) return;
+  StepArgs<T> a = step_args<T>(h, device_dt, dt);
+  run_list(h, K_PROLONG, k_prolong<T>, a, L, DOM_GHOST5);
   if (sizeof(T) == 4) {
     // FP32: primitives recomputed inside the predictor; each leaf cell solves
     // its six faces and updates itself
-    launch(h, K_PREDICT, k_predict_u<T>, dim3(nblocks(a.LS)), dim3(256), a);
-    launch(h, K_FLUX, k_flux_update<T>, dim3(nblocks(8 * a.nl)), dim3(256), a);
+    run_list(h, K_PREDICT, k_predict_u<T>, a, L, DOM_CELLS);
+    run_list(h, K_FLUX, k_flux_update<T>, a, L, DOM_REAL);
   } else {
     // FP64: every predictor and every face solve exactly once
-    launch(h, K_PRIM, k_prim<T>, dim3(nblocks(a.LS)), dim3(256), a);
-    launch(h, K_PREDICT, k_predict<T>, dim3(nblocks(a.LS)), dim3(256), a);
-    launch(h, K_FLUX, k_flux<T>, dim3(nblocks(a.LS)), dim3(256), a);
-    launch(h, K_UPDATE, k_update<T>, dim3(nblocks(8 * a.nl)), dim3(256), a);
+    run_list(h, K_PRIM, k_prim<T>, a, L, DOM_CELLS);
+    run_list(h, K_PREDICT, k_predict<T>, a, L, DOM_CELLS);
+    run_list(h, K_FLUX, k_flux<T>, a, L, DOM_CELLS);
+    run_list(h, K_UPDATE, k_update<T>, a, L, DOM_REAL);
   }
-  const int do_restrict = l > h->p.levelmin;
-  const int64_t nq = (h->p.reflux ? 5 * int64_t(a.ncl) : 0) + (do_restrict ? 5 * int64_t(a.nl) : 0);
-  if (nq) launch(h, K_RESTRICT, k_reflux_restrict<T>, dim3(nblocks(nq)), dim3(256), a, do_restrict);
+  run_list(h, K_RESTRICT, k_reflux_restrict<T>, a, L, DOM_POST);
 }
 
-static void level_step(amr_mesh *h, int l, const double *dt_dev, double scale, double dt) {
+static void step_segments(amr_mesh *h, const SegList &L, bool device_dt, double dt) {
   if (h->p.precision == 4)
-    run_level_step<float>(h, l, dt_dev, scale, dt);
+    run_segments<float>(h, L, device_dt, dt);
   else
-    run_level_step<double>(h, l, dt_dev, scale, dt);
+    run_segments<double>(h, L, device_dt, dt);
+}
+
+template <class T>
+static void restrict_segments(amr_mesh *h, const SegList &L) {
+  if (L.nseg == 0) return;
+  run_list(h, K_RESTRICT, k_reflux_restrict<T>, step_args<T>(h, false, 0.0), L, DOM_POST);
 }
 
 static CflArgs cfl_args(amr_mesh *h) {
   CflArgs a{};
-  a.lmin = h->p.levelmin;
-  a.lmax = h->p.levelmax;
-  for (int l = 0; l <= kMaxLev + 1; ++l) a.lo[l] = h->lo[l];
+  a.segs = h->segs;
+  a.tiles = h->tiles + h->cfl_list.tile0[DOM_REAL];
+  a.ntiles = h->cfl_list.ntile[DOM_REAL];
   a.S = h->S;
   a.son = h->son;
-  a.gamma = h->p.gamma;
-  a.smallr = h->p.smallr;
-  a.smallp = h->p.smallc * h->p.smallc / h->p.gamma;
-  a.cfl = h->p.cfl;
+  a.mgamma = h->mgamma_d;
+  a.msmallr = h->msmallr_d;
+  a.msmallp = h->msmallp_d;
+  a.mcfl = h->mcfl_d;
+  a.mlmin = h->mlmin;
+  a.nmembers = h->M;
   a.smax = h->smax;
   a.dt_dev = h->dt_dev;
-  a.dtf_dev = h->dtf_dev;
+  a.dtdx_dev = h->dtdx_dev;
+  a.dtdxf_dev = h->dtdxf_dev;
   a.err = h->err;
   return a;
 }
 
 static void cfl_device(amr_mesh *h) {
   CflArgs a = cfl_args(h);
-  int64_t maxcells = 0;
-  for (int l = h->p.levelmin; l <= h->p.levelmax; ++l)
-    maxcells = std::max<int64_t>(maxcells, 8 * (h->lo[l + 1] - h->lo[l]));
-  // a few waves of 256-thread blocks per level, grid-stride inside
-  dim3 grid(std::min<unsigned>(nblocks(maxcells), 152 * 4), unsigned(h->p.levelmax - h->p.levelmin + 1));
-  if (h->p.precision == 4)
-    launch(h, K_CFL, k_cfl<float>, grid, dim3(256), a, (const float *)h->U);
-  else
-    launch(h, K_CFL, k_cfl<double>, grid, dim3(256), a, (const double *)h->U);
-  launch(h, K_DT, k_dt, dim3(1), dim3(1), a);
-}
-
-static void advance_level(amr_mesh *h, int l, double scale) {
-  if (l + 1 <= h->p.levelmax && h->lo[l + 2] > h->lo[l + 1]) {
-    advance_level(h, l + 1, 0.5 * scale);
-    advance_level(h, l + 1, 0.5 * scale);
+  const unsigned grid = unsigned(std::min(a.ntiles, 4 * h->sm_count));
+  if (grid) {
+    if (h->p.precision == 4)
+      launch(h, K_CFL, k_cfl<float>, dim3(grid), dim3(unsigned(h->tile_size)), a, (const float *)h->U);
+    else
+      launch(h, K_CFL, k_cfl<double>, dim3(grid), dim3(unsigned(h->tile_size)), a, (const double *)h->U);
   }
-  level_step(h, l, h->dt_dev, scale, 0.0);
+  launch(h, K_DT, k_dt, dim3(nblocks(h->M, 128)), dim3(128), a);
 }
 
 // ---------------------------------------------------------------------------
@@ -430,16 +585,14 @@ static amr_status build_index(amr_mesh *h, bool first) {
   cudaMemsetAsync(h->hash.key, 0xFF, sizeof(uint64_t) * h->hcap, h->s);
   cudaMemsetAsync(h->hash.val, 0, sizeof(int32_t) * h->hcap, h->s);
   cudaMemsetAsync(h->son, 0, sizeof(uint32_t) * N, h->s);
-  cudaMemsetAsync(h->counters, 0, sizeof(uint32_t) * 32, h->s);
+  cudaMemsetAsync(h->counters, 0, sizeof(uint32_t) * 4, h->s);
   launch(h, K_HASH_INSERT, k_hash_insert, dim3(nblocks(N)), dim3(256), h->hash,
          (const uint64_t *)h->key, N, h->err);
-  const int64_t first_fine = h->lo[h->p.levelmin + 1];
-  cudaMemsetAsync(h->father, 0xFF, sizeof(int32_t) * N, h->s);
-  launch(h, K_FATHER_SON, k_father_son, dim3(nblocks(N - first_fine)), dim3(256), h->hash,
-         (const uint64_t *)h->key, first_fine, N, h->father, h->son, h->err);
+  launch(h, K_FATHER_SON, k_father_son, dim3(nblocks(N)), dim3(256), h->hash,
+         (const uint64_t *)h->key, N, (const int *)h->mlmin, h->father, h->son, h->err);
   if (first)
-    launch(h, K_GRADING, k_grading, dim3(nblocks(8 * 27 * (N - first_fine))), dim3(256), h->hash,
-           (const uint64_t *)h->key, first_fine, N, h->err);
+    launch(h, K_GRADING, k_grading, dim3(nblocks(8 * 27 * N)), dim3(256), h->hash,
+           (const uint64_t *)h->key, N, (const int *)h->mlmin, h->err);
   launch(h, K_NEIGHBOURS, k_neighbours, dim3(nblocks(27 * N)), dim3(256), h->hash,
          (const uint64_t *)h->key, N, h->nbr27, h->claim, h->counters, h->claim_cap, h->err);
   if (first) {  // create: stop after the claims; the caller sizes the ghost buffers
@@ -450,37 +603,35 @@ static amr_status build_index(amr_mesh *h, bool first) {
     h->NC = nc;
     return AMR_OK;
   }
-  const int64_t NC = h->NC;
-  if (NC > 0) {
-    launch(h, K_CLAIM, k_claim_to_comp, dim3(nblocks(NC)), dim3(256), (const uint64_t *)h->claim,
-           NC, h->B, h->comp0, h->val0);
+  if (h->NC > 0) {
+    launch(h, K_CLAIM, k_claim_to_comp, dim3(nblocks(h->NC)), dim3(256), (const uint64_t *)h->claim,
+           h->NC, h->B, h->comp0, h->val0);
     uint64_t *k = h->comp0;
     uint32_t *v = h->val0;
-    radix_sort(h, &k, &v, h->comp1, h->val1, NC, digits_for(0, 4 + 3 * h->B));
-    launch(h, K_CACHE_FINALIZE, k_cache_finalize, dim3(nblocks(NC)), dim3(256), h->hash,
-           (const uint64_t *)k, NC, h->B, N, h->ckey, h->counters + 1, h->err);
+    radix_sort(h, &k, &v, h->comp1, h->val1, h->NC, digits_for(0, 4 + 3 * h->B + bits_for(h->M)));
+    launch(h, K_CACHE_FINALIZE, k_cache_finalize, dim3(nblocks(h->NC)), dim3(256), h->hash,
+           (const uint64_t *)k, h->NC, h->B, N, h->ckey, (uint32_t *)nullptr, h->err);
     launch(h, K_NBR_FIX, k_neighbours_fix, dim3(nblocks(27 * N)), dim3(256), h->hash,
            (const uint64_t *)h->key, N, h->nbr27, h->err);
   }
   return AMR_OK;
 }
 
-static amr_status build_faces_and_sources(amr_mesh *h) {
+static void build_faces_and_sources(amr_mesh *h) {
   launch(h, K_FACES, k_faces_real, dim3(nblocks(6 * h->N)), dim3(256), (const int32_t *)h->nbr27,
          h->N, h->NE, h->fnb);
+  cudaMemsetAsync(h->rslot, 0xFF, sizeof(int32_t) * 8 * h->N, h->s);
   if (h->NC) {
     launch(h, K_FACES, k_faces_cache, dim3(nblocks(6 * h->NC)), dim3(256), h->hash,
            (const uint64_t *)h->ckey, h->NC, h->N, h->NE, h->fnb);
-    cudaMemsetAsync(h->rslot, 0xFF, sizeof(int32_t) * 8 * h->N, h->s);
     launch(h, K_CACHE_SOURCES, k_cache_sources, dim3(nblocks(h->NC)), dim3(256), h->hash,
-           (const uint64_t *)h->ckey, h->NC, h->N, h->p.levelmin, h->csrc, h->rslot, h->err);
+           (const uint64_t *)h->ckey, h->NC, h->N, (const int *)h->mlmin, h->csrc, h->rslot, h->err);
   }
-  return AMR_OK;
 }
 
 static amr_status reindex(amr_mesh *h) {
   AMR_TRY(build_index(h, false));
-  AMR_TRY(build_faces_and_sources(h));
+  build_faces_and_sources(h);
   if (h->max_cs) cudaMemsetAsync(h->C, 0, h->elem() * 5 * size_t(h->max_cs), h->s);
   return AMR_OK;
 }
@@ -518,96 +669,180 @@ static void destroy_all(amr_mesh *h) {
 }
 
 template <class T>
-static void initial_restriction(amr_mesh *h) {
-  for (int l = h->p.levelmax; l > h->p.levelmin; --l) {
-    LevelArgs<T> a = level_args<T>(h, l, nullptr, 1.0, 0.0);
-    if (a.nl) launch(h, K_RESTRICT, k_restrict<T>, dim3(nblocks(5 * a.nl)), dim3(256), a);
+static amr_status upload_member_params(amr_mesh *h) {
+  std::vector<T> g(h->M), igm1(h->M), sr(h->M), sp(h->M);
+  for (int q = 0; q < h->M; ++q) {
+    const Member &m = h->mem[q];
+    g[q] = T(m.gamma);
+    igm1[q] = T(1.0 / (m.gamma - 1.0));
+    sr[q] = T(m.smallr);
+    sp[q] = T(m.smallc * m.smallc / m.gamma);
   }
+  T *a, *b, *c, *d;
+  AMR_TRY(upload(h, &a, g));
+  AMR_TRY(upload(h, &b, igm1));
+  AMR_TRY(upload(h, &c, sr));
+  AMR_TRY(upload(h, &d, sp));
+  h->mgamma_t = a;
+  h->migm1_t = b;
+  h->msmallr_t = c;
+  h->msmallp_t = d;
+  return AMR_OK;
 }
 
-static amr_status create_impl(amr_mesh *h, int64_t n, const uint8_t *level, const uint32_t *i,
-                              const uint32_t *j, const uint32_t *k, const uint64_t *hk,
-                              const double *U) {
+static amr_status create_impl(amr_mesh *h, const amr_member *members) {
   const amr_params &p = h->p;
-  // inputs to the device
+  const int M = h->M;
+  // --- members and host staging of the concatenated oct list ------------------
+  int64_t n = 0;
+  int have_hk = 0;
+  for (int q = 0; q < M; ++q) {
+    const amr_member &a = members[q];
+    Member &m = h->mem[q];
+    m.lmin = a.levelmin;
+    m.lmax = a.levelmax;
+    m.gamma = a.gamma;
+    m.cfl = a.cfl;
+    m.smallr = a.smallr;
+    m.smallc = a.smallc;
+    m.n_oct = a.n_oct;
+    n += a.n_oct;
+    have_hk += a.hilbert_key != nullptr;
+    h->lmax_all = std::max(h->lmax_all, a.levelmax);
+  }
+  if (have_hk != 0 && have_hk != M)
+    return fail(AMR_EINVAL, "amr_create: give sort keys for every member or for none");
+  if (n > (int64_t(1) << 26)) return fail(AMR_EINVAL, "amr_create: more than 2^26 octs in total");
+  std::vector<uint8_t> lv(n);
+  std::vector<uint32_t> ci(n), cj(n), ck(n);
+  std::vector<uint16_t> mm(n);
+  std::vector<uint64_t> hk(have_hk ? n : 0);
+  std::vector<double> U(40 * size_t(n));
+  {
+    int64_t off = 0;
+    for (int q = 0; q < M; ++q) {
+      const amr_member &a = members[q];
+      const int64_t nm = a.n_oct;
+      std::memcpy(lv.data() + off, a.level, nm);
+      std::memcpy(ci.data() + off, a.i, 4 * nm);
+      std::memcpy(cj.data() + off, a.j, 4 * nm);
+      std::memcpy(ck.data() + off, a.k, 4 * nm);
+      for (int64_t t = 0; t < nm; ++t) mm[off + t] = uint16_t(q);
+      if (have_hk) std::memcpy(hk.data() + off, a.hilbert_key, 8 * nm);
+      for (int v = 0; v < 5; ++v)
+        std::memcpy(U.data() + v * 8 * n + 8 * off, a.U + v * 8 * nm, sizeof(double) * 8 * nm);
+      off += nm;
+    }
+  }
+  h->N = n;
+  // --- member parameters on the device -----------------------------------------
+  {
+    std::vector<int> lmin(M), lmax(M);
+    std::vector<double> g(M), cfl(M), sr(M), sp(M);
+    for (int q = 0; q < M; ++q) {
+      const Member &m = h->mem[q];
+      lmin[q] = m.lmin;
+      lmax[q] = m.lmax;
+      g[q] = m.gamma;
+      cfl[q] = m.cfl;
+      sr[q] = m.smallr;
+      sp[q] = m.smallc * m.smallc / m.gamma;
+    }
+    AMR_TRY(upload(h, &h->mlmin, lmin));
+    AMR_TRY(upload(h, &h->mlmax, lmax));
+    AMR_TRY(upload(h, &h->mgamma_d, g));
+    AMR_TRY(upload(h, &h->mcfl_d, cfl));
+    AMR_TRY(upload(h, &h->msmallr_d, sr));
+    AMR_TRY(upload(h, &h->msmallp_d, sp));
+    if (p.precision == 4)
+      AMR_TRY(upload_member_params<float>(h));
+    else
+      AMR_TRY(upload_member_params<double>(h));
+  }
+  // --- inputs to the device ------------------------------------------------------
   uint8_t *d_lvl;
+  uint16_t *d_mem;
   uint32_t *d_i, *d_j, *d_k, *perm, *perm_alt;
   uint64_t *d_hk = nullptr, *comp, *comp_alt;
   double *d_U;
-  AMR_TRY(alloc_n(h, &d_lvl, n));
-  AMR_TRY(alloc_n(h, &d_i, n));
-  AMR_TRY(alloc_n(h, &d_j, n));
-  AMR_TRY(alloc_n(h, &d_k, n));
-  AMR_TRY(alloc_n(h, &d_U, 40 * n));
-  if (hk) AMR_TRY(alloc_n(h, &d_hk, n));
+  AMR_TRY(upload(h, &d_lvl, lv));
+  AMR_TRY(upload(h, &d_mem, mm));
+  AMR_TRY(upload(h, &d_i, ci));
+  AMR_TRY(upload(h, &d_j, cj));
+  AMR_TRY(upload(h, &d_k, ck));
+  AMR_TRY(upload(h, &d_U, U));
+  if (have_hk) AMR_TRY(upload(h, &d_hk, hk));
   AMR_TRY(alloc_n(h, &perm, n));
   AMR_TRY(alloc_n(h, &perm_alt, n));
   AMR_TRY(alloc_n(h, &comp, n));
   AMR_TRY(alloc_n(h, &comp_alt, n));
   AMR_TRY(alloc_n(h, &h->err, 1));
   CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
-  CUDA_TRY(cudaMemcpyAsync(d_lvl, level, n, cudaMemcpyHostToDevice, h->s));
-  CUDA_TRY(cudaMemcpyAsync(d_i, i, 4 * n, cudaMemcpyHostToDevice, h->s));
-  CUDA_TRY(cudaMemcpyAsync(d_j, j, 4 * n, cudaMemcpyHostToDevice, h->s));
-  CUDA_TRY(cudaMemcpyAsync(d_k, k, 4 * n, cudaMemcpyHostToDevice, h->s));
-  CUDA_TRY(cudaMemcpyAsync(d_U, U, sizeof(double) * 40 * n, cudaMemcpyHostToDevice, h->s));
-  if (hk) CUDA_TRY(cudaMemcpyAsync(d_hk, hk, 8 * n, cudaMemcpyHostToDevice, h->s));
 
-  // sort: Hilbert digits (LSD), then the level bucket pass with prefix sums
+  // --- order: Hilbert digits (LSD), the level bucket pass with prefix sums,
+  //     then the member digits ----------------------------------------------------
   h->table_cap = 256 * ((n + kRadixTile - 1) / kRadixTile) + 256;
   h->scan_cap = scan_tmp_size(h->table_cap);
   AMR_TRY(alloc_n(h, &h->table, h->table_cap));
   AMR_TRY(alloc_n(h, &h->scan_tmp, h->scan_cap));
   launch(h, K_SORT_KEYS, k_make_sort_keys, dim3(nblocks(n)), dim3(256), (const uint8_t *)d_lvl,
          (const uint32_t *)d_i, (const uint32_t *)d_j, (const uint32_t *)d_k,
-         (const uint64_t *)d_hk, n, p.levelmin, p.levelmax, comp, perm, h->err);
+         (const uint16_t *)d_mem, (const uint64_t *)d_hk, n, (const int *)h->mlmin,
+         (const int *)h->mlmax, comp, perm, h->err);
   AMR_TRY(check_device(h, "amr_create"));
-  int hbits = hk ? 58 : 3 * (p.levelmax - 1);
+  const int hbits = have_hk ? kHilbertBits : 3 * (h->lmax_all - 1);
   std::vector<std::pair<int, int>> digits = digits_for(0, hbits);
-  digits.push_back({58, 4});  // level bucket sort
+  digits.push_back({kHilbertBits, 4});  // level bucket sort
+  for (auto &d : digits_for(kHilbertBits + 4, bits_for(M))) digits.push_back(d);
   uint64_t *kk = comp;
   uint32_t *vv = perm;
   radix_sort(h, &kk, &vv, comp_alt, perm_alt, n, digits);
 
-  // keys in mesh order, level offsets
-  h->N = n;
+  // --- keys in mesh order, (member, level) offsets ----------------------------------
   AMR_TRY(alloc_n(h, &h->key, n));
-  AMR_TRY(alloc_n(h, &h->counters, 32));
-  CUDA_TRY(cudaMemsetAsync(h->counters, 0, sizeof(uint32_t) * 32, h->s));
+  AMR_TRY(alloc_n(h, &h->counters, 4));
+  AMR_TRY(alloc_n(h, &h->seg_count, 16 * int64_t(M)));
+  CUDA_TRY(cudaMemsetAsync(h->seg_count, 0, sizeof(uint32_t) * 16 * M, h->s));
   launch(h, K_GATHER, k_gather_octs<double>, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
          (const uint8_t *)d_lvl, (const uint32_t *)d_i, (const uint32_t *)d_j,
-         (const uint32_t *)d_k, (const double *)nullptr, n, h->key, (double *)nullptr, int64_t(0),
-         h->counters);
-  uint32_t counts[16];
-  CUDA_TRY(cudaMemcpyAsync(counts, h->counters, sizeof counts, cudaMemcpyDeviceToHost, h->s));
+         (const uint32_t *)d_k, (const uint16_t *)d_mem, (const double *)nullptr, n, h->key,
+         (double *)nullptr, int64_t(0), h->seg_count);
+  std::vector<uint32_t> counts(16 * size_t(M));
+  CUDA_TRY(cudaMemcpyAsync(counts.data(), h->seg_count, 4 * counts.size(), cudaMemcpyDeviceToHost, h->s));
   CUDA_TRY(cudaStreamSynchronize(h->s));
-  int64_t acc = 0;
-  for (int l = 0; l <= kMaxLev; ++l) {
-    h->lo[l] = acc;
-    acc += counts[l];
+  {
+    int64_t base = 0;
+    for (int q = 0; q < M; ++q) {
+      Member &m = h->mem[q];
+      m.oct_base = base;
+      int64_t acc = 0;
+      for (int l = 0; l <= kMaxLev; ++l) {
+        m.lo[l] = acc;
+        acc += counts[16 * q + l];
+      }
+      m.lo[kMaxLev + 1] = acc;
+      base += acc;
+      const int64_t side = int64_t(1) << (m.lmin - 1);
+      if (int64_t(counts[16 * q + m.lmin]) != side * side * side)
+        return fail(AMR_EGRADING, "amr_create: member %d level %d holds %u octs, a complete base needs %lld",
+                    q, m.lmin, counts[16 * q + m.lmin], (long long)(side * side * side));
+    }
   }
-  h->lo[kMaxLev + 1] = acc;
-  const int64_t side = int64_t(1) << (p.levelmin - 1);
-  if (int64_t(counts[p.levelmin]) != side * side * side)
-    return fail(AMR_EGRADING, "amr_create: level %d holds %u octs, a complete base needs %lld",
-                p.levelmin, counts[p.levelmin], (long long)(side * side * side));
 
-  // hash table, father/son, grading, neighbours, ghost cache
-  h->B = p.levelmax - 1 > 0 ? p.levelmax - 1 : 1;
+  // --- hash table, father/son, grading, neighbours, ghost cache ---------------------
+  h->B = std::max(1, h->lmax_all - 1);
   h->claim_cap = 4 * n + 1024;
   uint64_t cap = 1024;
   while (cap < uint64_t(4 * n)) cap <<= 1;
+  AMR_TRY(alloc_n(h, &h->son, n));
+  AMR_TRY(alloc_n(h, &h->father, n));
+  AMR_TRY(alloc_n(h, &h->nbr27, 27 * n));
+  AMR_TRY(alloc_n(h, &h->claim, h->claim_cap));
   for (int attempt = 0; attempt < 3; ++attempt) {
     h->hcap = cap;
     AMR_TRY(alloc_n(h, &h->hash.key, cap));
     AMR_TRY(alloc_n(h, &h->hash.val, cap));
     h->hash.mask = cap - 1;
-    if (!h->son) {
-      AMR_TRY(alloc_n(h, &h->son, n));
-      AMR_TRY(alloc_n(h, &h->father, n));
-      AMR_TRY(alloc_n(h, &h->nbr27, 27 * n));
-      AMR_TRY(alloc_n(h, &h->claim, h->claim_cap));
-    }
     AMR_TRY(build_index(h, true));
     if (uint64_t(2 * (n + h->NC)) <= cap && h->NC <= h->claim_cap) break;
     // too full for the ghosts: grow and rebuild
@@ -636,37 +871,43 @@ static amr_status create_impl(amr_mesh *h, int64_t n, const uint8_t *level, cons
     AMR_TRY(alloc_n(h, &h->table, h->table_cap));
     AMR_TRY(alloc_n(h, &h->scan_tmp, h->scan_cap));
   }
-  // finish the index (sorted ghosts, ghost slots in the table)
+  CUDA_TRY(cudaMemsetAsync(h->seg_count, 0, sizeof(uint32_t) * 16 * M, h->s));
   if (NC > 0) {
     launch(h, K_CLAIM, k_claim_to_comp, dim3(nblocks(NC)), dim3(256), (const uint64_t *)h->claim,
            NC, h->B, h->comp0, h->val0);
-    uint64_t *ck = h->comp0;
-    uint32_t *cv = h->val0;
-    radix_sort(h, &ck, &cv, h->comp1, h->val1, NC, digits_for(0, 4 + 3 * h->B));
+    uint64_t *ckk = h->comp0;
+    uint32_t *cvv = h->val0;
+    radix_sort(h, &ckk, &cvv, h->comp1, h->val1, NC, digits_for(0, 4 + 3 * h->B + bits_for(M)));
     launch(h, K_CACHE_FINALIZE, k_cache_finalize, dim3(nblocks(NC)), dim3(256), h->hash,
-           (const uint64_t *)ck, NC, h->B, n, h->ckey, h->counters + 1, h->err);
+           (const uint64_t *)ckk, NC, h->B, n, h->ckey, h->seg_count, h->err);
     launch(h, K_NBR_FIX, k_neighbours_fix, dim3(nblocks(27 * n)), dim3(256), h->hash,
            (const uint64_t *)h->key, n, h->nbr27, h->err);
   }
-  uint32_t ccounts[16];
-  CUDA_TRY(cudaMemcpyAsync(ccounts, h->counters + 1, sizeof ccounts, cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaMemcpyAsync(counts.data(), h->seg_count, 4 * counts.size(), cudaMemcpyDeviceToHost, h->s));
   AMR_TRY(check_device(h, "amr_create"));
-  acc = 0;
-  for (int l = 0; l <= kMaxLev; ++l) {
-    h->clo[l] = acc;
-    acc += ccounts[l];
+  {
+    int64_t base = 0;
+    for (int q = 0; q < M; ++q) {
+      Member &m = h->mem[q];
+      m.cache_base = base;
+      int64_t acc = 0;
+      for (int l = 0; l <= kMaxLev; ++l) {
+        m.clo[l] = acc;
+        acc += counts[16 * q + l];
+      }
+      m.clo[kMaxLev + 1] = acc;
+      base += acc;
+    }
   }
-  h->clo[kMaxLev + 1] = acc;
   h->NE = n + NC;
   h->S = 8 * h->NE;
   AMR_TRY(alloc_n(h, &h->fnb, 6 * h->NE));
   AMR_TRY(alloc_n(h, &h->csrc, 7 * (NC > 0 ? NC : 1)));
   AMR_TRY(alloc_n(h, &h->rslot, 8 * n));
-  CUDA_TRY(cudaMemsetAsync(h->rslot, 0xFF, sizeof(int32_t) * 8 * n, h->s));
-  AMR_TRY(build_faces_and_sources(h));
+  build_faces_and_sources(h);
   AMR_TRY(check_device(h, "amr_create"));
 
-  // state in mesh order
+  // --- state in mesh order ---------------------------------------------------------
   const size_t es = h->elem();
   AMR_TRY(dev_alloc(h, &h->U, es * 5 * size_t(h->S)));
   AMR_TRY(dev_alloc(h, &h->Rc, es * 5 * size_t(NC > 0 ? NC : 1)));
@@ -675,42 +916,47 @@ static amr_status create_impl(amr_mesh *h, int64_t n, const uint8_t *level, cons
   if (p.precision == 4)
     launch(h, K_GATHER, k_gather_octs<float>, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
            (const uint8_t *)d_lvl, (const uint32_t *)d_i, (const uint32_t *)d_j,
-           (const uint32_t *)d_k, (const double *)d_U, n, h->key, (float *)h->U, h->S,
-           (uint32_t *)nullptr);
+           (const uint32_t *)d_k, (const uint16_t *)d_mem, (const double *)d_U, n, h->key,
+           (float *)h->U, h->S, (uint32_t *)nullptr);
   else
     launch(h, K_GATHER, k_gather_octs<double>, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
            (const uint8_t *)d_lvl, (const uint32_t *)d_i, (const uint32_t *)d_j,
-           (const uint32_t *)d_k, (const double *)d_U, n, h->key, (double *)h->U, h->S,
-           (uint32_t *)nullptr);
+           (const uint32_t *)d_k, (const uint16_t *)d_mem, (const double *)d_U, n, h->key,
+           (double *)h->U, h->S, (uint32_t *)nullptr);
 
-  // leaf counts (host, from the level sizes: each oct above levelmin splits
-  // one cell of the level below)
-  for (int l = 0; l <= kMaxLev; ++l) h->leaf[l] = 8 * (h->lo[l + 1] - h->lo[l]);
-  for (int l = p.levelmin + 1; l <= kMaxLev; ++l) h->leaf[l - 1] -= h->lo[l + 1] - h->lo[l];
-
-  // scratch for the largest level step
-  for (int l = p.levelmin; l <= p.levelmax; ++l) {
-    const int64_t ls = 8 * ((h->lo[l + 1] - h->lo[l]) + (h->clo[l + 1] - h->clo[l]));
-    h->max_ls = std::max(h->max_ls, ls);
+  // leaf counts: each oct above a member's levelmin splits one cell below
+  for (auto &m : h->mem) {
+    for (int l = 0; l <= kMaxLev; ++l) m.leaf[l] = 8 * (m.lo[l + 1] - m.lo[l]);
+    for (int l = m.lmin + 1; l <= kMaxLev; ++l) m.leaf[l - 1] -= m.lo[l + 1] - m.lo[l];
   }
-  h->max_cs = 24 * h->NC;
-  AMR_TRY(dev_alloc(h, &h->W, es * 5 * size_t(h->max_ls)));
-  AMR_TRY(dev_alloc(h, &h->Q, es * 20 * size_t(h->max_ls)));
-  AMR_TRY(dev_alloc(h, &h->F, es * 15 * size_t(h->max_ls)));
+
+  // --- work lists, scratch, time-step arrays ------------------------------------------
+  build_lists(h);
+  AMR_TRY(upload(h, &h->segs, h->segs_h));
+  AMR_TRY(upload(h, &h->tiles, h->tiles_h));
+  h->max_cs = 24 * NC;
+  AMR_TRY(dev_alloc(h, &h->W, es * 5 * size_t(std::max<int64_t>(h->max_ls, 1))));
+  AMR_TRY(dev_alloc(h, &h->Q, es * 20 * size_t(std::max<int64_t>(h->max_ls, 1))));
+  AMR_TRY(dev_alloc(h, &h->F, es * 15 * size_t(std::max<int64_t>(h->max_ls, 1))));
   AMR_TRY(dev_alloc(h, &h->C, es * 5 * size_t(h->max_cs > 0 ? h->max_cs : 1)));
   if (h->max_cs) CUDA_TRY(cudaMemsetAsync(h->C, 0, es * 5 * size_t(h->max_cs), h->s));
-  AMR_TRY(alloc_n(h, &h->dt_dev, 1));
-  AMR_TRY(alloc_n(h, &h->dtf_dev, 1));
-  AMR_TRY(alloc_n(h, &h->smax, 16));
-  CUDA_TRY(cudaMemsetAsync(h->smax, 0, sizeof(unsigned long long) * 16, h->s));
+  AMR_TRY(alloc_n(h, &h->dt_dev, M));
+  AMR_TRY(alloc_n(h, &h->dtdx_dev, M));
+  AMR_TRY(alloc_n(h, &h->dtdxf_dev, M));
+  AMR_TRY(alloc_n(h, &h->smax, 16 * int64_t(M)));
+  CUDA_TRY(cudaMemsetAsync(h->smax, 0, sizeof(unsigned long long) * 16 * M, h->s));
 
-  if (p.precision == 4)
-    initial_restriction<float>(h);
-  else
-    initial_restriction<double>(h);
+  // split cells carry the mean of their children, finest level first
+  for (int l = kMaxLev; l >= 1; --l) {
+    if (p.precision == 4)
+      restrict_segments<float>(h, h->restrict_list[l]);
+    else
+      restrict_segments<double>(h, h->restrict_list[l]);
+  }
   AMR_TRY(check_device(h, "amr_create"));
   // release the input staging
   dev_free(h, d_lvl);
+  dev_free(h, d_mem);
   dev_free(h, d_i);
   dev_free(h, d_j);
   dev_free(h, d_k);
@@ -724,24 +970,35 @@ static amr_status create_impl(amr_mesh *h, int64_t n, const uint8_t *level, cons
   return AMR_OK;
 }
 
-extern "C" amr_status amr_create(const amr_params *p, int64_t n_oct, const uint8_t *level,
-                                 const uint32_t *i, const uint32_t *j, const uint32_t *k,
-                                 const uint64_t *hilbert_key, const double *U, amr_handle *out) {
+static amr_status check_member(const amr_member &a, int q) {
+  if (!a.level || !a.i || !a.j || !a.k || !a.U)
+    return fail(AMR_EINVAL, "amr_create: member %d has a NULL array", q);
+  if (a.levelmin < 1 || a.levelmax > kMaxLev || a.levelmin > a.levelmax)
+    return fail(AMR_EINVAL, "amr_create: levels must satisfy 1 <= levelmin <= levelmax <= %d", kMaxLev);
+  if (!(a.gamma > 1.0) || !(a.cfl > 0.0) || !(a.smallr > 0.0) || !(a.smallc > 0.0))
+    return fail(AMR_EINVAL, "amr_create: gamma > 1, cfl > 0, smallr > 0, smallc > 0 required");
+  if (a.n_oct < 1) return fail(AMR_EINVAL, "amr_create: member %d has no octs", q);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
+                                       const amr_member *members, amr_handle *out) {
   g_last_error.clear();
   if (!out) return fail(AMR_EINVAL, "amr_create: out is NULL");
   *out = nullptr;
-  if (!p || !level || !i || !j || !k || !U) return fail(AMR_EINVAL, "amr_create: NULL argument");
-  if (p->levelmin < 1 || p->levelmax > kMaxLev || p->levelmin > p->levelmax)
-    return fail(AMR_EINVAL, "amr_create: levels must satisfy 1 <= levelmin <= levelmax <= %d", kMaxLev);
-  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->smallr > 0.0) || !(p->smallc > 0.0))
-    return fail(AMR_EINVAL, "amr_create: gamma > 1, cfl > 0, smallr > 0, smallc > 0 required");
+  if (!p || !members) return fail(AMR_EINVAL, "amr_create: NULL argument");
+  if (n_members < 1 || n_members > kMaxMembers)
+    return fail(AMR_EINVAL, "amr_create_batch: n_members must be in [1, %d]", kMaxMembers);
   if (p->precision != 4 && p->precision != 8)
     return fail(AMR_EINVAL, "amr_create: precision must be 4 or 8");
-  if (n_oct < 1 || n_oct > (int64_t(1) << 26))
-    return fail(AMR_EINVAL, "amr_create: n_oct must be in [1, 2^26]");
+  for (int q = 0; q < n_members; ++q) AMR_TRY(check_member(members[q], q));
   amr_mesh *h = new amr_mesh();
   h->p = *p;
+  h->M = n_members;
+  h->mem.resize(n_members);
   cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (h->sm_count < 1) h->sm_count = 1;
   if (p->stream) {
     h->s = static_cast<cudaStream_t>(p->stream);
   } else {
@@ -751,7 +1008,7 @@ extern "C" amr_status amr_create(const amr_params *p, int64_t n_oct, const uint8
     }
     h->own_stream = true;
   }
-  amr_status s = create_impl(h, n_oct, level, i, j, k, hilbert_key, U);
+  amr_status s = create_impl(h, members);
   if (s != AMR_OK) {
     std::string msg = g_last_error;
     destroy_all(h);
@@ -760,6 +1017,32 @@ extern "C" amr_status amr_create(const amr_params *p, int64_t n_oct, const uint8
   }
   *out = h;
   return AMR_OK;
+}
+
+extern "C" amr_status amr_create(const amr_params *p, int64_t n_oct, const uint8_t *level,
+                                 const uint32_t *i, const uint32_t *j, const uint32_t *k,
+                                 const uint64_t *hilbert_key, const double *U, amr_handle *out) {
+  g_last_error.clear();
+  if (!out) return fail(AMR_EINVAL, "amr_create: out is NULL");
+  *out = nullptr;
+  if (!p || !level || !i || !j || !k || !U) return fail(AMR_EINVAL, "amr_create: NULL argument");
+  if (n_oct < 1 || n_oct > (int64_t(1) << 26))
+    return fail(AMR_EINVAL, "amr_create: n_oct must be in [1, 2^26]");
+  amr_member m{};
+  m.levelmin = p->levelmin;
+  m.levelmax = p->levelmax;
+  m.gamma = p->gamma;
+  m.cfl = p->cfl;
+  m.smallr = p->smallr;
+  m.smallc = p->smallc;
+  m.n_oct = n_oct;
+  m.level = level;
+  m.i = i;
+  m.j = j;
+  m.k = k;
+  m.hilbert_key = hilbert_key;
+  m.U = U;
+  return amr_create_batch(p, 1, &m, out);
 }
 
 extern "C" amr_status amr_destroy(amr_handle h) {
@@ -774,17 +1057,23 @@ extern "C" amr_status amr_destroy(amr_handle h) {
 extern "C" amr_status amr_cfl_dt(amr_handle h, double *dt_out) {
   if (!h || !dt_out) return fail(AMR_EINVAL, "amr_cfl_dt: NULL argument");
   cfl_device(h);
-  CUDA_TRY(cudaMemcpyAsync(dt_out, h->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaMemcpyAsync(dt_out, h->dt_dev + h->sel, sizeof(double), cudaMemcpyDeviceToHost, h->s));
   return check_device(h, "amr_cfl_dt");
+}
+
+extern "C" amr_status amr_member_dt(amr_handle h, double *dt_out, int n) {
+  if (!h || !dt_out) return fail(AMR_EINVAL, "amr_member_dt: NULL argument");
+  if (n < h->M) return fail(AMR_EINVAL, "amr_member_dt: room for %d members needed", h->M);
+  CUDA_TRY(cudaMemcpyAsync(dt_out, h->dt_dev, sizeof(double) * h->M, cudaMemcpyDeviceToHost, h->s));
+  return check_device(h, "amr_member_dt");
 }
 
 extern "C" amr_status amr_step_level(amr_handle h, int level, double dt) {
   if (!h) return fail(AMR_EINVAL, "amr_step_level: NULL handle");
-  if (level < h->p.levelmin || level > h->p.levelmax)
-    return fail(AMR_EINVAL, "amr_step_level: level %d outside [%d, %d]", level, h->p.levelmin,
-                h->p.levelmax);
+  if (level < 1 || level > h->lmax_all)
+    return fail(AMR_EINVAL, "amr_step_level: level %d outside [1, %d]", level, h->lmax_all);
   if (!(dt > 0.0)) return fail(AMR_EINVAL, "amr_step_level: dt must be > 0");
-  level_step(h, level, nullptr, 1.0, dt);
+  step_segments(h, h->level_list[level], false, dt);
   if (h->launch_err != cudaSuccess) return check_device(h, "amr_step_level");
   return AMR_OK;
 }
@@ -792,7 +1081,7 @@ extern "C" amr_status amr_step_level(amr_handle h, int level, double dt) {
 static void coarse_step(amr_mesh *h) {
   if (h->p.reindex_every_step) reindex(h);
   cfl_device(h);
-  advance_level(h, h->p.levelmin, 1.0);
+  for (auto &L : h->phases) step_segments(h, L, true, 0.0);
 }
 
 extern "C" amr_status amr_advance(amr_handle h, int n, double *dt_last) {
@@ -826,7 +1115,7 @@ extern "C" amr_status amr_advance(amr_handle h, int n, double *dt_last) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_advance: %s", cudaGetErrorString(e));
   if (dt_last) {
-    CUDA_TRY(cudaMemcpyAsync(dt_last, h->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaMemcpyAsync(dt_last, h->dt_dev + h->sel, sizeof(double), cudaMemcpyDeviceToHost, h->s));
     return check_device(h, "amr_advance");
   }
   return AMR_OK;
@@ -835,8 +1124,7 @@ extern "C" amr_status amr_advance(amr_handle h, int n, double *dt_last) {
 extern "C" amr_status amr_reindex(amr_handle h) {
   if (!h) return fail(AMR_EINVAL, "amr_reindex: NULL handle");
   AMR_TRY(reindex(h));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_reindex: %s", cudaGetErrorString(e));
+  if (h->launch_err != cudaSuccess) return check_device(h, "amr_reindex");
   return AMR_OK;
 }
 
@@ -847,19 +1135,24 @@ extern "C" amr_status amr_sync(amr_handle h) {
 
 extern "C" amr_status amr_fill_ghosts(amr_handle h, int level) {
   if (!h) return fail(AMR_EINVAL, "amr_fill_ghosts: NULL handle");
-  if (level < h->p.levelmin || level > h->p.levelmax) return fail(AMR_EINVAL, "amr_fill_ghosts: bad level");
-  if (h->p.precision == 4) {
-    LevelArgs<float> a = level_args<float>(h, level, nullptr, 1.0, 0.0);
-    if (a.ncl) launch(h, K_PROLONG, k_prolong<float>, dim3(nblocks(5 * a.ncl)), dim3(256), a);
-  } else {
-    LevelArgs<double> a = level_args<double>(h, level, nullptr, 1.0, 0.0);
-    if (a.ncl) launch(h, K_PROLONG, k_prolong<double>, dim3(nblocks(5 * a.ncl)), dim3(256), a);
-  }
+  if (level < 1 || level > kMaxLev) return fail(AMR_EINVAL, "amr_fill_ghosts: bad level");
+  const SegList &L = h->level_list[level];
+  if (h->p.precision == 4)
+    run_list(h, K_PROLONG, k_prolong<float>, step_args<float>(h, false, 0.0), L, DOM_GHOST5);
+  else
+    run_list(h, K_PROLONG, k_prolong<double>, step_args<double>(h, false, 0.0), L, DOM_GHOST5);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_select_member(amr_handle h, int member) {
+  if (!h) return fail(AMR_EINVAL, "amr_select_member: NULL handle");
+  if (member < 0 || member >= h->M) return fail(AMR_EINVAL, "amr_select_member: no member %d", member);
+  h->sel = member;
   return AMR_OK;
 }
 
 // ---------------------------------------------------------------------------
-// state in / out
+// state in / out (selected member)
 // ---------------------------------------------------------------------------
 // copy [5][count] values starting at element `first` of each row of a
 // device array with row stride `stride` into host doubles
@@ -882,23 +1175,30 @@ static amr_status rows_to_host(amr_mesh *h, const void *src, int64_t stride, int
   return AMR_OK;
 }
 
+static bool level_ok(int level) { return level >= 0 && level <= kMaxLev; }
+
 extern "C" amr_status amr_read(amr_handle h, int level, int64_t *n_oct_out, uint64_t *keys,
                                double *U, int64_t cap) {
   if (!h) return fail(AMR_EINVAL, "amr_read: NULL handle");
-  if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_read: bad level");
-  const int64_t lo = h->lo[level], nl = h->lo[level + 1] - lo;
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_read: bad level");
+  const Member &m = h->mem[h->sel];
+  const int64_t lo = m.oct_base + m.lo[level], nl = m.lo[level + 1] - m.lo[level];
   if (n_oct_out) *n_oct_out = nl;
   if ((keys || U) && cap < nl) return fail(AMR_EINVAL, "amr_read: cap %lld < %lld octs", (long long)cap, (long long)nl);
-  if (keys && nl)
+  if (keys && nl) {
     CUDA_TRY(cudaMemcpyAsync(keys, h->key + lo, 8 * nl, cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+    for (int64_t t = 0; t < nl; ++t) keys[t] = external_key(keys[t]);
+  }
   if (U) AMR_TRY(rows_to_host(h, h->U, h->S, 8 * lo, 8 * nl, U));
   return check_device(h, "amr_read");
 }
 
 extern "C" amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_t cap) {
   if (!h || !R) return fail(AMR_EINVAL, "amr_read_reflux: NULL argument");
-  if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_read_reflux: bad level");
-  const int64_t lo = h->lo[level], nl = h->lo[level + 1] - lo;
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_read_reflux: bad level");
+  const Member &m = h->mem[h->sel];
+  const int64_t lo = m.oct_base + m.lo[level], nl = m.lo[level + 1] - m.lo[level];
   if (cap < nl) return fail(AMR_EINVAL, "amr_read_reflux: cap too small");
   const int64_t n8 = 8 * nl;
   for (int64_t t = 0; t < 5 * n8; ++t) R[t] = 0.0;
@@ -916,8 +1216,9 @@ extern "C" amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_
 
 extern "C" amr_status amr_write(amr_handle h, int level, const double *U, int64_t n) {
   if (!h || !U) return fail(AMR_EINVAL, "amr_write: NULL argument");
-  if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_write: bad level");
-  const int64_t lo = h->lo[level], nl = h->lo[level + 1] - lo;
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_write: bad level");
+  const Member &m = h->mem[h->sel];
+  const int64_t lo = m.oct_base + m.lo[level], nl = m.lo[level + 1] - m.lo[level];
   if (n != nl) return fail(AMR_EINVAL, "amr_write: level %d holds %lld octs, got %lld", level, (long long)nl, (long long)n);
   if (nl == 0) return AMR_OK;
   const int64_t count = 8 * nl;
@@ -937,30 +1238,41 @@ extern "C" amr_status amr_write(amr_handle h, int level, const double *U, int64_
 }
 
 // ---------------------------------------------------------------------------
-// introspection
+// introspection (selected member)
 // ---------------------------------------------------------------------------
 extern "C" amr_status amr_lookup(amr_handle h, int64_t n, const uint64_t *keys, int64_t *idx_out) {
   if (!h || (n > 0 && (!keys || !idx_out))) return fail(AMR_EINVAL, "amr_lookup: NULL argument");
   if (n <= 0) return AMR_OK;
+  const Member &m = h->mem[h->sel];
+  std::vector<uint64_t> ik(n);
+  for (int64_t t = 0; t < n; ++t) {
+    const uint64_t k = keys[t];
+    const int l = int(k >> 60);
+    const uint32_t x = uint32_t(k >> 40) & 0xFFFFF, y = uint32_t(k >> 20) & 0xFFFFF, z = uint32_t(k) & 0xFFFFF;
+    // coordinates beyond 15 bits cannot be in any mesh: a key that matches nothing
+    ik[t] = (x >> 15 || y >> 15 || z >> 15) ? ~0ull - 1 : ikey(h->sel, l, x, y, z);
+  }
   uint64_t *dk;
   int64_t *dout;
-  AMR_TRY(alloc_n(h, &dk, n));
+  AMR_TRY(upload(h, &dk, ik));
   AMR_TRY(alloc_n(h, &dout, n));
-  CUDA_TRY(cudaMemcpyAsync(dk, keys, 8 * n, cudaMemcpyHostToDevice, h->s));
   launch(h, K_LOOKUP, k_lookup, dim3(nblocks(8 * n)), dim3(256), h->hash, (const uint64_t *)dk, n,
          h->N, dout);
   CUDA_TRY(cudaMemcpyAsync(idx_out, dout, 8 * n, cudaMemcpyDeviceToHost, h->s));
   CUDA_TRY(cudaStreamSynchronize(h->s));
   dev_free(h, dk);
   dev_free(h, dout);
+  for (int64_t t = 0; t < n; ++t)
+    if (idx_out[t] >= 0) idx_out[t] -= m.oct_base;
   return check_device(h, "amr_lookup");
 }
 
 extern "C" amr_status amr_read_index(amr_handle h, int level, int64_t *nbr, uint8_t *split,
                                      int64_t cap) {
   if (!h) return fail(AMR_EINVAL, "amr_read_index: NULL handle");
-  if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_read_index: bad level");
-  const int64_t lo = h->lo[level], nl = h->lo[level + 1] - lo;
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_read_index: bad level");
+  const Member &m = h->mem[h->sel];
+  const int64_t lo = m.oct_base + m.lo[level], nl = m.lo[level + 1] - m.lo[level];
   if (cap < nl) return fail(AMR_EINVAL, "amr_read_index: cap too small");
   if (nl == 0) return AMR_OK;
   if (nbr) {
@@ -972,7 +1284,7 @@ extern "C" amr_status amr_read_index(amr_handle h, int level, int64_t *nbr, uint
     for (int64_t t = 0; t < nl; ++t)
       for (int e = 0; e < 27; ++e) {
         const int64_t x = tmp[e * nl + t];
-        nbr[27 * t + e] = x < h->N ? x : -(1 + (x - h->N));
+        nbr[27 * t + e] = x < h->N ? x - m.oct_base : -(1 + (x - h->N - m.cache_base));
       }
   }
   if (split) {
@@ -988,12 +1300,17 @@ extern "C" amr_status amr_read_index(amr_handle h, int level, int64_t *nbr, uint
 extern "C" amr_status amr_read_cache(amr_handle h, int level, int64_t *n_out, int64_t *first_out,
                                      uint64_t *keys, double *Ug, int64_t cap) {
   if (!h) return fail(AMR_EINVAL, "amr_read_cache: NULL handle");
-  if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_read_cache: bad level");
-  const int64_t c0 = h->clo[level], nc = h->clo[level + 1] - c0;
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_read_cache: bad level");
+  const Member &m = h->mem[h->sel];
+  const int64_t c0 = m.cache_base + m.clo[level], nc = m.clo[level + 1] - m.clo[level];
   if (n_out) *n_out = nc;
-  if (first_out) *first_out = c0;
+  if (first_out) *first_out = m.clo[level];
   if ((keys || Ug) && cap < nc) return fail(AMR_EINVAL, "amr_read_cache: cap too small");
-  if (keys && nc) CUDA_TRY(cudaMemcpyAsync(keys, h->ckey + c0, 8 * nc, cudaMemcpyDeviceToHost, h->s));
+  if (keys && nc) {
+    CUDA_TRY(cudaMemcpyAsync(keys, h->ckey + c0, 8 * nc, cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+    for (int64_t t = 0; t < nc; ++t) keys[t] = external_key(keys[t]);
+  }
   if (Ug) AMR_TRY(rows_to_host(h, h->U, h->S, 8 * (h->N + c0), 8 * nc, Ug));
   return check_device(h, "amr_read_cache");
 }
@@ -1003,17 +1320,26 @@ extern "C" amr_status amr_get_info(amr_handle h, amr_info *info) {
   std::memset(info, 0, sizeof *info);
   info->n_oct = h->N;
   info->n_cache = h->NC;
+  const Member &m = h->mem[h->sel];
+  for (auto &q : h->mem) {
+    for (int l = 0; l <= kMaxLev; ++l) {
+      info->n_leaf_cells += q.leaf[l];
+      if (q.lo[l + 1] > q.lo[l] && l >= q.lmin) info->work_per_step += q.leaf[l] << (l - q.lmin);
+    }
+  }
   for (int l = 0; l <= kMaxLev; ++l) {
-    info->level_octs[l] = h->lo[l + 1] - h->lo[l];
-    info->level_cache[l] = h->clo[l + 1] - h->clo[l];
-    info->level_leaf_cells[l] = h->leaf[l];
-    info->n_leaf_cells += h->leaf[l];
+    info->level_octs[l] = m.lo[l + 1] - m.lo[l];
+    info->level_cache[l] = m.clo[l + 1] - m.clo[l];
+    info->level_leaf_cells[l] = m.leaf[l];
   }
   info->device_bytes = int64_t(h->bytes);
   info->kernel_launches = h->launches;
   info->graph_launches = h->graph_launches;
   info->hash_capacity = int64_t(h->hcap);
   info->precision = h->p.precision;
+  info->n_members = h->M;
+  info->member = h->sel;
+  info->phases = int(h->phases.size());
   return AMR_OK;
 }
 

@@ -26,15 +26,33 @@ enum : int {
 };
 
 // ---------------------------------------------------------------------------
-// keys (Sec. 2.1): level in bits 60..63, i/j/k in three 20-bit fields
+// keys (Sec. 2.1).  External keys (the C ABI's): level in bits 60..63, i/j/k
+// in three 20-bit fields.  Internal keys also carry the member mesh of a
+// batched handle: member in bits 49..63, level in 45..48, i/j/k in three
+// 15-bit fields (levels <= 15 keep coordinates below 2^14).
 // ---------------------------------------------------------------------------
+constexpr int kMaxMembers = 1 << 15;
+
 __host__ __device__ __forceinline__ uint64_t key_pack(int l, uint32_t i, uint32_t j, uint32_t k) {
   return (uint64_t(l) << 60) | (uint64_t(i) << 40) | (uint64_t(j) << 20) | uint64_t(k);
 }
-__host__ __device__ __forceinline__ int key_lev(uint64_t key) { return int(key >> 60); }
-__host__ __device__ __forceinline__ uint32_t key_x(uint64_t key) { return uint32_t(key >> 40) & 0xFFFFFu; }
-__host__ __device__ __forceinline__ uint32_t key_y(uint64_t key) { return uint32_t(key >> 20) & 0xFFFFFu; }
-__host__ __device__ __forceinline__ uint32_t key_z(uint64_t key) { return uint32_t(key) & 0xFFFFFu; }
+__host__ __device__ __forceinline__ uint64_t ikey(int m, int l, uint32_t i, uint32_t j, uint32_t k) {
+  return (uint64_t(m) << 49) | (uint64_t(l) << 45) | (uint64_t(i) << 30) | (uint64_t(j) << 15) |
+         uint64_t(k);
+}
+__host__ __device__ __forceinline__ int ikey_member(uint64_t key) { return int(key >> 49); }
+__host__ __device__ __forceinline__ int ikey_lev(uint64_t key) { return int(key >> 45) & 15; }
+__host__ __device__ __forceinline__ uint32_t ikey_x(uint64_t key) { return uint32_t(key >> 30) & 0x7FFFu; }
+__host__ __device__ __forceinline__ uint32_t ikey_y(uint64_t key) { return uint32_t(key >> 15) & 0x7FFFu; }
+__host__ __device__ __forceinline__ uint32_t ikey_z(uint64_t key) { return uint32_t(key) & 0x7FFFu; }
+// same member and coordinates, another level
+__host__ __device__ __forceinline__ uint64_t ikey_at(uint64_t key, int l, uint32_t i, uint32_t j,
+                                                    uint32_t k) {
+  return ikey(ikey_member(key), l, i, j, k);
+}
+__host__ __device__ __forceinline__ uint64_t external_key(uint64_t key) {
+  return key_pack(ikey_lev(key), ikey_x(key), ikey_y(key), ikey_z(key));
+}
 
 // FNV-1a 64 over the key's 8 bytes, least significant byte first (Sec. 6).
 __device__ __forceinline__ uint64_t fnv1a64(uint64_t key) {

@@ -4,49 +4,70 @@
 
 namespace amr {
 
-// Everything one level step needs, passed by value.  "Local" cell indices
-// t in [0, LS) number the level's real cells first (8*nl) and then the
-// cells of its ghost octs (8*ncl); scratch arrays are indexed by t.  Every
-// count fits in 32 bits (at most 2^26 real octs), so kernels index with int.
+// One (member mesh, level) piece of a level-step launch.  Real octs of the
+// segment are mesh indices [lo, lo+nl), its ghost octs cache slots
+// [clo, clo+ncl).  "Local" cell indices t in [0, 8(nl+ncl)) number the real
+// cells first, then the ghost cells; the scratch arrays hold the segment at
+// [base, base + 8(nl+ncl)).
+struct Seg {
+  int member, level;
+  int lo, nl;
+  int clo, ncl;
+  int base;
+  int flags;  // kSegReflux: sum coarse-fine fluxes; kSegRestrict: restrict
+};
+enum : int { kSegReflux = 1, kSegRestrict = 2 };
+
+// A launch covers a flattened list of tiles; tile (seg, start) is the block
+// of domain items [start, start + blockDim.x) of segment seg.
+struct Tile {
+  int seg, start;
+};
+
+// Everything a level-step launch needs, passed by value.  Every count fits in
+// 32 bits (at most 2^26 real octs), so kernels index with int.
 template <class T>
-struct LevelArgs {
-  int l, lmin;
-  int lo, nl;     // real octs of the level: mesh indices [lo, lo+nl)
-  int clo, ncl;   // ghost octs of the level: cache slots [clo, clo+ncl)
-  int N, NE, NC;  // real octs; real + ghost octs; ghost octs
-  int LS;         // stride of the scratch arrays (8*(nl+ncl))
-  int64_t S;      // stride of U (8*NE)
-  int64_t CS;     // stride of the reflux contribution slots (24*NC): every
-                  // ghost oct owns 24 slots, written only by its own level
+struct StepArgs {
+  int N, NE, NC;      // real octs; real + ghost octs; ghost octs (all members)
+  int LS;             // stride of the scratch arrays
+  int64_t S;          // stride of U (8*NE)
+  int64_t CS;         // stride of the reflux slots (24*NC)
   T *U;
   T *Rc;                  // [5][NC] pending reflux of the father of ghost oct s
   const int32_t *rslot;   // [8N] ghost slot whose father is this cell, or -1
   const int32_t *fnb;     // [6][NE] face neighbours (extended index, -1 none)
   const uint32_t *son;    // [N] split mask
-  const int32_t *father;  // [N] father oct (mesh index), -1 at levelmin
-  const uint64_t *key;    // [N]
+  const int32_t *father;  // [N] father oct (mesh index), -1 at a member's levelmin
+  const uint64_t *key;    // [N] internal keys
   const int32_t *csrc;    // [7][NC] prolongation sources (global cell indices)
-  T *W, *Q, *F, *C;       // scratch: W[5][LS], Q[20][LS], F[15][LS]; C[5][CS]
-  // dt/dx of this level step: from the device dt of the coarse step
-  // (dt_dev, or its float copy dtf_dev) times dtdx_scale = 2^(l - k) for the
-  // k-th halving, or the host value dtdx_host when both pointers are NULL
-  const double *dt_dev;
-  const float *dtf_dev;
-  double dtdx_scale;
-  T dtdx_host;
-  T gamma, igm1, smallr, smallp;  // igm1 = 1/(gamma - 1)
+  T *W, *Q, *F, *C;       // scratch W[5][LS], Q[20][LS], F[15][LS]; slots C[5][CS]
+  const Seg *segs;
+  const Tile *tiles;
+  int ntiles;
+  // per member: gamma, 1/(gamma-1), floors
+  const T *mgamma, *migm1, *msmallr, *msmallp;
+  // dt/dx: from the device time step of each member's coarse step
+  // (dt_m 2^levelmin_m, the same for every level of the member), or, when
+  // both pointers are NULL, dt_host 2^level for every segment
+  const double *dtdx_dev;
+  const float *dtdxf_dev;
+  double dt_host;
   int reflux;
 };
 
 struct CflArgs {
-  int lmin, lmax;
-  int64_t lo[kMaxLev + 2];  // level offsets of the real octs
+  const Seg *segs;
+  const Tile *tiles;
+  int ntiles;
   int64_t S;
   const uint32_t *son;
-  double gamma, smallr, smallp, cfl;
-  unsigned long long *smax;  // [16] bit patterns of per-level maxima
-  double *dt_dev;
-  float *dtf_dev;            // float copy of dt for the FP32 kernels
+  const double *mgamma, *msmallr, *msmallp, *mcfl;
+  const int *mlmin;
+  int nmembers;
+  unsigned long long *smax;  // [16 * members] bit patterns of per-level maxima
+  double *dt_dev;            // [members] coarse dt
+  double *dtdx_dev;          // [members] dt_m 2^levelmin_m
+  float *dtdxf_dev;          // float copy for the FP32 kernels
   int *err;
 };
 

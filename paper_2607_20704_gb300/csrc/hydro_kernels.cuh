@@ -8,14 +8,20 @@
 //   k_predict   limited slopes and the Hancock half-step, once per cell
 //   k_flux      one HLLC flux per face (owned by the cell on its minus side)
 //   k_update    conservative update of leaf cells + pending reflux
-//   k_reflux    fixed-order sum of coarse-fine fluxes for level l-1 cells
-//   k_restrict  father cell = mean of its 8 children
+//   k_reflux_restrict  fixed-order sum of coarse-fine fluxes for the coarse
+//               cells, and father cell = mean of its 8 children
+//
+// (FP32 fuses k_prim into k_predict_u and k_flux with k_update.)
 //
 // The paper's kernels gather a 6x6x6 stencil per oct and recompute the
 // slopes and predictor of its ghost ring (8x work per cell at nsubgrid=1).
 // On GB300 the FP64 rate is far below the memory rate, so each cell's
 // predictor and each face's Riemann solve is computed exactly once and the
 // intermediate states go through L2/HBM instead.
+//
+// Every kernel is persistent over a flattened work list of tiles, each tile
+// one block's worth of items of one (member mesh, level) segment, so one
+// launch advances a level of many meshes at once.
 #pragma once
 #include "hydro_args.cuh"
 
@@ -65,141 +71,231 @@ __device__ __forceinline__ float rcp(float x) {
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// segment context: what a thread needs to know about its (member, level)
+// ---------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ T level_dtdx(const LevelArgs<T> &a);
-template <>
-__device__ __forceinline__ double level_dtdx<double>(const LevelArgs<double> &a) {
-  return a.dt_dev ? __ldg(a.dt_dev) * a.dtdx_scale : a.dtdx_host;
+struct SegCtx {
+  int lo, nl, clo, ncl, base, flags;
+  T gamma, igm1, smallr, smallp, dtdx;
+};
+
+__device__ __forceinline__ double seg_dtdx(const StepArgs<double> &a, const Seg &s) {
+  return a.dtdx_dev ? __ldg(a.dtdx_dev + s.member) : ldexp(a.dt_host, s.level);
 }
-template <>
-__device__ __forceinline__ float level_dtdx<float>(const LevelArgs<float> &a) {
-  // dtdx_scale is a power of two, exact in float
-  return a.dtf_dev ? __ldg(a.dtf_dev) * float(a.dtdx_scale) : a.dtdx_host;
+__device__ __forceinline__ float seg_dtdx(const StepArgs<float> &a, const Seg &s) {
+  // scaling by a power of two is exact, so this is float(dt 2^l)
+  return a.dtdxf_dev ? __ldg(a.dtdxf_dev + s.member) : ldexpf(float(a.dt_host), s.level);
+}
+
+template <class T>
+__device__ __forceinline__ SegCtx<T> seg_ctx(const StepArgs<T> &a, int seg) {
+  const Seg s = a.segs[seg];
+  SegCtx<T> c;
+  c.lo = s.lo;
+  c.nl = s.nl;
+  c.clo = s.clo;
+  c.ncl = s.ncl;
+  c.base = s.base;
+  c.flags = s.flags;
+  c.gamma = __ldg(a.mgamma + s.member);
+  c.igm1 = __ldg(a.migm1 + s.member);
+  c.smallr = __ldg(a.msmallr + s.member);
+  c.smallp = __ldg(a.msmallp + s.member);
+  c.dtdx = seg_dtdx(a, s);
+  return c;
+}
+
+// persistent loop over the launch's tiles: body(ctx, item) for every item of
+// the tile that lies inside the segment's domain of `size(ctx)` items
+template <class T, class Size, class Body>
+__device__ __forceinline__ void tile_loop(const StepArgs<T> &a, Size size, Body body) {
+  for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
+    const Tile td = a.tiles[ti];
+    const SegCtx<T> sc = seg_ctx(a, td.seg);
+    const int item = td.start + threadIdx.x;
+    if (item < size(sc)) body(sc, item);
+  }
 }
 
 // extended oct index of local oct index q, and back
 template <class T>
-__device__ __forceinline__ int ext_of_local(const LevelArgs<T> &a, int q) {
-  return q < a.nl ? a.lo + q : a.N + a.clo + (q - a.nl);
+__device__ __forceinline__ int ext_of_local(const StepArgs<T> &a, const SegCtx<T> &s, int q) {
+  return q < s.nl ? s.lo + q : a.N + s.clo + (q - s.nl);
 }
 template <class T>
-__device__ __forceinline__ int local_of_ext(const LevelArgs<T> &a, int e) {
-  return e < a.N ? e - a.lo : e - a.N - a.clo + a.nl;
+__device__ __forceinline__ int local_of_ext(const StepArgs<T> &a, const SegCtx<T> &s, int e) {
+  return e < a.N ? e - s.lo : e - a.N - s.clo + s.nl;
 }
 
 // local index of the face neighbour of local cell t (extended oct e, cell c)
 // along axis d on side `plus`; -1 when the neighbouring oct does not exist
 template <class T>
-__device__ __forceinline__ int nbr_local(const LevelArgs<T> &a, int t, int e, int c, int d,
-                                         int plus) {
+__device__ __forceinline__ int nbr_local(const StepArgs<T> &a, const SegCtx<T> &s, int t, int e,
+                                         int c, int d, int plus) {
   const int bit = 1 << d;
   if (((c >> d) & 1) != plus) return t ^ bit;
   const int32_t ne = __ldg(a.fnb + (2 * d + plus) * int64_t(a.NE) + e);
   if (ne < 0) return -1;
-  return 8 * local_of_ext(a, ne) + (c ^ bit);
+  return 8 * local_of_ext(a, s, ne) + (c ^ bit);
 }
 
 template <class T>
-__device__ __forceinline__ bool cell_is_split(const LevelArgs<T> &a, int t) {
+__device__ __forceinline__ bool cell_is_split(const StepArgs<T> &a, const SegCtx<T> &s, int t) {
   const int q = t >> 3;
-  if (q >= a.nl) return false;  // ghost cells are leaves
-  return (__ldg(a.son + a.lo + q) >> (t & 7)) & 1u;
+  if (q >= s.nl) return false;  // ghost cells are leaves
+  return (__ldg(a.son + s.lo + q) >> (t & 7)) & 1u;
 }
 
 // ---------------------------------------------------------------------------
 // ghost octs: child = U_C + sum_d (+-1/4) minmod(U(C+e_d)-U(C), U(C)-U(C-e_d))
+// domain: 5 * ncl (variable, ghost oct)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_prolong(LevelArgs<T> a) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= 5 * a.ncl) return;
-  const int v = q / a.ncl;
-  const int s = q - v * a.ncl;
-  const int cs = a.clo + s;
-  const T *Uv = a.U + v * a.S;
-  T src[7];
+__global__ void k_prolong(StepArgs<T> a) {
+  tile_loop(a, [](const SegCtx<T> &s) { return 5 * s.ncl; }, [&](const SegCtx<T> &s, int q) {
+    const int v = q / s.ncl;
+    const int cs = s.clo + (q - v * s.ncl);
+    const T *Uv = a.U + v * a.S;
+    T src[7];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) src[k] = Uv[__ldg(a.csrc + k * int64_t(a.NC) + cs)];
-  const T uc = src[0];
-  const T sx = minmod(src[2] - uc, uc - src[1]);
-  const T sy = minmod(src[4] - uc, uc - src[3]);
-  const T sz = minmod(src[6] - uc, uc - src[5]);
-  T *dst = a.U + v * a.S + 8 * int64_t(a.N + cs);
-  const T h = T(0.25);
+    for (int k = 0; k < 7; ++k) src[k] = Uv[__ldg(a.csrc + k * int64_t(a.NC) + cs)];
+    const T uc = src[0];
+    const T sx = minmod(src[2] - uc, uc - src[1]);
+    const T sy = minmod(src[4] - uc, uc - src[3]);
+    const T sz = minmod(src[6] - uc, uc - src[5]);
+    T *dst = a.U + v * a.S + 8 * int64_t(a.N + cs);
+    const T h = T(0.25);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const T hx = (c & 1) ? h : -h, hy = (c & 2) ? h : -h, hz = (c & 4) ? h : -h;
-    dst[c] = ((uc + hx * sx) + hy * sy) + hz * sz;
-  }
+    for (int c = 0; c < 8; ++c) {
+      const T hx = (c & 1) ? h : -h, hy = (c & 2) ? h : -h, hz = (c & 4) ? h : -h;
+      dst[c] = ((uc + hx * sx) + hy * sy) + hz * sz;
+    }
+  });
 }
 
 // ---------------------------------------------------------------------------
-// primitives of every real and ghost cell of the level
+// primitives of every real and ghost cell; domain: 8 (nl + ncl)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_prim(LevelArgs<T> a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.LS) return;
-  const int g = 8 * ext_of_local(a, t >> 3) + (t & 7);
-  const T u0 = a.U[g], u1 = a.U[a.S + g], u2 = a.U[2 * a.S + g], u3 = a.U[3 * a.S + g],
-          u4 = a.U[4 * a.S + g];
-  const T r = vmax(u0, a.smallr);
+__device__ __forceinline__ void prim_at(const StepArgs<T> &a, const SegCtx<T> &s, int t,
+                                        T (&w)[5]) {
+  const int g = 8 * ext_of_local(a, s, t >> 3) + (t & 7);
+  const T r = vmax(a.U[g], s.smallr);
   const T ir = rcp(r);
-  const T vx = u1 * ir, vy = u2 * ir, vz = u3 * ir;
+  const T vx = a.U[a.S + g] * ir, vy = a.U[2 * a.S + g] * ir, vz = a.U[3 * a.S + g] * ir;
   const T ek = T(0.5) * r * ((vx * vx + vy * vy) + vz * vz);
-  const T p = vmax((a.gamma - T(1)) * (u4 - ek), r * a.smallp);
-  a.W[t] = r;
-  a.W[a.LS + t] = vx;
-  a.W[2 * a.LS + t] = vy;
-  a.W[3 * a.LS + t] = vz;
-  a.W[4 * a.LS + t] = p;
+  w[0] = r;
+  w[1] = vx;
+  w[2] = vy;
+  w[3] = vz;
+  w[4] = vmax((s.gamma - T(1)) * (a.U[4 * a.S + g] - ek), r * s.smallp);
+}
+
+template <class T>
+__global__ void k_prim(StepArgs<T> a) {
+  tile_loop(a, [](const SegCtx<T> &s) { return 8 * (s.nl + s.ncl); },
+            [&](const SegCtx<T> &s, int t) {
+              T w[5];
+              prim_at(a, s, t, w);
+              const int o = s.base + t;
+#pragma unroll
+              for (int v = 0; v < 5; ++v) a.W[v * a.LS + o] = w[v];
+            });
 }
 
 // ---------------------------------------------------------------------------
 // limited slopes and Hancock predictor W* = W + dt/(2dx) S(W, dW)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_predict(LevelArgs<T> a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.LS) return;
-  const int e = ext_of_local(a, t >> 3);
-  const int c = t & 7;
-  T w[5], dw[3][5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) w[v] = a.W[v * a.LS + t];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int tm = nbr_local(a, t, e, c, d, 0);
-    const int tp = nbr_local(a, t, e, c, d, 1);
-    if (tm < 0 || tp < 0) {  // outer ring of a ghost oct: never used
-#pragma unroll
-      for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
-      continue;
-    }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const T wm = a.W[v * a.LS + tm], wp = a.W[v * a.LS + tp];
-      dw[d][v] = minmod(wp - w[v], w[v] - wm);
-    }
-  }
-  const T r = w[0], p = w[4], g = a.gamma;
+__device__ __forceinline__ void predictor(const SegCtx<T> &s, const T (&w)[5],
+                                          const T (&dw)[3][5], T (&ws)[5]) {
+  const T r = w[0], p = w[4], g = s.gamma;
   const T ir = rcp(r);
   const T gp = g * p;
-  T s[5];
-  s[0] = -(((w[1] * dw[0][0] + r * dw[0][1]) + (w[2] * dw[1][0] + r * dw[1][2])) +
-           (w[3] * dw[2][0] + r * dw[2][3]));
+  T src[5];
+  src[0] = -(((w[1] * dw[0][0] + r * dw[0][1]) + (w[2] * dw[1][0] + r * dw[1][2])) +
+             (w[3] * dw[2][0] + r * dw[2][3]));
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    s[1 + k] = -((w[1] * dw[0][1 + k] + w[2] * dw[1][1 + k]) + w[3] * dw[2][1 + k]) - dw[k][4] * ir;
-  s[4] = -(((w[1] * dw[0][4] + gp * dw[0][1]) + (w[2] * dw[1][4] + gp * dw[1][2])) +
-           (w[3] * dw[2][4] + gp * dw[2][3]));
-  const T hdt = T(0.5) * level_dtdx(a);
+    src[1 + k] =
+        -((w[1] * dw[0][1 + k] + w[2] * dw[1][1 + k]) + w[3] * dw[2][1 + k]) - dw[k][4] * ir;
+  src[4] = -(((w[1] * dw[0][4] + gp * dw[0][1]) + (w[2] * dw[1][4] + gp * dw[1][2])) +
+             (w[3] * dw[2][4] + gp * dw[2][3]));
+  const T hdt = T(0.5) * s.dtdx;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) a.Q[v * a.LS + t] = w[v] + hdt * s[v];
+  for (int v = 0; v < 5; ++v) ws[v] = w[v] + hdt * src[v];
+}
+
+template <class T>
+__device__ __forceinline__ void store_q(const StepArgs<T> &a, int o, const T (&ws)[5],
+                                        const T (&dw)[3][5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) a.Q[v * a.LS + o] = ws[v];
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) a.Q[(5 + 5 * d + v) * a.LS + t] = dw[d][v];
+    for (int v = 0; v < 5; ++v) a.Q[(5 + 5 * d + v) * a.LS + o] = dw[d][v];
+}
+
+template <class T>
+__global__ void k_predict(StepArgs<T> a) {
+  tile_loop(a, [](const SegCtx<T> &s) { return 8 * (s.nl + s.ncl); },
+            [&](const SegCtx<T> &s, int t) {
+              const int e = ext_of_local(a, s, t >> 3);
+              const int c = t & 7;
+              const int o = s.base + t;
+              T w[5], dw[3][5], ws[5];
+#pragma unroll
+              for (int v = 0; v < 5; ++v) w[v] = a.W[v * a.LS + o];
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                const int tm = nbr_local(a, s, t, e, c, d, 0);
+                const int tp = nbr_local(a, s, t, e, c, d, 1);
+                if (tm < 0 || tp < 0) {  // outer ring of a ghost oct: never used
+#pragma unroll
+                  for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
+                  continue;
+                }
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                  const T wm = a.W[v * a.LS + s.base + tm], wp = a.W[v * a.LS + s.base + tp];
+                  dw[d][v] = minmod(wp - w[v], w[v] - wm);
+                }
+              }
+              predictor(s, w, dw, ws);
+              store_q(a, o, ws, dw);
+            });
+}
+
+// FP32: primitives of the cell and its six face neighbours derived from U
+// directly (no W array)
+template <class T>
+__global__ void k_predict_u(StepArgs<T> a) {
+  tile_loop(a, [](const SegCtx<T> &s) { return 8 * (s.nl + s.ncl); },
+            [&](const SegCtx<T> &s, int t) {
+              const int e = ext_of_local(a, s, t >> 3);
+              const int c = t & 7;
+              T w[5], dw[3][5], ws[5];
+              prim_at(a, s, t, w);
+#pragma unroll
+              for (int d = 0; d < 3; ++d) {
+                const int tm = nbr_local(a, s, t, e, c, d, 0);
+                const int tp = nbr_local(a, s, t, e, c, d, 1);
+                if (tm < 0 || tp < 0) {
+#pragma unroll
+                  for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
+                  continue;
+                }
+                T wm[5], wp[5];
+                prim_at(a, s, tm, wm);
+                prim_at(a, s, tp, wp);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) dw[d][v] = minmod(wp[v] - w[v], w[v] - wm[v]);
+              }
+              predictor(s, w, dw, ws);
+              store_q(a, s.base + t, ws, dw);
+            });
 }
 
 // ---------------------------------------------------------------------------
@@ -250,52 +346,58 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   F[4] = (eo + po) * uo;
 }
 
-// flux across the plus face of local cell t along axis D (neighbour tn)
+// flux across the face between local cells tl (minus side) and tr (plus side)
 template <int D, class T>
-__device__ __forceinline__ void face_flux(const LevelArgs<T> &a, int t, int tn, T (&F)[5]) {
+__device__ __forceinline__ void face_flux(const StepArgs<T> &a, const SegCtx<T> &s, int tl, int tr,
+                                          T (&F)[5]) {
   T qL[5], qR[5];
+  const int ol = s.base + tl, orr = s.base + tr;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    qL[v] = a.Q[v * a.LS + t] + T(0.5) * a.Q[(5 + 5 * D + v) * a.LS + t];
-    qR[v] = a.Q[v * a.LS + tn] - T(0.5) * a.Q[(5 + 5 * D + v) * a.LS + tn];
+    qL[v] = a.Q[v * a.LS + ol] + T(0.5) * a.Q[(5 + 5 * D + v) * a.LS + ol];
+    qR[v] = a.Q[v * a.LS + orr] - T(0.5) * a.Q[(5 + 5 * D + v) * a.LS + orr];
   }
-  qL[0] = vmax(qL[0], a.smallr);
-  qR[0] = vmax(qR[0], a.smallr);
-  qL[4] = vmax(qL[4], qL[0] * a.smallp);
-  qR[4] = vmax(qR[4], qR[0] * a.smallp);
-  hllc<D>(qL, qR, a.gamma, a.igm1, F);
+  qL[0] = vmax(qL[0], s.smallr);
+  qR[0] = vmax(qR[0], s.smallr);
+  qL[4] = vmax(qL[4], qL[0] * s.smallp);
+  qR[4] = vmax(qR[4], qR[0] * s.smallp);
+  hllc<D>(qL, qR, s.gamma, s.igm1, F);
+}
+
+// reflux slot of a coarse-fine face: ghost oct g (local oct index), the
+// direction of the face seen from the ghost's father cell X, fine face (a,b)
+template <int D>
+__device__ __forceinline__ int reflux_slot(int clo, int nl, int gq, int dirX, int c) {
+  constexpr int d1 = D == 0 ? 1 : 0, d2 = D == 2 ? 1 : 2;
+  const int ab = (((c >> d1) & 1) << 1) | ((c >> d2) & 1);
+  return (clo + gq - nl) * 24 + dirX * 4 + ab;
 }
 
 template <int D, class T>
-__device__ __forceinline__ void flux_dir(const LevelArgs<T> &a, int t, int e, int c, int q,
-                                         bool real, bool split, T dtdx) {
+__device__ __forceinline__ void flux_dir(const StepArgs<T> &a, const SegCtx<T> &s, int t, int e,
+                                         int c, bool real, bool split) {
   T F[5] = {T(0), T(0), T(0), T(0), T(0)};
-  const int tn = nbr_local(a, t, e, c, D, 1);
+  const int tn = nbr_local(a, s, t, e, c, D, 1);
   bool need = false, nreal = false;
   if (tn >= 0) {
-    nreal = (tn >> 3) < a.nl;
-    need = (real || nreal) && !split && !cell_is_split(a, tn);
+    nreal = (tn >> 3) < s.nl;
+    need = (real || nreal) && !split && !cell_is_split(a, s, tn);
   }
   if (need) {
-    face_flux<D>(a, t, tn, F);
+    face_flux<D>(a, s, t, tn, F);
     if (a.reflux && (real != nreal)) {
-      constexpr int d1 = D == 0 ? 1 : 0, d2 = D == 2 ? 1 : 2;
-      const int ab = (((c >> d1) & 1) << 1) | ((c >> d2) & 1);
-      int gslot;
-      T sg;
-      if (real) {  // ghost on the plus side: the face is the coarse cell's minus face
-        gslot = (a.clo + (tn >> 3) - a.nl) * 24 + (2 * D) * 4 + ab;
-        sg = T(1);
-      } else {     // ghost on the minus side: the coarse cell's plus face
-        gslot = (a.clo + q - a.nl) * 24 + (2 * D + 1) * 4 + ab;
-        sg = T(-1);
-      }
+      // ghost on the plus side: the coarse cell's minus face (sigma +1);
+      // ghost on the minus side: its plus face (sigma -1)
+      const int gslot = real ? reflux_slot<D>(s.clo, s.nl, tn >> 3, 2 * D, c)
+                             : reflux_slot<D>(s.clo, s.nl, t >> 3, 2 * D + 1, c);
+      const T sg = real ? T(1) : T(-1);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (sg * dtdx) * F[v] / T(8);
+      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (sg * s.dtdx) * F[v] / T(8);
     }
   }
+  const int o = s.base + t;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) a.F[(5 * D + v) * a.LS + t] = F[v];
+  for (int v = 0; v < 5; ++v) a.F[(5 * D + v) * a.LS + o] = F[v];
 }
 
 // One thread per real or ghost cell: the fluxes of its three plus faces.
@@ -304,41 +406,29 @@ __device__ __forceinline__ void flux_dir(const LevelArgs<T> &a, int t, int e, in
 // is a coarse-fine face: its flux, times sigma dt/dx / 8, goes to slot
 // (direction seen from the coarse cell, fine face a,b) of the ghost oct.
 template <class T>
-__global__ void k_flux(LevelArgs<T> a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.LS) return;
-  const int q = t >> 3;
-  const int e = ext_of_local(a, q);
-  const int c = t & 7;
-  const bool real = q < a.nl;
-  const bool split = cell_is_split(a, t);
-  const T dtdx = level_dtdx(a);
-  flux_dir<0>(a, t, e, c, q, real, split, dtdx);
-  flux_dir<1>(a, t, e, c, q, real, split, dtdx);
-  flux_dir<2>(a, t, e, c, q, real, split, dtdx);
+__global__ void k_flux(StepArgs<T> a) {
+  tile_loop(a, [](const SegCtx<T> &s) { return 8 * (s.nl + s.ncl); },
+            [&](const SegCtx<T> &s, int t) {
+              const int q = t >> 3;
+              const int e = ext_of_local(a, s, q);
+              const int c = t & 7;
+              const bool real = q < s.nl;
+              const bool split = cell_is_split(a, s, t);
+              flux_dir<0>(a, s, t, e, c, real, split);
+              flux_dir<1>(a, s, t, e, c, real, split);
+              flux_dir<2>(a, s, t, e, c, real, split);
+            });
 }
 
 // U <- (U + dt/dx sum_d (F_d- - F_d+)) + R on leaf cells; R <- 0
 template <class T>
-__global__ void k_update(LevelArgs<T> a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 8 * a.nl) return;
-  if (cell_is_split(a, t)) return;
-  const int e = a.lo + (t >> 3);
-  const int c = t & 7;
-  const int tm0 = nbr_local(a, t, e, c, 0, 0), tm1 = nbr_local(a, t, e, c, 1, 0),
-            tm2 = nbr_local(a, t, e, c, 2, 0);
-  const T dtdx = level_dtdx(a);
-  const int g = 8 * e + c;
+__device__ __forceinline__ void update_cell(const StepArgs<T> &a, const SegCtx<T> &s, int g,
+                                            const T (&dx)[5], const T (&dy)[5], const T (&dz)[5]) {
   const int rs = __ldg(a.rslot + g);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const T dx = a.F[(0 + v) * a.LS + tm0] - a.F[(0 + v) * a.LS + t];
-    const T dy = a.F[(5 + v) * a.LS + tm1] - a.F[(5 + v) * a.LS + t];
-    const T dz = a.F[(10 + v) * a.LS + tm2] - a.F[(10 + v) * a.LS + t];
-    const T du = (dx + dy) + dz;
     T *Ug = a.U + v * a.S + g;
-    T u = *Ug + dtdx * du;
+    T u = *Ug + s.dtdx * ((dx[v] + dy[v]) + dz[v]);
     if (rs >= 0) {
       T *Rv = a.Rc + v * int64_t(a.NC) + rs;
       u = u + *Rv;
@@ -348,128 +438,49 @@ __global__ void k_update(LevelArgs<T> a) {
   }
 }
 
-// R(X) += sum of the 24 slots of the ghost oct whose father is X, in slot
-// order (direction -x,+x,-y,+y,-z,+z seen from X, then fine face)
 template <class T>
-__global__ void k_reflux(LevelArgs<T> a) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= 5 * a.ncl) return;
-  const int v = q / a.ncl;
-  const int s = a.clo + (q - v * a.ncl);
-  const T *cv = a.C + v * a.CS + 24 * int64_t(s);
-  T *Rv = a.Rc + v * int64_t(a.NC) + s;
-  T acc = *Rv;
+__global__ void k_update(StepArgs<T> a) {
+  tile_loop(a, [](const SegCtx<T> &s) { return 8 * s.nl; }, [&](const SegCtx<T> &s, int t) {
+    if (cell_is_split(a, s, t)) return;
+    const int e = s.lo + (t >> 3);
+    const int c = t & 7;
+    const int o = s.base + t;
+    const int om[3] = {s.base + nbr_local(a, s, t, e, c, 0, 0), s.base + nbr_local(a, s, t, e, c, 1, 0),
+                       s.base + nbr_local(a, s, t, e, c, 2, 0)};
+    T dx[5], dy[5], dz[5];
 #pragma unroll
-  for (int k = 0; k < 24; ++k) acc += cv[k];
-  *Rv = acc;
-}
-
-// father cell = (sum of the 8 children in child order) / 8
-template <class T>
-__global__ void k_restrict(LevelArgs<T> a) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= 5 * a.nl) return;
-  const int v = q / a.nl;
-  const int o = a.lo + (q - v * a.nl);
-  const uint64_t k = __ldg(a.key + o);
-  const int fc = int((key_x(k) & 1) | ((key_y(k) & 1) << 1) | ((key_z(k) & 1) << 2));
-  const int f = __ldg(a.father + o);
-  const T *src = a.U + v * a.S + 8 * o;
-  T s = T(0);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) s += src[c];
-  a.U[v * a.S + 8 * f + fc] = s * T(0.125);
-}
-
-// ---------------------------------------------------------------------------
-// FP32 level step in fewer launches.  FP32 arithmetic is cheap on GB300, so
-// these kernels trade recomputation for memory round trips and launches:
-// k_predict_u derives the primitives of a cell and its six face neighbours
-// from U directly (no W array); k_flux_update solves all six faces of a
-// real leaf cell and updates it in place (each interior face is solved by
-// both of its cells, bit-identically, so the update matches the split
-// kernels); coarse-fine faces are owned by the real cell.
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ void prim_at(const LevelArgs<T> &a, int t, T (&w)[5]) {
-  const int g = 8 * ext_of_local(a, t >> 3) + (t & 7);
-  const T r = vmax(a.U[g], a.smallr);
-  const T ir = rcp(r);
-  const T vx = a.U[a.S + g] * ir, vy = a.U[2 * a.S + g] * ir, vz = a.U[3 * a.S + g] * ir;
-  const T ek = T(0.5) * r * ((vx * vx + vy * vy) + vz * vz);
-  w[0] = r;
-  w[1] = vx;
-  w[2] = vy;
-  w[3] = vz;
-  w[4] = vmax((a.gamma - T(1)) * (a.U[4 * a.S + g] - ek), r * a.smallp);
-}
-
-template <class T>
-__global__ void k_predict_u(LevelArgs<T> a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.LS) return;
-  const int e = ext_of_local(a, t >> 3);
-  const int c = t & 7;
-  T w[5], dw[3][5];
-  prim_at(a, t, w);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int tm = nbr_local(a, t, e, c, d, 0);
-    const int tp = nbr_local(a, t, e, c, d, 1);
-    if (tm < 0 || tp < 0) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
-      continue;
+    for (int v = 0; v < 5; ++v) {
+      dx[v] = a.F[(0 + v) * a.LS + om[0]] - a.F[(0 + v) * a.LS + o];
+      dy[v] = a.F[(5 + v) * a.LS + om[1]] - a.F[(5 + v) * a.LS + o];
+      dz[v] = a.F[(10 + v) * a.LS + om[2]] - a.F[(10 + v) * a.LS + o];
     }
-    T wm[5], wp[5];
-    prim_at(a, tm, wm);
-    prim_at(a, tp, wp);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) dw[d][v] = minmod(wp[v] - w[v], w[v] - wm[v]);
-  }
-  const T r = w[0], p = w[4], g = a.gamma;
-  const T ir = rcp(r);
-  const T gp = g * p;
-  T s[5];
-  s[0] = -(((w[1] * dw[0][0] + r * dw[0][1]) + (w[2] * dw[1][0] + r * dw[1][2])) +
-           (w[3] * dw[2][0] + r * dw[2][3]));
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    s[1 + k] = -((w[1] * dw[0][1 + k] + w[2] * dw[1][1 + k]) + w[3] * dw[2][1 + k]) - dw[k][4] * ir;
-  s[4] = -(((w[1] * dw[0][4] + gp * dw[0][1]) + (w[2] * dw[1][4] + gp * dw[1][2])) +
-           (w[3] * dw[2][4] + gp * dw[2][3]));
-  const T hdt = T(0.5) * level_dtdx(a);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) a.Q[v * a.LS + t] = w[v] + hdt * s[v];
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int v = 0; v < 5; ++v) a.Q[(5 + 5 * d + v) * a.LS + t] = dw[d][v];
+    update_cell(a, s, 8 * e + c, dx, dy, dz);
+  });
 }
 
-// the two faces of local cell t along axis D; du += F(minus) - F(plus)
+// FP32: the two faces of local cell t along axis D, du = F(minus) - F(plus);
+// each interior face is solved by both of its cells (bit-identically), and a
+// coarse-fine face by its real cell, which also fills the reflux slot
 template <int D, class T>
-__device__ __forceinline__ void faces_dir(const LevelArgs<T> &a, int t, int e, int c, T dtdx,
-                                          T (&du)[5]) {
-  constexpr int d1 = D == 0 ? 1 : 0, d2 = D == 2 ? 1 : 2;
-  const int ab = (((c >> d1) & 1) << 1) | ((c >> d2) & 1);
+__device__ __forceinline__ void faces_dir(const StepArgs<T> &a, const SegCtx<T> &s, int t, int e,
+                                          int c, T (&du)[5]) {
   T Fm[5] = {T(0), T(0), T(0), T(0), T(0)}, Fp[5] = {T(0), T(0), T(0), T(0), T(0)};
-  const int tm = nbr_local(a, t, e, c, D, 0);
-  if (!cell_is_split(a, tm)) {
-    face_flux<D>(a, tm, t, Fm);
-    if (a.reflux && (tm >> 3) >= a.nl) {  // ghost on the minus side
-      const int gslot = (a.clo + (tm >> 3) - a.nl) * 24 + (2 * D + 1) * 4 + ab;
+  const int tm = nbr_local(a, s, t, e, c, D, 0);
+  if (!cell_is_split(a, s, tm)) {
+    face_flux<D>(a, s, tm, t, Fm);
+    if (a.reflux && (tm >> 3) >= s.nl) {
+      const int gslot = reflux_slot<D>(s.clo, s.nl, tm >> 3, 2 * D + 1, c);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(-1) * dtdx) * Fm[v] / T(8);
+      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(-1) * s.dtdx) * Fm[v] / T(8);
     }
   }
-  const int tp = nbr_local(a, t, e, c, D, 1);
-  if (!cell_is_split(a, tp)) {
-    face_flux<D>(a, t, tp, Fp);
-    if (a.reflux && (tp >> 3) >= a.nl) {  // ghost on the plus side
-      const int gslot = (a.clo + (tp >> 3) - a.nl) * 24 + (2 * D) * 4 + ab;
+  const int tp = nbr_local(a, s, t, e, c, D, 1);
+  if (!cell_is_split(a, s, tp)) {
+    face_flux<D>(a, s, t, tp, Fp);
+    if (a.reflux && (tp >> 3) >= s.nl) {
+      const int gslot = reflux_slot<D>(s.clo, s.nl, tp >> 3, 2 * D, c);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(1) * dtdx) * Fp[v] / T(8);
+      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(1) * s.dtdx) * Fp[v] / T(8);
     }
   }
 #pragma unroll
@@ -477,123 +488,123 @@ __device__ __forceinline__ void faces_dir(const LevelArgs<T> &a, int t, int e, i
 }
 
 template <class T>
-__global__ void k_flux_update(LevelArgs<T> a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 8 * a.nl) return;
-  if (cell_is_split(a, t)) return;
-  const int e = a.lo + (t >> 3);
-  const int c = t & 7;
-  const T dtdx = level_dtdx(a);
-  T dx[5], dy[5], dz[5];
-  faces_dir<0>(a, t, e, c, dtdx, dx);
-  faces_dir<1>(a, t, e, c, dtdx, dy);
-  faces_dir<2>(a, t, e, c, dtdx, dz);
-  const int g = 8 * e + c;
-  const int rs = __ldg(a.rslot + g);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    T *Ug = a.U + v * a.S + g;
-    T u = *Ug + dtdx * ((dx[v] + dy[v]) + dz[v]);
-    if (rs >= 0) {
-      T *Rv = a.Rc + v * int64_t(a.NC) + rs;
-      u = u + *Rv;
-      *Rv = T(0);
-    }
-    *Ug = u;
-  }
+__global__ void k_flux_update(StepArgs<T> a) {
+  tile_loop(a, [](const SegCtx<T> &s) { return 8 * s.nl; }, [&](const SegCtx<T> &s, int t) {
+    if (cell_is_split(a, s, t)) return;
+    const int e = s.lo + (t >> 3);
+    const int c = t & 7;
+    T dx[5], dy[5], dz[5];
+    faces_dir<0>(a, s, t, e, c, dx);
+    faces_dir<1>(a, s, t, e, c, dy);
+    faces_dir<2>(a, s, t, e, c, dz);
+    update_cell(a, s, 8 * e + c, dx, dy, dz);
+  });
 }
 
-// k_reflux and k_restrict in one launch: they touch disjoint data (reflux
-// sums go to the pending reflux of leaf cells of level l-1, restriction
-// writes split cells of level l-1)
+// Reflux: R(X) += sum of the 24 slots of the ghost oct whose father is X, in
+// slot order (direction -x,+x,-y,+y,-z,+z seen from X, then fine face).
+// Restriction: father cell = (sum of the 8 children in child order) / 8.
+// They touch disjoint data (leaf cells' pending reflux, split cells).
+// domain: 5 ncl (if kSegReflux) + 5 nl (if kSegRestrict)
 template <class T>
-__global__ void k_reflux_restrict(LevelArgs<T> a, int do_restrict) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nref = a.reflux ? 5 * a.ncl : 0;
-  if (q < nref) {
-    const int v = q / a.ncl;
-    const int s = a.clo + (q - v * a.ncl);
-    const T *cv = a.C + v * a.CS + 24 * int64_t(s);
-    T *Rv = a.Rc + v * int64_t(a.NC) + s;
-    T acc = *Rv;
+__global__ void k_reflux_restrict(StepArgs<T> a) {
+  tile_loop(a,
+            [](const SegCtx<T> &s) {
+              return ((s.flags & kSegReflux) ? 5 * s.ncl : 0) + ((s.flags & kSegRestrict) ? 5 * s.nl : 0);
+            },
+            [&](const SegCtx<T> &s, int q) {
+              const int nref = (s.flags & kSegReflux) ? 5 * s.ncl : 0;
+              if (q < nref) {
+                const int v = q / s.ncl;
+                const int g = s.clo + (q - v * s.ncl);
+                const T *cv = a.C + v * a.CS + 24 * int64_t(g);
+                T *Rv = a.Rc + v * int64_t(a.NC) + g;
+                T acc = *Rv;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) acc += cv[k];
-    *Rv = acc;
-    return;
-  }
-  const int r = q - nref;
-  if (!do_restrict || r >= 5 * a.nl) return;
-  const int v = r / a.nl;
-  const int o = a.lo + (r - v * a.nl);
-  const uint64_t k = __ldg(a.key + o);
-  const int fc = int((key_x(k) & 1) | ((key_y(k) & 1) << 1) | ((key_z(k) & 1) << 2));
-  const int f = __ldg(a.father + o);
-  const T *src = a.U + v * a.S + 8 * o;
-  T sum = T(0);
+                for (int k = 0; k < 24; ++k) acc += cv[k];
+                *Rv = acc;
+                return;
+              }
+              const int r = q - nref;
+              const int v = r / s.nl;
+              const int o = s.lo + (r - v * s.nl);
+              const uint64_t k = __ldg(a.key + o);
+              const int fc = int((ikey_x(k) & 1) | ((ikey_y(k) & 1) << 1) | ((ikey_z(k) & 1) << 2));
+              const int f = __ldg(a.father + o);
+              const T *src = a.U + v * a.S + 8 * int64_t(o);
+              T sum = T(0);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) sum += src[c];
-  a.U[v * a.S + 8 * f + fc] = sum * T(0.125);
+              for (int c = 0; c < 8; ++c) sum += src[c];
+              a.U[v * a.S + 8 * int64_t(f) + fc] = sum * T(0.125);
+            });
 }
 
 // ---------------------------------------------------------------------------
-// CFL time step: per-level max of sum_d (|u_d| + c) over leaf cells (cell
-// speeds in the state's precision, the maximum and dt in FP64), warp-shuffle
-// then block reduction, one integer atomicMax per block on the bit pattern
-// (non-negative doubles order like their bits), then dt on one thread.
+// CFL time step: per (member, level) max of sum_d (|u_d| + c) over leaf cells
+// (cell speeds in the state's precision, the maximum and dt in FP64): block
+// reduction of each tile (warp shuffles, then shared memory), one integer
+// atomicMax per tile on the bit pattern (non-negative doubles order like their
+// bits); then one thread per member computes its dt.
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_cfl(CflArgs a, const T *U) {
-  const int l = a.lmin + blockIdx.y;
-  const int64_t lo = a.lo[l], n8 = 8 * (a.lo[l + 1] - lo);
-  const T g = T(a.gamma), smallr = T(a.smallr), smallp = T(a.smallp);
-  double s = 0.0;
-  bool bad = false;
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n8;
-       t += int64_t(gridDim.x) * blockDim.x) {
-    if ((__ldg(a.son + lo + (t >> 3)) >> (t & 7)) & 1u) continue;
-    const int64_t gi = 8 * lo + t;
-    const T u0 = U[gi], u1 = U[a.S + gi], u2 = U[2 * a.S + gi], u3 = U[3 * a.S + gi],
-            u4 = U[4 * a.S + gi];
-    const T r = vmax(u0, smallr);
-    const T ir = rcp(r);
-    const T vx = u1 * ir, vy = u2 * ir, vz = u3 * ir;
-    const T ek = T(0.5) * r * ((vx * vx + vy * vy) + vz * vz);
-    const T p = vmax((g - T(1)) * (u4 - ek), r * smallp);
-    const T cs = vsqrt(g * p * ir);
-    const T st = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
-    if (!isfinite(st) || !isfinite(u0 + u1 + u2 + u3 + u4))
-      bad = true;
-    else
-      s = fmax(s, double(st));
-  }
-  if (bad) atomicOr(a.err, kErrNaN);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
   __shared__ double wmax[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) wmax[warp] = s;
-  __syncthreads();
-  if (warp == 0) {
-    s = lane < int(blockDim.x >> 5) ? wmax[lane] : 0.0;
+  for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
+    const Tile td = a.tiles[ti];
+    const Seg sg = a.segs[td.seg];
+    const int t = td.start + threadIdx.x;
+    double s = 0.0;
+    if (t < 8 * sg.nl && !((__ldg(a.son + sg.lo + (t >> 3)) >> (t & 7)) & 1u)) {
+      const T g = T(a.mgamma[sg.member]), smallr = T(a.msmallr[sg.member]),
+              smallp = T(a.msmallp[sg.member]);
+      const int64_t gi = 8 * int64_t(sg.lo) + t;
+      const T u0 = U[gi], u1 = U[a.S + gi], u2 = U[2 * a.S + gi], u3 = U[3 * a.S + gi],
+              u4 = U[4 * a.S + gi];
+      const T r = vmax(u0, smallr);
+      const T ir = rcp(r);
+      const T vx = u1 * ir, vy = u2 * ir, vz = u3 * ir;
+      const T ek = T(0.5) * r * ((vx * vx + vy * vy) + vz * vz);
+      const T p = vmax((g - T(1)) * (u4 - ek), r * smallp);
+      const T cs = vsqrt(g * p * ir);
+      const T st = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
+      if (!isfinite(st) || !isfinite(u0 + u1 + u2 + u3 + u4))
+        atomicOr(a.err, kErrNaN);
+      else
+        s = double(st);
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
-    if (lane == 0 && s > 0.0) atomicMax(a.smax + l, (unsigned long long)__double_as_longlong(s));
+    if (lane == 0) wmax[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+      s = lane < int(blockDim.x >> 5) ? wmax[lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+      if (lane == 0 && s > 0.0)
+        atomicMax(a.smax + 16 * sg.member + sg.level, (unsigned long long)__double_as_longlong(s));
+    }
+    __syncthreads();
   }
 }
 
 __global__ void k_dt(CflArgs a) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.nmembers) return;
+  const int lmin = a.mlmin[m];
   double dt = __longlong_as_double(0x7FF0000000000000ll);  // +inf
-  for (int l = a.lmin; l <= a.lmax; ++l) {
-    const unsigned long long b = a.smax[l];
-    a.smax[l] = 0ull;
+  for (int l = lmin; l <= kMaxLev; ++l) {
+    const unsigned long long b = a.smax[16 * m + l];
+    a.smax[16 * m + l] = 0ull;
     if (b == 0ull) continue;
     const double smax = __longlong_as_double((long long)b);
-    const double dtl = a.cfl * ldexp(1.0, -l) / smax;
-    const double dtc = dtl * ldexp(1.0, l - a.lmin);
+    const double dtl = a.mcfl[m] * ldexp(1.0, -l) / smax;
+    const double dtc = dtl * ldexp(1.0, l - lmin);
     dt = fmin(dt, dtc);
   }
-  *a.dt_dev = dt;
-  *a.dtf_dev = float(dt);
+  a.dt_dev[m] = dt;
+  a.dtdx_dev[m] = ldexp(dt, lmin);
+  a.dtdxf_dev[m] = ldexpf(float(dt), lmin);
 }
 
 template <class T>

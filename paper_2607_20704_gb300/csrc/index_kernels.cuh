@@ -1,33 +1,40 @@
 // index_kernels.cuh -- create-time and re-index kernels: oct ordering (level
 // bucket sort with prefix sums after a Hilbert-key LSD radix sort, Sec. 2.2),
-// the FNV-1a 64 linear-probing hash table (Sec. 2.1), father/son flags,
-// the 27-entry neighbour array and the ghost-oct cache (Sec. 2.3).
+// the FNV-1a 64 linear-probing hash table (Sec. 2.1, Sec. 6), father/son
+// flags, the 27-entry neighbour array and the ghost-oct cache (Sec. 2.3).
+// Every oct carries the member mesh it belongs to (a handle may hold many
+// independent meshes); neighbours, fathers and ghosts never cross members.
 #pragma once
 #include "amr_internal.cuh"
 
 namespace amr {
 
 // ---------------------------------------------------------------------------
-// input validation and sort keys
+// input validation and sort keys: (member, level, Hilbert key within level)
 // ---------------------------------------------------------------------------
+constexpr int kHilbertBits = 42;  // 3 x 14 bits: levels up to 15
+
 __global__ void k_make_sort_keys(const uint8_t *__restrict__ lvl, const uint32_t *__restrict__ ci,
                                  const uint32_t *__restrict__ cj, const uint32_t *__restrict__ ck,
-                                 const uint64_t *__restrict__ hkey_in, int64_t n, int lmin, int lmax,
-                                 uint64_t *__restrict__ comp, uint32_t *__restrict__ perm,
-                                 int *__restrict__ err) {
+                                 const uint16_t *__restrict__ mem, const uint64_t *__restrict__ hkey_in,
+                                 int64_t n, const int *__restrict__ mlmin,
+                                 const int *__restrict__ mlmax, uint64_t *__restrict__ comp,
+                                 uint32_t *__restrict__ perm, int *__restrict__ err) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= n) return;
   const int l = lvl[t];
+  const int m = mem[t];
   uint64_t h = 0;
-  if (l < lmin || l > lmax) {
+  if (l < mlmin[m] || l > mlmax[m]) {
     atomicOr(err, kErrRange);
   } else {
     const uint32_t side = 1u << (l - 1);
     if (ci[t] >= side || cj[t] >= side || ck[t] >= side) atomicOr(err, kErrRange);
     h = hkey_in ? hkey_in[t] : hilbert_index(ci[t], cj[t], ck[t], l - 1);
-    if (h >> 58) atomicOr(err, kErrRange);
+    if (h >> kHilbertBits) atomicOr(err, kErrRange);
   }
-  comp[t] = (uint64_t(l & 15) << 58) | (h & ((1ull << 58) - 1));
+  comp[t] = (uint64_t(m) << (kHilbertBits + 4)) | (uint64_t(l & 15) << kHilbertBits) |
+            (h & ((1ull << kHilbertBits) - 1));
   perm[t] = uint32_t(t);
 }
 
@@ -97,7 +104,7 @@ __global__ void k_scan_block(uint32_t *__restrict__ data, int64_t n, uint32_t *_
     s[q] = t < n ? data[t] : 0u;
   }
   __syncthreads();
-  // Hillis-Steele on 1024 items with 256 threads: each thread owns 4 items
+  // each of the 256 threads owns 4 items; Hillis-Steele over the thread sums
   const int q0 = threadIdx.x * 4;
   uint32_t a0 = s[q0], a1 = s[q0 + 1], a2 = s[q0 + 2], a3 = s[q0 + 3];
   const uint32_t tot = a0 + a1 + a2 + a3;
@@ -129,19 +136,19 @@ __global__ void k_scan_add(uint32_t *__restrict__ data, int64_t n, const uint32_
 }
 
 // ---------------------------------------------------------------------------
-// gather octs and state into mesh order
+// gather octs and state into mesh order; counts octs per (member, level)
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_gather_octs(const uint32_t *__restrict__ perm, const uint8_t *__restrict__ lvl,
                               const uint32_t *__restrict__ ci, const uint32_t *__restrict__ cj,
-                              const uint32_t *__restrict__ ck, const double *__restrict__ Uin,
-                              int64_t n, uint64_t *__restrict__ key, T *__restrict__ U, int64_t S,
-                              uint32_t *__restrict__ level_count) {
+                              const uint32_t *__restrict__ ck, const uint16_t *__restrict__ mem,
+                              const double *__restrict__ Uin, int64_t n, uint64_t *__restrict__ key,
+                              T *__restrict__ U, int64_t S, uint32_t *__restrict__ seg_count) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= n) return;
   const uint32_t s = perm[t];
-  key[t] = key_pack(lvl[s], ci[s], cj[s], ck[s]);
-  if (level_count) atomicAdd(level_count + lvl[s], 1u);
+  key[t] = ikey(mem[s], lvl[s], ci[s], cj[s], ck[s]);
+  if (seg_count) atomicAdd(seg_count + 16 * int(mem[s]) + lvl[s], 1u);
   if (!U) return;
   for (int v = 0; v < kNV; ++v)
 #pragma unroll
@@ -164,14 +171,19 @@ __global__ void k_hash_insert(HashView h, const uint64_t *__restrict__ key, int6
   h.val[s] = int32_t(t + 1);
 }
 
-__global__ void k_father_son(HashView h, const uint64_t *__restrict__ key, int64_t first, int64_t n,
-                             int32_t *__restrict__ father, uint32_t *__restrict__ son, int *err) {
-  const int64_t t = first + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+__global__ void k_father_son(HashView h, const uint64_t *__restrict__ key, int64_t n,
+                             const int *__restrict__ mlmin, int32_t *__restrict__ father,
+                             uint32_t *__restrict__ son, int *err) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= n) return;
   const uint64_t k = key[t];
-  const int l = key_lev(k);
-  const uint32_t x = key_x(k), y = key_y(k), z = key_z(k);
-  const int32_t v = hash_probe1(h, key_pack(l - 1, x >> 1, y >> 1, z >> 1));
+  const int l = ikey_lev(k);
+  if (l <= mlmin[ikey_member(k)]) {
+    father[t] = -1;
+    return;
+  }
+  const uint32_t x = ikey_x(k), y = ikey_y(k), z = ikey_z(k);
+  const int32_t v = hash_probe1(h, ikey_at(k, l - 1, x >> 1, y >> 1, z >> 1));
   if (v <= 0) {
     atomicOr(err, kErrGrading);
     father[t] = -1;
@@ -181,26 +193,36 @@ __global__ void k_father_son(HashView h, const uint64_t *__restrict__ key, int64
   atomicOr(son + (v - 1), 1u << ((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)));
 }
 
-// 27 level-(l-1) cells around the father cell of each oct above levelmin
-__global__ void k_grading(HashView h, const uint64_t *__restrict__ key, int64_t first, int64_t n,
-                          int *err) {
+// 27 level-(l-1) cells around the father cell of each oct above its
+// member's levelmin (8-lane cooperative probes)
+__global__ void k_grading(HashView h, const uint64_t *__restrict__ key, int64_t n,
+                          const int *__restrict__ mlmin, int *err) {
   const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 3;
-  const int64_t t = first + q / 27;
+  const int64_t t = q / 27;
   if (t >= n) return;
   const int e = int(q % 27);
   const uint64_t k = key[t];
-  const int l = key_lev(k);
+  const int l = ikey_lev(k);
+  if (l <= mlmin[ikey_member(k)]) return;  // the whole lane group leaves together
   const int64_t cells = int64_t(1) << (l - 1);
-  const uint32_t x = wrapc(int64_t(key_x(k)) + (e % 3) - 1, cells);
-  const uint32_t y = wrapc(int64_t(key_y(k)) + (e / 3 % 3) - 1, cells);
-  const uint32_t z = wrapc(int64_t(key_z(k)) + (e / 9) - 1, cells);
-  const int32_t v = hash_probe8(h, key_pack(l - 1, x >> 1, y >> 1, z >> 1));
+  const uint32_t x = wrapc(int64_t(ikey_x(k)) + (e % 3) - 1, cells);
+  const uint32_t y = wrapc(int64_t(ikey_y(k)) + (e / 3 % 3) - 1, cells);
+  const uint32_t z = wrapc(int64_t(ikey_z(k)) + (e / 9) - 1, cells);
+  const int32_t v = hash_probe8(h, ikey_at(k, l - 1, x >> 1, y >> 1, z >> 1));
   if (v <= 0 && (threadIdx.x & 7) == 0) atomicOr(err, kErrGrading);
 }
 
 // ---------------------------------------------------------------------------
 // 27-neighbour array; missing neighbours are claimed as ghost keys
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t neighbour_key(uint64_t k, int e) {
+  const int l = ikey_lev(k);
+  const int64_t side = int64_t(1) << (l - 1);
+  return ikey_at(k, l, wrapc(int64_t(ikey_x(k)) + (e % 3) - 1, side),
+                 wrapc(int64_t(ikey_y(k)) + (e / 3 % 3) - 1, side),
+                 wrapc(int64_t(ikey_z(k)) + (e / 9) - 1, side));
+}
+
 __global__ void k_neighbours(HashView h, const uint64_t *__restrict__ key, int64_t n,
                              int32_t *__restrict__ nbr27, uint64_t *__restrict__ claim,
                              uint32_t *__restrict__ claim_count, int64_t claim_cap, int *err) {
@@ -215,12 +237,7 @@ __global__ void k_neighbours(HashView h, const uint64_t *__restrict__ key, int64
     nbr27[q] = int32_t(t);
     return;
   }
-  const uint64_t k = key[t];
-  const int l = key_lev(k);
-  const int64_t side = int64_t(1) << (l - 1);
-  const uint64_t nk = key_pack(l, wrapc(int64_t(key_x(k)) + (e % 3) - 1, side),
-                               wrapc(int64_t(key_y(k)) + (e / 3 % 3) - 1, side),
-                               wrapc(int64_t(key_z(k)) + (e / 9) - 1, side));
+  const uint64_t nk = neighbour_key(key[t], e);
   const int32_t v = hash_probe1(h, nk);
   if (v >= 1 && int64_t(v) <= n) {
     nbr27[q] = v - 1;
@@ -239,28 +256,29 @@ __global__ void k_neighbours(HashView h, const uint64_t *__restrict__ key, int64
   }
 }
 
-// compact sort key of a ghost key: (l, x, y, z) with B bits per coordinate
+// compact sort key of a ghost key: (member, l, x, y, z), B bits per coordinate
 __global__ void k_claim_to_comp(const uint64_t *__restrict__ claim, int64_t nc, int B,
                                 uint64_t *__restrict__ comp, uint32_t *__restrict__ val) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= nc) return;
   const uint64_t k = claim[t];
-  comp[t] = (uint64_t(key_lev(k)) << (3 * B)) | (uint64_t(key_x(k)) << (2 * B)) |
-            (uint64_t(key_y(k)) << B) | uint64_t(key_z(k));
+  comp[t] = (uint64_t(ikey_member(k)) << (4 + 3 * B)) | (uint64_t(ikey_lev(k)) << (3 * B)) |
+            (uint64_t(ikey_x(k)) << (2 * B)) | (uint64_t(ikey_y(k)) << B) | uint64_t(ikey_z(k));
   val[t] = 0;
 }
 
 __global__ void k_cache_finalize(HashView h, const uint64_t *__restrict__ comp, int64_t nc, int B,
                                  int64_t N, uint64_t *__restrict__ ckey,
-                                 uint32_t *__restrict__ level_count, int *err) {
+                                 uint32_t *__restrict__ seg_count, int *err) {
   const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (s >= nc) return;
   const uint64_t c = comp[s];
-  const uint64_t m = (1ull << B) - 1;
-  const int l = int(c >> (3 * B));
-  const uint64_t k = key_pack(l, uint32_t((c >> (2 * B)) & m), uint32_t((c >> B) & m), uint32_t(c & m));
+  const uint64_t msk = (1ull << B) - 1;
+  const int l = int((c >> (3 * B)) & 15);
+  const int m = int(c >> (4 + 3 * B));
+  const uint64_t k = ikey(m, l, uint32_t((c >> (2 * B)) & msk), uint32_t((c >> B) & msk), uint32_t(c & msk));
   ckey[s] = k;
-  atomicAdd(level_count + l, 1u);
+  if (seg_count) atomicAdd(seg_count + 16 * m + l, 1u);
   uint64_t p = fnv1a64(k) & h.mask;
   for (uint64_t r = 0; r <= h.mask; ++r) {
     if (h.key[p] == k) {
@@ -277,15 +295,9 @@ __global__ void k_neighbours_fix(HashView h, const uint64_t *__restrict__ key, i
   const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (q >= 27 * n) return;
   if (nbr27[q] >= 0) return;
-  const int64_t t = q % n;
   const int e = int(q / n);
-  const uint64_t k = key[t];
-  const int l = key_lev(k);
-  const int64_t side = int64_t(1) << (l - 1);
-  const uint64_t nk = key_pack(l, wrapc(int64_t(key_x(k)) + (e % 3) - 1, side),
-                               wrapc(int64_t(key_y(k)) + (e / 3 % 3) - 1, side),
-                               wrapc(int64_t(key_z(k)) + (e / 9) - 1, side));
-  const int32_t v = hash_probe1(h, nk);
+  const int64_t t = q - int64_t(e) * n;
+  const int32_t v = hash_probe1(h, neighbour_key(key[t], e));
   if (v <= n || v == kPending) {
     atomicOr(err, kErrCacheMismatch);
     return;
@@ -309,25 +321,20 @@ __global__ void k_faces_cache(HashView h, const uint64_t *__restrict__ ckey, int
   if (q >= 6 * nc) return;
   const int f = int(q / nc);
   const int64_t s = q % nc;
-  const uint64_t k = ckey[s];
-  const int l = key_lev(k);
-  const int64_t side = int64_t(1) << (l - 1);
   const int d = f >> 1, sg = (f & 1) ? 1 : -1;
-  const uint64_t nk = key_pack(l, wrapc(int64_t(key_x(k)) + (d == 0 ? sg : 0), side),
-                               wrapc(int64_t(key_y(k)) + (d == 1 ? sg : 0), side),
-                               wrapc(int64_t(key_z(k)) + (d == 2 ? sg : 0), side));
-  const int32_t v = hash_probe1(h, nk);
+  const int e = 13 + sg * (d == 0 ? 1 : (d == 1 ? 3 : 9));
+  const int32_t v = hash_probe1(h, neighbour_key(ckey[s], e));
   fnb[int64_t(f) * next + N + s] = (v >= 1 && v != kPending) ? v - 1 : -1;
 }
 
-// cell of level L at cell coordinates (x,y,z), or the coarser cell covering
-// it when its oct is absent; -1 if none down to levelmin.
-__device__ int64_t cell_or_coarser(HashView h, int L, int64_t x, int64_t y, int64_t z, int lmin,
-                                   int64_t N, int *found_level) {
+// cell of level L at cell coordinates (x,y,z) of member key km's mesh, or the
+// coarser cell covering it when its oct is absent; -1 if none down to lmin.
+__device__ int64_t cell_or_coarser(HashView h, uint64_t km, int L, int64_t x, int64_t y, int64_t z,
+                                   int lmin, int64_t N, int *found_level) {
   while (L >= lmin) {
     const int64_t side = int64_t(1) << L;
     const uint32_t X = wrapc(x, side), Y = wrapc(y, side), Z = wrapc(z, side);
-    const int32_t v = hash_probe1(h, key_pack(L, X >> 1, Y >> 1, Z >> 1));
+    const int32_t v = hash_probe1(h, ikey_at(km, L, X >> 1, Y >> 1, Z >> 1));
     if (v >= 1 && int64_t(v) <= N) {
       *found_level = L;
       return 8 * int64_t(v - 1) + ((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2));
@@ -342,35 +349,35 @@ __device__ int64_t cell_or_coarser(HashView h, int L, int64_t x, int64_t y, int6
 
 // prolongation sources of each ghost oct: its father cell C and C -/+ e_d
 // for d = x, y, z (order C, -x, +x, -y, +y, -z, +z); C is also the coarse
-// cell that receives the reflux of the ghost's faces.
+// cell that receives the reflux of the ghost's faces (rslot[C] = ghost slot).
 __global__ void k_cache_sources(HashView h, const uint64_t *__restrict__ ckey, int64_t nc, int64_t N,
-                                int lmin, int32_t *__restrict__ csrc, int32_t *__restrict__ rslot,
-                                int *err) {
+                                const int *__restrict__ mlmin, int32_t *__restrict__ csrc,
+                                int32_t *__restrict__ rslot, int *err) {
   const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (s >= nc) return;
   const uint64_t k = ckey[s];
-  const int l = key_lev(k);
-  const int64_t x = key_x(k), y = key_y(k), z = key_z(k);
+  const int l = ikey_lev(k);
+  const int lmin = mlmin[ikey_member(k)];
+  const int64_t x = ikey_x(k), y = ikey_y(k), z = ikey_z(k);
   for (int q = 0; q < 7; ++q) {
     const int d = (q - 1) >> 1;
     const int sg = (q & 1) ? -1 : 1;
     const int64_t dx = (q > 0 && d == 0) ? sg : 0, dy = (q > 0 && d == 1) ? sg : 0,
                   dz = (q > 0 && d == 2) ? sg : 0;
     int fl = -1;
-    const int64_t c = cell_or_coarser(h, l - 1, x + dx, y + dy, z + dz, lmin, N, &fl);
+    const int64_t c = cell_or_coarser(h, k, l - 1, x + dx, y + dy, z + dz, lmin, N, &fl);
     if (c < 0 || (q == 0 && fl != l - 1)) {
       atomicOr(err, kErrGrading);
       csrc[int64_t(q) * nc + s] = 0;
       continue;
     }
     csrc[int64_t(q) * nc + s] = int32_t(c);
-    // the father cell is the coarse cell that receives this ghost's reflux;
     // distinct ghost octs have distinct fathers
     if (q == 0) rslot[c] = int32_t(s);
   }
 }
 
-// hash_get for a batch of keys (introspection)
+// hash_get for a batch of internal keys (introspection), 8-lane groups
 __global__ void k_lookup(HashView h, const uint64_t *__restrict__ keys, int64_t nq, int64_t N,
                          int64_t *__restrict__ out) {
   const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 3;

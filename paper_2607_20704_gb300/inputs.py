@@ -382,3 +382,63 @@ def to_array(prob: Problem) -> np.ndarray:
     gz = (2 * prob.k.astype(np.int64)[:, None] + ((c >> 2) & 1)[None, :]).ravel()
     out[:, gx + n * (gy + n * gz)] = prob.U
     return out
+
+
+def batched(n_members: int = 512, seed: int = 11, max_extra: int = 3):
+    """Ensemble of independent meshes for batched advancing: Sod or Sedov
+    (50/50), base 16^3, 32^3 or 64^3 cells (uniform in log), 0..max_extra
+    extra levels (Sod: nested slabs around the interface; Sedov: nested
+    balls), all drawn from one seeded generator."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_members):
+        kind = "sod" if rng.random() < 0.5 else "sedov"
+        lmin = int(rng.integers(4, 7))
+        extra = int(rng.integers(0, max_extra + 1))
+        lmax = lmin + extra
+        if kind == "sod":
+            prob = _nested_sod(lmin, lmax, axis=int(rng.integers(0, 3)))
+        else:
+            radii = {l: 0.24 * 0.5 ** (l - lmin - 1) for l in range(lmin + 1, lmax + 1)}
+            prob = sedov(lmin, lmax, radii=radii)
+        out.append(prob)
+    return out
+
+
+def _nested_sod(levelmin: int, levelmax: int, axis: int = 0, gamma: float = 1.4, cfl: float = 0.8):
+    """Sod tube with nested refined slabs around the interface at 1/2:
+    level l+1 covers the level-l cells within 0.05 * 2^-(l-levelmin) of it
+    and, below the first extra level, within 0.3 * 2^-(l-levelmin) of the
+    tube's axis (a patch of the interface)."""
+    split = {}
+    for l in range(levelmin, levelmax):
+        half = 0.05 * 0.5 ** (l - levelmin)
+        side = 1 << l
+        g = np.arange(side, dtype=np.int64)
+        c = (g + 0.5) / side
+        sel = g[np.abs(c - 0.5) < half]
+        A, B, Cc = np.meshgrid(sel, g, g, indexing="ij")
+        A, B, Cc = A.ravel(), B.ravel(), Cc.ravel()
+        if l > levelmin:
+            r = 0.3 * 0.5 ** (l - levelmin)
+            tb, tc = (B + 0.5) / side - 0.5, (Cc + 0.5) / side - 0.5
+            keep = tb * tb + tc * tc < r * r
+            A, B, Cc = A[keep], B[keep], Cc[keep]
+        coords = [None, None, None]
+        coords[axis] = A
+        others = [d for d in range(3) if d != axis]
+        coords[others[0]] = B
+        coords[others[1]] = Cc
+        split[l] = _code(*coords)
+    lv, i, j, k = graded_octs(levelmin, split)
+
+    def fn(x, y, z):
+        c = (x, y, z)[axis]
+        left = c < 0.5
+        rho = np.where(left, 1.0, 0.125)
+        p = np.where(left, 1.0, 0.1)
+        zero = np.zeros_like(rho)
+        return rho, zero, zero.copy(), zero.copy(), p
+
+    return Problem("sod", levelmin, levelmax, gamma, cfl, lv, i, j, k, _state(gamma, lv, i, j, k, fn),
+                   {"axis": axis})

@@ -38,7 +38,7 @@ def test_status_strings_and_kernel_names(lib):
     for code, name in amr.STATUS.items():
         assert lib.amr_status_string(code).decode() == name
     names = amr.kernel_names()
-    for k in ("prolong", "predict", "flux", "update", "reflux", "restrict", "cfl", "neighbours"):
+    for k in ("prolong", "predict", "flux", "update", "reflux_restrict", "cfl", "neighbours"):
         assert k in names
 
 

@@ -1,0 +1,107 @@
+"""Batched handles: many independent meshes advanced by the same launches.
+Each member must equal the same mesh in a handle of its own, bit for bit,
+and match its FP64 oracle within the W-cycle tolerance."""
+import numpy as np
+import pytest
+
+from paper_2607_20704_gb300 import inputs
+from parity import compare_all
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_20704_gb300 import amr, build
+    build.build()
+    amr.load()
+
+
+def _mixed(seed):
+    """Members with different levelmin, depth, gamma and level ranges."""
+    return [inputs.random_mesh(3, 5, seed=seed).shuffled(1),
+            inputs.sedov(3, 5, radii={5: 0.1, 4: 0.2}),
+            inputs.random_mesh(4, 4, seed=seed + 1),
+            inputs.sod(3, 4),
+            inputs.random_mesh(2, 5, seed=seed + 2, gamma=5.0 / 3.0),
+            inputs.random_mesh(3, 6, seed=seed + 3)]
+
+
+@pytest.mark.parametrize("precision", [8, 4])
+def test_members_equal_the_same_mesh_alone(precision):
+    from paper_2607_20704_gb300 import amr
+    probs = _mixed(31)
+    b = amr.Mesh.batch(probs, precision=precision)
+    assert b.info()["n_members"] == len(probs)
+    b.advance(3, sync=True)
+    dts = b.member_dt()
+    for q, pr in enumerate(probs):
+        alone = amr.Mesh(*pr.mesh_args(), **pr.params(), precision=precision)
+        dt = alone.advance(3, sync=True)
+        assert dts[q] == dt, (q, dts[q], dt)
+        b.select(q)
+        for l in alone.levels():
+            ka, Ua = alone.read(l)
+            kb, Ub = b.read(l)
+            assert np.array_equal(ka, kb)
+            assert np.array_equal(Ua, Ub), (q, l)
+        alone.close()
+
+
+def test_members_match_their_oracles():
+    import oracle
+    from paper_2607_20704_gb300 import amr
+    probs = _mixed(41)
+    b = amr.Mesh.batch(probs)
+    orcs = [oracle.Mesh(*pr.mesh_args(), **pr.params()) for pr in probs]
+    for _ in range(2):
+        b.advance(1, sync=True)
+        for o in orcs:
+            o.advance(1)
+    for q, o in enumerate(orcs):
+        b.select(q)
+        compare_all(b, o, 1e-11)
+        # index of each member against its own oracle, bit for bit
+        for l in o.levels():
+            nbg, spg = b.read_index(l)
+            assert np.array_equal(nbg, o.read_nbr(l))
+            assert np.array_equal(spg, o.read_split(l))
+            assert np.array_equal(b.read_cache(l)[0], o.read_cache(l))
+
+
+def test_member_level_steps_match():
+    """amr_step_level advances the level of every member with one dt."""
+    import oracle
+    from paper_2607_20704_gb300 import amr
+    probs = [inputs.random_mesh(3, 5, seed=51), inputs.random_mesh(3, 4, seed=52)]
+    b = amr.Mesh.batch(probs)
+    orcs = [oracle.Mesh(*pr.mesh_args(), **pr.params()) for pr in probs]
+    dt = min(o.cfl_dt() for o in orcs) * 0.25
+    for l in (5, 4, 3):
+        b.step_level(l, dt)
+        for o in orcs:
+            if o.num_octs(l):
+                o.step_level(l, dt)
+    for q, o in enumerate(orcs):
+        b.select(q)
+        compare_all(b, o, 1e-11)
+
+
+def test_ensemble_shape_and_lookup():
+    """The seeded ensemble generator's meshes load as one batch; lookups
+    resolve within the selected member only."""
+    from paper_2607_20704_gb300 import amr
+    probs = inputs.batched(24, seed=11, max_extra=2)
+    b = amr.Mesh.batch(probs)
+    inf = b.info()
+    assert inf["n_members"] == 24
+    assert inf["n_oct"] == sum(p.n_oct for p in probs)
+    b.advance(2, sync=True)
+    for q in (0, 7, 23):
+        b.select(q)
+        keys = np.concatenate([b.read(l)[0] for l in b.levels()])
+        idx = b.lookup(keys)
+        assert np.array_equal(idx, np.arange(len(keys)))
