@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 512-mesh batched ensemble measurement")
+    ap.add_argument("--batched-members", type=int, default=512)
     ap.add_argument("--profile-level", type=int, default=0,
                     help="profiling mode: build the mesh and run one eager level step of this "
                          "level (one launch of each level-step kernel), then exit")
@@ -112,33 +115,59 @@ class ClockSampler:
 
 
 # -- roofline bookkeeping -----------------------------------------------------------
-def kernel_traffic(info, levelmin, w):
-    """Algorithmic bytes of one coarse step per kernel: each kernel's inputs
-    read once and outputs written once (w = bytes per word).
-      prim     U in, W out                      10 w per real+ghost cell
-      predict  W in, (W*, dW) out               25 w per real+ghost cell
-      flux     (W*, dW) in, F out               35 w per real+ghost cell
-      update   F in (15 w), U in/out, reflux slot  25 w + 4 B per real cell
-      prolong  7 source cells in, 8 ghosts out  75 w per ghost oct
-      reflux   24 slots in, R in/out           130 w per ghost oct
-      restrict 8 children in, father out        45 w per real oct (l > lmin)
-    """
-    out = {k: 0.0 for k in ("prim", "predict", "flux", "update", "prolong", "reflux", "restrict")}
+def kernel_units(info_levels, levelmin):
+    """Per kernel: units processed in one coarse step (each level l runs
+    2^(l-levelmin) times): local cells (real + ghost), real cells, ghost
+    octs, real octs above levelmin."""
+    loc = real = ghost = fine = 0
     for l in range(levelmin, 16):
-        n, nc = info["level_octs"][l], info["level_cache"][l]
+        n, nc = info_levels["level_octs"][l], info_levels["level_cache"][l]
         if not n:
             continue
         reps = 2 ** (l - levelmin)
-        cells = 8 * (n + nc)
-        out["prim"] += reps * cells * 10 * w
-        out["predict"] += reps * cells * 25 * w
-        out["flux"] += reps * cells * 35 * w
-        out["update"] += reps * 8 * n * (25 * w + 4)
-        out["prolong"] += reps * nc * 75 * w
-        out["reflux"] += reps * nc * 130 * w
+        loc += reps * 8 * (n + nc)
+        real += reps * 8 * n
+        ghost += reps * nc
         if l > levelmin:
-            out["restrict"] += reps * n * 45 * w
+            fine += reps * n
+    return loc, real, ghost, fine
+
+
+def kernel_traffic(info, levelmin, w, fused):
+    """Algorithmic bytes of one coarse step per kernel: its inputs read once
+    and its outputs written once (w = bytes per word).
+      FP64 kernels (one pass each):
+      prim        U in, W out                       10 w per real+ghost cell
+      predict     W in, (W*, dW) out                25 w per real+ghost cell
+      flux        (W*, dW) in, three fluxes out     35 w per real+ghost cell
+      update      fluxes in (15 w), U in/out        25 w + 4 B per real cell
+      FP32 kernels (fused):
+      predict     U in, (W*, dW) out                25 w per real+ghost cell
+      flux        (W*, dW) in (20 w per real+ghost cell), U in/out + slot
+                  index (10 w + 4 B per real cell)
+      both:
+      prolong     7 sources in, 8 ghosts out        75 w per ghost oct
+      reflux_restrict  24 slots + R in/out per ghost oct (130 w), 8 children
+                  in + father out per real oct above levelmin (45 w)
+    """
+    loc, real, ghost, fine = kernel_units(info, levelmin)
+    out = {"prolong": ghost * 75 * w, "reflux_restrict": ghost * 130 * w + fine * 45 * w}
+    if fused:
+        out["predict"] = loc * 25 * w
+        out["flux"] = loc * 20 * w + real * (10 * w + 4)
+    else:
+        out["prim"] = loc * 10 * w
+        out["predict"] = loc * 25 * w
+        out["flux"] = loc * 35 * w
+        out["update"] = real * (25 * w + 4)
     return out
+
+
+# FP64 flops (2 per FMA) per real cell of the FP64 flux kernel (three HLLC
+# faces), and DRAM bytes per cell of the flux kernels, from one ncu capture
+# of the level-7 launch of the benchmark mesh (profiles/flux_sedov_level7.md)
+FLUX_FP64_FLOPS_PER_CELL = 325.5
+FLUX_DRAM_BYTES_PER_CELL = {8: 283.9, 4: 125.2}
 
 
 def load_peaks():
@@ -166,7 +195,8 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
         with torch.cuda.stream(st):
             flush_l2(flush)
     torch.cuda.synchronize(device)
-    launches0 = mesh.info()["kernel_launches"]
+    info = mesh.info()  # after the autotuner has picked tile and schedule
+    launches0 = info["kernel_launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     wall0 = time.perf_counter()
@@ -234,6 +264,41 @@ def run_e2e(prob, precision, steps, torch):
             "ms_per_step": 1e3 * dt / steps}
 
 
+def run_batched(members, steps, warmup, torch, device, flush):
+    """Leaf cell-updates/s of the seeded ensemble of independent Sod/Sedov
+    meshes, all advanced by the same launches (one handle), FP64 and FP32."""
+    from paper_2607_20704_gb300 import amr
+    out = {"members": len(members), "octs": int(sum(p.n_oct for p in members)),
+           "leaf_cells": int(sum(p.leaf_cells() for p in members))}
+    for prec, name in ((8, "fp64"), (4, "fp32")):
+        b = amr.Mesh.batch(members, precision=prec)
+        info = b.info()
+        upd = int(info["work_per_step"])
+        st = b.stream
+        b.advance(warmup)
+        torch.cuda.synchronize(device)
+        info = b.info()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        l0 = info["kernel_launches"]
+        for e0, e1 in ev:
+            e0.record(st)
+            b.advance(1)
+            e1.record(st)
+            with torch.cuda.stream(st):
+                flush_l2(flush)
+        torch.cuda.synchronize(device)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        info = b.info()
+        out[name] = {"value": upd * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "cell_updates_per_step": upd, "phases": info["phases"],
+                     "tile": info["tile"], "schedule": "persistent" if info["schedule"] else "one tile per block",
+                     "gpu_launches": info["kernel_launches"] - l0,
+                     "device_gb": round(info["device_bytes"] / 1e9, 2)}
+        b.close()
+    return out
+
+
 def cpu_baseline(prob, nsteps):
     import oracle
     m = oracle.Mesh(*prob.mesh_args(), **prob.params())
@@ -268,27 +333,47 @@ def fp64_peak(torch, device):
     return 2 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def roofline(res, prec, levelmin, peak_gbs, peak_src):
+def roofline(res, prec, levelmin, peak_gbs, peak_src, fp64_tflops=None):
+    """Roofline object of the dominant kernel: achieved = its algorithmic
+    bytes (FP32) or FP64 flops (FP64: the flux kernel is bound by the FP64
+    pipe) per launch / its average CUDA-event launch time."""
     w = WORD[prec]
-    traffic = kernel_traffic(res["info"], levelmin, w)
+    traffic = kernel_traffic(res["info"], levelmin, w, fused=(prec == 4))
     kt = res.get("kernels", {})
     if not kt:
         return None, None
-    top = max(kt.items(), key=lambda kv: kv[1][0])
-    name, (ms_tot, n_launch) = top
-    if name not in traffic:
-        return None, None
-    steps = res["steps"]
-    bytes_per_launch = traffic[name] * steps / n_launch
-    avg_ms = ms_tot / n_launch
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     tot = sum(v[0] for v in kt.values())
     table = {k: {"ms": round(v[0], 4), "launches": v[1], "share": round(v[0] / tot, 4)}
              for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
-    return ({"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak_gbs,
-             "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": None,
-             "peak_source": peak_src, "avg_launch_us": round(1e3 * avg_ms, 3),
-             "algorithmic_bytes_per_launch": int(bytes_per_launch)}, table)
+    name, (ms_tot, n_launch) = max(kt.items(), key=lambda kv: kv[1][0])
+    if name not in traffic:
+        return None, table
+    steps = res["steps"]
+    avg_s = ms_tot / n_launch * 1e-3
+    bytes_per_launch = traffic[name] * steps / n_launch
+    loc, real, _, _ = kernel_units(res["info"], levelmin)
+    cells_per_launch = (real if prec == 8 else loc) * steps / n_launch
+    hbm = {"bound": "hbm", "achieved": round(bytes_per_launch / avg_s / 1e9, 1), "peak": peak_gbs,
+           "unit": "GB/s", "frac": round(bytes_per_launch / avg_s / 1e9 / peak_gbs, 4),
+           "algorithmic_bytes_per_launch": int(bytes_per_launch), "peak_source": peak_src}
+    traffic_launch = None
+    if name == "flux":
+        real_per_launch = real * steps / n_launch
+        traffic_launch = int(FLUX_DRAM_BYTES_PER_CELL[prec] * real_per_launch)
+    hbm["traffic"] = traffic_launch
+    if prec == 8 and name == "flux" and fp64_tflops:
+        flops = FLUX_FP64_FLOPS_PER_CELL * cells_per_launch
+        ach = flops / avg_s / 1e12
+        rl = {"kernel": name, "bound": "alu", "achieved": round(ach, 4), "peak": fp64_tflops,
+              "unit": "TFLOP/s", "frac": round(ach / fp64_tflops, 4), "traffic": traffic_launch,
+              "peak_source": "measured: cuBLAS DGEMM 4096^3 in this run (FP64)",
+              "flops_per_launch": int(flops), "avg_launch_us": round(avg_s * 1e6, 3),
+              "hbm_view": hbm}
+    else:
+        rl = dict(hbm)
+        rl["kernel"] = name
+        rl["avg_launch_us"] = round(avg_s * 1e6, 3)
+    return rl, table
 
 
 def main():
@@ -359,6 +444,11 @@ def main():
         other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
         other["steps"] = args.steps
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
+        batched = None
+        if not args.no_batched:
+            ens = inputs.batched(args.batched_members, seed=11)
+            batched = run_batched(ens, min(args.steps, 5), 2, torch, device, flush)
+            del ens
     clocks = clk.summary()
 
     ms = main_res["ms"]
@@ -368,8 +458,12 @@ def main():
         ms = float(t.item())
     upd = main_res["updates_per_step"]
     value = upd * args.steps * world / (ms * 1e-3)
-    rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src)
-    rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src)
+    try:
+        dgemm = round(fp64_peak(torch, device), 4)
+    except Exception:
+        dgemm = None
+    rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src, dgemm)
+    rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src, dgemm)
     step_bytes = 2 * 5 * WORD[prec_main]
     line = {
         "metric": "leaf cell-updates/s",
@@ -397,6 +491,7 @@ def main():
                           "bytes_per_cell_update": step_bytes},
         "kernels": table,
         "gpu_launches": main_res["launches"],
+        "autotuned": {"tile": main_res["info"].get("tile"), "schedule": main_res["info"].get("schedule")},
         "clocks": clocks,
         "e2e": e2e,
         ("fp32" if prec_other == 4 else "fp64"): {
@@ -406,10 +501,9 @@ def main():
             "step_roofline_frac": round(upd * args.steps / (other["ms"] * 1e-3)
                                         * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)},
     }
-    try:
-        line["fp64_dgemm_tflops"] = round(fp64_peak(torch, device), 3)
-    except Exception:
-        line["fp64_dgemm_tflops"] = None
+    if batched is not None:
+        line["batched"] = batched
+    line["fp64_dgemm_tflops"] = dgemm
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_steps)
     if world > 1:

@@ -79,11 +79,16 @@ typedef struct {
   amr_alloc_fn alloc;       /* NULL: cudaMallocAsync on the stream */
   amr_free_fn free;
   void *alloc_user;
+  int tile;                 /* cells (threads) per work tile: 128, 256 or 512;
+                               0: autotune at the first amr_advance (default) */
+  int schedule;             /* 1: persistent grids sized by occupancy x SMs;
+                               0: one tile per block; -1: autotune (default) */
 } amr_params;
 
 /* Fills p with the defaults: levelmin = levelmax = 1, gamma = 1.4, cfl = 0.8,
  * smallr = smallc = 1e-10, precision 8, reflux 1, reindex_every_step 1,
- * use_graphs 1, no budget, NULL stream and allocator. */
+ * use_graphs 1, no budget, NULL stream and allocator, tile 0 and schedule -1
+ * (both picked by the autotuner). */
 void amr_params_default(amr_params *p);
 
 /*
@@ -179,7 +184,10 @@ amr_status amr_step_level(amr_handle h, int level, double dt);
  * twice when level l+1 holds octs and then amr_step_level(l, dt).  No host
  * synchronisation inside; with use_graphs the coarse step is one graph
  * launch.  If dt_last is not NULL the call synchronises and stores the last
- * coarse dt there.
+ * coarse dt there.  When the tile size or schedule is left to the autotuner,
+ * the first call times each candidate on full coarse steps from a snapshot of
+ * the state, restores the snapshot, and keeps the fastest (synchronous, once
+ * per handle; the results are the same for every candidate).
  */
 amr_status amr_advance(amr_handle h, int n_coarse_steps, double *dt_last);
 
@@ -242,6 +250,7 @@ typedef struct {
   int precision;
   int n_members, member;      /* members of the handle; the selected one */
   int phases;                 /* level-step phases of one coarse step */
+  int tile, schedule;         /* work-tile size and schedule in use */
 } amr_info;
 
 /* Counts of the mesh and of the work done so far. */

@@ -37,7 +37,8 @@ class amr_params(C.Structure):
                 ("precision", C.c_int), ("reflux", C.c_int),
                 ("reindex_every_step", C.c_int), ("use_graphs", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("tile", C.c_int), ("schedule", C.c_int)]
 
 
 class amr_info(C.Structure):
@@ -48,7 +49,7 @@ class amr_info(C.Structure):
                 ("graph_launches", C.c_int64), ("hash_capacity", C.c_int64),
                 ("work_per_step", C.c_int64),
                 ("precision", C.c_int), ("n_members", C.c_int), ("member", C.c_int),
-                ("phases", C.c_int)]
+                ("phases", C.c_int), ("tile", C.c_int), ("schedule", C.c_int)]
 
 
 class amr_member(C.Structure):
@@ -182,7 +183,8 @@ class Mesh:
     def __init__(self, level=None, i=None, j=None, k=None, U=None, *, levelmin=1, levelmax=1,
                  gamma=1.4, cfl=0.8, smallr=1e-10, smallc=1e-10, precision=8, reflux=True,
                  reindex_every_step=True, use_graphs=True, hbm_budget_bytes=0,
-                 hilbert_key=None, allocator="torch", stream=None, members=None):
+                 hilbert_key=None, allocator="torch", stream=None, members=None, tile=0,
+                 schedule=-1):
         torch = _torch()
         L = load()
         p = amr_params()
@@ -194,6 +196,7 @@ class Mesh:
         p.reindex_every_step = int(bool(reindex_every_step))
         p.use_graphs = int(bool(use_graphs))
         p.hbm_budget_bytes = int(hbm_budget_bytes)
+        p.tile, p.schedule = int(tile), int(schedule)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         p.stream = C.c_void_p(self.stream.cuda_stream)
         if allocator == "torch":
@@ -368,7 +371,8 @@ class Mesh:
             "kernel_launches": inf.kernel_launches, "graph_launches": inf.graph_launches,
             "hash_capacity": inf.hash_capacity, "precision": inf.precision,
             "work_per_step": inf.work_per_step, "n_members": inf.n_members,
-            "member": inf.member, "phases": inf.phases,
+            "member": inf.member, "phases": inf.phases, "tile": inf.tile,
+            "schedule": inf.schedule,
         }
 
     def set_timing(self, on: bool):

@@ -170,6 +170,9 @@ struct amr_mesh {
   std::vector<SegList> phases;
   SegList level_list[kMaxLev + 1], restrict_list[kMaxLev + 1], cfl_list;
   int tile_size = 256;
+  bool persistent = true;
+  bool tuned = false;
+  std::vector<std::pair<const void *, int>> occ;  // (kernel, blocks per SM) at tile_size
 
   // state and scratch
   void *U = nullptr, *Rc = nullptr;
@@ -501,13 +504,21 @@ static void run_list(amr_mesh *h, int kid, void (*kern)(StepArgs<T>), StepArgs<T
   if (L.ntile[dom] == 0) return;
   a.tiles = h->tiles + L.tile0[dom];
   a.ntiles = L.ntile[dom];
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, h->tile_size, 0) != cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
+  int grid = a.ntiles;
+  if (h->persistent) {
+    int per_sm = 0;
+    for (auto &o : h->occ)
+      if (o.first == (const void *)kern) per_sm = o.second;
+    if (per_sm == 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, h->tile_size, 0) != cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      h->occ.push_back({(const void *)kern, per_sm});
+    }
+    grid = std::min(a.ntiles, per_sm * h->sm_count);
   }
-  const int grid = std::min(a.ntiles, per_sm * h->sm_count);
   launch(h, kid, kern, dim3(unsigned(grid)), dim3(unsigned(h->tile_size)), a);
 }
 
@@ -641,6 +652,8 @@ static amr_status reindex(amr_mesh *h) {
 // ---------------------------------------------------------------------------
 extern "C" void amr_params_default(amr_params *p) {
   std::memset(p, 0, sizeof *p);
+  p->tile = 0;
+  p->schedule = -1;
   p->levelmin = 1;
   p->levelmax = 1;
   p->gamma = 1.4;
@@ -996,6 +1009,12 @@ extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
   h->p = *p;
   h->M = n_members;
   h->mem.resize(n_members);
+  if (p->tile != 0 && p->tile != 128 && p->tile != 256 && p->tile != 512) {
+    delete h;
+    return fail(AMR_EINVAL, "amr_create: tile must be 0, 128, 256 or 512");
+  }
+  h->tile_size = p->tile ? p->tile : 256;
+  h->persistent = p->schedule != 0;
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count < 1) h->sm_count = 1;
@@ -1084,9 +1103,76 @@ static void coarse_step(amr_mesh *h) {
   for (auto &L : h->phases) step_segments(h, L, true, 0.0);
 }
 
+static void coarse_step(amr_mesh *h);
+
+// Rebuild the tile lists for another tile size (segments and scratch do not
+// depend on it).
+static amr_status set_tile(amr_mesh *h, int tile) {
+  if (tile == h->tile_size && h->tiles) return AMR_OK;
+  h->tile_size = tile;
+  h->occ.clear();
+  build_lists(h);
+  dev_free(h, h->segs);
+  dev_free(h, h->tiles);
+  h->segs = nullptr;
+  h->tiles = nullptr;
+  AMR_TRY(upload(h, &h->segs, h->segs_h));
+  AMR_TRY(upload(h, &h->tiles, h->tiles_h));
+  return AMR_OK;
+}
+
+// Time candidate (tile, schedule) pairs on full coarse steps from a snapshot
+// of the state; restore the snapshot; keep the fastest.
+static amr_status autotune(amr_mesh *h) {
+  h->tuned = true;
+  std::vector<int> tiles = h->p.tile ? std::vector<int>{h->p.tile} : std::vector<int>{128, 256, 512};
+  std::vector<int> scheds = h->p.schedule >= 0 ? std::vector<int>{h->p.schedule} : std::vector<int>{1, 0};
+  if (tiles.size() * scheds.size() == 1) {
+    h->persistent = scheds[0] == 1;
+    return set_tile(h, tiles[0]);
+  }
+  const size_t ub = h->elem() * 5 * size_t(h->S), rb = h->elem() * 5 * size_t(h->NC > 0 ? h->NC : 1);
+  void *su = nullptr, *sr = nullptr;
+  AMR_TRY(dev_alloc(h, &su, ub));
+  AMR_TRY(dev_alloc(h, &sr, rb));
+  CUDA_TRY(cudaMemcpyAsync(su, h->U, ub, cudaMemcpyDeviceToDevice, h->s));
+  CUDA_TRY(cudaMemcpyAsync(sr, h->Rc, rb, cudaMemcpyDeviceToDevice, h->s));
+  cudaEvent_t e0 = take_event(h), e1 = take_event(h);
+  float best = 1e30f;
+  int best_tile = 256, best_sched = 1;
+  for (int t : tiles)
+    for (int sc : scheds) {
+      AMR_TRY(set_tile(h, t));
+      h->persistent = sc == 1;
+      coarse_step(h);  // warm-up
+      cudaEventRecord(e0, h->s);
+      coarse_step(h);
+      coarse_step(h);
+      cudaEventRecord(e1, h->s);
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_tile = t;
+        best_sched = sc;
+      }
+      CUDA_TRY(cudaMemcpyAsync(h->U, su, ub, cudaMemcpyDeviceToDevice, h->s));
+      CUDA_TRY(cudaMemcpyAsync(h->Rc, sr, rb, cudaMemcpyDeviceToDevice, h->s));
+    }
+  h->event_pool.push_back(e0);
+  h->event_pool.push_back(e1);
+  AMR_TRY(set_tile(h, best_tile));
+  h->persistent = best_sched == 1;
+  dev_free(h, su);
+  dev_free(h, sr);
+  return check_device(h, "amr_advance (autotune)");
+}
+
 extern "C" amr_status amr_advance(amr_handle h, int n, double *dt_last) {
   if (!h) return fail(AMR_EINVAL, "amr_advance: NULL handle");
   if (n < 0) return fail(AMR_EINVAL, "amr_advance: n must be >= 0");
+  if (!h->tuned && n > 0) AMR_TRY(autotune(h));
   const bool graphs = h->p.use_graphs && !h->timing;
   if (graphs && !h->graph && n > 0) {
     h->capturing = true;
@@ -1340,6 +1426,8 @@ extern "C" amr_status amr_get_info(amr_handle h, amr_info *info) {
   info->n_members = h->M;
   info->member = h->sel;
   info->phases = int(h->phases.size());
+  info->tile = h->tile_size;
+  info->schedule = h->persistent ? 1 : 0;
   return AMR_OK;
 }
 

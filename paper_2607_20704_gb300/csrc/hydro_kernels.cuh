@@ -71,6 +71,18 @@ __device__ __forceinline__ float rcp(float x) {
   return r;
 }
 
+// 1/sqrt(x) by Newton-Raphson for the reciprocal square root
+// (y <- y (3/2 - x/2 y^2)) from the hardware approximation; two steps reach
+// double precision.  x is a positive normal number here (gamma p rho).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double hx = 0.5 * x;
+  y = y * fma(-hx, y * y, 1.5);
+  return y * fma(-hx, y * y, 1.5);
+}
+__device__ __forceinline__ float rsqrt_nr(float x) { return rsqrtf(x); }
+
 // ---------------------------------------------------------------------------
 // segment context: what a thread needs to know about its (member, level)
 // ---------------------------------------------------------------------------
@@ -303,8 +315,9 @@ __global__ void k_predict_u(StepArgs<T> a) {
 // S_L = min(u) - max(c), S_R = max(u) + max(c); star speed and pressure from
 // the two-wave HLL jump conditions; physical flux of the state sampled at
 // x/t = 0 (Toro's HLLC); transverse velocities from the upwind side.
-// max(c) takes one square root: c^2 = gamma p / rho is compared across the
-// face by cross-multiplication and only the larger is divided and rooted.
+// max(c) takes one reciprocal square root: c^2 = gamma p / rho is compared
+// across the face by cross-multiplication, and for the larger side
+// c = gamma p / sqrt(gamma p rho).
 // ---------------------------------------------------------------------------
 template <int D, class T>
 __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T igm1, T (&F)[5]) {
@@ -315,7 +328,8 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   const T er = pr * igm1 + T(0.5) * rr * ((qR[1] * qR[1] + qR[2] * qR[2]) + qR[3] * qR[3]);
   const T gpl = g * pl, gpr = g * pr;
   const bool lbig = gpl * rr > gpr * rl;
-  const T cmax = vsqrt((lbig ? gpl : gpr) * rcp(lbig ? rl : rr));
+  const T gpk = lbig ? gpl : gpr;
+  const T cmax = gpk * rsqrt_nr(gpk * (lbig ? rl : rr));
   const T sl = vmin(ul, ur) - cmax;
   const T sr = vmax(ul, ur) + cmax;
   const T rcl = rl * (ul - sl), rcr = rr * (sr - ur);
@@ -547,14 +561,40 @@ __global__ void k_reflux_restrict(StepArgs<T> a) {
 // bits); then one thread per member computes its dt.
 // ---------------------------------------------------------------------------
 template <class T>
+__device__ __forceinline__ void cfl_flush(const CflArgs &a, double s, int seg, double *wmax) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+  if (lane == 0) wmax[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < int(blockDim.x >> 5) ? wmax[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+    if (lane == 0 && s > 0.0) {
+      const Seg sg = a.segs[seg];
+      atomicMax(a.smax + 16 * sg.member + sg.level, (unsigned long long)__double_as_longlong(s));
+    }
+  }
+  __syncthreads();
+}
+
+// Each block keeps a running maximum per thread while its tiles stay in one
+// segment and reduces it (one atomicMax) when the segment changes.
+template <class T>
 __global__ void k_cfl(CflArgs a, const T *U) {
   __shared__ double wmax[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double s = 0.0;
+  int cur = -1;
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
     const Tile td = a.tiles[ti];
+    if (td.seg != cur) {
+      if (cur >= 0) cfl_flush<T>(a, s, cur, wmax);
+      s = 0.0;
+      cur = td.seg;
+    }
     const Seg sg = a.segs[td.seg];
     const int t = td.start + threadIdx.x;
-    double s = 0.0;
     if (t < 8 * sg.nl && !((__ldg(a.son + sg.lo + (t >> 3)) >> (t & 7)) & 1u)) {
       const T g = T(a.mgamma[sg.member]), smallr = T(a.msmallr[sg.member]),
               smallp = T(a.msmallp[sg.member]);
@@ -571,21 +611,10 @@ __global__ void k_cfl(CflArgs a, const T *U) {
       if (!isfinite(st) || !isfinite(u0 + u1 + u2 + u3 + u4))
         atomicOr(a.err, kErrNaN);
       else
-        s = double(st);
+        s = fmax(s, double(st));
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
-    if (lane == 0) wmax[warp] = s;
-    __syncthreads();
-    if (warp == 0) {
-      s = lane < int(blockDim.x >> 5) ? wmax[lane] : 0.0;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s = fmax(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
-      if (lane == 0 && s > 0.0)
-        atomicMax(a.smax + 16 * sg.member + sg.level, (unsigned long long)__double_as_longlong(s));
-    }
-    __syncthreads();
   }
+  if (cur >= 0) cfl_flush<T>(a, s, cur, wmax);
 }
 
 __global__ void k_dt(CflArgs a) {

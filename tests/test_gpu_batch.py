@@ -105,3 +105,28 @@ def test_ensemble_shape_and_lookup():
         keys = np.concatenate([b.read(l)[0] for l in b.levels()])
         idx = b.lookup(keys)
         assert np.array_equal(idx, np.arange(len(keys)))
+
+
+def test_tile_size_and_schedule_do_not_change_results():
+    """The autotuner's choices (tile size, persistent or one-tile-per-block
+    grids) and its snapshot/restore leave every result bit-identical."""
+    from paper_2607_20704_gb300 import amr
+    probs = _mixed(61)
+    outs = []
+    for tile, sched in ((128, 0), (512, 1), (0, -1)):
+        b = amr.Mesh.batch(probs, tile=tile, schedule=sched)
+        b.advance(2, sync=True)
+        inf = b.info()
+        if tile:
+            assert (inf["tile"], inf["schedule"]) == (tile, sched)
+        else:
+            assert inf["tile"] in (128, 256, 512) and inf["schedule"] in (0, 1)
+        res = []
+        for q in range(len(probs)):
+            b.select(q)
+            res += [b.read(l)[1] for l in b.levels()]
+        outs.append(res)
+        b.close()
+    for other in outs[1:]:
+        for a, c in zip(outs[0], other):
+            assert np.array_equal(a, c)
