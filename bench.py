@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-mesh batched ensemble measurement")
     ap.add_argument("--batched-members", type=int, default=512)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
+    ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--profile-level", type=int, default=0,
                     help="profiling mode: build the mesh and run one eager level step of this "
                          "level (one launch of each level-step kernel), then exit")
@@ -299,6 +301,44 @@ def run_batched(members, steps, warmup, torch, device, flush):
     return out
 
 
+def run_serving(n_requests, rates, torch):
+    """Serving loop under Poisson arrivals at each rate of the sweep: p50/p99
+    latency (submit -> result on the host) and sustained leaf cell-updates/s
+    (completed work / first submission -> last completion)."""
+    import random
+    from paper_2607_20704_gb300 import amr, inputs
+    probs, reqs = inputs.serving_requests(n_requests, seed=13)
+    # warm-up: one small request of each precision
+    srv = amr.Server()
+    for prec in (4, 8):
+        srv.submit(probs[min(range(len(probs)), key=lambda t: probs[t].n_oct)], 2, prec)
+    srv.wait(-1, 600.0)
+    srv.close()
+    out = {"requests": n_requests, "pool_meshes": len(probs),
+           "pool_octs": int(sum(p.n_oct for p in probs)), "budget_gb": 120, "points": []}
+    for rate in rates:
+        rng = random.Random(13)
+        srv = amr.Server()
+        t0 = time.perf_counter()
+        next_t = 0.0
+        for pi, steps, prec in reqs:
+            next_t += rng.expovariate(rate)
+            dt = t0 + next_t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            srv.submit(probs[pi], steps, prec)
+        srv.wait(-1, 1800.0)
+        st = srv.stats()
+        srv.close()
+        out["points"].append({"arrival_rate_per_s": rate, "completed": st["completed"],
+                              "failed": st["failed"], "p50_ms": round(st["latency_p50_ms"], 2),
+                              "p99_ms": round(st["latency_p99_ms"], 2),
+                              "queue_p50_ms": round(st["queue_p50_ms"], 2),
+                              "cell_updates_per_s": st["cell_updates"] / max(st["span_s"], 1e-9),
+                              "span_s": round(st["span_s"], 3)})
+    return out
+
+
 def cpu_baseline(prob, nsteps):
     import oracle
     m = oracle.Mesh(*prob.mesh_args(), **prob.params())
@@ -444,6 +484,9 @@ def main():
         other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
         other["steps"] = args.steps
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
+        serving = None
+        if not args.no_serving:
+            serving = run_serving(args.serving_requests, (10.0, 40.0, 160.0), torch)
         batched = None
         if not args.no_batched:
             ens = inputs.batched(args.batched_members, seed=11)
@@ -503,6 +546,8 @@ def main():
     }
     if batched is not None:
         line["batched"] = batched
+    if serving is not None:
+        line["serving"] = serving
     line["fp64_dgemm_tflops"] = dgemm
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_steps)

@@ -146,6 +146,17 @@ amr_status amr_create_batch(const amr_params *p, int n_members, const amr_member
  * to (default 0). */
 amr_status amr_select_member(amr_handle h, int member);
 
+/* Coarse steps each member still takes: amr_advance skips members whose
+ * count is 0 (their state and dt stay as they are) and counts the others
+ * down; -1 means unlimited (the default).  steps holds n = n_members values.
+ * Synchronous. */
+amr_status amr_set_member_steps(amr_handle h, const int32_t *steps, int n);
+
+/* Per-member error flags (bit 0: a leaf state was not finite), copied into
+ * errs[0..n_members), after waiting for the handle's stream; also clears the
+ * handle-wide error that the next synchronising call would report. */
+amr_status amr_member_errors(amr_handle h, int32_t *errs, int n);
+
 /* The last coarse time step of every member (from amr_cfl_dt or
  * amr_advance), copied into dt_out[0..n_members) (synchronous). */
 amr_status amr_member_dt(amr_handle h, double *dt_out, int n);
@@ -292,6 +303,60 @@ const char *amr_kernel_name(int t);
 amr_status amr_cfl_dt_static(const double *U, int64_t n_cells, int64_t stride, int level,
                              double gamma, double cfl, double smallr, double smallc,
                              double *dt_out, void *stream);
+
+/* ---- serving ------------------------------------------------------------ */
+/*
+ * A serving loop for many independent solves (the paper has no serving
+ * layer; this is the batching of its level advance across requests).
+ * amr_server_submit queues a request (its arrays are copied) and returns at
+ * once.  A scheduler thread admits queued requests in arrival order whenever
+ * the device budget and the wave slots allow; the requests admitted together
+ * form a wave -- one batched handle (amr_create_batch) on its own stream, in
+ * which each member stops after its own number of coarse steps
+ * (amr_set_member_steps).  Waves admitted while others run overlap with them
+ * on the GPU.  A finished request's final state is copied to host memory;
+ * a wave whose members are all finished frees its device memory.  A
+ * request's result is bit-identical to the same solve in a handle of its own.
+ */
+typedef struct amr_server *amr_server_t;
+
+typedef struct {
+  size_t hbm_budget_bytes;  /* device memory the waves may hold; 0: 120e9 */
+  int max_waves;            /* waves in flight; <= 0: 8 */
+  int max_wave_members;     /* requests per wave; <= 0: 256 */
+  int device;               /* CUDA device; -1: the caller's current device */
+  int tile, schedule;       /* amr_params.tile / .schedule of the waves;
+                               0 and 0: 128-cell tiles, one tile per block */
+} amr_server_params;
+
+typedef struct {
+  amr_member mesh;          /* the mesh, as for amr_create_batch */
+  int n_coarse_steps;       /* >= 1 */
+  int precision;            /* 4 or 8 */
+} amr_request;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed, queued, running_waves;
+  double latency_p50_ms, latency_p99_ms, latency_mean_ms;  /* submit -> result */
+  double queue_p50_ms;      /* submit -> admission */
+  double cell_updates;      /* leaf cell-updates of the completed requests */
+  double span_s;            /* first submission -> last completion */
+  int64_t device_bytes;     /* held by the waves in flight */
+} amr_server_stats;
+
+amr_status amr_server_create(const amr_server_params *p, amr_server_t *out);
+amr_status amr_server_submit(amr_server_t s, const amr_request *req, int64_t *id_out);
+/* Wait until request id (or, for id < 0, every submitted request) is
+ * finished, at most timeout_s seconds (< 0: no limit); *done = 1 if so. */
+amr_status amr_server_wait(amr_server_t s, int64_t id, double timeout_s, int *done);
+/* Final state of a finished request, one level at a time, like amr_read. */
+amr_status amr_server_read(amr_server_t s, int64_t id, int level, int64_t *n_oct_out,
+                           uint64_t *keys, double *U, int64_t cap);
+/* Drop a finished request's result. */
+amr_status amr_server_release(amr_server_t s, int64_t id);
+amr_status amr_server_get_stats(amr_server_t s, amr_server_stats *st);
+/* Finish every submitted request, stop the scheduler, free everything. */
+amr_status amr_server_destroy(amr_server_t s);
 
 /* Wait for the handle's stream and report any pending device-side error. */
 amr_status amr_sync(amr_handle h);

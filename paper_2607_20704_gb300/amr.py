@@ -61,6 +61,25 @@ class amr_member(C.Structure):
                 ("hilbert_key", C.c_void_p), ("U", C.c_void_p)]
 
 
+class amr_server_params(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_waves", C.c_int),
+                ("max_wave_members", C.c_int), ("device", C.c_int), ("tile", C.c_int),
+                ("schedule", C.c_int)]
+
+
+class amr_request(C.Structure):
+    _fields_ = [("mesh", amr_member), ("n_coarse_steps", C.c_int), ("precision", C.c_int)]
+
+
+class amr_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("queued", C.c_int64), ("running_waves", C.c_int64),
+                ("latency_p50_ms", C.c_double), ("latency_p99_ms", C.c_double),
+                ("latency_mean_ms", C.c_double), ("queue_p50_ms", C.c_double),
+                ("cell_updates", C.c_double), ("span_s", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
 class AmrError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
@@ -76,7 +95,9 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_lookup", "amr_read_index", "amr_read_cache", "amr_fill_ghosts", "amr_get_info",
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
-           "amr_member_dt"]
+           "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_server_create", "amr_server_submit",
+           "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
+           "amr_server_destroy"]
 
 # fixed scratch limit of amr_cfl_dt_static (AMR_CFL_STATIC_MAX_CELLS in amr.h)
 CFL_STATIC_MAX_CELLS = 65536 * 256
@@ -120,6 +141,15 @@ def load(path: str | None = None):
             "amr_create_batch": (I, [C.POINTER(amr_params), I, C.POINTER(amr_member), C.POINTER(P)]),
             "amr_select_member": (I, [P, I]),
             "amr_member_dt": (I, [P, P, I]),
+            "amr_set_member_steps": (I, [P, P, I]),
+            "amr_member_errors": (I, [P, P, I]),
+            "amr_server_create": (I, [C.POINTER(amr_server_params), C.POINTER(P)]),
+            "amr_server_submit": (I, [P, C.POINTER(amr_request), C.POINTER(I64)]),
+            "amr_server_wait": (I, [P, I64, D, C.POINTER(I)]),
+            "amr_server_read": (I, [P, I64, I, C.POINTER(I64), P, P, I64]),
+            "amr_server_release": (I, [P, I64]),
+            "amr_server_get_stats": (I, [P, C.POINTER(amr_server_stats)]),
+            "amr_server_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -253,6 +283,18 @@ class Mesh:
         self._member = int(member)
         self.levelmin, self.levelmax = self.member_levels[int(member)]
         return self
+
+    def set_member_steps(self, steps):
+        """Coarse steps each member still takes (-1: unlimited)."""
+        st = np.ascontiguousarray(steps, dtype=np.int32)
+        _check(load().amr_set_member_steps(self._h, _ptr(st), len(st)), "amr_set_member_steps")
+
+    def member_errors(self):
+        """Per-member flags (1: a leaf state was not finite); clears the
+        handle-wide error the next synchronising call would otherwise report."""
+        out = np.zeros(self.n_members, np.int32)
+        _check(load().amr_member_errors(self._h, _ptr(out), self.n_members), "amr_member_errors")
+        return out
 
     def member_dt(self):
         out = np.zeros(self.n_members, np.float64)
@@ -435,3 +477,73 @@ def amr_cfl_dt_static(U_ptr: int, n_cells: int, stride: int, level: int, gamma: 
                                float(gamma), float(cfl), float(smallr), float(smallc),
                                C.c_void_p(dt_out_ptr), C.c_void_p(stream_ptr or None)),
            "amr_cfl_dt_static")
+
+
+class Server:
+    """Continuous-batching serving loop (wraps ``amr_server_t``)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_waves=0, max_wave_members=0, device=-1,
+                 tile=0, schedule=0):
+        _torch()
+        L = load()
+        p = amr_server_params(int(hbm_budget_bytes), int(max_waves), int(max_wave_members),
+                              int(device), int(tile), int(schedule))
+        h = C.c_void_p()
+        _check(L.amr_server_create(C.byref(p), C.byref(h)), "amr_server_create")
+        self._h = h
+        self._levels = {}
+
+    def submit(self, prob, steps: int, precision: int = 8) -> int:
+        """Queue one solve of an ``inputs.Problem`` (its arrays are copied)."""
+        lv = np.ascontiguousarray(prob.level, dtype=np.uint8)
+        ii = np.ascontiguousarray(prob.i, dtype=np.uint32)
+        jj = np.ascontiguousarray(prob.j, dtype=np.uint32)
+        kk = np.ascontiguousarray(prob.k, dtype=np.uint32)
+        uu = np.ascontiguousarray(prob.U, dtype=np.float64)
+        r = amr_request()
+        m = r.mesh
+        m.levelmin, m.levelmax = int(prob.levelmin), int(prob.levelmax)
+        m.gamma, m.cfl, m.smallr, m.smallc = float(prob.gamma), float(prob.cfl), 1e-10, 1e-10
+        m.n_oct = lv.shape[0]
+        m.level, m.i, m.j, m.k, m.U = _ptr(lv), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(uu)
+        m.hilbert_key = None
+        r.n_coarse_steps, r.precision = int(steps), int(precision)
+        rid = C.c_int64()
+        _check(load().amr_server_submit(self._h, C.byref(r), C.byref(rid)), "amr_server_submit")
+        self._levels[rid.value] = (int(prob.levelmin), int(prob.levelmax))
+        return rid.value
+
+    def wait(self, rid: int = -1, timeout: float = -1.0) -> bool:
+        done = C.c_int()
+        _check(load().amr_server_wait(self._h, int(rid), float(timeout), C.byref(done)), "amr_server_wait")
+        return bool(done.value)
+
+    def read(self, rid: int, level: int):
+        L = load()
+        n = C.c_int64()
+        _check(L.amr_server_read(self._h, int(rid), int(level), C.byref(n), None, None, 0), "amr_server_read")
+        keys = np.zeros(max(n.value, 1), np.uint64)
+        U = np.zeros((NV, 8 * max(n.value, 1)), np.float64)
+        _check(L.amr_server_read(self._h, int(rid), int(level), C.byref(n), _ptr(keys), _ptr(U),
+                                 max(n.value, 1)), "amr_server_read")
+        return keys[:n.value], U[:, :8 * n.value]
+
+    def release(self, rid: int):
+        _check(load().amr_server_release(self._h, int(rid)), "amr_server_release")
+
+    def stats(self) -> dict:
+        st = amr_server_stats()
+        _check(load().amr_server_get_stats(self._h, C.byref(st)), "amr_server_get_stats")
+        return {f: getattr(st, f) for f, _ in amr_server_stats._fields_}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().amr_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libamr.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["amr_api.cu", "amr_static.cu"]  # hydro/index kernels live in csrc/*.cuh
+SOURCES = ["amr_api.cu", "amr_static.cu", "amr_server.cu"]  # hydro/index kernels live in csrc/*.cuh
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

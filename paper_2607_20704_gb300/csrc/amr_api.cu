@@ -159,6 +159,8 @@ struct amr_mesh {
   void *mgamma_t = nullptr, *migm1_t = nullptr, *msmallr_t = nullptr, *msmallp_t = nullptr;
   double *dt_dev = nullptr, *dtdx_dev = nullptr;
   float *dtdxf_dev = nullptr;
+  int *mrem = nullptr, *mact = nullptr;  // coarse steps left; active this step
+  int *merr = nullptr;                   // error bits per member
   unsigned long long *smax = nullptr;
   int *err = nullptr;
 
@@ -493,6 +495,7 @@ static StepArgs<T> step_args(amr_mesh *h, bool device_dt, double dt) {
   a.dtdx_dev = device_dt ? h->dtdx_dev : nullptr;
   a.dtdxf_dev = device_dt ? h->dtdxf_dev : nullptr;
   a.dt_host = dt;
+  a.mact = device_dt ? h->mact : nullptr;
   a.reflux = h->p.reflux;
   return a;
 }
@@ -569,15 +572,19 @@ static CflArgs cfl_args(amr_mesh *h) {
   a.mlmin = h->mlmin;
   a.nmembers = h->M;
   a.smax = h->smax;
+  a.mrem = h->mrem;
+  a.mact = h->mact;
   a.dt_dev = h->dt_dev;
   a.dtdx_dev = h->dtdx_dev;
   a.dtdxf_dev = h->dtdxf_dev;
   a.err = h->err;
+  a.merr = h->merr;
   return a;
 }
 
-static void cfl_device(amr_mesh *h) {
+static void cfl_device(amr_mesh *h, int consume) {
   CflArgs a = cfl_args(h);
+  a.consume = consume;
   const unsigned grid = unsigned(std::min(a.ntiles, 4 * h->sm_count));
   if (grid) {
     if (h->p.precision == 4)
@@ -958,6 +965,12 @@ static amr_status create_impl(amr_mesh *h, const amr_member *members) {
   AMR_TRY(alloc_n(h, &h->dtdxf_dev, M));
   AMR_TRY(alloc_n(h, &h->smax, 16 * int64_t(M)));
   CUDA_TRY(cudaMemsetAsync(h->smax, 0, sizeof(unsigned long long) * 16 * M, h->s));
+  AMR_TRY(alloc_n(h, &h->mrem, M));
+  AMR_TRY(alloc_n(h, &h->mact, M));
+  AMR_TRY(alloc_n(h, &h->merr, M));
+  CUDA_TRY(cudaMemsetAsync(h->merr, 0, sizeof(int) * M, h->s));
+  CUDA_TRY(cudaMemsetAsync(h->mrem, 0xFF, sizeof(int) * M, h->s));  // -1: unlimited
+  CUDA_TRY(cudaMemsetAsync(h->mact, 0, sizeof(int) * M, h->s));
 
   // split cells carry the mean of their children, finest level first
   for (int l = kMaxLev; l >= 1; --l) {
@@ -1075,7 +1088,7 @@ extern "C" amr_status amr_destroy(amr_handle h) {
 // ---------------------------------------------------------------------------
 extern "C" amr_status amr_cfl_dt(amr_handle h, double *dt_out) {
   if (!h || !dt_out) return fail(AMR_EINVAL, "amr_cfl_dt: NULL argument");
-  cfl_device(h);
+  cfl_device(h, 0);
   CUDA_TRY(cudaMemcpyAsync(dt_out, h->dt_dev + h->sel, sizeof(double), cudaMemcpyDeviceToHost, h->s));
   return check_device(h, "amr_cfl_dt");
 }
@@ -1099,7 +1112,7 @@ extern "C" amr_status amr_step_level(amr_handle h, int level, double dt) {
 
 static void coarse_step(amr_mesh *h) {
   if (h->p.reindex_every_step) reindex(h);
-  cfl_device(h);
+  cfl_device(h, 1);
   for (auto &L : h->phases) step_segments(h, L, true, 0.0);
 }
 
@@ -1132,11 +1145,16 @@ static amr_status autotune(amr_mesh *h) {
     return set_tile(h, tiles[0]);
   }
   const size_t ub = h->elem() * 5 * size_t(h->S), rb = h->elem() * 5 * size_t(h->NC > 0 ? h->NC : 1);
-  void *su = nullptr, *sr = nullptr;
+  const size_t mb = sizeof(int) * size_t(h->M);
+  void *su = nullptr, *sr = nullptr, *sm = nullptr;
   AMR_TRY(dev_alloc(h, &su, ub));
   AMR_TRY(dev_alloc(h, &sr, rb));
+  AMR_TRY(dev_alloc(h, &sm, mb));
   CUDA_TRY(cudaMemcpyAsync(su, h->U, ub, cudaMemcpyDeviceToDevice, h->s));
   CUDA_TRY(cudaMemcpyAsync(sr, h->Rc, rb, cudaMemcpyDeviceToDevice, h->s));
+  CUDA_TRY(cudaMemcpyAsync(sm, h->mrem, mb, cudaMemcpyDeviceToDevice, h->s));
+  // tune with every member stepping
+  CUDA_TRY(cudaMemsetAsync(h->mrem, 0xFF, mb, h->s));
   cudaEvent_t e0 = take_event(h), e1 = take_event(h);
   float best = 1e30f;
   int best_tile = 256, best_sched = 1;
@@ -1160,12 +1178,14 @@ static amr_status autotune(amr_mesh *h) {
       CUDA_TRY(cudaMemcpyAsync(h->U, su, ub, cudaMemcpyDeviceToDevice, h->s));
       CUDA_TRY(cudaMemcpyAsync(h->Rc, sr, rb, cudaMemcpyDeviceToDevice, h->s));
     }
+  CUDA_TRY(cudaMemcpyAsync(h->mrem, sm, mb, cudaMemcpyDeviceToDevice, h->s));
   h->event_pool.push_back(e0);
   h->event_pool.push_back(e1);
   AMR_TRY(set_tile(h, best_tile));
   h->persistent = best_sched == 1;
   dev_free(h, su);
   dev_free(h, sr);
+  dev_free(h, sm);
   return check_device(h, "amr_advance (autotune)");
 }
 
@@ -1227,6 +1247,31 @@ extern "C" amr_status amr_fill_ghosts(amr_handle h, int level) {
     run_list(h, K_PROLONG, k_prolong<float>, step_args<float>(h, false, 0.0), L, DOM_GHOST5);
   else
     run_list(h, K_PROLONG, k_prolong<double>, step_args<double>(h, false, 0.0), L, DOM_GHOST5);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_set_member_steps(amr_handle h, const int32_t *steps, int n) {
+  if (!h || !steps) return fail(AMR_EINVAL, "amr_set_member_steps: NULL argument");
+  if (n != h->M) return fail(AMR_EINVAL, "amr_set_member_steps: %d values for %d members", n, h->M);
+  for (int q = 0; q < n; ++q)
+    if (steps[q] < -1) return fail(AMR_EINVAL, "amr_set_member_steps: steps must be >= -1");
+  CUDA_TRY(cudaMemcpyAsync(h->mrem, steps, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_member_errors(amr_handle h, int32_t *errs, int n) {
+  if (!h || !errs) return fail(AMR_EINVAL, "amr_member_errors: NULL argument");
+  if (n < h->M) return fail(AMR_EINVAL, "amr_member_errors: room for %d members needed", h->M);
+  CUDA_TRY(cudaMemcpyAsync(errs, h->merr, sizeof(int32_t) * h->M, cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  // the per-member bits now carry the news: clear the handle-wide word too
+  CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
+  for (int q = 0; q < h->M; ++q) {
+    int32_t v = 0;
+    if (errs[q] & kErrNaN) v |= 1;
+    errs[q] = v;
+  }
   return AMR_OK;
 }
 

@@ -1,0 +1,448 @@
+// amr_server.cu -- continuous-batching serving loop over the level-advance
+// library (include/amr.h, amr_server_*).
+//
+// Requests (one mesh, a number of coarse steps, a precision) are queued by
+// amr_server_submit.  A scheduler thread admits queued requests, in arrival
+// order, whenever the device budget and the wave slots allow: the requests
+// admitted together form a wave, one batched handle on a stream of its own,
+// in which every member stops after its own number of coarse steps (the
+// handle's per-member step counters).  Waves admitted while others run
+// overlap with them on the GPU.  Each wave keeps at most two coarse steps in
+// flight; a CUDA event per coarse step tells the scheduler when members are
+// finished, their final state is copied to host memory, and a wave whose
+// members are all finished releases its device memory for the next wave.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "amr.h"
+
+void amr_set_error_text(const char *text);
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+amr_status set_error(amr_status s, const std::string &msg) {
+  amr_set_error_text(msg.c_str());
+  return s;
+}
+
+struct Request {
+  int64_t id = 0;
+  int levelmin = 1, levelmax = 1, steps = 1, precision = 8;
+  double gamma = 1.4, cfl = 0.8, smallr = 1e-10, smallc = 1e-10;
+  std::vector<uint8_t> level;
+  std::vector<uint32_t> i, j, k;
+  std::vector<uint64_t> hk;
+  std::vector<double> U;
+  size_t est_bytes = 0;
+  double t_submit = 0, t_admit = -1, t_done = -1;
+  double work = 0;  // leaf cell-updates of the whole solve
+  bool done = false, failed = false;
+  std::string error;
+  std::vector<std::vector<uint64_t>> keys;  // final state, per level
+  std::vector<std::vector<double>> Uout;
+};
+
+struct Wave {
+  amr_handle h = nullptr;
+  cudaStream_t s = nullptr;
+  std::vector<Request *> reqs;
+  int max_steps = 0, issued = 0, completed = 0;
+  std::vector<cudaEvent_t> ev;
+  size_t bytes = 0;
+};
+
+// device bytes of a handle per oct, for admission before the handle exists
+// (state with ghosts, level-step scratch, index, hash, create-time staging)
+size_t estimate_bytes(int64_t n_oct, int precision) {
+  const size_t w = precision == 4 ? 4 : 8;
+  return size_t(n_oct) * (w * (8 * 5 * 2 + 8 * 40) + 1024) + (8u << 20);
+}
+
+}  // namespace
+
+struct amr_server {
+  amr_server_params p{};
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request *> queue;
+  std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
+  std::vector<Wave *> waves;  // scheduler thread only
+  std::thread th;
+  std::atomic<bool> stop{false};
+  int64_t next_id = 1;
+  size_t bytes_in_use = 0;
+  int64_t submitted = 0, admitted = 0, completed = 0, failed = 0;
+  double cell_updates = 0, first_submit = -1, last_done = -1;
+  std::vector<double> latencies, queue_waits;
+  std::string fatal;
+
+  void loop();
+  bool admit();
+  bool progress(Wave *w);
+  void finish_member(Wave *w, Request *r, int member);
+};
+
+bool amr_server::admit() {
+  std::vector<Request *> take;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (queue.empty() || int(waves.size()) >= p.max_waves) return false;
+    const int prec = queue.front()->precision;
+    size_t budget_left = p.hbm_budget_bytes > bytes_in_use ? p.hbm_budget_bytes - bytes_in_use : 0;
+    size_t need = 0;
+    // in arrival order: the wave takes the leading requests of one precision
+    // that fit the remaining budget
+    while (!queue.empty() && int(take.size()) < p.max_wave_members) {
+      Request *r = queue.front();
+      if (r->precision != prec || need + r->est_bytes > budget_left) break;
+      need += r->est_bytes;
+      take.push_back(r);
+      queue.pop_front();
+    }
+    if (take.empty()) return false;
+    bytes_in_use += need;
+  }
+  Wave *w = new Wave();
+  w->reqs = take;
+  for (auto *r : take) w->bytes += r->est_bytes;
+  cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking);
+  amr_params prm;
+  amr_params_default(&prm);
+  prm.precision = take[0]->precision;
+  prm.stream = w->s;
+  prm.tile = p.tile ? p.tile : 128;
+  prm.schedule = p.schedule >= 0 ? p.schedule : 0;
+  std::vector<amr_member> mem(take.size());
+  std::vector<int32_t> steps(take.size());
+  for (size_t q = 0; q < take.size(); ++q) {
+    Request *r = take[q];
+    amr_member &m = mem[q];
+    m.levelmin = r->levelmin;
+    m.levelmax = r->levelmax;
+    m.gamma = r->gamma;
+    m.cfl = r->cfl;
+    m.smallr = r->smallr;
+    m.smallc = r->smallc;
+    m.n_oct = int64_t(r->level.size());
+    m.level = r->level.data();
+    m.i = r->i.data();
+    m.j = r->j.data();
+    m.k = r->k.data();
+    m.hilbert_key = r->hk.empty() ? nullptr : r->hk.data();
+    m.U = r->U.data();
+    steps[q] = r->steps;
+    w->max_steps = std::max(w->max_steps, r->steps);
+  }
+  amr_status s = amr_create_batch(&prm, int(take.size()), mem.data(), &w->h);
+  if (s == AMR_OK) s = amr_set_member_steps(w->h, steps.data(), int(steps.size()));
+  const double t = now_s();
+  std::lock_guard<std::mutex> g(mu);
+  if (s != AMR_OK) {
+    // the requests fail with the handle's error; their budget returns
+    const std::string msg = amr_last_error();
+    for (auto *r : take) {
+      r->failed = r->done = true;
+      r->error = msg;
+      r->t_done = t;
+      ++failed;
+    }
+    bytes_in_use -= w->bytes;
+    if (w->h) amr_destroy(w->h);
+    cudaStreamDestroy(w->s);
+    delete w;
+    cv_done.notify_all();
+    return true;
+  }
+  amr_info inf;
+  amr_get_info(w->h, &inf);
+  // account the handle's real footprint instead of the estimate
+  bytes_in_use = bytes_in_use - w->bytes + size_t(inf.device_bytes);
+  w->bytes = size_t(inf.device_bytes);
+  for (size_t q = 0; q < take.size(); ++q) {
+    Request *r = take[q];
+    r->t_admit = t;
+    ++admitted;
+    queue_waits.push_back(1e3 * (t - r->t_submit));
+    amr_select_member(w->h, int(q));
+    amr_info mi;
+    amr_get_info(w->h, &mi);
+    double per_step = 0;
+    for (int l = r->levelmin; l <= 15; ++l)
+      if (mi.level_octs[l]) per_step += double(mi.level_leaf_cells[l]) * double(int64_t(1) << (l - r->levelmin));
+    r->work = per_step * r->steps;
+  }
+  waves.push_back(w);
+  return true;
+}
+
+void amr_server::finish_member(Wave *w, Request *r, int member) {
+  // a non-finite state fails its own request only
+  std::vector<int32_t> errs(w->reqs.size());
+  amr_status s = amr_member_errors(w->h, errs.data(), int(errs.size()));
+  if (s == AMR_OK && errs[member]) {
+    std::lock_guard<std::mutex> g(mu);
+    r->failed = r->done = true;
+    r->error = "non-finite state";
+    r->t_done = now_s();
+    ++failed;
+    cv_done.notify_all();
+    return;
+  }
+  amr_select_member(w->h, member);
+  std::vector<std::vector<uint64_t>> keys(16);
+  std::vector<std::vector<double>> U(16);
+  for (int l = 0; l <= 15 && s == AMR_OK; ++l) {
+    int64_t n = 0;
+    s = amr_read(w->h, l, &n, nullptr, nullptr, 0);
+    if (s != AMR_OK || n == 0) continue;
+    keys[l].resize(n);
+    U[l].resize(40 * size_t(n));
+    s = amr_read(w->h, l, &n, keys[l].data(), U[l].data(), n);
+  }
+  const double t = now_s();
+  std::lock_guard<std::mutex> g(mu);
+  r->keys = std::move(keys);
+  r->Uout = std::move(U);
+  r->t_done = t;
+  r->done = true;
+  if (s != AMR_OK) {
+    r->failed = true;
+    r->error = amr_last_error();
+    ++failed;
+  } else {
+    ++completed;
+    latencies.push_back(1e3 * (t - r->t_submit));
+    cell_updates += r->work;
+    last_done = t;
+  }
+  cv_done.notify_all();
+}
+
+// Issue coarse steps (at most two in flight), finish members whose steps are
+// done; true when the wave is finished and can be dropped.
+bool amr_server::progress(Wave *w) {
+  while (w->completed < int(w->ev.size()) && cudaEventQuery(w->ev[w->completed]) == cudaSuccess)
+    ++w->completed;
+  while (w->issued < w->max_steps && w->issued - w->completed < 2) {
+    if (amr_advance(w->h, 1, nullptr) != AMR_OK) {
+      const std::string msg = amr_last_error();
+      std::lock_guard<std::mutex> g(mu);
+      for (auto *r : w->reqs)
+        if (!r->done) {
+          r->failed = r->done = true;
+          r->error = msg;
+          ++failed;
+        }
+      cv_done.notify_all();
+      return true;
+    }
+    cudaEvent_t e;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventRecord(e, w->s);
+    w->ev.push_back(e);
+    ++w->issued;
+  }
+  bool all = true;
+  for (size_t q = 0; q < w->reqs.size(); ++q) {
+    Request *r = w->reqs[q];
+    if (r->done) continue;
+    if (w->completed >= r->steps)
+      finish_member(w, r, int(q));
+    else
+      all = false;
+  }
+  return all;
+}
+
+void amr_server::loop() {
+  cudaSetDevice(device);
+  while (true) {
+    bool busy = false;
+    while (admit()) busy = true;
+    for (size_t t = 0; t < waves.size();) {
+      Wave *w = waves[t];
+      if (progress(w)) {
+        cudaStreamSynchronize(w->s);
+        amr_destroy(w->h);
+        for (auto e : w->ev) cudaEventDestroy(e);
+        cudaStreamDestroy(w->s);
+        {
+          std::lock_guard<std::mutex> g(mu);
+          bytes_in_use -= std::min(bytes_in_use, w->bytes);
+        }
+        delete w;
+        waves.erase(waves.begin() + t);
+        busy = true;
+      } else {
+        ++t;
+      }
+    }
+    std::unique_lock<std::mutex> lk(mu);
+    if (stop && queue.empty() && waves.empty()) break;
+    if (!busy)
+      cv_work.wait_for(lk, std::chrono::microseconds(waves.empty() ? 2000 : 100));
+  }
+}
+
+extern "C" amr_status amr_server_create(const amr_server_params *p, amr_server_t *out) {
+  if (!out) return set_error(AMR_EINVAL, "amr_server_create: out is NULL");
+  *out = nullptr;
+  amr_server *s = new amr_server();
+  if (p) s->p = *p;
+  if (s->p.hbm_budget_bytes == 0) s->p.hbm_budget_bytes = size_t(120) * 1000 * 1000 * 1000;
+  if (s->p.max_waves <= 0) s->p.max_waves = 8;
+  if (s->p.max_wave_members <= 0) s->p.max_wave_members = 256;
+  if (s->p.device < 0) cudaGetDevice(&s->device); else s->device = s->p.device;
+  s->th = std::thread([s] { s->loop(); });
+  *out = s;
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_server_submit(amr_server_t s, const amr_request *req, int64_t *id_out) {
+  if (!s || !req || !id_out) return set_error(AMR_EINVAL, "amr_server_submit: NULL argument");
+  const amr_member &m = req->mesh;
+  if (!m.level || !m.i || !m.j || !m.k || !m.U || m.n_oct < 1)
+    return set_error(AMR_EINVAL, "amr_server_submit: empty or NULL mesh");
+  if (req->n_coarse_steps < 1) return set_error(AMR_EINVAL, "amr_server_submit: n_coarse_steps < 1");
+  if (req->precision != 4 && req->precision != 8)
+    return set_error(AMR_EINVAL, "amr_server_submit: precision must be 4 or 8");
+  auto r = std::make_unique<Request>();
+  r->levelmin = m.levelmin;
+  r->levelmax = m.levelmax;
+  r->gamma = m.gamma;
+  r->cfl = m.cfl;
+  r->smallr = m.smallr;
+  r->smallc = m.smallc;
+  r->steps = req->n_coarse_steps;
+  r->precision = req->precision;
+  const int64_t n = m.n_oct;
+  r->level.assign(m.level, m.level + n);
+  r->i.assign(m.i, m.i + n);
+  r->j.assign(m.j, m.j + n);
+  r->k.assign(m.k, m.k + n);
+  if (m.hilbert_key) r->hk.assign(m.hilbert_key, m.hilbert_key + n);
+  r->U.assign(m.U, m.U + 40 * n);
+  r->est_bytes = estimate_bytes(n, r->precision);
+  if (r->est_bytes > s->p.hbm_budget_bytes)
+    return set_error(AMR_ENOMEM, "amr_server_submit: the request alone exceeds the device budget");
+  std::lock_guard<std::mutex> g(s->mu);
+  r->id = s->next_id++;
+  r->t_submit = now_s();
+  if (s->first_submit < 0) s->first_submit = r->t_submit;
+  *id_out = r->id;
+  s->queue.push_back(r.get());
+  s->reqs[r->id] = std::move(r);
+  ++s->submitted;
+  s->cv_work.notify_all();
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_server_wait(amr_server_t s, int64_t id, double timeout_s, int *done) {
+  if (!s) return set_error(AMR_EINVAL, "amr_server_wait: NULL server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto ready = [&] {
+    if (id < 0) return s->completed + s->failed == s->submitted;
+    auto it = s->reqs.find(id);
+    return it == s->reqs.end() || it->second->done;
+  };
+  if (id >= 0 && !s->reqs.count(id)) return set_error(AMR_EINVAL, "amr_server_wait: unknown request");
+  bool ok;
+  if (timeout_s < 0)
+    s->cv_done.wait(lk, ready), ok = true;
+  else
+    ok = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
+  if (done) *done = ok ? 1 : 0;
+  if (ok && id >= 0 && s->reqs[id]->failed)
+    return set_error(AMR_ECUDA, "request " + std::to_string(id) + " failed: " + s->reqs[id]->error);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_server_read(amr_server_t s, int64_t id, int level, int64_t *n_oct,
+                                      uint64_t *keys, double *U, int64_t cap) {
+  if (!s) return set_error(AMR_EINVAL, "amr_server_read: NULL server");
+  if (level < 0 || level > 15) return set_error(AMR_EINVAL, "amr_server_read: bad level");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return set_error(AMR_EINVAL, "amr_server_read: unknown request");
+  Request *r = it->second.get();
+  if (!r->done || r->failed) return set_error(AMR_EINVAL, "amr_server_read: request not finished");
+  const int64_t n = int64_t(r->keys[level].size());
+  if (n_oct) *n_oct = n;
+  if ((keys || U) && cap < n) return set_error(AMR_EINVAL, "amr_server_read: cap too small");
+  if (keys && n) std::memcpy(keys, r->keys[level].data(), 8 * n);
+  if (U && n) std::memcpy(U, r->Uout[level].data(), sizeof(double) * 40 * n);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_server_release(amr_server_t s, int64_t id) {
+  if (!s) return set_error(AMR_EINVAL, "amr_server_release: NULL server");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end() || !it->second->done)
+    return set_error(AMR_EINVAL, "amr_server_release: unknown or unfinished request");
+  s->reqs.erase(it);
+  return AMR_OK;
+}
+
+static double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * double(v.size() - 1);
+  const size_t a = size_t(pos);
+  const size_t b = std::min(a + 1, v.size() - 1);
+  return v[a] + (v[b] - v[a]) * (pos - double(a));
+}
+
+extern "C" amr_status amr_server_get_stats(amr_server_t s, amr_server_stats *st) {
+  if (!s || !st) return set_error(AMR_EINVAL, "amr_server_get_stats: NULL argument");
+  std::lock_guard<std::mutex> g(s->mu);
+  std::memset(st, 0, sizeof *st);
+  st->submitted = s->submitted;
+  st->admitted = s->admitted;
+  st->completed = s->completed;
+  st->failed = s->failed;
+  st->queued = int64_t(s->queue.size());
+  st->running_waves = int64_t(s->waves.size());
+  st->latency_p50_ms = percentile(s->latencies, 0.50);
+  st->latency_p99_ms = percentile(s->latencies, 0.99);
+  double sum = 0;
+  for (double x : s->latencies) sum += x;
+  st->latency_mean_ms = s->latencies.empty() ? 0.0 : sum / double(s->latencies.size());
+  st->queue_p50_ms = percentile(s->queue_waits, 0.50);
+  st->cell_updates = s->cell_updates;
+  st->span_s = (s->last_done > 0 && s->first_submit > 0) ? s->last_done - s->first_submit : 0.0;
+  st->device_bytes = int64_t(s->bytes_in_use);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_server_destroy(amr_server_t s) {
+  if (!s) return AMR_OK;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+    s->cv_work.notify_all();
+  }
+  if (s->th.joinable()) s->th.join();
+  delete s;
+  return AMR_OK;
+}

@@ -52,6 +52,8 @@ struct StepArgs {
   const double *dtdx_dev;
   const float *dtdxf_dev;
   double dt_host;
+  // members taking part in this coarse step (1) or finished (0); NULL: all
+  const int *mact;
   int reflux;
 };
 
@@ -65,10 +67,14 @@ struct CflArgs {
   const int *mlmin;
   int nmembers;
   unsigned long long *smax;  // [16 * members] bit patterns of per-level maxima
+  int *mrem;                 // [members] coarse steps left (-1: unlimited)
+  int *mact;                 // [members] 1 if the member steps in this coarse step
+  int consume;               // 1: this reduction starts a coarse step (counts down)
   double *dt_dev;            // [members] coarse dt
   double *dtdx_dev;          // [members] dt_m 2^levelmin_m
   float *dtdxf_dev;          // float copy for the FP32 kernels
   int *err;
+  int *merr;                 // [members] error bits of each member
 };
 
 }  // namespace amr

@@ -124,6 +124,7 @@ template <class T, class Size, class Body>
 __device__ __forceinline__ void tile_loop(const StepArgs<T> &a, Size size, Body body) {
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
     const Tile td = a.tiles[ti];
+    if (a.mact && !__ldg(a.mact + a.segs[td.seg].member)) continue;  // finished member
     const SegCtx<T> sc = seg_ctx(a, td.seg);
     const int item = td.start + threadIdx.x;
     if (item < size(sc)) body(sc, item);
@@ -310,14 +311,26 @@ __global__ void k_predict_u(StepArgs<T> a) {
             });
 }
 
+// max(c_L, c_R) with c^2 = gamma p / rho, from a = gamma p and rho per side.
+// FP64: c^2 compared by cross-multiplication, then for the larger side
+// c = a / sqrt(a rho) -- one reciprocal square root instead of a reciprocal
+// and a square root.  FP32 keeps the quotient form: a rho can leave float's
+// range at the density and pressure floors (about 1e-41), a / rho cannot.
+__device__ __forceinline__ double max_sound_speed(double al, double rl, double ar, double rr) {
+  const bool lbig = al * rr > ar * rl;
+  const double a = lbig ? al : ar;
+  return a * rsqrt_nr(a * (lbig ? rl : rr));
+}
+__device__ __forceinline__ float max_sound_speed(float al, float rl, float ar, float rr) {
+  return sqrtf(fmaxf(al * rcp(rl), ar * rcp(rr)));
+}
+
 // ---------------------------------------------------------------------------
 // HLLC flux normal to axis D from face states qL, qR (rho, u, v, w, p):
 // S_L = min(u) - max(c), S_R = max(u) + max(c); star speed and pressure from
 // the two-wave HLL jump conditions; physical flux of the state sampled at
 // x/t = 0 (Toro's HLLC); transverse velocities from the upwind side.
-// max(c) takes one reciprocal square root: c^2 = gamma p / rho is compared
-// across the face by cross-multiplication, and for the larger side
-// c = gamma p / sqrt(gamma p rho).
+// max(c) of the two sides, c^2 = gamma p / rho (see max_sound_speed).
 // ---------------------------------------------------------------------------
 template <int D, class T>
 __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T igm1, T (&F)[5]) {
@@ -326,10 +339,7 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   const T rr = qR[0], ur = qR[in], pr = qR[4];
   const T el = pl * igm1 + T(0.5) * rl * ((qL[1] * qL[1] + qL[2] * qL[2]) + qL[3] * qL[3]);
   const T er = pr * igm1 + T(0.5) * rr * ((qR[1] * qR[1] + qR[2] * qR[2]) + qR[3] * qR[3]);
-  const T gpl = g * pl, gpr = g * pr;
-  const bool lbig = gpl * rr > gpr * rl;
-  const T gpk = lbig ? gpl : gpr;
-  const T cmax = gpk * rsqrt_nr(gpk * (lbig ? rl : rr));
+  const T cmax = max_sound_speed(g * pl, rl, g * pr, rr);
   const T sl = vmin(ul, ur) - cmax;
   const T sr = vmax(ul, ur) + cmax;
   const T rcl = rl * (ul - sl), rcr = rr * (sr - ur);
@@ -595,7 +605,8 @@ __global__ void k_cfl(CflArgs a, const T *U) {
     }
     const Seg sg = a.segs[td.seg];
     const int t = td.start + threadIdx.x;
-    if (t < 8 * sg.nl && !((__ldg(a.son + sg.lo + (t >> 3)) >> (t & 7)) & 1u)) {
+    if (t < 8 * sg.nl && a.mrem[sg.member] != 0 &&
+        !((__ldg(a.son + sg.lo + (t >> 3)) >> (t & 7)) & 1u)) {
       const T g = T(a.mgamma[sg.member]), smallr = T(a.msmallr[sg.member]),
               smallp = T(a.msmallp[sg.member]);
       const int64_t gi = 8 * int64_t(sg.lo) + t;
@@ -608,10 +619,12 @@ __global__ void k_cfl(CflArgs a, const T *U) {
       const T p = vmax((g - T(1)) * (u4 - ek), r * smallp);
       const T cs = vsqrt(g * p * ir);
       const T st = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
-      if (!isfinite(st) || !isfinite(u0 + u1 + u2 + u3 + u4))
+      if (!isfinite(st) || !isfinite(u0 + u1 + u2 + u3 + u4)) {
         atomicOr(a.err, kErrNaN);
-      else
+        atomicOr(a.merr + sg.member, kErrNaN);
+      } else {
         s = fmax(s, double(st));
+      }
     }
   }
   if (cur >= 0) cfl_flush<T>(a, s, cur, wmax);
@@ -631,6 +644,13 @@ __global__ void k_dt(CflArgs a) {
     const double dtc = dtl * ldexp(1.0, l - lmin);
     dt = fmin(dt, dtc);
   }
+  // a member with no coarse steps left keeps its state and its last dt
+  const int rem = a.mrem[m];
+  if (a.consume) {
+    a.mact[m] = rem != 0;
+    if (rem > 0) a.mrem[m] = rem - 1;
+  }
+  if (rem == 0) return;
   a.dt_dev[m] = dt;
   a.dtdx_dev[m] = ldexp(dt, lmin);
   a.dtdxf_dev[m] = ldexpf(float(dt), lmin);

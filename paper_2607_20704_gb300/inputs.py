@@ -240,10 +240,12 @@ def sedov(levelmin: int = 7, levelmax: int = 10, radii=None, gamma: float = 5.0 
                     "centre": centre})
 
 
-def gaussian_field(n: int, index: float, sigma: float, rng) -> tuple[np.ndarray, np.ndarray]:
+def gaussian_field(n: int, index: float, sigma: float, rng,
+                   smooth: float = 0.0) -> tuple[np.ndarray, np.ndarray]:
     """Gaussian random field on an n^3 periodic grid with power spectrum
-    P(k) ~ k^index (k = 0 removed), rescaled to standard deviation sigma.
-    Returns the real field and its Fourier transform (rfftn layout)."""
+    P(k) ~ k^index (k = 0 removed), smoothed by a Gaussian of ``smooth`` grid
+    cells, rescaled to standard deviation sigma.  Returns the real field and
+    its Fourier transform (rfftn layout)."""
     kx = np.fft.fftfreq(n) * n
     kz = np.fft.rfftfreq(n) * n
     KX, KY, KZ = np.meshgrid(kx, kx, kz, indexing="ij")
@@ -251,6 +253,8 @@ def gaussian_field(n: int, index: float, sigma: float, rng) -> tuple[np.ndarray,
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (index / 4.0)  # sqrt(P) = k^(index/2)
+    if smooth > 0:
+        amp *= np.exp(-0.5 * k2 * (2.0 * np.pi * smooth / n) ** 2)
     noise = np.fft.rfftn(rng.standard_normal((n, n, n)))
     gk = noise * amp
     g = np.fft.irfftn(gk, s=(n, n, n), axes=(0, 1, 2))
@@ -260,17 +264,18 @@ def gaussian_field(n: int, index: float, sigma: float, rng) -> tuple[np.ndarray,
 
 def lognormal(levelmin: int = 8, extra: int = 4, sigma: float = 1.5, index: float = -2.0,
               seed: int = 7, vsigma: float = 0.1, gamma: float = 5.0 / 3.0,
-              cfl: float = 0.8, threshold: float = 8.0) -> Problem:
+              cfl: float = 0.8, threshold: float = 4.0, smooth: float = 1.0) -> Problem:
     """Cosmology-shaped clustered mesh: lognormal density rho = exp(g - s^2/2)
-    of a Gaussian field g (spectrum k^index, std ``sigma``) on the base level;
-    velocities v_a ~ i k_a / k^2 g_k, each component rescaled to std
-    ``vsigma``; p = 1e-4 rho^(5/3).  A cell of level l is refined where its
+    of a Gaussian field g (spectrum k^index smoothed over ``smooth`` base
+    cells, std ``sigma``) on the base level; velocities v_a ~ i k_a / k^2 g_k,
+    each component rescaled to std ``vsigma``; p = 0.01 rho (isothermal, sound
+    speed 0.13, peak Mach number about 3).  A cell of level l is refined where its
     mass exceeds ``threshold`` times the mean base-cell mass, i.e.
     rho > threshold^(1 + l - levelmin); up to ``extra`` levels, graded.
     Refined cells pass their values unchanged to their children."""
     rng = np.random.default_rng(seed)
     n = 1 << levelmin
-    g, gk = gaussian_field(n, index, sigma, rng)
+    g, gk = gaussian_field(n, index, sigma, rng, smooth)
     rho_b = np.exp(g - 0.5 * sigma * sigma)
     kx = np.fft.fftfreq(n) * n
     kz = np.fft.rfftfreq(n) * n
@@ -317,7 +322,7 @@ def lognormal(levelmin: int = 8, extra: int = 4, sigma: float = 1.5, index: floa
     u = vel[0][bx, by, bz]
     v = vel[1][bx, by, bz]
     w = vel[2][bx, by, bz]
-    p = 1e-4 * rho ** (5.0 / 3.0)
+    p = 1e-2 * rho
     U = prim_to_cons(gamma, rho, u, v, w, p)
     return Problem("lognormal", levelmin, int(lv.max()), gamma, cfl, lv, i, j, k, U,
                    {"sigma": sigma, "index": index, "seed": seed, "extra": extra})
@@ -442,3 +447,30 @@ def _nested_sod(levelmin: int, levelmax: int, axis: int = 0, gamma: float = 1.4,
 
     return Problem("sod", levelmin, levelmax, gamma, cfl, lv, i, j, k, _state(gamma, lv, i, j, k, fn),
                    {"axis": axis})
+
+
+def serving_requests(n_requests: int, seed: int = 13, pool: int = 24, max_level_base: int = 7,
+                     max_steps: int = 200):
+    """Seeded request stream for the serving loop: each request draws a mesh
+    from a pool of Sod / Sedov / lognormal-clustered problems (base 16^3 to
+    128^3 cells uniform in log, 0-3 extra levels), a number of coarse steps
+    (10..max_steps, uniform in log) and a precision (FP32 or FP64, 50/50).
+    Returns (problems, [(pool index, steps, precision)])."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for t in range(pool):
+        kind = ("sod", "sedov", "lognormal")[int(rng.integers(0, 3))]
+        lmin = int(rng.integers(4, max_level_base + 1))
+        extra = int(rng.integers(0, 4))
+        if kind == "sod":
+            probs.append(_nested_sod(lmin, lmin + extra, axis=int(rng.integers(0, 3))))
+        elif kind == "sedov":
+            radii = {l: 0.24 * 0.5 ** (l - lmin - 1) for l in range(lmin + 1, lmin + extra + 1)}
+            probs.append(sedov(lmin, lmin + extra, radii=radii))
+        else:
+            probs.append(lognormal(lmin, extra, seed=int(rng.integers(0, 1 << 30))))
+    reqs = []
+    for _ in range(n_requests):
+        steps = int(round(np.exp(rng.uniform(np.log(10), np.log(max_steps)))))
+        reqs.append((int(rng.integers(0, pool)), steps, 4 if rng.random() < 0.5 else 8))
+    return probs, reqs

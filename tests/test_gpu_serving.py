@@ -1,0 +1,134 @@
+"""Serving loop: requests admitted while others run share the GPU; each
+result must be bit-identical to the same solve alone."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2607_20704_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_20704_gb300 import amr, build
+    build.build()
+    amr.load()
+
+
+def _alone(prob, steps, precision):
+    from paper_2607_20704_gb300 import amr
+    m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, tile=128, schedule=0)
+    m.advance(steps, sync=True)
+    out = {l: m.read(l) for l in m.levels()}
+    m.close()
+    return out
+
+
+def _mix():
+    probs = [inputs.random_mesh(3, 5, seed=71), inputs.sedov(3, 5, radii={5: 0.1, 4: 0.2}),
+             inputs.sod(3, 4), inputs.random_mesh(2, 4, seed=72, gamma=5.0 / 3.0),
+             inputs.lognormal(4, 2, seed=3, threshold=2.0)]
+    reqs = [(0, 3, 8), (1, 5, 8), (2, 2, 4), (3, 4, 8), (4, 3, 4), (0, 6, 4), (1, 2, 8), (2, 7, 8)]
+    return probs, reqs
+
+
+def test_results_equal_alone_and_in_the_mix():
+    from paper_2607_20704_gb300 import amr
+    probs, reqs = _mix()
+    srv = amr.Server(max_waves=4)
+    ids = []
+    for t, (pi, steps, prec) in enumerate(reqs):
+        ids.append(srv.submit(probs[pi], steps, prec))
+        if t % 3 == 2:
+            time.sleep(0.02)  # later requests arrive while earlier waves run
+    assert srv.wait(-1, timeout=120.0)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
+    for rid, (pi, steps, prec) in zip(ids, reqs):
+        want = _alone(probs[pi], steps, prec)
+        for l, (kw, Uw) in want.items():
+            kg, Ug = srv.read(rid, l)
+            assert np.array_equal(kg, kw)
+            assert np.array_equal(Ug, Uw), (rid, l)
+        srv.release(rid)
+    srv.close()
+
+
+def test_admission_under_a_small_budget():
+    """With room for one request at a time, requests queue and are admitted
+    as memory is freed; results are unchanged."""
+    from paper_2607_20704_gb300 import amr
+    probs, reqs = _mix()
+    srv = amr.Server(hbm_budget_bytes=200 << 20, max_waves=8)
+    ids = [srv.submit(probs[pi], steps, prec) for pi, steps, prec in reqs[:4]]
+    seen_queue = srv.stats()["queued"]
+    assert srv.wait(-1, timeout=120.0)
+    st = srv.stats()
+    assert st["completed"] == 4 and st["failed"] == 0
+    assert seen_queue >= 1
+    for rid, (pi, steps, prec) in zip(ids, reqs[:4]):
+        want = _alone(probs[pi], steps, prec)
+        for l, (kw, Uw) in want.items():
+            assert np.array_equal(srv.read(rid, l)[1], Uw)
+    srv.close()
+
+
+def _poisoned(prob):
+    """The same mesh with one non-finite density (a bad request)."""
+    U = prob.U.copy()
+    q = int(np.flatnonzero(prob.level == prob.level.max())[-1])  # its cells are leaves
+    U[0, 8 * q + 3] = np.nan
+    return inputs.Problem(prob.name + "-nan", prob.levelmin, prob.levelmax, prob.gamma,
+                          prob.cfl, prob.level, prob.i, prob.j, prob.k, U, dict(prob.meta))
+
+
+def test_non_finite_member_fails_alone_in_a_batch():
+    from paper_2607_20704_gb300 import amr
+    probs = [inputs.random_mesh(3, 5, seed=71), _poisoned(inputs.sod(3, 4)),
+             inputs.random_mesh(2, 4, seed=72)]
+    for prec in (8, 4):
+        m = amr.Mesh.batch(probs, precision=prec, tile=128, schedule=0)
+        m.advance(2)
+        assert list(m.member_errors()) == [0, 1, 0]
+        for q in (0, 2):
+            want = _alone(probs[q], 2, prec)
+            m.select(q)
+            for l, (kw, Uw) in want.items():
+                kg, Ug = m.read(l)
+                assert np.array_equal(kg, kw) and np.array_equal(Ug, Uw), (prec, q, l)
+        m.close()
+
+
+def test_non_finite_request_fails_only_itself():
+    from paper_2607_20704_gb300 import amr
+    probs, reqs = _mix()
+    bad = _poisoned(probs[2])
+    srv = amr.Server(max_waves=2)
+    ids = [srv.submit(probs[pi], steps, prec) for pi, steps, prec in reqs[:3]]
+    bad_id = srv.submit(bad, 3, reqs[2][2])
+    ids += [srv.submit(probs[pi], steps, prec) for pi, steps, prec in reqs[3:5]]
+    assert srv.wait(-1, timeout=120.0)
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == 5
+    with pytest.raises(amr.AmrError):
+        srv.wait(bad_id)
+    for rid, (pi, steps, prec) in zip(ids, reqs[:3] + reqs[3:5]):
+        want = _alone(probs[pi], steps, prec)
+        for l, (kw, Uw) in want.items():
+            assert np.array_equal(srv.read(rid, l)[1], Uw), (rid, l)
+    srv.close()
+
+
+def test_request_larger_than_the_budget_is_refused():
+    from paper_2607_20704_gb300 import amr
+    srv = amr.Server(hbm_budget_bytes=1 << 20)
+    with pytest.raises(amr.AmrError) as e:
+        srv.submit(inputs.random_mesh(3, 5, seed=1), 2, 8)
+    assert e.value.status == amr.AMR_ENOMEM
+    srv.close()
