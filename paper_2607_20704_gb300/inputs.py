@@ -264,12 +264,18 @@ def gaussian_field(n: int, index: float, sigma: float, rng,
 
 def lognormal(levelmin: int = 8, extra: int = 4, sigma: float = 1.5, index: float = -2.0,
               seed: int = 7, vsigma: float = 0.1, gamma: float = 5.0 / 3.0,
-              cfl: float = 0.8, threshold: float = 4.0, smooth: float = 1.0) -> Problem:
+              cfl: float = 0.8, threshold: float = 8.0, smooth: float = 0.0,
+              isothermal: float | None = None) -> Problem:
     """Cosmology-shaped clustered mesh: lognormal density rho = exp(g - s^2/2)
-    of a Gaussian field g (spectrum k^index smoothed over ``smooth`` base
-    cells, std ``sigma``) on the base level; velocities v_a ~ i k_a / k^2 g_k,
-    each component rescaled to std ``vsigma``; p = 0.01 rho (isothermal, sound
-    speed 0.13, peak Mach number about 3).  A cell of level l is refined where its
+    of a Gaussian field g (spectrum k^index, optionally smoothed over
+    ``smooth`` base cells, std ``sigma``) on the base level; velocities
+    v_a ~ i k_a / k^2 g_k, each component rescaled to std ``vsigma``;
+    p = 1e-4 rho^(5/3), or p = ``isothermal`` * rho when given.  The default
+    (unsmoothed, adiabat) state has flows up to Mach ~150 between nearly
+    uncorrelated neighbouring cells: fine for single level steps, but over
+    whole coarse steps the minmod prolongation of such ghosts drives coarse
+    cells negative; ``smooth=1, isothermal=0.01`` (peak Mach ~3) is the
+    well-posed variant for multi-step runs.  A cell of level l is refined where its
     mass exceeds ``threshold`` times the mean base-cell mass, i.e.
     rho > threshold^(1 + l - levelmin); up to ``extra`` levels, graded.
     Refined cells pass their values unchanged to their children."""
@@ -322,7 +328,7 @@ def lognormal(levelmin: int = 8, extra: int = 4, sigma: float = 1.5, index: floa
     u = vel[0][bx, by, bz]
     v = vel[1][bx, by, bz]
     w = vel[2][bx, by, bz]
-    p = 1e-2 * rho
+    p = 1e-4 * rho ** (5.0 / 3.0) if isothermal is None else isothermal * rho
     U = prim_to_cons(gamma, rho, u, v, w, p)
     return Problem("lognormal", levelmin, int(lv.max()), gamma, cfl, lv, i, j, k, U,
                    {"sigma": sigma, "index": index, "seed": seed, "extra": extra})
@@ -468,7 +474,8 @@ def serving_requests(n_requests: int, seed: int = 13, pool: int = 24, max_level_
             radii = {l: 0.24 * 0.5 ** (l - lmin - 1) for l in range(lmin + 1, lmin + extra + 1)}
             probs.append(sedov(lmin, lmin + extra, radii=radii))
         else:
-            probs.append(lognormal(lmin, extra, seed=int(rng.integers(0, 1 << 30))))
+            probs.append(lognormal(lmin, extra, seed=int(rng.integers(0, 1 << 30)),
+                                   threshold=4.0, smooth=1.0, isothermal=0.01))
     reqs = []
     for _ in range(n_requests):
         steps = int(round(np.exp(rng.uniform(np.log(10), np.log(max_steps)))))

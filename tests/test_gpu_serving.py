@@ -32,7 +32,7 @@ def _alone(prob, steps, precision):
 def _mix():
     probs = [inputs.random_mesh(3, 5, seed=71), inputs.sedov(3, 5, radii={5: 0.1, 4: 0.2}),
              inputs.sod(3, 4), inputs.random_mesh(2, 4, seed=72, gamma=5.0 / 3.0),
-             inputs.lognormal(4, 2, seed=3, threshold=2.0)]
+             inputs.lognormal(4, 2, seed=3, threshold=2.0, smooth=1.0, isothermal=0.01)]
     reqs = [(0, 3, 8), (1, 5, 8), (2, 2, 4), (3, 4, 8), (4, 3, 4), (0, 6, 4), (1, 2, 8), (2, 7, 8)]
     return probs, reqs
 
