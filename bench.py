@@ -56,8 +56,8 @@ def parse():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
-            int(os.environ.get("LOCAL_RANK", 0)))
+    from paper_2607_20704_gb300 import dist
+    return dist.env()
 
 
 def work_per_step(info, levelmin=None):
@@ -201,6 +201,9 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
     launches0 = info["kernel_launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
+    from paper_2607_20704_gb300 import dist
+    dist.barrier()
+    torch.cuda.synchronize(device)
     wall0 = time.perf_counter()
     for e0, e1 in ev:
         e0.record(st)
@@ -210,6 +213,7 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
             flush_l2(flush)
     torch.cuda.synchronize(device)
     wall = time.perf_counter() - wall0
+    dist.barrier()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     launches = mesh.info()["kernel_launches"] - launches0
     res = {"ms": ms, "wall_s": wall, "updates_per_step": upd, "launches": launches, "info": info}
@@ -373,7 +377,19 @@ def fp64_peak(torch, device):
     return 2 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def roofline(res, prec, levelmin, peak_gbs, peak_src, fp64_tflops=None):
+# FP64 pipe of the GB300: 152 SMs, 2 FP64 FMA lanes per SM per clock (the
+# nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock: 152 x 2 x 2 x 2.07e9)
+N_SM = 152
+FP64_FMA_PER_SM_CLK = 2
+
+
+def fp64_peak_derived(sm_mhz):
+    """FP64 TFLOP/s (2 per FMA) at the given SM clock."""
+    return N_SM * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline(res, prec, levelmin, peak_gbs, peak_src, fp64_tflops=None, dgemm=None,
+             sm_mhz=None):
     """Roofline object of the dominant kernel: achieved = its algorithmic
     bytes (FP32) or FP64 flops (FP64: the flux kernel is bound by the FP64
     pipe) per launch / its average CUDA-event launch time."""
@@ -404,10 +420,13 @@ def roofline(res, prec, levelmin, peak_gbs, peak_src, fp64_tflops=None):
     if prec == 8 and name == "flux" and fp64_tflops:
         flops = FLUX_FP64_FLOPS_PER_CELL * cells_per_launch
         ach = flops / avg_s / 1e12
-        rl = {"kernel": name, "bound": "alu", "achieved": round(ach, 4), "peak": fp64_tflops,
-              "unit": "TFLOP/s", "frac": round(ach / fp64_tflops, 4), "traffic": traffic_launch,
-              "peak_source": "measured: cuBLAS DGEMM 4096^3 in this run (FP64)",
+        rl = {"kernel": name, "bound": "alu", "achieved": round(ach, 4),
+              "peak": round(fp64_tflops, 4), "unit": "TFLOP/s", "frac": round(ach / fp64_tflops, 4),
+              "traffic": traffic_launch,
+              "peak_source": f"derived: {N_SM} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 flops "
+                             f"x {sm_mhz:.0f} MHz (median SM clock under load)",
               "flops_per_launch": int(flops), "avg_launch_us": round(avg_s * 1e6, 3),
+              "dgemm_tflops": dgemm, "frac_of_dgemm": round(ach / dgemm, 4) if dgemm else None,
               "hbm_view": hbm}
     else:
         rl = dict(hbm)
@@ -421,12 +440,12 @@ def main():
     rank, world, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3
+    if args.impl == "reference" and rank != 0:
+        return 0  # the reference arm runs on rank 0 alone
     from paper_2607_20704_gb300 import inputs
     prob = inputs.sedov()
 
     if args.impl == "reference":
-        if rank != 0:
-            return 0
         import oracle
         m = oracle.Mesh(*prob.mesh_args(), **prob.params())
         upd = sum(int(np.count_nonzero(m.read_split(l) == 0)) * 2 ** (l - prob.levelmin)
@@ -463,9 +482,9 @@ def main():
                           "octs": m.num_octs(args.profile_level)}))
         m.close()
         return 0
+    from paper_2607_20704_gb300 import dist
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.init("nccl", torch.device("cuda", local))
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     from paper_2607_20704_gb300 import amr, build
@@ -477,8 +496,6 @@ def main():
     prec_main = args.precision
     prec_other = 4 if prec_main == 8 else 8
     with ClockSampler(local) as clk:
-        if world > 1:
-            dist.barrier()
         main_res = run_precision(prob, prec_main, args.steps, args.warmup, torch, device, flush)
         main_res["steps"] = args.steps
         other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
@@ -494,19 +511,20 @@ def main():
             del ens
     clocks = clk.summary()
 
-    ms = main_res["ms"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     upd = main_res["updates_per_step"]
-    value = upd * args.steps * world / (ms * 1e-3)
+    # whole job: every rank's cell-updates over the slowest rank's time
+    value, slowest_s = dist.throughput(upd * args.steps, main_res["ms"] * 1e-3, device)
+    ms = slowest_s * 1e3
+    other_value, other_s = dist.throughput(upd * args.steps, other["ms"] * 1e-3, device)
     try:
         dgemm = round(fp64_peak(torch, device), 4)
     except Exception:
         dgemm = None
-    rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src, dgemm)
-    rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src, dgemm)
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_pk = fp64_peak_derived(sm_mhz)
+    rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src, fp64_pk, dgemm, sm_mhz)
+    rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src, fp64_pk, dgemm,
+                             sm_mhz)
     step_bytes = 2 * 5 * WORD[prec_main]
     line = {
         "metric": "leaf cell-updates/s",
@@ -538,10 +556,10 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         ("fp32" if prec_other == 4 else "fp64"): {
-            "value": upd * args.steps * world / (other["ms"] * 1e-3),
-            "ms_per_step": other["ms"] / args.steps,
+            "value": other_value,
+            "ms_per_step": other_s * 1e3 / args.steps,
             "roofline": rl_o, "kernels": table_o, "gpu_launches": other["launches"],
-            "step_roofline_frac": round(upd * args.steps / (other["ms"] * 1e-3)
+            "step_roofline_frac": round(other_value / world
                                         * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)},
     }
     if batched is not None:
@@ -552,8 +570,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_steps)
     if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+        dist.finalize()
     if rank == 0:
         print(json.dumps(line))
     return 0

@@ -1,0 +1,58 @@
+"""Multi-process host logic on CPU (gloo, two ranks): the reductions that
+turn per-rank timings into the whole-job rate, and the reference arm's
+rank-0-only rule."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    from paper_2607_20704_gb300 import dist
+    assert dist.env() == (rank, world, rank)
+    dist.init("gloo")
+    dist.barrier()
+    mx = dist.max_over_ranks(rank + 1.0)
+    sm = dist.sum_over_ranks(rank + 1.0)
+    # rank r processed 10 units in (1 + r) seconds
+    rate, slowest = dist.throughput(10.0, 1.0 + rank)
+    dist.finalize()
+    with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+        f.write(f"{mx} {sm} {rate} {slowest}\n")
+
+
+def test_reductions_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.spawn(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        mx, sm, rate, slowest = map(float, (tmp_path / f"r{r}.txt").read_text().split())
+        assert mx == 2.0 and sm == 3.0
+        assert slowest == 2.0 and rate == pytest.approx(20.0 / 2.0)
+
+
+def test_single_process_reductions_are_identity():
+    from paper_2607_20704_gb300 import dist
+    assert dist.max_over_ranks(3.5) == 3.5
+    assert dist.throughput(12.0, 4.0) == (3.0, 4.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
