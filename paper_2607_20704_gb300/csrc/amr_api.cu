@@ -530,7 +530,7 @@ static void run_segments(amr_mesh *h, const SegList &L, bool device_dt, double d
   if (L.nseg == 0) return;
   StepArgs<T> a = step_args<T>(h, device_dt, dt);
   run_list(h, K_PROLONG, k_prolong<T>, a, L, DOM_GHOST5);
-  if (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {
     // FP32: primitives recomputed inside the predictor; each leaf cell solves
     // its six faces and updates itself
     run_list(h, K_PREDICT, k_predict_u<T>, a, L, DOM_CELLS);

@@ -284,7 +284,7 @@ __global__ void k_predict(StepArgs<T> a) {
 // FP32: primitives of the cell and its six face neighbours derived from U
 // directly (no W array)
 template <class T>
-__global__ void k_predict_u(StepArgs<T> a) {
+__global__ void __launch_bounds__(512, 3) k_predict_u(StepArgs<T> a) {
   tile_loop(a, [](const SegCtx<T> &s) { return 8 * (s.nl + s.ncl); },
             [&](const SegCtx<T> &s, int t) {
               const int e = ext_of_local(a, s, t >> 3);
@@ -512,7 +512,7 @@ __device__ __forceinline__ void faces_dir(const StepArgs<T> &a, const SegCtx<T> 
 }
 
 template <class T>
-__global__ void k_flux_update(StepArgs<T> a) {
+__global__ void __launch_bounds__(512, 3) k_flux_update(StepArgs<T> a) {
   tile_loop(a, [](const SegCtx<T> &s) { return 8 * s.nl; }, [&](const SegCtx<T> &s, int t) {
     if (cell_is_split(a, s, t)) return;
     const int e = s.lo + (t >> 3);
