@@ -44,10 +44,33 @@ __device__ __forceinline__ float minmod(float a, float b) {
   if (((ia ^ ib) < 0) | (ma == 0) | (mb == 0)) return 0.0f;
   return ma < mb ? a : b;
 }
-__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+// FP64 compares, min and max decided on the bit patterns: GB300's FP64 pipe
+// is 1/64 of its FP32 rate and these kernels are bound by it, while the
+// integer pipes have room.  ord() maps a non-NaN double to a signed integer
+// of the same order (-0 just below +0); a NaN argument propagates instead of
+// being dropped (the time-step reduction reports it).
+__device__ __forceinline__ long long ord(double x) {
+  const long long i = __double_as_longlong(x);
+  return i ^ ((i >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double vmax(double a, double b) { return ord(a) < ord(b) ? b : a; }
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return ord(b) < ord(a) ? b : a; }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+// x > 0
+__device__ __forceinline__ bool pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool pos(float x) { return x > 0.0f; }
+// x is neither infinite nor NaN (exponent field not all ones)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
+}
+__device__ __forceinline__ bool finite_bits(float x) {
+  return ((__float_as_int(x) >> 23) & 0xFF) != 0xFF;
+}
+// a > b for a, b >= 0
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
 __device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
 
@@ -317,7 +340,7 @@ __global__ void __launch_bounds__(512, 3) k_predict_u(StepArgs<T> a) {
 // and a square root.  FP32 keeps the quotient form: a rho can leave float's
 // range at the density and pressure floors (about 1e-41), a / rho cannot.
 __device__ __forceinline__ double max_sound_speed(double al, double rl, double ar, double rr) {
-  const bool lbig = al * rr > ar * rl;
+  const bool lbig = gt_nonneg(al * rr, ar * rl);
   const double a = lbig ? al : ar;
   return a * rsqrt_nr(a * (lbig ? rl : rr));
 }
@@ -347,14 +370,14 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   const T us = ((rcr * ur + rcl * ul) + (pl - pr)) * irc;
   const T ps = ((rcr * pl + rcl * pr) + rcl * rcr * (ul - ur)) * irc;
   T ro, uo, po, eo, v1, v2;
-  if (sl > T(0)) {
+  if (pos(sl)) {
     ro = rl; uo = ul; po = pl; eo = el; v1 = qL[t1]; v2 = qL[t2];
-  } else if (us > T(0)) {
+  } else if (pos(us)) {
     const T id = rcp(sl - us);
     ro = rl * (sl - ul) * id;
     eo = ((sl - ul) * el - pl * ul + ps * us) * id;
     uo = us; po = ps; v1 = qL[t1]; v2 = qL[t2];
-  } else if (sr > T(0)) {
+  } else if (pos(sr)) {
     const T id = rcp(sr - us);
     ro = rr * (sr - ur) * id;
     eo = ((sr - ur) * er - pr * ur + ps * us) * id;
@@ -619,11 +642,12 @@ __global__ void k_cfl(CflArgs a, const T *U) {
       const T p = vmax((g - T(1)) * (u4 - ek), r * smallp);
       const T cs = vsqrt(g * p * ir);
       const T st = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
-      if (!isfinite(st) || !isfinite(u0 + u1 + u2 + u3 + u4)) {
+      if (!finite_bits(st) || !(finite_bits(u0) && finite_bits(u1) && finite_bits(u2) &&
+                                finite_bits(u3) && finite_bits(u4))) {
         atomicOr(a.err, kErrNaN);
         atomicOr(a.merr + sg.member, kErrNaN);
-      } else {
-        s = fmax(s, double(st));
+      } else if (gt_nonneg(double(st), s)) {
+        s = double(st);
       }
     }
   }
