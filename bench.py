@@ -559,6 +559,7 @@ def main():
             "value": other_value,
             "ms_per_step": other_s * 1e3 / args.steps,
             "roofline": rl_o, "kernels": table_o, "gpu_launches": other["launches"],
+            "autotuned": {"tile": other["info"].get("tile"), "schedule": other["info"].get("schedule")},
             "step_roofline_frac": round(other_value / world
                                         * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)},
     }

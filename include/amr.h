@@ -79,7 +79,7 @@ typedef struct {
   amr_alloc_fn alloc;       /* NULL: cudaMallocAsync on the stream */
   amr_free_fn free;
   void *alloc_user;
-  int tile;                 /* cells (threads) per work tile: 128, 256 or 512;
+  int tile;                 /* cells (threads) per work tile: 64, 128, 256 or 512;
                                0: autotune at the first amr_advance (default) */
   int schedule;             /* 1: persistent grids sized by occupancy x SMs;
                                0: one tile per block; -1: autotune (default) */

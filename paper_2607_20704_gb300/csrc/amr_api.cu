@@ -1022,9 +1022,9 @@ extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
   h->p = *p;
   h->M = n_members;
   h->mem.resize(n_members);
-  if (p->tile != 0 && p->tile != 128 && p->tile != 256 && p->tile != 512) {
+  if (p->tile != 0 && p->tile != 64 && p->tile != 128 && p->tile != 256 && p->tile != 512) {
     delete h;
-    return fail(AMR_EINVAL, "amr_create: tile must be 0, 128, 256 or 512");
+    return fail(AMR_EINVAL, "amr_create: tile must be 0, 64, 128, 256 or 512");
   }
   h->tile_size = p->tile ? p->tile : 256;
   h->persistent = p->schedule != 0;
@@ -1134,16 +1134,36 @@ static amr_status set_tile(amr_mesh *h, int tile) {
   return AMR_OK;
 }
 
+// One coarse step captured as a CUDA graph, the way amr_advance replays it.
+static amr_status capture_coarse_step(amr_mesh *h, cudaGraphExec_t *out) {
+  *out = nullptr;
+  h->capturing = true;
+  h->capture_kernels = 0;
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+  coarse_step(h);
+  cudaError_t e = cudaStreamEndCapture(h->s, &g);
+  h->capturing = false;
+  if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_advance: capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_advance: instantiate failed: %s", cudaGetErrorString(e));
+  return AMR_OK;
+}
+
 // Time candidate (tile, schedule) pairs on full coarse steps from a snapshot
-// of the state; restore the snapshot; keep the fastest.
+// of the state, run as they will run (graph replays when graphs are on), the
+// best of three steps each; restore the snapshot; keep the fastest.
 static amr_status autotune(amr_mesh *h) {
   h->tuned = true;
-  std::vector<int> tiles = h->p.tile ? std::vector<int>{h->p.tile} : std::vector<int>{128, 256, 512};
+  std::vector<int> tiles =
+      h->p.tile ? std::vector<int>{h->p.tile} : std::vector<int>{64, 128, 256, 512};
   std::vector<int> scheds = h->p.schedule >= 0 ? std::vector<int>{h->p.schedule} : std::vector<int>{1, 0};
   if (tiles.size() * scheds.size() == 1) {
     h->persistent = scheds[0] == 1;
     return set_tile(h, tiles[0]);
   }
+  const bool graphs = h->p.use_graphs && !h->timing;
   const size_t ub = h->elem() * 5 * size_t(h->S), rb = h->elem() * 5 * size_t(h->NC > 0 ? h->NC : 1);
   const size_t mb = sizeof(int) * size_t(h->M);
   void *su = nullptr, *sr = nullptr, *sm = nullptr;
@@ -1162,16 +1182,28 @@ static amr_status autotune(amr_mesh *h) {
     for (int sc : scheds) {
       AMR_TRY(set_tile(h, t));
       h->persistent = sc == 1;
-      coarse_step(h);  // warm-up
-      cudaEventRecord(e0, h->s);
-      coarse_step(h);
-      coarse_step(h);
-      cudaEventRecord(e1, h->s);
-      CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
+      cudaGraphExec_t ge = nullptr;
+      if (graphs) AMR_TRY(capture_coarse_step(h, &ge));
+      auto step = [&] {
+        if (ge)
+          cudaGraphLaunch(ge, h->s);
+        else
+          coarse_step(h);
+      };
+      step();  // warm-up
+      float cand = 1e30f;
+      for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(e0, h->s);
+        step();
+        cudaEventRecord(e1, h->s);
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cand = std::min(cand, ms);
+      }
+      if (ge) cudaGraphExecDestroy(ge);
+      if (cand < best) {
+        best = cand;
         best_tile = t;
         best_sched = sc;
       }
@@ -1195,17 +1227,7 @@ extern "C" amr_status amr_advance(amr_handle h, int n, double *dt_last) {
   if (!h->tuned && n > 0) AMR_TRY(autotune(h));
   const bool graphs = h->p.use_graphs && !h->timing;
   if (graphs && !h->graph && n > 0) {
-    h->capturing = true;
-    h->capture_kernels = 0;
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-    coarse_step(h);
-    cudaError_t e = cudaStreamEndCapture(h->s, &g);
-    h->capturing = false;
-    if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_advance: capture failed: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&h->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_advance: instantiate failed: %s", cudaGetErrorString(e));
+    AMR_TRY(capture_coarse_step(h, &h->graph));
     h->graph_kernels = h->capture_kernels;
   }
   for (int t = 0; t < n; ++t) {
