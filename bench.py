@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--batched-members", type=int, default=512)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
     ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--no-other-precision", action="store_true",
+                    help="run only --precision (skip the other precision's pass)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="work-tile size of every handle (0: autotune at the first step)")
+    ap.add_argument("--schedule", type=int, default=-1,
+                    help="1 persistent grids, 0 one tile per block, -1 autotune")
     ap.add_argument("--profile-level", type=int, default=0,
                     help="profiling mode: build the mesh and run one eager level step of this "
                          "level (one launch of each level-step kernel), then exit")
@@ -169,7 +175,7 @@ def kernel_traffic(info, levelmin, w, fused):
 # faces), and DRAM bytes per cell of the flux kernels, from one ncu capture
 # of the level-7 launch of the benchmark mesh (profiles/flux_sedov_level7.md)
 FLUX_FP64_FLOPS_PER_CELL = 325.5
-FLUX_DRAM_BYTES_PER_CELL = {8: 283.9, 4: 125.2}
+FLUX_DRAM_BYTES_PER_CELL = {8: 272.8, 4: 127.4}
 
 
 def load_peaks():
@@ -186,9 +192,11 @@ def flush_l2(buf):
 
 
 # -- our arm ----------------------------------------------------------------------
+LAUNCH = {"tile": 0, "schedule": -1}  # set from --tile / --schedule
+
 def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=True):
     from paper_2607_20704_gb300 import amr
-    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision)
+    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, **LAUNCH)
     info = mesh.info()
     upd = work_per_step(info, prob.levelmin)
     st = mesh.stream
@@ -198,6 +206,7 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
             flush_l2(flush)
     torch.cuda.synchronize(device)
     info = mesh.info()  # after the autotuner has picked tile and schedule
+    mesh_tile, mesh_sched = info["tile"], info["schedule"]
     launches0 = info["kernel_launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
@@ -221,7 +230,8 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
     if kernels:
         # per-kernel device time: same K steps, each launch bracketed by CUDA
         # events on the library's stream (eager launches, no graph)
-        m2 = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision)
+        m2 = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision,
+                      tile=mesh_tile, schedule=mesh_sched)
         for _ in range(warmup):
             m2.advance(1)
         m2.sync()
@@ -240,7 +250,7 @@ def run_e2e(prob, precision, steps, torch):
     every level's state from pinned host memory, advance one coarse step,
     read every level back (synchronous)."""
     from paper_2607_20704_gb300 import amr
-    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision)
+    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, **LAUNCH)
     info = mesh.info()
     upd = work_per_step(info, prob.levelmin)
     levels = mesh.levels()
@@ -440,6 +450,7 @@ def main():
     rank, world, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3
+    LAUNCH.update(tile=args.tile, schedule=args.schedule)
     if args.impl == "reference" and rank != 0:
         return 0  # the reference arm runs on rank 0 alone
     from paper_2607_20704_gb300 import inputs
@@ -474,7 +485,7 @@ def main():
     import torch
     if args.profile_level:
         from paper_2607_20704_gb300 import amr
-        m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=args.precision)
+        m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=args.precision, **LAUNCH)
         dt = m.cfl_dt() * 0.5 ** (args.profile_level - prob.levelmin)
         m.step_level(args.profile_level, dt)
         m.sync()
@@ -498,8 +509,10 @@ def main():
     with ClockSampler(local) as clk:
         main_res = run_precision(prob, prec_main, args.steps, args.warmup, torch, device, flush)
         main_res["steps"] = args.steps
-        other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
-        other["steps"] = args.steps
+        other = None
+        if not args.no_other_precision:
+            other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
+            other["steps"] = args.steps
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
         serving = None
         if not args.no_serving:
@@ -515,7 +528,8 @@ def main():
     # whole job: every rank's cell-updates over the slowest rank's time
     value, slowest_s = dist.throughput(upd * args.steps, main_res["ms"] * 1e-3, device)
     ms = slowest_s * 1e3
-    other_value, other_s = dist.throughput(upd * args.steps, other["ms"] * 1e-3, device)
+    if other is not None:
+        other_value, other_s = dist.throughput(upd * args.steps, other["ms"] * 1e-3, device)
     try:
         dgemm = round(fp64_peak(torch, device), 4)
     except Exception:
@@ -523,8 +537,9 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_pk = fp64_peak_derived(sm_mhz)
     rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src, fp64_pk, dgemm, sm_mhz)
-    rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src, fp64_pk, dgemm,
-                             sm_mhz)
+    if other is not None:
+        rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src, fp64_pk,
+                                 dgemm, sm_mhz)
     step_bytes = 2 * 5 * WORD[prec_main]
     line = {
         "metric": "leaf cell-updates/s",
@@ -555,14 +570,15 @@ def main():
         "autotuned": {"tile": main_res["info"].get("tile"), "schedule": main_res["info"].get("schedule")},
         "clocks": clocks,
         "e2e": e2e,
-        ("fp32" if prec_other == 4 else "fp64"): {
+    }
+    if other is not None:
+        line["fp32" if prec_other == 4 else "fp64"] = {
             "value": other_value,
             "ms_per_step": other_s * 1e3 / args.steps,
             "roofline": rl_o, "kernels": table_o, "gpu_launches": other["launches"],
             "autotuned": {"tile": other["info"].get("tile"), "schedule": other["info"].get("schedule")},
             "step_roofline_frac": round(other_value / world
-                                        * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)},
-    }
+                                        * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)}
     if batched is not None:
         line["batched"] = batched
     if serving is not None:

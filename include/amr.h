@@ -318,8 +318,9 @@ amr_status amr_cfl_dt_static(const double *U, int64_t n_cells, int64_t stride, i
  * a wave whose members are all finished frees its device memory.  A
  * request's result is bit-identical to the same solve in a handle of its own.
  * Errors: submit refuses a request that alone exceeds the budget
- * (AMR_ENOMEM) or has bad arguments (AMR_EINVAL); a request whose state
- * turns non-finite, or whose wave cannot be created, fails alone --
+ * (AMR_ENOMEM) or has bad arguments (AMR_EINVAL); a request whose mesh is
+ * invalid (its wave is then rebuilt without it) or whose state turns
+ * non-finite fails alone --
  * amr_server_wait returns AMR_ECUDA with the reason in amr_last_error(), and
  * the other requests of its wave carry on.
  */

@@ -56,6 +56,7 @@ struct Request {
   double t_submit = 0, t_admit = -1, t_done = -1;
   double work = 0;  // leaf cell-updates of the whole solve
   bool done = false, failed = false;
+  bool solo = false;  // admitted alone (its wave-mates' batch could not be built)
   std::string error;
   std::vector<std::vector<uint64_t>> keys;  // final state, per level
   std::vector<std::vector<double>> Uout;
@@ -72,9 +73,18 @@ struct Wave {
 
 // device bytes of a handle per oct, for admission before the handle exists
 // (state with ghosts, level-step scratch, index, hash, create-time staging)
+struct Request;
+size_t need_bytes(const std::vector<Request *> &rs);
+
 size_t estimate_bytes(int64_t n_oct, int precision) {
   const size_t w = precision == 4 ? 4 : 8;
   return size_t(n_oct) * (w * (8 * 5 * 2 + 8 * 40) + 1024) + (8u << 20);
+}
+
+size_t need_bytes(const std::vector<Request *> &rs) {
+  size_t b = 0;
+  for (auto *r : rs) b += r->est_bytes;
+  return b;
 }
 
 }  // namespace
@@ -111,13 +121,15 @@ bool amr_server::admit() {
     size_t budget_left = p.hbm_budget_bytes > bytes_in_use ? p.hbm_budget_bytes - bytes_in_use : 0;
     size_t need = 0;
     // in arrival order: the wave takes the leading requests of one precision
-    // that fit the remaining budget
+    // that fit the remaining budget; a request marked solo goes alone
     while (!queue.empty() && int(take.size()) < p.max_wave_members) {
       Request *r = queue.front();
       if (r->precision != prec || need + r->est_bytes > budget_left) break;
+      if (r->solo && !take.empty()) break;
       need += r->est_bytes;
       take.push_back(r);
       queue.pop_front();
+      if (r->solo) break;
     }
     if (take.empty()) return false;
     bytes_in_use += need;
@@ -157,8 +169,21 @@ bool amr_server::admit() {
   if (s == AMR_OK) s = amr_set_member_steps(w->h, steps.data(), int(steps.size()));
   const double t = now_s();
   std::lock_guard<std::mutex> g(mu);
+  if (s != AMR_OK && take.size() > 1) {
+    // one of the meshes is invalid (or the batch too large): retry each
+    // request alone, in the same order, so that only the bad one fails
+    if (w->h) amr_destroy(w->h);
+    cudaStreamDestroy(w->s);
+    delete w;
+    bytes_in_use -= std::min(bytes_in_use, need_bytes(take));
+    for (auto it = take.rbegin(); it != take.rend(); ++it) {
+      (*it)->solo = true;
+      queue.push_front(*it);
+    }
+    return true;
+  }
   if (s != AMR_OK) {
-    // the requests fail with the handle's error; their budget returns
+    // the request fails with the handle's error; its budget returns
     const std::string msg = amr_last_error();
     for (auto *r : take) {
       r->failed = r->done = true;

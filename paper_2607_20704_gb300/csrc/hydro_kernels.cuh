@@ -401,8 +401,10 @@ __device__ __forceinline__ void face_flux(const StepArgs<T> &a, const SegCtx<T> 
   const int ol = s.base + tl, orr = s.base + tr;
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    qL[v] = a.Q[v * a.LS + ol] + T(0.5) * a.Q[(5 + 5 * D + v) * a.LS + ol];
-    qR[v] = a.Q[v * a.LS + orr] - T(0.5) * a.Q[(5 + 5 * D + v) * a.LS + orr];
+    // Q is read-only while faces are solved (the read-only path lets the
+    // compiler keep a cell's values across its faces)
+    qL[v] = __ldg(a.Q + v * a.LS + ol) + T(0.5) * __ldg(a.Q + (5 + 5 * D + v) * a.LS + ol);
+    qR[v] = __ldg(a.Q + v * a.LS + orr) - T(0.5) * __ldg(a.Q + (5 + 5 * D + v) * a.LS + orr);
   }
   qL[0] = vmax(qL[0], s.smallr);
   qR[0] = vmax(qR[0], s.smallr);

@@ -125,6 +125,43 @@ def test_non_finite_request_fails_only_itself():
     srv.close()
 
 
+def test_invalid_mesh_fails_only_its_own_request():
+    """A mesh with a hole in its base level cannot be built; the wave it
+    arrived in is rebuilt without it and the other requests complete."""
+    from paper_2607_20704_gb300 import amr
+    probs, reqs = _mix()
+    good = probs[2]
+    keep = np.ones(good.n_oct, bool)
+    keep[int(np.flatnonzero(good.level == good.levelmin)[5])] = False
+    cells = np.repeat(keep, 8)
+    bad = inputs.Problem("holey", good.levelmin, good.levelmax, good.gamma, good.cfl,
+                         good.level[keep], good.i[keep], good.j[keep], good.k[keep],
+                         np.ascontiguousarray(good.U[:, cells]), {})
+    srv = amr.Server(max_waves=1)
+    ids = [srv.submit(probs[0], 3, 8), srv.submit(bad, 2, 8), srv.submit(probs[3], 2, 8)]
+    assert srv.wait(-1, timeout=120.0)
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == 2
+    with pytest.raises(amr.AmrError):
+        srv.wait(ids[1])
+    for rid, (pi, steps) in zip((ids[0], ids[2]), ((0, 3), (3, 2))):
+        want = _alone(probs[pi], steps, 8)
+        for l, (kw, Uw) in want.items():
+            assert np.array_equal(srv.read(rid, l)[1], Uw)
+    srv.close()
+
+
+def test_bad_request_arguments_are_refused():
+    from paper_2607_20704_gb300 import amr
+    srv = amr.Server()
+    prob = inputs.random_mesh(3, 4, seed=2)
+    for steps, prec in ((0, 8), (2, 2)):
+        with pytest.raises(amr.AmrError) as e:
+            srv.submit(prob, steps, prec)
+        assert e.value.status == amr.AMR_EINVAL
+    srv.close()
+
+
 def test_request_larger_than_the_budget_is_refused():
     from paper_2607_20704_gb300 import amr
     srv = amr.Server(hbm_budget_bytes=1 << 20)
