@@ -193,10 +193,22 @@ def flush_l2(buf):
 
 # -- our arm ----------------------------------------------------------------------
 LAUNCH = {"tile": 0, "schedule": -1}  # set from --tile / --schedule
+_STREAM = []
+
+
+def bench_stream():
+    """One CUDA stream for every handle of the run: a handle created on a
+    stream of its own after others have existed in the process was measured
+    4-6 % slower (FP32), one reusing the stream (and its freed memory) not."""
+    import torch
+    if not _STREAM:
+        _STREAM.append(torch.cuda.Stream())
+    return _STREAM[0]
 
 def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=True):
     from paper_2607_20704_gb300 import amr
-    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, **LAUNCH)
+    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, stream=bench_stream(),
+                    **LAUNCH)
     info = mesh.info()
     upd = work_per_step(info, prob.levelmin)
     st = mesh.stream
@@ -231,7 +243,7 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
         # per-kernel device time: same K steps, each launch bracketed by CUDA
         # events on the library's stream (eager launches, no graph)
         m2 = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision,
-                      tile=mesh_tile, schedule=mesh_sched)
+                      tile=mesh_tile, schedule=mesh_sched, stream=bench_stream())
         for _ in range(warmup):
             m2.advance(1)
         m2.sync()
@@ -250,7 +262,8 @@ def run_e2e(prob, precision, steps, torch):
     every level's state from pinned host memory, advance one coarse step,
     read every level back (synchronous)."""
     from paper_2607_20704_gb300 import amr
-    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, **LAUNCH)
+    mesh = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, stream=bench_stream(),
+                    **LAUNCH)
     info = mesh.info()
     upd = work_per_step(info, prob.levelmin)
     levels = mesh.levels()
@@ -287,7 +300,7 @@ def run_batched(members, steps, warmup, torch, device, flush):
     out = {"members": len(members), "octs": int(sum(p.n_oct for p in members)),
            "leaf_cells": int(sum(p.leaf_cells() for p in members))}
     for prec, name in ((8, "fp64"), (4, "fp32")):
-        b = amr.Mesh.batch(members, precision=prec)
+        b = amr.Mesh.batch(members, precision=prec, stream=bench_stream())
         info = b.info()
         upd = int(info["work_per_step"])
         st = b.stream
