@@ -56,6 +56,11 @@ class _Params(C.Structure):
                 ("reflux", C.c_int)]
 
 
+class _RegridParams(C.Structure):
+    _fields_ = [("grad_rho", C.c_double), ("grad_p", C.c_double), ("mass", C.c_double),
+                ("expand", C.c_int)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -88,6 +93,9 @@ def lib():
                 "orc_uniform_step": (I, [I, P, D, D, D, D]),
                 "orc_uniform_cfl_dt": (D, [I, P, D, D, D, D]),
                 "orc_1d_step": (I, [I, P, D, D, D, D]),
+                "orc_flags": (I, [P, C.POINTER(_RegridParams), P]),
+                "orc_regrid": (I, [C.POINTER(P), C.POINTER(_RegridParams), C.POINTER(I64),
+                                   C.POINTER(I64)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -232,6 +240,34 @@ class Mesh:
         if rc:
             raise OracleError(rc, "advance")
         return dt.value
+
+    # -- regrid (Sec. 2.2) ------------------------------------------------------
+    def flags(self, grad_rho=0.1, grad_p=0.1, mass=0.0, expand=1):
+        """Final refinement flags [8n] in mesh order (all levels)."""
+        rp = _RegridParams(grad_rho, grad_p, mass, int(expand))
+        n = int(sum(self.num_octs(l) for l in range(16)))
+        out = np.zeros(8 * max(n, 1), np.uint8)
+        rc = lib().orc_flags(self._h, C.byref(rp), _ptr(out))
+        if rc:
+            raise OracleError(rc, "flags")
+        return out[:8 * n]
+
+    def level_flags(self, level, **kw):
+        """Final flags of the cells of one level, [8 n_level]."""
+        f = self.flags(**kw)
+        a = self.level_offset(level)
+        return f[8 * a: 8 * (a + self.num_octs(level))]
+
+    def regrid(self, grad_rho=0.1, grad_p=0.1, mass=0.0, expand=1):
+        """Regrid in place; returns (octs created, octs removed)."""
+        rp = _RegridParams(grad_rho, grad_p, mass, int(expand))
+        h = C.c_void_p(self._h.value if isinstance(self._h, C.c_void_p) else self._h)
+        cr, rm = C.c_int64(), C.c_int64()
+        rc = lib().orc_regrid(C.byref(h), C.byref(rp), C.byref(cr), C.byref(rm))
+        if rc:
+            raise OracleError(rc, "regrid")
+        self._h = h
+        return cr.value, rm.value
 
     def levels(self):
         return [l for l in range(self.levelmin, self.levelmax + 1) if self.num_octs(l) > 0]

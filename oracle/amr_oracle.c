@@ -1036,3 +1036,282 @@ int orc_1d_step(int n, double *U, double gamma, double dt, double smallr, double
   free(W); free(WS); free(DW); free(F);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* regrid (Sec. 2.2 "Refinement and De-Refinement")                          */
+/*                                                                           */
+/* The paper names the four stages (refine flagged cells by new child octs,  */
+/* remove the child oct of a split cell no longer flagged, level bucket sort,*/
+/* Hilbert sort) and leaves the criterion and the grading closure to the    */
+/* RAMSES conventions; the readings taken here:                             */
+/*   flag   a cell of level l < levelmax is flagged when, to one of its six  */
+/*          face neighbours (the same-level cell, else the coarser cell      */
+/*          covering it), the relative jump 2|a-b|/(|a|+|b|) of rho exceeds  */
+/*          grad_rho or that of p exceeds grad_p, or when rho dx_l^3 exceeds */
+/*          mass;                                                            */
+/*   expand with expand = 1 a flag also flags the 26 same-level cells       */
+/*          around it that exist;                                            */
+/*   grade  finest level first: a flagged cell X of level l flags, at level  */
+/*          l-1, the cell covering each of the 27 level-l cells around X, so */
+/*          the child oct of X has its 27 level-l neighbours (the 2:1 rule)  */
+/*          and the keep rule follows (X's own father is among them);       */
+/*   split  in the new mesh the flagged cells are the split ones: children  */
+/*          of flagged leaves are created, those of unflagged split cells   */
+/*          are removed, so a cell refines by at most one level per regrid;  */
+/*   state  new child octs, coarsest level first, are minmod prolongations  */
+/*          of their father from the father's six face neighbours in the new */
+/*          mesh (the ghost-oct formula); then the mesh is rebuilt as at     */
+/*          creation (order, lookup, grading check, cache, restriction).     */
+/* ------------------------------------------------------------------------- */
+
+static double rel_jump(double a, double b) {
+  double s = fabs(a) + fabs(b);
+  return s > 0.0 ? 2.0 * fabs(a - b) / s : 0.0;
+}
+
+/* oct index of the cell (x,y,z) of level L (same level only), or -1 */
+static int64_t cell_oct(const orc_mesh *m, int L, int64_t x, int64_t y, int64_t z, int *c) {
+  int64_t side = (int64_t)1 << L;
+  uint32_t X = wrap(x, side), Y = wrap(y, side), Z = wrap(z, side);
+  *c = (int)((X & 1) + 2 * (Y & 1) + 4 * (Z & 1));
+  return orc_lookup(m, orc_pack_key(L, X >> 1, Y >> 1, Z >> 1));
+}
+
+static int raw_flag(const orc_mesh *m, const phys *ph, const orc_regrid_params *rp, int64_t o,
+                    int c) {
+  int64_t N8 = 8 * m->n;
+  int l = m->lvl[o];
+  double uc[NV], wc[NV];
+  for (int v = 0; v < NV; ++v) uc[v] = m->U[v * N8 + 8 * o + c];
+  if (rp->mass > 0.0 && ldexp(uc[0], -3 * l) > rp->mass) return 1;
+  if (!(rp->grad_rho > 0.0) && !(rp->grad_p > 0.0)) return 0;
+  cons_to_prim(ph, uc, wc);
+  int64_t x = 2 * (int64_t)m->ci[o] + (c & 1), y = 2 * (int64_t)m->cj[o] + ((c >> 1) & 1),
+          z = 2 * (int64_t)m->ck[o] + ((c >> 2) & 1);
+  for (int d = 0; d < 3; ++d)
+    for (int s = -1; s <= 1; s += 2) {
+      double un[NV], wn[NV];
+      if (cell_value(m, l, x + (d == 0) * s, y + (d == 1) * s, z + (d == 2) * s, un)) continue;
+      cons_to_prim(ph, un, wn);
+      if (rp->grad_rho > 0.0 && rel_jump(wn[0], wc[0]) > rp->grad_rho) return 1;
+      if (rp->grad_p > 0.0 && rel_jump(wn[4], wc[4]) > rp->grad_p) return 1;
+    }
+  return 0;
+}
+
+int orc_flags(const orc_mesh *m, const orc_regrid_params *rp, uint8_t *flag) {
+  const phys ph = make_phys(&m->p);
+  int64_t n8 = 8 * m->n;
+  uint8_t *raw = (uint8_t *)calloc((size_t)n8 + 1, 1);
+  if (!raw) return ORC_ENOMEM;
+  memset(flag, 0, (size_t)n8);
+  for (int64_t o = 0; o < m->n; ++o) {
+    if (m->lvl[o] >= m->p.levelmax) continue;
+    for (int c = 0; c < 8; ++c) raw[8 * o + c] = (uint8_t)raw_flag(m, &ph, rp, o, c);
+  }
+  /* expansion over the 3x3x3 same-level block */
+  for (int64_t o = 0; o < m->n; ++o) {
+    int l = m->lvl[o];
+    if (l >= m->p.levelmax) continue;
+    for (int c = 0; c < 8; ++c) {
+      int64_t x = 2 * (int64_t)m->ci[o] + (c & 1), y = 2 * (int64_t)m->cj[o] + ((c >> 1) & 1),
+              z = 2 * (int64_t)m->ck[o] + ((c >> 2) & 1);
+      int f = raw[8 * o + c];
+      if (rp->expand)
+        for (int dz = -1; dz <= 1 && !f; ++dz)
+          for (int dy = -1; dy <= 1 && !f; ++dy)
+            for (int dx = -1; dx <= 1 && !f; ++dx) {
+              int cc;
+              int64_t e = cell_oct(m, l, x + dx, y + dy, z + dz, &cc);
+              if (e >= 0 && raw[8 * e + cc]) f = 1;
+            }
+      flag[8 * o + c] = (uint8_t)f;
+    }
+  }
+  free(raw);
+  /* grading closure, finest level first */
+  for (int l = m->p.levelmax - 1; l > m->p.levelmin; --l) {
+    for (int64_t o = m->lo[l]; o < m->lo[l + 1]; ++o)
+      for (int c = 0; c < 8; ++c) {
+        if (!flag[8 * o + c]) continue;
+        int64_t x = 2 * (int64_t)m->ci[o] + (c & 1), y = 2 * (int64_t)m->cj[o] + ((c >> 1) & 1),
+                z = 2 * (int64_t)m->ck[o] + ((c >> 2) & 1);
+        int64_t side = (int64_t)1 << l;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              /* the level-(l-1) cell covering the level-l cell around X */
+              int64_t X = wrap(x + dx, side), Y = wrap(y + dy, side), Z = wrap(z + dz, side);
+              int cc;
+              int64_t e = cell_oct(m, l - 1, X >> 1, Y >> 1, Z >> 1, &cc);
+              if (e < 0) return ORC_EGRADING;
+              flag[8 * e + cc] = 1;
+            }
+      }
+  }
+  return ORC_OK;
+}
+
+/* states of the new child octs of one level, coarsest level first: values
+ * at level L are read from the old mesh where the oct is kept, else from the
+ * new octs of level L created before */
+typedef struct {
+  int64_t n;
+  uint64_t *key; /* ascending */
+  double *U;     /* [n][8][NV] */
+} new_level;
+
+static int new_cell_value(const orc_mesh *m, const new_level *nl, int L, int64_t x, int64_t y,
+                          int64_t z, double u[NV]) {
+  int c;
+  int64_t o = cell_oct(m, L, x, y, z, &c);
+  if (o >= 0) {
+    for (int v = 0; v < NV; ++v) u[v] = m->U[v * 8 * m->n + 8 * o + c];
+    return 0;
+  }
+  int64_t side = (int64_t)1 << L;
+  uint64_t k = orc_pack_key(L, wrap(x, side) >> 1, wrap(y, side) >> 1, wrap(z, side) >> 1);
+  int64_t a = 0, b = nl[L].n;
+  while (a < b) {
+    int64_t h = a + (b - a) / 2;
+    if (nl[L].key[h] < k)
+      a = h + 1;
+    else
+      b = h;
+  }
+  if (a >= nl[L].n || nl[L].key[a] != k) return 1;
+  for (int v = 0; v < NV; ++v) u[v] = nl[L].U[(8 * a + c) * NV + v];
+  return 0;
+}
+
+int orc_regrid(orc_mesh **pm, const orc_regrid_params *rp, int64_t *created, int64_t *removed) {
+  orc_mesh *m = *pm;
+  const int64_t n = m->n, n8 = 8 * n;
+  const int lmin = m->p.levelmin, lmax = m->p.levelmax;
+  uint8_t *flag = (uint8_t *)malloc((size_t)n8 + 1);
+  if (!flag) return ORC_ENOMEM;
+  int e = orc_flags(m, rp, flag);
+  if (e) {
+    free(flag);
+    return e;
+  }
+  /* octs of the new mesh: the base level, and the children of flagged cells;
+   * an old oct of level l > levelmin is kept when its father is flagged */
+  int64_t kept = 0, ncreate = 0, nremove = 0;
+  uint8_t *keep = (uint8_t *)calloc((size_t)n + 1, 1);
+  new_level nl[ORC_MAXLEV + 1];
+  memset(nl, 0, sizeof nl);
+  if (!keep) {
+    free(flag);
+    return ORC_ENOMEM;
+  }
+  for (int64_t o = 0; o < n; ++o) {
+    int l = m->lvl[o];
+    int k = 1;
+    if (l > lmin) {
+      int c;
+      int64_t f = cell_oct(m, l - 1, m->ci[o], m->cj[o], m->ck[o], &c);
+      k = f >= 0 && flag[8 * f + c];
+    }
+    keep[o] = (uint8_t)k;
+    kept += k;
+    nremove += !k;
+  }
+  for (int l = lmin + 1; l <= lmax; ++l) {
+    /* flagged leaves of level l-1 whose child oct of level l is new */
+    int64_t cnt = 0;
+    for (int64_t o = m->lo[l - 1]; o < m->lo[l]; ++o)
+      for (int c = 0; c < 8; ++c)
+        if (flag[8 * o + c] && !m->split[8 * o + c]) ++cnt;
+    nl[l].n = cnt;
+    nl[l].key = (uint64_t *)malloc(sizeof(uint64_t) * (cnt ? cnt : 1));
+    nl[l].U = (double *)malloc(sizeof(double) * NV * 8 * (cnt ? cnt : 1));
+    if (!nl[l].key || !nl[l].U) {
+      e = ORC_ENOMEM;
+      goto done;
+    }
+    cnt = 0;
+    for (int64_t o = m->lo[l - 1]; o < m->lo[l]; ++o)
+      for (int c = 0; c < 8; ++c)
+        if (flag[8 * o + c] && !m->split[8 * o + c])
+          nl[l].key[cnt++] = orc_pack_key(l, 2 * m->ci[o] + (c & 1), 2 * m->cj[o] + ((c >> 1) & 1),
+                                          2 * m->ck[o] + ((c >> 2) & 1));
+    qsort(nl[l].key, (size_t)cnt, sizeof(uint64_t), cmp_u64);
+    ncreate += cnt;
+    /* prolongation of the father cell (level l-1) of each new oct */
+    for (int64_t t = 0; t < cnt; ++t) {
+      int64_t gi = key_i(nl[l].key[t]), gj = key_j(nl[l].key[t]), gk = key_k(nl[l].key[t]);
+      double uc[NV], up[NV], um[NV], sl[3][NV];
+      if (new_cell_value(m, nl, l - 1, gi, gj, gk, uc)) {
+        e = ORC_EGRADING;
+        goto done;
+      }
+      for (int d = 0; d < 3; ++d) {
+        int64_t ex = d == 0, ey = d == 1, ez = d == 2;
+        if (new_cell_value(m, nl, l - 1, gi + ex, gj + ey, gk + ez, up) ||
+            new_cell_value(m, nl, l - 1, gi - ex, gj - ey, gk - ez, um)) {
+          e = ORC_EGRADING;
+          goto done;
+        }
+        for (int v = 0; v < NV; ++v) sl[d][v] = minmod(up[v] - uc[v], uc[v] - um[v]);
+      }
+      for (int c = 0; c < 8; ++c) {
+        double hx = (c & 1) ? 0.25 : -0.25;
+        double hy = (c & 2) ? 0.25 : -0.25;
+        double hz = (c & 4) ? 0.25 : -0.25;
+        for (int v = 0; v < NV; ++v)
+          nl[l].U[(8 * t + c) * NV + v] = ((uc[v] + hx * sl[0][v]) + hy * sl[1][v]) + hz * sl[2][v];
+      }
+    }
+  }
+  {
+    int64_t nn = kept + ncreate, t = 0;
+    uint8_t *lv = (uint8_t *)malloc(nn ? nn : 1);
+    uint32_t *ii = (uint32_t *)malloc(sizeof(uint32_t) * (nn ? nn : 1));
+    uint32_t *jj = (uint32_t *)malloc(sizeof(uint32_t) * (nn ? nn : 1));
+    uint32_t *kk = (uint32_t *)malloc(sizeof(uint32_t) * (nn ? nn : 1));
+    double *U = (double *)malloc(sizeof(double) * NV * 8 * (nn ? nn : 1));
+    if (!lv || !ii || !jj || !kk || !U) {
+      free(lv); free(ii); free(jj); free(kk); free(U);
+      e = ORC_ENOMEM;
+      goto done;
+    }
+    for (int64_t o = 0; o < n; ++o) {
+      if (!keep[o]) continue;
+      lv[t] = m->lvl[o];
+      ii[t] = m->ci[o];
+      jj[t] = m->cj[o];
+      kk[t] = m->ck[o];
+      for (int v = 0; v < NV; ++v)
+        for (int c = 0; c < 8; ++c) U[v * 8 * nn + 8 * t + c] = m->U[v * n8 + 8 * o + c];
+      ++t;
+    }
+    for (int l = lmin + 1; l <= lmax; ++l)
+      for (int64_t q = 0; q < nl[l].n; ++q) {
+        lv[t] = (uint8_t)l;
+        ii[t] = key_i(nl[l].key[q]);
+        jj[t] = key_j(nl[l].key[q]);
+        kk[t] = key_k(nl[l].key[q]);
+        for (int v = 0; v < NV; ++v)
+          for (int c = 0; c < 8; ++c) U[v * 8 * nn + 8 * t + c] = nl[l].U[(8 * q + c) * NV + v];
+        ++t;
+      }
+    orc_mesh *out = NULL;
+    e = orc_create(&m->p, nn, lv, ii, jj, kk, U, &out);
+    free(lv); free(ii); free(jj); free(kk); free(U);
+    if (!e) {
+      orc_destroy(m);
+      *pm = out;
+      if (created) *created = ncreate;
+      if (removed) *removed = nremove;
+    }
+  }
+done:
+  for (int l = 0; l <= ORC_MAXLEV; ++l) {
+    free(nl[l].key);
+    free(nl[l].U);
+  }
+  free(keep);
+  free(flag);
+  return e;
+}

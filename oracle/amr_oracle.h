@@ -79,6 +79,26 @@ int orc_step_sample(orc_mesh *m, int level, double dt, int64_t ns,
                     const int64_t *octs, double *Unew);
 int orc_advance(orc_mesh *m, int nsteps, double *dt_last);
 
+/* --- regrid (Sec. 2.2: refinement, de-refinement, level and Hilbert order;
+ *     then the ghost cache of Sec. 2.3) ------------------------------------- */
+typedef struct {
+  double grad_rho; /* relative jump 2|a-b|/(|a|+|b|) of rho to a face neighbour; <= 0: off */
+  double grad_p;   /* the same for the pressure; <= 0: off */
+  double mass;     /* cell mass rho dx^3 above which a cell refines; <= 0: off */
+  int expand;      /* 1: a flag also flags the 26 same-level neighbours */
+} orc_regrid_params;
+
+/* Final refinement flags of every cell of the mesh (flag[8*oct + c], mesh
+ * order): criterion, expansion, then the grading closure, finest level
+ * first.  A flagged cell is split in the regridded mesh. */
+int orc_flags(const orc_mesh *m, const orc_regrid_params *rp, uint8_t *flag);
+/* Replace *pm by the regridded mesh: flagged leaves get a child oct whose
+ * cells are minmod prolongations of their father, split cells left unflagged
+ * lose their child oct, and the mesh is rebuilt in (level, Hilbert) order.
+ * Pending reflux is dropped (regrid runs between coarse steps, where it is
+ * zero).  created/removed: numbers of octs (may be NULL). */
+int orc_regrid(orc_mesh **pm, const orc_regrid_params *rp, int64_t *created, int64_t *removed);
+
 /* --- independent cross-check solvers ----------------------------------------- */
 int orc_uniform_step(int n, double *U, double gamma, double dt, double smallr,
                      double smallc);
