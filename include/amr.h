@@ -62,8 +62,10 @@ typedef struct {
   double gamma;             /* ratio of specific heats, > 1 */
   double cfl;               /* Courant number of amr_cfl_dt */
   double smallr, smallc;    /* floors: rho >= smallr, p >= rho smallc^2 / gamma */
-  /* refinement thresholds of the regrid stage; stored, not used while the
-   * mesh is static */
+  /* refinement criteria of amr_regrid (Sec. 2.2): a cell refines when the
+   * relative jump 2|a-b|/(|a|+|b|) of rho (of p) to a face neighbour exceeds
+   * refine_grad_rho (refine_grad_p), or when its mass rho dx^3 exceeds
+   * refine_mass; a criterion <= 0 is off */
   double refine_grad_rho, refine_grad_p, refine_mass;
   int precision;            /* 8: FP64 state and arithmetic; 4: FP32 state and
                                arithmetic, FP64 time-step reduction */
@@ -83,12 +85,18 @@ typedef struct {
                                0: autotune at the first amr_advance (default) */
   int schedule;             /* 1: persistent grids sized by occupancy x SMs;
                                0: one tile per block; -1: autotune (default) */
+  int regrid_expand;        /* 1: a refinement flag also flags the 26 cells
+                               around it (default); 0: off */
+  int regrid_every_step;    /* 1: amr_advance regrids before every coarse
+                               step; 0: the mesh only changes by amr_regrid
+                               (default) */
 } amr_params;
 
 /* Fills p with the defaults: levelmin = levelmax = 1, gamma = 1.4, cfl = 0.8,
  * smallr = smallc = 1e-10, precision 8, reflux 1, reindex_every_step 1,
  * use_graphs 1, no budget, NULL stream and allocator, tile 0 and schedule -1
- * (both picked by the autotuner). */
+ * (both picked by the autotuner), refinement criteria off, regrid_expand 1,
+ * regrid_every_step 0. */
 void amr_params_default(amr_params *p);
 
 /*
@@ -160,6 +168,34 @@ amr_status amr_member_errors(amr_handle h, int32_t *errs, int n);
 /* The last coarse time step of every member (from amr_cfl_dt or
  * amr_advance), copied into dt_out[0..n_members) (synchronous). */
 amr_status amr_member_dt(amr_handle h, double *dt_out, int n);
+
+/*
+ * amr_regrid -- one regrid of the mesh (Sec. 2.2, then the ghost cache of
+ * Sec. 2.3).  With the criteria of the handle's amr_params:
+ *   flag    cells of level l < levelmax meeting a criterion; the face
+ *           neighbour is the same-level cell, else the coarser cell covering
+ *           it; decided in FP64 with every operation rounded as written
+ *   expand  (regrid_expand) also the 26 same-level cells around a flag
+ *   grade   finest level first, a flagged cell of level l flags the level
+ *           l-1 cells covering its 27 level-l neighbours (2:1 rule)
+ * then flagged leaves get a child oct (minmod prolongation of the father
+ * from its six face neighbours, coarsest level first), split cells left
+ * unflagged lose their child oct, and the mesh is rebuilt as by amr_create
+ * (level bucket sort, Hilbert radix sort, hash, index, cache, restriction).
+ * A cell refines by at most one level per call.  Call between coarse steps
+ * (pending reflux, zero there, is dropped).  Device buffers are replaced:
+ * pointers from earlier calls are invalid, a captured graph is re-captured.
+ * created/removed (may be NULL): octs added and removed; both 0 leaves the
+ * handle untouched.  Synchronous.  Errors: AMR_ENOMEM, AMR_EINVAL (more than
+ * 2^26 octs would result), AMR_ECUDA.
+ */
+amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *removed);
+
+/* Refinement flags of the selected member's cells of one level after the
+ * flag, expand and grade stages of amr_regrid, without changing the mesh:
+ * flags[8 * n + c] = 1 for cell c of the n-th oct (amr_read order); cap >=
+ * 8 * octs of the level.  Synchronous. */
+amr_status amr_flag(amr_handle h, int level, uint8_t *flags, int64_t cap);
 
 /* Frees every device buffer of the handle (after synchronising its stream). */
 amr_status amr_destroy(amr_handle h);

@@ -38,7 +38,8 @@ class amr_params(C.Structure):
                 ("reindex_every_step", C.c_int), ("use_graphs", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("tile", C.c_int), ("schedule", C.c_int)]
+                ("tile", C.c_int), ("schedule", C.c_int),
+                ("regrid_expand", C.c_int), ("regrid_every_step", C.c_int)]
 
 
 class amr_info(C.Structure):
@@ -95,7 +96,7 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_lookup", "amr_read_index", "amr_read_cache", "amr_fill_ghosts", "amr_get_info",
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
-           "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_server_create", "amr_server_submit",
+           "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag", "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
            "amr_server_destroy"]
 
@@ -143,6 +144,8 @@ def load(path: str | None = None):
             "amr_member_dt": (I, [P, P, I]),
             "amr_set_member_steps": (I, [P, P, I]),
             "amr_member_errors": (I, [P, P, I]),
+            "amr_regrid": (I, [P, P, P]),
+            "amr_flag": (I, [P, I, P, I64]),
             "amr_server_create": (I, [C.POINTER(amr_server_params), C.POINTER(P)]),
             "amr_server_submit": (I, [P, C.POINTER(amr_request), C.POINTER(I64)]),
             "amr_server_wait": (I, [P, I64, D, C.POINTER(I)]),
@@ -214,7 +217,8 @@ class Mesh:
                  gamma=1.4, cfl=0.8, smallr=1e-10, smallc=1e-10, precision=8, reflux=True,
                  reindex_every_step=True, use_graphs=True, hbm_budget_bytes=0,
                  hilbert_key=None, allocator="torch", stream=None, members=None, tile=0,
-                 schedule=-1):
+                 schedule=-1, refine_grad_rho=0.0, refine_grad_p=0.0, refine_mass=0.0,
+                 regrid_expand=True, regrid_every_step=False):
         torch = _torch()
         L = load()
         p = amr_params()
@@ -227,6 +231,10 @@ class Mesh:
         p.use_graphs = int(bool(use_graphs))
         p.hbm_budget_bytes = int(hbm_budget_bytes)
         p.tile, p.schedule = int(tile), int(schedule)
+        p.refine_grad_rho, p.refine_grad_p = float(refine_grad_rho), float(refine_grad_p)
+        p.refine_mass = float(refine_mass)
+        p.regrid_expand = int(bool(regrid_expand))
+        p.regrid_every_step = int(bool(regrid_every_step))
         self.stream = stream if stream is not None else torch.cuda.Stream()
         p.stream = C.c_void_p(self.stream.cuda_stream)
         if allocator == "torch":
@@ -288,6 +296,20 @@ class Mesh:
         """Coarse steps each member still takes (-1: unlimited)."""
         st = np.ascontiguousarray(steps, dtype=np.int32)
         _check(load().amr_set_member_steps(self._h, _ptr(st), len(st)), "amr_set_member_steps")
+
+    def regrid(self):
+        """One regrid (Sec. 2.2) with the handle's criteria; returns
+        (octs created, octs removed)."""
+        cr, rm = C.c_int64(), C.c_int64()
+        _check(load().amr_regrid(self._h, C.byref(cr), C.byref(rm)), "amr_regrid")
+        return cr.value, rm.value
+
+    def flags(self, level: int):
+        """Refinement flags [8 n_level] of the selected member's level."""
+        n = self.num_octs(level)
+        out = np.zeros(8 * max(n, 1), np.uint8)
+        _check(load().amr_flag(self._h, int(level), _ptr(out), 8 * max(n, 1)), "amr_flag")
+        return out[:8 * n]
 
     def member_errors(self):
         """Per-member flags (1: a leaf state was not finite); clears the

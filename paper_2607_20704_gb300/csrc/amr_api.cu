@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "hydro_kernels.cuh"
+#include "regrid_kernels.cuh"
 #include "index_kernels.cuh"
 
 using namespace amr;
@@ -78,13 +79,13 @@ enum Kid {
   K_SORT_KEYS, K_RADIX_HIST, K_RADIX_SCATTER, K_SCAN, K_GATHER, K_HASH_INSERT, K_FATHER_SON,
   K_GRADING, K_NEIGHBOURS, K_CLAIM, K_CACHE_FINALIZE, K_NBR_FIX, K_FACES, K_CACHE_SOURCES,
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
-  K_CONVERT, K_COUNT
+  K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
     "father_son", "grading", "neighbours", "claim_comp", "cache_finalize", "neighbours_fix",
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
-    "reflux", "reflux_restrict", "cfl", "dt", "convert"};
+    "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -671,6 +672,8 @@ extern "C" void amr_params_default(amr_params *p) {
   p->reflux = 1;
   p->reindex_every_step = 1;
   p->use_graphs = 1;
+  p->regrid_expand = 1;
+  p->regrid_every_step = 0;
 }
 
 static void destroy_all(amr_mesh *h) {
@@ -710,8 +713,35 @@ static amr_status upload_member_params(amr_mesh *h) {
   return AMR_OK;
 }
 
+// member parameters on the device (from h->mem)
+static amr_status upload_members(amr_mesh *h) {
+  const int M = h->M;
+  std::vector<int> lmin(M), lmax(M);
+  std::vector<double> g(M), cfl(M), sr(M), sp(M);
+  for (int q = 0; q < M; ++q) {
+    const Member &m = h->mem[q];
+    lmin[q] = m.lmin;
+    lmax[q] = m.lmax;
+    g[q] = m.gamma;
+    cfl[q] = m.cfl;
+    sr[q] = m.smallr;
+    sp[q] = m.smallc * m.smallc / m.gamma;
+  }
+  AMR_TRY(upload(h, &h->mlmin, lmin));
+  AMR_TRY(upload(h, &h->mlmax, lmax));
+  AMR_TRY(upload(h, &h->mgamma_d, g));
+  AMR_TRY(upload(h, &h->mcfl_d, cfl));
+  AMR_TRY(upload(h, &h->msmallr_d, sr));
+  AMR_TRY(upload(h, &h->msmallp_d, sp));
+  if (h->p.precision == 4) return upload_member_params<float>(h);
+  return upload_member_params<double>(h);
+}
+
+static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
+                             uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
+                             double *d_U, uint8_t *d_new);
+
 static amr_status create_impl(amr_mesh *h, const amr_member *members) {
-  const amr_params &p = h->p;
   const int M = h->M;
   // --- members and host staging of the concatenated oct list ------------------
   int64_t n = 0;
@@ -755,35 +785,12 @@ static amr_status create_impl(amr_mesh *h, const amr_member *members) {
     }
   }
   h->N = n;
-  // --- member parameters on the device -----------------------------------------
-  {
-    std::vector<int> lmin(M), lmax(M);
-    std::vector<double> g(M), cfl(M), sr(M), sp(M);
-    for (int q = 0; q < M; ++q) {
-      const Member &m = h->mem[q];
-      lmin[q] = m.lmin;
-      lmax[q] = m.lmax;
-      g[q] = m.gamma;
-      cfl[q] = m.cfl;
-      sr[q] = m.smallr;
-      sp[q] = m.smallc * m.smallc / m.gamma;
-    }
-    AMR_TRY(upload(h, &h->mlmin, lmin));
-    AMR_TRY(upload(h, &h->mlmax, lmax));
-    AMR_TRY(upload(h, &h->mgamma_d, g));
-    AMR_TRY(upload(h, &h->mcfl_d, cfl));
-    AMR_TRY(upload(h, &h->msmallr_d, sr));
-    AMR_TRY(upload(h, &h->msmallp_d, sp));
-    if (p.precision == 4)
-      AMR_TRY(upload_member_params<float>(h));
-    else
-      AMR_TRY(upload_member_params<double>(h));
-  }
+  AMR_TRY(upload_members(h));
   // --- inputs to the device ------------------------------------------------------
   uint8_t *d_lvl;
   uint16_t *d_mem;
-  uint32_t *d_i, *d_j, *d_k, *perm, *perm_alt;
-  uint64_t *d_hk = nullptr, *comp, *comp_alt;
+  uint32_t *d_i, *d_j, *d_k;
+  uint64_t *d_hk = nullptr;
   double *d_U;
   AMR_TRY(upload(h, &d_lvl, lv));
   AMR_TRY(upload(h, &d_mem, mm));
@@ -792,6 +799,21 @@ static amr_status create_impl(amr_mesh *h, const amr_member *members) {
   AMR_TRY(upload(h, &d_k, ck));
   AMR_TRY(upload(h, &d_U, U));
   if (have_hk) AMR_TRY(upload(h, &d_hk, hk));
+  return build_mesh(h, n, have_hk != 0, d_lvl, d_mem, d_i, d_j, d_k, d_hk, d_U, nullptr);
+}
+
+// The mesh from device-resident inputs in any order (create and regrid):
+// order, hash, index, ghost cache, state, lists, scratch; d_new marks octs
+// whose state is to be prolonged from their father (regrid), before the
+// restriction.  Frees the inputs.
+static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
+                             uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
+                             double *d_U, uint8_t *d_new) {
+  const amr_params &p = h->p;
+  const int M = h->M;
+  h->N = n;
+  uint32_t *perm, *perm_alt;
+  uint64_t *comp, *comp_alt;
   AMR_TRY(alloc_n(h, &perm, n));
   AMR_TRY(alloc_n(h, &perm_alt, n));
   AMR_TRY(alloc_n(h, &comp, n));
@@ -971,6 +993,29 @@ static amr_status create_impl(amr_mesh *h, const amr_member *members) {
   CUDA_TRY(cudaMemsetAsync(h->merr, 0, sizeof(int) * M, h->s));
   CUDA_TRY(cudaMemsetAsync(h->mrem, 0xFF, sizeof(int) * M, h->s));  // -1: unlimited
   CUDA_TRY(cudaMemsetAsync(h->mact, 0, sizeof(int) * M, h->s));
+
+  // regrid: new octs take the prolongation of their father, coarsest first
+  if (d_new) {
+    uint8_t *isnew = nullptr;
+    AMR_TRY(alloc_n(h, &isnew, n));
+    launch(h, K_REGRID, k_gather_u8, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
+           (const uint8_t *)d_new, n, isnew);
+    for (auto &m : h->mem)
+      for (int l = m.lmin + 1; l <= m.lmax; ++l) {
+        const int lo = int(m.oct_base + m.lo[l]), hi = int(m.oct_base + m.lo[l + 1]);
+        if (hi <= lo) continue;
+        if (p.precision == 4)
+          launch(h, K_PROLONG_NEW, k_prolong_new<float>, dim3(nblocks(hi - lo)), dim3(256), int(n),
+                 int(h->NE), h->S, (const uint64_t *)h->key, (const int32_t *)h->father,
+                 (const int32_t *)h->fnb, (const uint8_t *)isnew, (float *)h->U, lo, hi, h->err);
+        else
+          launch(h, K_PROLONG_NEW, k_prolong_new<double>, dim3(nblocks(hi - lo)), dim3(256), int(n),
+                 int(h->NE), h->S, (const uint64_t *)h->key, (const int32_t *)h->father,
+                 (const int32_t *)h->fnb, (const uint8_t *)isnew, (double *)h->U, lo, hi, h->err);
+      }
+    dev_free(h, isnew);
+    dev_free(h, d_new);
+  }
 
   // split cells carry the mean of their children, finest level first
   for (int l = kMaxLev; l >= 1; --l) {
@@ -1226,11 +1271,12 @@ extern "C" amr_status amr_advance(amr_handle h, int n, double *dt_last) {
   if (n < 0) return fail(AMR_EINVAL, "amr_advance: n must be >= 0");
   if (!h->tuned && n > 0) AMR_TRY(autotune(h));
   const bool graphs = h->p.use_graphs && !h->timing;
-  if (graphs && !h->graph && n > 0) {
-    AMR_TRY(capture_coarse_step(h, &h->graph));
-    h->graph_kernels = h->capture_kernels;
-  }
   for (int t = 0; t < n; ++t) {
+    if (h->p.regrid_every_step) AMR_TRY(amr_regrid(h, nullptr, nullptr));
+    if (graphs && !h->graph) {
+      AMR_TRY(capture_coarse_step(h, &h->graph));
+      h->graph_kernels = h->capture_kernels;
+    }
     if (graphs) {
       CUDA_TRY(cudaGraphLaunch(h->graph, h->s));
       h->graph_launches++;
@@ -1295,6 +1341,204 @@ extern "C" amr_status amr_member_errors(amr_handle h, int32_t *errs, int n) {
     errs[q] = v;
   }
   return AMR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// regrid (Sec. 2.2)
+// ---------------------------------------------------------------------------
+static RegridArgs regrid_args(amr_mesh *h, uint32_t *raw, uint32_t *flag) {
+  RegridArgs a{};
+  a.N = int(h->N);
+  a.NE = int(h->NE);
+  a.NC = int(h->NC);
+  a.S = h->S;
+  a.key = h->key;
+  a.son = h->son;
+  a.father = h->father;
+  a.nbr27 = h->nbr27;
+  a.fnb = h->fnb;
+  a.csrc = h->csrc;
+  a.mlmin = h->mlmin;
+  a.mlmax = h->mlmax;
+  a.mgamma = h->mgamma_d;
+  a.msmallr = h->msmallr_d;
+  a.msmallp = h->msmallp_d;
+  a.grad_rho = h->p.refine_grad_rho;
+  a.grad_p = h->p.refine_grad_p;
+  a.mass = h->p.refine_mass;
+  a.expand = h->p.regrid_expand ? 1 : 0;
+  a.raw = raw;
+  a.flag = flag;
+  a.err = h->err;
+  return a;
+}
+
+// flag, expand and grade: final masks in flag[N]
+static amr_status compute_flags(amr_mesh *h, uint32_t *raw, uint32_t *flag, const char *where) {
+  const RegridArgs a = regrid_args(h, raw, flag);
+  const unsigned g = nblocks(h->N);
+  if (h->p.precision == 4)
+    launch(h, K_FLAG, k_flag_raw<float>, dim3(g), dim3(256), a, (const float *)h->U);
+  else
+    launch(h, K_FLAG, k_flag_raw<double>, dim3(g), dim3(256), a, (const double *)h->U);
+  launch(h, K_FLAG, k_flag_expand, dim3(g), dim3(256), a);
+  for (auto &m : h->mem)
+    for (int l = m.lmax - 1; l > m.lmin; --l) {
+      const int lo = int(m.oct_base + m.lo[l]), hi = int(m.oct_base + m.lo[l + 1]);
+      if (hi > lo) launch(h, K_FLAG, k_flag_grade, dim3(nblocks(hi - lo)), dim3(256), a, lo, hi);
+    }
+  return check_device(h, where);
+}
+
+extern "C" amr_status amr_flag(amr_handle h, int level, uint8_t *flags, int64_t cap) {
+  if (!h || !flags) return fail(AMR_EINVAL, "amr_flag: NULL argument");
+  if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_flag: level out of range");
+  const Member &m = h->mem[h->sel];
+  const int64_t lo = m.oct_base + m.lo[level], nl = m.lo[level + 1] - m.lo[level];
+  if (cap < 8 * nl) return fail(AMR_EINVAL, "amr_flag: room for %lld cells needed", (long long)(8 * nl));
+  uint32_t *raw = nullptr, *flag = nullptr;
+  AMR_TRY(alloc_n(h, &raw, h->N));
+  AMR_TRY(alloc_n(h, &flag, h->N));
+  amr_status st = compute_flags(h, raw, flag, "amr_flag");
+  if (st == AMR_OK && nl > 0) {
+    std::vector<uint32_t> mk(nl);
+    cudaError_t e = cudaMemcpyAsync(mk.data(), flag + lo, 4 * nl, cudaMemcpyDeviceToHost, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = fail(AMR_ECUDA, "amr_flag: %s", cudaGetErrorString(e));
+    for (int64_t q = 0; q < nl && st == AMR_OK; ++q)
+      for (int c = 0; c < 8; ++c) flags[8 * q + c] = uint8_t((mk[q] >> c) & 1u);
+  }
+  dev_free(h, raw);
+  dev_free(h, flag);
+  return st;
+}
+
+// A fresh handle shell that shares h's stream, parameters and members.
+static amr_mesh *regrid_shell(amr_mesh *h) {
+  amr_mesh *nh = new amr_mesh();
+  nh->p = h->p;
+  nh->s = h->s;
+  nh->own_stream = false;
+  nh->device = h->device;
+  nh->sm_count = h->sm_count;
+  nh->M = h->M;
+  nh->sel = h->sel;
+  nh->lmax_all = h->lmax_all;
+  nh->mem = h->mem;
+  nh->tile_size = h->tile_size;
+  nh->persistent = h->persistent;
+  nh->tuned = h->tuned;
+  return nh;
+}
+
+extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *removed) {
+  if (!h) return fail(AMR_EINVAL, "amr_regrid: NULL handle");
+  if (created) *created = 0;
+  if (removed) *removed = 0;
+  const int64_t N = h->N;
+  uint32_t *raw = nullptr, *flag = nullptr, *keep = nullptr, *nnew = nullptr, *kpos = nullptr,
+           *npos = nullptr, *tmp = nullptr;
+  auto release = [&] {
+    for (uint32_t **q : {&raw, &flag, &keep, &nnew, &kpos, &npos, &tmp})
+      if (*q) {
+        dev_free(h, *q);
+        *q = nullptr;
+      }
+  };
+  amr_status st = AMR_OK;
+#define REGRID_TRY(x)        \
+  do {                       \
+    st = (x);                \
+    if (st != AMR_OK) {      \
+      release();             \
+      return st;             \
+    }                        \
+  } while (0)
+  REGRID_TRY(alloc_n(h, &raw, N));
+  REGRID_TRY(alloc_n(h, &flag, N));
+  REGRID_TRY(alloc_n(h, &keep, N));
+  REGRID_TRY(alloc_n(h, &nnew, N));
+  REGRID_TRY(alloc_n(h, &kpos, N));
+  REGRID_TRY(alloc_n(h, &npos, N));
+  REGRID_TRY(alloc_n(h, &tmp, scan_tmp_size(N)));
+  REGRID_TRY(compute_flags(h, raw, flag, "amr_regrid"));
+  const RegridArgs a = regrid_args(h, raw, flag);
+  launch(h, K_REGRID, k_regrid_count, dim3(nblocks(N)), dim3(256), a, keep, nnew);
+  cudaMemcpyAsync(kpos, keep, 4 * N, cudaMemcpyDeviceToDevice, h->s);
+  cudaMemcpyAsync(npos, nnew, 4 * N, cudaMemcpyDeviceToDevice, h->s);
+  scan_exclusive(h, kpos, N, tmp);
+  scan_exclusive(h, npos, N, tmp);
+  uint32_t tail[4] = {0, 0, 0, 0};
+  cudaMemcpyAsync(tail + 0, kpos + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
+  cudaMemcpyAsync(tail + 1, keep + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
+  cudaMemcpyAsync(tail + 2, npos + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
+  cudaMemcpyAsync(tail + 3, nnew + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
+  REGRID_TRY(check_device(h, "amr_regrid"));
+  const int64_t K = int64_t(tail[0]) + tail[1], NN = int64_t(tail[2]) + tail[3];
+  if (created) *created = NN;
+  if (removed) *removed = N - K;
+  if (NN == 0 && K == N) {  // nothing changes
+    release();
+    return AMR_OK;
+  }
+  const int64_t n_out = K + NN;
+  if (n_out > (int64_t(1) << 26)) {
+    release();
+    return fail(AMR_EINVAL, "amr_regrid: the new mesh would hold more than 2^26 octs");
+  }
+  // the new oct list, in the new handle's memory
+  amr_mesh *nh = regrid_shell(h);
+  uint8_t *d_lvl = nullptr, *d_new = nullptr;
+  uint16_t *d_mem = nullptr;
+  uint32_t *d_i = nullptr, *d_j = nullptr, *d_k = nullptr;
+  double *d_U = nullptr;
+  auto abandon = [&](amr_status e) {
+    std::string msg = g_last_error;
+    cudaStreamSynchronize(h->s);
+    destroy_all(nh);
+    release();
+    g_last_error = msg;
+    return e;
+  };
+  if ((st = upload_members(nh)) != AMR_OK || (st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
+      (st = alloc_n(nh, &d_new, n_out)) != AMR_OK || (st = alloc_n(nh, &d_mem, n_out)) != AMR_OK ||
+      (st = alloc_n(nh, &d_i, n_out)) != AMR_OK || (st = alloc_n(nh, &d_j, n_out)) != AMR_OK ||
+      (st = alloc_n(nh, &d_k, n_out)) != AMR_OK || (st = alloc_n(nh, &d_U, 40 * n_out)) != AMR_OK)
+    return abandon(st);
+  if (h->p.precision == 4)
+    launch(h, K_REGRID, k_regrid_emit<float>, dim3(nblocks(N)), dim3(256), a, (const float *)h->U,
+           (const uint32_t *)kpos, (const uint32_t *)keep, (const uint32_t *)npos, K, n_out, d_lvl,
+           d_mem, d_i, d_j, d_k, d_U, d_new);
+  else
+    launch(h, K_REGRID, k_regrid_emit<double>, dim3(nblocks(N)), dim3(256), a, (const double *)h->U,
+           (const uint32_t *)kpos, (const uint32_t *)keep, (const uint32_t *)npos, K, n_out, d_lvl,
+           d_mem, d_i, d_j, d_k, d_U, d_new);
+  if ((st = check_device(h, "amr_regrid")) != AMR_OK) return abandon(st);
+  release();
+  if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, d_U, d_new)) != AMR_OK)
+    return abandon(st);
+  // carry the per-member step counters and last time steps over
+  cudaMemcpyAsync(nh->mrem, h->mrem, sizeof(int) * h->M, cudaMemcpyDeviceToDevice, h->s);
+  cudaMemcpyAsync(nh->dt_dev, h->dt_dev, sizeof(double) * h->M, cudaMemcpyDeviceToDevice, h->s);
+  cudaMemcpyAsync(nh->merr, h->merr, sizeof(int) * h->M, cudaMemcpyDeviceToDevice, h->s);
+  // the handle takes the new mesh; the old one is freed
+  nh->own_stream = h->own_stream;
+  h->own_stream = false;
+  nh->event_pool.swap(h->event_pool);
+  nh->pending.swap(h->pending);
+  nh->timing = h->timing;
+  nh->launches = h->launches;
+  nh->graph_launches = h->graph_launches;
+  std::memcpy(nh->kernel_ms, h->kernel_ms, sizeof h->kernel_ms);
+  std::memcpy(nh->kernel_n, h->kernel_n, sizeof h->kernel_n);
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  std::swap(*h, *nh);
+  destroy_all(nh);
+  return check_device(h, "amr_regrid");
+#undef REGRID_TRY
 }
 
 extern "C" amr_status amr_select_member(amr_handle h, int member) {

@@ -1,0 +1,302 @@
+// regrid_kernels.cuh -- flag, grade, count, emit and prolong kernels of one
+// regrid (paper Sec. 2.2: refinement of flagged cells by new child octs,
+// de-refinement of split cells no longer flagged, then the level bucket and
+// Hilbert sorts and the ghost cache of Sec. 2.3, which the mesh build
+// shared with creation performs).
+//
+// Flags live in a per-oct bit mask (bit c = cell c), like the split mask.
+//   flag    a cell of level l < levelmax refines when, to one of its six
+//           face neighbours (the same-level cell, else the coarser cell that
+//           covers it), the relative jump 2|a-b|/(|a|+|b|) of rho exceeds
+//           grad_rho or that of p exceeds grad_p, or when rho dx^3 exceeds
+//           mass.  The decision is taken in FP64 with each operation rounded
+//           as written (no contraction), so it is the same on every build.
+//   expand  with expand = 1 a flag also flags the 26 same-level cells around
+//   grade   finest level first, a flagged cell X of level l flags the level
+//           l-1 cells covering the 27 level-l cells around X (2:1 rule)
+//   count   an oct above levelmin stays when its father cell is flagged; a
+//           flagged leaf gets a new child oct
+//   emit    the new oct list (kept octs with their state, then new octs)
+//   prolong the new octs of each level, coarsest first, from their father
+//           and its six face neighbours (the ghost-oct minmod formula)
+#pragma once
+#include "hydro_kernels.cuh"
+
+namespace amr {
+
+struct RegridArgs {
+  int N, NE, NC;
+  int64_t S;
+  const uint64_t *key;    // [N] internal keys
+  const uint32_t *son;    // [N] split masks
+  const int32_t *father;  // [N] father oct, -1 at levelmin
+  const int32_t *nbr27;   // [27][N]
+  const int32_t *fnb;     // [6][NE]
+  const int32_t *csrc;    // [7][NC] (entry 0: the ghost's father cell)
+  const int *mlmin, *mlmax;
+  const double *mgamma, *msmallr, *msmallp;
+  double grad_rho, grad_p, mass;
+  int expand;
+  uint32_t *raw;   // [N] criterion masks
+  uint32_t *flag;  // [N] final masks
+  int *err;
+};
+
+// conservative -> primitive with floors, every operation rounded as written
+__device__ __forceinline__ void prim_exact(const double (&u)[5], double g, double smallr,
+                                           double smallp, double &rho, double &p) {
+  const double r = u[0] > smallr ? u[0] : smallr;
+  const double vx = __ddiv_rn(u[1], r), vy = __ddiv_rn(u[2], r), vz = __ddiv_rn(u[3], r);
+  const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+  const double ek = __dmul_rn(__dmul_rn(0.5, r), v2);
+  double pr = __dmul_rn(__dsub_rn(g, 1.0), __dsub_rn(u[4], ek));
+  const double pf = __dmul_rn(r, smallp);
+  if (pr < pf) pr = pf;
+  rho = r;
+  p = pr;
+}
+
+__device__ __forceinline__ double rel_jump(double a, double b) {
+  const double s = __dadd_rn(fabs(a), fabs(b));
+  return s > 0.0 ? __ddiv_rn(__dmul_rn(2.0, fabs(__dsub_rn(a, b))), s) : 0.0;
+}
+
+template <class T>
+__device__ __forceinline__ void load_cell(const T *U, int64_t S, int64_t g, double (&u)[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = double(U[v * S + g]);
+}
+
+// criterion masks: one thread per real oct
+template <class T>
+__global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= a.N) return;
+  const uint64_t key = a.key[o];
+  const int m = ikey_member(key), l = ikey_lev(key);
+  uint32_t mask = 0;
+  if (l < a.mlmax[m]) {
+    const double g = a.mgamma[m], sr = a.msmallr[m], sp = a.msmallp[m];
+    const bool grad = a.grad_rho > 0.0 || a.grad_p > 0.0;
+    for (int c = 0; c < 8; ++c) {
+      double uc[5];
+      load_cell(U, a.S, 8 * int64_t(o) + c, uc);
+      bool f = a.mass > 0.0 && ldexp(uc[0], -3 * l) > a.mass;
+      if (!f && grad) {
+        double rc, pc;
+        prim_exact(uc, g, sr, sp, rc, pc);
+        for (int d = 0; d < 3 && !f; ++d)
+          for (int plus = 0; plus < 2 && !f; ++plus) {
+            // face neighbour: same oct, a real oct, or a ghost oct whose
+            // father cell is the covering coarser cell
+            const int bit = 1 << d;
+            int64_t gn;
+            if (((c >> d) & 1) != plus) {
+              gn = 8 * int64_t(o) + (c ^ bit);
+            } else {
+              const int32_t ne = a.fnb[(2 * d + plus) * int64_t(a.NE) + o];
+              if (ne < 0) continue;
+              if (ne < a.N)
+                gn = 8 * int64_t(ne) + (c ^ bit);
+              else
+                gn = a.csrc[ne - a.N];
+            }
+            double un[5], rn, pn;
+            load_cell(U, a.S, gn, un);
+            prim_exact(un, g, sr, sp, rn, pn);
+            if (a.grad_rho > 0.0 && rel_jump(rn, rc) > a.grad_rho) f = true;
+            if (a.grad_p > 0.0 && rel_jump(pn, pc) > a.grad_p) f = true;
+          }
+      }
+      if (f) mask |= 1u << c;
+    }
+  }
+  a.raw[o] = mask;
+}
+
+// expansion over the 3x3x3 same-level block (or a copy when expand = 0)
+__global__ void k_flag_expand(RegridArgs a) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= a.N) return;
+  const uint64_t key = a.key[o];
+  const int m = ikey_member(key), l = ikey_lev(key);
+  uint32_t mask = 0;
+  if (l < a.mlmax[m]) {
+    if (!a.expand) {
+      mask = a.raw[o];
+    } else {
+      for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        bool f = false;
+        for (int dz = -1; dz <= 1 && !f; ++dz)
+          for (int dy = -1; dy <= 1 && !f; ++dy)
+            for (int dx = -1; dx <= 1 && !f; ++dx) {
+              const int fx = cx + dx, fy = cy + dy, fz = cz + dz;  // -1..2
+              const int ox = fx >> 1, oy = fy >> 1, oz = fz >> 1;  // arithmetic shift: -1..1
+              const int32_t e = a.nbr27[((oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)) * int64_t(a.N) + o];
+              if (e < 0 || e >= a.N) continue;  // a ghost: no real cell of this level there
+              const int cc = (fx & 1) | ((fy & 1) << 1) | ((fz & 1) << 2);
+              if ((a.raw[e] >> cc) & 1u) f = true;
+            }
+        if (f) mask |= 1u << c;
+      }
+    }
+  }
+  a.flag[o] = mask;
+}
+
+// grading closure from the octs [lo, hi) of one level l > levelmin: every
+// flagged cell flags the level-(l-1) cells covering its 27 neighbours
+__global__ void k_flag_grade(RegridArgs a, int lo, int hi) {
+  const int o = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= hi) return;
+  const uint32_t mask = a.flag[o];
+  if (!mask) return;
+  const uint64_t key = a.key[o];
+  const int l = ikey_lev(key);
+  const int fo = a.father[o];
+  if (fo < 0) return;
+  const int64_t side = int64_t(1) << l;              // cells per axis at level l
+  const int64_t oside = int64_t(1) << (l - 2 > 0 ? l - 2 : 0);  // octs per axis at l-1
+  const uint32_t oi = ikey_x(key), oj = ikey_y(key), okk = ikey_z(key);
+  for (int c = 0; c < 8; ++c) {
+    if (!((mask >> c) & 1u)) continue;
+    const int64_t x = 2 * int64_t(oi) + (c & 1), y = 2 * int64_t(oj) + ((c >> 1) & 1),
+                  z = 2 * int64_t(okk) + ((c >> 2) & 1);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int64_t X = ((x + dx) % side + side) % side, Y = ((y + dy) % side + side) % side,
+                        Z = ((z + dz) % side + side) % side;
+          const int64_t px = X >> 1, py = Y >> 1, pz = Z >> 1;  // covering level-(l-1) cell
+          // its oct, relative to the father cell's oct (oi>>1, oj>>1, ok>>1)
+          int rel[3];
+          const int64_t d3[3] = {(px >> 1) - int64_t(oi >> 1), (py >> 1) - int64_t(oj >> 1),
+                                 (pz >> 1) - int64_t(okk >> 1)};
+          for (int q = 0; q < 3; ++q) {
+            const int64_t dd = ((d3[q] % oside) + oside) % oside;
+            rel[q] = dd == 0 ? 0 : (dd == 1 ? 1 : -1);
+          }
+          const int32_t e = a.nbr27[((rel[2] + 1) * 9 + (rel[1] + 1) * 3 + (rel[0] + 1)) * int64_t(a.N) + fo];
+          if (e < 0 || e >= a.N) {
+            atomicOr(a.err, kErrGrading);
+            continue;
+          }
+          const int cc = int(px & 1) | (int(py & 1) << 1) | (int(pz & 1) << 2);
+          atomicOr(a.flag + e, 1u << cc);
+        }
+  }
+}
+
+// per oct: 1 if it stays (its father cell is flagged, or it is a base oct),
+// and the number of new child octs (flagged leaf cells)
+__global__ void k_regrid_count(RegridArgs a, uint32_t *keep, uint32_t *nnew) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= a.N) return;
+  const uint64_t key = a.key[o];
+  const int fo = a.father[o];
+  uint32_t k = 1;
+  if (fo >= 0) {
+    const int fc = int(ikey_x(key) & 1) | (int(ikey_y(key) & 1) << 1) | (int(ikey_z(key) & 1) << 2);
+    k = (a.flag[fo] >> fc) & 1u;
+  }
+  keep[o] = k;
+  nnew[o] = __popc(a.flag[o] & ~a.son[o]);
+}
+
+// the new oct list: kept octs at keep[o] (exclusive scan), new child octs
+// after all kept ones, at K + nnew[o] (exclusive scan) in cell order
+template <class T>
+__global__ void k_regrid_emit(RegridArgs a, const T *__restrict__ U, const uint32_t *keep_pos,
+                              const uint32_t *keep, const uint32_t *new_pos, int64_t K,
+                              int64_t n_out, uint8_t *lvl, uint16_t *mem, uint32_t *oi,
+                              uint32_t *oj, uint32_t *ok, double *Uout, uint8_t *is_new) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= a.N) return;
+  const uint64_t key = a.key[o];
+  const int l = ikey_lev(key);
+  const uint32_t x = ikey_x(key), y = ikey_y(key), z = ikey_z(key);
+  if (keep[o]) {
+    const int64_t t = keep_pos[o];
+    lvl[t] = uint8_t(l);
+    mem[t] = uint16_t(ikey_member(key));
+    oi[t] = x;
+    oj[t] = y;
+    ok[t] = z;
+    is_new[t] = 0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) Uout[v * 8 * n_out + 8 * t + c] = double(U[v * a.S + 8 * int64_t(o) + c]);
+  }
+  const uint32_t nm = a.flag[o] & ~a.son[o];
+  int64_t t = K + new_pos[o];
+  for (int c = 0; c < 8; ++c) {
+    if (!((nm >> c) & 1u)) continue;
+    lvl[t] = uint8_t(l + 1);
+    mem[t] = uint16_t(ikey_member(key));
+    oi[t] = 2 * x + (c & 1);
+    oj[t] = 2 * y + ((c >> 1) & 1);
+    ok[t] = 2 * z + ((c >> 2) & 1);
+    is_new[t] = 1;
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) Uout[v * 8 * n_out + 8 * t + q] = 0.0;
+    ++t;
+  }
+}
+
+// new octs of [lo, hi) (one level) take the minmod prolongation of their
+// father cell from the father's face neighbours (all real after grading)
+template <class T>
+__global__ void k_prolong_new(int N, int NE, int64_t S, const uint64_t *__restrict__ key,
+                              const int32_t *__restrict__ father, const int32_t *__restrict__ fnb,
+                              const uint8_t *__restrict__ is_new, T *U, int lo, int hi, int *err) {
+  const int o = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= hi || !is_new[o]) return;
+  const int fo = father[o];
+  const uint64_t k = key[o];
+  const int fc = int(ikey_x(k) & 1) | (int(ikey_y(k) & 1) << 1) | (int(ikey_z(k) & 1) << 2);
+  int64_t gm[3], gp[3];
+  for (int d = 0; d < 3; ++d) {
+    const int bit = 1 << d;
+    for (int plus = 0; plus < 2; ++plus) {
+      int64_t g;
+      if (((fc >> d) & 1) != plus) {
+        g = 8 * int64_t(fo) + (fc ^ bit);
+      } else {
+        const int32_t ne = fnb[(2 * d + plus) * int64_t(NE) + fo];
+        if (ne < 0 || ne >= N) {
+          atomicOr(err, kErrGrading);
+          return;
+        }
+        g = 8 * int64_t(ne) + (fc ^ bit);
+      }
+      (plus ? gp : gm)[d] = g;
+    }
+  }
+  const int64_t gc = 8 * int64_t(fo) + fc;
+  for (int v = 0; v < 5; ++v) {
+    const T *Uv = U + v * S;
+    const T uc = Uv[gc];
+    const T sx = minmod(Uv[gp[0]] - uc, uc - Uv[gm[0]]);
+    const T sy = minmod(Uv[gp[1]] - uc, uc - Uv[gm[1]]);
+    const T sz = minmod(Uv[gp[2]] - uc, uc - Uv[gm[2]]);
+    T *dst = U + v * S + 8 * int64_t(o);
+    const T h = T(0.25);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const T hx = (c & 1) ? h : -h, hy = (c & 2) ? h : -h, hz = (c & 4) ? h : -h;
+      dst[c] = ((uc + hx * sx) + hy * sy) + hz * sz;
+    }
+  }
+}
+
+__global__ void k_gather_u8(const uint32_t *__restrict__ perm, const uint8_t *__restrict__ src,
+                            int64_t n, uint8_t *__restrict__ dst) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < n) dst[t] = src[perm[t]];
+}
+
+}  // namespace amr

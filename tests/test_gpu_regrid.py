@@ -1,0 +1,159 @@
+"""Regrid on the GPU (Sec. 2.2) against the oracle: refinement flags and the
+new meshes bit for bit, states of the kept and new octs, and coarse steps
+interleaved with regrids."""
+import numpy as np
+import pytest
+
+from paper_2607_20704_gb300 import inputs
+from parity import close, compare_all
+
+pytestmark = pytest.mark.gpu
+
+CRIT = [dict(grad_rho=0.1, grad_p=0.1, mass=0.0, expand=1),
+        dict(grad_rho=0.05, grad_p=0.0, mass=0.0, expand=0),
+        dict(grad_rho=0.0, grad_p=0.0, mass=2e-4, expand=1)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_20704_gb300 import amr, build
+    build.build()
+    amr.load()
+
+
+def _pair(prob, crit, precision=8, **kw):
+    import oracle
+    from paper_2607_20704_gb300 import amr
+    g = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision,
+                 refine_grad_rho=crit["grad_rho"], refine_grad_p=crit["grad_p"],
+                 refine_mass=crit["mass"], regrid_expand=bool(crit["expand"]), **kw)
+    o = oracle.Mesh(*prob.mesh_args(), **prob.params())
+    return g, o
+
+
+def _problems():
+    return [inputs.random_mesh(3, 6, seed=31), inputs.random_mesh(4, 6, seed=32).shuffled(3),
+            inputs.sod(4, 6), inputs.sedov(4, 6, radii={5: 0.15, 6: 0.08})]
+
+
+@pytest.mark.parametrize("ci", range(len(CRIT)))
+def test_flags_match_the_oracle_bit_for_bit(ci):
+    crit = CRIT[ci]
+    for prob in _problems():
+        g, o = _pair(prob, crit)
+        for l in o.levels():
+            assert np.array_equal(g.flags(l), o.level_flags(l, **crit)), (prob.name, l)
+        g.close()
+
+
+@pytest.mark.parametrize("ci", range(len(CRIT)))
+def test_regrid_matches_the_oracle(ci):
+    """New mesh (keys, split flags, neighbour array, ghost keys) bit for bit;
+    kept and prolonged states within 1e-14."""
+    crit = CRIT[ci]
+    for prob in _problems():
+        g, o = _pair(prob, crit)
+        cg = g.regrid()
+        co = o.regrid(**crit)
+        assert cg == co, (prob.name, cg, co)
+        assert g.levels() == o.levels()
+        compare_all(g, o, 1e-14, reflux=False)
+        for l in o.levels():
+            nbg, spg = g.read_index(l)
+            assert np.array_equal(nbg, o.read_nbr(l)), l
+            assert np.array_equal(spg, o.read_split(l)), l
+            assert np.array_equal(g.read_cache(l)[0], o.read_cache(l)), l
+        g.close()
+
+
+def test_regrid_and_steps_interleaved():
+    """Three rounds of regrid + one coarse step from a Sod tube and a
+    blast: meshes equal, states within the chained-step tolerance."""
+    for prob in (inputs.sod(4, 6), inputs.sedov(4, 6, radii={5: 0.15, 6: 0.08})):
+        crit = CRIT[0]
+        g, o = _pair(prob, crit)
+        for _ in range(3):
+            assert g.regrid() == o.regrid(**crit)
+            dtg = g.advance(1, sync=True)
+            dto = o.advance(1)
+            assert abs(dtg - dto) <= 1e-12 * dto
+        compare_all(g, o, 1e-11)
+        g.close()
+
+
+def test_regrid_every_step_equals_explicit_regrids():
+    from paper_2607_20704_gb300 import amr
+    prob = inputs.sod(4, 6)
+    crit = CRIT[0]
+    kw = dict(refine_grad_rho=crit["grad_rho"], refine_grad_p=crit["grad_p"])
+    a = amr.Mesh(*prob.mesh_args(), **prob.params(), regrid_every_step=True, **kw)
+    b = amr.Mesh(*prob.mesh_args(), **prob.params(), **kw)
+    a.advance(3, sync=True)
+    for _ in range(3):
+        b.regrid()
+        b.advance(1, sync=True)
+    assert a.levels() == b.levels()
+    for l in a.levels():
+        ka, Ua = a.read(l)
+        kb, Ub = b.read(l)
+        assert np.array_equal(ka, kb) and np.array_equal(Ua, Ub), l
+    a.close()
+    b.close()
+
+
+def test_graphs_and_eager_agree_after_regrid():
+    from paper_2607_20704_gb300 import amr
+    prob = inputs.random_mesh(3, 5, seed=33)
+    out = []
+    for graphs in (True, False):
+        m = amr.Mesh(*prob.mesh_args(), **prob.params(), use_graphs=graphs, refine_grad_rho=0.1,
+                     refine_grad_p=0.1)
+        m.advance(1)
+        m.regrid()
+        m.advance(2, sync=True)
+        out.append({l: m.read(l)[1] for l in m.levels()})
+        m.close()
+    assert out[0].keys() == out[1].keys()
+    for l in out[0]:
+        assert np.array_equal(out[0][l], out[1][l])
+
+
+def test_uniform_state_coarsens_to_the_base():
+    prob = inputs.uniform_state(3, 6, seed=9)
+    g, o = _pair(prob, CRIT[0])
+    n_above = sum(g.num_octs(l) for l in g.levels() if l > 3)
+    assert g.regrid() == (0, n_above)
+    assert g.levels() == [3]
+    _, U = g.read(3)
+    assert np.max(np.abs(U - prob.U[:, :1])) <= 1e-14 * np.abs(prob.U).max()
+    g.close()
+
+
+def test_fp32_regrid_follows_the_fp64_mesh():
+    """Piecewise-constant Sod states give the same flags in both precisions;
+    the FP32 handle's meshes follow the FP64 ones and conserve mass."""
+    from paper_2607_20704_gb300 import amr
+    prob = inputs.sod(4, 6)
+    kw = dict(refine_grad_rho=0.1, refine_grad_p=0.1)
+    g8 = amr.Mesh(*prob.mesh_args(), **prob.params(), **kw)
+    g4 = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=4, **kw)
+
+    def mass(m):
+        t = 0.0
+        for l in m.levels():
+            _, U = m.read(l)
+            _, sp = m.read_index(l)
+            t += U[0, sp == 0].sum() * 2.0 ** (-3 * l)
+        return t
+    m0 = mass(g4)
+    assert g4.regrid() == g8.regrid()
+    for l in g8.levels():
+        assert np.array_equal(g4.read(l)[0], g8.read(l)[0])
+        close(g4.read(l)[1], g8.read(l)[1], 1e-6, f"level {l}")
+    g4.advance(2, sync=True)
+    assert abs(mass(g4) - m0) <= 1e-6 * m0
+    g4.close()
+    g8.close()
