@@ -48,6 +48,8 @@ def parse():
                     help="skip the 512-mesh batched ensemble measurement")
     ap.add_argument("--batched-members", type=int, default=512)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the adaptive run (regrid before every coarse step)")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--no-other-precision", action="store_true",
                     help="run only --precision (skip the other precision's pass)")
@@ -328,6 +330,57 @@ def run_batched(members, steps, warmup, torch, device, flush):
     return out
 
 
+def run_adaptive(prob, precision, steps, torch, device):
+    """The blast with its mesh following it: a regrid (relative jump of rho
+    or p above 0.1, one-cell expansion) before every coarse step.  Regrids
+    synchronise with the host, so both phases are timed on the wall clock
+    around a device synchronisation."""
+    from paper_2607_20704_gb300 import amr
+    m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, stream=bench_stream(),
+                 refine_grad_rho=0.1, refine_grad_p=0.1, **LAUNCH)
+    octs0 = m.info()["n_oct"]
+    for _ in range(2):
+        m.regrid()
+        m.advance(1)
+    torch.cuda.synchronize(device)
+    t_regrid, t_step, upd, changes = [], [], 0, []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        changes.append(m.regrid())
+        torch.cuda.synchronize(device)
+        t1 = time.perf_counter()
+        upd += int(m.info()["work_per_step"])
+        m.advance(1)
+        torch.cuda.synchronize(device)
+        t2 = time.perf_counter()
+        t_regrid.append(1e3 * (t1 - t0))
+        t_step.append(1e3 * (t2 - t1))
+    # kernel time inside regrids (CUDA events around every launch)
+    m.set_timing(True)
+    for _ in range(3):
+        m.regrid()
+    m.sync()
+    kt = m.read_timing()
+    m.set_timing(False)
+    ktot = sum(v[0] for v in kt.values()) or 1.0
+    regrid_kernels = {k: {"ms_per_regrid": round(v[0] / 3, 4), "share": round(v[0] / ktot, 4)}
+                      for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])[:8]}
+    inf = m.info()
+    m.close()
+    total_s = 1e-3 * (sum(t_regrid) + sum(t_step))
+    return {"steps": steps, "criterion": "relative jump of rho or p to a face neighbour > 0.1, "
+            "expand 1, regrid before every coarse step",
+            "cell_updates_per_s": upd / total_s,
+            "regrid_ms_median": round(statistics.median(t_regrid), 3),
+            "step_ms_median": round(statistics.median(t_step), 3),
+            "regrid_share": round(sum(t_regrid) / (sum(t_regrid) + sum(t_step)), 4),
+            "octs_start": int(octs0), "octs_end": int(inf["n_oct"]),
+            "leaf_cells_end": int(inf["n_leaf_cells"]),
+            "octs_created_per_regrid": round(float(np.mean([c[0] for c in changes])), 1),
+            "octs_removed_per_regrid": round(float(np.mean([c[1] for c in changes])), 1),
+            "regrid_kernel_ms": round(ktot / 3, 4), "regrid_kernels": regrid_kernels}
+
+
 def run_serving(n_requests, rates, torch):
     """Serving loop under Poisson arrivals at each rate of the sweep: p50/p99
     latency (submit -> result on the host) and sustained leaf cell-updates/s
@@ -527,6 +580,10 @@ def main():
             other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
             other["steps"] = args.steps
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
+        adaptive = None
+        if not args.no_adaptive:
+            adaptive = {("fp64" if p == 8 else "fp32"): run_adaptive(prob, p, 10, torch, device)
+                        for p in (8, 4)}
         serving = None
         if not args.no_serving:
             serving = run_serving(args.serving_requests, (10.0, 40.0, 160.0), torch)
@@ -592,6 +649,8 @@ def main():
             "autotuned": {"tile": other["info"].get("tile"), "schedule": other["info"].get("schedule")},
             "step_roofline_frac": round(other_value / world
                                         * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)}
+    if adaptive is not None:
+        line["adaptive"] = adaptive
     if batched is not None:
         line["batched"] = batched
     if serving is not None:

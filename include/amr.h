@@ -174,7 +174,9 @@ amr_status amr_member_dt(amr_handle h, double *dt_out, int n);
  * Sec. 2.3).  With the criteria of the handle's amr_params:
  *   flag    cells of level l < levelmax meeting a criterion; the face
  *           neighbour is the same-level cell, else the coarser cell covering
- *           it; decided in FP64 with every operation rounded as written
+ *           it; the jump test is 2|a-b| > threshold (|a|+|b|) and the
+ *           pressure (gamma-1)(E - (m.m/2)/rho) with the floors, decided in
+ *           FP64 with every operation rounded as written
  *   expand  (regrid_expand) also the 26 same-level cells around a flag
  *   grade   finest level first, a flagged cell of level l flags the level
  *           l-1 cells covering its 27 level-l neighbours (2:1 rule)

@@ -1048,7 +1048,9 @@ int orc_1d_step(int n, double *U, double gamma, double dt, double smallr, double
 /*          face neighbours (the same-level cell, else the coarser cell      */
 /*          covering it), the relative jump 2|a-b|/(|a|+|b|) of rho exceeds  */
 /*          grad_rho or that of p exceeds grad_p, or when rho dx_l^3 exceeds */
-/*          mass;                                                            */
+/*          mass; the jump test is taken as 2|a-b| > thr (|a|+|b|) and the   */
+/*          pressure as (gamma-1)(E - (m.m/2)/rho) with the floors, so that  */
+/*          a criterion costs one division per cell;                         */
 /*   expand with expand = 1 a flag also flags the 26 same-level cells       */
 /*          around it that exist;                                            */
 /*   grade  finest level first: a flagged cell X of level l flags, at level  */
@@ -1064,9 +1066,20 @@ int orc_1d_step(int n, double *U, double gamma, double dt, double smallr, double
 /*          creation (order, lookup, grading check, cache, restriction).     */
 /* ------------------------------------------------------------------------- */
 
-static double rel_jump(double a, double b) {
-  double s = fabs(a) + fabs(b);
-  return s > 0.0 ? 2.0 * fabs(a - b) / s : 0.0;
+/* the relative jump of a and b exceeds thr: 2|a-b| > thr (|a|+|b|) */
+static int jump_exceeds(double a, double b, double thr) {
+  return 2.0 * fabs(a - b) > thr * (fabs(a) + fabs(b));
+}
+
+/* density and pressure of the flag criterion, with the floors */
+static void flag_rho_p(const phys *ph, const double u[NV], double *rho, double *p) {
+  double r = u[0] > ph->smallr ? u[0] : ph->smallr;
+  double m2 = (u[1] * u[1] + u[2] * u[2]) + u[3] * u[3];
+  double ek = (0.5 * m2) / r;
+  double pr = (ph->g - 1.0) * (u[4] - ek);
+  double pf = r * ph->smallp;
+  *rho = r;
+  *p = pr < pf ? pf : pr;
 }
 
 /* oct index of the cell (x,y,z) of level L (same level only), or -1 */
@@ -1081,20 +1094,20 @@ static int raw_flag(const orc_mesh *m, const phys *ph, const orc_regrid_params *
                     int c) {
   int64_t N8 = 8 * m->n;
   int l = m->lvl[o];
-  double uc[NV], wc[NV];
+  double uc[NV], rc, pc;
   for (int v = 0; v < NV; ++v) uc[v] = m->U[v * N8 + 8 * o + c];
   if (rp->mass > 0.0 && ldexp(uc[0], -3 * l) > rp->mass) return 1;
   if (!(rp->grad_rho > 0.0) && !(rp->grad_p > 0.0)) return 0;
-  cons_to_prim(ph, uc, wc);
+  flag_rho_p(ph, uc, &rc, &pc);
   int64_t x = 2 * (int64_t)m->ci[o] + (c & 1), y = 2 * (int64_t)m->cj[o] + ((c >> 1) & 1),
           z = 2 * (int64_t)m->ck[o] + ((c >> 2) & 1);
   for (int d = 0; d < 3; ++d)
     for (int s = -1; s <= 1; s += 2) {
-      double un[NV], wn[NV];
+      double un[NV], rn, pn;
       if (cell_value(m, l, x + (d == 0) * s, y + (d == 1) * s, z + (d == 2) * s, un)) continue;
-      cons_to_prim(ph, un, wn);
-      if (rp->grad_rho > 0.0 && rel_jump(wn[0], wc[0]) > rp->grad_rho) return 1;
-      if (rp->grad_p > 0.0 && rel_jump(wn[4], wc[4]) > rp->grad_p) return 1;
+      flag_rho_p(ph, un, &rn, &pn);
+      if (rp->grad_rho > 0.0 && jump_exceeds(rn, rc, rp->grad_rho)) return 1;
+      if (rp->grad_p > 0.0 && jump_exceeds(pn, pc, rp->grad_p)) return 1;
     }
   return 0;
 }

@@ -82,7 +82,7 @@ int orc_advance(orc_mesh *m, int nsteps, double *dt_last);
 /* --- regrid (Sec. 2.2: refinement, de-refinement, level and Hilbert order;
  *     then the ghost cache of Sec. 2.3) ------------------------------------- */
 typedef struct {
-  double grad_rho; /* relative jump 2|a-b|/(|a|+|b|) of rho to a face neighbour; <= 0: off */
+  double grad_rho; /* relative jump of rho to a face neighbour, 2|a-b| > grad_rho (|a|+|b|); <= 0: off */
   double grad_p;   /* the same for the pressure; <= 0: off */
   double mass;     /* cell mass rho dx^3 above which a cell refines; <= 0: off */
   int expand;      /* 1: a flag also flags the 26 same-level neighbours */

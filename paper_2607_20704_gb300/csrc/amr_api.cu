@@ -1377,10 +1377,18 @@ static RegridArgs regrid_args(amr_mesh *h, uint32_t *raw, uint32_t *flag) {
 static amr_status compute_flags(amr_mesh *h, uint32_t *raw, uint32_t *flag, const char *where) {
   const RegridArgs a = regrid_args(h, raw, flag);
   const unsigned g = nblocks(h->N);
-  if (h->p.precision == 4)
-    launch(h, K_FLAG, k_flag_raw<float>, dim3(g), dim3(256), a, (const float *)h->U);
-  else
-    launch(h, K_FLAG, k_flag_raw<double>, dim3(g), dim3(256), a, (const double *)h->U);
+  double *rp = nullptr;
+  AMR_TRY(alloc_n(h, &rp, 16 * h->N));
+  if (h->p.precision == 4) {
+    launch(h, K_FLAG, k_flag_rp<float>, dim3(nblocks(8 * h->N)), dim3(256), a, (const float *)h->U, rp);
+    launch(h, K_FLAG, k_flag_raw<float>, dim3(g), dim3(256), a, (const float *)h->U,
+           (const double *)rp);
+  } else {
+    launch(h, K_FLAG, k_flag_rp<double>, dim3(nblocks(8 * h->N)), dim3(256), a, (const double *)h->U, rp);
+    launch(h, K_FLAG, k_flag_raw<double>, dim3(g), dim3(256), a, (const double *)h->U,
+           (const double *)rp);
+  }
+  dev_free(h, rp);
   launch(h, K_FLAG, k_flag_expand, dim3(g), dim3(256), a);
   for (auto &m : h->mem)
     for (int l = m.lmax - 1; l > m.lmin; --l) {

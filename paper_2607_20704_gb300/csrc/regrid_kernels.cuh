@@ -7,10 +7,11 @@
 // Flags live in a per-oct bit mask (bit c = cell c), like the split mask.
 //   flag    a cell of level l < levelmax refines when, to one of its six
 //           face neighbours (the same-level cell, else the coarser cell that
-//           covers it), the relative jump 2|a-b|/(|a|+|b|) of rho exceeds
-//           grad_rho or that of p exceeds grad_p, or when rho dx^3 exceeds
+//           covers it), the relative jump of rho, 2|a-b| > grad_rho (|a|+|b|),
+//           or that of p exceeds its threshold, or when rho dx^3 exceeds
 //           mass.  The decision is taken in FP64 with each operation rounded
-//           as written (no contraction), so it is the same on every build.
+//           as written (no contraction), so it is the same on every build;
+//           density and pressure are computed once per cell first.
 //   expand  with expand = 1 a flag also flags the 26 same-level cells around
 //   grade   finest level first, a flagged cell X of level l flags the level
 //           l-1 cells covering the 27 level-l cells around X (2:1 rule)
@@ -42,23 +43,23 @@ struct RegridArgs {
   int *err;
 };
 
-// conservative -> primitive with floors, every operation rounded as written
-__device__ __forceinline__ void prim_exact(const double (&u)[5], double g, double smallr,
+// density and pressure of the criterion, with the floors, every operation
+// rounded as written: p = (gamma-1)(E - (m.m/2)/rho), one division per cell
+__device__ __forceinline__ void flag_rho_p(const double (&u)[5], double g, double smallr,
                                            double smallp, double &rho, double &p) {
   const double r = u[0] > smallr ? u[0] : smallr;
-  const double vx = __ddiv_rn(u[1], r), vy = __ddiv_rn(u[2], r), vz = __ddiv_rn(u[3], r);
-  const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
-  const double ek = __dmul_rn(__dmul_rn(0.5, r), v2);
-  double pr = __dmul_rn(__dsub_rn(g, 1.0), __dsub_rn(u[4], ek));
+  const double m2 = __dadd_rn(__dadd_rn(__dmul_rn(u[1], u[1]), __dmul_rn(u[2], u[2])),
+                              __dmul_rn(u[3], u[3]));
+  const double ek = __ddiv_rn(__dmul_rn(0.5, m2), r);
+  const double pr = __dmul_rn(__dsub_rn(g, 1.0), __dsub_rn(u[4], ek));
   const double pf = __dmul_rn(r, smallp);
-  if (pr < pf) pr = pf;
   rho = r;
-  p = pr;
+  p = pr < pf ? pf : pr;
 }
 
-__device__ __forceinline__ double rel_jump(double a, double b) {
-  const double s = __dadd_rn(fabs(a), fabs(b));
-  return s > 0.0 ? __ddiv_rn(__dmul_rn(2.0, fabs(__dsub_rn(a, b))), s) : 0.0;
+// the relative jump of a and b exceeds thr: 2|a-b| > thr (|a|+|b|)
+__device__ __forceinline__ bool jump_exceeds(double a, double b, double thr) {
+  return __dmul_rn(2.0, fabs(__dsub_rn(a, b))) > __dmul_rn(thr, __dadd_rn(fabs(a), fabs(b)));
 }
 
 template <class T>
@@ -67,47 +68,49 @@ __device__ __forceinline__ void load_cell(const T *U, int64_t S, int64_t g, doub
   for (int v = 0; v < 5; ++v) u[v] = double(U[v * S + g]);
 }
 
+// density and pressure of every real cell: rp[0][8N], rp[1][8N]
+template <class T>
+__global__ void k_flag_rp(RegridArgs a, const T *__restrict__ U, double *__restrict__ rp) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= 8 * int64_t(a.N)) return;
+  const int m = ikey_member(a.key[g >> 3]);
+  double u[5], r, p;
+  load_cell(U, a.S, g, u);
+  flag_rho_p(u, a.mgamma[m], a.msmallr[m], a.msmallp[m], r, p);
+  rp[g] = r;
+  rp[8 * int64_t(a.N) + g] = p;
+}
+
 // criterion masks: one thread per real oct
 template <class T>
-__global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U) {
+__global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *__restrict__ rp) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= a.N) return;
   const uint64_t key = a.key[o];
   const int m = ikey_member(key), l = ikey_lev(key);
+  const int64_t N8 = 8 * int64_t(a.N);
   uint32_t mask = 0;
   if (l < a.mlmax[m]) {
-    const double g = a.mgamma[m], sr = a.msmallr[m], sp = a.msmallp[m];
-    const bool grad = a.grad_rho > 0.0 || a.grad_p > 0.0;
     for (int c = 0; c < 8; ++c) {
-      double uc[5];
-      load_cell(U, a.S, 8 * int64_t(o) + c, uc);
-      bool f = a.mass > 0.0 && ldexp(uc[0], -3 * l) > a.mass;
-      if (!f && grad) {
-        double rc, pc;
-        prim_exact(uc, g, sr, sp, rc, pc);
-        for (int d = 0; d < 3 && !f; ++d)
-          for (int plus = 0; plus < 2 && !f; ++plus) {
-            // face neighbour: same oct, a real oct, or a ghost oct whose
-            // father cell is the covering coarser cell
-            const int bit = 1 << d;
-            int64_t gn;
-            if (((c >> d) & 1) != plus) {
-              gn = 8 * int64_t(o) + (c ^ bit);
-            } else {
-              const int32_t ne = a.fnb[(2 * d + plus) * int64_t(a.NE) + o];
-              if (ne < 0) continue;
-              if (ne < a.N)
-                gn = 8 * int64_t(ne) + (c ^ bit);
-              else
-                gn = a.csrc[ne - a.N];
-            }
-            double un[5], rn, pn;
-            load_cell(U, a.S, gn, un);
-            prim_exact(un, g, sr, sp, rn, pn);
-            if (a.grad_rho > 0.0 && rel_jump(rn, rc) > a.grad_rho) f = true;
-            if (a.grad_p > 0.0 && rel_jump(pn, pc) > a.grad_p) f = true;
+      const int64_t gc = 8 * int64_t(o) + c;
+      bool f = a.mass > 0.0 && ldexp(double(U[gc]), -3 * l) > a.mass;
+      const double rc = rp[gc], pc = rp[N8 + gc];
+      for (int d = 0; d < 3 && !f; ++d)
+        for (int plus = 0; plus < 2 && !f; ++plus) {
+          // face neighbour: same oct, a real oct, or a ghost oct whose
+          // father cell is the covering coarser cell
+          const int bit = 1 << d;
+          int64_t gn;
+          if (((c >> d) & 1) != plus) {
+            gn = 8 * int64_t(o) + (c ^ bit);
+          } else {
+            const int32_t ne = a.fnb[(2 * d + plus) * int64_t(a.NE) + o];
+            if (ne < 0) continue;
+            gn = ne < a.N ? 8 * int64_t(ne) + (c ^ bit) : int64_t(a.csrc[ne - a.N]);
           }
-      }
+          if (a.grad_rho > 0.0 && jump_exceeds(rp[gn], rc, a.grad_rho)) f = true;
+          if (a.grad_p > 0.0 && jump_exceeds(rp[N8 + gn], pc, a.grad_p)) f = true;
+        }
       if (f) mask |= 1u << c;
     }
   }
