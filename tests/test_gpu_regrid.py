@@ -157,3 +157,29 @@ def test_fp32_regrid_follows_the_fp64_mesh():
     assert abs(mass(g4) - m0) <= 1e-6 * m0
     g4.close()
     g8.close()
+
+
+@pytest.mark.parametrize("precision", [8, 4])
+def test_batched_regrid_equals_each_member_alone(precision):
+    """A batched handle regrids every member with the handle's criteria; each
+    member's new mesh and state equal the same mesh regridded alone."""
+    from paper_2607_20704_gb300 import amr
+    probs = [inputs.sod(3, 5), inputs.random_mesh(3, 5, seed=41), inputs.sedov(4, 5, radii={5: 0.15})]
+    kw = dict(refine_grad_rho=0.1, refine_grad_p=0.1, precision=precision, tile=128, schedule=0)
+    b = amr.Mesh.batch(probs, **kw)
+    b.advance(1)
+    b.regrid()
+    b.advance(1, sync=True)
+    for q, pr in enumerate(probs):
+        a = amr.Mesh(*pr.mesh_args(), **pr.params(), **kw)
+        a.advance(1)
+        a.regrid()
+        a.advance(1, sync=True)
+        b.select(q)
+        assert b.levels() == a.levels(), q
+        for l in a.levels():
+            ka, Ua = a.read(l)
+            kb, Ub = b.read(l)
+            assert np.array_equal(ka, kb) and np.array_equal(Ua, Ub), (q, l)
+        a.close()
+    b.close()
