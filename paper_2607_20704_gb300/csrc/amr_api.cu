@@ -79,13 +79,14 @@ enum Kid {
   K_SORT_KEYS, K_RADIX_HIST, K_RADIX_SCATTER, K_SCAN, K_GATHER, K_HASH_INSERT, K_FATHER_SON,
   K_GRADING, K_NEIGHBOURS, K_CLAIM, K_CACHE_FINALIZE, K_NBR_FIX, K_FACES, K_CACHE_SOURCES,
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
-  K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_COUNT
+  K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
     "father_son", "grading", "neighbours", "claim_comp", "cache_finalize", "neighbours_fix",
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
-    "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new"};
+    "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
+    "flag_rp", "flag_expand", "flag_grade"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -181,6 +182,7 @@ struct amr_mesh {
   void *U = nullptr, *Rc = nullptr;
   void *W = nullptr, *Q = nullptr, *F = nullptr, *C = nullptr;
   int64_t max_ls = 0, max_cs = 0;
+  int64_t ls_cap = 0, cs_cap = 0;  // elements the scratch arrays hold
 
   // work accounting
   int64_t launches = 0, graph_launches = 0;
@@ -236,6 +238,19 @@ static void dev_free(amr_mesh *h, void *ptr) {
       return;
     }
   }
+}
+
+// hand a buffer from one handle to another (no copy)
+static void move_buf(amr_mesh *to, amr_mesh *from, void *ptr) {
+  if (!ptr) return;
+  for (size_t t = 0; t < from->bufs.size(); ++t)
+    if (from->bufs[t].p == ptr) {
+      to->bufs.push_back(from->bufs[t]);
+      to->bytes += from->bufs[t].bytes;
+      from->bytes -= from->bufs[t].bytes;
+      from->bufs.erase(from->bufs.begin() + t);
+      return;
+    }
 }
 
 template <class P>
@@ -713,6 +728,32 @@ static amr_status upload_member_params(amr_mesh *h) {
   return AMR_OK;
 }
 
+// level-step scratch for max_ls / max_cs: kept when the buffers a regrid
+// handed over are large enough, else (re)allocated
+static amr_status ensure_scratch(amr_mesh *h) {
+  const size_t es = h->elem();
+  const int64_t ls = std::max<int64_t>(h->max_ls, 1), cs = std::max<int64_t>(h->max_cs, 1);
+  if (!h->W || !h->Q || !h->F || h->ls_cap < ls) {
+    dev_free(h, h->W);
+    dev_free(h, h->Q);
+    dev_free(h, h->F);
+    h->W = h->Q = h->F = nullptr;
+    h->ls_cap = 0;
+    AMR_TRY(dev_alloc(h, &h->W, es * 5 * size_t(ls)));
+    AMR_TRY(dev_alloc(h, &h->Q, es * 20 * size_t(ls)));
+    AMR_TRY(dev_alloc(h, &h->F, es * 15 * size_t(ls)));
+    h->ls_cap = ls;
+  }
+  if (!h->C || h->cs_cap < cs) {
+    dev_free(h, h->C);
+    h->C = nullptr;
+    h->cs_cap = 0;
+    AMR_TRY(dev_alloc(h, &h->C, es * 5 * size_t(cs)));
+    h->cs_cap = cs;
+  }
+  return AMR_OK;
+}
+
 // member parameters on the device (from h->mem)
 static amr_status upload_members(amr_mesh *h) {
   const int M = h->M;
@@ -977,10 +1018,7 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   AMR_TRY(upload(h, &h->segs, h->segs_h));
   AMR_TRY(upload(h, &h->tiles, h->tiles_h));
   h->max_cs = 24 * NC;
-  AMR_TRY(dev_alloc(h, &h->W, es * 5 * size_t(std::max<int64_t>(h->max_ls, 1))));
-  AMR_TRY(dev_alloc(h, &h->Q, es * 20 * size_t(std::max<int64_t>(h->max_ls, 1))));
-  AMR_TRY(dev_alloc(h, &h->F, es * 15 * size_t(std::max<int64_t>(h->max_ls, 1))));
-  AMR_TRY(dev_alloc(h, &h->C, es * 5 * size_t(h->max_cs > 0 ? h->max_cs : 1)));
+  AMR_TRY(ensure_scratch(h));
   if (h->max_cs) CUDA_TRY(cudaMemsetAsync(h->C, 0, es * 5 * size_t(h->max_cs), h->s));
   AMR_TRY(alloc_n(h, &h->dt_dev, M));
   AMR_TRY(alloc_n(h, &h->dtdx_dev, M));
@@ -1379,21 +1417,23 @@ static amr_status compute_flags(amr_mesh *h, uint32_t *raw, uint32_t *flag, cons
   const unsigned g = nblocks(h->N);
   double *rp = nullptr;
   AMR_TRY(alloc_n(h, &rp, 16 * h->N));
+  const unsigned g8 = nblocks(8 * h->N);  // 256-thread blocks: whole octs per warp
   if (h->p.precision == 4) {
-    launch(h, K_FLAG, k_flag_rp<float>, dim3(nblocks(8 * h->N)), dim3(256), a, (const float *)h->U, rp);
-    launch(h, K_FLAG, k_flag_raw<float>, dim3(g), dim3(256), a, (const float *)h->U,
+    launch(h, K_FLAG_RP, k_flag_rp<float>, dim3(g8), dim3(256), a, (const float *)h->U, rp);
+    launch(h, K_FLAG, k_flag_raw<float>, dim3(g8), dim3(256), a, (const float *)h->U,
            (const double *)rp);
   } else {
-    launch(h, K_FLAG, k_flag_rp<double>, dim3(nblocks(8 * h->N)), dim3(256), a, (const double *)h->U, rp);
-    launch(h, K_FLAG, k_flag_raw<double>, dim3(g), dim3(256), a, (const double *)h->U,
+    launch(h, K_FLAG_RP, k_flag_rp<double>, dim3(g8), dim3(256), a, (const double *)h->U, rp);
+    launch(h, K_FLAG, k_flag_raw<double>, dim3(g8), dim3(256), a, (const double *)h->U,
            (const double *)rp);
   }
   dev_free(h, rp);
-  launch(h, K_FLAG, k_flag_expand, dim3(g), dim3(256), a);
+  launch(h, K_FLAG_EXPAND, k_flag_expand, dim3(g8), dim3(256), a);
+  (void)g;
   for (auto &m : h->mem)
     for (int l = m.lmax - 1; l > m.lmin; --l) {
       const int lo = int(m.oct_base + m.lo[l]), hi = int(m.oct_base + m.lo[l + 1]);
-      if (hi > lo) launch(h, K_FLAG, k_flag_grade, dim3(nblocks(hi - lo)), dim3(256), a, lo, hi);
+      if (hi > lo) launch(h, K_FLAG_GRADE, k_flag_grade, dim3(nblocks(hi - lo)), dim3(256), a, lo, hi);
     }
   return check_device(h, where);
 }
@@ -1503,10 +1543,26 @@ extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *remove
   auto abandon = [&](amr_status e) {
     std::string msg = g_last_error;
     cudaStreamSynchronize(h->s);
+    // the old mesh keeps (or gets back) level-step scratch of its own size
+    if (nh->W && nh->Q && nh->F) {
+      for (void *b : {nh->W, nh->Q, nh->F}) move_buf(h, nh, b);
+      h->W = nh->W;
+      h->Q = nh->Q;
+      h->F = nh->F;
+      h->ls_cap = nh->ls_cap;
+      nh->W = nh->Q = nh->F = nullptr;
+    }
+    if (nh->C) {
+      move_buf(h, nh, nh->C);
+      h->C = nh->C;
+      h->cs_cap = nh->cs_cap;
+      nh->C = nullptr;
+    }
     destroy_all(nh);
     release();
+    const amr_status se = ensure_scratch(h);
     g_last_error = msg;
-    return e;
+    return se != AMR_OK ? se : e;
   };
   if ((st = upload_members(nh)) != AMR_OK || (st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_new, n_out)) != AMR_OK || (st = alloc_n(nh, &d_mem, n_out)) != AMR_OK ||
@@ -1523,6 +1579,16 @@ extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *remove
            d_mem, d_i, d_j, d_k, d_U, d_new);
   if ((st = check_device(h, "amr_regrid")) != AMR_OK) return abandon(st);
   release();
+  // the level-step scratch goes over to the new mesh (reused if large enough)
+  for (void **b : {&h->W, &h->Q, &h->F, &h->C}) move_buf(nh, h, *b);
+  nh->W = h->W;
+  nh->Q = h->Q;
+  nh->F = h->F;
+  nh->C = h->C;
+  nh->ls_cap = h->ls_cap;
+  nh->cs_cap = h->cs_cap;
+  h->W = h->Q = h->F = h->C = nullptr;
+  h->ls_cap = h->cs_cap = 0;
   if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, d_U, d_new)) != AMR_OK)
     return abandon(st);
   // carry the per-member step counters and last time steps over

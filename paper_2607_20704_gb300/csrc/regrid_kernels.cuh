@@ -57,9 +57,12 @@ __device__ __forceinline__ void flag_rho_p(const double (&u)[5], double g, doubl
   p = pr < pf ? pf : pr;
 }
 
-// the relative jump of a and b exceeds thr: 2|a-b| > thr (|a|+|b|)
+// the relative jump of a and b exceeds thr > 0: 2|a-b| > thr (|a|+|b|); both
+// sides are non-negative, so they compare as the integers of their bits
 __device__ __forceinline__ bool jump_exceeds(double a, double b, double thr) {
-  return __dmul_rn(2.0, fabs(__dsub_rn(a, b))) > __dmul_rn(thr, __dadd_rn(fabs(a), fabs(b)));
+  const double lhs = __dmul_rn(2.0, fabs(__dsub_rn(a, b)));
+  const double rhs = __dmul_rn(thr, __dadd_rn(fabs(a), fabs(b)));
+  return __double_as_longlong(lhs) > __double_as_longlong(rhs);
 }
 
 template <class T>
@@ -81,19 +84,20 @@ __global__ void k_flag_rp(RegridArgs a, const T *__restrict__ U, double *__restr
   rp[8 * int64_t(a.N) + g] = p;
 }
 
-// criterion masks: one thread per real oct
+// criterion masks: one thread per real cell, the 8 cells of an oct in
+// consecutive lanes; a ballot assembles the oct's mask
 template <class T>
 __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *__restrict__ rp) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= a.N) return;
-  const uint64_t key = a.key[o];
-  const int m = ikey_member(key), l = ikey_lev(key);
+  const int64_t gc = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t N8 = 8 * int64_t(a.N);
-  uint32_t mask = 0;
-  if (l < a.mlmax[m]) {
-    for (int c = 0; c < 8; ++c) {
-      const int64_t gc = 8 * int64_t(o) + c;
-      bool f = a.mass > 0.0 && ldexp(double(U[gc]), -3 * l) > a.mass;
+  const bool in = gc < N8;
+  const int o = int(gc >> 3), c = int(gc & 7);
+  bool f = false;
+  if (in) {
+    const uint64_t key = a.key[o];
+    const int m = ikey_member(key), l = ikey_lev(key);
+    if (l < a.mlmax[m]) {
+      f = a.mass > 0.0 && ldexp(double(U[gc]), -3 * l) > a.mass;
       const double rc = rp[gc], pc = rp[N8 + gc];
       for (int d = 0; d < 3 && !f; ++d)
         for (int plus = 0; plus < 2 && !f; ++plus) {
@@ -111,26 +115,27 @@ __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *
           if (a.grad_rho > 0.0 && jump_exceeds(rp[gn], rc, a.grad_rho)) f = true;
           if (a.grad_p > 0.0 && jump_exceeds(rp[N8 + gn], pc, a.grad_p)) f = true;
         }
-      if (f) mask |= 1u << c;
     }
   }
-  a.raw[o] = mask;
+  const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
+  if (in && c == 0) a.raw[o] = (b >> (threadIdx.x & 24)) & 0xFFu;
 }
 
-// expansion over the 3x3x3 same-level block (or a copy when expand = 0)
+// expansion over the 3x3x3 same-level block (or a copy when expand = 0);
+// one thread per real cell, masks assembled by a ballot
 __global__ void k_flag_expand(RegridArgs a) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= a.N) return;
-  const uint64_t key = a.key[o];
-  const int m = ikey_member(key), l = ikey_lev(key);
-  uint32_t mask = 0;
-  if (l < a.mlmax[m]) {
-    if (!a.expand) {
-      mask = a.raw[o];
-    } else {
-      for (int c = 0; c < 8; ++c) {
+  const int64_t gc = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const bool in = gc < 8 * int64_t(a.N);
+  const int o = int(gc >> 3), c = int(gc & 7);
+  bool f = false;
+  if (in) {
+    const uint64_t key = a.key[o];
+    const int m = ikey_member(key), l = ikey_lev(key);
+    if (l < a.mlmax[m]) {
+      if (!a.expand) {
+        f = (a.raw[o] >> c) & 1u;
+      } else {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-        bool f = false;
         for (int dz = -1; dz <= 1 && !f; ++dz)
           for (int dy = -1; dy <= 1 && !f; ++dy)
             for (int dx = -1; dx <= 1 && !f; ++dx) {
@@ -141,11 +146,11 @@ __global__ void k_flag_expand(RegridArgs a) {
               const int cc = (fx & 1) | ((fy & 1) << 1) | ((fz & 1) << 2);
               if ((a.raw[e] >> cc) & 1u) f = true;
             }
-        if (f) mask |= 1u << c;
       }
     }
   }
-  a.flag[o] = mask;
+  const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
+  if (in && c == 0) a.flag[o] = (b >> (threadIdx.x & 24)) & 0xFFu;
 }
 
 // grading closure from the octs [lo, hi) of one level l > levelmin: every
