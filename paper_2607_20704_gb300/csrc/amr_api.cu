@@ -330,6 +330,8 @@ static amr_status check_device(amr_mesh *h, const char *where) {
     return fail(AMR_EGRADING, "%s: the octree is not graded (a father-cell neighbourhood is missing)", where);
   if (err & kErrNaN) return fail(AMR_ENAN, "%s: non-finite leaf state", where);
   if (err & kErrTimeout) return fail(AMR_ETIMEOUT, "%s: a device wait gave up", where);
+  if (err & kErrIndex)
+    return fail(AMR_ECUDA, "%s: an index-table entry out of range (bounds-checked build)", where);
   return fail(AMR_ECUDA, "%s: internal index error (bits 0x%x)", where, err);
 }
 
@@ -513,6 +515,7 @@ static StepArgs<T> step_args(amr_mesh *h, bool device_dt, double dt) {
   a.dt_host = dt;
   a.mact = device_dt ? h->mact : nullptr;
   a.reflux = h->p.reflux;
+  a.err = h->err;
   return a;
 }
 

@@ -23,7 +23,27 @@ enum : int {
   kErrClaimOverflow = 32,
   kErrCacheMismatch = 64,
   kErrTimeout = 128,
+  kErrIndex = 256,  // bounds-checked builds: an index-table entry out of range
 };
+
+// Bounds-checked builds (compiled with AMR_CHECKED): an index read from an
+// index table is tested against the extent of what it addresses; a bad one
+// sets kErrIndex in the error word and is replaced by `fallback`, so that no
+// access leaves its array.  Plain builds pass the index through.
+#ifdef AMR_CHECKED
+__device__ __forceinline__ int64_t checked(int64_t i, int64_t lo, int64_t hi, int *err,
+                                           int64_t fallback = 0) {
+  if (i < lo || i >= hi) {
+    atomicOr(err, kErrIndex);
+    return fallback;
+  }
+  return i;
+}
+#else
+__device__ __forceinline__ int64_t checked(int64_t i, int64_t, int64_t, int *, int64_t = 0) {
+  return i;
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // keys (Sec. 2.1).  External keys (the C ABI's): level in bits 60..63, i/j/k

@@ -55,6 +55,7 @@ struct StepArgs {
   // members taking part in this coarse step (1) or finished (0); NULL: all
   const int *mact;
   int reflux;
+  int *err;  // device error word (range errors of bounds-checked builds)
 };
 
 struct CflArgs {

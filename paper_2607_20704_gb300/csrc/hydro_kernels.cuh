@@ -149,6 +149,13 @@ __device__ __forceinline__ void tile_loop(const StepArgs<T> &a, Size size, Body 
     const Tile td = a.tiles[ti];
     if (a.mact && !__ldg(a.mact + a.segs[td.seg].member)) continue;  // finished member
     const SegCtx<T> sc = seg_ctx(a, td.seg);
+#ifdef AMR_CHECKED
+    // the segment's local cells must fit the scratch arrays
+    if (sc.base < 0 || sc.base + 8 * (sc.nl + sc.ncl) > a.LS) {
+      atomicOr(a.err, kErrIndex);
+      continue;
+    }
+#endif
     const int item = td.start + threadIdx.x;
     if (item < size(sc)) body(sc, item);
   }
@@ -173,7 +180,9 @@ __device__ __forceinline__ int nbr_local(const StepArgs<T> &a, const SegCtx<T> &
   if (((c >> d) & 1) != plus) return t ^ bit;
   const int32_t ne = __ldg(a.fnb + (2 * d + plus) * int64_t(a.NE) + e);
   if (ne < 0) return -1;
-  return 8 * local_of_ext(a, s, ne) + (c ^ bit);
+  // a face neighbour is in the same (member, level) segment: else "none"
+  const int q = int(checked(local_of_ext(a, s, ne), 0, s.nl + s.ncl, a.err, -1));
+  return q < 0 ? -1 : 8 * q + (c ^ bit);
 }
 
 template <class T>
@@ -195,7 +204,8 @@ __global__ void k_prolong(StepArgs<T> a) {
     const T *Uv = a.U + v * a.S;
     T src[7];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) src[k] = Uv[__ldg(a.csrc + k * int64_t(a.NC) + cs)];
+    for (int k = 0; k < 7; ++k)
+      src[k] = Uv[checked(__ldg(a.csrc + k * int64_t(a.NC) + cs), 0, 8 * int64_t(a.NE), a.err)];
     const T uc = src[0];
     const T sx = minmod(src[2] - uc, uc - src[1]);
     const T sy = minmod(src[4] - uc, uc - src[3]);
@@ -441,7 +451,8 @@ __device__ __forceinline__ void flux_dir(const StepArgs<T> &a, const SegCtx<T> &
                              : reflux_slot<D>(s.clo, s.nl, t >> 3, 2 * D + 1, c);
       const T sg = real ? T(1) : T(-1);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (sg * s.dtdx) * F[v] / T(8);
+      for (int v = 0; v < 5; ++v)
+        a.C[v * a.CS + checked(gslot, 0, a.CS, a.err)] = (sg * s.dtdx) * F[v] / T(8);
     }
   }
   const int o = s.base + t;
@@ -473,7 +484,7 @@ __global__ void k_flux(StepArgs<T> a) {
 template <class T>
 __device__ __forceinline__ void update_cell(const StepArgs<T> &a, const SegCtx<T> &s, int g,
                                             const T (&dx)[5], const T (&dy)[5], const T (&dz)[5]) {
-  const int rs = __ldg(a.rslot + g);
+  const int rs = int(checked(__ldg(a.rslot + g), -1, a.NC, a.err, -1));
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     T *Ug = a.U + v * a.S + g;
@@ -520,7 +531,8 @@ __device__ __forceinline__ void faces_dir(const StepArgs<T> &a, const SegCtx<T> 
     if (a.reflux && (tm >> 3) >= s.nl) {
       const int gslot = reflux_slot<D>(s.clo, s.nl, tm >> 3, 2 * D + 1, c);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(-1) * s.dtdx) * Fm[v] / T(8);
+      for (int v = 0; v < 5; ++v)
+        a.C[v * a.CS + checked(gslot, 0, a.CS, a.err)] = (T(-1) * s.dtdx) * Fm[v] / T(8);
     }
   }
   const int tp = nbr_local(a, s, t, e, c, D, 1);
@@ -529,7 +541,8 @@ __device__ __forceinline__ void faces_dir(const StepArgs<T> &a, const SegCtx<T> 
     if (a.reflux && (tp >> 3) >= s.nl) {
       const int gslot = reflux_slot<D>(s.clo, s.nl, tp >> 3, 2 * D, c);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) a.C[v * a.CS + gslot] = (T(1) * s.dtdx) * Fp[v] / T(8);
+      for (int v = 0; v < 5; ++v)
+        a.C[v * a.CS + checked(gslot, 0, a.CS, a.err)] = (T(1) * s.dtdx) * Fp[v] / T(8);
     }
   }
 #pragma unroll
@@ -579,7 +592,7 @@ __global__ void k_reflux_restrict(StepArgs<T> a) {
               const int o = s.lo + (r - v * s.nl);
               const uint64_t k = __ldg(a.key + o);
               const int fc = int((ikey_x(k) & 1) | ((ikey_y(k) & 1) << 1) | ((ikey_z(k) & 1) << 2));
-              const int f = __ldg(a.father + o);
+              const int f = int(checked(__ldg(a.father + o), 0, a.N, a.err));
               const T *src = a.U + v * a.S + 8 * int64_t(o);
               T sum = T(0);
 #pragma unroll

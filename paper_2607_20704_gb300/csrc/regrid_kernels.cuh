@@ -110,7 +110,8 @@ __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *
           } else {
             const int32_t ne = a.fnb[(2 * d + plus) * int64_t(a.NE) + o];
             if (ne < 0) continue;
-            gn = ne < a.N ? 8 * int64_t(ne) + (c ^ bit) : int64_t(a.csrc[ne - a.N]);
+            gn = ne < a.N ? 8 * int64_t(ne) + (c ^ bit)
+                          : checked(a.csrc[checked(ne - a.N, 0, a.NC, a.err)], 0, N8, a.err);
           }
           if (a.grad_rho > 0.0 && jump_exceeds(rp[gn], rc, a.grad_rho)) f = true;
           if (a.grad_p > 0.0 && jump_exceeds(rp[N8 + gn], pc, a.grad_p)) f = true;
