@@ -94,6 +94,8 @@ def lib():
                 "orc_uniform_cfl_dt": (D, [I, P, D, D, D, D]),
                 "orc_1d_step": (I, [I, P, D, D, D, D]),
                 "orc_flags": (I, [P, C.POINTER(_RegridParams), P]),
+                "orc_mg_solve": (I, [I, D, P, D, I, I, I, P, P]),
+                "orc_mg_residual": (D, [I, D, P, D, P]),
                 "orc_regrid": (I, [C.POINTER(P), C.POINTER(_RegridParams), C.POINTER(I64),
                                    C.POINTER(I64)]),
             }
@@ -297,3 +299,29 @@ def step_1d(U, gamma, dt, smallr=1e-10, smallc=1e-10):
     if rc:
         raise OracleError(rc, "1d_step")
     return U
+
+
+def mg_solve(rho, dx, fourpiG=1.0, ncycles=4, nu1=2, nu2=2, phi0=None):
+    """Multigrid V-cycles (Sec. 5) for (Laplacian phi) = fourpiG (rho - mean)
+    on a periodic n^3 grid.  rho is an (n, n, n) array indexed [x, y, z].
+    Returns (phi [x, y, z] with zero mean, residual L2 norm after each cycle)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    n = rho.shape[0]
+    assert rho.shape == (n, n, n)
+    r = np.ascontiguousarray(rho.ravel(order="F"))
+    phi = np.zeros(n ** 3) if phi0 is None else np.ascontiguousarray(
+        np.asarray(phi0, dtype=np.float64).ravel(order="F"))
+    res = np.zeros(max(ncycles, 1))
+    rc = lib().orc_mg_solve(n, float(dx), _ptr(r), float(fourpiG), int(ncycles), int(nu1),
+                            int(nu2), _ptr(phi), _ptr(res))
+    if rc:
+        raise OracleError(rc, "mg_solve")
+    return phi.reshape((n, n, n), order="F"), res[:ncycles]
+
+
+def mg_residual(rho, dx, phi, fourpiG=1.0):
+    rho = np.asarray(rho, dtype=np.float64)
+    n = rho.shape[0]
+    r = np.ascontiguousarray(rho.ravel(order="F"))
+    p = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).ravel(order="F"))
+    return float(lib().orc_mg_residual(n, float(dx), _ptr(r), float(fourpiG), _ptr(p)))

@@ -99,6 +99,20 @@ int orc_flags(const orc_mesh *m, const orc_regrid_params *rp, uint8_t *flag);
  * zero).  created/removed: numbers of octs (may be NULL). */
 int orc_regrid(orc_mesh **pm, const orc_regrid_params *rp, int64_t *created, int64_t *removed);
 
+/* --- self-gravity: multigrid Poisson V-cycles on a periodic level (Sec. 5) --
+ * Solves (sum of the 6 neighbours - 6 phi) / dx^2 = fourpiG (rho - mean rho)
+ * on an n^3 periodic grid (n a power of two, arrays [x + n (y + n z)]):
+ * red-black Gauss-Seidel smoothing (colour = parity of x + y + z, the parity
+ * of the cell index inside its oct), residual restricted by the mean of the
+ * 8 children, correction prolongated trilinearly with weights
+ * (1, 3, 3, 9, 3, 9, 9, 27)/64, down to a 2^3 grid.  phi holds the initial
+ * guess and receives the solution (mean subtracted at the end); resid[c]
+ * gets the L2 norm of the residual after V-cycle c (may be NULL). */
+int orc_mg_solve(int n, double dx, const double *rho, double fourpiG, int ncycles, int nu1,
+                 int nu2, double *phi, double *resid);
+/* L2 norm of the residual of phi for the source fourpiG (rho - mean rho) */
+double orc_mg_residual(int n, double dx, const double *rho, double fourpiG, const double *phi);
+
 /* --- independent cross-check solvers ----------------------------------------- */
 int orc_uniform_step(int n, double *U, double gamma, double dt, double smallr,
                      double smallc);
