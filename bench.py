@@ -48,6 +48,8 @@ def parse():
                     help="skip the 512-mesh batched ensemble measurement")
     ap.add_argument("--batched-members", type=int, default=512)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop sweep")
+    ap.add_argument("--no-poisson", action="store_true",
+                    help="skip the multigrid V-cycle measurement")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the adaptive run (regrid before every coarse step)")
     ap.add_argument("--serving-requests", type=int, default=48)
@@ -381,6 +383,58 @@ def run_adaptive(prob, precision, steps, torch, device):
             "regrid_kernel_ms": round(ktot / 3, 4), "regrid_kernels": regrid_kernels}
 
 
+def run_poisson(level, cycles, torch, device):
+    """Multigrid V-cycles on a periodic 2^level grid holding a lognormal
+    density (the cosmology-shaped configuration's base level): cell-updates
+    per V-cycle per second (cells of the grid per V-cycle over its time, the
+    paper's unit for the solver; one call of `cycles` V-cycles including the
+    density gather and the potential scatter, no residual norms), residual
+    reduction per V-cycle (from a separate call), and the kernel breakdown."""
+    from paper_2607_20704_gb300 import amr
+    rng = np.random.default_rng(7)
+    n = 1 << level
+    g, _ = inputs_gaussian(n, rng)
+    rho_b = np.exp(g - 0.5 * 1.5 ** 2)
+
+    def fn(x, y, z):
+        bx = np.minimum((x * n).astype(np.int64), n - 1)
+        by = np.minimum((y * n).astype(np.int64), n - 1)
+        bz = np.minimum((z * n).astype(np.int64), n - 1)
+        zero = 0.0 * x
+        return rho_b[bx, by, bz], zero, zero, zero, 1.0 + zero
+    from paper_2607_20704_gb300 import inputs
+    prob = inputs.uniform_grid(level, fn)
+    m = amr.Mesh(*prob.mesh_args(), **prob.params(), stream=bench_stream())
+    st = m.stream
+    res = m.poisson(1.0, 6)  # warm-up (allocates the hierarchy); convergence
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    m.poisson(1.0, cycles, residuals=False)
+    e1.record(st)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1)
+    m.set_timing(True)
+    m.poisson(1.0, 2, residuals=False)
+    kt = m.read_timing()
+    m.set_timing(False)
+    m.close()
+    cells = n ** 3
+    rates = res[1:] / res[:-1]
+    ktot = sum(v[0] for v in kt.values()) or 1.0
+    return {"grid": f"{n}^3 periodic", "cells": cells, "vcycles": cycles,
+            "ms_per_vcycle": round(ms / cycles, 4),
+            "cell_updates_per_s": cells * cycles / (ms * 1e-3),
+            "residual_reduction_per_vcycle": round(float(np.median(rates)), 4),
+            "smoother": "red-black Gauss-Seidel, 2 + 2 sweeps; restriction 1/8; trilinear prolongation",
+            "kernels": {k: round(v[0] / ktot, 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}}
+
+
+def inputs_gaussian(n, rng):
+    from paper_2607_20704_gb300 import inputs
+    return inputs.gaussian_field(n, -2.0, 1.5, rng)
+
+
 def run_serving(n_requests, rates, torch):
     """Serving loop under Poisson arrivals at each rate of the sweep: p50/p99
     latency (submit -> result on the host) and sustained leaf cell-updates/s
@@ -580,6 +634,7 @@ def main():
             other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
             other["steps"] = args.steps
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
+        poisson = None if args.no_poisson else run_poisson(8, 10, torch, device)
         adaptive = None
         if not args.no_adaptive:
             adaptive = {("fp64" if p == 8 else "fp32"): run_adaptive(prob, p, 10, torch, device)
@@ -651,6 +706,8 @@ def main():
                                         * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)}
     if adaptive is not None:
         line["adaptive"] = adaptive
+    if poisson is not None:
+        line["poisson"] = poisson
     if batched is not None:
         line["batched"] = batched
     if serving is not None:

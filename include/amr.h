@@ -199,6 +199,28 @@ amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *removed);
  * 8 * octs of the level.  Synchronous. */
 amr_status amr_flag(amr_handle h, int level, uint8_t *flags, int64_t cap);
 
+/*
+ * amr_poisson -- self-gravity potential of the selected member's base level
+ * (Sec. 5): n_vcycles multigrid V-cycles for
+ *     (sum of the 6 face neighbours - 6 phi) / dx^2 = fourpiG (rho - mean rho)
+ * on the periodic levelmin grid (complete by construction): red-black
+ * Gauss-Seidel smoothing (colour = parity of the cell's index inside its oct;
+ * 2 sweeps before and after the coarse correction), residual restriction by
+ * the mean of the 8 children, trilinear prolongation with weights
+ * (1,3,3,9,3,9,9,27)/64, down to 2^3 cells (8 sweeps there).  The solution
+ * of the previous call is the initial guess (zero at first and after a
+ * regrid); the potential returned by amr_read_phi has zero mean.  resid
+ * (may be NULL) receives the L2 norm of the base-level residual after each
+ * V-cycle.  FP64 whatever the precision of the state.  Synchronous.  Errors:
+ * AMR_EINVAL (n_vcycles outside [0, 1020], levelmin above 10).
+ */
+amr_status amr_poisson(amr_handle h, double fourpiG, int n_vcycles, double *resid);
+
+/* Potential of the selected member's base-level cells after amr_poisson,
+ * phi[8 * n + c] for cell c of the n-th oct (amr_read order); cap >= 8 *
+ * octs of levelmin. */
+amr_status amr_read_phi(amr_handle h, double *phi, int64_t cap);
+
 /* Frees every device buffer of the handle (after synchronising its stream). */
 amr_status amr_destroy(amr_handle h);
 

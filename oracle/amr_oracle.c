@@ -1338,6 +1338,8 @@ done:
 /* trilinear interpolation with weights (1,3,3,9,3,9,9,27)/64.  On the      */
 /* periodic base level the hierarchy is the same box at half the resolution */
 /* per level, down to 2^3 cells; the coarsest grid is smoothed (8 sweeps). */
+/* The Gauss-Seidel update multiplies by the rounded 1/6 and the residual   */
+/* by 1/dx^2 (exact, dx being a power of two), so that no step divides.     */
 /* ------------------------------------------------------------------------- */
 
 static int64_t mg_at(int n, int64_t x, int64_t y, int64_t z) {
@@ -1358,7 +1360,7 @@ static void mg_smooth(int n, double dx2, const double *f, double *phi) {
         for (int64_t x = 0; x < n; ++x) {
           if ((int)((x + y + z) & 1) != colour) continue;
           int64_t t = mg_at(n, x, y, z);
-          phi[t] = (mg_nbsum(n, phi, x, y, z) - dx2 * f[t]) / 6.0;
+          phi[t] = (mg_nbsum(n, phi, x, y, z) - dx2 * f[t]) * (1.0 / 6.0);
         }
 }
 
@@ -1367,7 +1369,7 @@ static void mg_residual(int n, double dx2, const double *f, const double *phi, d
     for (int64_t y = 0; y < n; ++y)
       for (int64_t x = 0; x < n; ++x) {
         int64_t t = mg_at(n, x, y, z);
-        r[t] = f[t] - (mg_nbsum(n, phi, x, y, z) - 6.0 * phi[t]) / dx2;
+        r[t] = f[t] - (mg_nbsum(n, phi, x, y, z) - 6.0 * phi[t]) * (1.0 / dx2);
       }
 }
 

@@ -96,7 +96,8 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_lookup", "amr_read_index", "amr_read_cache", "amr_fill_ghosts", "amr_get_info",
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
-           "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag", "amr_server_create", "amr_server_submit",
+           "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag",
+           "amr_poisson", "amr_read_phi", "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
            "amr_server_destroy"]
 
@@ -146,6 +147,8 @@ def load(path: str | None = None):
             "amr_member_errors": (I, [P, P, I]),
             "amr_regrid": (I, [P, P, P]),
             "amr_flag": (I, [P, I, P, I64]),
+            "amr_poisson": (I, [P, D, I, P]),
+            "amr_read_phi": (I, [P, P, I64]),
             "amr_server_create": (I, [C.POINTER(amr_server_params), C.POINTER(P)]),
             "amr_server_submit": (I, [P, C.POINTER(amr_request), C.POINTER(I64)]),
             "amr_server_wait": (I, [P, I64, D, C.POINTER(I)]),
@@ -309,6 +312,24 @@ class Mesh:
         n = self.num_octs(level)
         out = np.zeros(8 * max(n, 1), np.uint8)
         _check(load().amr_flag(self._h, int(level), _ptr(out), 8 * max(n, 1)), "amr_flag")
+        return out[:8 * n]
+
+    def poisson(self, fourpiG: float = 1.0, n_vcycles: int = 4, residuals: bool = True):
+        """Multigrid V-cycles (Sec. 5) on the base level; returns the L2 norm
+        of the residual after each cycle (None when residuals=False, which
+        skips computing them)."""
+        if not residuals:
+            _check(load().amr_poisson(self._h, float(fourpiG), int(n_vcycles), None), "amr_poisson")
+            return None
+        res = np.zeros(max(int(n_vcycles), 1), np.float64)
+        _check(load().amr_poisson(self._h, float(fourpiG), int(n_vcycles), _ptr(res)), "amr_poisson")
+        return res[:int(n_vcycles)]
+
+    def read_phi(self):
+        """Potential of the base-level cells, [8 n] in read order."""
+        n = self.num_octs(self.levelmin)
+        out = np.zeros(8 * max(n, 1), np.float64)
+        _check(load().amr_read_phi(self._h, _ptr(out), 8 * max(n, 1)), "amr_read_phi")
         return out[:8 * n]
 
     def member_errors(self):

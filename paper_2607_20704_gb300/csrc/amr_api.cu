@@ -20,6 +20,7 @@
 
 #include "hydro_kernels.cuh"
 #include "regrid_kernels.cuh"
+#include "mg_kernels.cuh"
 #include "index_kernels.cuh"
 
 using namespace amr;
@@ -79,14 +80,15 @@ enum Kid {
   K_SORT_KEYS, K_RADIX_HIST, K_RADIX_SCATTER, K_SCAN, K_GATHER, K_HASH_INSERT, K_FATHER_SON,
   K_GRADING, K_NEIGHBOURS, K_CLAIM, K_CACHE_FINALIZE, K_NBR_FIX, K_FACES, K_CACHE_SOURCES,
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
-  K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE, K_COUNT
+  K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
+  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
     "father_son", "grading", "neighbours", "claim_comp", "cache_finalize", "neighbours_fix",
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
-    "flag_rp", "flag_expand", "flag_grade"};
+    "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -183,6 +185,17 @@ struct amr_mesh {
   void *W = nullptr, *Q = nullptr, *F = nullptr, *C = nullptr;
   int64_t max_ls = 0, max_cs = 0;
   int64_t ls_cap = 0, cs_cap = 0;  // elements the scratch arrays hold
+
+  // multigrid (base level of the selected member): dense arrays per level,
+  // finest first; the potential of the base cells in mesh order
+  struct MGLevel {
+    int n = 0;
+    double *f = nullptr, *p = nullptr;
+  };
+  std::vector<MGLevel> mg;
+  int mg_member = -1;
+  double *mg_rho = nullptr, *mg_r = nullptr, *mg_part = nullptr, *mg_res = nullptr;
+  double *phi = nullptr;
 
   // work accounting
   int64_t launches = 0, graph_launches = 0;
@@ -1616,6 +1629,125 @@ extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *remove
   destroy_all(nh);
   return check_device(h, "amr_regrid");
 #undef REGRID_TRY
+}
+
+// ---------------------------------------------------------------------------
+// self-gravity: multigrid V-cycles on the base level (Sec. 5)
+// ---------------------------------------------------------------------------
+constexpr int kMGParts = 1024;  // blocks of the reductions
+constexpr int kMGPre = 2, kMGPost = 2, kMGCoarsest = 8;
+
+static amr_status mg_setup(amr_mesh *h, int member, int lmin) {
+  if (h->mg_member == member && !h->mg.empty() && h->mg[0].n == (1 << lmin)) return AMR_OK;
+  for (auto &L : h->mg) {
+    dev_free(h, L.f);
+    dev_free(h, L.p);
+  }
+  h->mg.clear();
+  for (void *b : {(void *)h->mg_rho, (void *)h->mg_r, (void *)h->mg_part, (void *)h->mg_res,
+                  (void *)h->phi})
+    dev_free(h, b);
+  const int n0 = 1 << lmin;
+  for (int n = n0; n >= 2; n >>= 1) {
+    amr_mesh::MGLevel L;
+    L.n = n;
+    const int64_t m = int64_t(n) * n * n;
+    AMR_TRY(alloc_n(h, &L.f, m));
+    AMR_TRY(alloc_n(h, &L.p, m));
+    CUDA_TRY(cudaMemsetAsync(L.p, 0, sizeof(double) * m, h->s));
+    h->mg.push_back(L);
+  }
+  const int64_t m0 = int64_t(n0) * n0 * n0;
+  AMR_TRY(alloc_n(h, &h->mg_rho, m0));
+  AMR_TRY(alloc_n(h, &h->mg_r, m0));
+  AMR_TRY(alloc_n(h, &h->mg_part, 2 * kMGParts));
+  AMR_TRY(alloc_n(h, &h->mg_res, 1024));
+  AMR_TRY(alloc_n(h, &h->phi, m0));
+  h->mg_member = member;
+  return AMR_OK;
+}
+
+static unsigned mg_blocks(int64_t m) { return unsigned(std::min<int64_t>((m + 255) / 256, kMGParts)); }
+
+static void mg_vcycle(amr_mesh *h, size_t k, double dx) {
+  amr_mesh::MGLevel &L = h->mg[k];
+  const int n = L.n;
+  const double dx2 = dx * dx;
+  if (n <= 2) {
+    launch(h, K_MG_OTHER, k_mg_coarsest, dim3(1), dim3(8), dx2, (const double *)L.f, L.p, kMGCoarsest);
+    return;
+  }
+  const int64_t m = int64_t(n) * n * n;
+  for (int s = 0; s < kMGPre; ++s)
+    for (int colour = 0; colour < 2; ++colour)
+      launch(h, K_MG_SMOOTH, k_mg_smooth, dim3(nblocks(m / 2)), dim3(256), n, dx2, (const double *)L.f,
+             L.p, colour);
+  amr_mesh::MGLevel &C = h->mg[k + 1];
+  launch(h, K_MG_RESTRICT, k_mg_restrict, dim3(nblocks(m / 8)), dim3(256), n, 1.0 / dx2,
+         (const double *)L.f, (const double *)L.p, C.f, C.p);
+  mg_vcycle(h, k + 1, 2.0 * dx);
+  launch(h, K_MG_PROLONG, k_mg_prolong, dim3(nblocks(m)), dim3(256), n, (const double *)C.p, L.p);
+  for (int s = 0; s < kMGPost; ++s)
+    for (int colour = 0; colour < 2; ++colour)
+      launch(h, K_MG_SMOOTH, k_mg_smooth, dim3(nblocks(m / 2)), dim3(256), n, dx2, (const double *)L.f,
+             L.p, colour);
+}
+
+extern "C" amr_status amr_poisson(amr_handle h, double fourpiG, int n_vcycles, double *resid) {
+  if (!h) return fail(AMR_EINVAL, "amr_poisson: NULL handle");
+  if (n_vcycles < 0 || n_vcycles > 1020) return fail(AMR_EINVAL, "amr_poisson: n_vcycles must be in [0, 1020]");
+  const Member &mb = h->mem[h->sel];
+  const int lmin = mb.lmin;
+  if (lmin > 10) return fail(AMR_EINVAL, "amr_poisson: levelmin above 10 (more than 1024^3 cells)");
+  const int n = 1 << lmin;
+  const int64_t m0 = int64_t(n) * n * n;
+  const int lo = int(mb.oct_base + mb.lo[lmin]), nl = int(mb.lo[lmin + 1] - mb.lo[lmin]);
+  if (8 * int64_t(nl) != m0) return fail(AMR_EGRADING, "amr_poisson: the base level is not complete");
+  AMR_TRY(mg_setup(h, h->sel, lmin));
+  const double dx = std::ldexp(1.0, -lmin);
+  if (h->p.precision == 4)
+    launch(h, K_MG_OTHER, k_mg_gather<float>, dim3(nblocks(m0)), dim3(256), (const float *)h->U,
+           (const uint64_t *)h->key, lo, nl, n, h->mg_rho);
+  else
+    launch(h, K_MG_OTHER, k_mg_gather<double>, dim3(nblocks(m0)), dim3(256), (const double *)h->U,
+           (const uint64_t *)h->key, lo, nl, n, h->mg_rho);
+  const unsigned nb = mg_blocks(m0);
+  double *mean = h->mg_res + 1022;  // two scalars at the end of the residual array
+  launch(h, K_MG_OTHER, k_mg_sum, dim3(nb), dim3(256), (const double *)h->mg_rho, m0, 0, h->mg_part);
+  launch(h, K_MG_OTHER, k_mg_total, dim3(1), dim3(32), (const double *)h->mg_part, int(nb),
+         1.0 / double(m0), mean);
+  launch(h, K_MG_OTHER, k_mg_source, dim3(nb), dim3(256), (const double *)h->mg_rho, m0,
+         (const double *)mean, fourpiG, h->mg[0].f);
+  for (int c = 0; c < n_vcycles; ++c) {
+    mg_vcycle(h, 0, dx);
+    if (resid) {
+      launch(h, K_MG_OTHER, k_mg_residual, dim3(nblocks(m0)), dim3(256), n, 1.0 / (dx * dx),
+             (const double *)h->mg[0].f, (const double *)h->mg[0].p, h->mg_r);
+      launch(h, K_MG_OTHER, k_mg_sum, dim3(nb), dim3(256), (const double *)h->mg_r, m0, 1, h->mg_part);
+      launch(h, K_MG_OTHER, k_mg_norm, dim3(1), dim3(32), (const double *)h->mg_part, int(nb),
+             h->mg_res + c);
+    }
+  }
+  // potential of the base cells, mean removed
+  launch(h, K_MG_OTHER, k_mg_sum, dim3(nb), dim3(256), (const double *)h->mg[0].p, m0, 0,
+         h->mg_part + kMGParts);
+  launch(h, K_MG_OTHER, k_mg_total, dim3(1), dim3(32), (const double *)(h->mg_part + kMGParts),
+         int(nb), 1.0 / double(m0), mean + 1);
+  launch(h, K_MG_OTHER, k_mg_scatter, dim3(nblocks(m0)), dim3(256), (const double *)h->mg[0].p,
+         (const uint64_t *)h->key, lo, nl, n, (const double *)(mean + 1), h->phi);
+  if (resid && n_vcycles > 0)
+    CUDA_TRY(cudaMemcpyAsync(resid, h->mg_res, sizeof(double) * n_vcycles, cudaMemcpyDeviceToHost, h->s));
+  return check_device(h, "amr_poisson");
+}
+
+extern "C" amr_status amr_read_phi(amr_handle h, double *phi, int64_t cap) {
+  if (!h || !phi) return fail(AMR_EINVAL, "amr_read_phi: NULL argument");
+  const Member &mb = h->mem[h->sel];
+  const int64_t nl = mb.lo[mb.lmin + 1] - mb.lo[mb.lmin];
+  if (!h->phi || h->mg_member != h->sel) return fail(AMR_EINVAL, "amr_read_phi: no potential (call amr_poisson)");
+  if (cap < 8 * nl) return fail(AMR_EINVAL, "amr_read_phi: room for %lld cells needed", (long long)(8 * nl));
+  CUDA_TRY(cudaMemcpyAsync(phi, h->phi, sizeof(double) * 8 * nl, cudaMemcpyDeviceToHost, h->s));
+  return check_device(h, "amr_read_phi");
 }
 
 extern "C" amr_status amr_select_member(amr_handle h, int member) {

@@ -1,0 +1,176 @@
+// mg_kernels.cuh -- multigrid Poisson V-cycles on the periodic base level
+// (paper Sec. 5, self-gravity).
+//
+//   (sum of the 6 neighbours - 6 phi) / dx^2 = fourpiG (rho - mean rho)
+//
+// Smoother: red-black Gauss-Seidel, colour = parity of x + y + z (the parity
+// of the cell's index inside its oct).  Restriction: the residuals of the 8
+// children, averaged into the coarse source.  Prolongation: trilinear, weights
+// (1, 3, 3, 9, 3, 9, 9, 27)/64.  Hierarchy: the same periodic box at half the
+// resolution per level, down to 2^3 cells, smoothed 8 times there.
+//
+// The base level lives in the mesh's oct order; the solver works on dense
+// arrays [x + n (y + n z)] of every multigrid level (unit-stride x, so every
+// stencil access is coalesced), gathered from and scattered back to the octs.
+// On GB300 the FP64 pipe bounds these stencils (about 8 FP64 operations per
+// cell against 16 bytes of traffic); no step divides (the Gauss-Seidel update
+// multiplies by the rounded 1/6, the residual by the exact 1/dx^2).
+#pragma once
+#include "amr_internal.cuh"
+
+namespace amr {
+
+__device__ __forceinline__ int64_t mg_at(int n, int x, int y, int z) {
+  const int m = n - 1;  // n is a power of two: periodic wrap by masking
+  return int64_t(x & m) + int64_t(n) * (int64_t(y & m) + int64_t(n) * int64_t(z & m));
+}
+
+__device__ __forceinline__ double mg_nbsum(int n, const double *__restrict__ p, int x, int y, int z) {
+  return ((p[mg_at(n, x - 1, y, z)] + p[mg_at(n, x + 1, y, z)]) +
+          (p[mg_at(n, x, y - 1, z)] + p[mg_at(n, x, y + 1, z)])) +
+         (p[mg_at(n, x, y, z - 1)] + p[mg_at(n, x, y, z + 1)]);
+}
+
+// base-level density (oct order) into the dense array; one thread per cell
+template <class T>
+__global__ void k_mg_gather(const T *__restrict__ U, const uint64_t *__restrict__ key, int lo,
+                            int nl, int n, double *__restrict__ rho) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= 8 * int64_t(nl)) return;
+  const int o = lo + int(g >> 3), c = int(g & 7);
+  const uint64_t k = key[o];
+  const int x = 2 * int(ikey_x(k)) + (c & 1), y = 2 * int(ikey_y(k)) + ((c >> 1) & 1),
+            z = 2 * int(ikey_z(k)) + ((c >> 2) & 1);
+  rho[mg_at(n, x, y, z)] = double(U[8 * int64_t(o) + c]);
+}
+
+// block sums of a[0..m) into part[blockIdx.x] (warp shuffles, then shared
+// memory); squared when sq
+__global__ void k_mg_sum(const double *__restrict__ a, int64_t m, int sq, double *__restrict__ part) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < m; t += int64_t(gridDim.x) * blockDim.x)
+    s += sq ? a[t] * a[t] : a[t];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+// out = scale * (sum of the partial sums); one thread
+__global__ void k_mg_total(const double *__restrict__ part, int nparts, double scale,
+                           double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int q = 0; q < nparts; ++q) s += part[q];
+  *out = s * scale;
+}
+
+// f = fourpiG (rho - mean)
+__global__ void k_mg_source(const double *__restrict__ rho, int64_t m, const double *__restrict__ mean,
+                            double fourpiG, double *__restrict__ f) {
+  const double mu = *mean;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < m; t += int64_t(gridDim.x) * blockDim.x)
+    f[t] = fourpiG * (rho[t] - mu);
+}
+
+// one colour of a red-black sweep: thread t -> (x, y, z) with x + y + z of
+// the colour's parity
+__global__ void k_mg_smooth(int n, double dx2, const double *__restrict__ f, double *p, int colour) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t half = int64_t(n) * n * n / 2;
+  if (t >= half) return;
+  const int h = n >> 1;
+  const int xh = int(t % h);
+  const int64_t yz = t / h;
+  const int y = int(yz % n), z = int(yz / n);
+  const int x = 2 * xh + ((y + z + colour) & 1);
+  const int64_t i = mg_at(n, x, y, z);
+  p[i] = (mg_nbsum(n, p, x, y, z) - dx2 * f[i]) * (1.0 / 6.0);
+}
+
+// coarse source = mean of the 8 children's residuals; coarse correction = 0
+__global__ void k_mg_restrict(int n, double inv_dx2, const double *__restrict__ f,
+                              const double *__restrict__ p, double *__restrict__ fc, double *__restrict__ ec) {
+  const int h = n >> 1;
+  const int64_t T = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (T >= int64_t(h) * h * h) return;
+  const int X = int(T % h), Y = int((T / h) % h), Z = int(T / (int64_t(h) * h));
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int x = 2 * X + (c & 1), y = 2 * Y + ((c >> 1) & 1), z = 2 * Z + ((c >> 2) & 1);
+    const int64_t i = mg_at(n, x, y, z);
+    s += f[i] - (mg_nbsum(n, p, x, y, z) - 6.0 * p[i]) * inv_dx2;
+  }
+  fc[T] = s * 0.125;
+  ec[T] = 0.0;
+}
+
+// phi += trilinear prolongation of the coarse correction
+__global__ void k_mg_prolong(int n, const double *__restrict__ ec, double *__restrict__ p) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= int64_t(n) * n * n) return;
+  const int h = n >> 1;
+  const int x = int(t % n), y = int((t / n) % n), z = int(t / (int64_t(n) * n));
+  const int X = x >> 1, Y = y >> 1, Z = z >> 1;
+  const int sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
+  double v = 27.0 * ec[mg_at(h, X, Y, Z)];
+  v += 9.0 * ((ec[mg_at(h, X + sx, Y, Z)] + ec[mg_at(h, X, Y + sy, Z)]) + ec[mg_at(h, X, Y, Z + sz)]);
+  v += 3.0 * ((ec[mg_at(h, X + sx, Y + sy, Z)] + ec[mg_at(h, X + sx, Y, Z + sz)]) +
+              ec[mg_at(h, X, Y + sy, Z + sz)]);
+  v += ec[mg_at(h, X + sx, Y + sy, Z + sz)];
+  p[t] += v / 64.0;
+}
+
+// the 2^3 grid: `sweeps` red-black sweeps by one block of 8 threads
+__global__ void k_mg_coarsest(double dx2, const double *__restrict__ f, double *p, int sweeps) {
+  const int t = threadIdx.x;  // 0..7: (x, y, z) = bits of t
+  const int x = t & 1, y = (t >> 1) & 1, z = (t >> 2) & 1;
+  for (int s = 0; s < sweeps; ++s)
+    for (int colour = 0; colour < 2; ++colour) {
+      if (((x + y + z) & 1) == colour) {
+        const int64_t i = mg_at(2, x, y, z);
+        p[i] = (mg_nbsum(2, p, x, y, z) - dx2 * f[i]) * (1.0 / 6.0);
+      }
+      __syncthreads();
+    }
+}
+
+// residual of the base level into r (for its L2 norm)
+__global__ void k_mg_residual(int n, double inv_dx2, const double *__restrict__ f,
+                              const double *__restrict__ p, double *__restrict__ r) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= int64_t(n) * n * n) return;
+  const int x = int(t % n), y = int((t / n) % n), z = int(t / (int64_t(n) * n));
+  r[t] = f[t] - (mg_nbsum(n, p, x, y, z) - 6.0 * p[t]) * inv_dx2;
+}
+
+// sqrt of the sum of the partial sums into out
+__global__ void k_mg_norm(const double *__restrict__ part, int nparts, double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int q = 0; q < nparts; ++q) s += part[q];
+  *out = sqrt(s);
+}
+
+// phi - mean into the octs' cells (mesh order)
+__global__ void k_mg_scatter(const double *__restrict__ p, const uint64_t *__restrict__ key, int lo,
+                             int nl, int n, const double *__restrict__ mean,
+                             double *__restrict__ phi_cells) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= 8 * int64_t(nl)) return;
+  const int o = lo + int(g >> 3), c = int(g & 7);
+  const uint64_t k = key[o];
+  const int x = 2 * int(ikey_x(k)) + (c & 1), y = 2 * int(ikey_y(k)) + ((c >> 1) & 1),
+            z = 2 * int(ikey_z(k)) + ((c >> 2) & 1);
+  phi_cells[g] = p[mg_at(n, x, y, z)] - *mean;
+}
+
+}  // namespace amr
