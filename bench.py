@@ -59,6 +59,8 @@ def parse():
                     help="work-tile size of every handle (0: autotune at the first step)")
     ap.add_argument("--schedule", type=int, default=-1,
                     help="1 persistent grids, 0 one tile per block, -1 autotune")
+    ap.add_argument("--profile-poisson", type=int, default=0,
+                    help="profiling mode: one multigrid V-cycle on a periodic 2^L grid, then exit")
     ap.add_argument("--profile-level", type=int, default=0,
                     help="profiling mode: build the mesh and run one eager level step of this "
                          "level (one launch of each level-step kernel), then exit")
@@ -603,6 +605,20 @@ def main():
         return 0
 
     import torch
+    if args.profile_poisson:
+        from paper_2607_20704_gb300 import amr, build
+        build.build()
+        amr.load()
+        L = args.profile_poisson
+        n = 1 << L
+        pr = inputs.uniform_grid(L, lambda x, y, z: (1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y),
+                                                     0 * x, 0 * x, 0 * x, 1.0 + 0 * x))
+        m = amr.Mesh(*pr.mesh_args(), **pr.params())
+        m.poisson(1.0, 1, residuals=False)
+        m.sync()
+        print(json.dumps({"profile_poisson": L, "cells": n ** 3}))
+        m.close()
+        return 0
     if args.profile_level:
         from paper_2607_20704_gb300 import amr
         m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=args.precision, **LAUNCH)
