@@ -95,6 +95,7 @@ def lib():
                 "orc_1d_step": (I, [I, P, D, D, D, D]),
                 "orc_flags": (I, [P, C.POINTER(_RegridParams), P]),
                 "orc_mg_solve": (I, [I, D, P, D, I, I, I, P, P]),
+                "orc_cic_deposit": (I, [I, I64, P, P, P, P, P]),
                 "orc_mg_residual": (D, [I, D, P, D, P]),
                 "orc_regrid": (I, [C.POINTER(P), C.POINTER(_RegridParams), C.POINTER(I64),
                                    C.POINTER(I64)]),
@@ -325,3 +326,15 @@ def mg_residual(rho, dx, phi, fourpiG=1.0):
     r = np.ascontiguousarray(rho.ravel(order="F"))
     p = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).ravel(order="F"))
     return float(lib().orc_mg_residual(n, float(dx), _ptr(r), float(fourpiG), _ptr(p)))
+
+
+def cic_deposit(n, x, y, z, m):
+    """Cloud-in-cell density (Sec. 4) of particles on an n^3 periodic grid,
+    returned as an (n, n, n) array indexed [i, j, k]."""
+    x, y, z, m = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, m))
+    rho = np.zeros(n ** 3)
+    rc = lib().orc_cic_deposit(int(n), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(z), _ptr(m),
+                               _ptr(rho))
+    if rc:
+        raise OracleError(rc, "cic_deposit")
+    return rho.reshape((n, n, n), order="F")

@@ -113,6 +113,16 @@ int orc_mg_solve(int n, double dx, const double *rho, double fourpiG, int ncycle
 /* L2 norm of the residual of phi for the source fourpiG (rho - mean rho) */
 double orc_mg_residual(int n, double dx, const double *rho, double fourpiG, const double *phi);
 
+/* --- particles: cloud-in-cell mass deposition (Sec. 4) ----------------------
+ * np particles at positions (x, y, z) in the periodic unit box with masses m
+ * deposit onto an n^3 grid of cells of size 1/n (n a power of two; arrays
+ * [i + n (j + n k)]): along each axis s = x n - 1/2, i0 = floor(s),
+ * f = s - i0, weights 1 - f for cell i0 and f for cell i0 + 1 (periodic);
+ * a particle gives m (wx wy) wz to each of its 8 cells, corner order
+ * c = cx + 2 cy + 4 cz, particles in index order; rho = sum / dx^3. */
+int orc_cic_deposit(int n, int64_t np, const double *x, const double *y, const double *z,
+                    const double *m, double *rho);
+
 /* --- independent cross-check solvers ----------------------------------------- */
 int orc_uniform_step(int n, double *U, double gamma, double dt, double smallr,
                      double smallc);

@@ -481,3 +481,120 @@ def serving_requests(n_requests: int, seed: int = 13, pool: int = 24, max_level_
         steps = int(round(np.exp(rng.uniform(np.log(10), np.log(max_steps)))))
         reqs.append((int(rng.integers(0, pool)), steps, 4 if rng.random() < 0.5 else 8))
     return probs, reqs
+
+
+# ---------------------------------------------------------------------------
+# particles in the periodic unit box (mass deposition workloads)
+# ---------------------------------------------------------------------------
+@dataclass
+class ParticleSet:
+    name: str
+    n: int  # grid cells per axis of the deposition
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    m: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def np(self) -> int:
+        return int(self.x.shape[0])
+
+    def args(self):
+        return self.n, self.x, self.y, self.z, self.m
+
+
+def _into_box(a: np.ndarray) -> np.ndarray:
+    a = np.mod(a, 1.0)
+    a[a >= 1.0] = 0.0  # a tiny negative value rounds up to 1.0 under mod
+    return a
+
+
+def _upsample_axis(f: np.ndarray, axis: int, L: int) -> np.ndarray:
+    """Periodic linear interpolation of f along `axis` from its m points
+    (cell centres of an m-grid) to the centres of an L-grid."""
+    m = f.shape[axis]
+    u = (np.arange(L) + 0.5) * (m / L) - 0.5
+    i0 = np.floor(u).astype(np.int64)
+    w1 = u - i0
+    shape = [1] * f.ndim
+    shape[axis] = L
+    a = np.take(f, i0 % m, axis=axis)
+    b = np.take(f, (i0 + 1) % m, axis=axis)
+    return a * (1.0 - w1).reshape(shape) + b * w1.reshape(shape)
+
+
+def particles(n: int, kind: str = "cosmo", seed: int = 0, lattice: int | None = None,
+              n_particles: int | None = None, disp: float = 1.0, halo_fraction: float = 0.25,
+              halo_particles: int = 4096, index: float = -3.0, masses: str = "equal",
+              chunk: int = 32) -> ParticleSet:
+    """Seeded particle sets for deposition on an n^3 grid.
+
+    kind "cosmo": a cosmological-simulation-shaped distribution -- a lattice
+    of `lattice`^3 particles (default n^3, one per cell) displaced by a
+    Zel'dovich-like field (the gradient of a Gaussian potential with power
+    spectrum k^index on a coarse 64^3 grid, linearly interpolated, scaled to
+    an rms displacement of `disp` cells), with a fraction `halo_fraction`
+    of the particles moved into compact halos of about `halo_particles`
+    particles each (Gaussian profiles with radii log-uniform in 0.3..3
+    cells), so that voids hold ~1 particle per cell and halo cores hundreds.
+    kind "uniform": `n_particles` positions uniform in the box.
+    kind "clump": `n_particles` in one Gaussian clump of radius one cell.
+    masses "equal": every particle 1/N (mean density 1); "random": lognormal
+    masses of unit median."""
+    rng = np.random.default_rng(seed)
+    if kind == "cosmo":
+        L = int(lattice or n)
+        N = L ** 3
+        mc = min(L, 64)
+        phi, _ = gaussian_field(mc, index, 1.0, rng)
+        psi = [0.5 * (np.roll(phi, -1, axis=a) - np.roll(phi, 1, axis=a)) for a in range(3)]
+        rms = np.sqrt(np.mean(psi[0] ** 2 + psi[1] ** 2 + psi[2] ** 2))
+        psi = [p * (disp / n / max(rms, 1e-300)) for p in psi]
+        x, y, z = (np.empty(N) for _ in range(3))
+        q = (np.arange(L) + 0.5) / L
+        # psi at the lattice points, `chunk` planes of the first axis at a time
+        up1 = [_upsample_axis(_upsample_axis(p, 1, L), 2, L) for p in psi]  # (mc, L, L)
+        for a0 in range(0, L, chunk):
+            a1 = min(L, a0 + chunk)
+            u = (np.arange(a0, a1) + 0.5) * (mc / L) - 0.5
+            i0 = np.floor(u).astype(np.int64)
+            w1 = (u - i0)[:, None, None]
+            sl = slice(a0 * L * L, a1 * L * L)
+            for out, comp, axis_q in ((x, 0, 0), (y, 1, 1), (z, 2, 2)):
+                f = up1[comp]
+                d = f[i0 % mc] * (1.0 - w1) + f[(i0 + 1) % mc] * w1  # (a1-a0, L, L)
+                qq = np.broadcast_to(
+                    (q[a0:a1][:, None, None], q[None, :, None], q[None, None, :])[axis_q],
+                    d.shape)
+                out[sl] = (qq + d).reshape(-1)
+        nh = int(round(halo_fraction * N))
+        if nh > 0:
+            pick = np.flatnonzero(rng.random(N) < halo_fraction)
+            nh = pick.shape[0]
+            n_halo = max(1, nh // max(1, halo_particles))
+            centre = rng.random((n_halo, 3))
+            radius = np.exp(rng.uniform(np.log(0.3), np.log(3.0), n_halo)) / n
+            hid = rng.integers(0, n_halo, nh)
+            for out, a in ((x, 0), (y, 1), (z, 2)):
+                out[pick] = centre[hid, a] + radius[hid] * rng.standard_normal(nh)
+        meta = {"lattice": L, "disp_cells": disp, "halo_fraction": halo_fraction,
+                "halo_particles": halo_particles, "index": index}
+    elif kind in ("uniform", "clump"):
+        N = int(n_particles if n_particles is not None else n ** 3)
+        if kind == "uniform":
+            x, y, z = rng.random(N), rng.random(N), rng.random(N)
+        else:
+            c = rng.random(3)
+            x, y, z = (c[a] + rng.standard_normal(N) / n for a in range(3))
+        meta = {}
+    else:
+        raise ValueError(f"unknown particle set kind {kind!r}")
+    x, y, z = _into_box(x), _into_box(y), _into_box(z)
+    if masses == "equal":
+        m = np.full(N, 1.0 / max(N, 1))
+    elif masses == "random":
+        m = np.exp(0.5 * rng.standard_normal(N))
+    else:
+        raise ValueError(f"unknown masses {masses!r}")
+    return ParticleSet(kind, int(n), x, y, z, m, meta)
