@@ -52,6 +52,13 @@ def parse():
                     help="skip the multigrid V-cycle measurement")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the adaptive run (regrid before every coarse step)")
+    ap.add_argument("--no-cic", action="store_true",
+                    help="skip the Cloud-in-Cell particle deposition measurement")
+    ap.add_argument("--cic-grid", type=int, default=512,
+                    help="grid cells per axis of the deposition measurement (N_part = N_grid)")
+    ap.add_argument("--profile-cic", type=int, default=0,
+                    help="profiling mode: one sort and one deposit of each algorithm of n^3 "
+                         "cosmological particles on the n^3 grid (FP64), then exit")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--no-other-precision", action="store_true",
                     help="run only --precision (skip the other precision's pass)")
@@ -432,6 +439,67 @@ def run_poisson(level, cycles, torch, device):
             "kernels": {k: round(v[0] / ktot, 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}}
 
 
+def run_cic(n, reps, warmup, torch, peak_gbs, peak_src):
+    """Cloud-in-Cell mass deposition (Sec. 4) of a cosmological particle set
+    with N_part = N_grid = n^3 on the periodic n^3 grid: particle
+    depositions per second of the atomic (warp-combining) kernel and of the
+    deterministic segment kernel, grid zeroing included; of the source-cell
+    Hilbert sort; and of sort + atomic deposit.  FP64 and FP32.  Particle
+    arrays and the grid exceed L2, so nothing is flushed between repeats.
+    The deposit kernel's algorithmic bytes: the 4 particle arrays read once,
+    the grid read and written once."""
+    from paper_2607_20704_gb300 import amr, inputs
+    t0 = time.perf_counter()
+    ps = inputs.particles(n, "cosmo", seed=2607)
+    gen_s = time.perf_counter() - t0
+    st = bench_stream()
+    out = {"grid": f"{n}^3 periodic", "particles": ps.np,
+           "set": "lattice of n^3 particles, Zel'dovich-like displacements (rms 1 cell), "
+                  "25% of the particles in Gaussian halos of ~4096 (radii 0.3-3 cells)",
+           "l2": "inputs and grid larger than L2; not flushed", "input_generation_s": round(gen_s, 1)}
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for prec in (8, 4):
+        p = amr.Particles(*ps.args(), precision=prec, stream=st)
+        p.sort()
+        res = {}
+        for name, fn in (("sort", p.sort), ("deposit_atomic", lambda: p.deposit("atomic")),
+                         ("deposit_segment", lambda: p.deposit("segment")),
+                         ("sort_and_deposit_atomic", lambda: (p.sort(), p.deposit("atomic")))):
+            ms = timed(fn)
+            res[name] = {"ms": round(ms, 4), "particles_per_s": ps.np / (ms * 1e-3)}
+        p.set_timing(True)
+        p.sort()
+        p.deposit("atomic")
+        p.deposit("segment")
+        kt = p.read_timing()
+        p.set_timing(False)
+        res["segments"] = p.info()["n_segments"]
+        esz = WORD[prec]
+        k_ms = kt["cic_atomic"][0] / kt["cic_atomic"][1]
+        alg = ps.np * 4 * esz + 2 * n ** 3 * esz
+        res["cic_atomic_roofline"] = {"bound": "hbm", "unit": "GB/s",
+                                      "achieved": round(alg / (k_ms * 1e-3) / 1e9, 1),
+                                      "peak": peak_gbs, "peak_source": peak_src,
+                                      "frac": round(alg / (k_ms * 1e-3) / 1e9 / peak_gbs, 4),
+                                      "algorithmic_bytes": alg, "kernel_ms": round(k_ms, 4)}
+        res["kernels_ms"] = {k: round(v[0], 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+        out["fp64" if prec == 8 else "fp32"] = res
+        p.close()
+    return out
+
+
 def inputs_gaussian(n, rng):
     from paper_2607_20704_gb300 import inputs
     return inputs.gaussian_field(n, -2.0, 1.5, rng)
@@ -619,6 +687,19 @@ def main():
         print(json.dumps({"profile_poisson": L, "cells": n ** 3}))
         m.close()
         return 0
+    if args.profile_cic:
+        from paper_2607_20704_gb300 import amr, build
+        build.build()
+        amr.load()
+        ps = inputs.particles(args.profile_cic, "cosmo", seed=2607)
+        p = amr.Particles(*ps.args())
+        p.sort()
+        p.deposit("atomic")
+        p.deposit("segment")
+        p.rho()
+        print(json.dumps({"profile_cic": args.profile_cic, "particles": ps.np}))
+        p.close()
+        return 0
     if args.profile_level:
         from paper_2607_20704_gb300 import amr
         m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=args.precision, **LAUNCH)
@@ -651,6 +732,7 @@ def main():
             other["steps"] = args.steps
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
         poisson = None if args.no_poisson else run_poisson(8, 10, torch, device)
+        cic = None if args.no_cic else run_cic(args.cic_grid, 5, 3, torch, peak_gbs, peak_src)
         adaptive = None
         if not args.no_adaptive:
             adaptive = {("fp64" if p == 8 else "fp32"): run_adaptive(prob, p, 10, torch, device)
@@ -724,6 +806,8 @@ def main():
         line["adaptive"] = adaptive
     if poisson is not None:
         line["poisson"] = poisson
+    if cic is not None:
+        line["cic"] = cic
     if batched is not None:
         line["batched"] = batched
     if serving is not None:

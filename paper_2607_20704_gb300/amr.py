@@ -101,6 +101,26 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
            "amr_server_destroy"]
 
+# exported symbols of the particle C ABI (include/amr_particles.h)
+PART_SYMBOLS = ["amr_part_create", "amr_part_write", "amr_part_sort", "amr_cic_deposit",
+                "amr_part_read_rho", "amr_part_read", "amr_part_device", "amr_part_get_info",
+                "amr_part_set_timing", "amr_part_read_timing", "amr_part_kernel_name",
+                "amr_part_destroy"]
+
+AMR_CIC_ATOMIC, AMR_CIC_SEGMENT = 2, 3
+CIC_ALGOS = {"atomic": AMR_CIC_ATOMIC, "segment": AMR_CIC_SEGMENT}
+
+
+class amr_part_params(C.Structure):
+    _fields_ = [("n", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p)]
+
+
+class amr_part_info(C.Structure):
+    _fields_ = [("np", C.c_int64), ("n", C.c_int), ("precision", C.c_int), ("sorted", C.c_int),
+                ("n_segments", C.c_int64), ("device_bytes", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+
 # fixed scratch limit of amr_cfl_dt_static (AMR_CFL_STATIC_MAX_CELLS in amr.h)
 CFL_STATIC_MAX_CELLS = 65536 * 256
 
@@ -156,6 +176,19 @@ def load(path: str | None = None):
             "amr_server_release": (I, [P, I64]),
             "amr_server_get_stats": (I, [P, C.POINTER(amr_server_stats)]),
             "amr_server_destroy": (I, [P]),
+            "amr_part_create": (I, [C.POINTER(amr_part_params), I64, P, P, P, P, C.POINTER(P)]),
+            "amr_part_write": (I, [P, P, P, P, P]),
+            "amr_part_sort": (I, [P]),
+            "amr_cic_deposit": (I, [P, I]),
+            "amr_part_read_rho": (I, [P, P, I64]),
+            "amr_part_read": (I, [P, P, P, P, P, P, I64]),
+            "amr_part_device": (I, [P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                    C.POINTER(P)]),
+            "amr_part_get_info": (I, [P, C.POINTER(amr_part_info)]),
+            "amr_part_set_timing": (I, [P, I]),
+            "amr_part_read_timing": (I, [P, I, P, P]),
+            "amr_part_kernel_name": (C.c_char_p, [I]),
+            "amr_part_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -583,6 +616,97 @@ class Server:
         h = getattr(self, "_h", None)
         if h:
             load().amr_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def part_kernel_names():
+    L = load()
+    out = []
+    while True:
+        n = L.amr_part_kernel_name(len(out))
+        if n is None:
+            return out
+        out.append(n.decode())
+
+
+class Particles:
+    """Particles resident on the device with a periodic n^3 grid (wraps an
+    ``amr_part_handle``): the source-cell Hilbert sort and the Cloud-in-Cell
+    mass deposition of Sec. 4."""
+
+    def __init__(self, n, x, y, z, m, *, precision=8, stream=None):
+        torch = _torch()
+        L = load()
+        x, y, z, m = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, m))
+        if not (x.shape == y.shape == z.shape == m.shape and x.ndim == 1):
+            raise ValueError("x, y, z, m must be 1-D arrays of one length")
+        p = amr_part_params()
+        p.n, p.precision = int(n), int(precision)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        p.stream = C.c_void_p(self.stream.cuda_stream)
+        h = C.c_void_p()
+        _check(L.amr_part_create(C.byref(p), x.shape[0], _ptr(x), _ptr(y), _ptr(z), _ptr(m),
+                                 C.byref(h)), "amr_part_create")
+        self._h = h
+        self.n, self.np, self.precision = int(n), int(x.shape[0]), int(precision)
+
+    def write(self, x, y, z, m):
+        x, y, z, m = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, m))
+        if any(a.shape != (self.np,) for a in (x, y, z, m)):
+            raise ValueError(f"arrays must have shape ({self.np},)")
+        _check(load().amr_part_write(self._h, _ptr(x), _ptr(y), _ptr(z), _ptr(m)), "amr_part_write")
+
+    def sort(self):
+        _check(load().amr_part_sort(self._h), "amr_part_sort")
+
+    def deposit(self, algo="atomic"):
+        _check(load().amr_cic_deposit(self._h, CIC_ALGOS.get(algo, algo)), "amr_cic_deposit")
+
+    def rho(self) -> np.ndarray:
+        """The grid as an (n, n, n) array indexed [i, j, k]."""
+        out = np.empty(self.n ** 3)
+        _check(load().amr_part_read_rho(self._h, _ptr(out), out.shape[0]), "amr_part_read_rho")
+        return out.reshape((self.n,) * 3, order="F")
+
+    def read(self):
+        """Positions, masses and identifiers in the handle's current order."""
+        x, y, z, m = (np.empty(self.np) for _ in range(4))
+        ids = np.empty(self.np, np.int64)
+        _check(load().amr_part_read(self._h, _ptr(x), _ptr(y), _ptr(z), _ptr(m), _ptr(ids),
+                                    self.np), "amr_part_read")
+        return x, y, z, m, ids
+
+    def device(self) -> dict:
+        ptrs = [C.c_void_p() for _ in range(5)]
+        _check(load().amr_part_device(self._h, *[C.byref(q) for q in ptrs]), "amr_part_device")
+        return dict(zip(("rho", "x", "y", "z", "m"), (q.value for q in ptrs)))
+
+    def info(self) -> dict:
+        inf = amr_part_info()
+        _check(load().amr_part_get_info(self._h, C.byref(inf)), "amr_part_get_info")
+        return {f: getattr(inf, f) for f, _ in amr_part_info._fields_}
+
+    def set_timing(self, on=True):
+        _check(load().amr_part_set_timing(self._h, int(bool(on))), "amr_part_set_timing")
+
+    def read_timing(self) -> dict:
+        names = part_kernel_names()
+        ms = np.zeros(len(names))
+        n = np.zeros(len(names), np.int64)
+        _check(load().amr_part_read_timing(self._h, len(names), _ptr(ms), _ptr(n)),
+               "amr_part_read_timing")
+        return {nm: (float(ms[t]), int(n[t])) for t, nm in enumerate(names) if n[t]}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().amr_part_destroy(h)
             self._h = None
 
     def __del__(self):

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libamr.so")
 # a bad index is reported as an error instead of leaving its array)
 LIB_CHECKED = os.path.join(BUILD, "libamr_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["amr_api.cu", "amr_static.cu", "amr_server.cu"]  # hydro/index kernels live in csrc/*.cuh
+SOURCES = ["amr_api.cu", "amr_static.cu", "amr_server.cu", "amr_particles.cu"]  # hydro/index kernels live in csrc/*.cuh
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

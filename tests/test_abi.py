@@ -17,8 +17,8 @@ def lib():
     return amr.load()
 
 
-def _declared():
-    text = open(os.path.join(ROOT, "include", "amr.h")).read()
+def _declared(header="amr.h"):
+    text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = set(re.findall(r"\b(amr_[a-z_]+)\s*\(", text))
     return sorted(n for n in names if not n.endswith("_fn"))
@@ -31,6 +31,10 @@ def test_every_declared_symbol_is_exported(lib):
     for name in declared:
         assert hasattr(lib, name), name
     assert sorted(amr.SYMBOLS) == declared
+    part = [n for n in _declared("amr_particles.h") if n not in declared]
+    for name in part:
+        assert hasattr(lib, name), name
+    assert sorted(amr.PART_SYMBOLS) == part
 
 
 def test_status_strings_and_kernel_names(lib):
@@ -77,3 +81,30 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.amr_step_level(None, 3, 0.1) == amr.AMR_EINVAL
     assert lib.amr_advance(None, 1, None) == amr.AMR_EINVAL
     assert lib.amr_destroy(None) == amr.AMR_OK
+
+
+def test_particle_calls_check_their_arguments_on_the_host(lib):
+    from paper_2607_20704_gb300 import amr
+    import numpy as np
+    h = C.c_void_p()
+    x = np.array([0.25, 0.5])
+    m = np.ones(2)
+    for n, prec in ((3, 8), (0, 8), (2048, 8), (16, 2)):
+        p = amr.amr_part_params(n, prec, None)
+        assert lib.amr_part_create(C.byref(p), 2, x.ctypes.data, x.ctypes.data, x.ctypes.data,
+                                   m.ctypes.data, C.byref(h)) == amr.AMR_EINVAL
+        assert not h.value
+    p = amr.amr_part_params(16, 8, None)
+    for bad in (np.array([0.25, 1.0]), np.array([-0.1, 0.5]), np.array([0.25, np.nan])):
+        assert lib.amr_part_create(C.byref(p), 2, bad.ctypes.data, x.ctypes.data, x.ctypes.data,
+                                   m.ctypes.data, C.byref(h)) == amr.AMR_EINVAL
+        assert "outside" in lib.amr_last_error().decode()
+    inf = np.array([1.0, np.inf])
+    assert lib.amr_part_create(C.byref(p), 2, x.ctypes.data, x.ctypes.data, x.ctypes.data,
+                               inf.ctypes.data, C.byref(h)) == amr.AMR_EINVAL
+    assert lib.amr_part_sort(None) == amr.AMR_EINVAL
+    assert lib.amr_cic_deposit(None, 2) == amr.AMR_EINVAL
+    assert lib.amr_part_destroy(None) == amr.AMR_OK
+    names = amr.part_kernel_names()
+    for k in ("part_keys", "psort_scatter", "cic_atomic", "seg_sum", "seg_gather"):
+        assert k in names
