@@ -1503,7 +1503,7 @@ int orc_cic_deposit(int n, int64_t np, const double *x, const double *y, const d
       int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
       int64_t t = (int64_t)wrap(ix + cx, n) +
                   (int64_t)n * ((int64_t)wrap(iy + cy, n) + (int64_t)n * wrap(iz + cz, n));
-      rho[t] += m[p] * ((wx[cx] * wy[cy]) * wz[cz]);
+      rho[t] += ((m[p] * wx[cx]) * wy[cy]) * wz[cz];
     }
   }
   /* mass -> density: divide by dx^3 = n^-3, an exact scaling */

@@ -118,7 +118,7 @@ double orc_mg_residual(int n, double dx, const double *rho, double fourpiG, cons
  * deposit onto an n^3 grid of cells of size 1/n (n a power of two; arrays
  * [i + n (j + n k)]): along each axis s = x n - 1/2, i0 = floor(s),
  * f = s - i0, weights 1 - f for cell i0 and f for cell i0 + 1 (periodic);
- * a particle gives m (wx wy) wz to each of its 8 cells, corner order
+ * a particle gives ((m wx) wy) wz to each of its 8 cells, corner order
  * c = cx + 2 cy + 4 cz, particles in index order; rho = sum / dx^3. */
 int orc_cic_deposit(int n, int64_t np, const double *x, const double *y, const double *z,
                     const double *m, double *rho);
