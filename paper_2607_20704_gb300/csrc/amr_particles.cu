@@ -22,11 +22,11 @@ namespace {
 
 enum PKid {
   P_KEYS, P_SORT_HIST, P_SORT_SCAN, P_SORT_SCATTER, P_GATHER, P_ZERO, P_CIC_ATOMIC,
-  P_SEG_HEADS, P_SEG_SCAN, P_SEG_STARTS, P_SEG_SUM, P_SEG_GATHER, P_CONVERT, P_COUNT
+  P_SEG_HEADS, P_SEG_SCAN, P_SEG_STARTS, P_SEG_PARTIAL, P_SEG_CARRY, P_SEG_GATHER, P_CONVERT, P_COUNT
 };
 const char *const kPartKernelNames[P_COUNT] = {
     "part_keys", "psort_hist", "psort_scan", "psort_scatter", "part_gather", "grid_zero",
-    "cic_atomic", "seg_heads", "seg_scan", "seg_starts", "seg_sum", "seg_gather", "convert"};
+    "cic_atomic", "seg_heads", "seg_scan", "seg_starts", "seg_partial", "seg_carry", "seg_gather", "convert"};
 
 amr_status set_error(amr_status s, const std::string &msg) {
   amr_set_error_text(msg.c_str());
@@ -56,7 +56,7 @@ struct amr_particles {
   void *rho = nullptr;
   // segment deposition (allocated on first use)
   uint32_t *flag = nullptr, *start = nullptr, *nseg = nullptr;
-  void *sums = nullptr;
+  void *sums = nullptr, *carry = nullptr;
   int32_t *cellmap = nullptr;
   double *stage = nullptr;  // device staging of host doubles (FP32 handles)
   bool sorted = false;
@@ -216,7 +216,7 @@ void release(amr_particles *h) {
   for (void *p : {h->x, h->y, h->z, h->m, h->x2, h->y2, h->z2, h->m2, (void *)h->id, (void *)h->id2,
                   (void *)h->key, (void *)h->val, (void *)h->key2, (void *)h->val2, (void *)h->table,
                   (void *)h->scan_tmp, h->rho, (void *)h->flag, (void *)h->start, (void *)h->nseg,
-                  h->sums, (void *)h->cellmap, (void *)h->stage})
+                  h->sums, h->carry, (void *)h->cellmap, (void *)h->stage})
     dfree(p);
   for (auto &t : h->pending) {
     cudaEventDestroy(t.e0);
@@ -228,12 +228,18 @@ void release(amr_particles *h) {
 
 int64_t cells(const amr_particles *h) { return int64_t(h->n) * h->n * h->n; }
 int64_t ntiles(const amr_particles *h) { return (h->np + kSortTile - 1) / kSortTile; }
+int64_t ngroups(const amr_particles *h) { return (h->np + 31) / 32; }
+
+template <class T>
+CicGrid<T> grid_of(const amr_particles *h) {
+  return CicGrid<T>{h->n, h->bits, T(h->n), T(double(cells(h)))};
+}
 
 template <class T>
 void sort_impl(amr_particles *h) {
   const int64_t np = h->np, nt = ntiles(h);
-  launch(h, P_KEYS, k_part_keys<T>, dim3(nblocks(np)), dim3(256), np, h->n, h->bits,
-         (const T *)h->x, (const T *)h->y, (const T *)h->z, h->key, h->val);
+  launch(h, P_KEYS, k_part_keys<T>, dim3(nblocks(np)), dim3(256), np, grid_of<T>(h), (const T *)h->x,
+         (const T *)h->y, (const T *)h->z, h->key, h->val);
   uint32_t *ka = h->key, *kb = h->key2, *va = h->val, *vb = h->val2;
   const int total = 3 * h->bits;
   for (int shift = 0; shift < total; shift += 8) {
@@ -262,15 +268,13 @@ void sort_impl(amr_particles *h) {
 template <class T>
 void deposit_atomic(amr_particles *h) {
   zero(h, P_ZERO, h->rho, 0, size_t(cells(h)) * sizeof(T));
-  const T scale = T(double(cells(h)));
-  launch(h, P_CIC_ATOMIC, k_cic_atomic<T>, dim3(nblocks(h->np)), dim3(256), h->np, h->n, scale,
+  launch(h, P_CIC_ATOMIC, k_cic_atomic<T>, dim3(nblocks(h->np)), dim3(256), h->np, grid_of<T>(h),
          (const T *)h->x, (const T *)h->y, (const T *)h->z, (const T *)h->m, (T *)h->rho);
 }
 
 template <class T>
 void deposit_segment(amr_particles *h) {
-  const int64_t np = h->np;
-  const T scale = T(double(cells(h)));
+  const int64_t np = h->np, cap = np > 0 ? np : 1, ng = ngroups(h) > 0 ? ngroups(h) : 1;
   zero(h, P_ZERO, h->cellmap, 0xFF, size_t(cells(h)) * sizeof(int32_t));
   zero(h, P_ZERO, h->nseg, 0, sizeof(uint32_t));
   if (np > 0) {
@@ -279,11 +283,13 @@ void deposit_segment(amr_particles *h) {
     scan_exclusive(h, P_SEG_SCAN, h->flag, np, h->scan_tmp);
     launch(h, P_SEG_STARTS, k_seg_starts, dim3(nblocks(np)), dim3(256), np, (const uint32_t *)h->sorted_key,
            (const uint32_t *)h->flag, h->start, h->nseg);
-    launch(h, P_SEG_SUM, k_seg_sum<T>, dim3(nblocks(np)), dim3(256), np, h->n, scale,
-           (const uint32_t *)h->nseg, (const uint32_t *)h->start, (const T *)h->x, (const T *)h->y,
-           (const T *)h->z, (const T *)h->m, (T *)h->sums, h->cellmap);
+    launch(h, P_SEG_PARTIAL, k_seg_partial<T>, dim3(nblocks(np)), dim3(256), np, grid_of<T>(h),
+           (const uint32_t *)h->sorted_key, (const uint32_t *)h->flag, (const T *)h->x, (const T *)h->y,
+           (const T *)h->z, (const T *)h->m, cap, ng, (T *)h->sums, (T *)h->carry, h->cellmap);
+    launch(h, P_SEG_CARRY, k_seg_carry<T>, dim3(nblocks(np)), dim3(256), (const uint32_t *)h->nseg,
+           (const uint32_t *)h->start, cap, ng, (const T *)h->carry, (T *)h->sums);
   }
-  launch(h, P_SEG_GATHER, k_seg_gather<T>, dim3(nblocks(cells(h))), dim3(256), h->n, np > 0 ? np : int64_t(1),
+  launch(h, P_SEG_GATHER, k_seg_gather<T>, dim3(nblocks(cells(h))), dim3(256), h->n, cap,
          (const int32_t *)h->cellmap, (const T *)h->sums, (T *)h->rho);
 }
 
@@ -376,8 +382,10 @@ extern "C" amr_status amr_cic_deposit(amr_part_handle h, int algo) {
     if (e == cudaSuccess) e = dalloc(h, &h->nseg, 4);
     if (e == cudaSuccess) e = dalloc(h, &h->cellmap, size_t(cells(h)) * 4);
     if (e == cudaSuccess) e = dalloc(h, &h->sums, 8 * cap * h->esize);
+    if (e == cudaSuccess) e = dalloc(h, &h->carry, 8 * size_t(ngroups(h) > 0 ? ngroups(h) : 1) * h->esize);
     if (e != cudaSuccess) {
-      for (void **q : {(void **)&h->flag, (void **)&h->start, (void **)&h->nseg, (void **)&h->cellmap, &h->sums}) {
+      for (void **q : {(void **)&h->flag, (void **)&h->start, (void **)&h->nseg, (void **)&h->cellmap, &h->sums,
+                       &h->carry}) {
         dfree(*q);
         *q = nullptr;
       }

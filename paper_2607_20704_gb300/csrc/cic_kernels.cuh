@@ -37,14 +37,68 @@ constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 8;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 2048 items per tile
 
-// source cell and weights along one axis; x n is exact for n a power of two
+// Grid of the deposition: n = 2^bits cells per axis; fn = n in the state type.
 template <class T>
-__device__ __forceinline__ int cic_axis(T x, int n, T &w0, T &w1) {
-  const T s = x * T(n) - T(0.5);
+struct CicGrid {
+  int n, bits;
+  T fn, scale;  // scale = n^3 (mass -> density), exact
+};
+
+// floor(x 2^k) for a double 0 <= x < 1, from its bits on the integer pipe
+// (GB300 runs FP64 at 1/64 of the FP32 rate, so the deposition keeps its
+// FP64 instruction count low).  Out-of-range inputs give some value that the
+// callers mask into the grid.
+__device__ __forceinline__ int floor_scaled(double x, int k) {
+  const uint64_t u = uint64_t(__double_as_longlong(x));
+  const int E = int(u >> 52) & 0x7FF;
+  const uint64_t M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = 1075 - E - k;
+  if (E == 0 || sh >= 64) return 0;
+  if (sh <= 0) return 0x7FFFFFFF;
+  return int(M >> sh);
+}
+
+// (2 i + 1) / 2 as a double, built on the integer pipe (|2 i + 1| < 2^31)
+__device__ __forceinline__ double half_odd(int i) {
+  const int k = 2 * i + 1;
+  const uint32_t a = uint32_t(k < 0 ? -k : k);
+  const int lz = __clz(a);
+  const int e = 31 - lz;                              // a = 1.frac 2^e
+  const uint32_t frac = e ? (a << (lz + 1)) : 0u;     // bits below the leading one, left aligned
+  const uint32_t hi = (uint32_t(k < 0) << 31) | (uint32_t(1022 + e) << 20) | (frac >> 12);
+  return __hiloint2double(int(hi), int(frac << 20));
+}
+
+// source cell along one axis: floor(x n - 1/2), unmasked
+template <class T>
+__device__ __forceinline__ int cic_cell(T x, const CicGrid<T> &g) {
+  return int(floor(x * g.fn - T(0.5)));
+}
+template <>
+__device__ __forceinline__ int cic_cell<double>(double x, const CicGrid<double> &g) {
+  // floor(x n - 1/2) = floor((floor(2 x n) - 1) / 2)
+  return (floor_scaled(x, g.bits + 1) - 1) >> 1;
+}
+
+// source cell (masked into the grid) and weights along one axis:
+// s = x n - 1/2, i0 = floor(s), w1 = f = s - i0, w0 = 1 - f
+template <class T>
+__device__ __forceinline__ int cic_axis(T x, const CicGrid<T> &g, T &w0, T &w1) {
+  const T s = x * g.fn - T(0.5);
   const T fl = floor(s);
   w1 = s - fl;
   w0 = T(1) - w1;
-  return int(fl) & (n - 1);
+  return int(fl) & (g.n - 1);
+}
+template <>
+__device__ __forceinline__ int cic_axis<double>(double x, const CicGrid<double> &g, double &w0,
+                                                double &w1) {
+  // x n and x n - 1/2 - i0 are exact, so one FMA gives the same f as
+  // (x n - 1/2) - floor(x n - 1/2)
+  const int i0 = cic_cell(x, g);
+  w1 = fma(x, g.fn, -half_odd(i0));
+  w0 = 1.0 - w1;
+  return i0 & (g.n - 1);
 }
 
 __device__ __forceinline__ uint32_t grid_at(int n, int i, int j, int k) {
@@ -52,31 +106,82 @@ __device__ __forceinline__ uint32_t grid_at(int n, int i, int j, int k) {
   return uint32_t(i & m) + uint32_t(n) * (uint32_t(j & m) + uint32_t(n) * uint32_t(k & m));
 }
 
-// the 8 contributions of one particle, corner c = cx + 2 cy + 4 cz
+// the 8 contributions ((m n^3 wx) wy) wz of one particle, corner
+// c = cx + 2 cy + 4 cz; (i, j, k) its source cell
 template <class T>
-__device__ __forceinline__ void cic_weights(T x, T y, T z, T ms, int n, int &i, int &j, int &k,
-                                            T w[8]) {
+__device__ __forceinline__ void cic_weights(T x, T y, T z, T m, const CicGrid<T> &g, int &i, int &j,
+                                            int &k, T w[8]) {
   T wx[2], wy[2], wz[2];
-  i = cic_axis(x, n, wx[0], wx[1]);
-  j = cic_axis(y, n, wy[0], wy[1]);
-  k = cic_axis(z, n, wz[0], wz[1]);
+  i = cic_axis(x, g, wx[0], wx[1]);
+  j = cic_axis(y, g, wy[0], wy[1]);
+  k = cic_axis(z, g, wz[0], wz[1]);
+  const T ms = m * g.scale;
+  T a[2], b[4];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) w[c] = ms * ((wx[c & 1] * wy[(c >> 1) & 1]) * wz[c >> 2]);
+  for (int cx = 0; cx < 2; ++cx) a[cx] = ms * wx[cx];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) b[q] = a[q & 1] * wy[q >> 1];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) w[c] = b[c & 3] * wz[c >> 2];
+}
+
+// Sums of the lanes' w over runs of lanes (`runs`: bit L set where a run
+// starts at lane L; bit 0 always set): a backward segmented scan that leaves
+// each run's total in its first lane.  The tree depends only on the run
+// lengths, so equal inputs give equal sums.
+template <class T>
+__device__ __forceinline__ void warp_run_sums(T w[8], unsigned runs, unsigned lane) {
+  const unsigned above = runs & ~((2u << lane) - 1u);  // run starts after this lane
+  const unsigned next = above ? unsigned(__ffs(above) - 1) : 32u;
+  const unsigned len = ((runs >> lane) & 1u) ? next - lane : 0u;
+  const unsigned maxrun = __reduce_max_sync(0xFFFFFFFFu, len);
+  for (unsigned off = 1; off < maxrun; off <<= 1) {
+    const bool take = lane + off < next;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const T o = __shfl_down_sync(0xFFFFFFFFu, w[c], off);
+      if (take) w[c] += o;
+    }
+  }
+}
+
+// The 8 sums over all 32 lanes, reduce-scatter style (9 additions per lane
+// instead of 40): afterwards lane L holds the total of component L >> 2.
+template <class T>
+__device__ __forceinline__ T warp_total_scatter(const T w[8], unsigned lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  T h[4], q[2];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const T send = b4 ? w[c] : w[c + 4];
+    const T keep = b4 ? w[c + 4] : w[c];
+    h[c] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const T send = b3 ? h[c] : h[c + 2];
+    const T keep = b3 ? h[c + 2] : h[c];
+    q[c] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+  }
+  T v = (b2 ? q[1] : q[0]) + __shfl_xor_sync(0xFFFFFFFFu, b2 ? q[0] : q[1], 4);
+  v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+  v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+  return v;
 }
 
 // ---------------------------------------------------------------------------
 // sort
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_part_keys(int64_t np, int n, int bits, const T *__restrict__ x,
-                            const T *__restrict__ y, const T *__restrict__ z,
-                            uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+__global__ void k_part_keys(int64_t np, CicGrid<T> g, const T *__restrict__ x, const T *__restrict__ y,
+                            const T *__restrict__ z, uint32_t *__restrict__ key,
+                            uint32_t *__restrict__ val) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= np) return;
-  T w0, w1;
-  const int i = cic_axis(x[t], n, w0, w1), j = cic_axis(y[t], n, w0, w1),
-            k = cic_axis(z[t], n, w0, w1);
-  key[t] = uint32_t(hilbert_index(uint32_t(i), uint32_t(j), uint32_t(k), bits));
+  const uint32_t m = uint32_t(g.n - 1);
+  const uint32_t i = uint32_t(cic_cell(x[t], g)) & m, j = uint32_t(cic_cell(y[t], g)) & m,
+                 k = uint32_t(cic_cell(z[t], g)) & m;
+  key[t] = uint32_t(hilbert_index(i, j, k, g.bits));
   val[t] = uint32_t(t);
 }
 
@@ -197,7 +302,7 @@ __global__ void k_part_gather(int64_t np, const uint32_t *__restrict__ perm, con
 // atomic deposit (warp combining of equal source cells)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_cic_atomic(int64_t np, int n, T scale, const T *__restrict__ x,
+__global__ void __launch_bounds__(256) k_cic_atomic(int64_t np, CicGrid<T> g, const T *__restrict__ x,
                                                     const T *__restrict__ y, const T *__restrict__ z,
                                                     const T *__restrict__ m, T *__restrict__ rho) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -207,34 +312,30 @@ __global__ void __launch_bounds__(256) k_cic_atomic(int64_t np, int n, T scale, 
   int i = 0, j = 0, k = 0;
   uint32_t cell = 0xFFFFFFFFu;
   if (valid) {
-    cic_weights(x[t], y[t], z[t], m[t] * scale, n, i, j, k, w);
-    cell = grid_at(n, i, j, k);
+    cic_weights(x[t], y[t], z[t], m[t], g, i, j, k, w);
+    cell = grid_at(g.n, i, j, k);
   } else {
 #pragma unroll
     for (int c = 0; c < 8; ++c) w[c] = T(0);
   }
-  // segments: runs of equal source cells among the warp's lanes
+  // runs of equal source cells among the warp's lanes
   const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cell, 1);
-  const unsigned heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != cell);
-  if (heads != 0xFFFFFFFFu) {
-    const unsigned above = heads & ~((2u << lane) - 1u);  // heads after this lane (lane 31: none)
-    const unsigned next = above ? unsigned(__ffs(above) - 1) : 32u;
-    const unsigned len = ((heads >> lane) & 1u) ? next - lane : 0u;
-    const unsigned maxrun = __reduce_max_sync(0xFFFFFFFFu, len);
-    // backward segmented inclusive scan: the head lane ends with its
-    // segment's total
-    for (unsigned off = 1; off < maxrun; off <<= 1) {
-      const bool take = lane + off < next;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const T o = __shfl_down_sync(0xFFFFFFFFu, w[c], off);
-        if (take) w[c] += o;
-      }
+  const unsigned runs = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != cell);
+  if (runs == 1u) {
+    // one source cell for the whole warp (or no particle at all): lanes
+    // 0, 4, .., 28 add one component each
+    if (cell == 0xFFFFFFFFu) return;
+    const T v = warp_total_scatter(w, lane);
+    if ((lane & 3) == 0) {
+      const int c = int(lane >> 2);
+      atomicAdd(&rho[grid_at(g.n, i + (c & 1), j + ((c >> 1) & 1), k + (c >> 2))], v);
     }
+    return;
   }
-  if (valid && ((heads >> lane) & 1u)) {
+  if (runs != 0xFFFFFFFFu) warp_run_sums(w, runs, lane);
+  if (valid && ((runs >> lane) & 1u)) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) atomicAdd(&rho[grid_at(n, i + (c & 1), j + ((c >> 1) & 1), k + (c >> 2))], w[c]);
+    for (int c = 0; c < 8; ++c) atomicAdd(&rho[grid_at(g.n, i + (c & 1), j + ((c >> 1) & 1), k + (c >> 2))], w[c]);
   }
 }
 
@@ -262,29 +363,82 @@ __global__ void k_seg_starts(int64_t np, const uint32_t *__restrict__ key, const
   }
 }
 
-// one thread per segment: the 8 sums of its particles' contributions, in
-// particle order, into sums[c * cap + s]; the segment's source cell maps to s
+// Per particle, in aligned groups of 32 (one warp each): the contributions
+// summed over each run of equal source cells inside the group (fixed shuffle
+// tree).  A run that starts segment s writes its sums to sums[c * cap + s]
+// and maps its source cell to s; the run at the start of group G that
+// continues a segment from earlier groups writes them to carry[c * ngroups + G].
 template <class T>
-__global__ void k_seg_sum(int64_t cap, int n, T scale, const uint32_t *__restrict__ nseg,
-                          const uint32_t *__restrict__ start, const T *__restrict__ x,
-                          const T *__restrict__ y, const T *__restrict__ z, const T *__restrict__ m,
-                          T *__restrict__ sums, int32_t *__restrict__ cellmap) {
+__global__ void __launch_bounds__(256) k_seg_partial(int64_t np, CicGrid<T> g, const uint32_t *__restrict__ key,
+                                                     const uint32_t *__restrict__ scan, const T *__restrict__ x,
+                                                     const T *__restrict__ y, const T *__restrict__ z,
+                                                     const T *__restrict__ m, int64_t cap, int64_t ngroups,
+                                                     T *__restrict__ sums, T *__restrict__ carry,
+                                                     int32_t *__restrict__ cellmap) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31;
+  const bool valid = t < np;
+  T w[8];
+  int i = 0, j = 0, k = 0;
+  uint32_t kk = 0xFFFFFFFFu;
+  bool head = false;
+  if (valid) {
+    cic_weights(x[t], y[t], z[t], m[t], g, i, j, k, w);
+    kk = key[t];
+    head = t == 0 || key[t - 1] != kk;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) w[c] = T(0);
+  }
+  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, kk, 1);
+  const unsigned runs = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != kk);
+  if (runs == 1u) {
+    // the whole group is one run: reduce-scatter, lane 4c writes component c
+    if (kk == 0xFFFFFFFFu) return;
+    const T v = warp_total_scatter(w, lane);
+    const bool head0 = __shfl_sync(0xFFFFFFFFu, head, 0);
+    if ((lane & 3) == 0) {
+      const int c = int(lane >> 2);
+      if (head0)
+        sums[c * cap + int64_t(scan[t - lane])] = v;
+      else
+        carry[c * ngroups + (t >> 5)] = v;
+    }
+    if (lane == 0 && head0) cellmap[grid_at(g.n, i, j, k)] = int32_t(scan[t]);
+    return;
+  }
+  if (runs != 0xFFFFFFFFu) warp_run_sums(w, runs, lane);
+  if (!valid) return;
+  if (head) {
+    const int64_t s = scan[t];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sums[c * cap + s] = w[c];
+    cellmap[grid_at(g.n, i, j, k)] = int32_t(s);
+  } else if (lane == 0) {
+    const int64_t G = t >> 5;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) carry[c * ngroups + G] = w[c];
+  }
+}
+
+// Per segment that spans groups: add the carries of its later groups, in
+// group order.
+template <class T>
+__global__ void k_seg_carry(const uint32_t *__restrict__ nseg, const uint32_t *__restrict__ start, int64_t cap,
+                            int64_t ngroups, const T *__restrict__ carry, T *__restrict__ sums) {
   const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (s >= int64_t(*nseg)) return;
-  const uint32_t q0 = start[s], q1 = start[s + 1];
+  const int64_t g0 = int64_t(start[s]) >> 5, g1 = (int64_t(start[s + 1]) - 1) >> 5;
+  if (g1 == g0) return;
   T acc[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) acc[c] = T(0);
-  int i = 0, j = 0, k = 0;
-  for (uint32_t q = q0; q < q1; ++q) {
-    T w[8];
-    cic_weights(x[q], y[q], z[q], m[q] * scale, n, i, j, k, w);
+  for (int c = 0; c < 8; ++c) acc[c] = sums[c * cap + s];
+  for (int64_t G = g0 + 1; G <= g1; ++G) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] += w[c];
+    for (int c = 0; c < 8; ++c) acc[c] += carry[c * ngroups + G];
   }
 #pragma unroll
   for (int c = 0; c < 8; ++c) sums[c * cap + s] = acc[c];
-  cellmap[grid_at(n, i, j, k)] = int32_t(s);
 }
 
 // one thread per grid cell: rho = the sums of the (up to) 8 segments whose

@@ -106,5 +106,5 @@ def test_particle_calls_check_their_arguments_on_the_host(lib):
     assert lib.amr_cic_deposit(None, 2) == amr.AMR_EINVAL
     assert lib.amr_part_destroy(None) == amr.AMR_OK
     names = amr.part_kernel_names()
-    for k in ("part_keys", "psort_scatter", "cic_atomic", "seg_sum", "seg_gather"):
+    for k in ("part_keys", "psort_scatter", "cic_atomic", "seg_partial", "seg_gather"):
         assert k in names

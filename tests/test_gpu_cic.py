@@ -221,7 +221,7 @@ def test_info_and_timing():
     p.deposit("atomic")
     p.deposit("segment")
     t = p.read_timing()
-    for k in ("part_keys", "psort_hist", "psort_scatter", "part_gather", "cic_atomic", "seg_sum",
+    for k in ("part_keys", "psort_hist", "psort_scatter", "part_gather", "cic_atomic", "seg_partial",
               "seg_gather"):
         assert k in t and t[k][1] >= 1, k
     inf = p.info()
