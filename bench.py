@@ -58,7 +58,7 @@ def parse():
                     help="grid cells per axis of the deposition measurement (N_part = N_grid)")
     ap.add_argument("--profile-cic", type=int, default=0,
                     help="profiling mode: one sort and one deposit of each algorithm of n^3 "
-                         "cosmological particles on the n^3 grid (FP64), then exit")
+                         "cosmological particles on the n^3 grid (--precision), then exit")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--no-other-precision", action="store_true",
                     help="run only --precision (skip the other precision's pass)")
@@ -692,12 +692,13 @@ def main():
         build.build()
         amr.load()
         ps = inputs.particles(args.profile_cic, "cosmo", seed=2607)
-        p = amr.Particles(*ps.args())
+        p = amr.Particles(*ps.args(), precision=args.precision)
         p.sort()
         p.deposit("atomic")
         p.deposit("segment")
         p.rho()
-        print(json.dumps({"profile_cic": args.profile_cic, "particles": ps.np}))
+        print(json.dumps({"profile_cic": args.profile_cic, "particles": ps.np,
+                          "precision": args.precision}))
         p.close()
         return 0
     if args.profile_level:

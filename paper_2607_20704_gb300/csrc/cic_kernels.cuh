@@ -196,10 +196,15 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_hist(const uint32_t *__r
   for (int d = threadIdx.x; d < ndig; d += blockDim.x) hist[d] = 0;
   __syncthreads();
   const int64_t base = blockIdx.x * int64_t(kSortTile);
+  unsigned dk[kSortRounds];  // all loads of the tile in flight at once
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t t = base + r * kSortThreads + threadIdx.x;
-    const unsigned dig = t < np ? (keys[t] >> shift) & unsigned(ndig - 1) : 0xFFFFFFFFu;
+    dk[r] = t < np ? __ldcs(keys + t) : 0xFFFFFFFFu;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const unsigned dig = dk[r] != 0xFFFFFFFFu ? (dk[r] >> shift) & unsigned(ndig - 1) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
     if (dig != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&hist[dig], unsigned(__popc(peers)));
   }
@@ -241,12 +246,20 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_scatter(
   }
   lstart[threadIdx.x] = part[threadIdx.x] - cnt;
   run[threadIdx.x] = part[threadIdx.x] - cnt;
+  uint32_t kr[kSortRounds], vr[kSortRounds];  // all loads of the tile in flight at once
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int q = r * kSortThreads + threadIdx.x;
+    kr[r] = q < nt ? __ldcs(kin + base + q) : 0u;
+    vr[r] = q < nt ? __ldcs(vin + base + q) : 0u;
+  }
   __syncthreads();
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int q = r * kSortThreads + threadIdx.x;
     const bool valid = q < nt;
-    const uint32_t k = valid ? kin[base + q] : 0u;
-    const uint32_t v = valid ? vin[base + q] : 0u;
+    const uint32_t k = kr[r];
+    const uint32_t v = vr[r];
     const unsigned dig = valid ? (k >> shift) & unsigned(ndig - 1) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
     const unsigned rank = __popc(peers & ((1u << lane) - 1u));
@@ -332,8 +345,12 @@ __global__ void __launch_bounds__(256) k_cic_atomic(int64_t np, CicGrid<T> g, co
     }
     return;
   }
-  if (runs != 0xFFFFFFFFu) warp_run_sums(w, runs, lane);
-  if (valid && ((runs >> lane) & 1u)) {
+  // Partial runs: FP32 sums them before its atomics; FP64, whose additions
+  // cost 1/64 of the FP32 rate on GB300, lets every particle add its own 8
+  // contributions (L2 absorbs the extra atomics).
+  const bool combine = sizeof(T) == 4;
+  if (combine && runs != 0xFFFFFFFFu) warp_run_sums(w, runs, lane);
+  if (valid && (!combine || ((runs >> lane) & 1u))) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) atomicAdd(&rho[grid_at(g.n, i + (c & 1), j + ((c >> 1) & 1), k + (c >> 2))], w[c]);
   }
