@@ -90,13 +90,23 @@ typedef struct {
   int regrid_every_step;    /* 1: amr_advance regrids before every coarse
                                step; 0: the mesh only changes by amr_regrid
                                (default) */
+  int nsubgrid;             /* level-step kernel (Sec. 3): 0: per-cell passes
+                               (primitives, predictor, faces, update, each
+                               computed once); 1, 2 or 4 (4: precision 4
+                               only): the paper's fused shared-memory kernel
+                               ("rock") on blocks of nsubgrid^3 octs staged
+                               with one ring of octs (6^3, 8^3 or 12^3
+                               cells); -1 (default): picked by the autotuner
+                               among these when tile is 0, else the per-cell
+                               passes.  All give the same results bit for
+                               bit. */
 } amr_params;
 
 /* Fills p with the defaults: levelmin = levelmax = 1, gamma = 1.4, cfl = 0.8,
  * smallr = smallc = 1e-10, precision 8, reflux 1, reindex_every_step 1,
- * use_graphs 1, no budget, NULL stream and allocator, tile 0 and schedule -1
- * (both picked by the autotuner), refinement criteria off, regrid_expand 1,
- * regrid_every_step 0. */
+ * use_graphs 1, no budget, NULL stream and allocator, tile 0, schedule -1 and
+ * nsubgrid -1 (picked by the autotuner), refinement criteria off,
+ * regrid_expand 1, regrid_every_step 0. */
 void amr_params_default(amr_params *p);
 
 /*
@@ -322,6 +332,7 @@ typedef struct {
   int n_members, member;      /* members of the handle; the selected one */
   int phases;                 /* level-step phases of one coarse step */
   int tile, schedule;         /* work-tile size and schedule in use */
+  int nsubgrid;               /* level-step kernel in use (amr_params.nsubgrid) */
 } amr_info;
 
 /* Counts of the mesh and of the work done so far. */

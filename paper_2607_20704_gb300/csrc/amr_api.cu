@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "hydro_kernels.cuh"
+#include "rock_kernels.cuh"
 #include "regrid_kernels.cuh"
 #include "mg_kernels.cuh"
 #include "index_kernels.cuh"
@@ -81,14 +82,15 @@ enum Kid {
   K_GRADING, K_NEIGHBOURS, K_CLAIM, K_CACHE_FINALIZE, K_NBR_FIX, K_FACES, K_CACHE_SOURCES,
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
-  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_COUNT
+  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_ROCK_COMMIT, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
     "father_son", "grading", "neighbours", "claim_comp", "cache_finalize", "neighbours_fix",
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
-    "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other"};
+    "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
+    "rock", "rock_commit"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -105,12 +107,12 @@ struct DevBuf {
 };
 
 // level-step launch domains of a segment
-enum Dom { DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_COUNT = 4 };
+enum Dom { DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_BLOCKS = 4, DOM_COUNT = 5 };
 
 // a list of segments and, per domain, its flattened tiles
 struct SegList {
   int seg0 = 0, nseg = 0;
-  int tile0[DOM_COUNT] = {0, 0, 0, 0}, ntile[DOM_COUNT] = {0, 0, 0, 0};
+  int tile0[DOM_COUNT] = {0, 0, 0, 0, 0}, ntile[DOM_COUNT] = {0, 0, 0, 0, 0};
   int ls = 0;  // scratch cells used
 };
 
@@ -178,6 +180,13 @@ struct amr_mesh {
   int tile_size = 256;
   bool persistent = true;
   bool tuned = false;
+  // fused shared-memory level step ("rock" kernel): octs per axis of a block
+  // (0: the per-cell passes), block starts (mesh indices) and, on the host,
+  // the block of every oct
+  int nsub = 0;
+  int32_t *blk = nullptr;
+  std::vector<int32_t> blkid_h;
+  std::vector<float> tune_ms;  // the autotuner's best step time per candidate
   std::vector<std::pair<const void *, int>> occ;  // (kernel, blocks per SM) at tile_size
 
   // state and scratch
@@ -320,6 +329,34 @@ static void launch(amr_mesh *h, int kid, void (*kern)(KArgs...), dim3 grid, dim3
     ++h->launches;
 }
 
+// launch() with dynamic shared memory
+template <class... KArgs, class... Args>
+static void launch_smem(amr_mesh *h, int kid, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                        Args &&...args) {
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+  const bool timed = h->timing && !h->capturing;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (timed) {
+    e0 = take_event(h);
+    cudaEventRecord(e0, h->s);
+  }
+  kern<<<grid, block, smem, h->s>>>(std::forward<Args>(args)...);
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess && h->launch_err == cudaSuccess) {
+    h->launch_err = le;
+    h->launch_err_kid = kid;
+  }
+  if (timed) {
+    e1 = take_event(h);
+    cudaEventRecord(e1, h->s);
+    h->pending.push_back({kid, e0, e1});
+  }
+  if (h->capturing)
+    ++h->capture_kernels;
+  else
+    ++h->launches;
+}
+
 static inline unsigned nblocks(int64_t n, int b = 256) { return unsigned((n + b - 1) / b); }
 
 // device error word -> status
@@ -412,6 +449,7 @@ static int dom_size(const Seg &s, int dom) {
     case DOM_CELLS: return 8 * (s.nl + s.ncl);
     case DOM_REAL: return 8 * s.nl;
     case DOM_GHOST5: return 5 * s.ncl;
+    case DOM_BLOCKS: return s.nblk;
     default:
       return ((s.flags & kSegReflux) ? 5 * s.ncl : 0) + ((s.flags & kSegRestrict) ? 5 * s.nl : 0);
   }
@@ -434,6 +472,12 @@ static SegList make_list(amr_mesh *h, const std::vector<std::pair<int, int>> &ml
     s.clo = int(m.cache_base + m.clo[l]);
     s.ncl = int(m.clo[l + 1] - m.clo[l]);
     s.base = base;
+    s.blk0 = 0;
+    s.nblk = 0;
+    if (h->nsub > 0 && s.nl > 0 && !h->blkid_h.empty()) {
+      s.blk0 = h->blkid_h[size_t(s.lo)];
+      s.nblk = h->blkid_h[size_t(s.lo + s.nl - 1)] - s.blk0 + 1;
+    }
     if (mode == 1)
       s.flags = l > m.lmin ? kSegRestrict : 0;
     else
@@ -448,7 +492,8 @@ static SegList make_list(amr_mesh *h, const std::vector<std::pair<int, int>> &ml
     L.tile0[d] = int(h->tiles_h.size());
     for (int q = 0; q < L.nseg; ++q) {
       const int n = dom_size(h->segs_h[L.seg0 + q], d);
-      for (int st = 0; st < n; st += h->tile_size) h->tiles_h.push_back({L.seg0 + q, st});
+      const int step = d == DOM_BLOCKS ? 1 : h->tile_size;  // one block of octs per tile
+      for (int st = 0; st < n; st += step) h->tiles_h.push_back({L.seg0 + q, st});
     }
     L.ntile[d] = int(h->tiles_h.size()) - L.tile0[d];
   }
@@ -510,6 +555,7 @@ static StepArgs<T> step_args(amr_mesh *h, bool device_dt, double dt) {
   a.Rc = static_cast<T *>(h->Rc);
   a.rslot = h->rslot;
   a.fnb = h->fnb;
+  a.nbr27 = h->nbr27;
   a.son = h->son;
   a.father = h->father;
   a.key = h->key;
@@ -557,12 +603,47 @@ static void run_list(amr_mesh *h, int kid, void (*kern)(StepArgs<T>), StepArgs<T
   launch(h, kid, kern, dim3(unsigned(grid)), dim3(unsigned(h->tile_size)), a);
 }
 
+// the fused kernel over the blocks of a list (dynamic shared memory)
+template <class T, int NS>
+static void run_rock_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
+  if (L.ntile[DOM_BLOCKS] == 0) return;
+  a.tiles = h->tiles + L.tile0[DOM_BLOCKS];
+  a.ntiles = L.ntile[DOM_BLOCKS];
+  constexpr size_t smem = Rock<NS>::template smem<T>();
+  auto kern = k_rock<T, NS>;
+  int per_sm = 0;
+  for (auto &o : h->occ)
+    if (o.first == (const void *)kern) per_sm = o.second;
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Rock<NS>::THREADS, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    h->occ.push_back({(const void *)kern, per_sm});
+  }
+  const int grid = h->persistent ? std::min(a.ntiles, per_sm * h->sm_count) : a.ntiles;
+  launch_smem(h, K_ROCK, kern, dim3(unsigned(grid)), dim3(unsigned(Rock<NS>::THREADS)), smem, a,
+              (const int32_t *)h->blk);
+}
+
 template <class T>
 static void run_segments(amr_mesh *h, const SegList &L, bool device_dt, double dt) {
   if (L.nseg == 0) return;
   StepArgs<T> a = step_args<T>(h, device_dt, dt);
   run_list(h, K_PROLONG, k_prolong<T>, a, L, DOM_GHOST5);
-  if constexpr (sizeof(T) == 4) {
+  if (h->nsub > 0) {
+    // the paper's fused kernel: one block of nsub^3 octs per CTA, then the new
+    // leaf states from the scratch into U
+    if (h->nsub == 1)
+      run_rock_ns<T, 1>(h, a, L);
+    else if (h->nsub == 2)
+      run_rock_ns<T, 2>(h, a, L);
+    else if constexpr (sizeof(T) == 4)
+      run_rock_ns<T, 4>(h, a, L);
+    run_list(h, K_ROCK_COMMIT, k_rock_commit<T>, a, L, DOM_REAL);
+  } else if constexpr (sizeof(T) == 4) {
     // FP32: primitives recomputed inside the predictor; each leaf cell solves
     // its six faces and updates itself
     run_list(h, K_PREDICT, k_predict_u<T>, a, L, DOM_CELLS);
@@ -705,6 +786,7 @@ extern "C" void amr_params_default(amr_params *p) {
   p->use_graphs = 1;
   p->regrid_expand = 1;
   p->regrid_every_step = 0;
+  p->nsubgrid = -1;
 }
 
 static void destroy_all(amr_mesh *h) {
@@ -793,6 +875,8 @@ static amr_status upload_members(amr_mesh *h) {
   if (h->p.precision == 4) return upload_member_params<float>(h);
   return upload_member_params<double>(h);
 }
+
+static amr_status build_blocks(amr_mesh *h);
 
 static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
                              uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
@@ -1030,6 +1114,7 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   }
 
   // --- work lists, scratch, time-step arrays ------------------------------------------
+  if (h->nsub > 0) AMR_TRY(build_blocks(h));
   build_lists(h);
   AMR_TRY(upload(h, &h->segs, h->segs_h));
   AMR_TRY(upload(h, &h->tiles, h->tiles_h));
@@ -1125,8 +1210,13 @@ extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
     delete h;
     return fail(AMR_EINVAL, "amr_create: tile must be 0, 64, 128, 256 or 512");
   }
+  if (!(p->nsubgrid >= -1 && p->nsubgrid <= 2) && !(p->nsubgrid == 4 && p->precision == 4)) {
+    delete h;
+    return fail(AMR_EINVAL, "amr_create: nsubgrid must be -1, 0, 1, 2, or 4 with precision 4");
+  }
   h->tile_size = p->tile ? p->tile : 256;
   h->persistent = p->schedule != 0;
+  h->nsub = p->nsubgrid > 0 ? p->nsubgrid : 0;
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count < 1) h->sm_count = 1;
@@ -1217,11 +1307,48 @@ static void coarse_step(amr_mesh *h) {
 
 static void coarse_step(amr_mesh *h);
 
-// Rebuild the tile lists for another tile size (segments and scratch do not
-// depend on it).
-static amr_status set_tile(amr_mesh *h, int tile) {
-  if (tile == h->tile_size && h->tiles) return AMR_OK;
+// Blocks of the fused kernel: runs of real octs (mesh order) of one (member,
+// level) whose coordinates lie in one aligned group of nsub^3 oct positions.
+// The level's Hilbert order visits every aligned group in one run; with
+// caller-given sort keys a group may come in several runs, which then form
+// several blocks (each updates only its own octs).
+static amr_status build_blocks(amr_mesh *h) {
+  const int64_t N = h->N;
+  std::vector<uint64_t> key(size_t(N > 0 ? N : 1));
+  if (N > 0) {
+    CUDA_TRY(cudaMemcpyAsync(key.data(), h->key, 8 * size_t(N), cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+  }
+  const unsigned sh = h->nsub == 4 ? 2u : h->nsub == 2 ? 1u : 0u;
+  h->blkid_h.assign(size_t(N), 0);
+  std::vector<int32_t> start;
+  for (int64_t o = 0; o < N; ++o) {
+    const uint64_t k = key[size_t(o)];
+    bool head = o == 0;
+    if (!head) {
+      const uint64_t q = key[size_t(o - 1)];
+      head = (k >> 45) != (q >> 45) || (ikey_x(k) >> sh) != (ikey_x(q) >> sh) ||
+             (ikey_y(k) >> sh) != (ikey_y(q) >> sh) || (ikey_z(k) >> sh) != (ikey_z(q) >> sh);
+    }
+    if (head) start.push_back(int32_t(o));
+    h->blkid_h[size_t(o)] = int32_t(start.size()) - 1;
+  }
+  start.push_back(int32_t(N));
+  dev_free(h, h->blk);
+  h->blk = nullptr;
+  AMR_TRY(upload(h, &h->blk, start));
+  return AMR_OK;
+}
+
+// Rebuild the tile lists for another tile size or fused-kernel block size
+// (segments and scratch do not depend on them).
+static amr_status set_tile(amr_mesh *h, int tile, int nsub) {
+  if (tile == h->tile_size && nsub == h->nsub && h->tiles) return AMR_OK;
   h->tile_size = tile;
+  if (nsub != h->nsub) {
+    h->nsub = nsub;
+    if (nsub > 0) AMR_TRY(build_blocks(h));
+  }
   h->occ.clear();
   build_lists(h);
   dev_free(h, h->segs);
@@ -1250,17 +1377,37 @@ static amr_status capture_coarse_step(amr_mesh *h, cudaGraphExec_t *out) {
   return AMR_OK;
 }
 
-// Time candidate (tile, schedule) pairs on full coarse steps from a snapshot
-// of the state, run as they will run (graph replays when graphs are on), the
-// best of three steps each; restore the snapshot; keep the fastest.
+// Time candidate launch shapes on full coarse steps from a snapshot of the
+// state, run as they will run (graph replays when graphs are on), the best of
+// three steps each; restore the snapshot; keep the fastest.  Candidates: the
+// per-cell passes with every tile size x schedule and, unless the tile size
+// or the kernel was fixed, the fused kernel with nsubgrid 1, 2 (and 4 in
+// FP32) x schedule.
+struct LaunchShape {
+  int tile, sched, nsub;
+};
+
 static amr_status autotune(amr_mesh *h) {
   h->tuned = true;
   std::vector<int> tiles =
       h->p.tile ? std::vector<int>{h->p.tile} : std::vector<int>{64, 128, 256, 512};
   std::vector<int> scheds = h->p.schedule >= 0 ? std::vector<int>{h->p.schedule} : std::vector<int>{1, 0};
-  if (tiles.size() * scheds.size() == 1) {
-    h->persistent = scheds[0] == 1;
-    return set_tile(h, tiles[0]);
+  std::vector<int> nsubs;
+  if (h->p.nsubgrid > 0)
+    nsubs = {h->p.nsubgrid};
+  else if (h->p.nsubgrid == 0 || h->p.tile)
+    nsubs = {0};
+  else if (h->p.precision == 4)
+    nsubs = {0, 1, 2, 4};
+  else
+    nsubs = {0, 1, 2};
+  std::vector<LaunchShape> cands;
+  for (int ns : nsubs)
+    for (int t : (ns == 0 ? tiles : std::vector<int>{tiles[0]}))
+      for (int sc : scheds) cands.push_back({t, sc, ns});
+  if (cands.size() == 1) {
+    h->persistent = cands[0].sched == 1;
+    return set_tile(h, cands[0].tile, cands[0].nsub);
   }
   const bool graphs = h->p.use_graphs && !h->timing;
   const size_t ub = h->elem() * 5 * size_t(h->S), rb = h->elem() * 5 * size_t(h->NC > 0 ? h->NC : 1);
@@ -1276,44 +1423,43 @@ static amr_status autotune(amr_mesh *h) {
   CUDA_TRY(cudaMemsetAsync(h->mrem, 0xFF, mb, h->s));
   cudaEvent_t e0 = take_event(h), e1 = take_event(h);
   float best = 1e30f;
-  int best_tile = 256, best_sched = 1;
-  for (int t : tiles)
-    for (int sc : scheds) {
-      AMR_TRY(set_tile(h, t));
-      h->persistent = sc == 1;
-      cudaGraphExec_t ge = nullptr;
-      if (graphs) AMR_TRY(capture_coarse_step(h, &ge));
-      auto step = [&] {
-        if (ge)
-          cudaGraphLaunch(ge, h->s);
-        else
-          coarse_step(h);
-      };
-      step();  // warm-up
-      float cand = 1e30f;
-      for (int r = 0; r < 3; ++r) {
-        cudaEventRecord(e0, h->s);
-        step();
-        cudaEventRecord(e1, h->s);
-        CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cand = std::min(cand, ms);
-      }
-      if (ge) cudaGraphExecDestroy(ge);
-      if (cand < best) {
-        best = cand;
-        best_tile = t;
-        best_sched = sc;
-      }
-      CUDA_TRY(cudaMemcpyAsync(h->U, su, ub, cudaMemcpyDeviceToDevice, h->s));
-      CUDA_TRY(cudaMemcpyAsync(h->Rc, sr, rb, cudaMemcpyDeviceToDevice, h->s));
+  LaunchShape pick = cands[0];
+  for (const LaunchShape &cd : cands) {
+    AMR_TRY(set_tile(h, cd.tile, cd.nsub));
+    h->persistent = cd.sched == 1;
+    cudaGraphExec_t ge = nullptr;
+    if (graphs) AMR_TRY(capture_coarse_step(h, &ge));
+    auto step = [&] {
+      if (ge)
+        cudaGraphLaunch(ge, h->s);
+      else
+        coarse_step(h);
+    };
+    step();  // warm-up
+    float cand = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, h->s);
+      step();
+      cudaEventRecord(e1, h->s);
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cand = std::min(cand, ms);
     }
+    if (ge) cudaGraphExecDestroy(ge);
+    h->tune_ms.push_back(cand);
+    if (cand < best) {
+      best = cand;
+      pick = cd;
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->U, su, ub, cudaMemcpyDeviceToDevice, h->s));
+    CUDA_TRY(cudaMemcpyAsync(h->Rc, sr, rb, cudaMemcpyDeviceToDevice, h->s));
+  }
   CUDA_TRY(cudaMemcpyAsync(h->mrem, sm, mb, cudaMemcpyDeviceToDevice, h->s));
   h->event_pool.push_back(e0);
   h->event_pool.push_back(e1);
-  AMR_TRY(set_tile(h, best_tile));
-  h->persistent = best_sched == 1;
+  AMR_TRY(set_tile(h, pick.tile, pick.nsub));
+  h->persistent = pick.sched == 1;
   dev_free(h, su);
   dev_free(h, sr);
   dev_free(h, sm);
@@ -1492,6 +1638,7 @@ static amr_mesh *regrid_shell(amr_mesh *h) {
   nh->tile_size = h->tile_size;
   nh->persistent = h->persistent;
   nh->tuned = h->tuned;
+  nh->nsub = h->nsub;
   return nh;
 }
 
@@ -1948,6 +2095,7 @@ extern "C" amr_status amr_get_info(amr_handle h, amr_info *info) {
   info->phases = int(h->phases.size());
   info->tile = h->tile_size;
   info->schedule = h->persistent ? 1 : 0;
+  info->nsubgrid = h->nsub;
   return AMR_OK;
 }
 

@@ -15,6 +15,8 @@ struct Seg {
   int clo, ncl;
   int base;
   int flags;  // kSegReflux: sum coarse-fine fluxes; kSegRestrict: restrict
+  int blk0;   // fused kernel: the segment's first block of octs (global index)
+  int nblk;   // and its number of blocks
 };
 enum : int { kSegReflux = 1, kSegRestrict = 2 };
 
@@ -36,6 +38,7 @@ struct StepArgs {
   T *Rc;                  // [5][NC] pending reflux of the father of ghost oct s
   const int32_t *rslot;   // [8N] ghost slot whose father is this cell, or -1
   const int32_t *fnb;     // [6][NE] face neighbours (extended index, -1 none)
+  const int32_t *nbr27;   // [27][N] same-level octs around each real oct, (dz,dy,dx) order
   const uint32_t *son;    // [N] split mask
   const int32_t *father;  // [N] father oct (mesh index), -1 at a member's levelmin
   const uint64_t *key;    // [N] internal keys

@@ -223,19 +223,26 @@ __global__ void k_prolong(StepArgs<T> a) {
 // ---------------------------------------------------------------------------
 // primitives of every real and ghost cell; domain: 8 (nl + ncl)
 // ---------------------------------------------------------------------------
+// primitives (rho, u, v, w, p) of the conservative state (u0..u4), with the
+// density and pressure floors
 template <class T>
-__device__ __forceinline__ void prim_at(const StepArgs<T> &a, const SegCtx<T> &s, int t,
-                                        T (&w)[5]) {
-  const int g = 8 * ext_of_local(a, s, t >> 3) + (t & 7);
-  const T r = vmax(a.U[g], s.smallr);
+__device__ __forceinline__ void prim_of(const SegCtx<T> &s, T u0, T u1, T u2, T u3, T u4, T (&w)[5]) {
+  const T r = vmax(u0, s.smallr);
   const T ir = rcp(r);
-  const T vx = a.U[a.S + g] * ir, vy = a.U[2 * a.S + g] * ir, vz = a.U[3 * a.S + g] * ir;
+  const T vx = u1 * ir, vy = u2 * ir, vz = u3 * ir;
   const T ek = T(0.5) * r * ((vx * vx + vy * vy) + vz * vz);
   w[0] = r;
   w[1] = vx;
   w[2] = vy;
   w[3] = vz;
-  w[4] = vmax((s.gamma - T(1)) * (a.U[4 * a.S + g] - ek), r * s.smallp);
+  w[4] = vmax((s.gamma - T(1)) * (u4 - ek), r * s.smallp);
+}
+
+template <class T>
+__device__ __forceinline__ void prim_at(const StepArgs<T> &a, const SegCtx<T> &s, int t,
+                                        T (&w)[5]) {
+  const int g = 8 * ext_of_local(a, s, t >> 3) + (t & 7);
+  prim_of(s, a.U[g], a.U[a.S + g], a.U[2 * a.S + g], a.U[3 * a.S + g], a.U[4 * a.S + g], w);
 }
 
 template <class T>
@@ -403,6 +410,17 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   F[4] = (eo + po) * uo;
 }
 
+// face states W* +- dW/2 of the two cells of a face (with the floors) and
+// their HLLC flux
+template <int D, class T>
+__device__ __forceinline__ void face_flux_states(const SegCtx<T> &s, T (&qL)[5], T (&qR)[5], T (&F)[5]) {
+  qL[0] = vmax(qL[0], s.smallr);
+  qR[0] = vmax(qR[0], s.smallr);
+  qL[4] = vmax(qL[4], qL[0] * s.smallp);
+  qR[4] = vmax(qR[4], qR[0] * s.smallp);
+  hllc<D>(qL, qR, s.gamma, s.igm1, F);
+}
+
 // flux across the face between local cells tl (minus side) and tr (plus side)
 template <int D, class T>
 __device__ __forceinline__ void face_flux(const StepArgs<T> &a, const SegCtx<T> &s, int tl, int tr,
@@ -416,11 +434,7 @@ __device__ __forceinline__ void face_flux(const StepArgs<T> &a, const SegCtx<T> 
     qL[v] = __ldg(a.Q + v * a.LS + ol) + T(0.5) * __ldg(a.Q + (5 + 5 * D + v) * a.LS + ol);
     qR[v] = __ldg(a.Q + v * a.LS + orr) - T(0.5) * __ldg(a.Q + (5 + 5 * D + v) * a.LS + orr);
   }
-  qL[0] = vmax(qL[0], s.smallr);
-  qR[0] = vmax(qR[0], s.smallr);
-  qL[4] = vmax(qL[4], qL[0] * s.smallp);
-  qR[4] = vmax(qR[4], qR[0] * s.smallp);
-  hllc<D>(qL, qR, s.gamma, s.igm1, F);
+  face_flux_states<D>(s, qL, qR, F);
 }
 
 // reflux slot of a coarse-fine face: ghost oct g (local oct index), the
@@ -480,22 +494,30 @@ __global__ void k_flux(StepArgs<T> a) {
             });
 }
 
-// U <- (U + dt/dx sum_d (F_d- - F_d+)) + R on leaf cells; R <- 0
+// U <- (U + dt/dx sum_d (F_d- - F_d+)) + R on leaf cells; R <- 0.  The new
+// state goes to `out` (stride `ostride`): U itself, or a buffer when other
+// blocks may still read the old state.
 template <class T>
-__device__ __forceinline__ void update_cell(const StepArgs<T> &a, const SegCtx<T> &s, int g,
-                                            const T (&dx)[5], const T (&dy)[5], const T (&dz)[5]) {
+__device__ __forceinline__ void update_cell_to(const StepArgs<T> &a, const SegCtx<T> &s, int g,
+                                               const T (&dx)[5], const T (&dy)[5], const T (&dz)[5],
+                                               T *out, int64_t ostride) {
   const int rs = int(checked(__ldg(a.rslot + g), -1, a.NC, a.err, -1));
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    T *Ug = a.U + v * a.S + g;
-    T u = *Ug + s.dtdx * ((dx[v] + dy[v]) + dz[v]);
+    T u = a.U[v * a.S + g] + s.dtdx * ((dx[v] + dy[v]) + dz[v]);
     if (rs >= 0) {
       T *Rv = a.Rc + v * int64_t(a.NC) + rs;
       u = u + *Rv;
       *Rv = T(0);
     }
-    *Ug = u;
+    out[v * ostride] = u;
   }
+}
+
+template <class T>
+__device__ __forceinline__ void update_cell(const StepArgs<T> &a, const SegCtx<T> &s, int g,
+                                            const T (&dx)[5], const T (&dy)[5], const T (&dz)[5]) {
+  update_cell_to(a, s, g, dx, dy, dz, a.U + g, a.S);
 }
 
 template <class T>
