@@ -52,6 +52,8 @@ def parse():
                     help="skip the multigrid V-cycle measurement")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the adaptive run (regrid before every coarse step)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the per-cell vs fused (nsubgrid) level-step comparison")
     ap.add_argument("--no-cic", action="store_true",
                     help="skip the Cloud-in-Cell particle deposition measurement")
     ap.add_argument("--cic-grid", type=int, default=512,
@@ -256,7 +258,8 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
         # per-kernel device time: same K steps, each launch bracketed by CUDA
         # events on the library's stream (eager launches, no graph)
         m2 = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision,
-                      tile=mesh_tile, schedule=mesh_sched, stream=bench_stream())
+                      tile=mesh_tile, schedule=mesh_sched, nsubgrid=info["nsubgrid"],
+                      stream=bench_stream())
         for _ in range(warmup):
             m2.advance(1)
         m2.sync()
@@ -268,6 +271,42 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
         res["kernels"] = m2.read_timing()
         m2.close()
     return res
+
+
+def run_variants(prob, steps, torch, device, flush):
+    """The level-step kernels side by side on the workload: the per-cell
+    passes (autotuned tile and schedule) and the fused shared-memory kernel
+    with nsubgrid 1, 2 (and 4 in FP32), each schedule; median coarse-step
+    time of `steps` graph-replayed steps, L2 flushed between them."""
+    from paper_2607_20704_gb300 import amr
+    out = {}
+    for prec in (8, 4):
+        rows = []
+        shapes = [dict(nsubgrid=0)] + [dict(nsubgrid=ns, tile=128, schedule=sc)
+                                       for ns in ((1, 2) if prec == 8 else (1, 2, 4)) for sc in (0, 1)]
+        for shp in shapes:
+            m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=prec, stream=bench_stream(), **shp)
+            upd = work_per_step(m.info(), prob.levelmin)
+            st = m.stream
+            for _ in range(3):
+                m.advance(1)
+            ts = []
+            for _ in range(steps):
+                with torch.cuda.stream(st):
+                    flush_l2(flush)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                m.advance(1)
+                e1.record(st)
+                torch.cuda.synchronize(device)
+                ts.append(e0.elapsed_time(e1))
+            inf = m.info()
+            ms = float(np.median(ts))
+            rows.append({"nsubgrid": inf["nsubgrid"], "tile": inf["tile"], "schedule": inf["schedule"],
+                         "ms_per_step": round(ms, 4), "cell_updates_per_s": upd / (ms * 1e-3)})
+            m.close()
+        out["fp64" if prec == 8 else "fp32"] = rows
+    return out
 
 
 def run_e2e(prob, precision, steps, torch):
@@ -760,6 +799,7 @@ def main():
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
         poisson = None if args.no_poisson else run_poisson(8, 10, torch, device)
         cic = None if args.no_cic else run_cic(args.cic_grid, 5, 3, torch, peak_gbs, peak_src)
+        variants = None if args.no_variants else run_variants(prob, 7, torch, device, flush)
         adaptive = None
         if not args.no_adaptive:
             adaptive = {("fp64" if p == 8 else "fp32"): run_adaptive(prob, p, 10, torch, device)
@@ -818,7 +858,8 @@ def main():
                           "bytes_per_cell_update": step_bytes},
         "kernels": table,
         "gpu_launches": main_res["launches"],
-        "autotuned": {"tile": main_res["info"].get("tile"), "schedule": main_res["info"].get("schedule")},
+        "autotuned": {"tile": main_res["info"].get("tile"), "schedule": main_res["info"].get("schedule"),
+                      "nsubgrid": main_res["info"].get("nsubgrid")},
         "clocks": clocks,
         "e2e": e2e,
     }
@@ -827,7 +868,8 @@ def main():
             "value": other_value,
             "ms_per_step": other_s * 1e3 / args.steps,
             "roofline": rl_o, "kernels": table_o, "gpu_launches": other["launches"],
-            "autotuned": {"tile": other["info"].get("tile"), "schedule": other["info"].get("schedule")},
+            "autotuned": {"tile": other["info"].get("tile"), "schedule": other["info"].get("schedule"),
+                          "nsubgrid": other["info"].get("nsubgrid")},
             "step_roofline_frac": round(other_value / world
                                         * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)}
     if adaptive is not None:
@@ -836,6 +878,8 @@ def main():
         line["poisson"] = poisson
     if cic is not None:
         line["cic"] = cic
+    if variants is not None:
+        line["level_step_kernels"] = variants
     if batched is not None:
         line["batched"] = batched
     if serving is not None:
