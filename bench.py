@@ -68,6 +68,8 @@ def parse():
                     help="work-tile size of every handle (0: autotune at the first step)")
     ap.add_argument("--schedule", type=int, default=-1,
                     help="1 persistent grids, 0 one tile per block, -1 autotune")
+    ap.add_argument("--nsubgrid", type=int, default=-1,
+                    help="level-step kernel: 0 per-cell passes, 1/2/4 fused kernel, -1 autotune")
     ap.add_argument("--profile-poisson", type=int, default=0,
                     help="profiling mode: one multigrid V-cycle on a periodic 2^L grid, then exit")
     ap.add_argument("--profile-level", type=int, default=0,
@@ -207,7 +209,7 @@ def flush_l2(buf):
 
 
 # -- our arm ----------------------------------------------------------------------
-LAUNCH = {"tile": 0, "schedule": -1}  # set from --tile / --schedule
+LAUNCH = {"tile": 0, "schedule": -1, "nsubgrid": -1}  # set from --tile / --schedule / --nsubgrid
 _STREAM = []
 
 
@@ -705,7 +707,7 @@ def main():
     rank, world, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3
-    LAUNCH.update(tile=args.tile, schedule=args.schedule)
+    LAUNCH.update(tile=args.tile, schedule=args.schedule, nsubgrid=args.nsubgrid)
     if args.impl == "reference" and rank != 0:
         return 0  # the reference arm runs on rank 0 alone
     from paper_2607_20704_gb300 import inputs
