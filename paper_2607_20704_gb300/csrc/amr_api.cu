@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -518,17 +519,28 @@ static void build_lists(amr_mesh *h) {
     w_cycle(m, m.lmin, m.seq);
     P = std::max(P, m.seq.size());
   }
+  // identical (member, level) sets share one list: a W-cycle repeats the
+  // phases of its finer levels, and a level list equals its level's phase
+  std::map<std::pair<std::vector<std::pair<int, int>>, int>, SegList> memo;
+  auto list_of = [&](const std::vector<std::pair<int, int>> &ml, int mode) {
+    auto key = std::make_pair(ml, mode);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    const SegList L = make_list(h, ml, mode);
+    memo.emplace(std::move(key), L);
+    return L;
+  };
   for (size_t k = 0; k < P; ++k) {
     std::vector<std::pair<int, int>> ml;
     for (int q = 0; q < h->M; ++q)
       if (k < h->mem[q].seq.size()) ml.push_back({q, h->mem[q].seq[k]});
-    h->phases.push_back(make_list(h, ml, 0));
+    h->phases.push_back(list_of(ml, 0));
   }
   for (int l = 0; l <= kMaxLev; ++l) {
     std::vector<std::pair<int, int>> ml;
     for (int q = 0; q < h->M; ++q) ml.push_back({q, l});
-    h->level_list[l] = make_list(h, ml, 0);
-    h->restrict_list[l] = make_list(h, ml, 1);
+    h->level_list[l] = list_of(ml, 0);
+    h->restrict_list[l] = list_of(ml, 1);
   }
   std::vector<std::pair<int, int>> all;
   for (int q = 0; q < h->M; ++q)

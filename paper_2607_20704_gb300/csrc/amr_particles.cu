@@ -238,12 +238,29 @@ CicGrid<T> grid_of(const amr_particles *h) {
 template <class T>
 void sort_impl(amr_particles *h) {
   const int64_t np = h->np, nt = ntiles(h);
-  launch(h, P_KEYS, k_part_keys<T>, dim3(nblocks(np)), dim3(256), np, grid_of<T>(h), (const T *)h->x,
-         (const T *)h->y, (const T *)h->z, h->key, h->val);
+  const CicGrid<T> g = grid_of<T>(h);
+  const T *px = (const T *)h->x, *py = (const T *)h->y, *pz = (const T *)h->z;
+  const dim3 kg(nblocks(np)), kb256(256);
+  switch (h->bits) {
+    case 1: launch(h, P_KEYS, k_part_keys<T, 1>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 2: launch(h, P_KEYS, k_part_keys<T, 2>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 3: launch(h, P_KEYS, k_part_keys<T, 3>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 4: launch(h, P_KEYS, k_part_keys<T, 4>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 5: launch(h, P_KEYS, k_part_keys<T, 5>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 6: launch(h, P_KEYS, k_part_keys<T, 6>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 7: launch(h, P_KEYS, k_part_keys<T, 7>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 8: launch(h, P_KEYS, k_part_keys<T, 8>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    case 9: launch(h, P_KEYS, k_part_keys<T, 9>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+    default: launch(h, P_KEYS, k_part_keys<T, 10>, kg, kb256, np, g, px, py, pz, h->key, h->val); break;
+  }
   uint32_t *ka = h->key, *kb = h->key2, *va = h->val, *vb = h->val2;
+  // passes of equal width, at most 8 bits each (27-bit keys of a 512^3 grid:
+  // 7, 7, 7, 6): fewer digits per pass keep each digit's run in a tile longer,
+  // so the scatter writes stay coalesced
   const int total = 3 * h->bits;
-  for (int shift = 0; shift < total; shift += 8) {
-    const int nbits = total - shift < 8 ? total - shift : 8;
+  const int passes = (total + 7) / 8, width = (total + passes - 1) / passes;
+  for (int shift = 0; shift < total; shift += width) {
+    const int nbits = total - shift < width ? total - shift : width;
     const int64_t len = (int64_t(1) << nbits) * nt;
     launch(h, P_SORT_HIST, k_psort_hist, dim3(unsigned(nt)), dim3(kSortThreads), (const uint32_t *)ka, np,
            shift, nbits, h->table, nt);
@@ -317,7 +334,7 @@ extern "C" amr_status amr_part_create(const amr_part_params *p, int64_t np, cons
   h->np = np;
   const size_t pb = size_t(np) * h->esize, ib = size_t(np) * 4;
   const int64_t nt = (np + kSortTile - 1) / kSortTile;
-  const int64_t tlen = 256 * nt + 1;
+  const int64_t tlen = int64_t(kSortBins) * nt + 1;
   cudaError_t e = cudaSuccess;
   for (void **q : {&h->x, &h->y, &h->z, &h->m, &h->x2, &h->y2, &h->z2, &h->m2})
     if (e == cudaSuccess) e = dalloc(h, q, pb);

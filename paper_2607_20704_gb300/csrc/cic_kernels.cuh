@@ -172,7 +172,47 @@ __device__ __forceinline__ T warp_total_scatter(const T w[8], unsigned lane) {
 // ---------------------------------------------------------------------------
 // sort
 // ---------------------------------------------------------------------------
-template <class T>
+// 3-D Hilbert index of (x, y, z) < 2^BITS (BITS <= 10), x most significant:
+// the same curve as hilbert_index (Skilling's transposed construction),
+// unrolled and branch-free: the conditional exchanges become masks, the
+// Gray-code step a suffix XOR, and the bit interleave magic-number spreads.
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  return (v | (v << 2)) & 0x09249249u;
+}
+
+template <int BITS>
+__device__ __forceinline__ uint32_t hilbert_index_u32(uint32_t a0, uint32_t a1, uint32_t a2) {
+#pragma unroll
+  for (int b = BITS - 1; b >= 1; --b) {
+    const uint32_t m = (1u << b) - 1u;
+    a0 ^= (0u - ((a0 >> b) & 1u)) & m;
+    const uint32_t s1 = 0u - ((a1 >> b) & 1u);
+    const uint32_t t1 = (a0 ^ a1) & m & ~s1;
+    a0 ^= (m & s1) | t1;
+    a1 ^= t1;
+    const uint32_t s2 = 0u - ((a2 >> b) & 1u);
+    const uint32_t t2 = (a0 ^ a2) & m & ~s2;
+    a0 ^= (m & s2) | t2;
+    a2 ^= t2;
+  }
+  a1 ^= a0;
+  a2 ^= a1;
+  uint32_t g = a2 >> 1;  // g_i = XOR of the bits of a2 above i
+  g ^= g >> 1;
+  g ^= g >> 2;
+  g ^= g >> 4;
+  g ^= g >> 8;
+  a0 ^= g;
+  a1 ^= g;
+  a2 ^= g;
+  return (spread3(a0) << 2) | (spread3(a1) << 1) | spread3(a2);
+}
+
+template <class T, int BITS>
 __global__ void k_part_keys(int64_t np, CicGrid<T> g, const T *__restrict__ x, const T *__restrict__ y,
                             const T *__restrict__ z, uint32_t *__restrict__ key,
                             uint32_t *__restrict__ val) {
@@ -181,16 +221,18 @@ __global__ void k_part_keys(int64_t np, CicGrid<T> g, const T *__restrict__ x, c
   const uint32_t m = uint32_t(g.n - 1);
   const uint32_t i = uint32_t(cic_cell(x[t], g)) & m, j = uint32_t(cic_cell(y[t], g)) & m,
                  k = uint32_t(cic_cell(z[t], g)) & m;
-  key[t] = uint32_t(hilbert_index(i, j, k, g.bits));
+  key[t] = hilbert_index_u32<BITS>(i, j, k);
   val[t] = uint32_t(t);
 }
 
-// per-tile digit counts, table[d * ntiles + tile]
+// per-tile digit counts, table[d * ntiles + tile]; digits of up to 8 bits
+constexpr int kSortBins = 256;
+
 __global__ void __launch_bounds__(kSortThreads) k_psort_hist(const uint32_t *__restrict__ keys,
                                                              int64_t np, int shift, int nbits,
                                                              uint32_t *__restrict__ table,
                                                              int64_t ntiles) {
-  __shared__ uint32_t hist[256];
+  __shared__ uint32_t hist[kSortBins];
   const int ndig = 1 << nbits;
   const int lane = threadIdx.x & 31;
   for (int d = threadIdx.x; d < ndig; d += blockDim.x) hist[d] = 0;
