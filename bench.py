@@ -52,6 +52,8 @@ def parse():
                     help="skip the multigrid V-cycle measurement")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the adaptive run (regrid before every coarse step)")
+    ap.add_argument("--no-unigrid", action="store_true",
+                    help="skip the uniform 256^3 blast (Godunov level step and coarse step)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the per-cell vs fused (nsubgrid) level-step comparison")
     ap.add_argument("--no-cic", action="store_true",
@@ -308,6 +310,55 @@ def run_variants(prob, steps, torch, device, flush):
                          "ms_per_step": round(ms, 4), "cell_updates_per_s": upd / (ms * 1e-3)})
             m.close()
         out["fp64" if prec == 8 else "fp32"] = rows
+    return out
+
+
+def run_unigrid(level, steps, torch, device):
+    """The blast on a uniform 2^level grid (one level, no refinement): the
+    Godunov level step alone (amr_step_level: primitives, predictor, HLLC
+    fluxes, update) and the whole coarse step (re-index, time step, level
+    step), median over `steps`, each precision.  The paper quotes its
+    unigrid Sedov rates this way (rock kernel, H200, FP32)."""
+    from paper_2607_20704_gb300 import amr, inputs
+    n = 1 << level
+    r0 = 2.0 / n
+
+    def fn(x, y, z):
+        r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2
+        p = np.where(r2 < r0 * r0, (5.0 / 3.0 - 1.0) / (4.0 / 3.0 * np.pi * r0 ** 3), 1e-5)
+        zero = 0.0 * x
+        return 1.0 + zero, zero, zero, zero, p
+    prob = inputs.uniform_grid(level, fn, gamma=5.0 / 3.0)
+    out = {"grid": f"{n}^3 cells, one level", "cells": n ** 3}
+    for prec in (8, 4):
+        m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=prec, stream=bench_stream())
+        st = m.stream
+        m.advance(3, sync=True)
+        dt = m.cfl_dt() * 1e-3
+        ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        lv, cs = [], []
+        for _ in range(steps):
+            e0, e1 = ev()
+            e0.record(st)
+            m.step_level(level, dt)
+            e1.record(st)
+            torch.cuda.synchronize(device)
+            lv.append(e0.elapsed_time(e1))
+            e0, e1 = ev()
+            e0.record(st)
+            m.advance(1)
+            e1.record(st)
+            torch.cuda.synchronize(device)
+            cs.append(e0.elapsed_time(e1))
+        inf = m.info()
+        lms, cms = float(np.median(lv)), float(np.median(cs))
+        out["fp64" if prec == 8 else "fp32"] = {
+            "level_step_ms": round(lms, 4), "level_step_cell_updates_per_s": n ** 3 / (lms * 1e-3),
+            "coarse_step_ms": round(cms, 4), "coarse_step_cell_updates_per_s": n ** 3 / (cms * 1e-3),
+            "tile": inf["tile"], "schedule": inf["schedule"], "nsubgrid": inf["nsubgrid"]}
+        m.close()
+    out["paper_context"] = ("H200, FP32 with fast math, unigrid Sedov, Godunov only: rock kernel "
+                            "nsubgrid 4 0.09 ns per cell (11.1e9 /s), paper kernel 0.2 ns (5e9 /s)")
     return out
 
 
@@ -802,6 +853,7 @@ def main():
         poisson = None if args.no_poisson else run_poisson(8, 10, torch, device)
         cic = None if args.no_cic else run_cic(args.cic_grid, 5, 3, torch, peak_gbs, peak_src)
         variants = None if args.no_variants else run_variants(prob, 7, torch, device, flush)
+        unigrid = None if args.no_unigrid else run_unigrid(8, 7, torch, device)
         adaptive = None
         if not args.no_adaptive:
             adaptive = {("fp64" if p == 8 else "fp32"): run_adaptive(prob, p, 10, torch, device)
@@ -882,6 +934,8 @@ def main():
         line["cic"] = cic
     if variants is not None:
         line["level_step_kernels"] = variants
+    if unigrid is not None:
+        line["unigrid"] = unigrid
     if batched is not None:
         line["batched"] = batched
     if serving is not None:
