@@ -37,6 +37,17 @@ def main():
             else:
                 g.sync()
             g.close()
+    # the fused shared-memory level step (blocks, 27-neighbour ring, reflux slots)
+    for ns, precision in ((1, 8), (2, 8), (2, 4), (4, 4)):
+        prob = cases[0]
+        g = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, nsubgrid=ns, tile=128,
+                     schedule=1)
+        g.advance(2, sync=True)
+        if precision == 8:
+            o = oracle.Mesh(*prob.mesh_args(), **prob.params())
+            o.advance(2)
+            compare_all(g, o, 1e-11)
+        g.close()
     b = amr.Mesh.batch(cases[:3])
     b.advance(2, sync=True)
     b.close()
