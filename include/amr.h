@@ -296,6 +296,26 @@ amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_t cap);
  */
 amr_status amr_write(amr_handle h, int level, const double *U, int64_t n);
 
+/*
+ * amr_load_state_async / amr_store_state_async -- the state of every real oct
+ * of the selected member, all levels in mesh order (level by level, each as
+ * amr_read orders it), as one host array [5][8 n], n = the member's octs.
+ * Both return at once and overlap the level steps: two copy streams of the
+ * handle (uploads, downloads) move the host data to and from device staging
+ * buffers while the handle's stream steps, and the handle's stream moves
+ * staging <-> U.  In
+ * stream order, a load takes effect after the work queued before it and
+ * before the work queued after it; a store captures the state the work
+ * queued before it leaves.  So "load, advance, store" per step pipelines the
+ * copies of neighbouring steps with the compute.  Host buffers must be
+ * pinned to overlap (pageable memory works but blocks) and stay untouched
+ * until amr_sync returns: a store's host array is complete only then.
+ * Errors: AMR_EINVAL (NULL, n != the member's octs, cap too small),
+ * AMR_ENOMEM (staging), AMR_ECUDA.
+ */
+amr_status amr_load_state_async(amr_handle h, const double *U, int64_t n);
+amr_status amr_store_state_async(amr_handle h, double *U, int64_t cap);
+
 /* ---- index introspection (parity tests; not on the hot path) -------------- */
 
 /* hash_get of Sec. 2.1 for n host keys: idx_out[t] = mesh index of the oct
@@ -435,7 +455,8 @@ amr_status amr_server_get_stats(amr_server_t s, amr_server_stats *st);
 /* Finish every submitted request, stop the scheduler, free everything. */
 amr_status amr_server_destroy(amr_server_t s);
 
-/* Wait for the handle's stream and report any pending device-side error. */
+/* Wait for the handle's stream and its state-copy streams, and report any
+ * pending device-side error. */
 amr_status amr_sync(amr_handle h);
 
 /* Text of the last error on the calling thread ("" if none). */

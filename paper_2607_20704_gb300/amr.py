@@ -99,7 +99,8 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
            "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag",
-           "amr_poisson", "amr_read_phi", "amr_server_create", "amr_server_submit",
+           "amr_poisson", "amr_read_phi", "amr_load_state_async", "amr_store_state_async",
+           "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
            "amr_server_destroy"]
 
@@ -178,6 +179,8 @@ def load(path: str | None = None):
             "amr_server_release": (I, [P, I64]),
             "amr_server_get_stats": (I, [P, C.POINTER(amr_server_stats)]),
             "amr_server_destroy": (I, [P]),
+            "amr_load_state_async": (I, [P, P, I64]),
+            "amr_store_state_async": (I, [P, P, I64]),
             "amr_part_create": (I, [C.POINTER(amr_part_params), I64, P, P, P, P, C.POINTER(P)]),
             "amr_part_write": (I, [P, P, P, P, P]),
             "amr_part_sort": (I, [P]),
@@ -428,6 +431,7 @@ class Mesh:
 
     def sync(self):
         _check(load().amr_sync(self._h), "amr_sync")
+        self._keep = []
 
     # -- state -----------------------------------------------------------------------
     def num_octs(self, level: int) -> int:
@@ -449,6 +453,32 @@ class Mesh:
         R = np.zeros((NV, 8 * max(n, 1)), np.float64)
         _check(load().amr_read_reflux(self._h, int(level), _ptr(R), max(n, 1)), "amr_read_reflux")
         return R[:, :8 * n]
+
+    def load_state_async(self, U):
+        """Queue the whole state (all levels, mesh order, [5][8 n] doubles)
+        as the input of the work queued next; returns at once.  U must stay
+        untouched until sync() (pinned memory overlaps the copy)."""
+        U = np.asarray(U)
+        if U.dtype != np.float64 or not U.flags.c_contiguous or U.ndim != 2 or U.shape[0] != NV:
+            raise ValueError("U must be a C-contiguous float64 array of shape (5, 8 n)")
+        self._keep = getattr(self, "_keep", [])
+        self._keep.append(U)
+        _check(load().amr_load_state_async(self._h, _ptr(U), U.shape[1] // 8), "amr_load_state_async")
+
+    def store_state_async(self, out):
+        """Queue a copy of the whole state after the work queued so far into
+        `out` ((5, 8 n) float64); complete after sync()."""
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.ndim != 2 or out.shape[0] != NV:
+            raise ValueError("out must be a C-contiguous float64 array of shape (5, 8 n)")
+        self._keep = getattr(self, "_keep", [])
+        self._keep.append(out)
+        _check(load().amr_store_state_async(self._h, _ptr(out), out.shape[1] // 8),
+               "amr_store_state_async")
+        return out
+
+    def state_octs(self) -> int:
+        """Octs of the selected member, all levels."""
+        return int(sum(self.num_octs(l) for l in self.levels()))
 
     def write(self, level: int, U):
         U = np.ascontiguousarray(U, dtype=np.float64)

@@ -188,6 +188,14 @@ struct amr_mesh {
   int32_t *blk = nullptr;
   std::vector<int32_t> blkid_h;
   std::vector<float> tune_ms;  // the autotuner's best step time per candidate
+  // asynchronous whole-state copies: copy streams (uploads, downloads; each
+  // direction its own, so that one never queues behind the other), input and
+  // output staging buffers (doubles, [5][8 n] of the selected member) and
+  // their events
+  cudaStream_t cs = nullptr, cs_out = nullptr;
+  double *st_in = nullptr, *st_out = nullptr;
+  int64_t st_n = 0;
+  cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
   std::vector<std::pair<const void *, int>> occ;  // (kernel, blocks per SM) at tile_size
 
   // state and scratch
@@ -803,7 +811,13 @@ extern "C" void amr_params_default(amr_params *p) {
 
 static void destroy_all(amr_mesh *h) {
   if (!h) return;
+  if (h->cs) cudaStreamSynchronize(h->cs);
+  if (h->cs_out) cudaStreamSynchronize(h->cs_out);
   if (h->s) cudaStreamSynchronize(h->s);
+  for (cudaEvent_t e : {h->ev_in_ready, h->ev_in_free, h->ev_out_ready, h->ev_out_free})
+    if (e) cudaEventDestroy(e);
+  if (h->cs) cudaStreamDestroy(h->cs);
+  if (h->cs_out) cudaStreamDestroy(h->cs_out);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (auto &t : h->pending) {
     cudaEventDestroy(t.e0);
@@ -1516,7 +1530,90 @@ extern "C" amr_status amr_reindex(amr_handle h) {
 
 extern "C" amr_status amr_sync(amr_handle h) {
   if (!h) return fail(AMR_EINVAL, "amr_sync: NULL handle");
+  if (h->cs) CUDA_TRY(cudaStreamSynchronize(h->cs));
+  if (h->cs_out) CUDA_TRY(cudaStreamSynchronize(h->cs_out));
   return check_device(h, "amr_sync");
+}
+
+// ---------------------------------------------------------------------------
+// whole-state copies that overlap the level steps: a copy stream moves host
+// data to and from staging buffers while the compute stream steps; the
+// compute stream moves staging <-> U (device to device, or a conversion for
+// FP32 states).  Events order the reuse of each staging buffer.
+// ---------------------------------------------------------------------------
+static amr_status state_staging(amr_mesh *h, int64_t n) {
+  if (!h->cs) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->cs_out, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&h->ev_in_ready, &h->ev_in_free, &h->ev_out_ready, &h->ev_out_free})
+      CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  if (h->st_n != n) {
+    CUDA_TRY(cudaStreamSynchronize(h->cs));
+    CUDA_TRY(cudaStreamSynchronize(h->cs_out));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+    dev_free(h, h->st_in);
+    dev_free(h, h->st_out);
+    h->st_in = h->st_out = nullptr;
+    AMR_TRY(alloc_n(h, &h->st_in, 40 * (n > 0 ? n : 1)));
+    AMR_TRY(alloc_n(h, &h->st_out, 40 * (n > 0 ? n : 1)));
+    h->st_n = n;
+  }
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_load_state_async(amr_handle h, const double *U, int64_t n) {
+  if (!h || !U) return fail(AMR_EINVAL, "amr_load_state_async: NULL argument");
+  const Member &m = h->mem[h->sel];
+  const int64_t octs = m.lo[kMaxLev + 1];
+  if (n != octs)
+    return fail(AMR_EINVAL, "amr_load_state_async: the member holds %lld octs, got %lld", (long long)octs,
+                (long long)n);
+  if (n == 0) return AMR_OK;
+  AMR_TRY(state_staging(h, n));
+  const int64_t count = 8 * n, first = 8 * m.oct_base;
+  // copy stream: wait until the previous input has been consumed, upload
+  CUDA_TRY(cudaStreamWaitEvent(h->cs, h->ev_in_free, 0));
+  CUDA_TRY(cudaMemcpyAsync(h->st_in, U, sizeof(double) * 5 * count, cudaMemcpyHostToDevice, h->cs));
+  CUDA_TRY(cudaEventRecord(h->ev_in_ready, h->cs));
+  // compute stream: after the work already queued, take the input into U
+  CUDA_TRY(cudaStreamWaitEvent(h->s, h->ev_in_ready, 0));
+  if (h->p.precision == 8) {
+    for (int v = 0; v < 5; ++v)
+      CUDA_TRY(cudaMemcpyAsync(static_cast<double *>(h->U) + v * h->S + first, h->st_in + v * count,
+                               sizeof(double) * count, cudaMemcpyDeviceToDevice, h->s));
+  } else {
+    launch(h, K_CONVERT, k_from_double<float>, dim3(nblocks(5 * count)), dim3(256), (const double *)h->st_in,
+           count, static_cast<float *>(h->U) + first, h->S);
+  }
+  CUDA_TRY(cudaEventRecord(h->ev_in_free, h->s));
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_store_state_async(amr_handle h, double *U, int64_t cap) {
+  if (!h || !U) return fail(AMR_EINVAL, "amr_store_state_async: NULL argument");
+  const Member &m = h->mem[h->sel];
+  const int64_t n = m.lo[kMaxLev + 1];
+  if (cap < n) return fail(AMR_EINVAL, "amr_store_state_async: cap %lld < %lld octs", (long long)cap, (long long)n);
+  if (n == 0) return AMR_OK;
+  AMR_TRY(state_staging(h, n));
+  const int64_t count = 8 * n, first = 8 * m.oct_base;
+  // compute stream: once the previous output has left, snapshot U
+  CUDA_TRY(cudaStreamWaitEvent(h->s, h->ev_out_free, 0));
+  if (h->p.precision == 8) {
+    for (int v = 0; v < 5; ++v)
+      CUDA_TRY(cudaMemcpyAsync(h->st_out + v * count, static_cast<const double *>(h->U) + v * h->S + first,
+                               sizeof(double) * count, cudaMemcpyDeviceToDevice, h->s));
+  } else {
+    launch(h, K_CONVERT, k_to_double<float>, dim3(nblocks(5 * count)), dim3(256),
+           static_cast<const float *>(h->U) + first, h->S, count, h->st_out);
+  }
+  CUDA_TRY(cudaEventRecord(h->ev_out_ready, h->s));
+  // download stream: the snapshot to the host
+  CUDA_TRY(cudaStreamWaitEvent(h->cs_out, h->ev_out_ready, 0));
+  CUDA_TRY(cudaMemcpyAsync(U, h->st_out, sizeof(double) * 5 * count, cudaMemcpyDeviceToHost, h->cs_out));
+  CUDA_TRY(cudaEventRecord(h->ev_out_free, h->cs_out));
+  return AMR_OK;
 }
 
 extern "C" amr_status amr_fill_ghosts(amr_handle h, int level) {
@@ -1656,6 +1753,8 @@ static amr_mesh *regrid_shell(amr_mesh *h) {
 
 extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *removed) {
   if (!h) return fail(AMR_EINVAL, "amr_regrid: NULL handle");
+  if (h->cs) CUDA_TRY(cudaStreamSynchronize(h->cs));  // state copies in flight finish first
+  if (h->cs_out) CUDA_TRY(cudaStreamSynchronize(h->cs_out));
   if (created) *created = 0;
   if (removed) *removed = 0;
   const int64_t N = h->N;
