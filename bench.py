@@ -43,7 +43,8 @@ def parse():
                     help="state precision of the headline value (the other is reported beside it)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=6,
+                    help="coarse steps of the oracle in the CPU baseline (about 2 s each on one core)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-mesh batched ensemble measurement")
     ap.add_argument("--batched-members", type=int, default=512)
