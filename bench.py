@@ -876,7 +876,7 @@ def main():
         if not args.no_other_precision:
             other = run_precision(prob, prec_other, args.steps, args.warmup, torch, device, flush)
             other["steps"] = args.steps
-        e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 5), torch)
+        e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 2), torch)
         poisson = None if args.no_poisson else run_poisson(8, 10, torch, device)
         cic = None if args.no_cic else run_cic(args.cic_grid, 5, 3, torch, peak_gbs, peak_src)
         variants = None if args.no_variants else run_variants(prob, 7, torch, device, flush)
