@@ -85,6 +85,20 @@ __device__ __forceinline__ uint64_t fnv1a64(uint64_t key) {
   return h;
 }
 
+// Lanes of the warp with the same digit as this lane (nbits <= 8; radix-sort digits), from one
+// ballot per digit bit: cheaper on this GPU than __match_any_sync.  Invalid
+// lanes (past the end) match only each other.
+__device__ __forceinline__ unsigned digit_peers(unsigned dig, int nbits, bool valid) {
+  const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+  unsigned peers = valid ? vm : ~vm;
+  for (int b = 0; b < nbits; ++b) {
+    const bool bit = (dig >> b) & 1u;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, bit);
+    peers &= bit ? m : ~m;
+  }
+  return peers;
+}
+
 // 3-D Hilbert index with `bits` bits per axis, x the most significant axis
 // (Skilling's transposed-coordinate construction, AIP Conf. Proc. 707, 2004).
 __device__ __forceinline__ uint64_t hilbert_index(uint32_t x, uint32_t y, uint32_t z, int bits) {

@@ -262,12 +262,18 @@ void sort_impl(amr_particles *h) {
   for (int shift = 0; shift < total; shift += width) {
     const int nbits = total - shift < width ? total - shift : width;
     const int64_t len = (int64_t(1) << nbits) * nt;
+    const int ndig = 1 << nbits;
+    const int64_t nch = (nt + kScanChunk - 1) / kScanChunk;
+    uint32_t *pref = h->table + len, *base = pref + len, *dbase = base + int64_t(ndig) * nch;
     launch(h, P_SORT_HIST, k_psort_hist, dim3(unsigned(nt)), dim3(kSortThreads), (const uint32_t *)ka, np,
            shift, nbits, h->table, nt);
-    launch(h, P_SORT_HIST, k_table_end, dim3(1), dim3(1), h->table, len);
-    scan_exclusive(h, P_SORT_SCAN, h->table, len + 1, h->scan_tmp);
+    launch(h, P_SORT_SCAN, k_psort_chunks, dim3(unsigned(nch)), dim3(kSortThreads), (const uint32_t *)h->table,
+           nt, ndig, pref, base);
+    launch(h, P_SORT_SCAN, k_psort_digit_scan, dim3(unsigned(ndig)), dim3(kSortThreads), base, nch, ndig, dbase);
+    launch(h, P_SORT_SCAN, k_psort_digit_base, dim3(1), dim3(kSortThreads), dbase, ndig);
     launch(h, P_SORT_SCATTER, k_psort_scatter, dim3(unsigned(nt)), dim3(kSortThreads), (const uint32_t *)ka,
-           (const uint32_t *)va, kb, vb, np, shift, nbits, (const uint32_t *)h->table, nt);
+           (const uint32_t *)va, kb, vb, np, shift, nbits, (const uint32_t *)h->table, (const uint32_t *)pref,
+           (const uint32_t *)base, (const uint32_t *)dbase);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
@@ -334,7 +340,9 @@ extern "C" amr_status amr_part_create(const amr_part_params *p, int64_t np, cons
   h->np = np;
   const size_t pb = size_t(np) * h->esize, ib = size_t(np) * 4;
   const int64_t nt = (np + kSortTile - 1) / kSortTile;
-  const int64_t tlen = int64_t(kSortBins) * nt + 1;
+  // tile counts, their chunk prefixes, the chunk bases and the digit bases
+  const int64_t tlen =
+      2 * int64_t(kSortBins) * nt + int64_t(kSortBins) * ((nt + kScanChunk - 1) / kScanChunk) + kSortBins + 1;
   cudaError_t e = cudaSuccess;
   for (void **q : {&h->x, &h->y, &h->z, &h->m, &h->x2, &h->y2, &h->z2, &h->m2})
     if (e == cudaSuccess) e = dalloc(h, q, pb);

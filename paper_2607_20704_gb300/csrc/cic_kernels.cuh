@@ -225,7 +225,7 @@ __global__ void k_part_keys(int64_t np, CicGrid<T> g, const T *__restrict__ x, c
   val[t] = uint32_t(t);
 }
 
-// per-tile digit counts, table[d * ntiles + tile]; digits of up to 8 bits
+// per-tile digit counts, tile-major: table[tile * ndig + d]; digits of up to 8 bits
 constexpr int kSortBins = 256;
 
 __global__ void __launch_bounds__(kSortThreads) k_psort_hist(const uint32_t *__restrict__ keys,
@@ -234,7 +234,6 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_hist(const uint32_t *__r
                                                              int64_t ntiles) {
   __shared__ uint32_t hist[kSortBins];
   const int ndig = 1 << nbits;
-  const int lane = threadIdx.x & 31;
   for (int d = threadIdx.x; d < ndig; d += blockDim.x) hist[d] = 0;
   __syncthreads();
   const int64_t base = blockIdx.x * int64_t(kSortTile);
@@ -245,23 +244,85 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_hist(const uint32_t *__r
     dk[r] = t < np ? __ldcs(keys + t) : 0xFFFFFFFFu;
   }
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const unsigned dig = dk[r] != 0xFFFFFFFFu ? (dk[r] >> shift) & unsigned(ndig - 1) : 0xFFFFFFFFu;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
-    if (dig != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&hist[dig], unsigned(__popc(peers)));
-  }
+  for (int r = 0; r < kSortRounds; ++r)
+    if (dk[r] != 0xFFFFFFFFu) atomicAdd(&hist[(dk[r] >> shift) & unsigned(ndig - 1)], 1u);
   __syncthreads();
-  for (int d = threadIdx.x; d < ndig; d += blockDim.x) table[int64_t(d) * ntiles + blockIdx.x] = hist[d];
+  for (int d = threadIdx.x; d < ndig; d += blockDim.x) table[int64_t(blockIdx.x) * ndig + d] = hist[d];
+}
+
+// Offsets of the scatter from the tile-major counts cnt[tile][d]: per digit,
+// an exclusive prefix over tiles inside chunks of kScanChunk tiles (pref),
+// then the chunks' exclusive prefix per digit (base[chunk][d]), then the
+// digits' bases (dbase[d]); a tile's run of digit d starts at
+// pref[tile][d] + base[tile / kScanChunk][d] + dbase[d].  The counts, the
+// prefixes and the scatter's reads all run along the digits (coalesced).
+constexpr int kScanChunk = 32;
+
+__global__ void k_psort_chunks(const uint32_t *__restrict__ cnt, int64_t ntiles, int ndig,
+                               uint32_t *__restrict__ pref, uint32_t *__restrict__ base) {
+  const int d = threadIdx.x;
+  if (d >= ndig) return;
+  const int64_t t0 = blockIdx.x * int64_t(kScanChunk);
+  const int64_t t1 = t0 + kScanChunk < ntiles ? t0 + kScanChunk : ntiles;
+  uint32_t run = 0;
+  for (int64_t t = t0; t < t1; ++t) {
+    const uint32_t c = cnt[t * ndig + d];
+    pref[t * ndig + d] = run;
+    run += c;
+  }
+  base[int64_t(blockIdx.x) * ndig + d] = run;  // the chunk's total, for now
+}
+
+// one block per digit: exclusive scan of the digit's chunk totals (in place)
+// and the digit's total
+__global__ void __launch_bounds__(kSortThreads) k_psort_digit_scan(uint32_t *__restrict__ base, int64_t nchunks,
+                                                                  int ndig, uint32_t *__restrict__ dtot) {
+  __shared__ uint32_t part[kSortThreads];
+  const int d = blockIdx.x;
+  const int64_t per = (nchunks + kSortThreads - 1) / kSortThreads;
+  const int64_t c0 = threadIdx.x * per, c1 = c0 + per < nchunks ? c0 + per : nchunks;
+  uint32_t sum = 0;
+  for (int64_t c = c0; c < c1; ++c) sum += base[c * ndig + d];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < kSortThreads; off <<= 1) {
+    const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - sum;
+  for (int64_t c = c0; c < c1; ++c) {
+    const uint32_t x = base[c * ndig + d];
+    base[c * ndig + d] = run;
+    run += x;
+  }
+  if (threadIdx.x == kSortThreads - 1) dtot[d] = part[kSortThreads - 1];
+}
+
+// one block: the digits' bases, the exclusive scan of their totals (in place)
+__global__ void __launch_bounds__(kSortThreads) k_psort_digit_base(uint32_t *__restrict__ dtot, int ndig) {
+  __shared__ uint32_t part[kSortThreads];
+  const int d = threadIdx.x;
+  const uint32_t x = d < ndig ? dtot[d] : 0u;
+  part[d] = x;
+  __syncthreads();
+  for (int off = 1; off < kSortThreads; off <<= 1) {
+    const uint32_t v = d >= off ? part[d - off] : 0u;
+    __syncthreads();
+    part[d] += v;
+    __syncthreads();
+  }
+  if (d < ndig) dtot[d] = part[d] - x;
 }
 
 // stable scatter of one tile: ranks in item order (rounds, then warps, then
 // lanes), the tile staged in shared memory in digit order, then written out
 // so that consecutive threads write consecutive places of a digit's run.
-// offs = exclusive scan of the table, with offs[ndig * ntiles] = np.
 __global__ void __launch_bounds__(kSortThreads) k_psort_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t np, int shift, int nbits, const uint32_t *__restrict__ offs,
-    int64_t ntiles) {
+    uint32_t *__restrict__ vout, int64_t np, int shift, int nbits, const uint32_t *__restrict__ cnt,
+    const uint32_t *__restrict__ pref, const uint32_t *__restrict__ cbase, const uint32_t *__restrict__ dbase) {
   __shared__ uint32_t skey[kSortTile], sval[kSortTile];
   __shared__ uint32_t wcnt[kSortThreads / 32][256], wpre[kSortThreads / 32][256];
   __shared__ uint32_t lstart[256], run[256], part[kSortThreads];
@@ -269,15 +330,17 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_scatter(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = blockIdx.x * int64_t(kSortTile);
   const int nt = int(np - base < kSortTile ? np - base : kSortTile);
-  // digit counts of this tile from the scanned table, then their exclusive
-  // scan over the digits (one digit per thread; ndig <= 256)
+  // digit counts and global offsets of this tile, then the counts'
+  // exclusive scan over the digits (one digit per thread; ndig <= 256)
+  __shared__ uint32_t goff[256];
   const int d0 = threadIdx.x;
-  uint32_t cnt = 0;
+  uint32_t cnt_d = 0;
   if (d0 < ndig) {
-    const int64_t e = int64_t(d0) * ntiles + blockIdx.x;
-    cnt = offs[e + 1] - offs[e];
+    const int64_t e = int64_t(blockIdx.x) * ndig + d0;
+    cnt_d = cnt[e];
+    goff[d0] = pref[e] + cbase[int64_t(blockIdx.x / kScanChunk) * ndig + d0] + dbase[d0];
   }
-  part[threadIdx.x] = cnt;
+  part[threadIdx.x] = cnt_d;
   for (int w = 0; w < kSortThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
   __syncthreads();
   for (int off = 1; off < kSortThreads; off <<= 1) {
@@ -286,8 +349,8 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_scatter(
     part[threadIdx.x] += v;
     __syncthreads();
   }
-  lstart[threadIdx.x] = part[threadIdx.x] - cnt;
-  run[threadIdx.x] = part[threadIdx.x] - cnt;
+  lstart[threadIdx.x] = part[threadIdx.x] - cnt_d;
+  run[threadIdx.x] = part[threadIdx.x] - cnt_d;
   uint32_t kr[kSortRounds], vr[kSortRounds];  // all loads of the tile in flight at once
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
@@ -303,7 +366,7 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_scatter(
     const uint32_t k = kr[r];
     const uint32_t v = vr[r];
     const unsigned dig = valid ? (k >> shift) & unsigned(ndig - 1) : 0xFFFFFFFFu;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
+    const unsigned peers = digit_peers(dig, nbits, valid);
     const unsigned rank = __popc(peers & ((1u << lane) - 1u));
     if (valid && rank == 0) wcnt[warp][dig] = __popc(peers);
     __syncthreads();
@@ -330,7 +393,7 @@ __global__ void __launch_bounds__(kSortThreads) k_psort_scatter(
   for (int q = threadIdx.x; q < nt; q += kSortThreads) {
     const uint32_t k = skey[q];
     const unsigned dig = (k >> shift) & unsigned(ndig - 1);
-    const int64_t dst = int64_t(offs[int64_t(dig) * ntiles + blockIdx.x]) + (q - int64_t(lstart[dig]));
+    const int64_t dst = int64_t(goff[dig]) + (q - int64_t(lstart[dig]));
     kout[dst] = k;
     vout[dst] = sval[q];
   }
@@ -520,8 +583,6 @@ __global__ void k_seg_gather(int n, int64_t cap, const int32_t *__restrict__ cel
 // ---------------------------------------------------------------------------
 // host <-> device helpers of the particle handle
 // ---------------------------------------------------------------------------
-// the entry past the digit table: 0, so that its exclusive scan ends with np
-__global__ void k_table_end(uint32_t *table, int64_t at) { table[at] = 0u; }
 
 template <class T>
 __global__ void k_from_double(int64_t n, const double *__restrict__ a, T *__restrict__ b) {

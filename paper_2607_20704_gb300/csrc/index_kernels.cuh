@@ -42,7 +42,7 @@ __global__ void k_make_sort_keys(const uint8_t *__restrict__ lvl, const uint32_t
 // ---------------------------------------------------------------------------
 // stable LSD radix sort of (u64 key, u32 value) pairs, one item per thread,
 // 256-item tiles: tile histograms -> exclusive scan (digit-major) -> scatter
-// with warp-level ranks (__match_any_sync) and a warp-ordered prefix.
+// with warp-level ranks (one ballot per digit bit) and a warp-ordered prefix.
 // ---------------------------------------------------------------------------
 constexpr int kRadixTile = 256;
 constexpr int kTile = kRadixTile;
@@ -73,7 +73,7 @@ __global__ void k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t
   const uint64_t k = valid ? kin[t] : 0;
   const uint32_t v = valid ? vin[t] : 0;
   const unsigned dig = valid ? unsigned((k >> shift) & uint64_t(ndig - 1)) : 0xFFFFFFFFu;
-  const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
+  const unsigned peers = digit_peers(dig, nbits, valid);
   const unsigned rank = __popc(peers & ((1u << lane) - 1u));
   if (valid && rank == 0) wcnt[warp][dig] = __popc(peers);
   __syncthreads();
