@@ -280,15 +280,18 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
 
 def run_variants(prob, steps, torch, device, flush):
     """The level-step kernels side by side on the workload: the per-cell
-    passes (autotuned tile and schedule) and the fused shared-memory kernel
-    with nsubgrid 1, 2 (and 4 in FP32), each schedule; median coarse-step
-    time of `steps` graph-replayed steps, L2 flushed between them."""
+    passes (autotuned tile and schedule) and the fused shared-memory kernels,
+    cube staging (rock; nsubgrid 1, 2, and 4 in FP32) and planar sweep (paper
+    kernel; nsubgrid 1, 2, 4), each schedule; median coarse-step time of
+    `steps` graph-replayed steps, L2 flushed between them."""
     from paper_2607_20704_gb300 import amr
     out = {}
     for prec in (8, 4):
         rows = []
-        shapes = [dict(nsubgrid=0)] + [dict(nsubgrid=ns, tile=128, schedule=sc)
-                                       for ns in ((1, 2) if prec == 8 else (1, 2, 4)) for sc in (0, 1)]
+        shapes = [dict(nsubgrid=0)]
+        for planar in (0, 1):
+            for ns in ((1, 2) if (prec == 8 and planar == 0) else (1, 2, 4)):
+                shapes += [dict(nsubgrid=ns, planar=planar, tile=128, schedule=sc) for sc in (0, 1)]
         for shp in shapes:
             m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=prec, stream=bench_stream(), **shp)
             upd = work_per_step(m.info(), prob.levelmin)
@@ -307,7 +310,8 @@ def run_variants(prob, steps, torch, device, flush):
                 ts.append(e0.elapsed_time(e1))
             inf = m.info()
             ms = float(np.median(ts))
-            rows.append({"nsubgrid": inf["nsubgrid"], "tile": inf["tile"], "schedule": inf["schedule"],
+            rows.append({"nsubgrid": inf["nsubgrid"], "planar": inf["planar"], "tile": inf["tile"],
+                         "schedule": inf["schedule"],
                          "ms_per_step": round(ms, 4), "cell_updates_per_s": upd / (ms * 1e-3)})
             m.close()
         out["fp64" if prec == 8 else "fp32"] = rows
@@ -940,7 +944,7 @@ def main():
         "kernels": table,
         "gpu_launches": main_res["launches"],
         "autotuned": {"tile": main_res["info"].get("tile"), "schedule": main_res["info"].get("schedule"),
-                      "nsubgrid": main_res["info"].get("nsubgrid")},
+                      "nsubgrid": main_res["info"].get("nsubgrid"), "planar": main_res["info"].get("planar")},
         "clocks": clocks,
         "e2e": e2e,
     }
@@ -950,7 +954,7 @@ def main():
             "ms_per_step": other_s * 1e3 / args.steps,
             "roofline": rl_o, "kernels": table_o, "gpu_launches": other["launches"],
             "autotuned": {"tile": other["info"].get("tile"), "schedule": other["info"].get("schedule"),
-                          "nsubgrid": other["info"].get("nsubgrid")},
+                          "nsubgrid": other["info"].get("nsubgrid"), "planar": other["info"].get("planar")},
             "step_roofline_frac": round(other_value / world
                                         * 2 * 5 * WORD[prec_other] / 1e9 / peak_gbs, 4)}
     if adaptive is not None:

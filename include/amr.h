@@ -92,21 +92,27 @@ typedef struct {
                                (default) */
   int nsubgrid;             /* level-step kernel (Sec. 3): 0: per-cell passes
                                (primitives, predictor, faces, update, each
-                               computed once); 1, 2 or 4 (4: precision 4
-                               only): the paper's fused shared-memory kernel
-                               ("rock") on blocks of nsubgrid^3 octs staged
-                               with one ring of octs (6^3, 8^3 or 12^3
-                               cells); -1 (default): picked by the autotuner
-                               among these when tile is 0, else the per-cell
-                               passes.  All give the same results bit for
-                               bit. */
+                               computed once); 1, 2 or 4: the paper's fused
+                               shared-memory kernels on blocks of nsubgrid^3
+                               octs with one ring of octs (cubes of 6^3, 8^3
+                               or 12^3 cells); -1 (default): picked by the
+                               autotuner among these when tile is 0, else the
+                               per-cell passes.  All give the same results
+                               bit for bit. */
+  int planar;               /* with nsubgrid 1, 2 or 4: 0: stage the whole
+                               cube (the "rock" kernel; nsubgrid 4 needs
+                               precision 4); 1: sweep it along z keeping a
+                               three-plane window (the "paper" kernel);
+                               -1 (default): the autotuner's choice (with a
+                               fixed nsubgrid: rock, except nsubgrid 4 in
+                               FP64, which sweeps) */
 } amr_params;
 
 /* Fills p with the defaults: levelmin = levelmax = 1, gamma = 1.4, cfl = 0.8,
  * smallr = smallc = 1e-10, precision 8, reflux 1, reindex_every_step 1,
- * use_graphs 1, no budget, NULL stream and allocator, tile 0, schedule -1 and
- * nsubgrid -1 (picked by the autotuner), refinement criteria off,
- * regrid_expand 1, regrid_every_step 0. */
+ * use_graphs 1, no budget, NULL stream and allocator, tile 0, schedule -1,
+ * nsubgrid -1 and planar -1 (picked by the autotuner), refinement criteria
+ * off, regrid_expand 1, regrid_every_step 0. */
 void amr_params_default(amr_params *p);
 
 /*
@@ -353,6 +359,7 @@ typedef struct {
   int phases;                 /* level-step phases of one coarse step */
   int tile, schedule;         /* work-tile size and schedule in use */
   int nsubgrid;               /* level-step kernel in use (amr_params.nsubgrid) */
+  int planar;                 /* 1: the fused kernel sweeps planes (amr_params.planar) */
 } amr_info;
 
 /* Counts of the mesh and of the work done so far. */

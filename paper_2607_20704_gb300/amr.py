@@ -40,7 +40,7 @@ class amr_params(C.Structure):
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("tile", C.c_int), ("schedule", C.c_int),
                 ("regrid_expand", C.c_int), ("regrid_every_step", C.c_int),
-                ("nsubgrid", C.c_int)]
+                ("nsubgrid", C.c_int), ("planar", C.c_int)]
 
 
 class amr_info(C.Structure):
@@ -52,7 +52,7 @@ class amr_info(C.Structure):
                 ("work_per_step", C.c_int64),
                 ("precision", C.c_int), ("n_members", C.c_int), ("member", C.c_int),
                 ("phases", C.c_int), ("tile", C.c_int), ("schedule", C.c_int),
-                ("nsubgrid", C.c_int)]
+                ("nsubgrid", C.c_int), ("planar", C.c_int)]
 
 
 class amr_member(C.Structure):
@@ -259,7 +259,7 @@ class Mesh:
                  reindex_every_step=True, use_graphs=True, hbm_budget_bytes=0,
                  hilbert_key=None, allocator="torch", stream=None, members=None, tile=0,
                  schedule=-1, refine_grad_rho=0.0, refine_grad_p=0.0, refine_mass=0.0,
-                 regrid_expand=True, regrid_every_step=False, nsubgrid=-1):
+                 regrid_expand=True, regrid_every_step=False, nsubgrid=-1, planar=-1):
         torch = _torch()
         L = load()
         p = amr_params()
@@ -277,6 +277,7 @@ class Mesh:
         p.regrid_expand = int(bool(regrid_expand))
         p.regrid_every_step = int(bool(regrid_every_step))
         p.nsubgrid = int(nsubgrid)
+        p.planar = int(planar)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         p.stream = C.c_void_p(self.stream.cuda_stream)
         if allocator == "torch":
@@ -523,7 +524,7 @@ class Mesh:
             "hash_capacity": inf.hash_capacity, "precision": inf.precision,
             "work_per_step": inf.work_per_step, "n_members": inf.n_members,
             "member": inf.member, "phases": inf.phases, "tile": inf.tile,
-            "schedule": inf.schedule, "nsubgrid": inf.nsubgrid,
+            "schedule": inf.schedule, "nsubgrid": inf.nsubgrid, "planar": inf.planar,
         }
 
     def set_timing(self, on: bool):

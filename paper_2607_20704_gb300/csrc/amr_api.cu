@@ -83,7 +83,7 @@ enum Kid {
   K_GRADING, K_NEIGHBOURS, K_CLAIM, K_CACHE_FINALIZE, K_NBR_FIX, K_FACES, K_CACHE_SOURCES,
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
-  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_ROCK_COMMIT, K_COUNT
+  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_ROCK_COMMIT, K_SWEEP, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
@@ -91,7 +91,7 @@ static const char *kKernelNames[K_COUNT] = {
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
     "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
-    "rock", "rock_commit"};
+    "rock", "rock_commit", "sweep"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -185,6 +185,7 @@ struct amr_mesh {
   // (0: the per-cell passes), block starts (mesh indices) and, on the host,
   // the block of every oct
   int nsub = 0;
+  bool planar = false;  // the fused kernel sweeps planes (paper kernel), else stages the cube (rock)
   int32_t *blk = nullptr;
   std::vector<int32_t> blkid_h;
   std::vector<float> tune_ms;  // the autotuner's best step time per candidate
@@ -648,20 +649,52 @@ static void run_rock_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
               (const int32_t *)h->blk);
 }
 
+template <class T, int NS>
+static void run_sweep_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
+  if (L.ntile[DOM_BLOCKS] == 0) return;
+  a.tiles = h->tiles + L.tile0[DOM_BLOCKS];
+  a.ntiles = L.ntile[DOM_BLOCKS];
+  constexpr size_t smem = Sweep<NS>::template smem<T>();
+  auto kern = k_sweep<T, NS>;
+  int per_sm = 0;
+  for (auto &o : h->occ)
+    if (o.first == (const void *)kern) per_sm = o.second;
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sweep<NS>::THREADS, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    h->occ.push_back({(const void *)kern, per_sm});
+  }
+  const int grid = h->persistent ? std::min(a.ntiles, per_sm * h->sm_count) : a.ntiles;
+  launch_smem(h, K_SWEEP, kern, dim3(unsigned(grid)), dim3(unsigned(Sweep<NS>::THREADS)), smem, a,
+              (const int32_t *)h->blk);
+}
+
 template <class T>
 static void run_segments(amr_mesh *h, const SegList &L, bool device_dt, double dt) {
   if (L.nseg == 0) return;
   StepArgs<T> a = step_args<T>(h, device_dt, dt);
   run_list(h, K_PROLONG, k_prolong<T>, a, L, DOM_GHOST5);
   if (h->nsub > 0) {
-    // the paper's fused kernel: one block of nsub^3 octs per CTA, then the new
-    // leaf states from the scratch into U
-    if (h->nsub == 1)
+    // the paper's fused kernels (cube staging or planar sweep): one block of
+    // nsub^3 octs per CTA, then the new leaf states from the scratch into U
+    if (h->planar) {
+      if (h->nsub == 1)
+        run_sweep_ns<T, 1>(h, a, L);
+      else if (h->nsub == 2)
+        run_sweep_ns<T, 2>(h, a, L);
+      else
+        run_sweep_ns<T, 4>(h, a, L);
+    } else if (h->nsub == 1) {
       run_rock_ns<T, 1>(h, a, L);
-    else if (h->nsub == 2)
+    } else if (h->nsub == 2) {
       run_rock_ns<T, 2>(h, a, L);
-    else if constexpr (sizeof(T) == 4)
+    } else if constexpr (sizeof(T) == 4) {
       run_rock_ns<T, 4>(h, a, L);
+    }
     run_list(h, K_ROCK_COMMIT, k_rock_commit<T>, a, L, DOM_REAL);
   } else if constexpr (sizeof(T) == 4) {
     // FP32: primitives recomputed inside the predictor; each leaf cell solves
@@ -807,6 +840,7 @@ extern "C" void amr_params_default(amr_params *p) {
   p->regrid_expand = 1;
   p->regrid_every_step = 0;
   p->nsubgrid = -1;
+  p->planar = -1;
 }
 
 static void destroy_all(amr_mesh *h) {
@@ -1236,13 +1270,22 @@ extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
     delete h;
     return fail(AMR_EINVAL, "amr_create: tile must be 0, 64, 128, 256 or 512");
   }
-  if (!(p->nsubgrid >= -1 && p->nsubgrid <= 2) && !(p->nsubgrid == 4 && p->precision == 4)) {
+  if (!(p->nsubgrid >= -1 && p->nsubgrid <= 2) && p->nsubgrid != 4) {
     delete h;
-    return fail(AMR_EINVAL, "amr_create: nsubgrid must be -1, 0, 1, 2, or 4 with precision 4");
+    return fail(AMR_EINVAL, "amr_create: nsubgrid must be -1, 0, 1, 2 or 4");
+  }
+  if (p->planar < -1 || p->planar > 1) {
+    delete h;
+    return fail(AMR_EINVAL, "amr_create: planar must be -1, 0 or 1");
+  }
+  if (p->nsubgrid == 4 && p->precision == 8 && p->planar == 0) {
+    delete h;
+    return fail(AMR_EINVAL, "amr_create: nsubgrid 4 stages its cube in FP32 only (planar 1 sweeps it in FP64)");
   }
   h->tile_size = p->tile ? p->tile : 256;
   h->persistent = p->schedule != 0;
   h->nsub = p->nsubgrid > 0 ? p->nsubgrid : 0;
+  h->planar = h->nsub > 0 && (p->planar == 1 || (p->planar == -1 && h->nsub == 4 && p->precision == 8));
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count < 1) h->sm_count = 1;
@@ -1368,7 +1411,8 @@ static amr_status build_blocks(amr_mesh *h) {
 
 // Rebuild the tile lists for another tile size or fused-kernel block size
 // (segments and scratch do not depend on them).
-static amr_status set_tile(amr_mesh *h, int tile, int nsub) {
+static amr_status set_tile(amr_mesh *h, int tile, int nsub, bool planar = false) {
+  h->planar = planar;
   if (tile == h->tile_size && nsub == h->nsub && h->tiles) return AMR_OK;
   h->tile_size = tile;
   if (nsub != h->nsub) {
@@ -1411,6 +1455,7 @@ static amr_status capture_coarse_step(amr_mesh *h, cudaGraphExec_t *out) {
 // FP32) x schedule.
 struct LaunchShape {
   int tile, sched, nsub;
+  bool planar;
 };
 
 static amr_status autotune(amr_mesh *h) {
@@ -1423,17 +1468,20 @@ static amr_status autotune(amr_mesh *h) {
     nsubs = {h->p.nsubgrid};
   else if (h->p.nsubgrid == 0 || h->p.tile)
     nsubs = {0};
-  else if (h->p.precision == 4)
-    nsubs = {0, 1, 2, 4};
   else
-    nsubs = {0, 1, 2};
+    nsubs = {0, 1, 2, 4};
   std::vector<LaunchShape> cands;
   for (int ns : nsubs)
     for (int t : (ns == 0 ? tiles : std::vector<int>{tiles[0]}))
-      for (int sc : scheds) cands.push_back({t, sc, ns});
+      for (int sc : scheds)
+        for (int pl = 0; pl < (ns == 0 ? 1 : 2); ++pl) {
+          if (h->p.nsubgrid > 0 && h->p.planar >= 0 && pl != h->p.planar) continue;
+          if (ns == 4 && pl == 0 && h->p.precision == 8) continue;  // the FP64 cube exceeds shared memory
+          cands.push_back({t, sc, ns, pl == 1});
+        }
   if (cands.size() == 1) {
     h->persistent = cands[0].sched == 1;
-    return set_tile(h, cands[0].tile, cands[0].nsub);
+    return set_tile(h, cands[0].tile, cands[0].nsub, cands[0].planar);
   }
   const bool graphs = h->p.use_graphs && !h->timing;
   const size_t ub = h->elem() * 5 * size_t(h->S), rb = h->elem() * 5 * size_t(h->NC > 0 ? h->NC : 1);
@@ -1451,7 +1499,7 @@ static amr_status autotune(amr_mesh *h) {
   float best = 1e30f;
   LaunchShape pick = cands[0];
   for (const LaunchShape &cd : cands) {
-    AMR_TRY(set_tile(h, cd.tile, cd.nsub));
+    AMR_TRY(set_tile(h, cd.tile, cd.nsub, cd.planar));
     h->persistent = cd.sched == 1;
     cudaGraphExec_t ge = nullptr;
     if (graphs) AMR_TRY(capture_coarse_step(h, &ge));
@@ -1484,7 +1532,7 @@ static amr_status autotune(amr_mesh *h) {
   CUDA_TRY(cudaMemcpyAsync(h->mrem, sm, mb, cudaMemcpyDeviceToDevice, h->s));
   h->event_pool.push_back(e0);
   h->event_pool.push_back(e1);
-  AMR_TRY(set_tile(h, pick.tile, pick.nsub));
+  AMR_TRY(set_tile(h, pick.tile, pick.nsub, pick.planar));
   h->persistent = pick.sched == 1;
   dev_free(h, su);
   dev_free(h, sr);
@@ -1748,6 +1796,7 @@ static amr_mesh *regrid_shell(amr_mesh *h) {
   nh->persistent = h->persistent;
   nh->tuned = h->tuned;
   nh->nsub = h->nsub;
+  nh->planar = h->planar;
   return nh;
 }
 
@@ -2207,6 +2256,7 @@ extern "C" amr_status amr_get_info(amr_handle h, amr_info *info) {
   info->tile = h->tile_size;
   info->schedule = h->persistent ? 1 : 0;
   info->nsubgrid = h->nsub;
+  info->planar = h->planar ? 1 : 0;
   return AMR_OK;
 }
 

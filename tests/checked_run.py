@@ -37,11 +37,13 @@ def main():
             else:
                 g.sync()
             g.close()
-    # the fused shared-memory level step (blocks, 27-neighbour ring, reflux slots)
-    for ns, precision in ((1, 8), (2, 8), (2, 4), (4, 4)):
+    # the fused shared-memory level steps, cube and planar (blocks, 27-neighbour
+    # ring, reflux slots)
+    for ns, precision, planar in ((1, 8, 0), (2, 8, 0), (2, 4, 0), (4, 4, 0), (1, 8, 1), (2, 8, 1), (4, 8, 1),
+                                  (4, 4, 1)):
         prob = cases[0]
-        g = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, nsubgrid=ns, tile=128,
-                     schedule=1)
+        g = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision, nsubgrid=ns, planar=planar,
+                      tile=128, schedule=1)
         g.advance(2, sync=True)
         if precision == 8:
             o = oracle.Mesh(*prob.mesh_args(), **prob.params())
