@@ -73,6 +73,8 @@ def parse():
                     help="1 persistent grids, 0 one tile per block, -1 autotune")
     ap.add_argument("--nsubgrid", type=int, default=-1,
                     help="level-step kernel: 0 per-cell passes, 1/2/4 fused kernel, -1 autotune")
+    ap.add_argument("--planar", type=int, default=-1,
+                    help="fused kernel: 0 cube staging (rock), 1 planar sweep (paper kernel), -1 default")
     ap.add_argument("--profile-poisson", type=int, default=0,
                     help="profiling mode: one multigrid V-cycle on a periodic 2^L grid, then exit")
     ap.add_argument("--profile-level", type=int, default=0,
@@ -212,7 +214,7 @@ def flush_l2(buf):
 
 
 # -- our arm ----------------------------------------------------------------------
-LAUNCH = {"tile": 0, "schedule": -1, "nsubgrid": -1}  # set from --tile / --schedule / --nsubgrid
+LAUNCH = {"tile": 0, "schedule": -1, "nsubgrid": -1, "planar": -1}  # from --tile / --schedule / --nsubgrid / --planar
 _STREAM = []
 
 
@@ -789,7 +791,7 @@ def main():
     rank, world, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3
-    LAUNCH.update(tile=args.tile, schedule=args.schedule, nsubgrid=args.nsubgrid)
+    LAUNCH.update(tile=args.tile, schedule=args.schedule, nsubgrid=args.nsubgrid, planar=args.planar)
     if args.impl == "reference" and rank != 0:
         return 0  # the reference arm runs on rank 0 alone
     from paper_2607_20704_gb300 import inputs
