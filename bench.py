@@ -266,7 +266,7 @@ def run_precision(prob, precision, steps, warmup, torch, device, flush, kernels=
         # events on the library's stream (eager launches, no graph)
         m2 = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision,
                       tile=mesh_tile, schedule=mesh_sched, nsubgrid=info["nsubgrid"],
-                      stream=bench_stream())
+                      planar=info["planar"], stream=bench_stream())
         for _ in range(warmup):
             m2.advance(1)
         m2.sync()
