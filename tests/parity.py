@@ -2,12 +2,27 @@
 
 Tolerance (FP64 state, one step from identical inputs): per variable v,
 |gpu - oracle| <= rtol * max(|oracle|, s_v), s_v = max |U_v| over the
-level.  rtol = 1e-12 per level step; the W-cycle tests that chain many
-level steps from one initial state allow 1e-11 (round-off is re-amplified
-by the nonlinear limiter/Riemann steps that follow)."""
+level; for the three momentum components s_v is also at least the level's
+max sqrt(2 rho E), the largest momentum its energy allows (E >= |m|^2 / 2
+rho).  Round-off in a momentum update scales with the fluxes, i.e. with
+the energy present: a level at rest whose momenta are pure round-off
+(1e-19 against E ~ 1e2 on the coarse levels of a deep hierarchy) would
+otherwise be held to a relative bound on noise.  rtol = 1e-12 per level
+step; the W-cycle tests that chain many level steps from one initial state
+allow 1e-11 (round-off is re-amplified by the nonlinear limiter/Riemann
+steps that follow)."""
 import numpy as np
 
 from paper_2607_20704_gb300 import inputs
+
+
+def level_scale(U):
+    """s_v per variable of a [5][cells] state (see the module docstring)."""
+    s = np.abs(U).max(axis=1, keepdims=True).astype(np.float64)
+    if U.shape[0] == 5 and U.shape[1]:
+        e = np.sqrt(2.0 * np.maximum(U[0], 0.0) * np.maximum(U[4], 0.0)).max()
+        s[1:4] = np.maximum(s[1:4], e)
+    return s
 
 
 def close(gpu, orc, rtol, what=""):
@@ -16,7 +31,7 @@ def close(gpu, orc, rtol, what=""):
     assert gpu.shape == orc.shape, (what, gpu.shape, orc.shape)
     if orc.size == 0:
         return 0.0
-    s = np.abs(orc).max(axis=1, keepdims=True)
+    s = level_scale(orc)
     scale = np.maximum(np.abs(orc), s)
     scale[scale == 0] = 1.0
     err = np.abs(gpu - orc) / scale
@@ -42,7 +57,7 @@ def compare_all(g, o, rtol, levels=None, reflux=True):
         worst = max(worst, close(Ug, Uo, rtol, f"U level {l}"))
         if reflux:
             Rg, Ro = g.read_reflux(l), o.read_R(l)
-            s = np.maximum(np.abs(Uo).max(axis=1, keepdims=True), 1e-300)
+            s = np.maximum(level_scale(Uo), 1e-300)
             err = float((np.abs(Rg - Ro) / s).max()) if Ro.size else 0.0
             assert err <= rtol, f"R level {l}: {err:.3e}"
     return worst
