@@ -708,6 +708,22 @@ class Particles:
         _check(load().amr_part_read_rho(self._h, _ptr(out), out.shape[0]), "amr_part_read_rho")
         return out.reshape((self.n,) * 3, order="F")
 
+    def rho_device(self):
+        """The grid as a flat torch tensor on the device (cell i + n (j + n k);
+        the handle's precision), viewing the handle's memory without a copy.
+        The caller's current stream is ordered after the handle's work; the
+        view is valid until the next deposit or close()."""
+        torch = _torch()
+
+        class _View:
+            pass
+
+        v = _View()
+        v.__cuda_array_interface__ = {"shape": (self.n ** 3,), "typestr": "<f8" if self.precision == 8 else "<f4",
+                                      "data": (self.device()["rho"], False), "version": 2}
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return torch.as_tensor(v, device="cuda")
+
     def read(self):
         """Positions, masses and identifiers in the handle's current order."""
         x, y, z, m = (np.empty(self.np) for _ in range(4))

@@ -53,6 +53,16 @@ def main():
     b = amr.Mesh.batch(cases[:3])
     b.advance(2, sync=True)
     b.close()
+    # the deepest hierarchy a handle holds (levels 2..15, 14-bit coordinates)
+    deep = inputs.sedov(2, 15, radii={l: 3 * 2.0 ** -l for l in range(3, 16)}, centre=(0.3, 0.7, 0.55))
+    for precision in (8, 4):
+        g = amr.Mesh(*deep.mesh_args(), **deep.params(), precision=precision, tile=128, schedule=0, nsubgrid=0)
+        g.advance(1, sync=True)
+        if precision == 8:
+            o = oracle.Mesh(*deep.mesh_args(), **deep.params())
+            o.advance(1)
+            compare_all(g, o, 1e-11)
+        g.close()
     print("checked build: all cases passed")
 
 

@@ -1,6 +1,6 @@
 """The bounds-checked build runs the parity cases without an index out of
-range (the stand-in for a memory sanitizer, which this pool does not
-offer)."""
+range (it stands in for a memory sanitizer: every index read from an index
+table is tested against its array before it is used)."""
 import os
 import subprocess
 import sys

@@ -231,6 +231,20 @@ def test_info_and_timing():
     p.close()
 
 
+@pytest.mark.parametrize("precision", [8, 4])
+def test_device_view_of_the_grid(precision):
+    from paper_2607_20704_gb300 import amr
+    ps = inputs.particles(16, "cosmo", seed=13)
+    p = amr.Particles(*ps.args(), precision=precision)
+    p.deposit("atomic")
+    view = p.rho_device()
+    assert view.shape == (16 ** 3,) and view.is_cuda
+    assert str(view.dtype) == ("torch.float64" if precision == 8 else "torch.float32")
+    host = p.rho().reshape(-1, order="F")
+    assert np.array_equal(view.double().cpu().numpy(), host)
+    p.close()
+
+
 def _sampled_parity(ps, precision, algo, n_samples=48, seed=0):
     """Full-size check: total mass, and the oracle's density at sampled cells
     computed from just the particles whose stencils reach them."""
@@ -282,3 +296,79 @@ def _full_set():
     if "ps" not in _FULL:
         _FULL["ps"] = inputs.particles(512, "cosmo", seed=2607)
     return _FULL["ps"]
+
+
+def bound_at(n, x, y, z, m, ref, cells, precision):
+    """_bound() at the given cells only (flat indices i + n (j + n k), no
+    repeats), without n^3 arrays: K and M summed over the particles whose
+    (FP32-widened) stencil covers each cell."""
+    order = np.argsort(cells)
+    sc = cells[order]
+    K = np.zeros(cells.shape[0], np.int64)
+    M = np.zeros(cells.shape[0])
+    if precision == 8:
+        lo = [np.floor(a * n - 0.5).astype(np.int64) for a in (x, y, z)]
+        hi = [v + 1 for v in lo]
+    else:
+        d = n * 2.0 ** -23
+        lo = [np.floor(a * n - 0.5 - d).astype(np.int64) for a in (x, y, z)]
+        hi = [np.floor(a * n - 0.5 + d).astype(np.int64) + 1 for a in (x, y, z)]
+    reach = 2 if precision == 8 else 3
+    for ox in range(reach):
+        for oy in range(reach):
+            for oz in range(reach):
+                ok = (lo[0] + ox <= hi[0]) & (lo[1] + oy <= hi[1]) & (lo[2] + oz <= hi[2])
+                idx = ((lo[0] + ox) % n) + n * (((lo[1] + oy) % n) + n * ((lo[2] + oz) % n))
+                pos = np.minimum(np.searchsorted(sc, idx), sc.shape[0] - 1)
+                hit = ok & (sc[pos] == idx)
+                np.add.at(K, order[pos[hit]], 1)
+                np.add.at(M, order[pos[hit]], m[hit] * float(n) ** 3)
+    if precision == 8:
+        return 2 * K * U64 * ref
+    return (6 * n + 12 + K) * U32 * M
+
+
+@pytest.mark.parametrize("precision,algo", [(8, "atomic"), (8, "segment"), (4, "atomic"), (4, "segment")])
+def test_largest_grid(precision, algo):
+    """The largest grid a handle accepts (1024^3 cells: 30-bit source-cell
+    keys, sorted in four radix passes of 8, 8, 8 and 6 bits), with a
+    clustered set of 64^3 lattice particles and their halos: total mass and
+    sampled cells (read on the device; the oracle deposits only the
+    particles that reach them)."""
+    import torch
+    import oracle
+    from paper_2607_20704_gb300 import amr
+    ps = _largest_set()
+    n = ps.n
+    p = amr.Particles(*ps.args(), precision=precision)
+    p.sort()
+    p.deposit(algo)
+    rho = p.rho_device()
+    total = float(rho.double().sum()) / n ** 3
+    tol_mass = 1e-12 if precision == 8 else 1e-5
+    assert abs(total - ps.m.sum()) <= tol_mass * ps.m.sum()
+    rng = np.random.default_rng(1)
+    dense = torch.topk(rho, 32).indices.cpu().numpy().astype(np.int64)
+    cells = np.unique(np.concatenate([rng.integers(0, n ** 3, 32), dense]))
+    got = rho[torch.as_tensor(cells, device="cuda")].double().cpu().numpy()
+    del rho
+    p.close()
+    src = [np.floor(a * n - 0.5).astype(np.int64) % n for a in (ps.x, ps.y, ps.z)]
+    lin = src[0] + n * (src[1] + n * src[2])
+    ci, cj, ck = cells % n, (cells // n) % n, cells // (n * n)
+    want = set()
+    for ox in range(-2, 2):
+        for oy in range(-2, 2):
+            for oz in range(-2, 2):
+                want.update((((ci + ox) % n) + n * (((cj + oy) % n) + n * ((ck + oz) % n))).tolist())
+    sel = np.isin(lin, np.fromiter(want, np.int64))
+    sub = [a[sel] for a in (ps.x, ps.y, ps.z, ps.m)]
+    ref = oracle.cic_deposit(n, *sub).reshape(-1, order="F")[cells]
+    bound = bound_at(n, *sub, ref, cells, precision)
+    assert np.all(np.abs(got - ref) <= bound + 1e-300), (np.abs(got - ref) - bound).max()
+
+
+def _largest_set():
+    if "big" not in _FULL:
+        _FULL["big"] = inputs.particles(1024, "cosmo", seed=31, lattice=64, disp=4.0, halo_particles=512)
+    return _FULL["big"]

@@ -321,3 +321,48 @@ def test_fp32_runs_repeat_bit_for_bit():
         g.close()
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+def _deepest():
+    # levels 2..15 (the deepest a handle holds: 4-bit level, 14-bit
+    # coordinates), 27 octs per level around an off-centre point
+    return inputs.sedov(2, 15, radii={l: 3 * 2.0 ** -l for l in range(3, 16)}, centre=(0.3, 0.7, 0.55))
+
+
+def test_deepest_hierarchy_index_and_level_steps():
+    prob = _deepest()
+    assert prob.levelmax == 15
+    g, o = pair(prob)
+    for l in range(prob.levelmin, prob.levelmax + 1):
+        kg, _ = g.read(l)
+        assert np.array_equal(kg, o.read(l)[0]), f"order at level {l}"
+        nbg, spg = g.read_index(l)
+        assert np.array_equal(nbg, o.read_nbr(l)), f"neighbours at level {l}"
+        assert np.array_equal(spg, o.read_split(l)), f"split flags at level {l}"
+        assert np.array_equal(g.read_cache(l)[0], o.read_cache(l)), f"ghost keys at level {l}"
+    allk = np.concatenate([o.read(l)[0] for l in o.levels()])
+    rng = np.random.default_rng(15)
+    extra = []
+    for _ in range(2000):
+        l = int(rng.integers(1, 16))
+        a, b, c = rng.integers(0, 1 << (l - 1), 3)
+        extra.append((l << 60) | (int(a) << 40) | (int(b) << 20) | int(c))
+    keys = np.concatenate([allk, np.array(extra, np.uint64)])
+    assert np.array_equal(g.lookup(keys), np.array([o.lookup(int(k)) for k in keys.tolist()]))
+    for l in range(prob.levelmin, prob.levelmax + 1):
+        g, o = pair(prob)
+        dt = o.cfl_dt() * 0.5 ** (l - prob.levelmin)
+        g.step_level(l, dt)
+        o.step_level(l, dt)
+        compare_all(g, o, 1e-12)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_deepest_hierarchy_w_cycle(graphs):
+    """One coarse step of the 14-level hierarchy: 16,383 level steps."""
+    prob = _deepest()
+    g, o = pair(prob, gpu_kw=dict(use_graphs=graphs, tile=128, schedule=0, nsubgrid=0))
+    dtg = g.advance(1, sync=True)
+    dto = o.advance(1)
+    assert abs(dtg - dto) <= 1e-12 * dto
+    compare_all(g, o, 1e-11)
