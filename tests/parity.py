@@ -18,8 +18,10 @@ from paper_2607_20704_gb300 import inputs
 
 def level_scale(U):
     """s_v per variable of a [5][cells] state (see the module docstring)."""
+    if U.shape[1] == 0:
+        return np.zeros((U.shape[0], 1))
     s = np.abs(U).max(axis=1, keepdims=True).astype(np.float64)
-    if U.shape[0] == 5 and U.shape[1]:
+    if U.shape[0] == 5:
         e = np.sqrt(2.0 * np.maximum(U[0], 0.0) * np.maximum(U[4], 0.0)).max()
         s[1:4] = np.maximum(s[1:4], e)
     return s
