@@ -1,6 +1,6 @@
 """Multi-process host logic on CPU (gloo, two ranks): the reductions that
-turn per-rank timings into the whole-job rate, and the reference arm's
-rank-0-only rule."""
+turn per-rank timings into the whole-job rate, the reference arm's
+rank-0-only rule, and the reference arm's JSON line."""
 import os
 import socket
 import subprocess
@@ -56,3 +56,27 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--gpus", "2"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    """Rank 0 of the reference arm: one JSON line, the oracle timed on the
+    host, with the keys the driver reads."""
+    import json
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "leaf cell-updates/s"
+    assert d["unit"] == "leaf cell-updates/s" and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] >= 3 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    upd = d["config"]["cell_updates_per_step"]
+    assert abs(d["value"] - upd / (d["ms_per_step"] * 1e-3)) <= 1e-6 * d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "sedov_l7-10_static_nested_balls"
