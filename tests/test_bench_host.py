@@ -108,3 +108,12 @@ def test_measured_peaks_are_read():
     assert src in ("measured", "fallback")
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
         assert src == "measured" and gbs > 1000.0
+
+
+def test_all_core_oracle_baseline_runs_replicas():
+    """One oracle replica per host core, one coarse step each: a positive
+    rate over all cores, and a dictionary (never a hang) on any failure."""
+    out = bench.cpu_baseline_all_cores(3692312, 1)
+    assert "unavailable" not in out, out
+    assert out["cores"] == (os.cpu_count() or 1) and out["kind"] == "oracle"
+    assert out["value"] > 0
