@@ -582,7 +582,7 @@ def run_cic(n, reps, warmup, torch, peak_gbs, peak_src):
     gen_s = time.perf_counter() - t0
     st = bench_stream()
     out = {"grid": f"{n}^3 periodic", "particles": ps.np,
-           "set": "lattice of n^3 particles, Zel'dovich-like displacements (rms 1 cell), "
+           "set": "lattice of n^3 particles, Zel'dovich-like displacements (rms 0.75 cell at 512^3), "
                   "25% of the particles in Gaussian halos of ~4096 (radii 0.3-3 cells)",
            "l2": "inputs and grid larger than L2; not flushed", "input_generation_s": round(gen_s, 1)}
 

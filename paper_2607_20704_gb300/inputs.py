@@ -533,8 +533,10 @@ def particles(n: int, kind: str = "cosmo", seed: int = 0, lattice: int | None = 
     kind "cosmo": a cosmological-simulation-shaped distribution -- a lattice
     of `lattice`^3 particles (default n^3, one per cell) displaced by a
     Zel'dovich-like field (the gradient of a Gaussian potential with power
-    spectrum k^index on a coarse 64^3 grid, linearly interpolated, scaled to
-    an rms displacement of `disp` cells), with a fraction `halo_fraction`
+    spectrum k^index on a coarse 64^3 grid, scaled to an rms displacement
+    of `disp` cells at those points, then linearly interpolated to the
+    lattice, which lowers the rms on lattices finer than 64^3: 0.73 `disp`
+    at 128^3, 0.75 `disp` at 512^3), with a fraction `halo_fraction`
     of the particles moved into compact halos of about `halo_particles`
     particles each (Gaussian profiles with radii log-uniform in 0.3..3
     cells), so that voids hold ~1 particle per cell and halo cores hundreds.
