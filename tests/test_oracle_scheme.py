@@ -134,6 +134,23 @@ def test_conservation_with_reflux(orc, seed):
     assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
 
 
+def test_deepest_hierarchy_conserves_and_keeps_the_coarse_levels_at_rest(orc):
+    """Levels 2..15 (the deepest hierarchy), one coarse step = 16,383 level
+    steps: mass and energy conserved to round-off, and the coarse levels,
+    which the blast cannot reach in one step, keep momenta at round-off
+    against the energy present (the scale of the parity tolerance)."""
+    prob = inputs.sedov(2, 15, radii={l: 3 * 2.0 ** -l for l in range(3, 16)}, centre=(0.3, 0.7, 0.55))
+    m = orc.Mesh(*prob.mesh_args(), **prob.params())
+    t0 = m.totals()
+    m.advance(1)
+    t1 = m.totals()
+    assert np.all(np.abs(t1 - t0)[[0, 4]] <= 1e-13 * np.abs(t0[[0, 4]]))
+    for l in (2, 3, 4):
+        _, U = m.read(l)
+        scale = np.sqrt(2.0 * U[0] * U[4]).max()
+        assert np.abs(U[1:4]).max() <= 1e-15 * scale, (l, np.abs(U[1:4]).max(), scale)
+
+
 def test_conservation_fails_without_reflux(orc):
     """Negative control: without refluxing, coarse-fine faces leak."""
     prob = inputs.random_mesh(3, 5, seed=11)
