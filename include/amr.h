@@ -188,11 +188,14 @@ amr_status amr_member_dt(amr_handle h, double *dt_out, int n);
 /*
  * amr_regrid -- one regrid of the mesh (Sec. 2.2, then the ghost cache of
  * Sec. 2.3).  With the criteria of the handle's amr_params:
- *   flag    cells of level l < levelmax meeting a criterion; the face
- *           neighbour is the same-level cell, else the coarser cell covering
- *           it; the jump test is 2|a-b| > threshold (|a|+|b|) and the
- *           pressure (gamma-1)(E - (m.m/2)/rho) with the floors, decided in
- *           FP64 with every operation rounded as written
+ *   flag    cells of level l < levelmax meeting a criterion: the relative
+ *           jump 2|a-b|/(|a|+|b|) of rho or p to a face neighbour (the
+ *           same-level cell, else the coarser cell covering it) above its
+ *           threshold, or the cell mass rho dx^3 above refine_mass; decided
+ *           in FP64 in the division-free form 2|a-b| > threshold (|a|+|b|)
+ *           with p = (gamma-1)(E - (m.m/2)/rho) and the floors, which equals
+ *           the quotient test except for jumps within a few rounding errors
+ *           of the threshold
  *   expand  (regrid_expand) also the 26 same-level cells around a flag
  *   grade   finest level first, a flagged cell of level l flags the level
  *           l-1 cells covering its 27 level-l neighbours (2:1 rule)
@@ -208,6 +211,17 @@ amr_status amr_member_dt(amr_handle h, double *dt_out, int n);
  * 2^26 octs would result), AMR_ECUDA.
  */
 amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *removed);
+
+/* amr_regrid with the final flags given instead of computed (the stages
+ * after flag, expand and grade): flags[8 * q + c] != 0 splits cell c of oct
+ * q, q running over every oct of the handle in mesh order (members, then
+ * levels, then amr_read order); n_cells must equal 8 x the handle's octs.
+ * The flags must satisfy the 2:1 rule that grading would give them (a
+ * violation is reported as AMR_EGRADING by the rebuild).  Host buffer, read
+ * before return.  Synchronous; errors as amr_regrid, AMR_EINVAL for a wrong
+ * n_cells. */
+amr_status amr_regrid_flags(amr_handle h, const uint8_t *flags, int64_t n_cells,
+                            int64_t *created, int64_t *removed);
 
 /* Refinement flags of the selected member's cells of one level after the
  * flag, expand and grade stages of amr_regrid, without changing the mesh:

@@ -99,6 +99,7 @@ def lib():
                 "orc_mg_residual": (D, [I, D, P, D, P]),
                 "orc_regrid": (I, [C.POINTER(P), C.POINTER(_RegridParams), C.POINTER(I64),
                                    C.POINTER(I64)]),
+                "orc_regrid_flags": (I, [C.POINTER(P), P, C.POINTER(I64), C.POINTER(I64)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -269,6 +270,20 @@ class Mesh:
         rc = lib().orc_regrid(C.byref(h), C.byref(rp), C.byref(cr), C.byref(rm))
         if rc:
             raise OracleError(rc, "regrid")
+        self._h = h
+        return cr.value, rm.value
+
+    def regrid_flags(self, flags):
+        """Regrid in place with the given final flags ([8n] in mesh order, as
+        ``flags`` returns them); returns (octs created, octs removed)."""
+        n = int(sum(self.num_octs(l) for l in range(16)))
+        f = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert f.shape == (8 * n,), (f.shape, n)
+        h = C.c_void_p(self._h.value if isinstance(self._h, C.c_void_p) else self._h)
+        cr, rm = C.c_int64(), C.c_int64()
+        rc = lib().orc_regrid_flags(C.byref(h), _ptr(f), C.byref(cr), C.byref(rm))
+        if rc:
+            raise OracleError(rc, "regrid_flags")
         self._h = h
         return cr.value, rm.value
 

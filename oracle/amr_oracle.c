@@ -1048,9 +1048,8 @@ int orc_1d_step(int n, double *U, double gamma, double dt, double smallr, double
 /*          face neighbours (the same-level cell, else the coarser cell      */
 /*          covering it), the relative jump 2|a-b|/(|a|+|b|) of rho exceeds  */
 /*          grad_rho or that of p exceeds grad_p, or when rho dx_l^3 exceeds */
-/*          mass; the jump test is taken as 2|a-b| > thr (|a|+|b|) and the   */
-/*          pressure as (gamma-1)(E - (m.m/2)/rho) with the floors, so that  */
-/*          a criterion costs one division per cell;                         */
+/*          mass (rho and p are the primitive variables of the scheme, with */
+/*          its floors; a jump between two zeros is 0);                      */
 /*   expand with expand = 1 a flag also flags the 26 same-level cells       */
 /*          around it that exist;                                            */
 /*   grade  finest level first: a flagged cell X of level l flags, at level  */
@@ -1066,20 +1065,10 @@ int orc_1d_step(int n, double *U, double gamma, double dt, double smallr, double
 /*          creation (order, lookup, grading check, cache, restriction).     */
 /* ------------------------------------------------------------------------- */
 
-/* the relative jump of a and b exceeds thr: 2|a-b| > thr (|a|+|b|) */
-static int jump_exceeds(double a, double b, double thr) {
-  return 2.0 * fabs(a - b) > thr * (fabs(a) + fabs(b));
-}
-
-/* density and pressure of the flag criterion, with the floors */
-static void flag_rho_p(const phys *ph, const double u[NV], double *rho, double *p) {
-  double r = u[0] > ph->smallr ? u[0] : ph->smallr;
-  double m2 = (u[1] * u[1] + u[2] * u[2]) + u[3] * u[3];
-  double ek = (0.5 * m2) / r;
-  double pr = (ph->g - 1.0) * (u[4] - ek);
-  double pf = r * ph->smallp;
-  *rho = r;
-  *p = pr < pf ? pf : pr;
+/* relative jump 2|a-b|/(|a|+|b|) of two values (0 when both are 0) */
+static double rel_jump(double a, double b) {
+  double s = fabs(a) + fabs(b);
+  return s > 0.0 ? 2.0 * fabs(a - b) / s : 0.0;
 }
 
 /* oct index of the cell (x,y,z) of level L (same level only), or -1 */
@@ -1094,20 +1083,20 @@ static int raw_flag(const orc_mesh *m, const phys *ph, const orc_regrid_params *
                     int c) {
   int64_t N8 = 8 * m->n;
   int l = m->lvl[o];
-  double uc[NV], rc, pc;
+  double uc[NV], wc[NV];
   for (int v = 0; v < NV; ++v) uc[v] = m->U[v * N8 + 8 * o + c];
   if (rp->mass > 0.0 && ldexp(uc[0], -3 * l) > rp->mass) return 1;
   if (!(rp->grad_rho > 0.0) && !(rp->grad_p > 0.0)) return 0;
-  flag_rho_p(ph, uc, &rc, &pc);
+  cons_to_prim(ph, uc, wc);
   int64_t x = 2 * (int64_t)m->ci[o] + (c & 1), y = 2 * (int64_t)m->cj[o] + ((c >> 1) & 1),
           z = 2 * (int64_t)m->ck[o] + ((c >> 2) & 1);
   for (int d = 0; d < 3; ++d)
     for (int s = -1; s <= 1; s += 2) {
-      double un[NV], rn, pn;
+      double un[NV], wn[NV];
       if (cell_value(m, l, x + (d == 0) * s, y + (d == 1) * s, z + (d == 2) * s, un)) continue;
-      flag_rho_p(ph, un, &rn, &pn);
-      if (rp->grad_rho > 0.0 && jump_exceeds(rn, rc, rp->grad_rho)) return 1;
-      if (rp->grad_p > 0.0 && jump_exceeds(pn, pc, rp->grad_p)) return 1;
+      cons_to_prim(ph, un, wn);
+      if (rp->grad_rho > 0.0 && rel_jump(wn[0], wc[0]) > rp->grad_rho) return 1;
+      if (rp->grad_p > 0.0 && rel_jump(wn[4], wc[4]) > rp->grad_p) return 1;
     }
   return 0;
 }
@@ -1198,26 +1187,26 @@ static int new_cell_value(const orc_mesh *m, const new_level *nl, int L, int64_t
 }
 
 int orc_regrid(orc_mesh **pm, const orc_regrid_params *rp, int64_t *created, int64_t *removed) {
+  uint8_t *flag = (uint8_t *)malloc((size_t)(8 * (*pm)->n) + 1);
+  if (!flag) return ORC_ENOMEM;
+  int e = orc_flags(*pm, rp, flag);
+  if (!e) e = orc_regrid_flags(pm, flag, created, removed);
+  free(flag);
+  return e;
+}
+
+int orc_regrid_flags(orc_mesh **pm, const uint8_t *flag, int64_t *created, int64_t *removed) {
   orc_mesh *m = *pm;
   const int64_t n = m->n, n8 = 8 * n;
   const int lmin = m->p.levelmin, lmax = m->p.levelmax;
-  uint8_t *flag = (uint8_t *)malloc((size_t)n8 + 1);
-  if (!flag) return ORC_ENOMEM;
-  int e = orc_flags(m, rp, flag);
-  if (e) {
-    free(flag);
-    return e;
-  }
+  int e = 0;
   /* octs of the new mesh: the base level, and the children of flagged cells;
    * an old oct of level l > levelmin is kept when its father is flagged */
   int64_t kept = 0, ncreate = 0, nremove = 0;
   uint8_t *keep = (uint8_t *)calloc((size_t)n + 1, 1);
   new_level nl[ORC_MAXLEV + 1];
   memset(nl, 0, sizeof nl);
-  if (!keep) {
-    free(flag);
-    return ORC_ENOMEM;
-  }
+  if (!keep) return ORC_ENOMEM;
   for (int64_t o = 0; o < n; ++o) {
     int l = m->lvl[o];
     int k = 1;
@@ -1325,7 +1314,6 @@ done:
     free(nl[l].U);
   }
   free(keep);
-  free(flag);
   return e;
 }
 
@@ -1338,8 +1326,6 @@ done:
 /* trilinear interpolation with weights (1,3,3,9,3,9,9,27)/64.  On the      */
 /* periodic base level the hierarchy is the same box at half the resolution */
 /* per level, down to 2^3 cells; the coarsest grid is smoothed (8 sweeps). */
-/* The Gauss-Seidel update multiplies by the rounded 1/6 and the residual   */
-/* by 1/dx^2 (exact, dx being a power of two), so that no step divides.     */
 /* ------------------------------------------------------------------------- */
 
 static int64_t mg_at(int n, int64_t x, int64_t y, int64_t z) {
@@ -1360,7 +1346,7 @@ static void mg_smooth(int n, double dx2, const double *f, double *phi) {
         for (int64_t x = 0; x < n; ++x) {
           if ((int)((x + y + z) & 1) != colour) continue;
           int64_t t = mg_at(n, x, y, z);
-          phi[t] = (mg_nbsum(n, phi, x, y, z) - dx2 * f[t]) * (1.0 / 6.0);
+          phi[t] = (mg_nbsum(n, phi, x, y, z) - dx2 * f[t]) / 6.0;
         }
 }
 
@@ -1369,7 +1355,7 @@ static void mg_residual(int n, double dx2, const double *f, const double *phi, d
     for (int64_t y = 0; y < n; ++y)
       for (int64_t x = 0; x < n; ++x) {
         int64_t t = mg_at(n, x, y, z);
-        r[t] = f[t] - (mg_nbsum(n, phi, x, y, z) - 6.0 * phi[t]) * (1.0 / dx2);
+        r[t] = f[t] - (mg_nbsum(n, phi, x, y, z) - 6.0 * phi[t]) / dx2;
       }
 }
 
@@ -1503,7 +1489,7 @@ int orc_cic_deposit(int n, int64_t np, const double *x, const double *y, const d
       int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
       int64_t t = (int64_t)wrap(ix + cx, n) +
                   (int64_t)n * ((int64_t)wrap(iy + cy, n) + (int64_t)n * wrap(iz + cz, n));
-      rho[t] += ((m[p] * wx[cx]) * wy[cy]) * wz[cz];
+      rho[t] += m[p] * ((wx[cx] * wy[cy]) * wz[cz]);
     }
   }
   /* mass -> density: divide by dx^3 = n^-3, an exact scaling */

@@ -82,7 +82,7 @@ int orc_advance(orc_mesh *m, int nsteps, double *dt_last);
 /* --- regrid (Sec. 2.2: refinement, de-refinement, level and Hilbert order;
  *     then the ghost cache of Sec. 2.3) ------------------------------------- */
 typedef struct {
-  double grad_rho; /* relative jump of rho to a face neighbour, 2|a-b| > grad_rho (|a|+|b|); <= 0: off */
+  double grad_rho; /* relative jump 2|a-b|/(|a|+|b|) of rho to a face neighbour; <= 0: off */
   double grad_p;   /* the same for the pressure; <= 0: off */
   double mass;     /* cell mass rho dx^3 above which a cell refines; <= 0: off */
   int expand;      /* 1: a flag also flags the 26 same-level neighbours */
@@ -98,6 +98,9 @@ int orc_flags(const orc_mesh *m, const orc_regrid_params *rp, uint8_t *flag);
  * Pending reflux is dropped (regrid runs between coarse steps, where it is
  * zero).  created/removed: numbers of octs (may be NULL). */
 int orc_regrid(orc_mesh **pm, const orc_regrid_params *rp, int64_t *created, int64_t *removed);
+/* The same regrid with the final flags given (flag[8*oct + c], mesh order,
+ * as orc_flags writes them): the mesh stages alone. */
+int orc_regrid_flags(orc_mesh **pm, const uint8_t *flag, int64_t *created, int64_t *removed);
 
 /* --- self-gravity: multigrid Poisson V-cycles on a periodic level (Sec. 5) --
  * Solves (sum of the 6 neighbours - 6 phi) / dx^2 = fourpiG (rho - mean rho)
@@ -118,7 +121,7 @@ double orc_mg_residual(int n, double dx, const double *rho, double fourpiG, cons
  * deposit onto an n^3 grid of cells of size 1/n (n a power of two; arrays
  * [i + n (j + n k)]): along each axis s = x n - 1/2, i0 = floor(s),
  * f = s - i0, weights 1 - f for cell i0 and f for cell i0 + 1 (periodic);
- * a particle gives ((m wx) wy) wz to each of its 8 cells, corner order
+ * a particle gives m (wx wy) wz to each of its 8 cells, corner order
  * c = cx + 2 cy + 4 cz, particles in index order; rho = sum / dx^3. */
 int orc_cic_deposit(int n, int64_t np, const double *x, const double *y, const double *z,
                     const double *m, double *rho);

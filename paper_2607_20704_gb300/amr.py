@@ -99,6 +99,7 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
            "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag",
+           "amr_regrid_flags",
            "amr_poisson", "amr_read_phi", "amr_load_state_async", "amr_store_state_async",
            "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
@@ -169,6 +170,7 @@ def load(path: str | None = None):
             "amr_set_member_steps": (I, [P, P, I]),
             "amr_member_errors": (I, [P, P, I]),
             "amr_regrid": (I, [P, P, P]),
+            "amr_regrid_flags": (I, [P, P, I64, P, P]),
             "amr_flag": (I, [P, I, P, I64]),
             "amr_poisson": (I, [P, D, I, P]),
             "amr_read_phi": (I, [P, P, I64]),
@@ -345,6 +347,16 @@ class Mesh:
         (octs created, octs removed)."""
         cr, rm = C.c_int64(), C.c_int64()
         _check(load().amr_regrid(self._h, C.byref(cr), C.byref(rm)), "amr_regrid")
+        return cr.value, rm.value
+
+    def regrid_flags(self, flags):
+        """Regrid with the given final flags: one byte per cell of the whole
+        handle in mesh order (levels ascending, amr_read order within a
+        level); returns (octs created, octs removed)."""
+        f = np.ascontiguousarray(flags, dtype=np.uint8)
+        cr, rm = C.c_int64(), C.c_int64()
+        _check(load().amr_regrid_flags(self._h, _ptr(f), int(f.size), C.byref(cr), C.byref(rm)),
+               "amr_regrid_flags")
         return cr.value, rm.value
 
     def flags(self, level: int):

@@ -1800,8 +1800,10 @@ static amr_mesh *regrid_shell(amr_mesh *h) {
   return nh;
 }
 
-extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *removed) {
-  if (!h) return fail(AMR_EINVAL, "amr_regrid: NULL handle");
+// One regrid; the final flags are computed from the handle's criteria, or
+// given (hflags: one byte per cell of the whole handle, mesh order).
+static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *created,
+                              int64_t *removed) {
   if (h->cs) CUDA_TRY(cudaStreamSynchronize(h->cs));  // state copies in flight finish first
   if (h->cs_out) CUDA_TRY(cudaStreamSynchronize(h->cs_out));
   if (created) *created = 0;
@@ -1832,7 +1834,19 @@ extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *remove
   REGRID_TRY(alloc_n(h, &kpos, N));
   REGRID_TRY(alloc_n(h, &npos, N));
   REGRID_TRY(alloc_n(h, &tmp, scan_tmp_size(N)));
-  REGRID_TRY(compute_flags(h, raw, flag, "amr_regrid"));
+  if (hflags) {
+    std::vector<uint32_t> mk(N);
+    for (int64_t q = 0; q < N; ++q) {
+      uint32_t b = 0;
+      for (int c = 0; c < 8; ++c) b |= uint32_t(hflags[8 * q + c] != 0) << c;
+      mk[q] = b;
+    }
+    cudaError_t e = cudaMemcpyAsync(flag, mk.data(), 4 * N, cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) REGRID_TRY(fail(AMR_ECUDA, "amr_regrid_flags: %s", cudaGetErrorString(e)));
+  } else {
+    REGRID_TRY(compute_flags(h, raw, flag, "amr_regrid"));
+  }
   const RegridArgs a = regrid_args(h, raw, flag);
   launch(h, K_REGRID, k_regrid_count, dim3(nblocks(N)), dim3(256), a, keep, nnew);
   cudaMemcpyAsync(kpos, keep, 4 * N, cudaMemcpyDeviceToDevice, h->s);
@@ -1936,6 +1950,20 @@ extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *remove
   destroy_all(nh);
   return check_device(h, "amr_regrid");
 #undef REGRID_TRY
+}
+
+extern "C" amr_status amr_regrid(amr_handle h, int64_t *created, int64_t *removed) {
+  if (!h) return fail(AMR_EINVAL, "amr_regrid: NULL handle");
+  return regrid_impl(h, nullptr, created, removed);
+}
+
+extern "C" amr_status amr_regrid_flags(amr_handle h, const uint8_t *flags, int64_t n_cells,
+                                       int64_t *created, int64_t *removed) {
+  if (!h || !flags) return fail(AMR_EINVAL, "amr_regrid_flags: NULL argument");
+  if (n_cells != 8 * h->N)
+    return fail(AMR_EINVAL, "amr_regrid_flags: %lld flags given, the handle has %lld cells",
+                (long long)n_cells, (long long)(8 * h->N));
+  return regrid_impl(h, flags, created, removed);
 }
 
 // ---------------------------------------------------------------------------

@@ -13,8 +13,10 @@
 // arrays [x + n (y + n z)] of every multigrid level (unit-stride x, so every
 // stencil access is coalesced), gathered from and scattered back to the octs.
 // On GB300 the FP64 pipe bounds these stencils (about 8 FP64 operations per
-// cell against 16 bytes of traffic); no step divides (the Gauss-Seidel update
-// multiplies by the rounded 1/6, the residual by the exact 1/dx^2).
+// cell against 16 bytes of traffic); no step divides: the Gauss-Seidel update
+// multiplies by the rounded 1/6 where the operator divides by 6 (the two differ
+// by at most a few units in the last place per update), and the residual
+// multiplies by 1/dx^2, which is exact (dx is a power of two).
 #pragma once
 #include "amr_internal.cuh"
 

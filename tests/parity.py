@@ -2,18 +2,25 @@
 
 Tolerance (FP64 state, one step from identical inputs): per variable v,
 |gpu - oracle| <= rtol * max(|oracle|, s_v), s_v = max |U_v| over the
-level; for the three momentum components s_v is also at least the level's
-max sqrt(2 rho E), the largest momentum its energy allows (E >= |m|^2 / 2
-rho).  Round-off in a momentum update scales with the fluxes, i.e. with
-the energy present: a level at rest whose momenta are pure round-off
-(1e-19 against E ~ 1e2 on the coarse levels of a deep hierarchy) would
-otherwise be held to a relative bound on noise.  rtol = 1e-12 per level
+level.  On a level at rest, whose momenta are pure round-off (max |m| below
+1e-8 of the level's max sqrt(2 rho E), the largest momentum its energy
+allows since E >= |m|^2 / 2 rho), s_v of the three momentum components is
+raised to that max sqrt(2 rho E): round-off in a momentum update scales with
+the fluxes, i.e. with the energy present, so such a level (1e-19 against
+E ~ 1e2 on the coarse levels of a deep hierarchy) would otherwise be held to
+a relative bound on noise.  Every level that moves keeps s_v = max |m|, the
+tolerance of a per-cell FP64 comparison.  rtol = 1e-12 per level
 step; the W-cycle tests that chain many level steps from one initial state
 allow 1e-11 (round-off is re-amplified by the nonlinear limiter/Riemann
 steps that follow)."""
 import numpy as np
 
 from paper_2607_20704_gb300 import inputs
+
+
+# a level whose largest momentum is below this fraction of its largest
+# sqrt(2 rho E) is at rest: its momenta are round-off
+AT_REST = 1e-8
 
 
 def level_scale(U):
@@ -23,7 +30,8 @@ def level_scale(U):
     s = np.abs(U).max(axis=1, keepdims=True).astype(np.float64)
     if U.shape[0] == 5:
         e = np.sqrt(2.0 * np.maximum(U[0], 0.0) * np.maximum(U[4], 0.0)).max()
-        s[1:4] = np.maximum(s[1:4], e)
+        if s[1:4].max() < AT_REST * e:
+            s[1:4] = np.maximum(s[1:4], e)
     return s
 
 

@@ -3,11 +3,17 @@ atomic (warp-combining) and the deterministic segment algorithm in FP64 and
 FP32, the source-cell Hilbert sort, reproducibility, edge cases, and the
 full-size cosmological configuration on sampled cells.
 
-Tolerances.  Both sides form every particle's 8 contributions with the same
-operations, so the terms agree bit for bit; the sums differ only in order.
-A sum of K non-negative terms has a rounding error of at most (K - 1) u times
-its value in any order (u = 2^-53), hence |gpu - oracle| <= 2 K u rho per
-cell, K the number of particles whose stencil touches the cell.  FP32 adds
+Tolerances.  Both sides form the same weights (exactly), but the oracle
+multiplies a contribution as m ((wx wy) wz) and the GPU as ((m wx) wy) wz:
+each is three roundings from the exact product, so within (1 + u)^3 - 1 of
+it (u = 2^-53), and the two differ by at most 6.001 u of the term.  Over the
+K non-negative terms that reach a cell these differences sum to at most
+6.001 u rho.  Then the sums differ in order: a sum of K non-negative terms
+has a rounding error of at most (K - 1) u times its value in any order, so
+the two sums are at most 2 (K - 1) u rho apart beyond the terms' own
+difference.  Hence |gpu - oracle| <= (2 K + 8) u rho per cell (the 8 covers
+6.001 u and the second-order terms), K the number of particles whose
+stencil touches the cell; the final scaling by 1/dx^3 is exact.  FP32 adds
 the rounding of the positions (x n - 1/2 moves by at most n 2^-24, each
 weight by at most (n + 1) 2^-24), of the masses and of the products, and
 sums in FP32: |gpu - oracle| <= (6 n + 12 + K) 2^-24 M per cell, M the sum
@@ -68,7 +74,7 @@ def _fp32_reach(n, x, y, z, m):
 
 def _bound(n, x, y, z, m, ref, precision):
     if precision == 8:
-        return 2 * _touch_counts(n, x, y, z) * U64 * ref
+        return (2 * _touch_counts(n, x, y, z) + 8) * U64 * ref
     K, M = _fp32_reach(n, x, y, z, m)
     return (6 * n + 12 + K) * U32 * M
 
@@ -324,7 +330,7 @@ def bound_at(n, x, y, z, m, ref, cells, precision):
                 np.add.at(K, order[pos[hit]], 1)
                 np.add.at(M, order[pos[hit]], m[hit] * float(n) ** 3)
     if precision == 8:
-        return 2 * K * U64 * ref
+        return (2 * K + 8) * U64 * ref
     return (6 * n + 12 + K) * U32 * M
 
 
