@@ -569,7 +569,7 @@ static StepArgs<T> step_args(amr_mesh *h, bool device_dt, double dt) {
   a.N = int(h->N);
   a.NE = int(h->NE);
   a.NC = int(h->NC);
-  a.LS = int(h->max_ls);
+  a.LS = h->max_ls;
   a.S = h->S;
   a.CS = 24 * h->NC;
   a.U = static_cast<T *>(h->U);
@@ -1142,6 +1142,10 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
       base += acc;
     }
   }
+  // cell indices of real and ghost octs are 32-bit in the kernels and tables
+  if (8 * (n + NC) > int64_t(INT32_MAX))
+    return fail(AMR_EINVAL, "amr_create: %lld real + %lld ghost octs exceed 2^31 cells",
+                (long long)n, (long long)NC);
   h->NE = n + NC;
   h->S = 8 * h->NE;
   AMR_TRY(alloc_n(h, &h->fnb, 6 * h->NE));
@@ -1262,6 +1266,11 @@ extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
   if (p->precision != 4 && p->precision != 8)
     return fail(AMR_EINVAL, "amr_create: precision must be 4 or 8");
   for (int q = 0; q < n_members; ++q) AMR_TRY(check_member(members[q], q));
+  {
+    int64_t total = 0;
+    for (int q = 0; q < n_members; ++q) total += members[q].n_oct;
+    if (total > (int64_t(1) << 26)) return fail(AMR_EINVAL, "amr_create: more than 2^26 octs in total");
+  }
   amr_mesh *h = new amr_mesh();
   h->p = *p;
   h->M = n_members;

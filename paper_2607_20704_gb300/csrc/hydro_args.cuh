@@ -26,12 +26,15 @@ struct Tile {
   int seg, start;
 };
 
-// Everything a level-step launch needs, passed by value.  Every count fits in
-// 32 bits (at most 2^26 real octs), so kernels index with int.
+// Everything a level-step launch needs, passed by value.  Oct counts and cell
+// indices fit in 32 bits (at most 2^26 real octs, and 8 (real + ghost octs)
+// <= 2^31 - 1, both checked by the host before any state is allocated), so
+// kernels index cells with int; every product with a stride (S, LS, CS) is
+// formed in 64 bits, since 20 LS exceeds 2^31 from about 107 M local cells on.
 template <class T>
 struct StepArgs {
   int N, NE, NC;      // real octs; real + ghost octs; ghost octs (all members)
-  int LS;             // stride of the scratch arrays
+  int64_t LS;         // stride of the scratch arrays
   int64_t S;          // stride of U (8*NE)
   int64_t CS;         // stride of the reflux slots (24*NC)
   T *U;

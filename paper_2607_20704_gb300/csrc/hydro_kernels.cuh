@@ -440,10 +440,10 @@ __device__ __forceinline__ void face_flux(const StepArgs<T> &a, const SegCtx<T> 
 // reflux slot of a coarse-fine face: ghost oct g (local oct index), the
 // direction of the face seen from the ghost's father cell X, fine face (a,b)
 template <int D>
-__device__ __forceinline__ int reflux_slot(int clo, int nl, int gq, int dirX, int c) {
+__device__ __forceinline__ int64_t reflux_slot(int clo, int nl, int gq, int dirX, int c) {
   constexpr int d1 = D == 0 ? 1 : 0, d2 = D == 2 ? 1 : 2;
   const int ab = (((c >> d1) & 1) << 1) | ((c >> d2) & 1);
-  return (clo + gq - nl) * 24 + dirX * 4 + ab;
+  return int64_t(clo + gq - nl) * 24 + dirX * 4 + ab;
 }
 
 template <int D, class T>
@@ -461,7 +461,7 @@ __device__ __forceinline__ void flux_dir(const StepArgs<T> &a, const SegCtx<T> &
     if (a.reflux && (real != nreal)) {
       // ghost on the plus side: the coarse cell's minus face (sigma +1);
       // ghost on the minus side: its plus face (sigma -1)
-      const int gslot = real ? reflux_slot<D>(s.clo, s.nl, tn >> 3, 2 * D, c)
+      const int64_t gslot = real ? reflux_slot<D>(s.clo, s.nl, tn >> 3, 2 * D, c)
                              : reflux_slot<D>(s.clo, s.nl, t >> 3, 2 * D + 1, c);
       const T sg = real ? T(1) : T(-1);
 #pragma unroll
@@ -551,7 +551,7 @@ __device__ __forceinline__ void faces_dir(const StepArgs<T> &a, const SegCtx<T> 
   if (!cell_is_split(a, s, tm)) {
     face_flux<D>(a, s, tm, t, Fm);
     if (a.reflux && (tm >> 3) >= s.nl) {
-      const int gslot = reflux_slot<D>(s.clo, s.nl, tm >> 3, 2 * D + 1, c);
+      const int64_t gslot = reflux_slot<D>(s.clo, s.nl, tm >> 3, 2 * D + 1, c);
 #pragma unroll
       for (int v = 0; v < 5; ++v)
         a.C[v * a.CS + checked(gslot, 0, a.CS, a.err)] = (T(-1) * s.dtdx) * Fm[v] / T(8);
@@ -561,7 +561,7 @@ __device__ __forceinline__ void faces_dir(const StepArgs<T> &a, const SegCtx<T> 
   if (!cell_is_split(a, s, tp)) {
     face_flux<D>(a, s, t, tp, Fp);
     if (a.reflux && (tp >> 3) >= s.nl) {
-      const int gslot = reflux_slot<D>(s.clo, s.nl, tp >> 3, 2 * D, c);
+      const int64_t gslot = reflux_slot<D>(s.clo, s.nl, tp >> 3, 2 * D, c);
 #pragma unroll
       for (int v = 0; v < 5; ++v)
         a.C[v * a.CS + checked(gslot, 0, a.CS, a.err)] = (T(1) * s.dtdx) * Fp[v] / T(8);

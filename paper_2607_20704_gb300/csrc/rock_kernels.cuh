@@ -85,7 +85,7 @@ __device__ __forceinline__ void reflux_write(const StepArgs<T> &a, const SegCtx<
                                              int side, const T (&F)[5]) {
   const int d1 = D == 0 ? 1 : 0, d2 = D == 2 ? 1 : 2;
   const int ab = (((cmin >> d1) & 1) << 1) | ((cmin >> d2) & 1);
-  const int gslot = (eg - a.N) * 24 + (side > 0 ? 2 * D : 2 * D + 1) * 4 + ab;
+  const int64_t gslot = int64_t(eg - a.N) * 24 + (side > 0 ? 2 * D : 2 * D + 1) * 4 + ab;
   const T sgn = side > 0 ? T(1) : T(-1);
 #pragma unroll
   for (int v = 0; v < 5; ++v) a.C[v * a.CS + checked(gslot, 0, a.CS, a.err)] = (sgn * s.dtdx) * F[v] / T(8);

@@ -108,3 +108,34 @@ def test_particle_calls_check_their_arguments_on_the_host(lib):
     names = amr.part_kernel_names()
     for k in ("part_keys", "psort_scatter", "cic_atomic", "seg_partial", "seg_gather"):
         assert k in names
+
+
+def test_create_refuses_oversize_meshes_on_the_host(lib):
+    """More than 2^26 octs (one mesh, or the members of a batch together) is
+    refused before any device work: the arrays are never read, no stream or
+    allocation is made (this runs without a GPU).  Below that limit the
+    kernels form every product with a scratch stride in 64 bits (20 x the
+    local cells of a level exceeds 2^31 from about 107 M cells on)."""
+    from paper_2607_20704_gb300 import amr
+    import numpy as np
+    p = amr.amr_params()
+    lib.amr_params_default(C.byref(p))
+    one = np.ones(1, np.uint8)
+    z = np.zeros(1, np.uint32)
+    U = np.ones((5, 8))
+    h = C.c_void_p()
+    rc = lib.amr_create(C.byref(p), (1 << 26) + 1, one.ctypes.data, z.ctypes.data, z.ctypes.data,
+                        z.ctypes.data, None, U.ctypes.data, C.byref(h))
+    assert rc == amr.AMR_EINVAL and not h.value
+    assert "2^26" in lib.amr_last_error().decode()
+    members = (amr.amr_member * 2)()
+    for q in range(2):
+        m = members[q]
+        m.levelmin, m.levelmax, m.gamma, m.cfl = 3, 4, 1.4, 0.8
+        m.smallr = m.smallc = 1e-10
+        m.n_oct = (1 << 25) + 1
+        m.level, m.i, m.j, m.k = one.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data
+        m.U = U.ctypes.data
+    rc = lib.amr_create_batch(C.byref(p), 2, members, C.byref(h))
+    assert rc == amr.AMR_EINVAL and not h.value
+    assert "2^26" in lib.amr_last_error().decode()
