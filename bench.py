@@ -981,8 +981,8 @@ def main():
         "config": {"workload": WORKLOAD, "levelmin": 7, "levelmax": 10, "gamma": 5.0 / 3.0,
                    "n_oct": main_res["info"]["n_oct"], "n_ghost_oct": main_res["info"]["n_cache"],
                    "leaf_cells": main_res["info"]["n_leaf_cells"],
-                   "cell_updates_per_step": upd, "step": "one coarse W-cycle step (reindex + CFL + "
-                   "15 level steps)", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "cell_updates_per_step": upd, "step": "one coarse W-cycle step (CFL + 15 level "
+                   "steps; the static mesh is indexed once, at creation)", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": rl,
         "step_roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak_gbs,

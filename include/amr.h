@@ -73,7 +73,11 @@ typedef struct {
                                0: off (a negative control for tests) */
   int reindex_every_step;   /* 1: amr_advance rebuilds the hash table and the
                                neighbour/cache index at the start of every
-                               coarse step, as after a regrid (default) */
+                               coarse step, as after a regrid (the paper's
+                               per-step cache rebuild); 0 (default): the
+                               index is rebuilt only where the mesh changes
+                               (amr_create, amr_regrid, amr_reindex); the
+                               results are the same bit for bit */
   int use_graphs;           /* 1: amr_advance replays a captured CUDA graph of
                                one coarse step (default) */
   size_t hbm_budget_bytes;  /* 0: no limit; else AMR_ENOMEM beyond it */
@@ -109,7 +113,7 @@ typedef struct {
 } amr_params;
 
 /* Fills p with the defaults: levelmin = levelmax = 1, gamma = 1.4, cfl = 0.8,
- * smallr = smallc = 1e-10, precision 8, reflux 1, reindex_every_step 1,
+ * smallr = smallc = 1e-10, precision 8, reflux 1, reindex_every_step 0,
  * use_graphs 1, no budget, NULL stream and allocator, tile 0, schedule -1,
  * nsubgrid -1 and planar -1 (picked by the autotuner), refinement criteria
  * off, regrid_expand 1, regrid_every_step 0. */
@@ -305,6 +309,46 @@ amr_status amr_reindex(amr_handle h);
 amr_status amr_read(amr_handle h, int level, int64_t *n_oct_out, uint64_t *keys,
                     double *U, int64_t cap);
 
+/*
+ * amr_totals -- conserved totals of the selected member's leaf cells (the
+ * per-level conservation check of a cell-by-cell AMR update, Sec. 3: every
+ * flux leaves one cell and enters another, reflux closing coarse-fine
+ * faces): out[v] = sum over the leaf cells of `level` of U_v dx^3, dx =
+ * 2^-level; level 0: the sum over every level, the levels' totals added in
+ * ascending level order.  FP64 in both precisions (FP32 states are widened
+ * exactly); every addition in a fixed order (fixed blocks per level size, no
+ * atomics), so calls repeat bit for bit.  out: 5 doubles, host.  Waits for
+ * the handle's stream (synchronous).  Errors: AMR_EINVAL (NULL, level
+ * outside [0, 15]), AMR_ENOMEM, AMR_ECUDA.
+ */
+amr_status amr_totals(amr_handle h, int level, double *out);
+
+/*
+ * amr_hash -- FNV-1a 64 as the hash table computes it (Sec. 2.1 keys the
+ * table by an "fnv64" hash; Sec. 6 names FNV-1a 64): hash[q] = FNV-1a 64
+ * (offset basis 0xcbf29ce484222325, prime 0x100000001b3) over the 8 bytes of
+ * keys[q], least significant byte first, evaluated on the device by the
+ * function every table insert and probe uses.  keys, hash: n values, host
+ * buffers (0 <= n <= 2^28).  Uses the handle's stream and allocator;
+ * synchronous.  Errors: AMR_EINVAL, AMR_ENOMEM, AMR_ECUDA.
+ */
+amr_status amr_hash(amr_handle h, int64_t n, const uint64_t *keys, uint64_t *hash);
+
+/*
+ * amr_read_hash -- the handle's hash table as stored (Sec. 2.1: open
+ * addressing, linear probing, the home slot of a key is its FNV-1a 64 hash
+ * masked by capacity - 1).  *cap_out = capacity (a power of two, at least
+ * twice the real + ghost octs).  When keys / vals are not NULL (cap >=
+ * capacity) they receive every slot: empty slots hold the key all ones and
+ * value 0; an occupied slot holds the internal key
+ *     member << 49 | level << 45 | i << 30 | j << 15 | k
+ * (member 0 for a single mesh; i, j, k the oct coordinates) and the value
+ * 1 + the oct's extended index (real octs in mesh order first, then the
+ * ghost octs of the cache).  Synchronous.
+ */
+amr_status amr_read_hash(amr_handle h, int64_t *cap_out, uint64_t *keys, int32_t *vals,
+                         int64_t cap);
+
 /* Same as amr_read for the pending reflux R [5][8*n] of a level. */
 amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_t cap);
 
@@ -389,8 +433,14 @@ amr_status amr_read_timing(amr_handle h, int n, double *ms, int64_t *launches);
 const char *amr_kernel_name(int t);
 
 /*
- * amr_cfl_dt_static -- the time-step reduction of amr_cfl_dt for one level of
- * leaf cells held in caller device memory, with no device allocation at all.
+ * amr_cfl_dt_static -- the CFL time step of one level of leaf cells held in
+ * caller device memory, with no device allocation at all.  It computes the
+ * quantity amr_cfl_dt reduces for that level, dt_l = cfl dx_l / max sum_d
+ * (|u_d| + c), with three differences: it returns the level's dt_l, not the
+ * coarse step's dt; it divides (u_d / rho, gamma p / rho) where amr_cfl_dt
+ * multiplies by a Newton-refined reciprocal, so the two can differ in the
+ * last bit; and a non-finite cell makes the result NaN, where amr_cfl_dt
+ * reports AMR_ENAN.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory (device memory pre-reserved by another
  * runtime's pool, allocator-free real-time loops).  Its scratch is fixed
@@ -405,7 +455,9 @@ const char *amr_kernel_name(int t);
  *            NaN if a cell is not finite
  *   stream   cudaStream_t (NULL: legacy default stream); asynchronous
  * The first call on a device looks up the scratch address (with that device
- * current); make that first call before any stream capture.  Every call on a
+ * current) and keeps it for the process's life; make that first call before
+ * any stream capture, and do not call again after a cudaDeviceReset of that
+ * device.  Every call on a
  * device shares the same scratch: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller.  The
  * call clears the scratch counter it needs before its kernel runs.

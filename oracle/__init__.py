@@ -86,6 +86,7 @@ def lib():
                 "orc_ghost": (I, [P, I, P]),
                 "orc_write": (I, [P, I, P]),
                 "orc_totals": (None, [P, P]),
+                "orc_level_totals": (None, [P, I, P]),
                 "orc_cfl_dt": (D, [P]),
                 "orc_step_level": (I, [P, I, D]),
                 "orc_step_sample": (I, [P, I, D, I64, P, P]),
@@ -218,6 +219,12 @@ class Mesh:
     def totals(self):
         t = np.zeros(NV, np.float64)
         lib().orc_totals(self._h, _ptr(t))
+        return t
+
+    def level_totals(self, level: int):
+        """Sum of U dx^3 over the leaf cells of one level."""
+        t = np.zeros(NV, np.float64)
+        lib().orc_level_totals(self._h, int(level), _ptr(t))
         return t
 
     # -- stepping ------------------------------------------------------------

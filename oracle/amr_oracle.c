@@ -478,6 +478,19 @@ void orc_totals(const orc_mesh *m, double tot[NV]) {
   }
 }
 
+void orc_level_totals(const orc_mesh *m, int level, double tot[NV]) {
+  int64_t N8 = 8 * m->n;
+  double dx = ldexp(1.0, -level);
+  double vol = dx * dx * dx;
+  for (int v = 0; v < NV; ++v) tot[v] = 0.0;
+  if (level < 0 || level > ORC_MAXLEV) return;
+  for (int64_t o = m->lo[level]; o < m->lo[level + 1]; ++o)
+    for (int c = 0; c < 8; ++c) {
+      if (m->split[8 * o + c]) continue;
+      for (int v = 0; v < NV; ++v) tot[v] += m->U[v * N8 + 8 * o + c] * vol;
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* point-wise pieces of the Godunov scheme (Sec. 3)                          */
 /* ------------------------------------------------------------------------- */

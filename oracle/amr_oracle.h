@@ -71,6 +71,8 @@ int orc_read_cache(const orc_mesh *m, int level, uint64_t *keys);
 int orc_ghost(orc_mesh *m, int level, double *Ug);
 int orc_write(orc_mesh *m, int level, const double *U);
 void orc_totals(const orc_mesh *m, double tot[ORC_NV]);
+/* the same sum over the leaf cells of one level */
+void orc_level_totals(const orc_mesh *m, int level, double tot[ORC_NV]);
 
 /* --- time stepping (Sec. 3; stage order of Table 1) ------------------------ */
 double orc_cfl_dt(const orc_mesh *m);

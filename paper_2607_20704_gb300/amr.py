@@ -99,7 +99,7 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
            "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag",
-           "amr_regrid_flags",
+           "amr_regrid_flags", "amr_totals", "amr_hash", "amr_read_hash",
            "amr_poisson", "amr_read_phi", "amr_load_state_async", "amr_store_state_async",
            "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
@@ -171,6 +171,9 @@ def load(path: str | None = None):
             "amr_member_errors": (I, [P, P, I]),
             "amr_regrid": (I, [P, P, P]),
             "amr_regrid_flags": (I, [P, P, I64, P, P]),
+            "amr_totals": (I, [P, I, P]),
+            "amr_hash": (I, [P, I64, P, P]),
+            "amr_read_hash": (I, [P, P, P, P, I64]),
             "amr_flag": (I, [P, I, P, I64]),
             "amr_poisson": (I, [P, D, I, P]),
             "amr_read_phi": (I, [P, P, I64]),
@@ -258,7 +261,7 @@ class Mesh:
 
     def __init__(self, level=None, i=None, j=None, k=None, U=None, *, levelmin=1, levelmax=1,
                  gamma=1.4, cfl=0.8, smallr=1e-10, smallc=1e-10, precision=8, reflux=True,
-                 reindex_every_step=True, use_graphs=True, hbm_budget_bytes=0,
+                 reindex_every_step=False, use_graphs=True, hbm_budget_bytes=0,
                  hilbert_key=None, allocator="torch", stream=None, members=None, tile=0,
                  schedule=-1, refine_grad_rho=0.0, refine_grad_p=0.0, refine_mass=0.0,
                  regrid_expand=True, regrid_every_step=False, nsubgrid=-1, planar=-1):
@@ -348,6 +351,32 @@ class Mesh:
         cr, rm = C.c_int64(), C.c_int64()
         _check(load().amr_regrid(self._h, C.byref(cr), C.byref(rm)), "amr_regrid")
         return cr.value, rm.value
+
+    def totals(self, level: int = 0):
+        """FP64 totals of the leaf cells' U dx^3 (one level, or 0: all levels),
+        computed on the device in a fixed order."""
+        out = np.zeros(5, np.float64)
+        _check(load().amr_totals(self._h, int(level), _ptr(out)), "amr_totals")
+        return out
+
+    def hash(self, keys):
+        """FNV-1a 64 of each 64-bit value, evaluated by the device function
+        the hash table uses."""
+        k = np.ascontiguousarray(keys, dtype=np.uint64)
+        out = np.zeros(max(k.size, 1), np.uint64)
+        _check(load().amr_hash(self._h, int(k.size), _ptr(k), _ptr(out)), "amr_hash")
+        return out[:k.size]
+
+    def read_hash(self):
+        """The hash table as stored: (internal keys [cap], values [cap])."""
+        cap = C.c_int64()
+        L = load()
+        _check(L.amr_read_hash(self._h, C.byref(cap), None, None, 0), "amr_read_hash")
+        keys = np.zeros(cap.value, np.uint64)
+        vals = np.zeros(cap.value, np.int32)
+        _check(L.amr_read_hash(self._h, C.byref(cap), _ptr(keys), _ptr(vals), cap.value),
+               "amr_read_hash")
+        return keys, vals
 
     def regrid_flags(self, flags):
         """Regrid with the given final flags: one byte per cell of the whole

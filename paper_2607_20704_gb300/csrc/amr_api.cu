@@ -83,7 +83,8 @@ enum Kid {
   K_GRADING, K_NEIGHBOURS, K_CLAIM, K_CACHE_FINALIZE, K_NBR_FIX, K_FACES, K_CACHE_SOURCES,
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
-  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_ROCK_COMMIT, K_SWEEP, K_COUNT
+  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_ROCK_COMMIT, K_SWEEP, K_TOTALS,
+  K_FNV, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
@@ -91,7 +92,7 @@ static const char *kKernelNames[K_COUNT] = {
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
     "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
-    "rock", "rock_commit", "sweep"};
+    "rock", "rock_commit", "sweep", "totals", "fnv"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -835,7 +836,7 @@ extern "C" void amr_params_default(amr_params *p) {
   p->smallc = 1e-10;
   p->precision = 8;
   p->reflux = 1;
-  p->reindex_every_step = 1;
+  p->reindex_every_step = 0;
   p->use_graphs = 1;
   p->regrid_expand = 1;
   p->regrid_every_step = 0;
@@ -2142,6 +2143,68 @@ extern "C" amr_status amr_read(amr_handle h, int level, int64_t *n_oct_out, uint
   }
   if (U) AMR_TRY(rows_to_host(h, h->U, h->S, 8 * lo, 8 * nl, U));
   return check_device(h, "amr_read");
+}
+
+extern "C" amr_status amr_hash(amr_handle h, int64_t n, const uint64_t *keys, uint64_t *hash) {
+  if (!h || (n > 0 && (!keys || !hash))) return fail(AMR_EINVAL, "amr_hash: NULL argument");
+  if (n < 0 || n > (int64_t(1) << 28)) return fail(AMR_EINVAL, "amr_hash: n outside [0, 2^28]");
+  if (n == 0) return AMR_OK;
+  uint64_t *buf = nullptr;
+  AMR_TRY(alloc_n(h, &buf, 2 * n));
+  cudaError_t e = cudaMemcpyAsync(buf, keys, 8 * n, cudaMemcpyHostToDevice, h->s);
+  if (e == cudaSuccess) {
+    launch(h, K_FNV, k_fnv, dim3(nblocks(n)), dim3(256), (const uint64_t *)buf, n, buf + n);
+    e = cudaMemcpyAsync(hash, buf + n, 8 * n, cudaMemcpyDeviceToHost, h->s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  dev_free(h, buf);
+  if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_hash: %s", cudaGetErrorString(e));
+  return check_device(h, "amr_hash");
+}
+
+extern "C" amr_status amr_read_hash(amr_handle h, int64_t *cap_out, uint64_t *keys, int32_t *vals,
+                                    int64_t cap) {
+  if (!h || !cap_out) return fail(AMR_EINVAL, "amr_read_hash: NULL argument");
+  *cap_out = int64_t(h->hcap);
+  if ((keys || vals) && cap < int64_t(h->hcap))
+    return fail(AMR_EINVAL, "amr_read_hash: cap %lld < capacity %lld", (long long)cap, (long long)h->hcap);
+  if (keys) CUDA_TRY(cudaMemcpyAsync(keys, h->hash.key, 8 * h->hcap, cudaMemcpyDeviceToHost, h->s));
+  if (vals) CUDA_TRY(cudaMemcpyAsync(vals, h->hash.val, 4 * h->hcap, cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  return check_device(h, "amr_read_hash");
+}
+
+// FP64 conservation totals of the selected member's leaf cells (one level, or
+// every level added in ascending order); fixed grid per level size, so the
+// order of every addition is fixed.
+extern "C" amr_status amr_totals(amr_handle h, int level, double *out) {
+  if (!h || !out) return fail(AMR_EINVAL, "amr_totals: NULL argument");
+  if (level < 0 || level > kMaxLev) return fail(AMR_EINVAL, "amr_totals: level %d outside [0, %d]", level, kMaxLev);
+  const Member &m = h->mem[h->sel];
+  const int l0 = level ? level : m.lmin, l1 = level ? level : m.lmax;
+  constexpr int kMaxG = 1024;
+  double *buf = nullptr;
+  AMR_TRY(alloc_n(h, &buf, 5 * kMaxG + 5 * (kMaxLev + 1) + 5));
+  double *partial = buf, *lev = buf + 5 * kMaxG, *dout = lev + 5 * (kMaxLev + 1);
+  for (int l = l0; l <= l1; ++l) {
+    const int64_t lo = m.oct_base + m.lo[l], nl = m.lo[l + 1] - m.lo[l];
+    const int64_t n = 8 * nl;
+    const int G = int(std::max<int64_t>(1, std::min<int64_t>(kMaxG, (n + 2047) / 2048)));
+    const int64_t chunk = std::max<int64_t>(256, ((n + G - 1) / G + 255) / 256 * 256);
+    if (h->p.precision == 4)
+      launch(h, K_TOTALS, k_totals<float>, dim3(unsigned(G)), dim3(256), (const float *)h->U, h->S,
+             (const uint32_t *)h->son, 8 * lo, n, chunk, partial, G);
+    else
+      launch(h, K_TOTALS, k_totals<double>, dim3(unsigned(G)), dim3(256), (const double *)h->U, h->S,
+             (const uint32_t *)h->son, 8 * lo, n, chunk, partial, G);
+    launch(h, K_TOTALS, k_totals_sum, dim3(1), dim3(32), (const double *)partial, G, l, lev,
+           int(level == 0 && l == l1), l0, l1, dout);
+  }
+  cudaError_t e = cudaMemcpyAsync(out, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  dev_free(h, buf);
+  if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_totals: %s", cudaGetErrorString(e));
+  return check_device(h, "amr_totals");
 }
 
 extern "C" amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_t cap) {

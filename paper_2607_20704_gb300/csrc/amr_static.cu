@@ -13,7 +13,10 @@
 // loads the library holds them until the process exits (512 KiB + 8 bytes
 // per device).  Host code never dereferences their names: the device
 // address is taken once per device with cudaGetSymbolAddress (with that
-// device current) and passed to the kernel.
+// device current) and passed to the kernel.  The addresses are kept for the
+// life of the process; a cudaDeviceReset invalidates them (and the library's
+// module), so a caller that resets a device does not call this entry point
+// again in that process.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,7 +67,10 @@ __global__ void k_cfl_static(const double *__restrict__ U, int64_t n, int64_t st
     const double p = fmax((gamma - 1.0) * (u4 - ek), r * smallp);
     const double cs = sqrt(gamma * p / r);
     s = ((fabs(vx) + cs) + (fabs(vy) + cs)) + (fabs(vz) + cs);
-    if (!isfinite(s) || !isfinite(u0 + u1 + u2 + u3 + u4)) s = __longlong_as_double(0x7FF8000000000000ll);
+    // each input tested on its own: a sum of large finite values may overflow
+    if (!isfinite(s) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2) || !isfinite(u3) ||
+        !isfinite(u4))
+      s = __longlong_as_double(0x7FF8000000000000ll);
   }
   __shared__ double wmax[kBlock / 32];
   __shared__ bool last;

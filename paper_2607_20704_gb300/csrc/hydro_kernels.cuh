@@ -717,6 +717,60 @@ __global__ void k_dt(CflArgs a) {
   a.dtdxf_dev[m] = ldexpf(float(dt), lmin);
 }
 
+// ---------------------------------------------------------------------------
+// Conservation totals of one level (FP64 in both precisions, fixed order, no
+// atomics): block b sums the leaf cells of [b chunk, (b+1) chunk) of the
+// level's cells, thread t the cells b chunk + t + 256 k in increasing k, then
+// a fixed butterfly over each warp and the 8 warp sums in warp order;
+// partial[v G + b].  k_totals_sum adds a level's G partials in block order,
+// scales by dx^3 (exact: a power of two) into lev[5 l + v], and with
+// all_levels adds the levels' totals in ascending level order into out.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_totals(const T *__restrict__ U, int64_t S,
+                                                const uint32_t *__restrict__ son, int64_t c0,
+                                                int64_t n, int64_t chunk, double *partial, int G) {
+  __shared__ double ws[5][8];
+  const int64_t b0 = blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t t = b0 + threadIdx.x; t < b1; t += 256) {
+    const int64_t g = c0 + t;
+    if ((__ldg(son + (g >> 3)) >> (g & 7)) & 1u) continue;  // split: not a leaf
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += double(U[v * S + g]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[v] += __shfl_xor_sync(0xFFFFFFFFu, acc[v], off);
+    if (lane == 0) ws[v][warp] = acc[v];
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += ws[threadIdx.x][w];
+    partial[threadIdx.x * int64_t(G) + blockIdx.x] = sum;
+  }
+}
+
+__global__ void k_totals_sum(const double *partial, int G, int level, double *lev, int all_levels,
+                             int lmin, int lmax, double *out) {
+  const int v = threadIdx.x;
+  if (v >= 5) return;
+  double sum = 0.0;
+  for (int b = 0; b < G; ++b) sum += partial[v * int64_t(G) + b];
+  lev[5 * level + v] = ldexp(sum, -3 * level);
+  if (all_levels) {
+    double t = 0.0;
+    for (int l = lmin; l <= lmax; ++l) t += lev[5 * l + v];
+    out[v] = t;
+  } else {
+    out[v] = lev[5 * level + v];
+  }
+}
+
 template <class T>
 __global__ void k_to_double(const T *src, int64_t src_stride, int64_t count, double *dst) {
   const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;

@@ -344,4 +344,10 @@ __global__ void k_lookup(HashView h, const uint64_t *__restrict__ keys, int64_t 
   if ((threadIdx.x & 7) == 0) out[q] = (v >= 1 && int64_t(v) <= N) ? int64_t(v - 1) : -1;
 }
 
+// FNV-1a 64 of each value, by the function every hash insert and probe uses
+__global__ void k_fnv(const uint64_t *__restrict__ in, int64_t n, uint64_t *__restrict__ out) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q < n) out[q] = fnv1a64(in[q]);
+}
+
 }  // namespace amr

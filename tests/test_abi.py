@@ -50,7 +50,7 @@ def test_params_default(lib):
     from paper_2607_20704_gb300 import amr
     p = amr.amr_params()
     lib.amr_params_default(C.byref(p))
-    assert (p.precision, p.reflux, p.reindex_every_step, p.use_graphs) == (8, 1, 1, 1)
+    assert (p.precision, p.reflux, p.reindex_every_step, p.use_graphs) == (8, 1, 0, 1)
     assert p.gamma == 1.4 and p.cfl == 0.8 and p.smallr == 1e-10
     assert p.stream is None and p.hbm_budget_bytes == 0
 

@@ -28,13 +28,18 @@ def _l1(Ug, Uo):
     return d[0] / n[0], d[4] / n[4]
 
 
+def _leaf_terms(m, l, v):
+    """U_v dx^3 of the leaf cells of level l (host copy of the state)."""
+    _, U = m.read(l)
+    _, sp = m.read_index(l)
+    return (U[v, sp == 0] * 2.0 ** (-3 * l)).tolist()
+
+
 def _leaf_totals(m):
-    t = np.zeros(5)
-    for l in m.levels():
-        _, U = m.read(l)
-        _, sp = m.read_index(l)
-        t += U[:, sp == 0].sum(axis=1) * 2.0 ** (-3 * l)
-    return t
+    """Correctly rounded host sums of U dx^3 over the leaf cells (fsum)."""
+    import math
+    return np.array([math.fsum(x for l in m.levels() for x in _leaf_terms(m, l, v))
+                     for v in range(5)])
 
 
 def test_sod_ten_coarse_steps():
@@ -61,13 +66,21 @@ def test_sedov_fifty_coarse_steps_conserve(precision):
     momentum, energy over leaf cells, periodic box with refluxing).  The
     update conserves exactly in real arithmetic; what drifts is round-off,
     about 1e-14 of the total per level step in FP64 (energy, whose fluxes
-    are largest, measured 1.6e-12 after the 750 level steps)."""
+    are largest, measured 1.6e-12 after the 750 level steps).  The totals
+    are the device's FP64 fixed-order reduction (amr_totals) in both
+    precisions, checked once against an exact host sum of the state."""
+    import math
     from paper_2607_20704_gb300 import amr
     prob = inputs.sedov()
     g = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=precision)
-    t0 = _leaf_totals(g)
+    t0 = g.totals(0)
     g.advance(50, sync=True)
-    t1 = _leaf_totals(g)
+    t1 = g.totals(0)
+    host = _leaf_totals(g)
+    n_leaf = prob.leaf_cells()
+    for v in range(5):
+        absum = math.fsum(abs(x) for l in g.levels() for x in _leaf_terms(g, l, v))
+        assert abs(t1[v] - host[v]) <= 2 * n_leaf * 2.0 ** -53 * absum, (v, t1[v], host[v])
     sc = np.array([abs(t0[0])] * 4 + [abs(t0[4])])
     rel = np.abs(t1 - t0) / sc
     print(f"sedov 50 coarse steps, precision {precision}: relative drift {rel}")

@@ -110,6 +110,29 @@ def test_w_cycle_matches(graphs, reindex):
     compare_all(g, o, 1e-11)
 
 
+@pytest.mark.parametrize("precision", [8, 4])
+def test_reindex_only_on_change_equals_reindex_every_step(precision):
+    """Skipping the per-step index rebuild on an unchanged mesh changes
+    nothing: states and pending reflux equal the per-step rebuild bit for
+    bit after several coarse steps, a batch too, with and without graphs."""
+    from paper_2607_20704_gb300 import amr
+    probs = [_random(12, 3, 6), inputs.sedov(4, 6, radii={5: 0.15, 6: 0.08})]
+    for graphs in (True, False):
+        outs = []
+        for every in (True, False):
+            g = amr.Mesh.batch(probs, precision=precision, use_graphs=graphs,
+                               reindex_every_step=every, tile=128, schedule=0)
+            g.advance(3, sync=True)
+            o = []
+            for q in range(len(probs)):
+                g.select(q)
+                o += [g.read(l)[1] for l in g.levels()] + [g.read_reflux(l) for l in g.levels()]
+            outs.append(o)
+            g.close()
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b)
+
+
 def test_runs_repeat_bit_for_bit():
     prob = _random(8, 3, 6)
     from paper_2607_20704_gb300 import amr
