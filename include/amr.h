@@ -104,12 +104,10 @@ typedef struct {
                                per-cell passes.  All give the same results
                                bit for bit. */
   int planar;               /* with nsubgrid 1, 2 or 4: 0: stage the whole
-                               cube (the "rock" kernel; nsubgrid 4 needs
-                               precision 4); 1: sweep it along z keeping a
-                               three-plane window (the "paper" kernel);
-                               -1 (default): the autotuner's choice (with a
-                               fixed nsubgrid: rock, except nsubgrid 4 in
-                               FP64, which sweeps) */
+                               cube (the "rock" kernel); 1: sweep it along z
+                               keeping a three-plane window (the "paper"
+                               kernel); -1 (default): the autotuner's choice
+                               (with a fixed nsubgrid: rock) */
 } amr_params;
 
 /* Fills p with the defaults: levelmin = levelmax = 1, gamma = 1.4, cfl = 0.8,

@@ -83,7 +83,7 @@ enum Kid {
   K_GRADING, K_NEIGHBOURS, K_CLAIM, K_CACHE_FINALIZE, K_NBR_FIX, K_FACES, K_CACHE_SOURCES,
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
-  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_ROCK_COMMIT, K_SWEEP, K_TOTALS,
+  K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_COMMIT, K_SWEEP, K_TOTALS,
   K_FNV, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
@@ -92,7 +92,7 @@ static const char *kKernelNames[K_COUNT] = {
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
     "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
-    "rock", "rock_commit", "sweep", "totals", "fnv"};
+    "rock", "commit", "sweep", "totals", "fnv"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -109,7 +109,9 @@ struct DevBuf {
 };
 
 // level-step launch domains of a segment
-enum Dom { DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_BLOCKS = 4, DOM_COUNT = 5 };
+enum Dom {
+  DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_BLOCKS = 4, DOM_COMMIT = 5, DOM_COUNT = 6
+};
 
 // a list of segments and, per domain, its flattened tiles
 struct SegList {
@@ -461,6 +463,7 @@ static int dom_size(const Seg &s, int dom) {
     case DOM_REAL: return 8 * s.nl;
     case DOM_GHOST5: return 5 * s.ncl;
     case DOM_BLOCKS: return s.nblk;
+    case DOM_COMMIT: return ((s.flags & kSegReflux) ? 5 * s.ncl : 0) + 5 * s.nl;
     default:
       return ((s.flags & kSegReflux) ? 5 * s.ncl : 0) + ((s.flags & kSegRestrict) ? 5 * s.nl : 0);
   }
@@ -693,10 +696,12 @@ static void run_segments(amr_mesh *h, const SegList &L, bool device_dt, double d
       run_rock_ns<T, 1>(h, a, L);
     } else if (h->nsub == 2) {
       run_rock_ns<T, 2>(h, a, L);
-    } else if constexpr (sizeof(T) == 4) {
+    } else {
       run_rock_ns<T, 4>(h, a, L);
     }
-    run_list(h, K_ROCK_COMMIT, k_rock_commit<T>, a, L, DOM_REAL);
+    // new leaf states from the scratch into U, with reflux sums and restriction
+    run_list(h, K_COMMIT, k_commit_post<T>, a, L, DOM_COMMIT);
+    return;
   } else if constexpr (sizeof(T) == 4) {
     // FP32: primitives recomputed inside the predictor; each leaf cell solves
     // its six faces and updates itself
@@ -1288,14 +1293,10 @@ extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
     delete h;
     return fail(AMR_EINVAL, "amr_create: planar must be -1, 0 or 1");
   }
-  if (p->nsubgrid == 4 && p->precision == 8 && p->planar == 0) {
-    delete h;
-    return fail(AMR_EINVAL, "amr_create: nsubgrid 4 stages its cube in FP32 only (planar 1 sweeps it in FP64)");
-  }
   h->tile_size = p->tile ? p->tile : 256;
   h->persistent = p->schedule != 0;
   h->nsub = p->nsubgrid > 0 ? p->nsubgrid : 0;
-  h->planar = h->nsub > 0 && (p->planar == 1 || (p->planar == -1 && h->nsub == 4 && p->precision == 8));
+  h->planar = h->nsub > 0 && p->planar == 1;
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count < 1) h->sm_count = 1;
@@ -1486,7 +1487,6 @@ static amr_status autotune(amr_mesh *h) {
       for (int sc : scheds)
         for (int pl = 0; pl < (ns == 0 ? 1 : 2); ++pl) {
           if (h->p.nsubgrid > 0 && h->p.planar >= 0 && pl != h->p.planar) continue;
-          if (ns == 4 && pl == 0 && h->p.precision == 8) continue;  // the FP64 cube exceeds shared memory
           cands.push_back({t, sc, ns, pl == 1});
         }
   if (cands.size() == 1) {

@@ -1,27 +1,40 @@
 // rock_kernels.cuh -- the level step as one fused shared-memory kernel per
 // block of octs (the paper's "rock" kernel, Sec. 3, with `nsubgrid` NS octs
-// per axis in the inner block).
-//
-// nsubgrid 4 (a 12^3 cube, 150 KB of shared memory) exists for FP32 only:
-// in FP64 it would need 300 KB, more than an SM has.
+// per axis in the inner block), and the planar sweep (the paper's "paper"
+// kernel) further down.
 //
 // A CTA takes one block: the real octs of one (member, level) segment that
 // share an aligned NS^3 group of oct positions (consecutive in the level's
-// Hilbert order).  It stages the conservative state of the block and of one
-// ring of octs around it -- an E^3 cube of cells, E = 2 NS + 4, real or ghost
-// octs found through the 27-neighbour table -- in shared memory and does
-// the whole step there: primitives of the cube, limited slopes and the
-// Hancock predictor on the cube less its outer layer, the HLLC fluxes of
-// every face of the inner cells, and the update of the block's leaf cells
-// (with the pending reflux of coarse cells).  Coarse-fine faces fill their
-// reflux slots as in the per-cell passes.  Ring cells are staged by every
-// block that touches them and their faces are solved by both blocks, with
-// the same arithmetic, so the two sides of a face see the same flux.
+// Hilbert order).  Its cube is the block and one ring of octs around it, an
+// E^3 cube of cells (E = 2 NS + 4), real or ghost octs found through the
+// 27-neighbour table; the eight corner octs of the ring feed no face of the
+// block and are not staged.  Phases, separated by block barriers:
 //
-// The new states go to the level scratch W (other blocks still read the old
-// ones), and a second kernel copies them into U.  Every value is computed by
-// the same device functions as the per-cell passes (primitives, slopes,
-// predictor, face states, HLLC, update), so the two paths agree bit for bit.
+//   A  each thread holds one cell of the block's own octs in registers (a
+//      coalesced load in mesh order); every other oct of the cube is loaded
+//      with 16-byte vector loads, 8 cells per (oct, variable)
+//   B  primitives of every staged cell, in place
+//   C  limited slopes and the Hancock predictor of the inner IN^3 cells
+//      (IN = 2 NS; W* and three slopes kept) and of the six face rings
+//      around them, which keep only the face state they feed (W* +- dW/2
+//      towards the block)
+//   D  HLLC flux of every face of the inner cells, into the primitives'
+//      storage (no longer read); coarse-fine faces fill their reflux slots
+//   E  each thread updates its own leaf cell into the level scratch W
+//
+// Shared memory (FP32): 5 E^3 + 20 IN^3 + 30 IN^2 words, 84 KB at NS = 4 (two
+// blocks per SM), 17 KB at NS = 2.  Per inner cell at NS = 4 the block
+// computes 3.4 primitives, 1.75 predictors and 3.4 face solves, against
+// 1, 1 and 3 when each is computed once.  Ring cells are staged by every
+// block that touches them and a face between two blocks is solved by both,
+// with the same arithmetic, so both see the same flux.  Every value comes
+// from the device functions of the per-cell passes (primitives, slopes,
+// predictor, face states, HLLC, update) in the same order, so the two paths
+// agree bit for bit.
+//
+// Other blocks still read the old states of a block's cells while it runs,
+// so new states go to the level scratch W; k_commit_post copies them into U
+// together with the level's reflux sums and restriction.
 #pragma once
 #include "hydro_kernels.cuh"
 
@@ -29,20 +42,27 @@ namespace amr {
 
 template <int NS>
 struct Rock {
-  static constexpr int E = 2 * NS + 4;          // cells per axis of the staged cube
+  static constexpr int E = 2 * NS + 4;      // cells per axis of the cube
   static constexpr int C = E * E * E;
-  static constexpr int NO = NS + 2;             // octs per axis of the cube
+  static constexpr int NO = NS + 2;         // octs per axis of the cube
   static constexpr int NOC = NO * NO * NO;
-  static constexpr int QE = E - 2;              // predictor region [1, E-1)
-  static constexpr int QC = QE * QE * QE;
-  static constexpr int IN = 2 * NS;             // inner cells per axis, [2, 2 + IN)
+  static constexpr int NB = NS * NS * NS;   // oct positions of the block
+  static constexpr int IN = 2 * NS;         // inner cells per axis, cube cells [2, 2 + IN)
   static constexpr int IC = IN * IN * IN;
-  static constexpr int FP = IN + 1;             // face positions along an axis
-  static constexpr int FN = FP * IN * IN;       // faces per axis
-  static constexpr int THREADS = NS == 4 ? 512 : 256;
+  static constexpr int RC = IN * IN;        // cells of one face ring
+  static constexpr int FP = IN + 1;         // face positions along an axis
+  static constexpr int FN = FP * IN * IN;   // faces per axis
+  static constexpr int THREADS = NS == 4 ? 512 : NS == 2 ? 128 : 32;
+  static_assert(15 * FN <= 5 * C, "fluxes reuse the primitives' storage");
+  static_assert(THREADS >= 8 * NB, "one thread per cell of the block");
   template <class T>
   static constexpr size_t smem() {
-    return sizeof(T) * (5 * C + 20 * QC + 15 * FN) + 4 * NOC + 4 * NS * NS * NS + C;
+    return sizeof(T) * (5 * C + 20 * IC + 30 * RC) + 4 * (NOC + NB) + C;
+  }
+  // blocks per SM the register budget is sized for
+  template <class T>
+  static constexpr int min_blocks() {
+    return NS == 4 ? (sizeof(T) == 4 ? 2 : 1) : NS == 2 ? (sizeof(T) == 4 ? 8 : 4) : 16;
   }
 };
 
@@ -133,18 +153,72 @@ __device__ __forceinline__ uint8_t cube_cell(const StepArgs<T> &a, const int32_t
   return ty;
 }
 
-template <class T, int NS>
-__global__ void __launch_bounds__(Rock<NS>::THREADS) k_rock(StepArgs<T> a, const int32_t *__restrict__ blk) {
-  using R = Rock<NS>;
-  extern __shared__ __align__(16) unsigned char rock_smem[];
-  T *sW = reinterpret_cast<T *>(rock_smem);   // [5][C]: U, then W
-  T *sQ = sW + 5 * R::C;                      // [20][QC]: W*, dW_x, dW_y, dW_z
-  T *sF = sQ + 20 * R::QC;                    // [3][5][FN]
-  int32_t *octs = reinterpret_cast<int32_t *>(sF + 15 * R::FN);  // [NOC]
-  int32_t *opos = octs + R::NOC;                                  // [NS^3] block octs' positions
-  uint8_t *ctype = reinterpret_cast<uint8_t *>(opos + NS * NS * NS);  // [C]
-  constexpr int E = R::E, NO = R::NO, QE = R::QE, IN = R::IN, FP = R::FP, FN = R::FN;
 
+// 8 consecutive values (the cells of one oct, one variable) with 16-byte
+// loads and stores
+__device__ __forceinline__ void load_oct8(const float *p, float (&o)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+__device__ __forceinline__ void load_oct8(const double *p, double (&o)[8]) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + h);
+    o[2 * h] = a.x;
+    o[2 * h + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void store_oct8(float *p, const float (&o)[8]) {
+  reinterpret_cast<float4 *>(p)[0] = make_float4(o[0], o[1], o[2], o[3]);
+  reinterpret_cast<float4 *>(p)[1] = make_float4(o[4], o[5], o[6], o[7]);
+}
+__device__ __forceinline__ void store_oct8(double *p, const double (&o)[8]) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) reinterpret_cast<double2 *>(p)[h] = make_double2(o[2 * h], o[2 * h + 1]);
+}
+
+// the face between cube cells of kinds ta (minus side) and tb (plus side) is
+// solved when neither side is missing or split and one side is a leaf cell
+// of the block's own octs: 0 not solved, +1 / -1 a coarse-fine face with the
+// ghost on the plus / minus side, 2 otherwise
+__device__ __forceinline__ int face_kind(uint8_t ta_full, uint8_t tb_full) {
+  const uint8_t ta = ta_full & 15, tb = tb_full & 15;
+  const bool own_leaf = ta_full == (kCellLeaf | kCellOwn) || tb_full == (kCellLeaf | kCellOwn);
+  if (!(ta != kCellNone && tb != kCellNone && ta != kCellSplit && tb != kCellSplit && own_leaf)) return 0;
+  if ((ta == kCellGhost) == (tb == kCellGhost)) return 2;
+  return tb == kCellGhost ? 1 : -1;
+}
+
+template <class T>
+__device__ __forceinline__ void face_flux_dir(const SegCtx<T> &s, int D, T (&qL)[5], T (&qR)[5], T (&F)[5]) {
+  if (D == 0)
+    face_flux_states<0>(s, qL, qR, F);
+  else if (D == 1)
+    face_flux_states<1>(s, qL, qR, F);
+  else
+    face_flux_states<2>(s, qL, qR, F);
+}
+
+template <class T, int NS>
+__global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_blocks<T>())
+    k_rock(StepArgs<T> a, const int32_t *__restrict__ blk) {
+  using R = Rock<NS>;
+  constexpr int E = R::E, C = R::C, NO = R::NO, NOC = R::NOC, NB = R::NB, IN = R::IN, IC = R::IC,
+                RC = R::RC, FP = R::FP, FN = R::FN, TH = R::THREADS;
+  extern __shared__ __align__(16) unsigned char rock_smem[];
+  T *sP = reinterpret_cast<T *>(rock_smem);  // [5][C]: U, then primitives
+  T *sF = sP;                                // [3][5][FN]: fluxes (phase D on)
+  T *sQ = sP + 5 * C;                        // [20][IC]: W*, dW_x, dW_y, dW_z of inner cells
+  T *sR = sQ + 20 * IC;                      // [6][5][RC]: face states of the six rings
+  int32_t *octs = reinterpret_cast<int32_t *>(sR + 30 * RC);  // [NOC] extended oct index or -1
+  int32_t *pos_oct = octs + NOC;                               // [NB] own oct at each position
+  uint8_t *ctype = reinterpret_cast<uint8_t *>(pos_oct + NB);  // [C] kind of each cube cell
+  const int t = threadIdx.x;
+
+  for (int q = t; q < NB; q += TH) pos_oct[q] = -1;
+  __syncthreads();
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
     const Tile td = a.tiles[ti];
     const Seg sg = a.segs[td.seg];
@@ -153,125 +227,282 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS) k_rock(StepArgs<T> a, const
     const int gb = sg.blk0 + td.start;
     const int o0 = int(checked(__ldg(blk + gb), s.lo, s.lo + s.nl, a.err, s.lo));
     const int o1 = int(checked(__ldg(blk + gb + 1), o0 + 1, s.lo + s.nl + 1, a.err, o0 + 1));
+    const int nb = o1 - o0;
 
-    // 1. extended index of every oct of the cube
-    cube_octs<T, NS, R::THREADS>(a, o0, o1, opos, octs);
-
-    // 2. conservative state and kind of every cell of the cube
-    for (int q = threadIdx.x; q < R::C; q += R::THREADS) {
-      int e, c;
-      const uint8_t ty = cube_cell<T, NS>(a, octs, q % E, (q / E) % E, q / (E * E), o0, o1, e, c);
-      if (ty != kCellNone) {
-        const int64_t g = 8 * int64_t(e) + c;
+    // A. this thread's own cell: oct o0 + t/8, cell t%8 (coalesced in mesh order)
+    const bool mine = t < 8 * nb;
+    int mo = 0, mc = 0, mq = 0;
+    T u0[5];
+    if (mine) {
+      mo = o0 + (t >> 3);
+      mc = t & 7;
+      const uint64_t k = __ldg(a.key + mo);
+      const int bx = int(ikey_x(k) & (NS - 1)), by = int(ikey_y(k) & (NS - 1)), bz = int(ikey_z(k) & (NS - 1));
+      if (mc == 0) pos_oct[bx + NS * (by + NS * bz)] = mo;
+      mq = (2 + 2 * bx + (mc & 1)) + E * ((2 + 2 * by + ((mc >> 1) & 1)) + E * (2 + 2 * bz + (mc >> 2)));
+      const int64_t g = 8 * int64_t(mo) + mc;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) sW[v * R::C + q] = a.U[v * a.S + g];
-      }
-      ctype[q] = ty;
+      for (int v = 0; v < 5; ++v) u0[v] = __ldg(a.U + v * a.S + g);
     }
     __syncthreads();
 
-    // 3. primitives, in place
-    for (int q = threadIdx.x; q < R::C; q += R::THREADS) {
+    // the cube's octs: own octs from the position table; every other oct
+    // through the 27-neighbour entry of an own oct within one position
+    for (int p = t; p < NOC; p += TH) {
+      const int px = p % NO - 1, py = (p / NO) % NO - 1, pz = p / (NO * NO) - 1;
+      const int out = (px < 0 || px >= NS) + (py < 0 || py >= NS) + (pz < 0 || pz >= NS);
+      int e = -1;
+      if (out < 3) {
+        int rx = px < 0 ? 0 : px >= NS ? NS - 1 : px;
+        int ry = py < 0 ? 0 : py >= NS ? NS - 1 : py;
+        int rz = pz < 0 ? 0 : pz >= NS ? NS - 1 : pz;
+        int ob = pos_oct[rx + NS * (ry + NS * rz)];
+        if (ob < 0) {  // a partial block: any own oct within one position
+          for (int d = 0; d < 27 && ob < 0; ++d) {
+            const int qx = px + d % 3 - 1, qy = py + (d / 3) % 3 - 1, qz = pz + d / 9 - 1;
+            if (qx < 0 || qx >= NS || qy < 0 || qy >= NS || qz < 0 || qz >= NS) continue;
+            const int c = pos_oct[qx + NS * (qy + NS * qz)];
+            if (c >= 0) {
+              ob = c;
+              rx = qx;
+              ry = qy;
+              rz = qz;
+            }
+          }
+        }
+        if (ob >= 0) {
+          if (rx == px && ry == py && rz == pz) {
+            e = ob;
+          } else {
+            const int dir = (pz - rz + 1) * 9 + (py - ry + 1) * 3 + (px - rx + 1);
+            e = int(checked(__ldg(a.nbr27 + dir * int64_t(a.N) + ob), -1, a.NE, a.err, -1));
+          }
+        }
+      }
+      octs[p] = e;
+    }
+    __syncthreads();
+
+    // conservative states of the cube and the kind of every cube cell
+    if (mine) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sP[v * C + mq] = u0[v];
+    }
+    for (int idx = t; idx < 5 * NOC; idx += TH) {
+      const int v = idx / NOC, p = idx - v * NOC;
+      const int e = octs[p];
+      const int px = p % NO, py = (p / NO) % NO, pz = p / (NO * NO);
+      const bool inner = px >= 1 && px <= NS && py >= 1 && py <= NS && pz >= 1 && pz <= NS;
+      if (e < 0 || (inner && e >= o0 && e < o1)) continue;  // missing, or held by its own thread
+      T val[8];
+      load_oct8(a.U + v * a.S + 8 * int64_t(e), val);
+      const int q0 = 2 * px + E * (2 * py + E * 2 * pz);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) sP[v * C + q0 + (c & 1) + E * (((c >> 1) & 1) + E * (c >> 2))] = val[c];
+    }
+    for (int p = t; p < NOC; p += TH) {
+      const int e = octs[p];
+      const int px = p % NO, py = (p / NO) % NO, pz = p / (NO * NO);
+      const int q0 = 2 * px + E * (2 * py + E * 2 * pz);
+      const uint32_t sm = (e >= 0 && e < a.N) ? __ldg(a.son + e) : 0u;
+      const uint8_t own = (e >= o0 && e < o1) ? uint8_t(kCellOwn) : uint8_t(0);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        uint8_t ty = kCellNone;
+        if (e >= a.N)
+          ty = kCellGhost;
+        else if (e >= 0)
+          ty = uint8_t(((sm >> c) & 1u) ? kCellSplit : kCellLeaf) | own;
+        ctype[q0 + (c & 1) + E * (((c >> 1) & 1) + E * (c >> 2))] = ty;
+      }
+    }
+    __syncthreads();
+
+    // B. primitives, in place
+    for (int q = t; q < C; q += TH) {
       if (ctype[q] == kCellNone) continue;
       T w[5];
-      prim_of(s, sW[q], sW[R::C + q], sW[2 * R::C + q], sW[3 * R::C + q], sW[4 * R::C + q], w);
+      prim_of(s, sP[q], sP[C + q], sP[2 * C + q], sP[3 * C + q], sP[4 * C + q], w);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sW[v * R::C + q] = w[v];
+      for (int v = 0; v < 5; ++v) sP[v * C + q] = w[v];
     }
     __syncthreads();
 
-    // 4. slopes and predictor on [1, E-1)^3; a slope along an axis with a
-    // missing neighbour is zero (such cells feed no face of the block)
-    for (int q = threadIdx.x; q < R::QC; q += R::THREADS) {
-      const int x = 1 + q % QE, y = 1 + (q / QE) % QE, z = 1 + q / (QE * QE);
+    // C. slopes and predictor: inner cells g < IC (cube order), then the six
+    // face rings (side = 2 D + plus), transverse cells j + IN k
+    for (int g = t; g < IC + 6 * RC; g += TH) {
+      int x, y, z, side = -1, rr = 0;
+      if (g < IC) {
+        x = 2 + g % IN;
+        y = 2 + (g / IN) % IN;
+        z = 2 + g / (IN * IN);
+      } else {
+        side = (g - IC) / RC;
+        rr = (g - IC) - side * RC;
+        const int D = side >> 1, along = (side & 1) ? 2 + IN : 1;
+        const int j = 2 + rr % IN, k = 2 + rr / IN;
+        x = D == 0 ? along : j;
+        y = D == 1 ? along : (D == 0 ? j : k);
+        z = D == 2 ? along : k;
+      }
       const int cq = x + E * (y + E * z);
-      if (ctype[cq] == kCellNone) continue;
+      const uint8_t ty = ctype[cq] & 15;
+      if (ty == kCellNone || ty == kCellSplit) continue;  // feeds no solved face
       T w[5], dw[3][5], ws[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) w[v] = sW[v * R::C + cq];
-      const int st[3] = {1, E, E * E};
+      for (int v = 0; v < 5; ++v) w[v] = sP[v * C + cq];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const int cm = cq - st[d], cp = cq + st[d];
-        if (ctype[cm] == kCellNone || ctype[cp] == kCellNone) {
+        const int st = d == 0 ? 1 : d == 1 ? E : E * E;
+        if (ctype[cq - st] == kCellNone || ctype[cq + st] == kCellNone) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
           continue;
         }
 #pragma unroll
-        for (int v = 0; v < 5; ++v) dw[d][v] = minmod(sW[v * R::C + cp] - w[v], w[v] - sW[v * R::C + cm]);
+        for (int v = 0; v < 5; ++v) dw[d][v] = minmod(sP[v * C + cq + st] - w[v], w[v] - sP[v * C + cq - st]);
       }
       predictor(s, w, dw, ws);
+      if (side < 0) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sQ[v * R::QC + q] = ws[v];
+        for (int v = 0; v < 5; ++v) sQ[v * IC + g] = ws[v];
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
+        for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) sQ[(5 + 5 * d + v) * R::QC + q] = dw[d][v];
+          for (int v = 0; v < 5; ++v) sQ[(5 + 5 * d + v) * IC + g] = dw[d][v];
+      } else {
+        const int D = side >> 1;
+        T dd[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dd[v] = D == 0 ? dw[0][v] : D == 1 ? dw[1][v] : dw[2][v];
+        // the minus ring feeds the left state of face 0, the plus ring the
+        // right state of face IN
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          sR[(5 * side + v) * RC + rr] = (side & 1) ? ws[v] - T(0.5) * dd[v] : ws[v] + T(0.5) * dd[v];
+      }
     }
     __syncthreads();
 
-    // 5. fluxes of the faces of the inner cells: along axis D, face i lies
-    // between cube cells 1 + i and 2 + i; a face is solved when one side is
-    // a leaf cell of the block's own octs and neither side is split
-    for (int f = threadIdx.x; f < 3 * FN; f += R::THREADS) {
+    // D. fluxes: along axis D, face i lies between inner cells i - 1 and i
+    // (cube cells 1 + i and 2 + i); transverse inner coordinates j, k
+    for (int f = t; f < 3 * FN; f += TH) {
       const int D = f / FN, r = f - D * FN;
-      const int i = r % FP, j = 2 + (r / FP) % IN, k = 2 + r / (FP * IN);
-      int am[3], bm[3];
-      am[D] = 1 + i;
-      bm[D] = 2 + i;
-      am[D == 0 ? 1 : 0] = bm[D == 0 ? 1 : 0] = j;
-      am[D == 2 ? 1 : 2] = bm[D == 2 ? 1 : 2] = k;
-      const int ca = am[0] + E * (am[1] + E * am[2]), cb = bm[0] + E * (bm[1] + E * bm[2]);
-      const int qa = (am[0] - 1) + QE * ((am[1] - 1) + QE * (am[2] - 1));
-      const int qb = (bm[0] - 1) + QE * ((bm[1] - 1) + QE * (bm[2] - 1));
-      T F[5];
-      const int kind = solve_face(s, D, sQ + qa, sQ + qb, R::QC, ctype[ca], ctype[cb], F);
-      if (a.reflux && (kind == 1 || kind == -1)) {
-        const int cg = kind > 0 ? cb : ca;
-        const int gx = cg % E, gy = (cg / E) % E, gz = cg / (E * E);
-        const int eg = octs[(gx >> 1) + NO * ((gy >> 1) + NO * (gz >> 1))];
-        reflux_write(a, s, D, eg, (am[0] & 1) | ((am[1] & 1) << 1) | ((am[2] & 1) << 2), kind, F);
+      const int i = r % FP, j = (r / FP) % IN, k = r / (FP * IN);
+      const int ma = 1 + i, tj = 2 + j, tk = 2 + k;
+      const int xa = D == 0 ? ma : tj, ya = D == 1 ? ma : (D == 0 ? tj : tk), za = D == 2 ? ma : tk;
+      const int st = D == 0 ? 1 : D == 1 ? E : E * E;
+      const int ca = xa + E * (ya + E * za), cb = ca + st;
+      T F[5] = {T(0), T(0), T(0), T(0), T(0)};
+      const int kind = face_kind(ctype[ca], ctype[cb]);
+      if (kind) {
+        T qL[5], qR[5];
+        const int rr = j + IN * k;
+        if (i == 0) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qL[v] = sR[(5 * (2 * D) + v) * RC + rr];
+        } else {
+          const int qa = (xa - 2) + IN * ((ya - 2) + IN * (za - 2));
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qL[v] = sQ[v * IC + qa] + T(0.5) * sQ[(5 + 5 * D + v) * IC + qa];
+        }
+        if (i == IN) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qR[v] = sR[(5 * (2 * D + 1) + v) * RC + rr];
+        } else {
+          const int qb = (xa - 2 + (D == 0)) + IN * ((ya - 2 + (D == 1)) + IN * (za - 2 + (D == 2)));
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qR[v] = sQ[v * IC + qb] - T(0.5) * sQ[(5 + 5 * D + v) * IC + qb];
+        }
+        face_flux_dir(s, D, qL, qR, F);
+        if (a.reflux && (kind == 1 || kind == -1)) {
+          const int cg = kind > 0 ? cb : ca;
+          const int gx = cg % E, gy = (cg / E) % E, gz = cg / (E * E);
+          const int eg = octs[(gx >> 1) + NO * ((gy >> 1) + NO * (gz >> 1))];
+          reflux_write(a, s, D, eg, (xa & 1) | ((ya & 1) << 1) | ((za & 1) << 2), kind, F);
+        }
       }
+      // sF aliases sP, whose last reads (phase C) ended at the barrier above
 #pragma unroll
       for (int v = 0; v < 5; ++v) sF[(5 * D + v) * FN + r] = F[v];
     }
     __syncthreads();
 
-    // 6. the block's leaf cells: new state into the level scratch W
-    for (int q = threadIdx.x; q < R::IC; q += R::THREADS) {
-      const int x = 2 + q % IN, y = 2 + (q / IN) % IN, z = 2 + q / (IN * IN);
-      const int cq = x + E * (y + E * z);
-      if (ctype[cq] != (kCellLeaf | kCellOwn)) continue;
-      const int e = octs[(x >> 1) + NO * ((y >> 1) + NO * (z >> 1))];
-      const int c = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
-      const int m[3] = {x, y, z};
+    // E. update of this thread's own cell, if it is a leaf, into W
+    for (int q = t; q < NB; q += TH) pos_oct[q] = -1;  // for the next block
+    if (mine && ctype[mq] == (kCellLeaf | kCellOwn)) {
+      const int xi = mq % E - 2, yi = (mq / E) % E - 2, zi = mq / (E * E) - 2;
+      const int rf[3] = {xi + FP * (yi + IN * zi), yi + FP * (xi + IN * zi), zi + FP * (xi + IN * yi)};
       T du[3][5];
 #pragma unroll
-      for (int D = 0; D < 3; ++D) {
-        // faces of the cell along D: minus face i = m - 2, plus face i = m - 1
-        const int t1 = D == 0 ? y : x, t2 = D == 2 ? y : z;
-        const int rm = (m[D] - 2) + FP * ((t1 - 2) + IN * (t2 - 2));
+      for (int D = 0; D < 3; ++D)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) du[D][v] = sF[(5 * D + v) * FN + rm] - sF[(5 * D + v) * FN + rm + 1];
+        for (int v = 0; v < 5; ++v) du[D][v] = sF[(5 * D + v) * FN + rf[D]] - sF[(5 * D + v) * FN + rf[D] + 1];
+      const int64_t g = 8 * int64_t(mo) + mc;
+      const int rs = int(checked(__ldg(a.rslot + g), -1, a.NC, a.err, -1));
+      T *out = a.W + s.base + 8 * (mo - s.lo) + mc;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        T u = u0[v] + s.dtdx * ((du[0][v] + du[1][v]) + du[2][v]);
+        if (rs >= 0) {
+          T *Rv = a.Rc + v * int64_t(a.NC) + rs;
+          u = u + *Rv;
+          *Rv = T(0);
+        }
+        out[v * a.LS] = u;
       }
-      const int t = 8 * (e - s.lo) + c;
-      update_cell_to(a, s, 8 * e + c, du[0], du[1], du[2], a.W + s.base + t, int64_t(a.LS));
     }
     __syncthreads();
   }
 }
 
-// the new states of the leaf cells, from the level scratch into U
-// domain: 8 nl (real cells)
+// After a fused kernel: the new states of the level's leaf cells from the
+// scratch W into U, the reflux sums of the level's ghost octs and the
+// restriction onto the father cells (what k_reflux_restrict does after the
+// per-cell passes, with the commit folded in).  Thread per (oct, variable):
+// 8 values in, 8 out, the restriction from the same 8 values.
+// domain: 5 ncl (if kSegReflux) + 5 nl
 template <class T>
-__global__ void k_rock_commit(StepArgs<T> a) {
-  tile_loop(a, [](const SegCtx<T> &s) { return 8 * s.nl; }, [&](const SegCtx<T> &s, int t) {
-    if (cell_is_split(a, s, t)) return;
-    const int64_t g = 8 * int64_t(s.lo + (t >> 3)) + (t & 7);
+__global__ void k_commit_post(StepArgs<T> a) {
+  tile_loop(a,
+            [](const SegCtx<T> &s) { return ((s.flags & kSegReflux) ? 5 * s.ncl : 0) + 5 * s.nl; },
+            [&](const SegCtx<T> &s, int q) {
+              const int nref = (s.flags & kSegReflux) ? 5 * s.ncl : 0;
+              if (q < nref) {
+                const int v = q / s.ncl;
+                const int g = s.clo + (q - v * s.ncl);
+                const T *cv = a.C + v * a.CS + 24 * int64_t(g);
+                T *Rv = a.Rc + v * int64_t(a.NC) + g;
+                T acc = *Rv;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) a.U[v * a.S + g] = a.W[v * a.LS + s.base + t];
-  });
+                for (int k = 0; k < 24; ++k) acc += cv[k];
+                *Rv = acc;
+                return;
+              }
+              const int r = q - nref;
+              const int v = r / s.nl;
+              const int ol = r - v * s.nl;
+              const int o = s.lo + ol;
+              const uint32_t sm = __ldg(a.son + o);
+              T *u = a.U + v * a.S + 8 * int64_t(o);
+              T val[8];
+              load_oct8(a.W + v * a.LS + s.base + 8 * ol, val);  // leaf cells: new states
+              if (sm) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                  if ((sm >> c) & 1u) val[c] = u[c];  // split cells keep their restricted value
+              }
+              store_oct8(u, val);
+              if (s.flags & kSegRestrict) {
+                const uint64_t k = __ldg(a.key + o);
+                const int fc = int((ikey_x(k) & 1) | ((ikey_y(k) & 1) << 1) | ((ikey_z(k) & 1) << 2));
+                const int f = int(checked(__ldg(a.father + o), 0, a.N, a.err));
+                T sum = T(0);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) sum += val[c];
+                a.U[v * a.S + 8 * int64_t(f) + fc] = sum * T(0.125);
+              }
+            });
 }
 
 }  // namespace amr

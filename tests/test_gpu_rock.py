@@ -1,6 +1,5 @@
-"""The fused shared-memory level steps (the paper's rock kernel, Sec. 3, with
-nsubgrid 1 and 2, and 4 in FP32; its planar "paper" kernel with nsubgrid 1,
-2 and 4) against the per-cell passes: states, pending reflux and
+"""The fused shared-memory level steps (the paper's rock kernel, Sec. 3, and
+its planar "paper" kernel, each with nsubgrid 1, 2 and 4) against the per-cell passes: states, pending reflux and
 ghost values equal bit for bit in FP64 and FP32, for single level steps,
 W-cycles, batches and regrids, also with caller-given sort keys that split
 the aligned oct groups into several blocks; and against the oracle."""
@@ -48,7 +47,7 @@ def _mesh(prob, **kw):
     return amr.Mesh(*prob.mesh_args(), **prob.params(), **kw)
 
 
-@pytest.mark.parametrize("precision,ns,planar", [(8, 1, 0), (8, 2, 0), (4, 1, 0), (4, 2, 0), (4, 4, 0),
+@pytest.mark.parametrize("precision,ns,planar", [(8, 1, 0), (8, 2, 0), (8, 4, 0), (4, 1, 0), (4, 2, 0), (4, 4, 0),
                                                 (8, 1, 1), (8, 2, 1), (8, 4, 1), (4, 2, 1), (4, 4, 1)])
 def test_level_steps_equal_the_per_cell_passes(ns, planar, precision):
     for prob in _problems():
@@ -66,7 +65,8 @@ def test_level_steps_equal_the_per_cell_passes(ns, planar, precision):
 
 
 @pytest.mark.parametrize("precision,ns,schedule,planar", [
-    (8, 1, 0, 0), (8, 2, 1, 0), (8, 2, 0, 0), (4, 1, 0, 0), (4, 2, 1, 0), (4, 4, 1, 0), (4, 4, 0, 0),
+    (8, 1, 0, 0), (8, 2, 1, 0), (8, 2, 0, 0), (8, 4, 1, 0), (4, 1, 0, 0), (4, 2, 1, 0), (4, 4, 1, 0),
+    (4, 4, 0, 0),
     (8, 1, 1, 1), (8, 2, 0, 1), (8, 4, 1, 1), (4, 2, 1, 1), (4, 4, 0, 1)])
 def test_w_cycles_equal_the_per_cell_passes(ns, schedule, planar, precision):
     for prob in _problems()[:3]:
@@ -79,7 +79,8 @@ def test_w_cycles_equal_the_per_cell_passes(ns, schedule, planar, precision):
         rk.close()
 
 
-@pytest.mark.parametrize("ns,precision,planar", [(1, 8, 0), (2, 8, 0), (4, 4, 0), (2, 8, 1), (4, 8, 1)])
+@pytest.mark.parametrize("ns,precision,planar", [(1, 8, 0), (2, 8, 0), (4, 4, 0), (4, 8, 0), (2, 8, 1),
+                                                 (4, 8, 1)])
 def test_split_oct_groups_with_caller_keys(ns, precision, planar):
     """Random sort keys scatter each aligned oct group over several runs, so
     one group forms several blocks; each updates only its own octs."""
@@ -92,7 +93,7 @@ def test_split_oct_groups_with_caller_keys(ns, precision, planar):
     _same(ref, rk, ("caller keys", ns))
 
 
-@pytest.mark.parametrize("ns,planar", [(1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("ns,planar", [(1, 0), (2, 0), (4, 0), (2, 1)])
 def test_batched_and_regridded_meshes(ns, planar):
     from paper_2607_20704_gb300 import amr
     probs = [inputs.sod(3, 5), inputs.random_mesh(3, 5, seed=44), inputs.sedov(4, 5, radii={5: 0.15})]
@@ -113,7 +114,7 @@ def test_batched_and_regridded_meshes(ns, planar):
         b.close()
 
 
-@pytest.mark.parametrize("ns,planar", [(1, 0), (2, 0), (2, 1), (4, 1)])
+@pytest.mark.parametrize("ns,planar", [(1, 0), (2, 0), (4, 0), (2, 1), (4, 1)])
 def test_fused_kernel_matches_the_oracle(ns, planar):
     prob = inputs.random_mesh(3, 6, seed=45)
     g, o = pair(prob, gpu_kw=dict(nsubgrid=ns, planar=planar, tile=128, schedule=1))
@@ -138,10 +139,11 @@ def test_autotuner_choice_is_reported_and_exact(precision):
 def test_bad_nsubgrid_is_refused():
     from paper_2607_20704_gb300 import amr
     prob = inputs.sod(3, 4)
-    for bad, prec, planar in ((3, 8, -1), (-2, 8, -1), (4, 8, 0), (8, 4, -1), (2, 8, 2)):
+    for bad, prec, planar in ((3, 8, -1), (-2, 8, -1), (8, 4, -1), (2, 8, 2)):
         with pytest.raises(amr.AmrError) as e:
             _mesh(prob, nsubgrid=bad, precision=prec, planar=planar)
         assert e.value.status == amr.AMR_EINVAL
-    m = _mesh(prob, nsubgrid=4, precision=8)  # nsubgrid 4 in FP64 sweeps planes
-    assert m.info()["planar"] == 1
-    m.close()
+    for prec in (8, 4):  # a fixed nsubgrid stages the cube unless planar is asked for
+        m = _mesh(prob, nsubgrid=4, precision=prec)
+        assert m.info()["planar"] == 0
+        m.close()
