@@ -201,6 +201,14 @@ __device__ __forceinline__ void face_flux_dir(const SegCtx<T> &s, int D, T (&qL)
     face_flux_states<2>(s, qL, qR, F);
 }
 
+// cube oct position (px, py, pz) (0-based, the block at 1..NS) is the home
+// of own oct e: the position the oct's coordinates give
+template <int NS>
+__device__ __forceinline__ bool home_of(const int32_t *pos_oct, int px, int py, int pz, int e) {
+  if (px < 1 || px > NS || py < 1 || py > NS || pz < 1 || pz > NS) return false;
+  return pos_oct[(px - 1) + NS * ((py - 1) + NS * (pz - 1))] == e;
+}
+
 template <class T, int NS>
 __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_blocks<T>())
     k_rock(StepArgs<T> a, const int32_t *__restrict__ blk) {
@@ -288,12 +296,13 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
 #pragma unroll
       for (int v = 0; v < 5; ++v) sP[v * C + mq] = u0[v];
     }
+    // (an own oct met again elsewhere in the cube, through the periodic wrap
+    // of a level narrower than the block, is staged like any other oct)
     for (int idx = t; idx < 5 * NOC; idx += TH) {
       const int v = idx / NOC, p = idx - v * NOC;
       const int e = octs[p];
       const int px = p % NO, py = (p / NO) % NO, pz = p / (NO * NO);
-      const bool inner = px >= 1 && px <= NS && py >= 1 && py <= NS && pz >= 1 && pz <= NS;
-      if (e < 0 || (inner && e >= o0 && e < o1)) continue;  // missing, or held by its own thread
+      if (e < 0 || home_of<NS>(pos_oct, px, py, pz, e)) continue;  // missing, or held by its own thread
       T val[8];
       load_oct8(a.U + v * a.S + 8 * int64_t(e), val);
       const int q0 = 2 * px + E * (2 * py + E * 2 * pz);
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
       const int px = p % NO, py = (p / NO) % NO, pz = p / (NO * NO);
       const int q0 = 2 * px + E * (2 * py + E * 2 * pz);
       const uint32_t sm = (e >= 0 && e < a.N) ? __ldg(a.son + e) : 0u;
-      const uint8_t own = (e >= o0 && e < o1) ? uint8_t(kCellOwn) : uint8_t(0);
+      const uint8_t own = (e >= 0 && home_of<NS>(pos_oct, px, py, pz, e)) ? uint8_t(kCellOwn) : uint8_t(0);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         uint8_t ty = kCellNone;

@@ -147,3 +147,25 @@ def test_bad_nsubgrid_is_refused():
         m = _mesh(prob, nsubgrid=4, precision=prec)
         assert m.info()["planar"] == 0
         m.close()
+
+
+@pytest.mark.parametrize("precision", [8, 4])
+def test_levels_narrower_than_the_block(precision):
+    """Levels of 1, 2 and 4 octs per side with nsubgrid up to 4: the block
+    meets its own octs again across the periodic wrap; results equal the
+    per-cell passes bit for bit."""
+    rng = np.random.default_rng(7)
+    for lev in (1, 2, 3):
+        def fn(x, y, z):
+            return (1.0 + 0.5 * rng.random(x.shape), rng.standard_normal(x.shape),
+                    rng.standard_normal(x.shape), rng.standard_normal(x.shape),
+                    0.5 + rng.random(x.shape))
+        prob = inputs.uniform_grid(lev, fn)
+        for ns in (1, 2, 4):
+            ref = _mesh(prob, precision=precision, nsubgrid=0, tile=128, schedule=0)
+            rk = _mesh(prob, precision=precision, nsubgrid=ns, planar=0, tile=128, schedule=0)
+            ref.advance(2, sync=True)
+            rk.advance(2, sync=True)
+            _same(ref, rk, ("narrow level", lev, ns, precision))
+            ref.close()
+            rk.close()
