@@ -367,6 +367,29 @@ def run_unigrid(level, steps, torch, device):
             "coarse_step_ms": round(cms, 4), "coarse_step_cell_updates_per_s": n ** 3 / (cms * 1e-3),
             "tile": inf["tile"], "schedule": inf["schedule"], "nsubgrid": inf["nsubgrid"]}
         m.close()
+        # each level-step kernel on its own: the per-cell passes and the rock
+        # kernel with nsubgrid 2 and 4 (fixed launch shapes, no autotuning)
+        kern = []
+        for ns, tile, sched in ((0, 256, 0), (2, 128, 0), (4, 128, 0)):
+            m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=prec, stream=bench_stream(),
+                         nsubgrid=ns, planar=0, tile=tile, schedule=sched)
+            st = m.stream
+            m.advance(1, sync=True)
+            dt = m.cfl_dt() * 1e-3
+            lv = []
+            for _ in range(steps):
+                e0, e1 = ev()
+                e0.record(st)
+                m.step_level(level, dt)
+                e1.record(st)
+                torch.cuda.synchronize(device)
+                lv.append(e0.elapsed_time(e1))
+            lms = float(np.median(lv))
+            kern.append({"nsubgrid": ns, "planar": 0, "tile": tile, "schedule": sched,
+                         "level_step_ms": round(lms, 4),
+                         "level_step_cell_updates_per_s": n ** 3 / (lms * 1e-3)})
+            m.close()
+        out["fp64" if prec == 8 else "fp32"]["kernels"] = kern
     out["paper_context"] = ("H200, FP32 with fast math, unigrid Sedov, Godunov only: rock kernel "
                             "nsubgrid 4 0.09 ns per cell (11.1e9 /s), paper kernel 0.2 ns (5e9 /s)")
     return out

@@ -394,10 +394,26 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     __syncthreads();
 
     // D. fluxes: along axis D, face i lies between inner cells i - 1 and i
-    // (cube cells 1 + i and 2 + i); transverse inner coordinates j, k
+    // (cube cells 1 + i and 2 + i); transverse inner coordinates j, k (the
+    // lower axis first).  Faces are numbered x fastest for every axis, so a
+    // warp reads consecutive shared-memory words: r = i + FP (j + IN k) along
+    // x, j + IN (i + FP k) along y, j + IN (k + IN i) along z.
     for (int f = t; f < 3 * FN; f += TH) {
       const int D = f / FN, r = f - D * FN;
-      const int i = r % FP, j = (r / FP) % IN, k = r / (FP * IN);
+      int i, j, k;
+      if (D == 0) {
+        i = r % FP;
+        j = (r / FP) % IN;
+        k = r / (FP * IN);
+      } else if (D == 1) {
+        j = r % IN;
+        i = (r / IN) % FP;
+        k = r / (IN * FP);
+      } else {
+        j = r % IN;
+        k = (r / IN) % IN;
+        i = r / RC;
+      }
       const int ma = 1 + i, tj = 2 + j, tk = 2 + k;
       const int xa = D == 0 ? ma : tj, ya = D == 1 ? ma : (D == 0 ? tj : tk), za = D == 2 ? ma : tk;
       const int st = D == 0 ? 1 : D == 1 ? E : E * E;
@@ -441,12 +457,16 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     for (int q = t; q < NB; q += TH) pos_oct[q] = -1;  // for the next block
     if (mine && ctype[mq] == (kCellLeaf | kCellOwn)) {
       const int xi = mq % E - 2, yi = (mq / E) % E - 2, zi = mq / (E * E) - 2;
-      const int rf[3] = {xi + FP * (yi + IN * zi), yi + FP * (xi + IN * zi), zi + FP * (xi + IN * yi)};
+      // the cell's minus faces (face i = its coordinate) and the plus faces
+      // one face position further
+      const int rf[3] = {xi + FP * (yi + IN * zi), xi + IN * (yi + FP * zi), xi + IN * (yi + IN * zi)};
+      constexpr int rp[3] = {1, IN, RC};
       T du[3][5];
 #pragma unroll
       for (int D = 0; D < 3; ++D)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) du[D][v] = sF[(5 * D + v) * FN + rf[D]] - sF[(5 * D + v) * FN + rf[D] + 1];
+        for (int v = 0; v < 5; ++v)
+          du[D][v] = sF[(5 * D + v) * FN + rf[D]] - sF[(5 * D + v) * FN + rf[D] + rp[D]];
       const int64_t g = 8 * int64_t(mo) + mc;
       const int rs = int(checked(__ldg(a.rslot + g), -1, a.NC, a.err, -1));
       T *out = a.W + s.base + 8 * (mo - s.lo) + mc;
