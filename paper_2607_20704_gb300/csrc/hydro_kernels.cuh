@@ -38,11 +38,10 @@ __device__ __forceinline__ double minmod(double a, double b) {
   if (((ia ^ ib) < 0) | (ma == 0) | (mb == 0)) return 0.0;
   return ma < mb ? a : b;
 }
+// FP32: the definition as written, 0 when a b <= 0 (the FP32 pipes have room)
 __device__ __forceinline__ float minmod(float a, float b) {
-  const int ia = __float_as_int(a), ib = __float_as_int(b);
-  const int ma = ia & 0x7FFFFFFF, mb = ib & 0x7FFFFFFF;
-  if (((ia ^ ib) < 0) | (ma == 0) | (mb == 0)) return 0.0f;
-  return ma < mb ? a : b;
+  const float m = fabsf(a) < fabsf(b) ? a : b;
+  return a * b > 0.0f ? m : 0.0f;
 }
 // FP64 compares, min and max decided on the bit patterns: GB300's FP64 pipe
 // is 1/64 of its FP32 rate and these kernels are bound by it, while the
@@ -387,7 +386,25 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   const T us = ((rcr * ur + rcl * ul) + (pl - pr)) * irc;
   const T ps = ((rcr * pl + rcl * pr) + rcl * rcr * (ul - ur)) * irc;
   T ro, uo, po, eo, v1, v2;
-  if (pos(sl)) {
+  if constexpr (sizeof(T) == 4) {
+    // FP32: the same four cases without divergent branches.  The sampled
+    // side K is the left one when S_L > 0 or u* > 0; its star state is taken
+    // when S_L <= 0 (left) or S_R > 0 (right), with the same arithmetic as
+    // the branches below.
+    const bool left = pos(sl) || pos(us);
+    const bool star = left ? !pos(sl) : pos(sr);
+    const T rk = left ? rl : rr, uk = left ? ul : ur, pk = left ? pl : pr, ek = left ? el : er;
+    const T sk = left ? sl : sr;
+    v1 = left ? qL[t1] : qR[t1];
+    v2 = left ? qL[t2] : qR[t2];
+    const T id = rcp(sk - us);
+    const T rs = rk * (sk - uk) * id;
+    const T es = ((sk - uk) * ek - pk * uk + ps * us) * id;
+    ro = star ? rs : rk;
+    eo = star ? es : ek;
+    uo = star ? us : uk;
+    po = star ? ps : pk;
+  } else if (pos(sl)) {
     ro = rl; uo = ul; po = pl; eo = el; v1 = qL[t1]; v2 = qL[t2];
   } else if (pos(us)) {
     const T id = rcp(sl - us);

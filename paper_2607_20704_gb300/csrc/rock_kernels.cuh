@@ -50,10 +50,9 @@ struct Rock {
   static constexpr int IN = 2 * NS;         // inner cells per axis, cube cells [2, 2 + IN)
   static constexpr int IC = IN * IN * IN;
   static constexpr int RC = IN * IN;        // cells of one face ring
-  static constexpr int FP = IN + 1;         // face positions along an axis
-  static constexpr int FN = FP * IN * IN;   // faces per axis
+  static constexpr int FS = IC + RC;        // faces per axis: inner cells' minus faces + last layer
   static constexpr int THREADS = NS == 4 ? 512 : NS == 2 ? 128 : 32;
-  static_assert(15 * FN <= 5 * C, "fluxes reuse the primitives' storage");
+  static_assert(15 * FS <= 5 * C, "fluxes reuse the primitives' storage");
   static_assert(THREADS >= 8 * NB, "one thread per cell of the block");
   template <class T>
   static constexpr size_t smem() {
@@ -201,23 +200,16 @@ __device__ __forceinline__ void face_flux_dir(const SegCtx<T> &s, int D, T (&qL)
     face_flux_states<2>(s, qL, qR, F);
 }
 
-// cube oct position (px, py, pz) (0-based, the block at 1..NS) is the home
-// of own oct e: the position the oct's coordinates give
-template <int NS>
-__device__ __forceinline__ bool home_of(const int32_t *pos_oct, int px, int py, int pz, int e) {
-  if (px < 1 || px > NS || py < 1 || py > NS || pz < 1 || pz > NS) return false;
-  return pos_oct[(px - 1) + NS * ((py - 1) + NS * (pz - 1))] == e;
-}
-
 template <class T, int NS>
 __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_blocks<T>())
     k_rock(StepArgs<T> a, const int32_t *__restrict__ blk) {
   using R = Rock<NS>;
   constexpr int E = R::E, C = R::C, NO = R::NO, NOC = R::NOC, NB = R::NB, IN = R::IN, IC = R::IC,
-                RC = R::RC, FP = R::FP, FN = R::FN, TH = R::THREADS;
+                RC = R::RC, FS = R::FS, TH = R::THREADS;
+  constexpr int LIN = NS == 4 ? 3 : NS == 2 ? 2 : 1;  // log2(IN)
   extern __shared__ __align__(16) unsigned char rock_smem[];
-  T *sP = reinterpret_cast<T *>(rock_smem);  // [5][C]: U, then primitives
-  T *sF = sP;                                // [3][5][FN]: fluxes (phase D on)
+  T *sP = reinterpret_cast<T *>(rock_smem);  // [5][C]: primitives of the cube
+  T *sF = sP;                                // [3][5][FS]: fluxes (phase D on)
   T *sQ = sP + 5 * C;                        // [20][IC]: W*, dW_x, dW_y, dW_z of inner cells
   T *sR = sQ + 20 * IC;                      // [6][5][RC]: face states of the six rings
   int32_t *octs = reinterpret_cast<int32_t *>(sR + 30 * RC);  // [NOC] extended oct index or -1
@@ -237,7 +229,8 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     const int o1 = int(checked(__ldg(blk + gb + 1), o0 + 1, s.lo + s.nl + 1, a.err, o0 + 1));
     const int nb = o1 - o0;
 
-    // A. this thread's own cell: oct o0 + t/8, cell t%8 (coalesced in mesh order)
+    // A1. this thread's own cell: oct o0 + t/8, cell t%8 (coalesced in mesh
+    // order); the own octs' positions
     const bool mine = t < 8 * nb;
     int mo = 0, mc = 0, mq = 0;
     T u0[5];
@@ -254,12 +247,17 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     }
     __syncthreads();
 
-    // the cube's octs: own octs from the position table; every other oct
-    // through the 27-neighbour entry of an own oct within one position
+    // A2. one thread per cube oct: its extended index (own octs from the
+    // position table; every other oct through the 27-neighbour entry of an
+    // own oct within one position; the eight corners feed no face), the kind
+    // of its 8 cells and, unless it is an own oct at home (held by its
+    // threads), its state converted to primitives.  Own threads convert
+    // their own cell.
     for (int p = t; p < NOC; p += TH) {
       const int px = p % NO - 1, py = (p / NO) % NO - 1, pz = p / (NO * NO) - 1;
       const int out = (px < 0 || px >= NS) + (py < 0 || py >= NS) + (pz < 0 || pz >= NS);
       int e = -1;
+      bool home = false;
       if (out < 3) {
         int rx = px < 0 ? 0 : px >= NS ? NS - 1 : px;
         int ry = py < 0 ? 0 : py >= NS ? NS - 1 : py;
@@ -281,6 +279,7 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
         if (ob >= 0) {
           if (rx == px && ry == py && rz == pz) {
             e = ob;
+            home = true;
           } else {
             const int dir = (pz - rz + 1) * 9 + (py - ry + 1) * 3 + (px - rx + 1);
             e = int(checked(__ldg(a.nbr27 + dir * int64_t(a.N) + ob), -1, a.NE, a.err, -1));
@@ -288,68 +287,54 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
         }
       }
       octs[p] = e;
-    }
-    __syncthreads();
-
-    // conservative states of the cube and the kind of every cube cell
-    if (mine) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sP[v * C + mq] = u0[v];
-    }
-    // (an own oct met again elsewhere in the cube, through the periodic wrap
-    // of a level narrower than the block, is staged like any other oct)
-    for (int idx = t; idx < 5 * NOC; idx += TH) {
-      const int v = idx / NOC, p = idx - v * NOC;
-      const int e = octs[p];
-      const int px = p % NO, py = (p / NO) % NO, pz = p / (NO * NO);
-      if (e < 0 || home_of<NS>(pos_oct, px, py, pz, e)) continue;  // missing, or held by its own thread
-      T val[8];
-      load_oct8(a.U + v * a.S + 8 * int64_t(e), val);
-      const int q0 = 2 * px + E * (2 * py + E * 2 * pz);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) sP[v * C + q0 + (c & 1) + E * (((c >> 1) & 1) + E * (c >> 2))] = val[c];
-    }
-    for (int p = t; p < NOC; p += TH) {
-      const int e = octs[p];
-      const int px = p % NO, py = (p / NO) % NO, pz = p / (NO * NO);
-      const int q0 = 2 * px + E * (2 * py + E * 2 * pz);
+      const int q0 = 2 * (px + 1) + E * (2 * (py + 1) + E * 2 * (pz + 1));
       const uint32_t sm = (e >= 0 && e < a.N) ? __ldg(a.son + e) : 0u;
-      const uint8_t own = (e >= 0 && home_of<NS>(pos_oct, px, py, pz, e)) ? uint8_t(kCellOwn) : uint8_t(0);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         uint8_t ty = kCellNone;
         if (e >= a.N)
           ty = kCellGhost;
         else if (e >= 0)
-          ty = uint8_t(((sm >> c) & 1u) ? kCellSplit : kCellLeaf) | own;
+          ty = uint8_t(((sm >> c) & 1u) ? kCellSplit : kCellLeaf) | (home ? uint8_t(kCellOwn) : uint8_t(0));
         ctype[q0 + (c & 1) + E * (((c >> 1) & 1) + E * (c >> 2))] = ty;
       }
-    }
-    __syncthreads();
-
-    // B. primitives, in place
-    for (int q = t; q < C; q += TH) {
-      if (ctype[q] == kCellNone) continue;
-      T w[5];
-      prim_of(s, sP[q], sP[C + q], sP[2 * C + q], sP[3 * C + q], sP[4 * C + q], w);
+      if (e < 0 || home) continue;
+      T uv[5][8];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sP[v * C + q] = w[v];
+      for (int v = 0; v < 5; ++v) load_oct8(a.U + v * a.S + 8 * int64_t(e), uv[v]);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        T w[5];
+        prim_of(s, uv[0][c], uv[1][c], uv[2][c], uv[3][c], uv[4][c], w);
+        const int q = q0 + (c & 1) + E * (((c >> 1) & 1) + E * (c >> 2));
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sP[v * C + q] = w[v];
+      }
+    }
+    if (mine) {
+      T w[5];
+      prim_of(s, u0[0], u0[1], u0[2], u0[3], u0[4], w);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sP[v * C + mq] = w[v];
     }
     __syncthreads();
 
-    // C. slopes and predictor: inner cells g < IC (cube order), then the six
-    // face rings (side = 2 D + plus), transverse cells j + IN k
+    // C. slopes and predictor: inner cells g < IC (cube order, x fastest),
+    // then the six face rings (side = 2 D + plus; transverse cells
+    // rr = j + IN k, the lower axis j).  Every cell a solved face needs has
+    // all six neighbours staged (they lie within the own octs' 26-oct
+    // neighbourhoods); the slopes of other cells are not used.
     for (int g = t; g < IC + 6 * RC; g += TH) {
       int x, y, z, side = -1, rr = 0;
       if (g < IC) {
-        x = 2 + g % IN;
-        y = 2 + (g / IN) % IN;
-        z = 2 + g / (IN * IN);
+        x = 2 + (g & (IN - 1));
+        y = 2 + ((g >> LIN) & (IN - 1));
+        z = 2 + (g >> (2 * LIN));
       } else {
-        side = (g - IC) / RC;
-        rr = (g - IC) - side * RC;
+        side = (g - IC) >> (2 * LIN);
+        rr = (g - IC) & (RC - 1);
         const int D = side >> 1, along = (side & 1) ? 2 + IN : 1;
-        const int j = 2 + rr % IN, k = 2 + rr / IN;
+        const int j = 2 + (rr & (IN - 1)), k = 2 + (rr >> LIN);
         x = D == 0 ? along : j;
         y = D == 1 ? along : (D == 0 ? j : k);
         z = D == 2 ? along : k;
@@ -363,11 +348,6 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int st = d == 0 ? 1 : d == 1 ? E : E * E;
-        if (ctype[cq - st] == kCellNone || ctype[cq + st] == kCellNone) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) dw[d][v] = T(0);
-          continue;
-        }
 #pragma unroll
         for (int v = 0; v < 5; ++v) dw[d][v] = minmod(sP[v * C + cq + st] - w[v], w[v] - sP[v * C + cq - st]);
       }
@@ -381,75 +361,77 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
           for (int v = 0; v < 5; ++v) sQ[(5 + 5 * d + v) * IC + g] = dw[d][v];
       } else {
         const int D = side >> 1;
-        T dd[5];
+        // the minus ring feeds the left state of the first face, the plus
+        // ring the right state of the last
 #pragma unroll
-        for (int v = 0; v < 5; ++v) dd[v] = D == 0 ? dw[0][v] : D == 1 ? dw[1][v] : dw[2][v];
-        // the minus ring feeds the left state of face 0, the plus ring the
-        // right state of face IN
-#pragma unroll
-        for (int v = 0; v < 5; ++v)
-          sR[(5 * side + v) * RC + rr] = (side & 1) ? ws[v] - T(0.5) * dd[v] : ws[v] + T(0.5) * dd[v];
+        for (int v = 0; v < 5; ++v) {
+          const T dd = D == 0 ? dw[0][v] : D == 1 ? dw[1][v] : dw[2][v];
+          sR[(5 * side + v) * RC + rr] = (side & 1) ? ws[v] - T(0.5) * dd : ws[v] + T(0.5) * dd;
+        }
       }
     }
     __syncthreads();
 
-    // D. fluxes: along axis D, face i lies between inner cells i - 1 and i
-    // (cube cells 1 + i and 2 + i); transverse inner coordinates j, k (the
-    // lower axis first).  Faces are numbered x fastest for every axis, so a
-    // warp reads consecutive shared-memory words: r = i + FP (j + IN k) along
-    // x, j + IN (i + FP k) along y, j + IN (k + IN i) along z.
-    for (int f = t; f < 3 * FN; f += TH) {
-      const int D = f / FN, r = f - D * FN;
-      int i, j, k;
-      if (D == 0) {
-        i = r % FP;
-        j = (r / FP) % IN;
-        k = r / (FP * IN);
-      } else if (D == 1) {
-        j = r % IN;
-        i = (r / IN) % FP;
-        k = r / (IN * FP);
+    // D. fluxes.  Items w < 3 IC: the minus face along D = w / IC of inner
+    // cell w % IC, stored at [D][cell]; items beyond: the plus face of the
+    // last inner layer along D at transverse cell rr, stored at [D][IC + rr].
+    for (int wi = t; wi < 3 * (IC + RC); wi += TH) {
+      int D, gm, gp, rr;  // inner index of the minus / plus cell (-1: ring)
+      if (wi < 3 * IC) {
+        D = wi >> (3 * LIN);
+        gp = wi & (IC - 1);
+        const int xi = gp & (IN - 1), yi = (gp >> LIN) & (IN - 1), zi = gp >> (2 * LIN);
+        const int cd = D == 0 ? xi : D == 1 ? yi : zi;
+        rr = D == 0 ? yi + IN * zi : D == 1 ? xi + IN * zi : xi + IN * yi;
+        gm = cd > 0 ? gp - (D == 0 ? 1 : D == 1 ? IN : IN * IN) : -1;
       } else {
-        j = r % IN;
-        k = (r / IN) % IN;
-        i = r / RC;
+        D = (wi - 3 * IC) >> (2 * LIN);
+        rr = (wi - 3 * IC) & (RC - 1);
+        const int j = rr & (IN - 1), k = rr >> LIN;
+        gm = D == 0 ? (IN - 1) + IN * (j + IN * k) : D == 1 ? j + IN * ((IN - 1) + IN * k)
+                                                            : j + IN * (k + IN * (IN - 1));
+        gp = -1;
       }
-      const int ma = 1 + i, tj = 2 + j, tk = 2 + k;
-      const int xa = D == 0 ? ma : tj, ya = D == 1 ? ma : (D == 0 ? tj : tk), za = D == 2 ? ma : tk;
+      // cube cells of the two sides
       const int st = D == 0 ? 1 : D == 1 ? E : E * E;
-      const int ca = xa + E * (ya + E * za), cb = ca + st;
+      int cb;
+      if (gp >= 0) {
+        cb = (2 + (gp & (IN - 1))) + E * ((2 + ((gp >> LIN) & (IN - 1))) + E * (2 + (gp >> (2 * LIN))));
+      } else {
+        cb = (2 + (gm & (IN - 1))) + E * ((2 + ((gm >> LIN) & (IN - 1))) + E * (2 + (gm >> (2 * LIN)))) + st;
+      }
+      const int ca = cb - st;
       T F[5] = {T(0), T(0), T(0), T(0), T(0)};
       const int kind = face_kind(ctype[ca], ctype[cb]);
       if (kind) {
         T qL[5], qR[5];
-        const int rr = j + IN * k;
-        if (i == 0) {
+        if (gm < 0) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) qL[v] = sR[(5 * (2 * D) + v) * RC + rr];
         } else {
-          const int qa = (xa - 2) + IN * ((ya - 2) + IN * (za - 2));
 #pragma unroll
-          for (int v = 0; v < 5; ++v) qL[v] = sQ[v * IC + qa] + T(0.5) * sQ[(5 + 5 * D + v) * IC + qa];
+          for (int v = 0; v < 5; ++v) qL[v] = sQ[v * IC + gm] + T(0.5) * sQ[(5 + 5 * D + v) * IC + gm];
         }
-        if (i == IN) {
+        if (gp < 0) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) qR[v] = sR[(5 * (2 * D + 1) + v) * RC + rr];
         } else {
-          const int qb = (xa - 2 + (D == 0)) + IN * ((ya - 2 + (D == 1)) + IN * (za - 2 + (D == 2)));
 #pragma unroll
-          for (int v = 0; v < 5; ++v) qR[v] = sQ[v * IC + qb] - T(0.5) * sQ[(5 + 5 * D + v) * IC + qb];
+          for (int v = 0; v < 5; ++v) qR[v] = sQ[v * IC + gp] - T(0.5) * sQ[(5 + 5 * D + v) * IC + gp];
         }
         face_flux_dir(s, D, qL, qR, F);
         if (a.reflux && (kind == 1 || kind == -1)) {
           const int cg = kind > 0 ? cb : ca;
           const int gx = cg % E, gy = (cg / E) % E, gz = cg / (E * E);
           const int eg = octs[(gx >> 1) + NO * ((gy >> 1) + NO * (gz >> 1))];
-          reflux_write(a, s, D, eg, (xa & 1) | ((ya & 1) << 1) | ((za & 1) << 2), kind, F);
+          const int mx = ca % E, my = (ca / E) % E, mz = ca / (E * E);
+          reflux_write(a, s, D, eg, (mx & 1) | ((my & 1) << 1) | ((mz & 1) << 2), kind, F);
         }
       }
       // sF aliases sP, whose last reads (phase C) ended at the barrier above
+      const int fi = gp >= 0 ? gp : IC + rr;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sF[(5 * D + v) * FN + r] = F[v];
+      for (int v = 0; v < 5; ++v) sF[(5 * D + v) * FS + fi] = F[v];
     }
     __syncthreads();
 
@@ -457,16 +439,17 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     for (int q = t; q < NB; q += TH) pos_oct[q] = -1;  // for the next block
     if (mine && ctype[mq] == (kCellLeaf | kCellOwn)) {
       const int xi = mq % E - 2, yi = (mq / E) % E - 2, zi = mq / (E * E) - 2;
-      // the cell's minus faces (face i = its coordinate) and the plus faces
-      // one face position further
-      const int rf[3] = {xi + FP * (yi + IN * zi), xi + IN * (yi + FP * zi), xi + IN * (yi + IN * zi)};
-      constexpr int rp[3] = {1, IN, RC};
+      const int gi = xi + IN * (yi + IN * zi);
+      // minus face: [D][gi]; plus face: the next cell's minus face, or the
+      // last layer's plus face
+      const int pf[3] = {xi < IN - 1 ? gi + 1 : IC + yi + IN * zi,
+                         yi < IN - 1 ? gi + IN : IC + xi + IN * zi,
+                         zi < IN - 1 ? gi + IN * IN : IC + xi + IN * yi};
       T du[3][5];
 #pragma unroll
       for (int D = 0; D < 3; ++D)
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
-          du[D][v] = sF[(5 * D + v) * FN + rf[D]] - sF[(5 * D + v) * FN + rf[D] + rp[D]];
+        for (int v = 0; v < 5; ++v) du[D][v] = sF[(5 * D + v) * FS + gi] - sF[(5 * D + v) * FS + pf[D]];
       const int64_t g = 8 * int64_t(mo) + mc;
       const int rs = int(checked(__ldg(a.rslot + g), -1, a.NC, a.err, -1));
       T *out = a.W + s.base + 8 * (mo - s.lo) + mc;
