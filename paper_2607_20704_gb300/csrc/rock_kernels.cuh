@@ -169,6 +169,16 @@ __device__ __forceinline__ void load_oct8(const double *p, double (&o)[8]) {
     o[2 * h + 1] = a.y;
   }
 }
+// 4 consecutive values (16-byte aligned)
+__device__ __forceinline__ void load_oct4(const float *p, float (&o)[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void load_oct4(const double *p, double (&o)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
 __device__ __forceinline__ void store_oct8(float *p, const float (&o)[8]) {
   reinterpret_cast<float4 *>(p)[0] = make_float4(o[0], o[1], o[2], o[3]);
   reinterpret_cast<float4 *>(p)[1] = make_float4(o[4], o[5], o[6], o[7]);
@@ -229,31 +239,21 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     const int o1 = int(checked(__ldg(blk + gb + 1), o0 + 1, s.lo + s.nl + 1, a.err, o0 + 1));
     const int nb = o1 - o0;
 
-    // A1. this thread's own cell: oct o0 + t/8, cell t%8 (coalesced in mesh
-    // order); the own octs' positions
-    const bool mine = t < 8 * nb;
-    int mo = 0, mc = 0, mq = 0;
-    T u0[5];
-    if (mine) {
-      mo = o0 + (t >> 3);
-      mc = t & 7;
-      const uint64_t k = __ldg(a.key + mo);
-      const int bx = int(ikey_x(k) & (NS - 1)), by = int(ikey_y(k) & (NS - 1)), bz = int(ikey_z(k) & (NS - 1));
-      if (mc == 0) pos_oct[bx + NS * (by + NS * bz)] = mo;
-      mq = (2 + 2 * bx + (mc & 1)) + E * ((2 + 2 * by + ((mc >> 1) & 1)) + E * (2 + 2 * bz + (mc >> 2)));
-      const int64_t g = 8 * int64_t(mo) + mc;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) u0[v] = __ldg(a.U + v * a.S + g);
+    // A1. the own octs' positions in the block
+    for (int b = t; b < nb; b += TH) {
+      const uint64_t k = __ldg(a.key + o0 + b);
+      pos_oct[int(ikey_x(k) & (NS - 1)) + NS * (int(ikey_y(k) & (NS - 1)) + NS * int(ikey_z(k) & (NS - 1)))] =
+          o0 + b;
     }
     __syncthreads();
 
-    // A2. one thread per cube oct: its extended index (own octs from the
+    // A2. two threads per cube oct (cells 4 h .. 4 h + 3, one 16-byte load
+    // per variable in FP32): the oct's extended index (own octs from the
     // position table; every other oct through the 27-neighbour entry of an
     // own oct within one position; the eight corners feed no face), the kind
-    // of its 8 cells and, unless it is an own oct at home (held by its
-    // threads), its state converted to primitives.  Own threads convert
-    // their own cell.
-    for (int p = t; p < NOC; p += TH) {
+    // of its cells and their primitives
+    for (int it = t; it < 2 * NOC; it += TH) {
+      const int p = it >> 1, h = it & 1;
       const int px = p % NO - 1, py = (p / NO) % NO - 1, pz = p / (NO * NO) - 1;
       const int out = (px < 0 || px >= NS) + (py < 0 || py >= NS) + (pz < 0 || pz >= NS);
       int e = -1;
@@ -286,36 +286,32 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
           }
         }
       }
-      octs[p] = e;
-      const int q0 = 2 * (px + 1) + E * (2 * (py + 1) + E * 2 * (pz + 1));
+      if (h == 0) octs[p] = e;
+      // cells 4 h .. 4 h + 3 of the oct: the plane cz = h
+      const int q0 = 2 * (px + 1) + E * (2 * (py + 1) + E * (2 * (pz + 1) + h));
       const uint32_t sm = (e >= 0 && e < a.N) ? __ldg(a.son + e) : 0u;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < 4; ++c) {
         uint8_t ty = kCellNone;
         if (e >= a.N)
           ty = kCellGhost;
         else if (e >= 0)
-          ty = uint8_t(((sm >> c) & 1u) ? kCellSplit : kCellLeaf) | (home ? uint8_t(kCellOwn) : uint8_t(0));
-        ctype[q0 + (c & 1) + E * (((c >> 1) & 1) + E * (c >> 2))] = ty;
+          ty = uint8_t(((sm >> (4 * h + c)) & 1u) ? kCellSplit : kCellLeaf) |
+               (home ? uint8_t(kCellOwn) : uint8_t(0));
+        ctype[q0 + (c & 1) + E * (c >> 1)] = ty;
       }
-      if (e < 0 || home) continue;
-      T uv[5][8];
+      if (e < 0) continue;
+      T uv[5][4];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) load_oct8(a.U + v * a.S + 8 * int64_t(e), uv[v]);
+      for (int v = 0; v < 5; ++v) load_oct4(a.U + v * a.S + 8 * int64_t(e) + 4 * h, uv[v]);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < 4; ++c) {
         T w[5];
         prim_of(s, uv[0][c], uv[1][c], uv[2][c], uv[3][c], uv[4][c], w);
-        const int q = q0 + (c & 1) + E * (((c >> 1) & 1) + E * (c >> 2));
+        const int q = q0 + (c & 1) + E * (c >> 1);
 #pragma unroll
         for (int v = 0; v < 5; ++v) sP[v * C + q] = w[v];
       }
-    }
-    if (mine) {
-      T w[5];
-      prim_of(s, u0[0], u0[1], u0[2], u0[3], u0[4], w);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sP[v * C + mq] = w[v];
     }
     __syncthreads();
 
@@ -435,11 +431,15 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     }
     __syncthreads();
 
-    // E. update of this thread's own cell, if it is a leaf, into W
+    // E. update, one thread per inner cell (cube order): a leaf cell of the
+    // block's own octs takes its new state into W
     for (int q = t; q < NB; q += TH) pos_oct[q] = -1;  // for the next block
-    if (mine && ctype[mq] == (kCellLeaf | kCellOwn)) {
-      const int xi = mq % E - 2, yi = (mq / E) % E - 2, zi = mq / (E * E) - 2;
-      const int gi = xi + IN * (yi + IN * zi);
+    for (int gi = t; gi < IC; gi += TH) {
+      const int xi = gi & (IN - 1), yi = (gi >> LIN) & (IN - 1), zi = gi >> (2 * LIN);
+      const int cq = (2 + xi) + E * ((2 + yi) + E * (2 + zi));
+      if (ctype[cq] != (kCellLeaf | kCellOwn)) continue;
+      const int e = octs[(1 + (xi >> 1)) + NO * ((1 + (yi >> 1)) + NO * (1 + (zi >> 1)))];
+      const int c = (xi & 1) | ((yi & 1) << 1) | ((zi & 1) << 2);
       // minus face: [D][gi]; plus face: the next cell's minus face, or the
       // last layer's plus face
       const int pf[3] = {xi < IN - 1 ? gi + 1 : IC + yi + IN * zi,
@@ -450,12 +450,12 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
       for (int D = 0; D < 3; ++D)
 #pragma unroll
         for (int v = 0; v < 5; ++v) du[D][v] = sF[(5 * D + v) * FS + gi] - sF[(5 * D + v) * FS + pf[D]];
-      const int64_t g = 8 * int64_t(mo) + mc;
+      const int64_t g = 8 * int64_t(e) + c;
       const int rs = int(checked(__ldg(a.rslot + g), -1, a.NC, a.err, -1));
-      T *out = a.W + s.base + 8 * (mo - s.lo) + mc;
+      T *out = a.W + s.base + 8 * (e - s.lo) + c;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        T u = u0[v] + s.dtdx * ((du[0][v] + du[1][v]) + du[2][v]);
+        T u = __ldg(a.U + v * a.S + g) + s.dtdx * ((du[0][v] + du[1][v]) + du[2][v]);
         if (rs >= 0) {
           T *Rv = a.Rc + v * int64_t(a.NC) + rs;
           u = u + *Rv;
