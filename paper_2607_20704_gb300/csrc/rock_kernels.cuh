@@ -56,7 +56,7 @@ struct Rock {
   static_assert(THREADS >= 8 * NB, "one thread per cell of the block");
   template <class T>
   static constexpr size_t smem() {
-    return sizeof(T) * (5 * C + 20 * IC + 30 * RC + 5 * IC) + 4 * (NOC + NB + 27 * NB + IC) + C;
+    return sizeof(T) * (5 * C + 20 * IC + 30 * RC + 5 * IC) + 4 * (NOC + NB + IC) + C;
   }
   // blocks per SM the register budget is sized for
   template <class T>
@@ -225,8 +225,7 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
   T *sU = sR + 30 * RC;                      // [5][IC]: conservative state of the inner cells
   int32_t *octs = reinterpret_cast<int32_t *>(sU + 5 * IC);   // [NOC] extended oct index or -1
   int32_t *pos_oct = octs + NOC;                               // [NB] own oct at each position
-  int32_t *nbs = pos_oct + NB;                                 // [27][NB] own octs' neighbour rows
-  int32_t *rss = nbs + 27 * NB;                                // [IC] reflux slot of inner cells
+  int32_t *rss = pos_oct + NB;                                 // [IC] reflux slot of inner cells
   uint8_t *ctype = reinterpret_cast<uint8_t *>(rss + IC);      // [C] kind of each cube cell
   const int t = threadIdx.x;
 
@@ -242,16 +241,11 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
     const int o1 = int(checked(__ldg(blk + gb + 1), o0 + 1, s.lo + s.nl + 1, a.err, o0 + 1));
     const int nb = o1 - o0;
 
-    // A1. the own octs' positions in the block and their 27-neighbour rows
-    // (direction-major in memory: coalesced)
+    // A1. the own octs' positions in the block
     for (int b = t; b < nb; b += TH) {
       const uint64_t k = __ldg(a.key + o0 + b);
       pos_oct[int(ikey_x(k) & (NS - 1)) + NS * (int(ikey_y(k) & (NS - 1)) + NS * int(ikey_z(k) & (NS - 1)))] =
           o0 + b;
-    }
-    for (int idx = t; idx < 27 * NB; idx += TH) {
-      const int dir = idx / NB, b = idx - dir * NB;
-      if (b < nb) nbs[idx] = int(checked(__ldg(a.nbr27 + dir * int64_t(a.N) + o0 + b), -1, a.NE, a.err, -1));
     }
     __syncthreads();
 
@@ -290,7 +284,7 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
             home = true;
           } else {
             const int dir = (pz - rz + 1) * 9 + (py - ry + 1) * 3 + (px - rx + 1);
-            e = nbs[dir * NB + (ob - o0)];
+            e = int(checked(__ldg(a.nbr27 + dir * int64_t(a.N) + ob), -1, a.NE, a.err, -1));
           }
         }
       }
