@@ -56,7 +56,7 @@ struct Rock {
   static_assert(THREADS >= 8 * NB, "one thread per cell of the block");
   template <class T>
   static constexpr size_t smem() {
-    return sizeof(T) * (5 * C + 20 * IC + 30 * RC + 5 * IC) + 4 * (NOC + NB + IC) + C;
+    return sizeof(T) * (5 * C + 20 * IC + 30 * RC) + 4 * (NOC + NB) + C;
   }
   // blocks per SM the register budget is sized for
   template <class T>
@@ -222,11 +222,9 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
   T *sF = sP;                                // [3][5][FS]: fluxes (phase D on)
   T *sQ = sP + 5 * C;                        // [20][IC]: W*, dW_x, dW_y, dW_z of inner cells
   T *sR = sQ + 20 * IC;                      // [6][5][RC]: face states of the six rings
-  T *sU = sR + 30 * RC;                      // [5][IC]: conservative state of the inner cells
-  int32_t *octs = reinterpret_cast<int32_t *>(sU + 5 * IC);   // [NOC] extended oct index or -1
+  int32_t *octs = reinterpret_cast<int32_t *>(sR + 30 * RC);  // [NOC] extended oct index or -1
   int32_t *pos_oct = octs + NOC;                               // [NB] own oct at each position
-  int32_t *rss = pos_oct + NB;                                 // [IC] reflux slot of inner cells
-  uint8_t *ctype = reinterpret_cast<uint8_t *>(rss + IC);      // [C] kind of each cube cell
+  uint8_t *ctype = reinterpret_cast<uint8_t *>(pos_oct + NB);  // [C] kind of each cube cell
   const int t = threadIdx.x;
 
   for (int q = t; q < NB; q += TH) pos_oct[q] = -1;
@@ -306,14 +304,6 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
       T uv[5][4];
 #pragma unroll
       for (int v = 0; v < 5; ++v) load_oct4(a.U + v * a.S + 8 * int64_t(e) + 4 * h, uv[v]);
-      int rsv[4];
-      if (home) {  // the update's inputs of the block's own cells
-        const int4 r4 = __ldg(reinterpret_cast<const int4 *>(a.rslot + 8 * int64_t(e) + 4 * h));
-        rsv[0] = r4.x;
-        rsv[1] = r4.y;
-        rsv[2] = r4.z;
-        rsv[3] = r4.w;
-      }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         T w[5];
@@ -321,12 +311,6 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
         const int q = q0 + (c & 1) + E * (c >> 1);
 #pragma unroll
         for (int v = 0; v < 5; ++v) sP[v * C + q] = w[v];
-        if (home) {
-          const int gi = (2 * px + (c & 1)) + IN * ((2 * py + (c >> 1)) + IN * (2 * pz + h));
-#pragma unroll
-          for (int v = 0; v < 5; ++v) sU[v * IC + gi] = uv[v][c];
-          rss[gi] = int(checked(rsv[c], -1, a.NC, a.err, -1));
-        }
       }
     }
     __syncthreads();
@@ -466,11 +450,12 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
       for (int D = 0; D < 3; ++D)
 #pragma unroll
         for (int v = 0; v < 5; ++v) du[D][v] = sF[(5 * D + v) * FS + gi] - sF[(5 * D + v) * FS + pf[D]];
-      const int rs = rss[gi];
+      const int64_t g = 8 * int64_t(e) + c;
+      const int rs = int(checked(__ldg(a.rslot + g), -1, a.NC, a.err, -1));
       T *out = a.W + s.base + 8 * (e - s.lo) + c;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        T u = sU[v * IC + gi] + s.dtdx * ((du[0][v] + du[1][v]) + du[2][v]);
+        T u = __ldg(a.U + v * a.S + g) + s.dtdx * ((du[0][v] + du[1][v]) + du[2][v]);
         if (rs >= 0) {
           T *Rv = a.Rc + v * int64_t(a.NC) + rs;
           u = u + *Rv;
