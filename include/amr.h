@@ -183,6 +183,29 @@ amr_status amr_set_member_steps(amr_handle h, const int32_t *steps, int n);
  * handle-wide error that the next synchronising call would report. */
 amr_status amr_member_errors(amr_handle h, int32_t *errs, int n);
 
+/*
+ * amr_batch_repack -- continuous batching of independent meshes (no
+ * counterpart in the paper: the serving loop's admission between coarse
+ * steps).  The handle is rebuilt with members keep[0..n_keep) of the current
+ * ones (indices in increasing order; their states stay on the device and are
+ * carried over bit for bit, with their remaining coarse-step counts, last
+ * time steps and error bits) followed by n_add new meshes added[] (copied
+ * from the host as by amr_create_batch), each to take added_steps[q] coarse
+ * steps (-1: unlimited).  Members that are not kept are dropped and their
+ * device memory freed.  After the call member q < n_keep is the old member
+ * keep[q] and member n_keep + q the added mesh q; member 0 is selected.  A
+ * member's results do not depend on the other members, so a kept member
+ * continues exactly as it would alone.  Call between coarse steps (no
+ * reflux is pending there); the rebuild holds the old and the new mesh for
+ * its duration.  Device buffers are replaced (a captured graph is
+ * re-captured; the launch shape chosen by the autotuner is kept).
+ * Synchronous.  Errors: AMR_EINVAL (counts, unordered keep, bad mesh, more
+ * than 2^26 octs), AMR_EGRADING / AMR_EDUP (an added mesh), AMR_ENOMEM,
+ * AMR_ECUDA; on error the handle is unchanged.
+ */
+amr_status amr_batch_repack(amr_handle h, int n_keep, const int32_t *keep, int n_add,
+                            const amr_member *added, const int32_t *added_steps);
+
 /* The last coarse time step of every member (from amr_cfl_dt or
  * amr_advance), copied into dt_out[0..n_members) (synchronous). */
 amr_status amr_member_dt(amr_handle h, double *dt_out, int n);

@@ -99,7 +99,7 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_set_timing", "amr_read_timing", "amr_kernel_name", "amr_sync", "amr_last_error",
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
            "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag",
-           "amr_regrid_flags", "amr_totals", "amr_hash", "amr_read_hash",
+           "amr_regrid_flags", "amr_totals", "amr_hash", "amr_read_hash", "amr_batch_repack",
            "amr_poisson", "amr_read_phi", "amr_load_state_async", "amr_store_state_async",
            "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
@@ -172,6 +172,7 @@ def load(path: str | None = None):
             "amr_regrid": (I, [P, P, P]),
             "amr_regrid_flags": (I, [P, P, I64, P, P]),
             "amr_totals": (I, [P, I, P]),
+            "amr_batch_repack": (I, [P, I, P, I, P, P]),
             "amr_hash": (I, [P, I64, P, P]),
             "amr_read_hash": (I, [P, P, P, P, I64]),
             "amr_flag": (I, [P, I, P, I64]),
@@ -255,6 +256,33 @@ def kernel_names():
         t += 1
 
 
+def _member_array(members):
+    """ctypes array of amr_member for a list of member dicts, and the numpy
+    arrays it points into (the caller keeps them alive during the call)."""
+    keep = []
+    arr = (amr_member * len(members))()
+    for t, mb in enumerate(members):
+        lv = np.ascontiguousarray(mb["level"], dtype=np.uint8)
+        ii = np.ascontiguousarray(mb["i"], dtype=np.uint32)
+        jj = np.ascontiguousarray(mb["j"], dtype=np.uint32)
+        kk = np.ascontiguousarray(mb["k"], dtype=np.uint32)
+        uu = np.ascontiguousarray(mb["U"], dtype=np.float64)
+        n = lv.shape[0]
+        if uu.shape != (NV, 8 * n):
+            raise ValueError(f"U must have shape (5, {8 * n}), got {uu.shape}")
+        hk = mb.get("hilbert_key")
+        hk = None if hk is None else np.ascontiguousarray(hk, dtype=np.uint64)
+        keep += [lv, ii, jj, kk, uu, hk]
+        m = arr[t]
+        m.levelmin, m.levelmax = int(mb["levelmin"]), int(mb["levelmax"])
+        m.gamma, m.cfl = float(mb["gamma"]), float(mb.get("cfl", 0.8))
+        m.smallr, m.smallc = float(mb.get("smallr", 1e-10)), float(mb.get("smallc", 1e-10))
+        m.n_oct = n
+        m.level, m.i, m.j, m.k, m.U = (_ptr(lv), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(uu))
+        m.hilbert_key = _ptr(hk) if hk is not None else None
+    return arr, keep
+
+
 class Mesh:
     """One resident handle (wraps an ``amr_handle``): a single mesh, or with
     ``Mesh.batch`` many independent member meshes advanced together."""
@@ -292,27 +320,7 @@ class Mesh:
             members = [dict(level=level, i=i, j=j, k=k, U=U, levelmin=levelmin, levelmax=levelmax,
                             gamma=gamma, cfl=cfl, smallr=smallr, smallc=smallc,
                             hilbert_key=hilbert_key)]
-        keep = []
-        arr = (amr_member * len(members))()
-        for t, mb in enumerate(members):
-            lv = np.ascontiguousarray(mb["level"], dtype=np.uint8)
-            ii = np.ascontiguousarray(mb["i"], dtype=np.uint32)
-            jj = np.ascontiguousarray(mb["j"], dtype=np.uint32)
-            kk = np.ascontiguousarray(mb["k"], dtype=np.uint32)
-            uu = np.ascontiguousarray(mb["U"], dtype=np.float64)
-            n = lv.shape[0]
-            if uu.shape != (NV, 8 * n):
-                raise ValueError(f"U must have shape (5, {8 * n}), got {uu.shape}")
-            hk = mb.get("hilbert_key")
-            hk = None if hk is None else np.ascontiguousarray(hk, dtype=np.uint64)
-            keep += [lv, ii, jj, kk, uu, hk]
-            m = arr[t]
-            m.levelmin, m.levelmax = int(mb["levelmin"]), int(mb["levelmax"])
-            m.gamma, m.cfl = float(mb["gamma"]), float(mb.get("cfl", 0.8))
-            m.smallr, m.smallc = float(mb.get("smallr", 1e-10)), float(mb.get("smallc", 1e-10))
-            m.n_oct = n
-            m.level, m.i, m.j, m.k, m.U = (_ptr(lv), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(uu))
-            m.hilbert_key = _ptr(hk) if hk is not None else None
+        arr, keep = _member_array(members)
         h = C.c_void_p()
         rc = L.amr_create_batch(C.byref(p), len(members), arr, C.byref(h))
         _check(rc, "amr_create")
@@ -323,6 +331,29 @@ class Mesh:
         self.gamma = float(members[0]["gamma"])
         self.precision = int(precision)
         self._member = 0
+
+    def repack(self, keep, problems=(), steps=()):
+        """Continuous batching: keep the members listed in ``keep`` (increasing
+        order; their states stay on the device) and append the meshes of
+        ``problems`` (``inputs.Problem``), each taking ``steps[q]`` coarse
+        steps (-1: unlimited)."""
+        kp = np.ascontiguousarray(keep, dtype=np.int32)
+        members = []
+        for pr in problems:
+            lv, i, j, k, U = pr.mesh_args()
+            members.append(dict(level=lv, i=i, j=j, k=k, U=U, **pr.params()))
+        arr, hold = _member_array(members) if members else (None, [])
+        st = np.ascontiguousarray(steps, dtype=np.int32)
+        assert st.size == len(members)
+        _check(load().amr_batch_repack(self._h, int(kp.size), _ptr(kp) if kp.size else None,
+                                       len(members), arr, _ptr(st) if st.size else None),
+               "amr_batch_repack")
+        del hold
+        self.member_levels = [self.member_levels[int(q)] for q in kp] + \
+            [(int(mb["levelmin"]), int(mb["levelmax"])) for mb in members]
+        self.n_members = len(self.member_levels)
+        self._member = 0
+        self.levelmin, self.levelmax = self.member_levels[0]
 
     @classmethod
     def batch(cls, problems, **kw):

@@ -2174,6 +2174,185 @@ extern "C" amr_status amr_read_hash(amr_handle h, int64_t *cap_out, uint64_t *ke
   return check_device(h, "amr_read_hash");
 }
 
+// ---------------------------------------------------------------------------
+// batch repack (continuous batching): a new oct list from the kept members'
+// octs (device to device) and the added meshes (from the host), rebuilt as
+// by amr_create; per-member step counters, time steps and error bits of the
+// kept members carried over
+// ---------------------------------------------------------------------------
+extern "C" amr_status amr_batch_repack(amr_handle h, int n_keep, const int32_t *keep, int n_add,
+                                       const amr_member *added, const int32_t *added_steps) {
+  if (!h) return fail(AMR_EINVAL, "amr_batch_repack: NULL handle");
+  if (n_keep < 0 || n_add < 0 || n_keep + n_add < 1 || n_keep > h->M ||
+      n_keep + n_add > kMaxMembers)
+    return fail(AMR_EINVAL, "amr_batch_repack: member counts out of range");
+  if ((n_keep && !keep) || (n_add && (!added || !added_steps)))
+    return fail(AMR_EINVAL, "amr_batch_repack: NULL argument");
+  for (int q = 0; q < n_keep; ++q)
+    if (keep[q] < 0 || keep[q] >= h->M || (q && keep[q] <= keep[q - 1]))
+      return fail(AMR_EINVAL, "amr_batch_repack: keep must list member indices in increasing order");
+  int64_t n_out = 0;
+  for (int q = 0; q < n_keep; ++q) n_out += h->mem[keep[q]].lo[kMaxLev + 1];
+  const int64_t K = n_out;
+  for (int q = 0; q < n_add; ++q) {
+    AMR_TRY(check_member(added[q], n_keep + q));
+    if (added_steps[q] == 0 || added_steps[q] < -1)
+      return fail(AMR_EINVAL, "amr_batch_repack: steps of an added member must be >= 1 or -1");
+    n_out += added[q].n_oct;
+  }
+  if (n_out > (int64_t(1) << 26)) return fail(AMR_EINVAL, "amr_batch_repack: more than 2^26 octs in total");
+  if (h->cs) CUDA_TRY(cudaStreamSynchronize(h->cs));  // state copies in flight finish first
+  if (h->cs_out) CUDA_TRY(cudaStreamSynchronize(h->cs_out));
+  // per-member step counters, time steps and errors of the current members
+  std::vector<int> rem(h->M), merr(h->M);
+  std::vector<double> dt(h->M);
+  CUDA_TRY(cudaMemcpyAsync(rem.data(), h->mrem, sizeof(int) * h->M, cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaMemcpyAsync(merr.data(), h->merr, sizeof(int) * h->M, cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaMemcpyAsync(dt.data(), h->dt_dev, sizeof(double) * h->M, cudaMemcpyDeviceToHost, h->s));
+  AMR_TRY(check_device(h, "amr_batch_repack"));
+  // the new handle's members: kept ones in order, then the added ones
+  amr_mesh *nh = regrid_shell(h);
+  nh->M = n_keep + n_add;
+  nh->mem.assign(size_t(nh->M), Member());
+  nh->sel = 0;
+  nh->lmax_all = 1;
+  std::vector<int> remap(size_t(h->M), -1);
+  std::vector<int64_t> dst(size_t(h->M), 0), base(size_t(h->M), 0);
+  {
+    int64_t off = 0;
+    for (int q = 0; q < n_keep; ++q) {
+      const Member &om = h->mem[keep[q]];
+      Member &m = nh->mem[q];
+      m.lmin = om.lmin;
+      m.lmax = om.lmax;
+      m.gamma = om.gamma;
+      m.cfl = om.cfl;
+      m.smallr = om.smallr;
+      m.smallc = om.smallc;
+      m.n_oct = om.lo[kMaxLev + 1];
+      remap[keep[q]] = q;
+      dst[keep[q]] = off;
+      base[keep[q]] = om.oct_base;
+      off += m.n_oct;
+    }
+    for (int q = 0; q < n_add; ++q) {
+      const amr_member &a = added[q];
+      Member &m = nh->mem[n_keep + q];
+      m.lmin = a.levelmin;
+      m.lmax = a.levelmax;
+      m.gamma = a.gamma;
+      m.cfl = a.cfl;
+      m.smallr = a.smallr;
+      m.smallc = a.smallc;
+      m.n_oct = a.n_oct;
+    }
+    for (auto &m : nh->mem) nh->lmax_all = std::max(nh->lmax_all, m.lmax);
+  }
+  nh->N = n_out;
+  uint8_t *d_lvl = nullptr;
+  uint16_t *d_mem = nullptr;
+  uint32_t *d_i = nullptr, *d_j = nullptr, *d_k = nullptr;
+  double *d_U = nullptr;
+  int *d_remap = nullptr;
+  int64_t *d_dst = nullptr, *d_base = nullptr;
+  amr_status st = AMR_OK;
+  auto abandon = [&](amr_status e) {
+    std::string msg = g_last_error;
+    cudaStreamSynchronize(h->s);
+    destroy_all(nh);
+    g_last_error = msg;
+    return e;
+  };
+  if ((st = upload_members(nh)) != AMR_OK || (st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
+      (st = alloc_n(nh, &d_mem, n_out)) != AMR_OK || (st = alloc_n(nh, &d_i, n_out)) != AMR_OK ||
+      (st = alloc_n(nh, &d_j, n_out)) != AMR_OK || (st = alloc_n(nh, &d_k, n_out)) != AMR_OK ||
+      (st = alloc_n(nh, &d_U, 40 * n_out)) != AMR_OK || (st = upload(nh, &d_remap, remap)) != AMR_OK ||
+      (st = upload(nh, &d_dst, dst)) != AMR_OK || (st = upload(nh, &d_base, base)) != AMR_OK)
+    return abandon(st);
+  if (K > 0) {
+    if (h->p.precision == 4)
+      launch(h, K_REGRID, k_repack_emit<float>, dim3(nblocks(h->N)), dim3(256), h->N, h->S,
+             (const uint64_t *)h->key, (const float *)h->U, (const int *)d_remap,
+             (const int64_t *)d_dst, (const int64_t *)d_base, n_out, d_lvl, d_mem, d_i, d_j, d_k, d_U);
+    else
+      launch(h, K_REGRID, k_repack_emit<double>, dim3(nblocks(h->N)), dim3(256), h->N, h->S,
+             (const uint64_t *)h->key, (const double *)h->U, (const int *)d_remap,
+             (const int64_t *)d_dst, (const int64_t *)d_base, n_out, d_lvl, d_mem, d_i, d_j, d_k, d_U);
+  }
+  // the added meshes, staged on the host in the new list's layout
+  if (n_add > 0) {
+    const int64_t na = n_out - K;
+    const size_t nas = static_cast<size_t>(na);
+    std::vector<uint8_t> lv(nas);
+    std::vector<uint16_t> mm(nas);
+    std::vector<uint32_t> ci(nas), cj(nas), ck(nas);
+    std::vector<double> U(40 * nas);
+    int64_t off = 0;
+    for (int q = 0; q < n_add; ++q) {
+      const amr_member &a = added[q];
+      const int64_t nm = a.n_oct;
+      std::memcpy(lv.data() + off, a.level, size_t(nm));
+      std::memcpy(ci.data() + off, a.i, 4 * size_t(nm));
+      std::memcpy(cj.data() + off, a.j, 4 * size_t(nm));
+      std::memcpy(ck.data() + off, a.k, 4 * size_t(nm));
+      for (int64_t t = 0; t < nm; ++t) mm[size_t(off + t)] = uint16_t(n_keep + q);
+      for (int v = 0; v < 5; ++v)
+        std::memcpy(U.data() + v * 8 * na + 8 * off, a.U + v * 8 * nm, sizeof(double) * 8 * size_t(nm));
+      off += nm;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_lvl + K, lv.data(), size_t(na), cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mem + K, mm.data(), 2 * size_t(na), cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_i + K, ci.data(), 4 * size_t(na), cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_j + K, cj.data(), 4 * size_t(na), cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_k + K, ck.data(), 4 * size_t(na), cudaMemcpyHostToDevice, h->s);
+    for (int v = 0; v < 5 && e == cudaSuccess; ++v)
+      e = cudaMemcpyAsync(d_U + v * 8 * n_out + 8 * K, U.data() + v * 8 * na, sizeof(double) * 8 * size_t(na),
+                          cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);  // the host staging goes out of scope
+    if (e != cudaSuccess) return abandon(fail(AMR_ECUDA, "amr_batch_repack: %s", cudaGetErrorString(e)));
+  }
+  if ((st = check_device(h, "amr_batch_repack")) != AMR_OK) return abandon(st);
+  dev_free(nh, d_remap);
+  dev_free(nh, d_dst);
+  dev_free(nh, d_base);
+  if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, d_U, nullptr)) != AMR_OK)
+    return abandon(st);
+  // step counters, last time steps and error bits of the kept members; the
+  // added members take their step counts
+  {
+    std::vector<int> nrem(size_t(nh->M)), nerr(size_t(nh->M), 0);
+    std::vector<double> ndt(size_t(nh->M), 0.0);
+    for (int q = 0; q < n_keep; ++q) {
+      nrem[size_t(q)] = rem[size_t(keep[q])];
+      nerr[size_t(q)] = merr[size_t(keep[q])];
+      ndt[size_t(q)] = dt[size_t(keep[q])];
+    }
+    for (int q = 0; q < n_add; ++q) nrem[size_t(n_keep + q)] = added_steps[q];
+    cudaError_t e = cudaMemcpyAsync(nh->mrem, nrem.data(), sizeof(int) * nh->M, cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nh->merr, nerr.data(), sizeof(int) * nh->M, cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nh->dt_dev, ndt.data(), sizeof(double) * nh->M, cudaMemcpyHostToDevice, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) return abandon(fail(AMR_ECUDA, "amr_batch_repack: %s", cudaGetErrorString(e)));
+  }
+  // the handle takes the new mesh; the old one is freed
+  nh->own_stream = h->own_stream;
+  h->own_stream = false;
+  nh->event_pool.swap(h->event_pool);
+  nh->pending.swap(h->pending);
+  nh->timing = h->timing;
+  nh->launches = h->launches;
+  nh->graph_launches = h->graph_launches;
+  std::memcpy(nh->kernel_ms, h->kernel_ms, sizeof h->kernel_ms);
+  std::memcpy(nh->kernel_n, h->kernel_n, sizeof h->kernel_n);
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  std::swap(*h, *nh);
+  destroy_all(nh);
+  return check_device(h, "amr_batch_repack");
+}
+
 // FP64 conservation totals of the selected member's leaf cells (one level, or
 // every level added in ascending order); fixed grid per level size, so the
 // order of every addition is fixed.

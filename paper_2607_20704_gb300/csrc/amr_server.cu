@@ -2,15 +2,20 @@
 // library (include/amr.h, amr_server_*).
 //
 // Requests (one mesh, a number of coarse steps, a precision) are queued by
-// amr_server_submit.  A scheduler thread admits queued requests, in arrival
-// order, whenever the device budget and the wave slots allow: the requests
-// admitted together form a wave, one batched handle on a stream of its own,
+// amr_server_submit.  A scheduler thread admits, in arrival order, every
+// queued request that fits the device budget (a request that does not fit
+// waits without holding back later ones): it joins a running wave of its
+// precision that has a free member slot, else it starts a new wave while
+// wave slots remain.  A wave is one batched handle on a stream of its own,
 // in which every member stops after its own number of coarse steps (the
-// handle's per-member step counters).  Waves admitted while others run
-// overlap with them on the GPU.  Each wave keeps at most two coarse steps in
-// flight; a CUDA event per coarse step tells the scheduler when members are
-// finished, their final state is copied to host memory, and a wave whose
-// members are all finished releases its device memory for the next wave.
+// handle's per-member step counters); waves overlap on the GPU.  Each wave
+// keeps at most two coarse steps in flight; a CUDA event per coarse step
+// tells the scheduler when members are finished, and their final state is
+// copied to host memory.  Between coarse steps a wave is repacked
+// (amr_batch_repack) when requests wait to join it or when finished members
+// hold a quarter of its octs: finished members are dropped, their device
+// memory and budget return, joining requests are added, and the members that
+// keep running continue bit for bit as they would alone.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -65,10 +70,15 @@ struct Request {
 struct Wave {
   amr_handle h = nullptr;
   cudaStream_t s = nullptr;
-  std::vector<Request *> reqs;
-  int max_steps = 0, issued = 0, completed = 0;
+  int precision = 8;
+  std::vector<Request *> reqs;     // members, in the handle's member order
+  std::vector<int> joined;         // coarse steps the wave had completed when each joined
+  std::vector<Request *> joiners;  // admitted, to be added at the next repack
+  int issued = 0, completed = 0;
   std::vector<cudaEvent_t> ev;
-  size_t bytes = 0;
+  size_t bytes = 0;        // device bytes of the handle
+  size_t reserved = 0;     // budget held for the joiners
+  bool want_repack = false;
 };
 
 // device bytes of a handle per oct, for admission before the handle exists
@@ -108,62 +118,117 @@ struct amr_server {
 
   void loop();
   bool admit();
+  void start_wave(std::vector<Request *> take);
   bool progress(Wave *w);
+  void repack(Wave *w);
   void finish_member(Wave *w, Request *r, int member);
+  void joined_now(Wave *w, Request *r, int member, double t);
 };
 
+namespace {
+
+amr_member member_of(const Request *r) {
+  amr_member m{};
+  m.levelmin = r->levelmin;
+  m.levelmax = r->levelmax;
+  m.gamma = r->gamma;
+  m.cfl = r->cfl;
+  m.smallr = r->smallr;
+  m.smallc = r->smallc;
+  m.n_oct = int64_t(r->level.size());
+  m.level = r->level.data();
+  m.i = r->i.data();
+  m.j = r->j.data();
+  m.k = r->k.data();
+  m.hilbert_key = r->hk.empty() ? nullptr : r->hk.data();
+  m.U = r->U.data();
+  return m;
+}
+
+}  // namespace
+
+// bookkeeping of a request that has just become member `member` of a wave
+// (mu held)
+void amr_server::joined_now(Wave *w, Request *r, int member, double t) {
+  r->t_admit = t;
+  ++admitted;
+  queue_waits.push_back(1e3 * (t - r->t_submit));
+  amr_select_member(w->h, member);
+  amr_info mi;
+  amr_get_info(w->h, &mi);
+  double per_step = 0;
+  for (int l = r->levelmin; l <= 15; ++l)
+    if (mi.level_octs[l]) per_step += double(mi.level_leaf_cells[l]) * double(int64_t(1) << (l - r->levelmin));
+  r->work = per_step * r->steps;
+}
+
+// Admission, in arrival order: every queued request whose estimated bytes
+// fit the remaining budget joins a running wave of its precision with a
+// free member slot, or starts a new wave (with the other new requests of
+// its precision) while wave slots remain.  A request marked solo starts a
+// wave of its own.
 bool amr_server::admit() {
-  std::vector<Request *> take;
+  std::vector<std::vector<Request *>> groups;
   {
     std::lock_guard<std::mutex> g(mu);
-    if (queue.empty() || int(waves.size()) >= p.max_waves) return false;
-    const int prec = queue.front()->precision;
-    size_t budget_left = p.hbm_budget_bytes > bytes_in_use ? p.hbm_budget_bytes - bytes_in_use : 0;
-    size_t need = 0;
-    // in arrival order: the wave takes the leading requests of one precision
-    // that fit the remaining budget; a request marked solo goes alone
-    while (!queue.empty() && int(take.size()) < p.max_wave_members) {
-      Request *r = queue.front();
-      if (r->precision != prec || need + r->est_bytes > budget_left) break;
-      if (r->solo && !take.empty()) break;
-      need += r->est_bytes;
-      take.push_back(r);
-      queue.pop_front();
-      if (r->solo) break;
+    if (queue.empty()) return false;
+    size_t left = p.hbm_budget_bytes > bytes_in_use ? p.hbm_budget_bytes - bytes_in_use : 0;
+    int slots = p.max_waves - int(waves.size());
+    int open[2] = {-1, -1};  // the new group of each precision
+    for (auto it = queue.begin(); it != queue.end();) {
+      Request *r = *it;
+      if (r->est_bytes > left) {
+        ++it;
+        continue;
+      }
+      Wave *w = nullptr;
+      if (!r->solo)
+        for (Wave *x : waves)
+          if (x->precision == r->precision && int(x->reqs.size() + x->joiners.size()) < p.max_wave_members) {
+            w = x;
+            break;
+          }
+      const int pi = r->precision == 8 ? 1 : 0;
+      if (w) {
+        w->joiners.push_back(r);
+        w->reserved += r->est_bytes;
+      } else if (!r->solo && open[pi] >= 0 && int(groups[size_t(open[pi])].size()) < p.max_wave_members) {
+        groups[size_t(open[pi])].push_back(r);
+      } else if (slots > 0) {
+        --slots;
+        groups.push_back({r});
+        if (!r->solo) open[pi] = int(groups.size()) - 1;
+      } else {
+        ++it;
+        continue;
+      }
+      left -= r->est_bytes;
+      bytes_in_use += r->est_bytes;
+      it = queue.erase(it);
     }
-    if (take.empty()) return false;
-    bytes_in_use += need;
   }
+  for (auto &gq : groups) start_wave(gq);
+  return !groups.empty();
+}
+
+void amr_server::start_wave(std::vector<Request *> take) {
   Wave *w = new Wave();
   w->reqs = take;
-  for (auto *r : take) w->bytes += r->est_bytes;
+  w->precision = take[0]->precision;
+  size_t est = 0;
+  for (auto *r : take) est += r->est_bytes;
   cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking);
   amr_params prm;
   amr_params_default(&prm);
-  prm.precision = take[0]->precision;
+  prm.precision = w->precision;
   prm.stream = w->s;
   prm.tile = p.tile ? p.tile : 128;
   prm.schedule = p.schedule >= 0 ? p.schedule : 0;
   std::vector<amr_member> mem(take.size());
   std::vector<int32_t> steps(take.size());
   for (size_t q = 0; q < take.size(); ++q) {
-    Request *r = take[q];
-    amr_member &m = mem[q];
-    m.levelmin = r->levelmin;
-    m.levelmax = r->levelmax;
-    m.gamma = r->gamma;
-    m.cfl = r->cfl;
-    m.smallr = r->smallr;
-    m.smallc = r->smallc;
-    m.n_oct = int64_t(r->level.size());
-    m.level = r->level.data();
-    m.i = r->i.data();
-    m.j = r->j.data();
-    m.k = r->k.data();
-    m.hilbert_key = r->hk.empty() ? nullptr : r->hk.data();
-    m.U = r->U.data();
-    steps[q] = r->steps;
-    w->max_steps = std::max(w->max_steps, r->steps);
+    mem[q] = member_of(take[q]);
+    steps[q] = take[q]->steps;
   }
   amr_status s = amr_create_batch(&prm, int(take.size()), mem.data(), &w->h);
   if (s == AMR_OK) s = amr_set_member_steps(w->h, steps.data(), int(steps.size()));
@@ -175,12 +240,12 @@ bool amr_server::admit() {
     if (w->h) amr_destroy(w->h);
     cudaStreamDestroy(w->s);
     delete w;
-    bytes_in_use -= std::min(bytes_in_use, need_bytes(take));
+    bytes_in_use -= std::min(bytes_in_use, est);
     for (auto it = take.rbegin(); it != take.rend(); ++it) {
       (*it)->solo = true;
       queue.push_front(*it);
     }
-    return true;
+    return;
   }
   if (s != AMR_OK) {
     // the request fails with the handle's error; its budget returns
@@ -191,33 +256,21 @@ bool amr_server::admit() {
       r->t_done = t;
       ++failed;
     }
-    bytes_in_use -= w->bytes;
+    bytes_in_use -= std::min(bytes_in_use, est);
     if (w->h) amr_destroy(w->h);
     cudaStreamDestroy(w->s);
     delete w;
     cv_done.notify_all();
-    return true;
+    return;
   }
   amr_info inf;
   amr_get_info(w->h, &inf);
   // account the handle's real footprint instead of the estimate
-  bytes_in_use = bytes_in_use - w->bytes + size_t(inf.device_bytes);
+  bytes_in_use = bytes_in_use - std::min(bytes_in_use, est) + size_t(inf.device_bytes);
   w->bytes = size_t(inf.device_bytes);
-  for (size_t q = 0; q < take.size(); ++q) {
-    Request *r = take[q];
-    r->t_admit = t;
-    ++admitted;
-    queue_waits.push_back(1e3 * (t - r->t_submit));
-    amr_select_member(w->h, int(q));
-    amr_info mi;
-    amr_get_info(w->h, &mi);
-    double per_step = 0;
-    for (int l = r->levelmin; l <= 15; ++l)
-      if (mi.level_octs[l]) per_step += double(mi.level_leaf_cells[l]) * double(int64_t(1) << (l - r->levelmin));
-    r->work = per_step * r->steps;
-  }
+  w->joined.assign(take.size(), 0);
+  for (size_t q = 0; q < take.size(); ++q) joined_now(w, take[q], int(q), t);
   waves.push_back(w);
-  return true;
 }
 
 void amr_server::finish_member(Wave *w, Request *r, int member) {
@@ -263,12 +316,130 @@ void amr_server::finish_member(Wave *w, Request *r, int member) {
   cv_done.notify_all();
 }
 
-// Issue coarse steps (at most two in flight), finish members whose steps are
-// done; true when the wave is finished and can be dropped.
+// Between coarse steps: drop the finished members, add the joiners.  If the
+// joiners cannot be added together (an invalid mesh among them), they are
+// added one at a time and only the invalid one fails.
+void amr_server::repack(Wave *w) {
+  std::vector<int32_t> keep;
+  std::vector<Request *> reqs;
+  std::vector<int> joined;
+  for (size_t q = 0; q < w->reqs.size(); ++q)
+    if (!w->reqs[q]->done) {
+      keep.push_back(int32_t(q));
+      reqs.push_back(w->reqs[q]);
+      joined.push_back(w->joined[q]);
+    }
+  std::vector<Request *> add = w->joiners;
+  std::vector<amr_member> mem;
+  std::vector<int32_t> steps;
+  for (auto *r : add) {
+    mem.push_back(member_of(r));
+    steps.push_back(r->steps);
+  }
+  std::vector<Request *> joined_ok, joined_bad;
+  std::string bad_msg;
+  amr_status s = keep.empty() && add.empty()
+                     ? AMR_OK
+                     : amr_batch_repack(w->h, int(keep.size()), keep.data(), int(add.size()), mem.data(),
+                                        steps.data());
+  if (s == AMR_OK) {
+    joined_ok = add;
+  } else {
+    // drop the finished members first, then try the joiners one by one
+    s = keep.empty() ? AMR_OK : amr_batch_repack(w->h, int(keep.size()), keep.data(), 0, nullptr, nullptr);
+    if (s != AMR_OK) {
+      // the wave itself cannot be rebuilt: its running members fail
+      const std::string msg = amr_last_error();
+      std::lock_guard<std::mutex> g(mu);
+      for (auto *r : reqs) {
+        r->failed = r->done = true;
+        r->error = msg;
+        r->t_done = now_s();
+        ++failed;
+      }
+      for (auto *r : add) {
+        r->failed = r->done = true;
+        r->error = msg;
+        r->t_done = now_s();
+        ++failed;
+      }
+      reqs.clear();
+      joined.clear();
+      add.clear();
+      w->joiners.clear();
+      cv_done.notify_all();
+    } else {
+      for (size_t q = 0; q < add.size(); ++q) {
+        std::vector<int32_t> all;
+        for (size_t t = 0; t < reqs.size() + joined_ok.size(); ++t) all.push_back(int32_t(t));
+        amr_status sj = amr_batch_repack(w->h, int(all.size()), all.data(), 1, &mem[q], &steps[q]);
+        if (sj == AMR_OK) {
+          joined_ok.push_back(add[q]);
+        } else {
+          joined_bad.push_back(add[q]);
+          bad_msg = amr_last_error();
+        }
+      }
+    }
+  }
+  const double t = now_s();
+  amr_info inf;
+  amr_get_info(w->h, &inf);
+  std::lock_guard<std::mutex> g(mu);
+  for (auto *r : joined_bad) {
+    r->failed = r->done = true;
+    r->error = bad_msg;
+    r->t_done = t;
+    ++failed;
+  }
+  bytes_in_use -= std::min(bytes_in_use, w->bytes + w->reserved);
+  w->reserved = 0;
+  w->joiners.clear();
+  w->reqs = reqs;
+  w->joined = joined;
+  for (auto *r : joined_ok) {
+    w->reqs.push_back(r);
+    w->joined.push_back(w->completed);
+    joined_now(w, r, int(w->reqs.size()) - 1, t);
+  }
+  w->bytes = w->reqs.empty() ? 0 : size_t(inf.device_bytes);
+  bytes_in_use += w->bytes;
+  if (!joined_bad.empty()) cv_done.notify_all();
+}
+
+// Finish members whose steps are done, repack when joiners wait or finished
+// members hold a quarter of the octs (once the wave is idle), issue coarse
+// steps (at most two in flight); true when the wave has nothing left.
 bool amr_server::progress(Wave *w) {
   while (w->completed < int(w->ev.size()) && cudaEventQuery(w->ev[w->completed]) == cudaSuccess)
     ++w->completed;
-  while (w->issued < w->max_steps && w->issued - w->completed < 2) {
+  int64_t fin_octs = 0, all_octs = 0;
+  bool running = false;
+  for (size_t q = 0; q < w->reqs.size(); ++q) {
+    Request *r = w->reqs[q];
+    if (!r->done && w->completed - w->joined[q] >= r->steps) finish_member(w, r, int(q));
+    const int64_t n = int64_t(r->level.size());
+    all_octs += n;
+    if (r->done)
+      fin_octs += n;
+    else
+      running = true;
+  }
+  bool want_repack;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!running && w->joiners.empty()) return true;
+    want_repack = !w->joiners.empty() || (fin_octs > 0 && 4 * fin_octs >= all_octs);
+  }
+  if (want_repack) {
+    if (w->issued != w->completed) return false;  // let the steps in flight finish
+    repack(w);
+    if (w->reqs.empty()) return true;
+  }
+  int need = 0;
+  for (size_t q = 0; q < w->reqs.size(); ++q)
+    if (!w->reqs[q]->done) need = std::max(need, w->joined[q] + w->reqs[q]->steps - w->issued);
+  while (need > 0 && w->issued - w->completed < 2) {
     if (amr_advance(w->h, 1, nullptr) != AMR_OK) {
       const std::string msg = amr_last_error();
       std::lock_guard<std::mutex> g(mu);
@@ -286,17 +457,9 @@ bool amr_server::progress(Wave *w) {
     cudaEventRecord(e, w->s);
     w->ev.push_back(e);
     ++w->issued;
+    --need;
   }
-  bool all = true;
-  for (size_t q = 0; q < w->reqs.size(); ++q) {
-    Request *r = w->reqs[q];
-    if (r->done) continue;
-    if (w->completed >= r->steps)
-      finish_member(w, r, int(q));
-    else
-      all = false;
-  }
-  return all;
+  return false;
 }
 
 void amr_server::loop() {
@@ -313,7 +476,9 @@ void amr_server::loop() {
         cudaStreamDestroy(w->s);
         {
           std::lock_guard<std::mutex> g(mu);
-          bytes_in_use -= std::min(bytes_in_use, w->bytes);
+          bytes_in_use -= std::min(bytes_in_use, w->bytes + w->reserved);
+          // joiners of a wave that ended before their repack go back to the queue
+          for (auto it = w->joiners.rbegin(); it != w->joiners.rend(); ++it) queue.push_front(*it);
         }
         delete w;
         waves.erase(waves.begin() + t);

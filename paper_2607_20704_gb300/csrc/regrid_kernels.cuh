@@ -256,6 +256,34 @@ __global__ void k_regrid_emit(RegridArgs a, const T *__restrict__ U, const uint3
   }
 }
 
+// Batch repack: every oct of a kept member goes to its place in the new oct
+// list (member id remapped, state widened to FP64 exactly); octs of dropped
+// members (remap -1) are left out.  dst[m] is the new list position of old
+// member m's first oct, base[m] its old first mesh index.
+template <class T>
+__global__ void k_repack_emit(int64_t N, int64_t S, const uint64_t *__restrict__ key,
+                              const T *__restrict__ U, const int *__restrict__ remap,
+                              const int64_t *__restrict__ dst, const int64_t *__restrict__ base,
+                              int64_t n_out, uint8_t *lvl, uint16_t *mem, uint32_t *oi, uint32_t *oj,
+                              uint32_t *ok, double *Uout) {
+  const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (o >= N) return;
+  const uint64_t k = key[o];
+  const int mb = ikey_member(k);
+  const int nm = remap[mb];
+  if (nm < 0) return;
+  const int64_t t = dst[mb] + (o - base[mb]);
+  lvl[t] = uint8_t(ikey_lev(k));
+  mem[t] = uint16_t(nm);
+  oi[t] = ikey_x(k);
+  oj[t] = ikey_y(k);
+  ok[t] = ikey_z(k);
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Uout[v * 8 * n_out + 8 * t + c] = double(U[v * S + 8 * o + c]);
+}
+
 // new octs of [lo, hi) (one level) take the minmod prolongation of their
 // father cell from the father's face neighbours (all real after grading)
 template <class T>

@@ -130,3 +130,53 @@ def test_tile_size_and_schedule_do_not_change_results():
     for other in outs[1:]:
         for a, c in zip(outs[0], other):
             assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("precision", [8, 4])
+def test_repack_keeps_members_bit_for_bit(precision):
+    """A batch repacked between coarse steps (one finished member dropped, a
+    new mesh added): every member's state equals the same mesh advanced
+    alone, bit for bit, and step counts carry over."""
+    from paper_2607_20704_gb300 import amr
+    kw = dict(precision=precision, tile=128, schedule=0)
+    probs = [inputs.sod(3, 5), inputs.random_mesh(3, 5, seed=71), inputs.sedov(4, 5, radii={5: 0.15})]
+    new = inputs.random_mesh(3, 4, seed=72)
+    b = amr.Mesh.batch(probs, **kw)
+    b.set_member_steps([5, 2, -1])
+    b.advance(2, sync=True)
+    b.repack([0, 2], [new], [3])
+    assert b.n_members == 3
+    b.advance(3, sync=True)
+    for q, (pr, n) in enumerate([(probs[0], 5), (probs[2], 5), (new, 3)]):
+        a = amr.Mesh(*pr.mesh_args(), **pr.params(), **kw)
+        a.advance(n, sync=True)
+        b.select(q)
+        assert b.levels() == a.levels(), q
+        for l in a.levels():
+            ka, Ua = a.read(l)
+            kb, Ub = b.read(l)
+            assert np.array_equal(ka, kb) and np.array_equal(Ua, Ub), (q, l)
+        a.close()
+    # a repack that only drops members, then one that only adds
+    b.repack([1])
+    b.repack([0], [probs[1]], [-1])
+    assert b.n_members == 2
+    b.close()
+
+
+def test_repack_rejects_bad_arguments_and_keeps_the_handle():
+    from paper_2607_20704_gb300 import amr
+    probs = [inputs.sod(3, 4), inputs.random_mesh(3, 4, seed=73)]
+    b = amr.Mesh.batch(probs)
+    before = [b.select(q).read(3)[1].copy() for q in range(2)]
+    for keep in ([1, 0], [0, 0], [2], []):
+        with pytest.raises(amr.AmrError) as e:
+            b.repack(keep)
+        assert e.value.status == amr.AMR_EINVAL
+    bad = inputs.sod(3, 4)
+    bad.level[0] = 7  # a level-7 oct in a levelmax-4 mesh
+    with pytest.raises(amr.AmrError):
+        b.repack([0], [bad], [1])
+    for q in range(2):
+        assert np.array_equal(b.select(q).read(3)[1], before[q])
+    b.close()
