@@ -685,7 +685,9 @@ def inputs_gaussian(n, rng):
 def run_serving(n_requests, rates, torch):
     """Serving loop under Poisson arrivals at each rate of the sweep: p50/p99
     latency (submit -> result on the host) and sustained leaf cell-updates/s
-    (completed work / first submission -> last completion)."""
+    (completed work / first submission -> last completion).  The low rates
+    load the GPU below its capacity, so their latency is the solve itself;
+    the high ones saturate it and add queueing."""
     import random
     from paper_2607_20704_gb300 import amr, inputs
     probs, reqs = inputs.serving_requests(n_requests, seed=13)
@@ -962,7 +964,7 @@ def main():
                         for p in (8, 4)}
         serving = None
         if not args.no_serving:
-            serving = run_serving(args.serving_requests, (10.0, 40.0, 160.0), torch)
+            serving = run_serving(args.serving_requests, (2.0, 4.0, 10.0, 40.0), torch)
         batched = None
         if not args.no_batched:
             ens = inputs.batched(args.batched_members, seed=11)
