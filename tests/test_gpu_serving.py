@@ -2,9 +2,9 @@
 result must be bit-identical to the same solve alone, and match the FP64
 oracle (FP64 requests within the chained-step tolerance 1e-11, FP32
 requests by the L1 error of rho and E relative to the oracle's L1 norm,
-below 2e-5 after up to seven coarse steps: FP32 round-off, 6e-8 per
-operation, carried through the steps' limiter and Riemann solves; the
-measured values are printed)."""
+below 5e-6 after up to seven coarse steps, the bound of the other FP32
+tests: FP32 round-off, 6e-8 per operation, carried through the steps'
+limiter and Riemann solves; measured 4e-8 .. 7e-8, printed)."""
 import time
 
 import numpy as np
@@ -48,8 +48,12 @@ _ORACLE = {}
 
 def _oracle(prob, steps):
     """The FP64 oracle's state after `steps` coarse steps, per level."""
+    import hashlib
     import oracle
-    key = (id(prob), steps)
+    dig = hashlib.sha1()
+    for arr in (prob.level, prob.i, prob.j, prob.k, prob.U):
+        dig.update(np.ascontiguousarray(arr).tobytes())
+    key = (dig.hexdigest(), prob.gamma, steps)
     if key not in _ORACLE:
         o = oracle.Mesh(*prob.mesh_args(), **prob.params())
         o.advance(steps)
@@ -74,7 +78,7 @@ def _check_against_oracle(srv, rid, prob, steps, prec):
             num[t] += np.abs(Ug[v] - Uo[v]).sum()
             den[t] += np.abs(Uo[v]).sum()
     l1 = float((num / den).max())
-    assert l1 < 2e-5, (rid, l1)
+    assert l1 < 5e-6, (rid, l1)
     return l1
 
 
