@@ -5,9 +5,10 @@ Workload: the Sedov blast on a static graded octree, levels 7-10 (128^3 base
 cells, nested refined balls of radius 0.12 / 0.06 / 0.03 around the centre,
 about 2.4 M leaf cells), gamma = 5/3, synthetic seeded input.  One step is
 one coarse time step of the level-by-level W-cycle through the C ABI
-(amr_advance): rebuild of the hash table, neighbour array and ghost cache,
-device CFL reduction, then every level step (ghosts, primitives, predictor,
-HLLC fluxes, update, reflux, restriction) with 2^(l-7) substeps per level.
+(amr_advance): device CFL reduction, then every level step (ghosts,
+primitives, predictor, HLLC fluxes, update, reflux, restriction) with
+2^(l-7) substeps per level; the static mesh's hash table, neighbour array
+and ghost cache are built once, at creation.
 The unit of work is one leaf cell advanced by one level step.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
@@ -857,6 +858,20 @@ def roofline(res, prec, levelmin, peak_gbs, peak_src, fp64_tflops=None, dgemm=No
     return rl, table
 
 
+def workload_config(n_oct, n_ghost, leaf, upd, world):
+    """The workload as both arms name it (the GPU arm and the CPU reference
+    arm print the same dict for the same mesh)."""
+    return {"workload": WORKLOAD, "levelmin": 7, "levelmax": 10, "gamma": 5.0 / 3.0,
+            "n_oct": int(n_oct), "n_ghost_oct": int(n_ghost), "leaf_cells": int(leaf),
+            "cell_updates_per_step": int(upd),
+            "step": "one coarse W-cycle step (CFL + 15 level steps; the static mesh is indexed "
+                    "once, at creation)",
+            "l2": f"GPU arm: a {L2_FLUSH_BYTES >> 20} MiB write between timed steps; CPU "
+                  "reference arm: no device",
+            "parallelism": (f"{world} GPU processes, replicas; the CPU reference arm runs on rank 0"
+                            if world > 1 else "single GPU; the CPU reference arm on the host")}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -873,6 +888,8 @@ def main():
         m = oracle.Mesh(*prob.mesh_args(), **prob.params())
         upd = sum(int(np.count_nonzero(m.read_split(l) == 0)) * 2 ** (l - prob.levelmin)
                   for l in m.levels())
+        leaf = sum(int(np.count_nonzero(m.read_split(l) == 0)) for l in m.levels())
+        n_ghost = sum(m.num_cache(l) for l in m.levels())
         m.advance(args.warmup)
         t0 = time.perf_counter()
         m.advance(args.steps)
@@ -883,8 +900,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "levelmin": 7, "levelmax": 10, "n_oct": prob.n_oct,
-                           "cell_updates_per_step": upd},
+                "config": workload_config(prob.n_oct, n_ghost, leaf, upd, world),
                 "cpu_baseline": {"value": v, "unit": "leaf cell-updates/s", "cores": 1,
                                  "kind": "oracle",
                                  "sample": f"{args.steps} full coarse steps of the workload, "
@@ -1003,12 +1019,8 @@ def main():
         "vs_baseline": None,
         "dtype": "f64" if prec_main == 8 else "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "levelmin": 7, "levelmax": 10, "gamma": 5.0 / 3.0,
-                   "n_oct": main_res["info"]["n_oct"], "n_ghost_oct": main_res["info"]["n_cache"],
-                   "leaf_cells": main_res["info"]["n_leaf_cells"],
-                   "cell_updates_per_step": upd, "step": "one coarse W-cycle step (CFL + 15 level "
-                   "steps; the static mesh is indexed once, at creation)", "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(main_res["info"]["n_oct"], main_res["info"]["n_cache"],
+                                  main_res["info"]["n_leaf_cells"], upd, world),
         "roofline": rl,
         "step_roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak_gbs,
                           "achieved": round(value / world * step_bytes / 1e9, 1),

@@ -80,3 +80,12 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "sedov_l7-10_static_nested_balls"
+    # the same config dict as the GPU arm prints for this mesh (the GPU
+    # arm's counts come from the library; the ghost and leaf counts of the
+    # mesh are pinned against the oracle by the parity tests)
+    import bench
+    from paper_2607_20704_gb300 import inputs
+    prob = inputs.sedov()
+    want = bench.workload_config(prob.n_oct, d["config"]["n_ghost_oct"], prob.leaf_cells(), upd, 1)
+    assert d["config"] == want
+    assert d["config"]["leaf_cells"] == 2416184 and d["config"]["n_ghost_oct"] == 14280
