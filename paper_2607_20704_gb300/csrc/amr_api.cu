@@ -113,10 +113,12 @@ enum Dom {
   DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_BLOCKS = 4, DOM_COMMIT = 5, DOM_COUNT = 6
 };
 
-// a list of segments and, per domain, its flattened tiles
+// a list of segments and, per domain, its tiles: the offset of its tile
+// prefix (nseg + 1 cumulative counts) in the handle's prefix array, and the
+// number of tiles
 struct SegList {
   int seg0 = 0, nseg = 0;
-  int tile0[DOM_COUNT] = {0, 0, 0, 0, 0}, ntile[DOM_COUNT] = {0, 0, 0, 0, 0};
+  int tpre0[DOM_COUNT] = {0, 0, 0, 0, 0, 0}, ntile[DOM_COUNT] = {0, 0, 0, 0, 0, 0};
   int ls = 0;  // scratch cells used
 };
 
@@ -176,9 +178,9 @@ struct amr_mesh {
 
   // segments and tiles
   std::vector<Seg> segs_h;
-  std::vector<Tile> tiles_h;
+  std::vector<int> tpre_h;
   Seg *segs = nullptr;
-  Tile *tiles = nullptr;
+  int *tpre = nullptr;
   std::vector<SegList> phases;
   SegList level_list[kMaxLev + 1], restrict_list[kMaxLev + 1], cfl_list;
   int tile_size = 256;
@@ -503,13 +505,16 @@ static SegList make_list(amr_mesh *h, const std::vector<std::pair<int, int>> &ml
   L.nseg = int(h->segs_h.size()) - L.seg0;
   L.ls = base;
   for (int d = 0; d < DOM_COUNT; ++d) {
-    L.tile0[d] = int(h->tiles_h.size());
+    L.tpre0[d] = int(h->tpre_h.size());
+    const int step = d == DOM_BLOCKS ? 1 : h->tile_size;  // one block of octs per tile
+    int acc = 0;
     for (int q = 0; q < L.nseg; ++q) {
+      h->tpre_h.push_back(acc);
       const int n = dom_size(h->segs_h[L.seg0 + q], d);
-      const int step = d == DOM_BLOCKS ? 1 : h->tile_size;  // one block of octs per tile
-      for (int st = 0; st < n; st += step) h->tiles_h.push_back({L.seg0 + q, st});
+      acc += (n + step - 1) / step;
     }
-    L.ntile[d] = int(h->tiles_h.size()) - L.tile0[d];
+    h->tpre_h.push_back(acc);
+    L.ntile[d] = acc;
   }
   return L;
 }
@@ -524,7 +529,7 @@ static void w_cycle(const Member &m, int l, std::vector<int> &out) {
 
 static void build_lists(amr_mesh *h) {
   h->segs_h.clear();
-  h->tiles_h.clear();
+  h->tpre_h.clear();
   h->phases.clear();
   size_t P = 0;
   for (auto &m : h->mem) {
@@ -567,6 +572,16 @@ static void build_lists(amr_mesh *h) {
 // ---------------------------------------------------------------------------
 // level-step launches
 // ---------------------------------------------------------------------------
+// the tiles of domain `dom` of list L in the launch arguments
+template <class A>
+static void set_tiles(amr_mesh *h, A &a, const SegList &L, int dom) {
+  a.tpre = h->tpre + L.tpre0[dom];
+  a.tseg0 = L.seg0;
+  a.tnseg = L.nseg;
+  a.tstep = dom == DOM_BLOCKS ? 1 : h->tile_size;
+  a.ntiles = L.ntile[dom];
+}
+
 template <class T>
 static StepArgs<T> step_args(amr_mesh *h, bool device_dt, double dt) {
   StepArgs<T> a{};
@@ -608,8 +623,7 @@ template <class T>
 static void run_list(amr_mesh *h, int kid, void (*kern)(StepArgs<T>), StepArgs<T> a,
                      const SegList &L, int dom) {
   if (L.ntile[dom] == 0) return;
-  a.tiles = h->tiles + L.tile0[dom];
-  a.ntiles = L.ntile[dom];
+  set_tiles(h, a, L, dom);
   int grid = a.ntiles;
   if (h->persistent) {
     int per_sm = 0;
@@ -632,8 +646,7 @@ static void run_list(amr_mesh *h, int kid, void (*kern)(StepArgs<T>), StepArgs<T
 template <class T, int NS>
 static void run_rock_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
   if (L.ntile[DOM_BLOCKS] == 0) return;
-  a.tiles = h->tiles + L.tile0[DOM_BLOCKS];
-  a.ntiles = L.ntile[DOM_BLOCKS];
+  set_tiles(h, a, L, DOM_BLOCKS);
   constexpr size_t smem = Rock<NS>::template smem<T>();
   auto kern = k_rock<T, NS>;
   int per_sm = 0;
@@ -656,8 +669,7 @@ static void run_rock_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
 template <class T, int NS>
 static void run_sweep_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
   if (L.ntile[DOM_BLOCKS] == 0) return;
-  a.tiles = h->tiles + L.tile0[DOM_BLOCKS];
-  a.ntiles = L.ntile[DOM_BLOCKS];
+  set_tiles(h, a, L, DOM_BLOCKS);
   constexpr size_t smem = Sweep<NS>::template smem<T>();
   auto kern = k_sweep<T, NS>;
   int per_sm = 0;
@@ -733,8 +745,7 @@ static void restrict_segments(amr_mesh *h, const SegList &L) {
 static CflArgs cfl_args(amr_mesh *h) {
   CflArgs a{};
   a.segs = h->segs;
-  a.tiles = h->tiles + h->cfl_list.tile0[DOM_REAL];
-  a.ntiles = h->cfl_list.ntile[DOM_REAL];
+  set_tiles(h, a, h->cfl_list, DOM_REAL);
   a.S = h->S;
   a.son = h->son;
   a.mgamma = h->mgamma_d;
@@ -1187,7 +1198,7 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   if (h->nsub > 0) AMR_TRY(build_blocks(h));
   build_lists(h);
   AMR_TRY(upload(h, &h->segs, h->segs_h));
-  AMR_TRY(upload(h, &h->tiles, h->tiles_h));
+  AMR_TRY(upload(h, &h->tpre, h->tpre_h));
   h->max_cs = 24 * NC;
   AMR_TRY(ensure_scratch(h));
   if (h->max_cs) CUDA_TRY(cudaMemsetAsync(h->C, 0, es * 5 * size_t(h->max_cs), h->s));
@@ -1424,7 +1435,7 @@ static amr_status build_blocks(amr_mesh *h) {
 // (segments and scratch do not depend on them).
 static amr_status set_tile(amr_mesh *h, int tile, int nsub, bool planar = false) {
   h->planar = planar;
-  if (tile == h->tile_size && nsub == h->nsub && h->tiles) return AMR_OK;
+  if (tile == h->tile_size && nsub == h->nsub && h->tpre) return AMR_OK;
   h->tile_size = tile;
   if (nsub != h->nsub) {
     h->nsub = nsub;
@@ -1433,11 +1444,11 @@ static amr_status set_tile(amr_mesh *h, int tile, int nsub, bool planar = false)
   h->occ.clear();
   build_lists(h);
   dev_free(h, h->segs);
-  dev_free(h, h->tiles);
+  dev_free(h, h->tpre);
   h->segs = nullptr;
-  h->tiles = nullptr;
+  h->tpre = nullptr;
   AMR_TRY(upload(h, &h->segs, h->segs_h));
-  AMR_TRY(upload(h, &h->tiles, h->tiles_h));
+  AMR_TRY(upload(h, &h->tpre, h->tpre_h));
   return AMR_OK;
 }
 

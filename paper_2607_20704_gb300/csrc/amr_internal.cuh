@@ -212,9 +212,9 @@ __device__ __forceinline__ int32_t hash_probe1(HashView h, uint64_t key) {
   return 0;
 }
 
+// x modulo a power-of-two period (cells or octs per axis of a level)
 __device__ __forceinline__ uint32_t wrapc(int64_t x, int64_t period) {
-  int64_t r = x % period;
-  return uint32_t(r < 0 ? r + period : r);
+  return uint32_t(x & (period - 1));
 }
 
 // Face directions: 2d = minus side, 2d+1 = plus side, d = 0 (x), 1 (y), 2 (z).

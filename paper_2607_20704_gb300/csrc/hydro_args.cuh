@@ -21,10 +21,27 @@ struct Seg {
 enum : int { kSegReflux = 1, kSegRestrict = 2 };
 
 // A launch covers a flattened list of tiles; tile (seg, start) is the block
-// of domain items [start, start + blockDim.x) of segment seg.
+// of domain items [start, start + step) of segment seg.  A list stores only
+// its segments' cumulative tile counts (tpre[q] = first tile of its q-th
+// segment, tpre[nseg] = all tiles); a kernel finds the segment of tile ti by
+// binary search.
 struct Tile {
   int seg, start;
 };
+
+// the last segment of the list whose first tile is <= ti (segments without
+// tiles share their successor's first tile and are passed over)
+__device__ __forceinline__ Tile tile_at(const int *__restrict__ tpre, int seg0, int nseg, int step, int ti) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(tpre + mid) <= ti)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return Tile{seg0 + lo, (ti - __ldg(tpre + lo)) * step};
+}
 
 // Everything a level-step launch needs, passed by value.  Oct counts and cell
 // indices fit in 32 bits (at most 2^26 real octs, and 8 (real + ghost octs)
@@ -48,8 +65,8 @@ struct StepArgs {
   const int32_t *csrc;    // [7][NC] prolongation sources (global cell indices)
   T *W, *Q, *F, *C;       // scratch W[5][LS], Q[20][LS], F[15][LS]; slots C[5][CS]
   const Seg *segs;
-  const Tile *tiles;
-  int ntiles;
+  const int *tpre;                  // the list's tile prefix (see Tile)
+  int tseg0, tnseg, tstep, ntiles;  // first segment, segments, items per tile, tiles
   // per member: gamma, 1/(gamma-1), floors
   const T *mgamma, *migm1, *msmallr, *msmallp;
   // dt/dx: from the device time step of each member's coarse step
@@ -66,8 +83,8 @@ struct StepArgs {
 
 struct CflArgs {
   const Seg *segs;
-  const Tile *tiles;
-  int ntiles;
+  const int *tpre;
+  int tseg0, tnseg, tstep, ntiles;
   int64_t S;
   const uint32_t *son;
   const double *mgamma, *msmallr, *msmallp, *mcfl;

@@ -145,7 +145,7 @@ __device__ __forceinline__ SegCtx<T> seg_ctx(const StepArgs<T> &a, int seg) {
 template <class T, class Size, class Body>
 __device__ __forceinline__ void tile_loop(const StepArgs<T> &a, Size size, Body body) {
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
-    const Tile td = a.tiles[ti];
+    const Tile td = tile_at(a.tpre, a.tseg0, a.tnseg, a.tstep, ti);
     if (a.mact && !__ldg(a.mact + a.segs[td.seg].member)) continue;  // finished member
     const SegCtx<T> sc = seg_ctx(a, td.seg);
 #ifdef AMR_CHECKED
@@ -674,7 +674,7 @@ __global__ void k_cfl(CflArgs a, const T *U) {
   double s = 0.0;
   int cur = -1;
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
-    const Tile td = a.tiles[ti];
+    const Tile td = tile_at(a.tpre, a.tseg0, a.tnseg, a.tstep, ti);
     if (td.seg != cur) {
       if (cur >= 0) cfl_flush<T>(a, s, cur, wmax);
       s = 0.0;

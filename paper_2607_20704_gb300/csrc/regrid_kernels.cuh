@@ -175,15 +175,15 @@ __global__ void k_flag_grade(RegridArgs a, int lo, int hi) {
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
-          const int64_t X = ((x + dx) % side + side) % side, Y = ((y + dy) % side + side) % side,
-                        Z = ((z + dz) % side + side) % side;
+          // periodic wrap (side is a power of two)
+          const int64_t X = (x + dx) & (side - 1), Y = (y + dy) & (side - 1), Z = (z + dz) & (side - 1);
           const int64_t px = X >> 1, py = Y >> 1, pz = Z >> 1;  // covering level-(l-1) cell
           // its oct, relative to the father cell's oct (oi>>1, oj>>1, ok>>1)
           int rel[3];
           const int64_t d3[3] = {(px >> 1) - int64_t(oi >> 1), (py >> 1) - int64_t(oj >> 1),
                                  (pz >> 1) - int64_t(okk >> 1)};
           for (int q = 0; q < 3; ++q) {
-            const int64_t dd = ((d3[q] % oside) + oside) % oside;
+            const int64_t dd = d3[q] & (oside - 1);  // oside is a power of two
             rel[q] = dd == 0 ? 0 : (dd == 1 ? 1 : -1);
           }
           const int32_t e = a.nbr27[((rel[2] + 1) * 9 + (rel[1] + 1) * 3 + (rel[0] + 1)) * int64_t(a.N) + fo];

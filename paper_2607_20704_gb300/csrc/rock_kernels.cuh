@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
   for (int q = t; q < NB; q += TH) pos_oct[q] = -1;
   __syncthreads();
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
-    const Tile td = a.tiles[ti];
+    const Tile td = tile_at(a.tpre, a.tseg0, a.tnseg, a.tstep, ti);
     const Seg sg = a.segs[td.seg];
     if (a.mact && !__ldg(a.mact + sg.member)) continue;  // finished member (block-uniform)
     const SegCtx<T> s = seg_ctx(a, td.seg);
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(Sweep<NS>::THREADS) k_sweep(StepArgs<T> a, con
                 ZF = R::ZF, FNP = R::FNP, TH = R::THREADS;
 
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
-    const Tile td = a.tiles[ti];
+    const Tile td = tile_at(a.tpre, a.tseg0, a.tnseg, a.tstep, ti);
     const Seg sg = a.segs[td.seg];
     if (a.mact && !__ldg(a.mact + sg.member)) continue;  // finished member (block-uniform)
     const SegCtx<T> s = seg_ctx(a, td.seg);
