@@ -82,7 +82,10 @@ typedef struct {
                                one coarse step (default) */
   size_t hbm_budget_bytes;  /* 0: no limit; else AMR_ENOMEM beyond it */
   void *stream;             /* cudaStream_t; NULL: the legacy default stream */
-  amr_alloc_fn alloc;       /* NULL: cudaMallocAsync on the stream */
+  amr_alloc_fn alloc;       /* NULL: the library's own stream-ordered pool on
+                               the current device (memory a handle frees stays
+                               reserved there for later allocations of the
+                               process, so regrids and repacks reuse it) */
   amr_free_fn free;
   void *alloc_user;
   int tile;                 /* cells (threads) per work tile: 64, 128, 256 or 512;

@@ -192,7 +192,7 @@ struct amr_mesh {
   int nsub = 0;
   bool planar = false;  // the fused kernel sweeps planes (paper kernel), else stages the cube (rock)
   int32_t *blk = nullptr;
-  std::vector<int32_t> blkid_h;
+  std::vector<int32_t> blk_first, blk_last;  // block of the first / last oct of each (member, level)
   std::vector<float> tune_ms;  // the autotuner's best step time per candidate
   // asynchronous whole-state copies: copy streams (uploads, downloads; each
   // direction its own, so that one never queues behind the other), input and
@@ -490,9 +490,10 @@ static SegList make_list(amr_mesh *h, const std::vector<std::pair<int, int>> &ml
     s.base = base;
     s.blk0 = 0;
     s.nblk = 0;
-    if (h->nsub > 0 && s.nl > 0 && !h->blkid_h.empty()) {
-      s.blk0 = h->blkid_h[size_t(s.lo)];
-      s.nblk = h->blkid_h[size_t(s.lo + s.nl - 1)] - s.blk0 + 1;
+    if (h->nsub > 0 && s.nl > 0 && !h->blk_first.empty()) {
+      const size_t ml = size_t(pr.first) * (kMaxLev + 1) + size_t(l);
+      s.blk0 = h->blk_first[ml];
+      s.nblk = h->blk_last[ml] - s.blk0 + 1;
     }
     if (mode == 1)
       s.flags = l > m.lmin ? kSegRestrict : 0;
@@ -1405,30 +1406,47 @@ static void coarse_step(amr_mesh *h);
 // several blocks (each updates only its own octs).
 static amr_status build_blocks(amr_mesh *h) {
   const int64_t N = h->N;
-  std::vector<uint64_t> key(size_t(N > 0 ? N : 1));
-  if (N > 0) {
-    CUDA_TRY(cudaMemcpyAsync(key.data(), h->key, 8 * size_t(N), cudaMemcpyDeviceToHost, h->s));
-    CUDA_TRY(cudaStreamSynchronize(h->s));
-  }
   const unsigned sh = h->nsub == 4 ? 2u : h->nsub == 2 ? 1u : 0u;
-  h->blkid_h.assign(size_t(N), 0);
-  std::vector<int32_t> start;
-  for (int64_t o = 0; o < N; ++o) {
-    const uint64_t k = key[size_t(o)];
-    bool head = o == 0;
-    if (!head) {
-      const uint64_t q = key[size_t(o - 1)];
-      head = (k >> 45) != (q >> 45) || (ikey_x(k) >> sh) != (ikey_x(q) >> sh) ||
-             (ikey_y(k) >> sh) != (ikey_y(q) >> sh) || (ikey_z(k) >> sh) != (ikey_z(q) >> sh);
-    }
-    if (head) start.push_back(int32_t(o));
-    h->blkid_h[size_t(o)] = int32_t(start.size()) - 1;
-  }
-  start.push_back(int32_t(N));
   dev_free(h, h->blk);
   h->blk = nullptr;
-  AMR_TRY(upload(h, &h->blk, start));
-  return AMR_OK;
+  AMR_TRY(alloc_n(h, &h->blk, N + 1));
+  h->blk_first.assign(size_t(h->M) * (kMaxLev + 1), 0);
+  h->blk_last.assign(size_t(h->M) * (kMaxLev + 1), 0);
+  if (N == 0) return AMR_OK;
+  // block heads (a new (member, level) or aligned group), their exclusive
+  // prefix sum = block of every oct, and the blocks' first octs
+  uint32_t *head = nullptr, *pos = nullptr, *tmp = nullptr;
+  int32_t *ask = nullptr, *got = nullptr;
+  std::vector<int32_t> at;  // first and last oct of every (member, level)
+  for (int q = 0; q < h->M; ++q)
+    for (int l = 0; l <= kMaxLev; ++l) {
+      const Member &m = h->mem[q];
+      const int64_t lo = m.oct_base + m.lo[l], nl = m.lo[l + 1] - m.lo[l];
+      at.push_back(int32_t(nl > 0 ? lo : 0));
+      at.push_back(int32_t(nl > 0 ? lo + nl - 1 : 0));
+    }
+  amr_status st = AMR_OK;
+  if ((st = alloc_n(h, &head, N)) == AMR_OK && (st = alloc_n(h, &pos, N)) == AMR_OK &&
+      (st = alloc_n(h, &tmp, scan_tmp_size(N))) == AMR_OK && (st = upload(h, &ask, at)) == AMR_OK &&
+      (st = alloc_n(h, &got, int64_t(at.size()))) == AMR_OK) {
+    launch(h, K_GATHER, k_block_heads, dim3(nblocks(N)), dim3(256), (const uint64_t *)h->key, N, sh, head);
+    CUDA_TRY(cudaMemcpyAsync(pos, head, 4 * size_t(N), cudaMemcpyDeviceToDevice, h->s));
+    scan_exclusive(h, pos, N, tmp);
+    launch(h, K_GATHER, k_block_starts, dim3(nblocks(N)), dim3(256), (const uint32_t *)head,
+           (const uint32_t *)pos, N, h->blk);
+    launch(h, K_GATHER, k_block_of, dim3(nblocks(int64_t(at.size()))), dim3(256), (const uint32_t *)head,
+           (const uint32_t *)pos, (const int32_t *)ask, int64_t(at.size()), got);
+    std::vector<int32_t> blk_at(at.size());
+    cudaError_t e = cudaMemcpyAsync(blk_at.data(), got, 4 * at.size(), cudaMemcpyDeviceToHost, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = fail(AMR_ECUDA, "block list: %s", cudaGetErrorString(e));
+    for (size_t t = 0; 2 * t < blk_at.size(); ++t) {
+      h->blk_first[t] = blk_at[2 * t];
+      h->blk_last[t] = blk_at[2 * t + 1];
+    }
+  }
+  for (void *b : {(void *)head, (void *)pos, (void *)tmp, (void *)ask, (void *)got}) dev_free(h, b);
+  return st;
 }
 
 // Rebuild the tile lists for another tile size or fused-kernel block size

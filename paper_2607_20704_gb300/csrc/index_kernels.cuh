@@ -350,4 +350,39 @@ __global__ void k_fnv(const uint64_t *__restrict__ in, int64_t n, uint64_t *__re
   if (q < n) out[q] = fnv1a64(in[q]);
 }
 
+// Blocks of the fused kernels: runs of octs (mesh order) of one (member,
+// level) whose coordinates lie in one aligned group of 2^sh octs per axis.
+// head[o] = 1 where a block starts.
+__global__ void k_block_heads(const uint64_t *__restrict__ key, int64_t n, unsigned sh,
+                              uint32_t *__restrict__ head) {
+  const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (o >= n) return;
+  bool h = o == 0;
+  if (!h) {
+    const uint64_t k = key[o], q = key[o - 1];
+    h = (k >> 45) != (q >> 45) || (ikey_x(k) >> sh) != (ikey_x(q) >> sh) ||
+        (ikey_y(k) >> sh) != (ikey_y(q) >> sh) || (ikey_z(k) >> sh) != (ikey_z(q) >> sh);
+  }
+  head[o] = h ? 1u : 0u;
+}
+
+// first oct of every block (pos = exclusive prefix sum of head), and the end
+// of the list after the last block
+__global__ void k_block_starts(const uint32_t *__restrict__ head, const uint32_t *__restrict__ pos,
+                               int64_t n, int32_t *__restrict__ start) {
+  const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (o >= n) return;
+  if (head[o]) start[pos[o]] = int32_t(o);
+  if (o == n - 1) start[pos[o] + head[o]] = int32_t(n);
+}
+
+// block of the octs ask[0..m)
+__global__ void k_block_of(const uint32_t *__restrict__ head, const uint32_t *__restrict__ pos,
+                           const int32_t *__restrict__ ask, int64_t m, int32_t *__restrict__ out) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= m) return;
+  const int32_t o = ask[t];
+  out[t] = int32_t(pos[o] + head[o]) - 1;
+}
+
 }  // namespace amr
