@@ -87,6 +87,7 @@ def lib():
                 "orc_write": (I, [P, I, P]),
                 "orc_totals": (None, [P, P]),
                 "orc_level_totals": (None, [P, I, P]),
+                "orc_cic_deposit_levels": (I, [P, I64, P, P, P, P, P, P]),
                 "orc_cfl_dt": (D, [P]),
                 "orc_step_level": (I, [P, I, D]),
                 "orc_step_sample": (I, [P, I, D, I64, P, P]),
@@ -220,6 +221,23 @@ class Mesh:
         t = np.zeros(NV, np.float64)
         lib().orc_totals(self._h, _ptr(t))
         return t
+
+    def cic_deposit_levels(self, x, y, z, m):
+        """CIC deposition onto every level (Sec. 4): per level the density of
+        its cells [8 n_level] (read order) and the size of its particle list."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, m)]
+        n = int(sum(self.num_octs(l) for l in range(16)))
+        rho = np.zeros(8 * max(n, 1), np.float64)
+        cnt = np.zeros(16, np.int64)
+        rc = lib().orc_cic_deposit_levels(self._h, int(arrs[0].size), *[_ptr(a) for a in arrs],
+                                          _ptr(rho), _ptr(cnt))
+        if rc:
+            raise OracleError(rc, "cic_deposit_levels")
+        out = {}
+        for l in self.levels():
+            a = self.level_offset(l)
+            out[l] = rho[8 * a: 8 * (a + self.num_octs(l))]
+        return out, cnt
 
     def level_totals(self, level: int):
         """Sum of U dx^3 over the leaf cells of one level."""

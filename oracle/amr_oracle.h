@@ -127,6 +127,17 @@ double orc_mg_residual(int n, double dx, const double *rho, double fourpiG, cons
  * c = cx + 2 cy + 4 cz, particles in index order; rho = sum / dx^3. */
 int orc_cic_deposit(int n, int64_t np, const double *x, const double *y, const double *z,
                     const double *m, double *rho);
+/* The same deposition onto the levels of a mesh (Sec. 4: at level l the
+ * particles of level l and of all finer levels deposit, then the list is
+ * split for level l+1).  The list of levelmin holds every particle; at level
+ * l each particle of the list gives m (wx wy) wz, the CIC weights at cell
+ * size 2^-l, to each of its 8 stencil cells that exists at level l (a cell
+ * of a level-l oct); the list of level l+1 keeps, in order, the particles
+ * whose host cell at level l (the cell containing the particle) is split.
+ * rho[8*oct + c] (mesh order, all levels; split cells included) = sum /
+ * dx_l^3; count[l] (16 entries) = particles in the list of level l. */
+int orc_cic_deposit_levels(const orc_mesh *m, int64_t np, const double *x, const double *y,
+                           const double *z, const double *mass, double *rho, int64_t *count);
 
 /* --- independent cross-check solvers ----------------------------------------- */
 int orc_uniform_step(int n, double *U, double gamma, double dt, double smallr,
