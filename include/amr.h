@@ -373,6 +373,40 @@ amr_status amr_hash(amr_handle h, int64_t n, const uint64_t *keys, uint64_t *has
 amr_status amr_read_hash(amr_handle h, int64_t *cap_out, uint64_t *keys, int32_t *vals,
                          int64_t cap);
 
+/*
+ * amr_cic_deposit_levels -- Cloud-in-Cell mass deposition of np particles onto
+ * every level of the selected member (Sec. 4, "Mass Deposition": at level l
+ * the particles of level l and of every finer level deposit, then the list is
+ * split for level l+1).  The list of levelmin holds every particle; at level
+ * l each particle of the list adds m (wx wy) wz / dx_l^3 -- the CIC weights
+ * at cell size dx_l = 2^-l with the half-cell-shifted stencil: along each
+ * axis s = x 2^l - 1/2, i0 = floor(s), f = s - i0, weights 1 - f and f on
+ * cells i0 and i0 + 1 (periodic) -- to each of its 8 stencil cells that
+ * exists at level l (a cell of a real level-l oct); the list of level l+1
+ * keeps, in order, the particles whose host cell at level l (the cell
+ * containing the particle) is split.  The result is the density of every
+ * cell of the member's levels (split cells included), read with
+ * amr_read_particle_rho; count[l] (16 entries, may be NULL) receives the
+ * size of each level's list.  One thread per particle of a list, atomic
+ * additions: reproducible to rounding only.
+ *   x, y, z, m  host arrays of np doubles; positions in [0, 1), finite masses
+ *               (checked: AMR_EINVAL); np < 2^32
+ * Copies the particles to the device in the handle's precision; synchronous.
+ */
+amr_status amr_cic_deposit_levels(amr_handle h, int64_t np, const double *x, const double *y,
+                                  const double *z, const double *m, int64_t *count);
+
+/* The same deposition from device arrays of the handle's precision (double
+ * for precision 8, float for 4), caller-owned, not checked; asynchronous on
+ * the handle's stream unless count is not NULL (then synchronous). */
+amr_status amr_cic_deposit_levels_device(amr_handle h, int64_t np, const void *x, const void *y,
+                                         const void *z, const void *m, int64_t *count);
+
+/* Density of the last deposition for the selected member's cells of one
+ * level, [8 n] in amr_read order (FP32 widened).  AMR_EINVAL when the mesh
+ * has no deposition or has changed since (regrid, repack).  Synchronous. */
+amr_status amr_read_particle_rho(amr_handle h, int level, double *rho, int64_t cap);
+
 /* Same as amr_read for the pending reflux R [5][8*n] of a level. */
 amr_status amr_read_reflux(amr_handle h, int level, double *R, int64_t cap);
 

@@ -100,6 +100,7 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_status_string", "amr_cfl_dt_static", "amr_create_batch", "amr_select_member",
            "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag",
            "amr_regrid_flags", "amr_totals", "amr_hash", "amr_read_hash", "amr_batch_repack",
+           "amr_cic_deposit_levels", "amr_cic_deposit_levels_device", "amr_read_particle_rho",
            "amr_poisson", "amr_read_phi", "amr_load_state_async", "amr_store_state_async",
            "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
@@ -173,6 +174,9 @@ def load(path: str | None = None):
             "amr_regrid_flags": (I, [P, P, I64, P, P]),
             "amr_totals": (I, [P, I, P]),
             "amr_batch_repack": (I, [P, I, P, I, P, P]),
+            "amr_cic_deposit_levels": (I, [P, I64, P, P, P, P, P]),
+            "amr_cic_deposit_levels_device": (I, [P, I64, P, P, P, P, P]),
+            "amr_read_particle_rho": (I, [P, I, P, I64]),
             "amr_hash": (I, [P, I64, P, P]),
             "amr_read_hash": (I, [P, P, P, P, I64]),
             "amr_flag": (I, [P, I, P, I64]),
@@ -382,6 +386,32 @@ class Mesh:
         cr, rm = C.c_int64(), C.c_int64()
         _check(load().amr_regrid(self._h, C.byref(cr), C.byref(rm)), "amr_regrid")
         return cr.value, rm.value
+
+    def cic_deposit_levels(self, x, y, z, m):
+        """CIC deposition of the particles onto every level of the selected
+        member (Sec. 4); returns the size of each level's particle list."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, m)]
+        cnt = np.zeros(16, np.int64)
+        _check(load().amr_cic_deposit_levels(self._h, int(arrs[0].size), *[_ptr(a) for a in arrs],
+                                             _ptr(cnt)), "amr_cic_deposit_levels")
+        return cnt
+
+    def cic_deposit_levels_device(self, x, y, z, m, counts=True):
+        """The same from device tensors of the handle's precision."""
+        cnt = np.zeros(16, np.int64)
+        _check(load().amr_cic_deposit_levels_device(
+            self._h, int(x.numel()), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+            C.c_void_p(z.data_ptr()), C.c_void_p(m.data_ptr()), _ptr(cnt) if counts else None),
+            "amr_cic_deposit_levels_device")
+        return cnt if counts else None
+
+    def particle_rho(self, level: int):
+        """Density of the last deposition at the cells of one level [8 n]."""
+        n = self.num_octs(level)
+        out = np.zeros(8 * max(n, 1), np.float64)
+        _check(load().amr_read_particle_rho(self._h, int(level), _ptr(out), max(n, 1)),
+               "amr_read_particle_rho")
+        return out[:8 * n]
 
     def totals(self, level: int = 0):
         """FP64 totals of the leaf cells' U dx^3 (one level, or 0: all levels),

@@ -11,6 +11,7 @@
 // (phase k runs the k-th level step of every member in one launch per
 // kernel), and one coarse step is captured once as a CUDA graph.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,7 @@
 #include "regrid_kernels.cuh"
 #include "mg_kernels.cuh"
 #include "index_kernels.cuh"
+#include "deposit_kernels.cuh"
 
 using namespace amr;
 
@@ -84,7 +86,7 @@ enum Kid {
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
   K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_COMMIT, K_SWEEP, K_TOTALS,
-  K_FNV, K_COUNT
+  K_FNV, K_DEPOSIT, K_SPLIT, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
@@ -92,7 +94,7 @@ static const char *kKernelNames[K_COUNT] = {
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
     "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
-    "rock", "commit", "sweep", "totals", "fnv"};
+    "rock", "commit", "sweep", "totals", "fnv", "deposit_level", "split_level"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -220,6 +222,16 @@ struct amr_mesh {
   int mg_member = -1;
   double *mg_rho = nullptr, *mg_r = nullptr, *mg_part = nullptr, *mg_res = nullptr;
   double *phi = nullptr;
+
+  // particle deposition onto the levels: positions and masses (the handle's
+  // precision), two particle lists, split flags and their prefix sums, list
+  // lengths per level, and the density of every cell
+  void *px = nullptr, *py = nullptr, *pz = nullptr, *pm = nullptr;
+  uint32_t *plist0 = nullptr, *plist1 = nullptr, *pflag = nullptr, *ppos = nullptr, *ptmp = nullptr;
+  int64_t *pcount = nullptr;
+  int64_t pcap = 0;
+  void *prho = nullptr;
+  int64_t prho_n = 0;
 
   // work accounting
   int64_t launches = 0, graph_launches = 0;
@@ -2380,6 +2392,148 @@ extern "C" amr_status amr_batch_repack(amr_handle h, int n_keep, const int32_t *
   std::swap(*h, *nh);
   destroy_all(nh);
   return check_device(h, "amr_batch_repack");
+}
+
+// ---------------------------------------------------------------------------
+// CIC deposition onto the levels of the selected member (Sec. 4)
+// ---------------------------------------------------------------------------
+__global__ void k_iota_u32(uint32_t *a, int64_t n) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < n) a[t] = uint32_t(t);
+}
+
+static amr_status ensure_particles(amr_mesh *h, int64_t np, bool positions) {
+  const size_t es = h->elem();
+  if (np > h->pcap || (positions && !h->px)) {
+    for (void **b : {&h->px, &h->py, &h->pz, &h->pm}) {
+      dev_free(h, *b);
+      *b = nullptr;
+    }
+    for (uint32_t **b : {&h->plist0, &h->plist1, &h->pflag, &h->ppos, &h->ptmp}) {
+      dev_free(h, *b);
+      *b = nullptr;
+    }
+    h->pcap = 0;
+    const int64_t cap = std::max<int64_t>(np, 1);
+    if (positions)
+      for (void **b : {&h->px, &h->py, &h->pz, &h->pm}) AMR_TRY(dev_alloc(h, b, es * size_t(cap)));
+    for (uint32_t **b : {&h->plist0, &h->plist1, &h->pflag, &h->ppos}) AMR_TRY(alloc_n(h, b, cap));
+    AMR_TRY(alloc_n(h, &h->ptmp, scan_tmp_size(cap)));
+    h->pcap = cap;
+  }
+  if (!h->pcount) AMR_TRY(alloc_n(h, &h->pcount, kMaxLev + 2));
+  if (h->prho_n != 8 * h->N) {
+    dev_free(h, h->prho);
+    h->prho = nullptr;
+    AMR_TRY(dev_alloc(h, &h->prho, es * size_t(8 * std::max<int64_t>(h->N, 1))));
+    h->prho_n = 8 * h->N;
+  }
+  return AMR_OK;
+}
+
+template <class T>
+static void deposit_levels(amr_mesh *h, int64_t np, const T *x, const T *y, const T *z, const T *m) {
+  const Member &mb = h->mem[h->sel];
+  const int N = int(h->N);
+  cudaMemsetAsync(h->prho, 0, sizeof(T) * size_t(8 * h->N), h->s);
+  std::vector<int64_t> cnt(kMaxLev + 2, 0);
+  cnt[size_t(mb.lmin)] = np;
+  cudaMemcpyAsync(h->pcount, cnt.data(), sizeof(int64_t) * cnt.size(), cudaMemcpyHostToDevice, h->s);
+  if (np == 0) return;
+  launch(h, K_DEPOSIT, k_iota_u32, dim3(nblocks(np)), dim3(256), h->plist0, np);
+  uint32_t *cur = h->plist0, *nxt = h->plist1;
+  for (int l = mb.lmin; l <= mb.lmax; ++l) {
+    launch(h, K_DEPOSIT, k_deposit_level<T>, dim3(nblocks(np)), dim3(256), h->hash, h->sel, l, N, x, y,
+           z, m, (const uint32_t *)cur, (const int64_t *)h->pcount, static_cast<T *>(h->prho));
+    if (l == mb.lmax) break;
+    launch(h, K_SPLIT, k_split_level<T>, dim3(nblocks(np)), dim3(256), h->hash, h->sel, l, N,
+           (const uint32_t *)h->son, x, y, z, (const uint32_t *)cur, (const int64_t *)h->pcount, np,
+           h->pflag);
+    cudaMemcpyAsync(h->ppos, h->pflag, 4 * size_t(np), cudaMemcpyDeviceToDevice, h->s);
+    scan_exclusive(h, h->ppos, np, h->ptmp);
+    launch(h, K_SPLIT, k_compact_level, dim3(nblocks(np)), dim3(256), (const uint32_t *)cur,
+           (const uint32_t *)h->pflag, (const uint32_t *)h->ppos, np, l, nxt, h->pcount);
+    std::swap(cur, nxt);
+  }
+}
+
+static amr_status deposit_counts(amr_mesh *h, int64_t *count) {
+  if (!count) return AMR_OK;
+  std::vector<int64_t> cnt(kMaxLev + 2, 0);
+  CUDA_TRY(cudaMemcpyAsync(cnt.data(), h->pcount, sizeof(int64_t) * cnt.size(), cudaMemcpyDeviceToHost, h->s));
+  AMR_TRY(check_device(h, "amr_cic_deposit_levels"));
+  const Member &mb = h->mem[h->sel];
+  for (int l = 0; l <= kMaxLev; ++l) count[l] = l >= mb.lmin && l <= mb.lmax ? cnt[size_t(l)] : 0;
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_cic_deposit_levels_device(amr_handle h, int64_t np, const void *x, const void *y,
+                                                    const void *z, const void *m, int64_t *count) {
+  if (!h) return fail(AMR_EINVAL, "amr_cic_deposit_levels_device: NULL handle");
+  if (np < 0 || np >= (int64_t(1) << 32)) return fail(AMR_EINVAL, "amr_cic_deposit_levels_device: np outside [0, 2^32)");
+  if (np > 0 && (!x || !y || !z || !m)) return fail(AMR_EINVAL, "amr_cic_deposit_levels_device: NULL array");
+  AMR_TRY(ensure_particles(h, np, false));
+  if (h->p.precision == 4)
+    deposit_levels<float>(h, np, (const float *)x, (const float *)y, (const float *)z, (const float *)m);
+  else
+    deposit_levels<double>(h, np, (const double *)x, (const double *)y, (const double *)z, (const double *)m);
+  if (h->launch_err != cudaSuccess) return check_device(h, "amr_cic_deposit_levels_device");
+  return deposit_counts(h, count);
+}
+
+template <class T>
+static amr_status stage_particles(amr_mesh *h, int64_t np, const double *x, const double *y,
+                                  const double *z, const double *m) {
+  std::vector<T> buf(size_t(std::max<int64_t>(np, 1)));
+  const double *src[4] = {x, y, z, m};
+  void *dst[4] = {h->px, h->py, h->pz, h->pm};
+  for (int a = 0; a < 4; ++a) {
+    for (int64_t t = 0; t < np; ++t) buf[size_t(t)] = T(src[a][t]);
+    CUDA_TRY(cudaMemcpyAsync(dst[a], buf.data(), sizeof(T) * size_t(np), cudaMemcpyHostToDevice, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));  // buf is reused
+  }
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_cic_deposit_levels(amr_handle h, int64_t np, const double *x, const double *y,
+                                             const double *z, const double *m, int64_t *count) {
+  if (!h) return fail(AMR_EINVAL, "amr_cic_deposit_levels: NULL handle");
+  if (np < 0 || np >= (int64_t(1) << 32)) return fail(AMR_EINVAL, "amr_cic_deposit_levels: np outside [0, 2^32)");
+  if (np > 0 && (!x || !y || !z || !m)) return fail(AMR_EINVAL, "amr_cic_deposit_levels: NULL array");
+  for (int64_t t = 0; t < np; ++t)
+    if (!(x[t] >= 0.0 && x[t] < 1.0 && y[t] >= 0.0 && y[t] < 1.0 && z[t] >= 0.0 && z[t] < 1.0) ||
+        !std::isfinite(m[t]))
+      return fail(AMR_EINVAL, "amr_cic_deposit_levels: particle %lld outside [0, 1)^3 or with a non-finite mass",
+                  (long long)t);
+  AMR_TRY(ensure_particles(h, np, true));
+  if (np > 0) {
+    if (h->p.precision == 4)
+      AMR_TRY(stage_particles<float>(h, np, x, y, z, m));
+    else
+      AMR_TRY(stage_particles<double>(h, np, x, y, z, m));
+  }
+  return amr_cic_deposit_levels_device(h, np, h->px, h->py, h->pz, h->pm, count);
+}
+
+extern "C" amr_status amr_read_particle_rho(amr_handle h, int level, double *rho, int64_t cap) {
+  if (!h || !rho) return fail(AMR_EINVAL, "amr_read_particle_rho: NULL argument");
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_read_particle_rho: bad level");
+  if (!h->prho || h->prho_n != 8 * h->N) return fail(AMR_EINVAL, "amr_read_particle_rho: no deposition on this mesh");
+  const Member &mb = h->mem[h->sel];
+  const int64_t lo = mb.oct_base + mb.lo[level], nl = mb.lo[level + 1] - mb.lo[level];
+  if (cap < nl) return fail(AMR_EINVAL, "amr_read_particle_rho: cap %lld < %lld octs", (long long)cap, (long long)nl);
+  if (nl == 0) return AMR_OK;
+  if (h->p.precision == 8) {
+    CUDA_TRY(cudaMemcpyAsync(rho, static_cast<const double *>(h->prho) + 8 * lo, sizeof(double) * 8 * nl,
+                             cudaMemcpyDeviceToHost, h->s));
+  } else {
+    std::vector<float> f(size_t(8 * nl));
+    CUDA_TRY(cudaMemcpyAsync(f.data(), static_cast<const float *>(h->prho) + 8 * lo, sizeof(float) * 8 * nl,
+                             cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+    for (int64_t t = 0; t < 8 * nl; ++t) rho[t] = double(f[size_t(t)]);
+  }
+  return check_device(h, "amr_read_particle_rho");
 }
 
 // FP64 conservation totals of the selected member's leaf cells (one level, or
