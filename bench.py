@@ -659,6 +659,31 @@ def run_cic(n, reps, warmup, torch, peak_gbs, peak_src):
         res["kernels_ms"] = {k: round(v[0], 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
         out["fp64" if prec == 8 else "fp32"] = res
         p.close()
+    out["levels"] = run_cic_levels(timed, torch, st)
+    return out
+
+
+def run_cic_levels(timed, torch, st):
+    """Deposition onto the AMR levels (Sec. 4: each level's particle list,
+    then the split by host cells refined): the cosmological particle set
+    with 256^3 particles on the cosmology-shaped mesh (levels 8-11, 2.5 M
+    octs), from device arrays, list sizes per level, deposits per second
+    (every list entry deposits once at its level)."""
+    from paper_2607_20704_gb300 import amr, inputs
+    ps = inputs.particles(256, "cosmo", seed=2607)
+    prob = inputs.lognormal()
+    out = {"mesh": "lognormal levels 8-11", "octs": int(prob.n_oct), "particles": int(ps.np)}
+    for prec in (8, 4):
+        m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=prec, stream=st)
+        dt = torch.float64 if prec == 8 else torch.float32
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dt) for a in ps.args()[1:]]
+        cnt = m.cic_deposit_levels_device(*arrs)
+        ms = timed(lambda: m.cic_deposit_levels_device(*arrs, counts=False))
+        total = int(cnt.sum())
+        out["fp64" if prec == 8 else "fp32"] = {
+            "ms": round(ms, 4), "list_sizes": {int(l): int(c) for l, c in enumerate(cnt) if c},
+            "deposits_per_s": total / (ms * 1e-3)}
+        m.close()
     return out
 
 
