@@ -88,6 +88,7 @@ def lib():
                 "orc_totals": (None, [P, P]),
                 "orc_level_totals": (None, [P, I, P]),
                 "orc_cic_deposit_levels": (I, [P, I64, P, P, P, P, P, P]),
+                "orc_mg_level": (I, [P, I, D, D, P, I, P, P]),
                 "orc_cfl_dt": (D, [P]),
                 "orc_step_level": (I, [P, I, D]),
                 "orc_step_sample": (I, [P, I, D, I64, P, P]),
@@ -238,6 +239,21 @@ class Mesh:
             a = self.level_offset(l)
             out[l] = rho[8 * a: 8 * (a + self.num_octs(l))]
         return out, cnt
+
+    def mg_level(self, level, phic, fourpiG=1.0, rho_bar=1.0, ncycles=4, phi0=None):
+        """Poisson on refined level `level` with the Dirichlet data of the
+        coarser level's potential phic (8 n_{level-1}, read order); returns
+        (phi [8 n_level], residual norms)."""
+        n = self.num_octs(level)
+        phic = np.ascontiguousarray(phic, dtype=np.float64)
+        assert phic.size == 8 * self.num_octs(level - 1)
+        phi = np.zeros(8 * n) if phi0 is None else np.array(phi0, dtype=np.float64)
+        res = np.zeros(max(ncycles, 1))
+        rc = lib().orc_mg_level(self._h, int(level), float(fourpiG), float(rho_bar), _ptr(phic),
+                                int(ncycles), _ptr(phi), _ptr(res))
+        if rc:
+            raise OracleError(rc, "mg_level")
+        return phi, res[:ncycles]
 
     def level_totals(self, level: int):
         """Sum of U dx^3 over the leaf cells of one level."""

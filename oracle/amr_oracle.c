@@ -1471,6 +1471,269 @@ int orc_mg_solve(int n, double dx, const double *rho, double fourpiG, int ncycle
 }
 
 /* ------------------------------------------------------------------------- */
+/* self-gravity on a refined level (Sec. 5: the potential is built level by  */
+/* level with V-cycles; the domain boundary takes Dirichlet values through   */
+/* an adjusted diagonal).  Readings:                                         */
+/*   domain   the cells of the level-L octs; the operator is the 7-point     */
+/*            Laplacian (sum of the 6 neighbours - 6 phi) / dx^2 = f, f =    */
+/*            fourpiG (rho - rho_bar);                                       */
+/*   boundary a face to a cell outside the domain takes phi_b, the mean of   */
+/*            the coarse potential of the cell's father and of the level-    */
+/*            (L-1) cell across the face, through the ghost value            */
+/*            2 phi_b - phi (phi_b on the face): the diagonal becomes        */
+/*            -(6 + b) for b such faces and 2 sum phi_b moves to the source; */
+/*   cycle    MG level 0 is the domain; MG level k the level-(L-k) cells     */
+/*            with a child oct holding a cell of MG level k-1, down to       */
+/*            levelmin; the correction equations take homogeneous Dirichlet  */
+/*            values at their boundaries; red-black Gauss-Seidel (colour =   */
+/*            parity of x+y+z), residuals restricted by the sum of the       */
+/*            children in the level below over 8, corrections prolonged      */
+/*            trilinearly ((1,3,3,9,3,9,9,27)/64; coarse cells outside the   */
+/*            MG level count 0); 2 sweeps before and after, 8 on the         */
+/*            coarsest MG level.                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int L;                /* AMR level of the cells */
+  int64_t n;            /* cells */
+  uint64_t *codes;      /* [n] sorted cell codes (x, y, z) */
+  int64_t *x, *y, *z;   /* cell coordinates at level L */
+  int64_t *nb;          /* [6 n] index of the face neighbour in this MG level, or -1 */
+  int *nbnd;            /* faces to the outside */
+  double *bsum;         /* 2 sum of phi_b over those faces (MG level 0 only) */
+  double *e, *f, *r;
+} mg_lvl;
+
+/* index of cell (x,y,z) of level L in the sorted code list of an MG level */
+static uint64_t mg_code(int64_t x, int64_t y, int64_t z) {
+  return ((uint64_t)x << 42) | ((uint64_t)y << 21) | (uint64_t)z;
+}
+static int cmp_code(const void *a, const void *b) {
+  const uint64_t u = *(const uint64_t *)a, v = *(const uint64_t *)b;
+  return u < v ? -1 : u > v;
+}
+static int64_t mg_find(const uint64_t *codes, int64_t n, uint64_t c) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (codes[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return lo < n && codes[lo] == c ? lo : -1;
+}
+
+static void mg_lvl_free(mg_lvl *g) {
+  free(g->codes); free(g->x); free(g->y); free(g->z); free(g->nb); free(g->nbnd); free(g->bsum);
+  free(g->e); free(g->f); free(g->r);
+  memset(g, 0, sizeof *g);
+}
+
+static int64_t mg_find_lvl(const mg_lvl *g, int64_t x, int64_t y, int64_t z) {
+  return mg_find(g->codes, g->n, mg_code(x, y, z));
+}
+
+/* the cells of the MG level of AMR level L given as sorted codes */
+static int mg_lvl_make(mg_lvl *g, int L, const uint64_t *codes, int64_t n) {
+  memset(g, 0, sizeof *g);
+  g->L = L;
+  g->n = n;
+  g->codes = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n + 1));
+  g->x = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  g->y = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  g->z = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  g->nb = (int64_t *)malloc(sizeof(int64_t) * (size_t)(6 * n + 1));
+  g->nbnd = (int *)calloc((size_t)(n + 1), sizeof(int));
+  g->bsum = (double *)calloc((size_t)(n + 1), sizeof(double));
+  g->e = (double *)calloc((size_t)(n + 1), sizeof(double));
+  g->f = (double *)calloc((size_t)(n + 1), sizeof(double));
+  g->r = (double *)calloc((size_t)(n + 1), sizeof(double));
+  if (!g->codes || !g->x || !g->y || !g->z || !g->nb || !g->nbnd || !g->bsum || !g->e || !g->f || !g->r)
+    return ORC_ENOMEM;
+  memcpy(g->codes, codes, sizeof(uint64_t) * (size_t)n);
+  const int64_t side = (int64_t)1 << L;
+  for (int64_t t = 0; t < n; ++t) {
+    g->x[t] = (int64_t)(codes[t] >> 42);
+    g->y[t] = (int64_t)((codes[t] >> 21) & 0x1FFFFF);
+    g->z[t] = (int64_t)(codes[t] & 0x1FFFFF);
+    for (int d = 0; d < 3; ++d)
+      for (int s = 0; s < 2; ++s) {
+        const int64_t dd = s ? 1 : -1;
+        const int64_t X = wrap(g->x[t] + (d == 0) * dd, side), Y = wrap(g->y[t] + (d == 1) * dd, side),
+                      Z = wrap(g->z[t] + (d == 2) * dd, side);
+        const int64_t q = mg_find(codes, n, mg_code(X, Y, Z));
+        g->nb[6 * t + 2 * d + s] = q;
+        if (q < 0) g->nbnd[t] += 1;
+      }
+  }
+  return ORC_OK;
+}
+
+/* red-black Gauss-Seidel sweep: colour 0 (x+y+z even) then colour 1 */
+static void mg_lvl_smooth(mg_lvl *g) {
+  const double dx = ldexp(1.0, -g->L), dx2 = dx * dx;
+  for (int colour = 0; colour < 2; ++colour)
+    for (int64_t t = 0; t < g->n; ++t) {
+      if ((int)((g->x[t] + g->y[t] + g->z[t]) & 1) != colour) continue;
+      double s = 0.0;
+      for (int k = 0; k < 6; ++k) {
+        const int64_t q = g->nb[6 * t + k];
+        if (q >= 0) s += g->e[q];
+      }
+      g->e[t] = ((s + g->bsum[t]) - dx2 * g->f[t]) / (double)(6 + g->nbnd[t]);
+    }
+}
+
+static void mg_lvl_residual(mg_lvl *g) {
+  const double dx = ldexp(1.0, -g->L), dx2 = dx * dx;
+  for (int64_t t = 0; t < g->n; ++t) {
+    double s = 0.0;
+    for (int k = 0; k < 6; ++k) {
+      const int64_t q = g->nb[6 * t + k];
+      if (q >= 0) s += g->e[q];
+    }
+    g->r[t] = g->f[t] - ((s + g->bsum[t]) - (double)(6 + g->nbnd[t]) * g->e[t]) / dx2;
+  }
+}
+
+static void mg_lvl_cycle(mg_lvl *lv, int k, int K) {
+  mg_lvl *g = &lv[k];
+  if (k == K) {
+    for (int s = 0; s < 8; ++s) mg_lvl_smooth(g);
+    return;
+  }
+  mg_lvl *c = &lv[k + 1];
+  for (int s = 0; s < 2; ++s) mg_lvl_smooth(g);
+  mg_lvl_residual(g);
+  /* restriction: the residuals of the children in the finer MG level,
+   * summed in the order (cx, cy, cz) with cz fastest, over 8 */
+  for (int64_t t = 0; t < c->n; ++t) {
+    double s = 0.0;
+    for (int cx = 0; cx < 2; ++cx)
+      for (int cy = 0; cy < 2; ++cy)
+        for (int cz = 0; cz < 2; ++cz) {
+          const int64_t q = mg_find_lvl(g, 2 * c->x[t] + cx, 2 * c->y[t] + cy, 2 * c->z[t] + cz);
+          if (q >= 0) s += g->r[q];
+        }
+    c->f[t] = s / 8.0;
+    c->e[t] = 0.0;
+  }
+  mg_lvl_cycle(lv, k + 1, K);
+  /* trilinear prolongation of the correction */
+  const int64_t cside = (int64_t)1 << c->L;
+  for (int64_t t = 0; t < g->n; ++t) {
+    const int64_t X = g->x[t] >> 1, Y = g->y[t] >> 1, Z = g->z[t] >> 1;
+    const int64_t sx = (g->x[t] & 1) ? 1 : -1, sy = (g->y[t] & 1) ? 1 : -1, sz = (g->z[t] & 1) ? 1 : -1;
+    double e3[2][2][2];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int d = 0; d < 2; ++d) {
+          const int64_t q = mg_find_lvl(c, wrap(X + a * sx, cside), wrap(Y + b * sy, cside), wrap(Z + d * sz, cside));
+          e3[a][b][d] = q >= 0 ? c->e[q] : 0.0;
+        }
+    double v = 27.0 * e3[0][0][0];
+    v += 9.0 * ((e3[1][0][0] + e3[0][1][0]) + e3[0][0][1]);
+    v += 3.0 * ((e3[1][1][0] + e3[1][0][1]) + e3[0][1][1]);
+    v += e3[1][1][1];
+    g->e[t] += v / 64.0;
+  }
+  for (int s = 0; s < 2; ++s) mg_lvl_smooth(g);
+}
+
+static uint64_t mg_code_of_cell(const orc_mesh *m, int64_t o, int c) {
+  return mg_code(2 * (int64_t)m->ci[o] + (c & 1), 2 * (int64_t)m->cj[o] + ((c >> 1) & 1),
+                 2 * (int64_t)m->ck[o] + ((c >> 2) & 1));
+}
+
+/* potential of a level-(L-1) cell (x, y, z) from phic (read order of level L-1) */
+static double mg_coarse_phi(const orc_mesh *m, int Lc, const double *phic, int64_t x, int64_t y, int64_t z) {
+  const int64_t side = (int64_t)1 << Lc;
+  const uint32_t X = wrap(x, side), Y = wrap(y, side), Z = wrap(z, side);
+  const int64_t o = orc_lookup(m, orc_pack_key(Lc, X >> 1, Y >> 1, Z >> 1));
+  const int c = (int)((X & 1) + 2 * (Y & 1) + 4 * (Z & 1));
+  return phic[8 * (o - m->lo[Lc]) + c];  /* the cell exists: graded mesh */
+}
+
+int orc_mg_level(const orc_mesh *m, int L, double fourpiG, double rho_bar, const double *phic,
+                 int ncycles, double *phi, double *resid) {
+  const int lmin = m->p.levelmin;
+  if (L <= lmin || L > m->p.levelmax || ncycles < 0) return ORC_EINVAL;
+  const int64_t no = m->lo[L + 1] - m->lo[L];
+  if (no == 0) return ORC_EINVAL;
+  const int K = L - lmin;  /* MG levels 0..K: AMR levels L..lmin */
+  mg_lvl *lv = (mg_lvl *)calloc((size_t)(K + 1), sizeof(mg_lvl));
+  const int64_t n0 = 8 * no;
+  uint64_t *codes = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n0);
+  int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)n0);  /* read order -> MG index */
+  int e = ORC_OK;
+  if (!lv || !codes || !pos) {
+    e = ORC_ENOMEM;
+    goto done;
+  }
+  for (int64_t q = 0; q < no; ++q)
+    for (int c = 0; c < 8; ++c) codes[8 * q + c] = mg_code_of_cell(m, m->lo[L] + q, c);
+  qsort(codes, (size_t)n0, sizeof(uint64_t), cmp_code);
+  if ((e = mg_lvl_make(&lv[0], L, codes, n0))) goto done;
+  for (int64_t q = 0; q < no; ++q)
+    for (int c = 0; c < 8; ++c) pos[8 * q + c] = mg_find(codes, n0, mg_code_of_cell(m, m->lo[L] + q, c));
+  /* coarser MG levels: the parents of the cells of the level above */
+  for (int k = 1; k <= K; ++k) {
+    const mg_lvl *g = &lv[k - 1];
+    int64_t nc = 0;
+    for (int64_t t = 0; t < g->n; ++t) {
+      const uint64_t pc = mg_code(g->x[t] >> 1, g->y[t] >> 1, g->z[t] >> 1);
+      codes[nc++] = pc;
+    }
+    qsort(codes, (size_t)nc, sizeof(uint64_t), cmp_code);
+    int64_t u = 0;
+    for (int64_t t = 0; t < nc; ++t)
+      if (t == 0 || codes[t] != codes[t - 1]) codes[u++] = codes[t];
+    if ((e = mg_lvl_make(&lv[k], L - k, codes, u))) goto done;
+  }
+  /* source, boundary values and initial guess of the level */
+  {
+    mg_lvl *g = &lv[0];
+    const int64_t N8 = 8 * m->n;
+    const int64_t side = (int64_t)1 << L;
+    for (int64_t q = 0; q < no; ++q)
+      for (int c = 0; c < 8; ++c) {
+        const int64_t t = pos[8 * q + c];
+        g->f[t] = fourpiG * (m->U[N8 * 0 + 8 * (m->lo[L] + q) + c] - rho_bar);
+        g->e[t] = phi[8 * q + c];
+      }
+    for (int64_t t = 0; t < g->n; ++t) {
+      double bs = 0.0;
+      const double pf = mg_coarse_phi(m, L - 1, phic, g->x[t] >> 1, g->y[t] >> 1, g->z[t] >> 1);
+      for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s) {
+          if (g->nb[6 * t + 2 * d + s] >= 0) continue;
+          const int64_t dd = s ? 1 : -1;
+          const int64_t X = wrap(g->x[t] + (d == 0) * dd, side), Y = wrap(g->y[t] + (d == 1) * dd, side),
+                        Z = wrap(g->z[t] + (d == 2) * dd, side);
+          const double pc = mg_coarse_phi(m, L - 1, phic, X >> 1, Y >> 1, Z >> 1);
+          bs += 2.0 * (0.5 * (pf + pc));
+        }
+      g->bsum[t] = bs;
+    }
+  }
+  for (int c = 0; c < ncycles; ++c) {
+    mg_lvl_cycle(lv, 0, K);
+    if (resid) {
+      mg_lvl_residual(&lv[0]);
+      double s = 0.0;
+      for (int64_t t = 0; t < lv[0].n; ++t) s += lv[0].r[t] * lv[0].r[t];
+      resid[c] = sqrt(s);
+    }
+  }
+  for (int64_t q = 0; q < no; ++q)
+    for (int c = 0; c < 8; ++c) phi[8 * q + c] = lv[0].e[pos[8 * q + c]];
+done:
+  if (lv)
+    for (int k = 0; k <= K; ++k) mg_lvl_free(&lv[k]);
+  free(lv);
+  free(codes);
+  free(pos);
+  return e;
+}
+
+/* ------------------------------------------------------------------------- */
 /* particles: cloud-in-cell deposition (Sec. 4)                              */
 /*                                                                           */
 /* The paper deposits particle masses with the Cloud-in-Cell scheme, by     */

@@ -118,6 +118,22 @@ int orc_mg_solve(int n, double dx, const double *rho, double fourpiG, int ncycle
 /* L2 norm of the residual of phi for the source fourpiG (rho - mean rho) */
 double orc_mg_residual(int n, double dx, const double *rho, double fourpiG, const double *phi);
 
+/* Poisson on refined level L > levelmin (Sec. 5, level by level): the
+ * cells of the level-L octs solve (sum of 6 neighbours - 6 phi) / dx^2 =
+ * fourpiG (rho - rho_bar), rho the density of the state; a face to a cell
+ * outside the level takes the value phi_b = (phic(father) + phic(cell
+ * across the face at level L-1)) / 2 through the ghost 2 phi_b - phi (the
+ * diagonal becomes -(6 + b)).  V-cycles over MG levels of the ancestors of
+ * the level's cells down to levelmin (homogeneous Dirichlet corrections),
+ * red-black Gauss-Seidel (2 + 2 sweeps, 8 on the coarsest), residual
+ * restriction by the children's sum over 8 (order cx, cy, cz with cz
+ * fastest), trilinear prolongation (1,3,3,9,3,9,9,27)/64.  phic: the
+ * potential of level L-1's cells (8 n, read order); phi: in, the initial
+ * guess, out, the result (8 n_L, read order); resid[ncycles] (may be NULL):
+ * L2 norm of the residual after each cycle. */
+int orc_mg_level(const orc_mesh *m, int L, double fourpiG, double rho_bar, const double *phic,
+                 int ncycles, double *phi, double *resid);
+
 /* --- particles: cloud-in-cell mass deposition (Sec. 4) ----------------------
  * np particles at positions (x, y, z) in the periodic unit box with masses m
  * deposit onto an n^3 grid of cells of size 1/n (n a power of two; arrays
