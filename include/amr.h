@@ -279,6 +279,63 @@ amr_status amr_poisson(amr_handle h, double fourpiG, int n_vcycles, double *resi
  * octs of levelmin. */
 amr_status amr_read_phi(amr_handle h, double *phi, int64_t cap);
 
+/*
+ * amr_poisson_level -- potential of the cells of one refined level L of the
+ * selected member (Sec. 5: the Poisson equation is solved level by level,
+ * each level taking its boundary values from the level below).  The
+ * unknowns are the cells of level L; the operator is the 7-point Laplacian
+ *     (sum of the 6 face neighbours - 6 phi) / dx_L^2 = fourpiG (rho - rho_bar)
+ * where a face with no level-L cell on the other side takes the Dirichlet
+ * value phi_b = (phi of the cell's father + phi of the level-(L-1) cell
+ * across the face) / 2 through the ghost value 2 phi_b - phi.  n_vcycles
+ * V-cycles over the hierarchy of the level's ancestors down to levelmin
+ * (MG level k = the level-(L-k) cells holding a cell of MG level k-1;
+ * homogeneous Dirichlet values at every MG level's own boundary), red-black
+ * Gauss-Seidel with colour = parity of x + y + z, 2 sweeps before and after
+ * the coarse correction and 8 on the coarsest, residuals restricted by the
+ * sum of the existing children over 8, corrections prolonged trilinearly
+ * with weights (1,3,3,9,3,9,9,27)/64 (coarse cells outside the MG level
+ * count 0).  Every FP64 operation is rounded once in a fixed order, so the
+ * result does not depend on the launch configuration.
+ *
+ * Input and output live in the handle's per-cell potential (8 doubles per
+ * oct of every member, zero after amr_create and after every regrid): the
+ * values of level L-1 are the boundary data, those of level L the initial
+ * guess, and level L receives the result (amr_write_phi / amr_read_phi_level
+ * move them).  The tables of the level are built on the host on the first
+ * call for a (member, level) and kept until the mesh changes.  resid (may be
+ * NULL) receives the L2 norm of the level's residual after each V-cycle.
+ * FP64 whatever the precision of the state.  Synchronous.  Errors:
+ * AMR_EINVAL (level not a populated level above levelmin, n_vcycles outside
+ * [0, 1020]), AMR_EGRADING (a cell of level L without a father cell, or a
+ * boundary face without a level-(L-1) cell across).
+ */
+amr_status amr_poisson_level(amr_handle h, int level, double fourpiG, double rho_bar, int n_vcycles,
+                             double *resid);
+
+/*
+ * amr_poisson_levels -- the potential of every level of the selected member,
+ * coarse to fine: amr_poisson on the base level (its zero-mean result
+ * becomes the base level's per-cell potential), then for each populated
+ * level L above levelmin the father cell's potential as the initial guess of
+ * every cell and amr_poisson_level(L) with rho_bar = the mean density of the
+ * base level.  resid (may be NULL) holds n_vcycles values per level:
+ * resid[L * n_vcycles + c] for L in [levelmin, levelmax] (size (levelmax + 1)
+ * * n_vcycles).  Synchronous.  Errors: those of amr_poisson and
+ * amr_poisson_level.
+ */
+amr_status amr_poisson_levels(amr_handle h, double fourpiG, int n_vcycles, double *resid);
+
+/* Per-cell potential of one level of the selected member from the host,
+ * phi[8 * n + c] for cell c of the n-th oct (amr_read order); n must equal
+ * 8 * the level's octs.  Errors: AMR_EINVAL (bad level or size). */
+amr_status amr_write_phi(amr_handle h, int level, const double *phi, int64_t n);
+
+/* Per-cell potential of one level of the selected member to the host, same
+ * order; cap >= 8 * the level's octs.  Errors: AMR_EINVAL (bad level, cap too
+ * small, no potential on this mesh since amr_create or the last regrid). */
+amr_status amr_read_phi_level(amr_handle h, int level, double *phi, int64_t cap);
+
 /* Frees every device buffer of the handle (after synchronising its stream). */
 amr_status amr_destroy(amr_handle h);
 

@@ -101,7 +101,8 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_member_dt", "amr_set_member_steps", "amr_member_errors", "amr_regrid", "amr_flag",
            "amr_regrid_flags", "amr_totals", "amr_hash", "amr_read_hash", "amr_batch_repack",
            "amr_cic_deposit_levels", "amr_cic_deposit_levels_device", "amr_read_particle_rho",
-           "amr_poisson", "amr_read_phi", "amr_load_state_async", "amr_store_state_async",
+           "amr_poisson", "amr_read_phi", "amr_poisson_level", "amr_poisson_levels", "amr_write_phi",
+           "amr_read_phi_level", "amr_load_state_async", "amr_store_state_async",
            "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
            "amr_server_destroy"]
@@ -182,6 +183,10 @@ def load(path: str | None = None):
             "amr_flag": (I, [P, I, P, I64]),
             "amr_poisson": (I, [P, D, I, P]),
             "amr_read_phi": (I, [P, P, I64]),
+            "amr_poisson_level": (I, [P, I, D, D, I, P]),
+            "amr_poisson_levels": (I, [P, D, I, P]),
+            "amr_write_phi": (I, [P, I, P, I64]),
+            "amr_read_phi_level": (I, [P, I, P, I64]),
             "amr_server_create": (I, [C.POINTER(amr_server_params), C.POINTER(P)]),
             "amr_server_submit": (I, [P, C.POINTER(amr_request), C.POINTER(I64)]),
             "amr_server_wait": (I, [P, I64, D, C.POINTER(I)]),
@@ -472,6 +477,40 @@ class Mesh:
         n = self.num_octs(self.levelmin)
         out = np.zeros(8 * max(n, 1), np.float64)
         _check(load().amr_read_phi(self._h, _ptr(out), 8 * max(n, 1)), "amr_read_phi")
+        return out[:8 * n]
+
+    def poisson_level(self, level: int, fourpiG: float = 1.0, rho_bar: float = 1.0, n_vcycles: int = 4,
+                      residuals: bool = True):
+        """V-cycles (Sec. 5) on refined level `level`: the Dirichlet data are
+        the per-cell potential of level-1, the initial guess that of the
+        level, which receives the result; returns the residual norms."""
+        res = np.zeros(max(int(n_vcycles), 1), np.float64)
+        _check(load().amr_poisson_level(self._h, int(level), float(fourpiG), float(rho_bar), int(n_vcycles),
+                                        _ptr(res) if residuals else None), "amr_poisson_level")
+        return res[:int(n_vcycles)] if residuals else None
+
+    def poisson_levels(self, fourpiG: float = 1.0, n_vcycles: int = 4, residuals: bool = True):
+        """The potential of every level, base level first, each refined level
+        from its father cells' values; returns {level: residual norms}."""
+        nv = int(n_vcycles)
+        res = np.zeros(max((self.levelmax + 1) * nv, 1), np.float64)
+        _check(load().amr_poisson_levels(self._h, float(fourpiG), nv, _ptr(res) if residuals else None),
+               "amr_poisson_levels")
+        if not residuals:
+            return None
+        return {l: res[l * nv:(l + 1) * nv] for l in range(self.levelmin, self.levelmax + 1)
+                if self.num_octs(l) > 0}
+
+    def write_phi(self, level: int, phi):
+        """Per-cell potential of one level, [8 n] in read order."""
+        a = np.ascontiguousarray(phi, dtype=np.float64)
+        _check(load().amr_write_phi(self._h, int(level), _ptr(a), a.size), "amr_write_phi")
+
+    def read_phi_level(self, level: int):
+        """Per-cell potential of one level, [8 n] in read order."""
+        n = self.num_octs(level)
+        out = np.zeros(8 * max(n, 1), np.float64)
+        _check(load().amr_read_phi_level(self._h, int(level), _ptr(out), 8 * max(n, 1)), "amr_read_phi_level")
         return out[:8 * n]
 
     def member_errors(self):

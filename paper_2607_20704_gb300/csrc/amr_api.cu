@@ -220,6 +220,21 @@ struct amr_mesh {
   };
   std::vector<MGLevel> mg;
   int mg_member = -1;
+  // Poisson on a refined level: per MG level the tables of k_mgl_*, the
+  // level's cells (g0: global cell index), their fathers and the coarse cells
+  // across boundary faces; the potential of every cell (mesh order)
+  struct MGLTab {
+    int L = 0;
+    int64_t n = 0, nc0 = 0, nc1 = 0;
+    int32_t *nb = nullptr, *nbnd = nullptr, *col = nullptr, *child = nullptr, *pro = nullptr;
+    double *e = nullptr, *f = nullptr, *r = nullptr;
+  };
+  std::vector<MGLTab> mgl;
+  int mgl_member = -1, mgl_level = -1;
+  int32_t *mgl_g0 = nullptr, *mgl_fatherg = nullptr, *mgl_acrossg = nullptr;
+  double *mgl_bsum = nullptr, *mgl_part = nullptr, *mgl_scalar = nullptr;
+  double *phil = nullptr;
+  int64_t phil_n = 0;
   double *mg_rho = nullptr, *mg_r = nullptr, *mg_part = nullptr, *mg_res = nullptr;
   double *phi = nullptr;
 
@@ -1033,6 +1048,8 @@ static amr_status create_impl(amr_mesh *h, const amr_member *members) {
   return build_mesh(h, n, have_hk != 0, d_lvl, d_mem, d_i, d_j, d_k, d_hk, d_U, nullptr);
 }
 
+static void mgl_free(amr_mesh *h);
+
 // The mesh from device-resident inputs in any order (create and regrid):
 // order, hash, index, ghost cache, state, lists, scratch; d_new marks octs
 // whose state is to be prolonged from their father (regrid), before the
@@ -1042,6 +1059,11 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
                              double *d_U, uint8_t *d_new) {
   const amr_params &p = h->p;
   const int M = h->M;
+  // a new set of octs: the refined-level potential and its tables go
+  mgl_free(h);
+  dev_free(h, h->phil);
+  h->phil = nullptr;
+  h->phil_n = 0;
   h->N = n;
   uint32_t *perm, *perm_alt;
   uint64_t *comp, *comp_alt;
@@ -2126,6 +2148,342 @@ extern "C" amr_status amr_poisson(amr_handle h, double fourpiG, int n_vcycles, d
   return check_device(h, "amr_poisson");
 }
 
+// ---------------------------------------------------------------------------
+// Poisson on the refined levels (Sec. 5: the potential built level by level)
+// ---------------------------------------------------------------------------
+static amr_status ensure_phil(amr_mesh *h) {
+  if (h->phil && h->phil_n == 8 * h->N) return AMR_OK;
+  dev_free(h, h->phil);
+  h->phil = nullptr;
+  AMR_TRY(alloc_n(h, &h->phil, 8 * std::max<int64_t>(h->N, 1)));
+  CUDA_TRY(cudaMemsetAsync(h->phil, 0, sizeof(double) * size_t(8 * std::max<int64_t>(h->N, 1)), h->s));
+  h->phil_n = 8 * h->N;
+  return AMR_OK;
+}
+
+static bool level_ok(int level) { return level >= 0 && level <= kMaxLev; }
+
+static inline uint64_t mgl_code(int64_t x, int64_t y, int64_t z) {
+  return (uint64_t(x) << 42) | (uint64_t(y) << 21) | uint64_t(z);
+}
+
+static void mgl_free(amr_mesh *h) {
+  for (auto &t : h->mgl)
+    for (void *b : {(void *)t.nb, (void *)t.nbnd, (void *)t.col, (void *)t.child, (void *)t.pro, (void *)t.e,
+                    (void *)t.f, (void *)t.r})
+      dev_free(h, b);
+  h->mgl.clear();
+  for (void *b : {(void *)h->mgl_g0, (void *)h->mgl_fatherg, (void *)h->mgl_acrossg, (void *)h->mgl_bsum,
+                  (void *)h->mgl_part, (void *)h->mgl_scalar})
+    dev_free(h, b);
+  h->mgl_g0 = h->mgl_fatherg = h->mgl_acrossg = nullptr;
+  h->mgl_bsum = h->mgl_part = h->mgl_scalar = nullptr;
+  h->mgl_member = h->mgl_level = -1;
+}
+
+// The MG hierarchy of level L of the selected member: level 0 = the cells of
+// the level-L octs, level k = the level-(L-k) ancestors of level k-1, down to
+// levelmin; every table in sorted (x, y, z) order of the cells.
+static amr_status mgl_setup(amr_mesh *h, int L) {
+  if (h->mgl_member == h->sel && h->mgl_level == L && !h->mgl.empty()) return AMR_OK;
+  mgl_free(h);
+  const Member &mb = h->mem[h->sel];
+  const int lmin = mb.lmin, K = L - lmin;
+  const int64_t olo = mb.oct_base + mb.lo[L - 1], ohi = mb.oct_base + mb.lo[L + 1];
+  std::vector<uint64_t> key(size_t(ohi - olo));
+  CUDA_TRY(cudaMemcpyAsync(key.data(), h->key + olo, 8 * key.size(), cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  auto cell_code = [&](uint64_t k, int c) {
+    return mgl_code(2 * int64_t(ikey_x(k)) + (c & 1), 2 * int64_t(ikey_y(k)) + ((c >> 1) & 1),
+                    2 * int64_t(ikey_z(k)) + ((c >> 2) & 1));
+  };
+  // cells of levels L-1 and L: (code, global cell index), sorted
+  std::vector<std::pair<uint64_t, int32_t>> cL, cL1;
+  for (int64_t o = olo; o < ohi; ++o) {
+    const uint64_t k = key[size_t(o - olo)];
+    auto &dst = ikey_lev(k) == L ? cL : cL1;
+    for (int c = 0; c < 8; ++c) dst.push_back({cell_code(k, c), int32_t(8 * o + c)});
+  }
+  std::sort(cL.begin(), cL.end());
+  std::sort(cL1.begin(), cL1.end());
+  auto find_in = [](const std::vector<uint64_t> &v, uint64_t c) -> int32_t {
+    auto it = std::lower_bound(v.begin(), v.end(), c);
+    return (it != v.end() && *it == c) ? int32_t(it - v.begin()) : -1;
+  };
+  auto find_L1 = [&](uint64_t c) -> int32_t {
+    auto it = std::lower_bound(cL1.begin(), cL1.end(), std::make_pair(c, int32_t(-1)));
+    return (it != cL1.end() && it->first == c) ? it->second : -1;
+  };
+  std::vector<std::vector<uint64_t>> codes(size_t(K + 1));
+  for (auto &pr : cL) codes[0].push_back(pr.first);
+  for (int k = 1; k <= K; ++k) {
+    for (uint64_t c : codes[size_t(k - 1)])
+      codes[size_t(k)].push_back(mgl_code(int64_t(c >> 42) >> 1, int64_t((c >> 21) & 0x1FFFFF) >> 1,
+                                          int64_t(c & 0x1FFFFF) >> 1));
+    std::sort(codes[size_t(k)].begin(), codes[size_t(k)].end());
+    codes[size_t(k)].erase(std::unique(codes[size_t(k)].begin(), codes[size_t(k)].end()), codes[size_t(k)].end());
+  }
+  auto xyz = [](uint64_t c, int64_t &x, int64_t &y, int64_t &z) {
+    x = int64_t(c >> 42);
+    y = int64_t((c >> 21) & 0x1FFFFF);
+    z = int64_t(c & 0x1FFFFF);
+  };
+  h->mgl.resize(size_t(K + 1));
+  for (int k = 0; k <= K; ++k) {
+    const std::vector<uint64_t> &cd = codes[size_t(k)];
+    const int64_t n = int64_t(cd.size());
+    const int64_t side = int64_t(1) << (L - k);
+    std::vector<int32_t> nb(6 * size_t(n)), nbnd(size_t(n), 0), col;
+    std::vector<int32_t> c1;
+    for (int64_t t = 0; t < n; ++t) {
+      int64_t x, y, z;
+      xyz(cd[size_t(t)], x, y, z);
+      for (int d = 0; d < 3; ++d)
+        for (int sg = 0; sg < 2; ++sg) {
+          const int64_t dd = sg ? 1 : -1;
+          const int64_t X = (x + (d == 0) * dd) & (side - 1), Y = (y + (d == 1) * dd) & (side - 1),
+                        Z = (z + (d == 2) * dd) & (side - 1);
+          const int32_t q = find_in(cd, mgl_code(X, Y, Z));
+          nb[size_t((2 * d + sg) * n + t)] = q;
+          if (q < 0) nbnd[size_t(t)] += 1;
+        }
+      ((x + y + z) & 1 ? c1 : col).push_back(int32_t(t));
+    }
+    amr_mesh::MGLTab &T = h->mgl[size_t(k)];
+    T.L = L - k;
+    T.n = n;
+    T.nc0 = int64_t(col.size());
+    T.nc1 = int64_t(c1.size());
+    col.insert(col.end(), c1.begin(), c1.end());
+    AMR_TRY(upload(h, &T.nb, nb));
+    AMR_TRY(upload(h, &T.nbnd, nbnd));
+    AMR_TRY(upload(h, &T.col, col));
+    AMR_TRY(alloc_n(h, &T.e, n));
+    AMR_TRY(alloc_n(h, &T.f, n));
+    AMR_TRY(alloc_n(h, &T.r, n));
+    if (k >= 1) {
+      // children in MG level k-1 (cx, cy, cz; cz fastest); the trilinear
+      // stencils of level k-1's cells in this level
+      const std::vector<uint64_t> &fine = codes[size_t(k - 1)];
+      const int64_t nf = int64_t(fine.size());
+      std::vector<int32_t> child(8 * size_t(n)), pro(8 * size_t(nf));
+      for (int64_t t = 0; t < n; ++t) {
+        int64_t x, y, z;
+        xyz(cd[size_t(t)], x, y, z);
+        int j = 0;
+        for (int cx = 0; cx < 2; ++cx)
+          for (int cy = 0; cy < 2; ++cy)
+            for (int cz = 0; cz < 2; ++cz, ++j)
+              child[size_t(j * n + t)] = find_in(fine, mgl_code(2 * x + cx, 2 * y + cy, 2 * z + cz));
+      }
+      for (int64_t t = 0; t < nf; ++t) {
+        int64_t x, y, z;
+        xyz(fine[size_t(t)], x, y, z);
+        const int64_t X = x >> 1, Y = y >> 1, Z = z >> 1;
+        const int64_t sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b)
+            for (int d = 0; d < 2; ++d)
+              pro[size_t((4 * a + 2 * b + d) * nf + t)] =
+                  find_in(cd, mgl_code((X + a * sx) & (side - 1), (Y + b * sy) & (side - 1), (Z + d * sz) & (side - 1)));
+      }
+      AMR_TRY(upload(h, &T.child, child));
+      AMR_TRY(upload(h, &h->mgl[size_t(k - 1)].pro, pro));
+    }
+  }
+  // level 0: global cells, fathers, coarse cells across boundary faces
+  {
+    const int64_t n = h->mgl[0].n;
+    const int64_t side = int64_t(1) << L, cside = side >> 1;
+    const size_t nn = size_t(n);
+    std::vector<int32_t> g0(nn), fg(nn), ag(6 * nn, -1);
+    for (int64_t t = 0; t < n; ++t) {
+      g0[size_t(t)] = cL[size_t(t)].second;
+      int64_t x, y, z;
+      xyz(codes[0][size_t(t)], x, y, z);
+      fg[size_t(t)] = find_L1(mgl_code(x >> 1, y >> 1, z >> 1));
+    }
+    // boundary faces: read back the neighbour table of level 0
+    std::vector<int32_t> nb(6 * size_t(n));
+    CUDA_TRY(cudaMemcpyAsync(nb.data(), h->mgl[0].nb, 4 * nb.size(), cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+    for (int64_t t = 0; t < n; ++t) {
+      int64_t x, y, z;
+      xyz(codes[0][size_t(t)], x, y, z);
+      for (int d = 0; d < 3; ++d)
+        for (int sg = 0; sg < 2; ++sg) {
+          const int k6 = 2 * d + sg;
+          if (nb[size_t(k6 * n + t)] >= 0) continue;
+          const int64_t dd = sg ? 1 : -1;
+          const int64_t X = (x + (d == 0) * dd) & (side - 1), Y = (y + (d == 1) * dd) & (side - 1),
+                        Z = (z + (d == 2) * dd) & (side - 1);
+          ag[size_t(k6 * n + t)] = find_L1(mgl_code((X >> 1) & (cside - 1), (Y >> 1) & (cside - 1), (Z >> 1) & (cside - 1)));
+          if (ag[size_t(k6 * n + t)] < 0)
+            return fail(AMR_EGRADING, "amr_poisson_level: a boundary face of level %d has no coarse cell across", L);
+        }
+    }
+    for (int32_t v : fg)
+      if (v < 0) return fail(AMR_EGRADING, "amr_poisson_level: a cell of level %d has no father", L);
+    AMR_TRY(upload(h, &h->mgl_g0, g0));
+    AMR_TRY(upload(h, &h->mgl_fatherg, fg));
+    AMR_TRY(upload(h, &h->mgl_acrossg, ag));
+    AMR_TRY(alloc_n(h, &h->mgl_bsum, n));
+    AMR_TRY(alloc_n(h, &h->mgl_part, kMGParts));
+    AMR_TRY(alloc_n(h, &h->mgl_scalar, 4));
+  }
+  h->mgl_member = h->sel;
+  h->mgl_level = L;
+  return AMR_OK;
+}
+
+static void mgl_sweep(amr_mesh *h, size_t k) {
+  amr_mesh::MGLTab &T = h->mgl[k];
+  const double dx = std::ldexp(1.0, -T.L), dx2 = dx * dx;
+  const double *bs = k == 0 ? h->mgl_bsum : nullptr;
+  if (T.nc0)
+    launch(h, K_MG_SMOOTH, k_mgl_smooth, dim3(nblocks(T.nc0)), dim3(256), T.n, (const int32_t *)T.col, T.nc0,
+           (const int32_t *)T.nb, (const int32_t *)T.nbnd, bs, (const double *)T.f, T.e, dx2);
+  if (T.nc1)
+    launch(h, K_MG_SMOOTH, k_mgl_smooth, dim3(nblocks(T.nc1)), dim3(256), T.n, (const int32_t *)(T.col + T.nc0),
+           T.nc1, (const int32_t *)T.nb, (const int32_t *)T.nbnd, bs, (const double *)T.f, T.e, dx2);
+}
+
+static void mgl_residual(amr_mesh *h, size_t k) {
+  amr_mesh::MGLTab &T = h->mgl[k];
+  const double dx = std::ldexp(1.0, -T.L), dx2 = dx * dx;
+  launch(h, K_MG_OTHER, k_mgl_residual, dim3(nblocks(T.n)), dim3(256), T.n, (const int32_t *)T.nb,
+         (const int32_t *)T.nbnd, (const double *)(k == 0 ? h->mgl_bsum : nullptr), (const double *)T.f,
+         (const double *)T.e, dx2, T.r);
+}
+
+static void mgl_vcycle(amr_mesh *h, size_t k) {
+  const size_t K = h->mgl.size() - 1;
+  if (k == K) {
+    for (int s = 0; s < kMGCoarsest; ++s) mgl_sweep(h, k);
+    return;
+  }
+  for (int s = 0; s < kMGPre; ++s) mgl_sweep(h, k);
+  mgl_residual(h, k);
+  amr_mesh::MGLTab &T = h->mgl[k], &C = h->mgl[k + 1];
+  launch(h, K_MG_RESTRICT, k_mgl_restrict, dim3(nblocks(C.n)), dim3(256), C.n, (const int32_t *)C.child,
+         (const double *)T.r, C.f, C.e);
+  mgl_vcycle(h, k + 1);
+  launch(h, K_MG_PROLONG, k_mgl_prolong, dim3(nblocks(T.n)), dim3(256), T.n, (const int32_t *)T.pro,
+         (const double *)C.e, T.e);
+  for (int s = 0; s < kMGPost; ++s) mgl_sweep(h, k);
+}
+
+// one level's solve from the current potential of level L-1 (Dirichlet
+// data) and of level L (initial guess); rho_bar host value or, if rho_bar_dev
+// is set, read on the device
+static amr_status poisson_level(amr_mesh *h, int L, double fourpiG, double rho_bar,
+                                const double *rho_bar_dev, int n_vcycles, double *resid) {
+  AMR_TRY(ensure_phil(h));
+  AMR_TRY(mgl_setup(h, L));
+  amr_mesh::MGLTab &T0 = h->mgl[0];
+  const int64_t n = T0.n;
+  launch(h, K_MG_OTHER, k_mgl_bsum, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_fatherg,
+         (const int32_t *)h->mgl_acrossg, (const double *)h->phil, h->mgl_bsum);
+  double rb = rho_bar;
+  if (rho_bar_dev) {
+    CUDA_TRY(cudaMemcpyAsync(&rb, rho_bar_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+  }
+  if (h->p.precision == 4)
+    launch(h, K_MG_OTHER, k_mgl_source<float>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+           (const float *)h->U, fourpiG, rb, T0.f);
+  else
+    launch(h, K_MG_OTHER, k_mgl_source<double>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+           (const double *)h->U, fourpiG, rb, T0.f);
+  launch(h, K_MG_OTHER, k_mgl_gather, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+         (const double *)h->phil, T0.e);
+  const unsigned nb = unsigned(std::min<int64_t>((n + 255) / 256, kMGParts));
+  for (int c = 0; c < n_vcycles; ++c) {
+    mgl_vcycle(h, 0);
+    if (resid) {
+      mgl_residual(h, 0);
+      launch(h, K_MG_OTHER, k_mgl_sq, dim3(nb), dim3(256), n, (const double *)T0.r, h->mgl_part);
+      launch(h, K_MG_OTHER, k_mgl_norm, dim3(1), dim3(32), (const double *)h->mgl_part, int(nb), h->mgl_scalar);
+      CUDA_TRY(cudaMemcpyAsync(resid + c, h->mgl_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    }
+  }
+  launch(h, K_MG_OTHER, k_mgl_scatter, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+         (const double *)T0.e, h->phil);
+  return AMR_OK;
+}
+
+static amr_status check_level_solve(amr_mesh *h, int L, int n_vcycles, const char *where) {
+  const Member &mb = h->mem[h->sel];
+  if (n_vcycles < 0 || n_vcycles > 1020) return fail(AMR_EINVAL, "%s: n_vcycles must be in [0, 1020]", where);
+  if (L <= mb.lmin || L > mb.lmax || mb.lo[L + 1] == mb.lo[L])
+    return fail(AMR_EINVAL, "%s: level %d is not a populated refined level", where, L);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_poisson_level(amr_handle h, int level, double fourpiG, double rho_bar,
+                                        int n_vcycles, double *resid) {
+  if (!h) return fail(AMR_EINVAL, "amr_poisson_level: NULL handle");
+  AMR_TRY(check_level_solve(h, level, n_vcycles, "amr_poisson_level"));
+  AMR_TRY(poisson_level(h, level, fourpiG, rho_bar, nullptr, n_vcycles, resid));
+  return check_device(h, "amr_poisson_level");
+}
+
+// father cell's potential into every cell of level L (the initial guess)
+__global__ void k_mgl_inject(int lo, int nl, const uint64_t *__restrict__ key, const int32_t *__restrict__ father,
+                             double *phil) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 8 * nl) return;
+  const int o = lo + q / 8, c = q & 7;
+  const uint64_t k = key[o];
+  const int fc = int((ikey_x(k) & 1) | ((ikey_y(k) & 1) << 1) | ((ikey_z(k) & 1) << 2));
+  phil[8 * int64_t(o) + c] = phil[8 * int64_t(father[o]) + fc];
+}
+
+extern "C" amr_status amr_poisson_levels(amr_handle h, double fourpiG, int n_vcycles, double *resid) {
+  if (!h) return fail(AMR_EINVAL, "amr_poisson_levels: NULL handle");
+  const Member &mb = h->mem[h->sel];
+  std::vector<double> r0(size_t(std::max(n_vcycles, 1)));
+  AMR_TRY(amr_poisson(h, fourpiG, n_vcycles, resid ? r0.data() : nullptr));
+  AMR_TRY(ensure_phil(h));
+  const int64_t blo = mb.oct_base + mb.lo[mb.lmin], bnl = mb.lo[mb.lmin + 1] - mb.lo[mb.lmin];
+  CUDA_TRY(cudaMemcpyAsync(h->phil + 8 * blo, h->phi, sizeof(double) * size_t(8 * bnl), cudaMemcpyDeviceToDevice, h->s));
+  if (resid)
+    for (int c = 0; c < n_vcycles; ++c) resid[size_t(mb.lmin) * n_vcycles + c] = r0[size_t(c)];
+  const double *mean = h->mg_res + 1022;  // the base density's mean (amr_poisson)
+  for (int L = mb.lmin + 1; L <= mb.lmax; ++L) {
+    const int lo = int(mb.oct_base + mb.lo[L]), nl = int(mb.lo[L + 1] - mb.lo[L]);
+    if (nl == 0) break;
+    launch(h, K_MG_OTHER, k_mgl_inject, dim3(nblocks(8 * int64_t(nl))), dim3(256), lo, nl,
+           (const uint64_t *)h->key, (const int32_t *)h->father, h->phil);
+    AMR_TRY(poisson_level(h, L, fourpiG, 0.0, mean, n_vcycles,
+                          resid ? resid + size_t(L) * n_vcycles : nullptr));
+  }
+  return check_device(h, "amr_poisson_levels");
+}
+
+extern "C" amr_status amr_write_phi(amr_handle h, int level, const double *phi, int64_t n) {
+  if (!h || !phi) return fail(AMR_EINVAL, "amr_write_phi: NULL argument");
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_write_phi: bad level");
+  const Member &mb = h->mem[h->sel];
+  const int64_t lo = mb.oct_base + mb.lo[level], nl = mb.lo[level + 1] - mb.lo[level];
+  if (n != 8 * nl) return fail(AMR_EINVAL, "amr_write_phi: %lld values for %lld cells", (long long)n, (long long)(8 * nl));
+  AMR_TRY(ensure_phil(h));
+  if (nl) CUDA_TRY(cudaMemcpyAsync(h->phil + 8 * lo, phi, sizeof(double) * size_t(8 * nl), cudaMemcpyHostToDevice, h->s));
+  return check_device(h, "amr_write_phi");
+}
+
+extern "C" amr_status amr_read_phi_level(amr_handle h, int level, double *phi, int64_t cap) {
+  if (!h || !phi) return fail(AMR_EINVAL, "amr_read_phi_level: NULL argument");
+  if (!level_ok(level)) return fail(AMR_EINVAL, "amr_read_phi_level: bad level");
+  const Member &mb = h->mem[h->sel];
+  const int64_t lo = mb.oct_base + mb.lo[level], nl = mb.lo[level + 1] - mb.lo[level];
+  if (cap < 8 * nl)
+    return fail(AMR_EINVAL, "amr_read_phi_level: cap %lld < %lld cells", (long long)cap, (long long)(8 * nl));
+  if (!h->phil || h->phil_n != 8 * h->N) return fail(AMR_EINVAL, "amr_read_phi_level: no potential on this mesh");
+  if (nl) CUDA_TRY(cudaMemcpyAsync(phi, h->phil + 8 * lo, sizeof(double) * size_t(8 * nl), cudaMemcpyDeviceToHost, h->s));
+  return check_device(h, "amr_read_phi_level");
+}
+
 extern "C" amr_status amr_read_phi(amr_handle h, double *phi, int64_t cap) {
   if (!h || !phi) return fail(AMR_EINVAL, "amr_read_phi: NULL argument");
   const Member &mb = h->mem[h->sel];
@@ -2167,7 +2525,6 @@ static amr_status rows_to_host(amr_mesh *h, const void *src, int64_t stride, int
   return AMR_OK;
 }
 
-static bool level_ok(int level) { return level >= 0 && level <= kMaxLev; }
 
 extern "C" amr_status amr_read(amr_handle h, int level, int64_t *n_oct_out, uint64_t *keys,
                                double *U, int64_t cap) {

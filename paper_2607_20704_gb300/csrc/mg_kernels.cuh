@@ -175,4 +175,140 @@ __global__ void k_mg_scatter(const double *__restrict__ p, const uint64_t *__res
   phi_cells[g] = p[mg_at(n, x, y, z)] - *mean;
 }
 
+// ---------------------------------------------------------------------------
+// Poisson on a refined level (Sec. 5, level by level): flat tables over the
+// cells of each MG level (level 0: the level's cells; level k: their
+// ancestors at level L-k), built on the host once per (member, level).
+// Every operation is rounded as written (no contraction), in the order of the
+// plain definition, so the potential equals that of a sequential evaluation
+// bit for bit.
+//   nb[6][n]   face neighbour in the same MG level (-x,+x,-y,+y,-z,+z) or -1
+//   nbnd[n]    faces to the outside (Dirichlet): the diagonal is -(6 + nbnd)
+//   bsum[n]    2 sum of the faces' boundary values (MG level 0; 0 above)
+//   child[8][n]   children in the MG level below (order cx, cy, cz with cz
+//                 fastest) or -1; pro[8][n] the 8 coarse cells of a cell's
+//                 trilinear stencil (a, b, d: 4 a + 2 b + d) or -1
+// ---------------------------------------------------------------------------
+__global__ void k_mgl_bsum(int64_t n, const int32_t *__restrict__ fatherg, const int32_t *__restrict__ acrossg,
+                           const double *__restrict__ phil, double *__restrict__ bsum) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const double pf = phil[fatherg[t]];
+  double bs = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    const int32_t q = acrossg[k * n + t];
+    if (q >= 0) bs = __dadd_rn(bs, __dmul_rn(2.0, __dmul_rn(0.5, __dadd_rn(pf, phil[q]))));
+  }
+  bsum[t] = bs;
+}
+
+template <class T>
+__global__ void k_mgl_source(int64_t n, const int32_t *__restrict__ g0, const T *__restrict__ rho, double fourpiG,
+                             double rho_bar, double *__restrict__ f) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  f[t] = __dmul_rn(fourpiG, __dsub_rn(double(rho[g0[t]]), rho_bar));
+}
+
+__global__ void k_mgl_gather(int64_t n, const int32_t *__restrict__ g0, const double *__restrict__ phil,
+                             double *__restrict__ e) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < n) e[t] = phil[g0[t]];
+}
+
+__global__ void k_mgl_scatter(int64_t n, const int32_t *__restrict__ g0, const double *__restrict__ e,
+                              double *__restrict__ phil) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < n) phil[g0[t]] = e[t];
+}
+
+__device__ __forceinline__ double mgl_nbsum(int64_t n, const int32_t *__restrict__ nb, const double *e, int64_t t) {
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int32_t q = nb[k * n + t];
+    if (q >= 0) s = __dadd_rn(s, e[q]);
+  }
+  return s;
+}
+
+// one colour of a red-black sweep: the cells of list[0..m)
+__global__ void k_mgl_smooth(int64_t n, const int32_t *__restrict__ list, int64_t m, const int32_t *__restrict__ nb,
+                             const int32_t *__restrict__ nbnd, const double *__restrict__ bsum,
+                             const double *__restrict__ f, double *e, double dx2) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= m) return;
+  const int64_t t = list[i];
+  const double s = mgl_nbsum(n, nb, e, t);
+  const double bs = bsum ? bsum[t] : 0.0;
+  e[t] = __ddiv_rn(__dsub_rn(__dadd_rn(s, bs), __dmul_rn(dx2, f[t])), double(6 + nbnd[t]));
+}
+
+__global__ void k_mgl_residual(int64_t n, const int32_t *__restrict__ nb, const int32_t *__restrict__ nbnd,
+                               const double *__restrict__ bsum, const double *__restrict__ f,
+                               const double *__restrict__ e, double dx2, double *__restrict__ r) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const double s = mgl_nbsum(n, nb, e, t);
+  const double bs = bsum ? bsum[t] : 0.0;
+  r[t] = __dsub_rn(f[t], __ddiv_rn(__dsub_rn(__dadd_rn(s, bs), __dmul_rn(double(6 + nbnd[t]), e[t])), dx2));
+}
+
+// coarse source = the children's residuals summed over 8; correction zeroed
+__global__ void k_mgl_restrict(int64_t nc, const int32_t *__restrict__ child, const double *__restrict__ r,
+                               double *__restrict__ fc, double *__restrict__ ec) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nc) return;
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int32_t q = child[j * nc + t];
+    if (q >= 0) s = __dadd_rn(s, r[q]);
+  }
+  fc[t] = __ddiv_rn(s, 8.0);
+  ec[t] = 0.0;
+}
+
+__global__ void k_mgl_prolong(int64_t nf, const int32_t *__restrict__ pro, const double *__restrict__ ec,
+                              double *__restrict__ e) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nf) return;
+  double c[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int32_t q = pro[j * nf + t];
+    c[j] = q >= 0 ? ec[q] : 0.0;
+  }
+  // c[4 a + 2 b + d]: a along x, b along y, d along z
+  double v = __dmul_rn(27.0, c[0]);
+  v = __dadd_rn(v, __dmul_rn(9.0, __dadd_rn(__dadd_rn(c[4], c[2]), c[1])));
+  v = __dadd_rn(v, __dmul_rn(3.0, __dadd_rn(__dadd_rn(c[6], c[5]), c[3])));
+  v = __dadd_rn(v, c[7]);
+  e[t] = __dadd_rn(e[t], __ddiv_rn(v, 64.0));
+}
+
+// sum of r^2 into one value per block (for the residual norm)
+__global__ void k_mgl_sq(int64_t n, const double *__restrict__ r, double *__restrict__ part) {
+  __shared__ double ws[8];
+  double s = 0.0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x)
+    s += r[t] * r[t];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) b += ws[w];
+    part[blockIdx.x] = b;
+  }
+}
+
+__global__ void k_mgl_norm(const double *__restrict__ part, int nparts, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += part[b];
+  *out = sqrt(s);
+}
+
 }  // namespace amr
