@@ -591,6 +591,39 @@ def run_poisson(level, cycles, torch, device):
             "kernels": {k: round(v[0] / ktot, 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}}
 
 
+def run_poisson_levels(cycles, torch, device):
+    """The potential of every level of the cosmology-shaped mesh (levels 8-11,
+    Sec. 5: the base level's periodic solve, then each refined level from its
+    father cells' values with Dirichlet data from the level below):
+    cell-updates per V-cycle per second over all levels' cells (one call of
+    `cycles` V-cycles per level, no residual norms), the per-level cell counts
+    and residual reductions, and the one-off host build of the level
+    hierarchies (first call)."""
+    import time
+    from paper_2607_20704_gb300 import amr, inputs
+    prob = inputs.lognormal()
+    m = amr.Mesh(*prob.mesh_args(), **prob.params(), stream=bench_stream())
+    st = m.stream
+    t0 = time.perf_counter()
+    res = m.poisson_levels(1.0, cycles)  # builds the tables; convergence
+    build_s = time.perf_counter() - t0
+    m.poisson_levels(1.0, cycles, residuals=False)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    m.poisson_levels(1.0, cycles, residuals=False)
+    e1.record(st)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1)
+    cells = {l: 8 * m.num_octs(l) for l in res}
+    total = sum(cells.values())
+    m.close()
+    return {"mesh": "lognormal levels 8-11", "vcycles_per_level": cycles, "cells": cells,
+            "ms": round(ms, 4), "cell_updates_per_s": total * cycles / (ms * 1e-3),
+            "residual_reduction_per_vcycle": {l: round(float(np.median(r[1:] / r[:-1])), 4) for l, r in res.items()},
+            "first_call_s_host_tables": round(build_s, 3)}
+
+
 def run_cic(n, reps, warmup, torch, peak_gbs, peak_src):
     """Cloud-in-Cell mass deposition (Sec. 4) of a cosmological particle set
     with N_part = N_grid = n^3 on the periodic n^3 grid: particle
@@ -996,6 +1029,8 @@ def main():
             other["steps"] = args.steps
         e2e = None if args.no_e2e else run_e2e(prob, prec_main, max(3, args.steps // 2), torch)
         poisson = None if args.no_poisson else run_poisson(8, 10, torch, device)
+        if poisson is not None:
+            poisson["levels"] = run_poisson_levels(4, torch, device)
         cic = None if args.no_cic else run_cic(args.cic_grid, 5, 3, torch, peak_gbs, peak_src)
         variants = None if args.no_variants else run_variants(prob, 7, torch, device, flush)
         unigrid = None if args.no_unigrid else run_unigrid(8, 7, torch, device)

@@ -229,10 +229,13 @@ struct amr_mesh {
     int32_t *nb = nullptr, *nbnd = nullptr, *col = nullptr, *child = nullptr, *pro = nullptr;
     double *e = nullptr, *f = nullptr, *r = nullptr;
   };
-  std::vector<MGLTab> mgl;
-  int mgl_member = -1, mgl_level = -1;
-  int32_t *mgl_g0 = nullptr, *mgl_fatherg = nullptr, *mgl_acrossg = nullptr;
-  double *mgl_bsum = nullptr, *mgl_part = nullptr, *mgl_scalar = nullptr;
+  struct MGLSet {
+    std::vector<MGLTab> tab;
+    int32_t *g0 = nullptr, *fatherg = nullptr, *acrossg = nullptr;
+    double *bsum = nullptr;
+  };
+  std::map<int, MGLSet> mgls;  // key: member * 32 + level
+  double *mgl_part = nullptr, *mgl_scalar = nullptr;
   double *phil = nullptr;
   int64_t phil_n = 0;
   double *mg_rho = nullptr, *mg_r = nullptr, *mg_part = nullptr, *mg_res = nullptr;
@@ -2167,26 +2170,29 @@ static inline uint64_t mgl_code(int64_t x, int64_t y, int64_t z) {
   return (uint64_t(x) << 42) | (uint64_t(y) << 21) | uint64_t(z);
 }
 
-static void mgl_free(amr_mesh *h) {
-  for (auto &t : h->mgl)
+static void mgl_free_set(amr_mesh *h, amr_mesh::MGLSet &S) {
+  for (auto &t : S.tab)
     for (void *b : {(void *)t.nb, (void *)t.nbnd, (void *)t.col, (void *)t.child, (void *)t.pro, (void *)t.e,
                     (void *)t.f, (void *)t.r})
       dev_free(h, b);
-  h->mgl.clear();
-  for (void *b : {(void *)h->mgl_g0, (void *)h->mgl_fatherg, (void *)h->mgl_acrossg, (void *)h->mgl_bsum,
-                  (void *)h->mgl_part, (void *)h->mgl_scalar})
-    dev_free(h, b);
-  h->mgl_g0 = h->mgl_fatherg = h->mgl_acrossg = nullptr;
-  h->mgl_bsum = h->mgl_part = h->mgl_scalar = nullptr;
-  h->mgl_member = h->mgl_level = -1;
+  S.tab.clear();
+  for (void *b : {(void *)S.g0, (void *)S.fatherg, (void *)S.acrossg, (void *)S.bsum}) dev_free(h, b);
+  S.g0 = S.fatherg = S.acrossg = nullptr;
+  S.bsum = nullptr;
+}
+
+static void mgl_free(amr_mesh *h) {
+  for (auto &kv : h->mgls) mgl_free_set(h, kv.second);
+  h->mgls.clear();
+  dev_free(h, h->mgl_part);
+  dev_free(h, h->mgl_scalar);
+  h->mgl_part = h->mgl_scalar = nullptr;
 }
 
 // The MG hierarchy of level L of the selected member: level 0 = the cells of
 // the level-L octs, level k = the level-(L-k) ancestors of level k-1, down to
 // levelmin; every table in sorted (x, y, z) order of the cells.
-static amr_status mgl_setup(amr_mesh *h, int L) {
-  if (h->mgl_member == h->sel && h->mgl_level == L && !h->mgl.empty()) return AMR_OK;
-  mgl_free(h);
+static amr_status mgl_build(amr_mesh *h, int L, amr_mesh::MGLSet &S) {
   const Member &mb = h->mem[h->sel];
   const int lmin = mb.lmin, K = L - lmin;
   const int64_t olo = mb.oct_base + mb.lo[L - 1], ohi = mb.oct_base + mb.lo[L + 1];
@@ -2197,22 +2203,29 @@ static amr_status mgl_setup(amr_mesh *h, int L) {
     return mgl_code(2 * int64_t(ikey_x(k)) + (c & 1), 2 * int64_t(ikey_y(k)) + ((c >> 1) & 1),
                     2 * int64_t(ikey_z(k)) + ((c >> 2) & 1));
   };
-  // cells of levels L-1 and L: (code, global cell index), sorted
-  std::vector<std::pair<uint64_t, int32_t>> cL, cL1;
+  // cells of level L: (code, global cell index); octs of level L-1: (code,
+  // global oct index); both sorted
+  std::vector<std::pair<uint64_t, int32_t>> cL, oL1;
   for (int64_t o = olo; o < ohi; ++o) {
     const uint64_t k = key[size_t(o - olo)];
-    auto &dst = ikey_lev(k) == L ? cL : cL1;
-    for (int c = 0; c < 8; ++c) dst.push_back({cell_code(k, c), int32_t(8 * o + c)});
+    if (ikey_lev(k) == L)
+      for (int c = 0; c < 8; ++c) cL.push_back({cell_code(k, c), int32_t(8 * o + c)});
+    else
+      oL1.push_back({mgl_code(ikey_x(k), ikey_y(k), ikey_z(k)), int32_t(o)});
   }
   std::sort(cL.begin(), cL.end());
-  std::sort(cL1.begin(), cL1.end());
+  std::sort(oL1.begin(), oL1.end());
   auto find_in = [](const std::vector<uint64_t> &v, uint64_t c) -> int32_t {
     auto it = std::lower_bound(v.begin(), v.end(), c);
     return (it != v.end() && *it == c) ? int32_t(it - v.begin()) : -1;
   };
+  // global index of the level-(L-1) cell with the given code, or -1
   auto find_L1 = [&](uint64_t c) -> int32_t {
-    auto it = std::lower_bound(cL1.begin(), cL1.end(), std::make_pair(c, int32_t(-1)));
-    return (it != cL1.end() && it->first == c) ? it->second : -1;
+    const int64_t X = int64_t(c >> 42), Y = int64_t((c >> 21) & 0x1FFFFF), Z = int64_t(c & 0x1FFFFF);
+    const uint64_t oc = mgl_code(X >> 1, Y >> 1, Z >> 1);
+    auto it = std::lower_bound(oL1.begin(), oL1.end(), std::make_pair(oc, int32_t(-1)));
+    if (it == oL1.end() || it->first != oc) return -1;
+    return 8 * it->second + int32_t((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2));
   };
   std::vector<std::vector<uint64_t>> codes(size_t(K + 1));
   for (auto &pr : cL) codes[0].push_back(pr.first);
@@ -2228,7 +2241,7 @@ static amr_status mgl_setup(amr_mesh *h, int L) {
     y = int64_t((c >> 21) & 0x1FFFFF);
     z = int64_t(c & 0x1FFFFF);
   };
-  h->mgl.resize(size_t(K + 1));
+  S.tab.resize(size_t(K + 1));
   for (int k = 0; k <= K; ++k) {
     const std::vector<uint64_t> &cd = codes[size_t(k)];
     const int64_t n = int64_t(cd.size());
@@ -2249,7 +2262,7 @@ static amr_status mgl_setup(amr_mesh *h, int L) {
         }
       ((x + y + z) & 1 ? c1 : col).push_back(int32_t(t));
     }
-    amr_mesh::MGLTab &T = h->mgl[size_t(k)];
+    amr_mesh::MGLTab &T = S.tab[size_t(k)];
     T.L = L - k;
     T.n = n;
     T.nc0 = int64_t(col.size());
@@ -2288,12 +2301,12 @@ static amr_status mgl_setup(amr_mesh *h, int L) {
                   find_in(cd, mgl_code((X + a * sx) & (side - 1), (Y + b * sy) & (side - 1), (Z + d * sz) & (side - 1)));
       }
       AMR_TRY(upload(h, &T.child, child));
-      AMR_TRY(upload(h, &h->mgl[size_t(k - 1)].pro, pro));
+      AMR_TRY(upload(h, &S.tab[size_t(k - 1)].pro, pro));
     }
   }
   // level 0: global cells, fathers, coarse cells across boundary faces
   {
-    const int64_t n = h->mgl[0].n;
+    const int64_t n = S.tab[0].n;
     const int64_t side = int64_t(1) << L, cside = side >> 1;
     const size_t nn = size_t(n);
     std::vector<int32_t> g0(nn), fg(nn), ag(6 * nn, -1);
@@ -2305,7 +2318,7 @@ static amr_status mgl_setup(amr_mesh *h, int L) {
     }
     // boundary faces: read back the neighbour table of level 0
     std::vector<int32_t> nb(6 * size_t(n));
-    CUDA_TRY(cudaMemcpyAsync(nb.data(), h->mgl[0].nb, 4 * nb.size(), cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaMemcpyAsync(nb.data(), S.tab[0].nb, 4 * nb.size(), cudaMemcpyDeviceToHost, h->s));
     CUDA_TRY(cudaStreamSynchronize(h->s));
     for (int64_t t = 0; t < n; ++t) {
       int64_t x, y, z;
@@ -2324,22 +2337,40 @@ static amr_status mgl_setup(amr_mesh *h, int L) {
     }
     for (int32_t v : fg)
       if (v < 0) return fail(AMR_EGRADING, "amr_poisson_level: a cell of level %d has no father", L);
-    AMR_TRY(upload(h, &h->mgl_g0, g0));
-    AMR_TRY(upload(h, &h->mgl_fatherg, fg));
-    AMR_TRY(upload(h, &h->mgl_acrossg, ag));
-    AMR_TRY(alloc_n(h, &h->mgl_bsum, n));
-    AMR_TRY(alloc_n(h, &h->mgl_part, kMGParts));
-    AMR_TRY(alloc_n(h, &h->mgl_scalar, 4));
+    AMR_TRY(upload(h, &S.g0, g0));
+    AMR_TRY(upload(h, &S.fatherg, fg));
+    AMR_TRY(upload(h, &S.acrossg, ag));
+    AMR_TRY(alloc_n(h, &S.bsum, n));
   }
-  h->mgl_member = h->sel;
-  h->mgl_level = L;
   return AMR_OK;
 }
 
-static void mgl_sweep(amr_mesh *h, size_t k) {
-  amr_mesh::MGLTab &T = h->mgl[k];
+// the hierarchy of level L of the selected member, built on first use and
+// kept until the mesh changes
+static amr_status mgl_setup(amr_mesh *h, int L, amr_mesh::MGLSet **out) {
+  if (!h->mgl_part) {
+    AMR_TRY(alloc_n(h, &h->mgl_part, kMGParts));
+    AMR_TRY(alloc_n(h, &h->mgl_scalar, 4));
+  }
+  const int key = h->sel * 32 + L;
+  auto it = h->mgls.find(key);
+  if (it == h->mgls.end()) {
+    amr_mesh::MGLSet S;
+    const amr_status st = mgl_build(h, L, S);
+    if (st != AMR_OK) {
+      mgl_free_set(h, S);
+      return st;
+    }
+    it = h->mgls.emplace(key, std::move(S)).first;
+  }
+  *out = &it->second;
+  return AMR_OK;
+}
+
+static void mgl_sweep(amr_mesh *h, amr_mesh::MGLSet &S, size_t k) {
+  amr_mesh::MGLTab &T = S.tab[k];
   const double dx = std::ldexp(1.0, -T.L), dx2 = dx * dx;
-  const double *bs = k == 0 ? h->mgl_bsum : nullptr;
+  const double *bs = k == 0 ? S.bsum : nullptr;
   if (T.nc0)
     launch(h, K_MG_SMOOTH, k_mgl_smooth, dim3(nblocks(T.nc0)), dim3(256), T.n, (const int32_t *)T.col, T.nc0,
            (const int32_t *)T.nb, (const int32_t *)T.nbnd, bs, (const double *)T.f, T.e, dx2);
@@ -2348,29 +2379,29 @@ static void mgl_sweep(amr_mesh *h, size_t k) {
            T.nc1, (const int32_t *)T.nb, (const int32_t *)T.nbnd, bs, (const double *)T.f, T.e, dx2);
 }
 
-static void mgl_residual(amr_mesh *h, size_t k) {
-  amr_mesh::MGLTab &T = h->mgl[k];
+static void mgl_residual(amr_mesh *h, amr_mesh::MGLSet &S, size_t k) {
+  amr_mesh::MGLTab &T = S.tab[k];
   const double dx = std::ldexp(1.0, -T.L), dx2 = dx * dx;
   launch(h, K_MG_OTHER, k_mgl_residual, dim3(nblocks(T.n)), dim3(256), T.n, (const int32_t *)T.nb,
-         (const int32_t *)T.nbnd, (const double *)(k == 0 ? h->mgl_bsum : nullptr), (const double *)T.f,
+         (const int32_t *)T.nbnd, (const double *)(k == 0 ? S.bsum : nullptr), (const double *)T.f,
          (const double *)T.e, dx2, T.r);
 }
 
-static void mgl_vcycle(amr_mesh *h, size_t k) {
-  const size_t K = h->mgl.size() - 1;
+static void mgl_vcycle(amr_mesh *h, amr_mesh::MGLSet &S, size_t k) {
+  const size_t K = S.tab.size() - 1;
   if (k == K) {
-    for (int s = 0; s < kMGCoarsest; ++s) mgl_sweep(h, k);
+    for (int s = 0; s < kMGCoarsest; ++s) mgl_sweep(h, S, k);
     return;
   }
-  for (int s = 0; s < kMGPre; ++s) mgl_sweep(h, k);
-  mgl_residual(h, k);
-  amr_mesh::MGLTab &T = h->mgl[k], &C = h->mgl[k + 1];
+  for (int s = 0; s < kMGPre; ++s) mgl_sweep(h, S, k);
+  mgl_residual(h, S, k);
+  amr_mesh::MGLTab &T = S.tab[k], &C = S.tab[k + 1];
   launch(h, K_MG_RESTRICT, k_mgl_restrict, dim3(nblocks(C.n)), dim3(256), C.n, (const int32_t *)C.child,
          (const double *)T.r, C.f, C.e);
-  mgl_vcycle(h, k + 1);
+  mgl_vcycle(h, S, k + 1);
   launch(h, K_MG_PROLONG, k_mgl_prolong, dim3(nblocks(T.n)), dim3(256), T.n, (const int32_t *)T.pro,
          (const double *)C.e, T.e);
-  for (int s = 0; s < kMGPost; ++s) mgl_sweep(h, k);
+  for (int s = 0; s < kMGPost; ++s) mgl_sweep(h, S, k);
 }
 
 // one level's solve from the current potential of level L-1 (Dirichlet
@@ -2379,35 +2410,37 @@ static void mgl_vcycle(amr_mesh *h, size_t k) {
 static amr_status poisson_level(amr_mesh *h, int L, double fourpiG, double rho_bar,
                                 const double *rho_bar_dev, int n_vcycles, double *resid) {
   AMR_TRY(ensure_phil(h));
-  AMR_TRY(mgl_setup(h, L));
-  amr_mesh::MGLTab &T0 = h->mgl[0];
+  amr_mesh::MGLSet *Sp = nullptr;
+  AMR_TRY(mgl_setup(h, L, &Sp));
+  amr_mesh::MGLSet &S = *Sp;
+  amr_mesh::MGLTab &T0 = S.tab[0];
   const int64_t n = T0.n;
-  launch(h, K_MG_OTHER, k_mgl_bsum, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_fatherg,
-         (const int32_t *)h->mgl_acrossg, (const double *)h->phil, h->mgl_bsum);
+  launch(h, K_MG_OTHER, k_mgl_bsum, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.fatherg,
+         (const int32_t *)S.acrossg, (const double *)h->phil, S.bsum);
   double rb = rho_bar;
   if (rho_bar_dev) {
     CUDA_TRY(cudaMemcpyAsync(&rb, rho_bar_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
     CUDA_TRY(cudaStreamSynchronize(h->s));
   }
   if (h->p.precision == 4)
-    launch(h, K_MG_OTHER, k_mgl_source<float>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+    launch(h, K_MG_OTHER, k_mgl_source<float>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.g0,
            (const float *)h->U, fourpiG, rb, T0.f);
   else
-    launch(h, K_MG_OTHER, k_mgl_source<double>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+    launch(h, K_MG_OTHER, k_mgl_source<double>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.g0,
            (const double *)h->U, fourpiG, rb, T0.f);
-  launch(h, K_MG_OTHER, k_mgl_gather, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+  launch(h, K_MG_OTHER, k_mgl_gather, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.g0,
          (const double *)h->phil, T0.e);
   const unsigned nb = unsigned(std::min<int64_t>((n + 255) / 256, kMGParts));
   for (int c = 0; c < n_vcycles; ++c) {
-    mgl_vcycle(h, 0);
+    mgl_vcycle(h, S, 0);
     if (resid) {
-      mgl_residual(h, 0);
+      mgl_residual(h, S, 0);
       launch(h, K_MG_OTHER, k_mgl_sq, dim3(nb), dim3(256), n, (const double *)T0.r, h->mgl_part);
       launch(h, K_MG_OTHER, k_mgl_norm, dim3(1), dim3(32), (const double *)h->mgl_part, int(nb), h->mgl_scalar);
       CUDA_TRY(cudaMemcpyAsync(resid + c, h->mgl_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->s));
     }
   }
-  launch(h, K_MG_OTHER, k_mgl_scatter, dim3(nblocks(n)), dim3(256), n, (const int32_t *)h->mgl_g0,
+  launch(h, K_MG_OTHER, k_mgl_scatter, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.g0,
          (const double *)T0.e, h->phil);
   return AMR_OK;
 }
