@@ -81,6 +81,9 @@ def parse():
                     help="fused kernel: 0 cube staging (rock), 1 planar sweep (paper kernel), -1 default")
     ap.add_argument("--profile-poisson", type=int, default=0,
                     help="profiling mode: one multigrid V-cycle on a periodic 2^L grid, then exit")
+    ap.add_argument("--profile-unigrid", type=int, default=0,
+                    help="profiling mode: the blast on a uniform 2^L grid, one eager level step "
+                         "(one launch of each level-step kernel), then exit")
     ap.add_argument("--profile-level", type=int, default=0,
                     help="profiling mode: build the mesh and run one eager level step of this "
                          "level (one launch of each level-step kernel), then exit")
@@ -199,9 +202,10 @@ def kernel_traffic(info, levelmin, w, fused):
 
 # FP64 flops (2 per FMA) per real cell of the FP64 flux kernel (three HLLC
 # faces), and DRAM bytes per cell of the flux kernels, from one ncu capture
-# of the level-7 launch of the benchmark mesh (profiles/flux_sedov_level7.md)
+# of the level-7 launch of the benchmark mesh (ncu: FP64 instruction counts,
+# dram__bytes_read.sum + dram__bytes_write.sum)
 FLUX_FP64_FLOPS_PER_CELL = 325.5
-FLUX_DRAM_BYTES_PER_CELL = {8: 272.8, 4: 127.4}
+FLUX_DRAM_BYTES_PER_CELL = {8: 272.8, 4: 126.9}
 
 
 def load_peaks():
@@ -324,13 +328,10 @@ def run_variants(prob, steps, torch, device, flush):
     return out
 
 
-def run_unigrid(level, steps, torch, device):
-    """The blast on a uniform 2^level grid (one level, no refinement): the
-    Godunov level step alone (amr_step_level: primitives, predictor, HLLC
-    fluxes, update) and the whole coarse step (re-index, time step, level
-    step), median over `steps`, each precision.  The paper quotes its
-    unigrid Sedov rates this way (rock kernel, H200, FP32)."""
-    from paper_2607_20704_gb300 import amr, inputs
+def unigrid_problem(level):
+    """The blast on a uniform 2^level grid: unit density at rest, pressure
+    1e-5 outside a ball of radius 2 cells that holds unit energy."""
+    from paper_2607_20704_gb300 import inputs
     n = 1 << level
     r0 = 2.0 / n
 
@@ -339,7 +340,18 @@ def run_unigrid(level, steps, torch, device):
         p = np.where(r2 < r0 * r0, (5.0 / 3.0 - 1.0) / (4.0 / 3.0 * np.pi * r0 ** 3), 1e-5)
         zero = 0.0 * x
         return 1.0 + zero, zero, zero, zero, p
-    prob = inputs.uniform_grid(level, fn, gamma=5.0 / 3.0)
+    return inputs.uniform_grid(level, fn, gamma=5.0 / 3.0)
+
+
+def run_unigrid(level, steps, torch, device):
+    """The blast on a uniform 2^level grid (one level, no refinement): the
+    Godunov level step alone (amr_step_level: primitives, predictor, HLLC
+    fluxes, update) and the whole coarse step (re-index, time step, level
+    step), median over `steps`, each precision.  The paper quotes its
+    unigrid Sedov rates this way (rock kernel, H200, FP32)."""
+    from paper_2607_20704_gb300 import amr
+    n = 1 << level
+    prob = unigrid_problem(level)
     out = {"grid": f"{n}^3 cells, one level", "cells": n ** 3}
     for prec in (8, 4):
         m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=prec, stream=bench_stream())
@@ -997,8 +1009,22 @@ def main():
                           "precision": args.precision}))
         p.close()
         return 0
+    if args.profile_unigrid:
+        from paper_2607_20704_gb300 import amr, build
+        build.build()
+        amr.load()
+        L = args.profile_unigrid
+        up = unigrid_problem(L)
+        m = amr.Mesh(*up.mesh_args(), **up.params(), precision=args.precision, **LAUNCH)
+        m.step_level(L, m.cfl_dt() * 1e-3)
+        m.sync()
+        print(json.dumps({"profile_unigrid": L, "precision": args.precision, "cells": 8 * m.num_octs(L)}))
+        m.close()
+        return 0
     if args.profile_level:
-        from paper_2607_20704_gb300 import amr
+        from paper_2607_20704_gb300 import amr, build
+        build.build()
+        amr.load()
         m = amr.Mesh(*prob.mesh_args(), **prob.params(), precision=args.precision, **LAUNCH)
         dt = m.cfl_dt() * 0.5 ** (args.profile_level - prob.levelmin)
         m.step_level(args.profile_level, dt)
