@@ -71,23 +71,82 @@ __device__ __forceinline__ void load_cell(const T *U, int64_t S, int64_t g, doub
   for (int v = 0; v < 5; ++v) u[v] = double(U[v * S + g]);
 }
 
-// density and pressure of every real cell: rp[0][8N], rp[1][8N]
+// The jump tests are decided in FP32 wherever FP32 settles them, and in FP64
+// (the decision above, bit for bit) everywhere else.  Each cell gets FP32
+// images of its density and pressure and a bound on how far the FP32
+// pressure can lie from the FP64 one; a test whose FP32 value clears the
+// accumulated error bound by a factor 2 has the FP64 test's outcome, and a
+// test that does not is recomputed in FP64.  The result is the FP64
+// decision for every cell; GB300's FP64 rate (1/64 of FP32) made the plain
+// FP64 tests the regrid's largest kernel.
+//
+// Error model of the FP32 images (u = 2^-24, round to nearest): every state
+// component converts with relative error u; rho = max(rho, smallr) is
+// 1-Lipschitz, so it keeps error u rho; m.m/2/rho carries at most about
+// 6u of itself (conversions, squares, sum, approximate division); p =
+// (gamma-1)(E - ek) then errs by at most (gamma-1)(2u |E| + 7u ek) plus its
+// own roundings.  The bound stored is (gamma-1) 2^-17 (|E| + ek) (eight
+// times that), and 2^-21 p for the floor rho smallp (max is 1-Lipschitz).
+// A cell whose values leave [2^-60, 2^60] gets the bound +inf: its tests
+// always run in FP64.
 template <class T>
-__global__ void k_flag_rp(RegridArgs a, const T *__restrict__ U, double *__restrict__ rp) {
+__device__ __forceinline__ float to_f32(T x) {
+  return float(x);
+}
+template <>
+__device__ __forceinline__ float to_f32<double>(double x) {
+  return __double2float_rn(x);
+}
+
+__device__ __forceinline__ bool in_range32(float x) { return x >= 0x1p-60f && x <= 0x1p60f; }
+
+template <class T>
+__global__ void k_flag_rp(RegridArgs a, const T *__restrict__ U, float *__restrict__ rp) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (g >= 8 * int64_t(a.N)) return;
+  const int64_t N8 = 8 * int64_t(a.N);
+  if (g >= N8) return;
   const int m = ikey_member(a.key[g >> 3]);
-  double u[5], r, p;
-  load_cell(U, a.S, g, u);
-  flag_rho_p(u, a.mgamma[m], a.msmallr[m], a.msmallp[m], r, p);
+  float u[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = to_f32(U[v * a.S + g]);
+  const float gm1 = __double2float_rn(a.mgamma[m] - 1.0);
+  const float smallr = __double2float_rn(a.msmallr[m]), smallp = __double2float_rn(a.msmallp[m]);
+  const float r = fmaxf(u[0], smallr);
+  const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  const float ek = __fdividef(0.5f * m2, r);
+  const float pr = gm1 * (u[4] - ek);
+  const float pf = r * smallp;
+  const float p = fmaxf(pr, pf);
+  float e = fmaxf(gm1 * 0x1p-17f * (fabsf(u[4]) + ek), 0x1p-21f * pf);
+  const bool ok = in_range32(r) && in_range32(p) && in_range32(fabsf(u[4])) && ek <= 0x1p60f &&
+                  fabsf(u[1]) <= 0x1p60f && fabsf(u[2]) <= 0x1p60f && fabsf(u[3]) <= 0x1p60f &&
+                  gm1 >= 0x1p-30f && gm1 <= 0x1p30f;
+  if (!ok) e = INFINITY;
   rp[g] = r;
-  rp[8 * int64_t(a.N) + g] = p;
+  rp[N8 + g] = p;
+  rp[2 * N8 + g] = e;
+}
+
+// 1: the FP64 jump test 2|a-b| > thr (|a|+|b|) holds, 0: it does not, -1:
+// FP32 cannot tell.  a, b are FP32 images of positive values within ea, eb
+// of them; thr is the FP32 image of the threshold.  The FP32 evaluation errs
+// by at most (2 + thr)(ea + eb) + 2^-21 (1 + thr)(a + b) (conversions of the
+// threshold, the difference, the sum and the product, each within u of its
+// value); the FP64 test's own roundings are below 2^-50 of the sum.
+__device__ __forceinline__ int jump_exceeds32(float a, float b, float ea, float eb, float thr) {
+  const float s = a + b;
+  const float gt = 2.0f * fabsf(a - b) - thr * s;
+  const float bound = (2.0f + thr) * (ea + eb) + 0x1p-20f * (1.0f + thr) * s;
+  if (!(bound < INFINITY)) return -1;
+  if (gt > 2.0f * bound) return 1;
+  if (gt < -2.0f * bound) return 0;
+  return -1;
 }
 
 // criterion masks: one thread per real cell, the 8 cells of an oct in
 // consecutive lanes; a ballot assembles the oct's mask
 template <class T>
-__global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *__restrict__ rp) {
+__global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const float *__restrict__ rp) {
   const int64_t gc = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t N8 = 8 * int64_t(a.N);
   const bool in = gc < N8;
@@ -97,8 +156,15 @@ __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *
     const uint64_t key = a.key[o];
     const int m = ikey_member(key), l = ikey_lev(key);
     if (l < a.mlmax[m]) {
+      // the criteria's switches, decided once (FP64 compares use the slow pipe)
+      const bool test_r = a.grad_rho > 0.0, test_p = a.grad_p > 0.0;
       f = a.mass > 0.0 && ldexp(double(U[gc]), -3 * l) > a.mass;
-      const double rc = rp[gc], pc = rp[N8 + gc];
+      const float thr_r = __double2float_rn(a.grad_rho), thr_p = __double2float_rn(a.grad_p);
+      const bool use32 = (!test_r || (thr_r >= 0x1p-60f && thr_r <= 0x1p60f)) &&
+                         (!test_p || (thr_p >= 0x1p-60f && thr_p <= 0x1p60f));
+      const float rc = rp[gc], pc = rp[N8 + gc], ec = rp[2 * N8 + gc];
+      double rc64 = 0.0, pc64 = 0.0;
+      bool have64 = false;
       for (int d = 0; d < 3 && !f; ++d)
         for (int plus = 0; plus < 2 && !f; ++plus) {
           // face neighbour: same oct, a real oct, or a ghost oct whose
@@ -113,8 +179,30 @@ __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *
             gn = ne < a.N ? 8 * int64_t(ne) + (c ^ bit)
                           : checked(a.csrc[checked(ne - a.N, 0, a.NC, a.err)], 0, N8, a.err);
           }
-          if (a.grad_rho > 0.0 && jump_exceeds(rp[gn], rc, a.grad_rho)) f = true;
-          if (a.grad_p > 0.0 && jump_exceeds(rp[N8 + gn], pc, a.grad_p)) f = true;
+          const float en = rp[2 * N8 + gn];
+          int dr = test_r ? -1 : 0, dp = test_p ? -1 : 0;
+          if (use32) {
+            if (dr) dr = jump_exceeds32(rp[gn], rc, 0x1p-23f * rp[gn], 0x1p-23f * rc, thr_r);
+            if (dp && dr != 1) dp = jump_exceeds32(rp[N8 + gn], pc, en, ec, thr_p);
+          }
+          if (dr == 1 || dp == 1) {
+            f = true;
+            continue;
+          }
+          if (dr == 0 && dp == 0) continue;
+          // undecided in FP32: the FP64 test on the FP64 density and pressure
+          if (!have64) {
+            double u[5];
+            load_cell(U, a.S, gc, u);
+            flag_rho_p(u, a.mgamma[m], a.msmallr[m], a.msmallp[m], rc64, pc64);
+            have64 = true;
+          }
+          double u[5], rn64, pn64;
+          load_cell(U, a.S, gn, u);
+          const int mn = ikey_member(a.key[gn >> 3]);
+          flag_rho_p(u, a.mgamma[mn], a.msmallr[mn], a.msmallp[mn], rn64, pn64);
+          if (dr && jump_exceeds(rn64, rc64, a.grad_rho)) f = true;
+          if (dp && jump_exceeds(pn64, pc64, a.grad_p)) f = true;
         }
     }
   }
@@ -122,36 +210,52 @@ __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const double *
   if (in && c == 0) a.raw[o] = (b >> (threadIdx.x & 24)) & 0xFFu;
 }
 
-// expansion over the 3x3x3 same-level block (or a copy when expand = 0);
-// one thread per real cell, masks assembled by a ballot
+// expansion over the 3x3x3 same-level block (or a copy when expand = 0); one
+// thread per oct: the criterion masks of the 27 octs around it fill a 4^3
+// cube of cells (the oct's 2^3 cells and one layer around them, bit
+// (z+1)*16 + (y+1)*4 + (x+1) for cell offset x, y, z in [-1, 2]), and cell c
+// is flagged when any bit of its 3^3 window is set.  A neighbour that is a
+// ghost oct or missing holds no real cell of this level and adds nothing.
 __global__ void k_flag_expand(RegridArgs a) {
-  const int64_t gc = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const bool in = gc < 8 * int64_t(a.N);
-  const int o = int(gc >> 3), c = int(gc & 7);
-  bool f = false;
-  if (in) {
-    const uint64_t key = a.key[o];
-    const int m = ikey_member(key), l = ikey_lev(key);
-    if (l < a.mlmax[m]) {
-      if (!a.expand) {
-        f = (a.raw[o] >> c) & 1u;
-      } else {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= a.N) return;
+  const uint64_t key = a.key[o];
+  const int m = ikey_member(key), l = ikey_lev(key);
+  uint32_t out = 0;
+  if (l < a.mlmax[m]) {
+    if (!a.expand) {
+      out = a.raw[o];
+    } else {
+      uint64_t cube = 0;
+#pragma unroll
+      for (int k = 0; k < 27; ++k) {
+        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = k / 9 - 1;
+        const int32_t e = a.nbr27[k * int64_t(a.N) + o];
+        if (e < 0 || e >= a.N) continue;
+        const uint32_t r = a.raw[e];
+        if (!r) continue;
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          const int fx = 2 * ox + (cc & 1), fy = 2 * oy + ((cc >> 1) & 1), fz = 2 * oz + ((cc >> 2) & 1);
+          if (fx < -1 || fx > 2 || fy < -1 || fy > 2 || fz < -1 || fz > 2) continue;
+          cube |= uint64_t((r >> cc) & 1u) << ((fz + 1) * 16 + (fy + 1) * 4 + (fx + 1));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-        for (int dz = -1; dz <= 1 && !f; ++dz)
-          for (int dy = -1; dy <= 1 && !f; ++dy)
-            for (int dx = -1; dx <= 1 && !f; ++dx) {
-              const int fx = cx + dx, fy = cy + dy, fz = cz + dz;  // -1..2
-              const int ox = fx >> 1, oy = fy >> 1, oz = fz >> 1;  // arithmetic shift: -1..1
-              const int32_t e = a.nbr27[((oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)) * int64_t(a.N) + o];
-              if (e < 0 || e >= a.N) continue;  // a ghost: no real cell of this level there
-              const int cc = (fx & 1) | ((fy & 1) << 1) | ((fz & 1) << 2);
-              if ((a.raw[e] >> cc) & 1u) f = true;
-            }
+        uint64_t w = 0;
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) w |= uint64_t(1) << ((cz + dz) * 16 + (cy + dy) * 4 + (cx + dx));
+        if (cube & w) out |= 1u << c;
       }
     }
   }
-  const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
-  if (in && c == 0) a.flag[o] = (b >> (threadIdx.x & 24)) & 0xFFu;
+  a.flag[o] = out;
 }
 
 // grading closure from the octs [lo, hi) of one level l > levelmin: every
