@@ -882,7 +882,7 @@ def fp64_peak_derived(sm_mhz):
 
 
 def roofline(res, prec, levelmin, peak_gbs, peak_src, fp64_tflops=None, dgemm=None,
-             sm_mhz=None):
+             sm_mhz=None, fma64=None):
     """Roofline object of the dominant kernel: achieved = its algorithmic
     bytes (FP32) or FP64 flops (FP64: the flux kernel is bound by the FP64
     pipe) per launch / its average CUDA-event launch time."""
@@ -920,6 +920,8 @@ def roofline(res, prec, levelmin, peak_gbs, peak_src, fp64_tflops=None, dgemm=No
                              f"x {sm_mhz:.0f} MHz (median SM clock under load)",
               "flops_per_launch": int(flops), "avg_launch_us": round(avg_s * 1e6, 3),
               "dgemm_tflops": dgemm, "frac_of_dgemm": round(ach / dgemm, 4) if dgemm else None,
+              "fma_microbench_tflops": fma64,
+              "frac_of_fma_microbench": round(ach / fma64, 4) if fma64 else None,
               "hbm_view": hbm}
     else:
         rl = dict(hbm)
@@ -1084,13 +1086,20 @@ def main():
         dgemm = round(fp64_peak(torch, device), 4)
     except Exception:
         dgemm = None
+    try:  # the FMA rates of this GPU from the library's own microbenchmark
+        fma = {"fp64_tflops": round(amr.fma_rate(local, 8) / 1e12, 4),
+               "fp32_tflops": round(amr.fma_rate(local, 4) / 1e12, 3)}
+    except Exception:
+        fma = None
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_pk = fp64_peak_derived(sm_mhz)
     cic_alu_peak(cic, sm_mhz)
-    rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src, fp64_pk, dgemm, sm_mhz)
+    fma64 = fma["fp64_tflops"] if fma else None
+    rl, table = roofline(main_res, prec_main, prob.levelmin, peak_gbs, peak_src, fp64_pk, dgemm, sm_mhz,
+                         fma64)
     if other is not None:
         rl_o, table_o = roofline(other, prec_other, prob.levelmin, peak_gbs, peak_src, fp64_pk,
-                                 dgemm, sm_mhz)
+                                 dgemm, sm_mhz, fma64)
     step_bytes = 2 * 5 * WORD[prec_main]
     line = {
         "metric": "leaf cell-updates/s",
@@ -1143,6 +1152,7 @@ def main():
     if serving is not None:
         line["serving"] = serving
     line["fp64_dgemm_tflops"] = dgemm
+    line["fma_microbench"] = fma
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_steps, args.cpu_all_core_steps)
     if world > 1:

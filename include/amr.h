@@ -548,6 +548,17 @@ amr_status amr_read_timing(amr_handle h, int n, double *ms, int64_t *launches);
 const char *amr_kernel_name(int t);
 
 /*
+ * amr_fma_rate -- the FMA throughput of GPU `device` in the given precision
+ * (8: FP64, 4: FP32), measured by a kernel of independent FMA chains (8 per
+ * thread, 8 blocks of 256 threads per SM) timed with CUDA events on a
+ * private stream, best of three launches after a warm-up: *flops = 2 x FMAs
+ * per second.  The denominator of the arithmetic-bound rooflines, beside
+ * the rate derived from the unit counts and the clock.  Synchronous; uses no
+ * handle.  Errors: AMR_EINVAL (precision), AMR_ECUDA.
+ */
+amr_status amr_fma_rate(int device, int precision, double *flops);
+
+/*
  * amr_cfl_dt_static -- the CFL time step of one level of leaf cells held in
  * caller device memory, with no device allocation at all.  It computes the
  * quantity amr_cfl_dt reduces for that level, dt_l = cfl dx_l / max sum_d

@@ -102,7 +102,7 @@ SYMBOLS = ["amr_params_default", "amr_create", "amr_destroy", "amr_cfl_dt", "amr
            "amr_regrid_flags", "amr_totals", "amr_hash", "amr_read_hash", "amr_batch_repack",
            "amr_cic_deposit_levels", "amr_cic_deposit_levels_device", "amr_read_particle_rho",
            "amr_poisson", "amr_read_phi", "amr_poisson_level", "amr_poisson_levels", "amr_write_phi",
-           "amr_read_phi_level", "amr_load_state_async", "amr_store_state_async",
+           "amr_read_phi_level", "amr_fma_rate", "amr_load_state_async", "amr_store_state_async",
            "amr_server_create", "amr_server_submit",
            "amr_server_wait", "amr_server_read", "amr_server_release", "amr_server_get_stats",
            "amr_server_destroy"]
@@ -187,6 +187,7 @@ def load(path: str | None = None):
             "amr_poisson_levels": (I, [P, D, I, P]),
             "amr_write_phi": (I, [P, I, P, I64]),
             "amr_read_phi_level": (I, [P, I, P, I64]),
+            "amr_fma_rate": (I, [I, I, C.POINTER(D)]),
             "amr_server_create": (I, [C.POINTER(amr_server_params), C.POINTER(P)]),
             "amr_server_submit": (I, [P, C.POINTER(amr_request), C.POINTER(I64)]),
             "amr_server_wait": (I, [P, I64, D, C.POINTER(I)]),
@@ -290,6 +291,13 @@ def _member_array(members):
         m.level, m.i, m.j, m.k, m.U = (_ptr(lv), _ptr(ii), _ptr(jj), _ptr(kk), _ptr(uu))
         m.hilbert_key = _ptr(hk) if hk is not None else None
     return arr, keep
+
+
+def fma_rate(device: int = 0, precision: int = 8) -> float:
+    """FMA throughput of the GPU in FLOP/s (2 per FMA), FP64 or FP32."""
+    out = C.c_double()
+    _check(load().amr_fma_rate(int(device), int(precision), C.byref(out)), "amr_fma_rate")
+    return out.value
 
 
 class Mesh:

@@ -171,6 +171,7 @@ struct amr_mesh {
   int *mlmin = nullptr, *mlmax = nullptr;
   double *mgamma_d = nullptr, *mcfl_d = nullptr, *msmallr_d = nullptr, *msmallp_d = nullptr;
   void *mgamma_t = nullptr, *migm1_t = nullptr, *msmallr_t = nullptr, *msmallp_t = nullptr;
+  float *mflag32 = nullptr;  // per member: gamma - 1, smallr, smallp rounded to FP32 (regrid screen)
   double *dt_dev = nullptr, *dtdx_dev = nullptr;
   float *dtdxf_dev = nullptr;
   int *mrem = nullptr, *mact = nullptr;  // coarse steps left; active this step
@@ -253,6 +254,10 @@ struct amr_mesh {
   int64_t pcap = 0;
   void *prho = nullptr;
   int64_t prho_n = 0;
+  // oct index of every base-level oct of one member by its coordinates
+  // ((x * side + y) * side + z): the complete base level needs no hash probe
+  int32_t *btab = nullptr;
+  int btab_member = -1;
 
   // work accounting
   int64_t launches = 0, graph_launches = 0;
@@ -988,8 +993,43 @@ static amr_status upload_members(amr_mesh *h) {
   AMR_TRY(upload(h, &h->mcfl_d, cfl));
   AMR_TRY(upload(h, &h->msmallr_d, sr));
   AMR_TRY(upload(h, &h->msmallp_d, sp));
+  std::vector<float> f32(3 * size_t(M));
+  for (int q = 0; q < M; ++q) {
+    f32[3 * size_t(q)] = float(g[q] - 1.0);
+    f32[3 * size_t(q) + 1] = float(sr[q]);
+    f32[3 * size_t(q) + 2] = float(sp[q]);
+  }
+  AMR_TRY(upload(h, &h->mflag32, f32));
   if (h->p.precision == 4) return upload_member_params<float>(h);
   return upload_member_params<double>(h);
+}
+
+template <class P>
+static amr_status dup_n(amr_mesh *nh, P **dst, const P *src, int64_t n) {
+  AMR_TRY(alloc_n(nh, dst, n));
+  CUDA_TRY(cudaMemcpyAsync(*dst, src, sizeof(P) * size_t(n), cudaMemcpyDeviceToDevice, nh->s));
+  return AMR_OK;
+}
+
+// the member arrays of a new handle with the same members as h (a regrid):
+// device-to-device copies on the shared stream, no host round trip
+static amr_status clone_members(amr_mesh *nh, const amr_mesh *h) {
+  const int64_t M = h->M;
+  AMR_TRY(dup_n(nh, &nh->mlmin, (const int *)h->mlmin, M));
+  AMR_TRY(dup_n(nh, &nh->mlmax, (const int *)h->mlmax, M));
+  AMR_TRY(dup_n(nh, &nh->mgamma_d, (const double *)h->mgamma_d, M));
+  AMR_TRY(dup_n(nh, &nh->mcfl_d, (const double *)h->mcfl_d, M));
+  AMR_TRY(dup_n(nh, &nh->msmallr_d, (const double *)h->msmallr_d, M));
+  AMR_TRY(dup_n(nh, &nh->msmallp_d, (const double *)h->msmallp_d, M));
+  AMR_TRY(dup_n(nh, &nh->mflag32, (const float *)h->mflag32, 3 * M));
+  const size_t bytes = h->elem() * size_t(M);
+  void **dst[4] = {&nh->mgamma_t, &nh->migm1_t, &nh->msmallr_t, &nh->msmallp_t};
+  const void *src[4] = {h->mgamma_t, h->migm1_t, h->msmallr_t, h->msmallp_t};
+  for (int t = 0; t < 4; ++t) {
+    AMR_TRY(dev_alloc(nh, dst[t], bytes));
+    CUDA_TRY(cudaMemcpyAsync(*dst[t], src[t], bytes, cudaMemcpyDeviceToDevice, nh->s));
+  }
+  return AMR_OK;
 }
 
 static amr_status build_blocks(amr_mesh *h);
@@ -1808,6 +1848,14 @@ static RegridArgs regrid_args(amr_mesh *h, uint32_t *raw, uint32_t *flag) {
   a.grad_p = h->p.refine_grad_p;
   a.mass = h->p.refine_mass;
   a.expand = h->p.regrid_expand ? 1 : 0;
+  a.test_r = a.grad_rho > 0.0;
+  a.test_p = a.grad_p > 0.0;
+  a.test_mass = a.mass > 0.0;
+  a.thr_r32 = float(a.grad_rho);
+  a.thr_p32 = float(a.grad_p);
+  auto thr_ok = [](float t) { return t >= 0x1p-60f && t <= 0x1p60f; };
+  a.use32 = (!a.test_r || thr_ok(a.thr_r32)) && (!a.test_p || thr_ok(a.thr_p32));
+  a.mflag32 = h->mflag32;
   a.raw = raw;
   a.flag = flag;
   a.err = h->err;
@@ -1985,7 +2033,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
     g_last_error = msg;
     return se != AMR_OK ? se : e;
   };
-  if ((st = upload_members(nh)) != AMR_OK || (st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
+  if ((st = clone_members(nh, h)) != AMR_OK || (st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_new, n_out)) != AMR_OK || (st = alloc_n(nh, &d_mem, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_i, n_out)) != AMR_OK || (st = alloc_n(nh, &d_j, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_k, n_out)) != AMR_OK || (st = alloc_n(nh, &d_U, 40 * n_out)) != AMR_OK)
@@ -2425,17 +2473,12 @@ static amr_status poisson_level(amr_mesh *h, int L, double fourpiG, double rho_b
   const int64_t n = T0.n;
   launch(h, K_MG_OTHER, k_mgl_bsum, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.fatherg,
          (const int32_t *)S.acrossg, (const double *)h->phil, S.bsum);
-  double rb = rho_bar;
-  if (rho_bar_dev) {
-    CUDA_TRY(cudaMemcpyAsync(&rb, rho_bar_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    CUDA_TRY(cudaStreamSynchronize(h->s));
-  }
   if (h->p.precision == 4)
     launch(h, K_MG_OTHER, k_mgl_source<float>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.g0,
-           (const float *)h->U, fourpiG, rb, T0.f);
+           (const float *)h->U, fourpiG, rho_bar, rho_bar_dev, T0.f);
   else
     launch(h, K_MG_OTHER, k_mgl_source<double>, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.g0,
-           (const double *)h->U, fourpiG, rb, T0.f);
+           (const double *)h->U, fourpiG, rho_bar, rho_bar_dev, T0.f);
   launch(h, K_MG_OTHER, k_mgl_gather, dim3(nblocks(n)), dim3(256), n, (const int32_t *)S.g0,
          (const double *)h->phil, T0.e);
   const unsigned nb = unsigned(std::min<int64_t>((n + 255) / 256, kMGParts));
@@ -2829,6 +2872,22 @@ static amr_status ensure_particles(amr_mesh *h, int64_t np, bool positions) {
   return AMR_OK;
 }
 
+// the base-level table of the selected member (kept until the mesh changes:
+// a regrid or repack builds a new handle)
+static amr_status ensure_base_table(amr_mesh *h) {
+  const Member &mb = h->mem[h->sel];
+  if (h->btab && h->btab_member == h->sel) return AMR_OK;
+  dev_free(h, h->btab);
+  h->btab = nullptr;
+  const int64_t side = int64_t(1) << (mb.lmin - 1), nb = side * side * side;
+  AMR_TRY(alloc_n(h, &h->btab, nb));
+  const int lo = int(mb.oct_base + mb.lo[mb.lmin]);
+  launch(h, K_DEPOSIT, k_base_table, dim3(nblocks(nb)), dim3(256), (const uint64_t *)h->key, lo, nb,
+         mb.lmin, h->btab);
+  h->btab_member = h->sel;
+  return AMR_OK;
+}
+
 template <class T>
 static void deposit_levels(amr_mesh *h, int64_t np, const T *x, const T *y, const T *z, const T *m) {
   const Member &mb = h->mem[h->sel];
@@ -2838,15 +2897,24 @@ static void deposit_levels(amr_mesh *h, int64_t np, const T *x, const T *y, cons
   cnt[size_t(mb.lmin)] = np;
   cudaMemcpyAsync(h->pcount, cnt.data(), sizeof(int64_t) * cnt.size(), cudaMemcpyHostToDevice, h->s);
   if (np == 0) return;
-  launch(h, K_DEPOSIT, k_iota_u32, dim3(nblocks(np)), dim3(256), h->plist0, np);
   uint32_t *cur = h->plist0, *nxt = h->plist1;
   for (int l = mb.lmin; l <= mb.lmax; ++l) {
-    launch(h, K_DEPOSIT, k_deposit_level<T>, dim3(nblocks(np)), dim3(256), h->hash, h->sel, l, N, x, y,
-           z, m, (const uint32_t *)cur, (const int64_t *)h->pcount, static_cast<T *>(h->prho));
+    if (l == mb.lmin)  // every particle, every stencil cell exists: the base table
+      launch(h, K_DEPOSIT, k_deposit_base<T>, dim3(nblocks(np)), dim3(256), (const int32_t *)h->btab, l, np,
+             x, y, z, m, static_cast<T *>(h->prho));
+    else
+      launch(h, K_DEPOSIT, k_deposit_level<T>, dim3(nblocks(np)), dim3(256), h->hash, h->sel, l, N, x, y,
+             z, m, (const uint32_t *)cur, (const int64_t *)h->pcount, static_cast<T *>(h->prho));
     if (l == mb.lmax) break;
-    launch(h, K_SPLIT, k_split_level<T>, dim3(nblocks(np)), dim3(256), h->hash, h->sel, l, N,
-           (const uint32_t *)h->son, x, y, z, (const uint32_t *)cur, (const int64_t *)h->pcount, np,
-           h->pflag);
+    if (l == mb.lmin) {
+      launch(h, K_SPLIT, k_split_base<T>, dim3(nblocks(np)), dim3(256), (const int32_t *)h->btab, l,
+             (const uint32_t *)h->son, x, y, z, np, h->pflag);
+      launch(h, K_DEPOSIT, k_iota_u32, dim3(nblocks(np)), dim3(256), cur, np);
+    } else {
+      launch(h, K_SPLIT, k_split_level<T>, dim3(nblocks(np)), dim3(256), h->hash, h->sel, l, N,
+             (const uint32_t *)h->son, x, y, z, (const uint32_t *)cur, (const int64_t *)h->pcount, np,
+             h->pflag);
+    }
     cudaMemcpyAsync(h->ppos, h->pflag, 4 * size_t(np), cudaMemcpyDeviceToDevice, h->s);
     scan_exclusive(h, h->ppos, np, h->ptmp);
     launch(h, K_SPLIT, k_compact_level, dim3(nblocks(np)), dim3(256), (const uint32_t *)cur,
@@ -2871,6 +2939,7 @@ extern "C" amr_status amr_cic_deposit_levels_device(amr_handle h, int64_t np, co
   if (np < 0 || np >= (int64_t(1) << 32)) return fail(AMR_EINVAL, "amr_cic_deposit_levels_device: np outside [0, 2^32)");
   if (np > 0 && (!x || !y || !z || !m)) return fail(AMR_EINVAL, "amr_cic_deposit_levels_device: NULL array");
   AMR_TRY(ensure_particles(h, np, false));
+  AMR_TRY(ensure_base_table(h));
   if (h->p.precision == 4)
     deposit_levels<float>(h, np, (const float *)x, (const float *)y, (const float *)z, (const float *)m);
   else
@@ -2904,6 +2973,7 @@ extern "C" amr_status amr_cic_deposit_levels(amr_handle h, int64_t np, const dou
       return fail(AMR_EINVAL, "amr_cic_deposit_levels: particle %lld outside [0, 1)^3 or with a non-finite mass",
                   (long long)t);
   AMR_TRY(ensure_particles(h, np, true));
+  AMR_TRY(ensure_base_table(h));
   if (np > 0) {
     if (h->p.precision == 4)
       AMR_TRY(stage_particles<float>(h, np, x, y, z, m));
@@ -3143,4 +3213,64 @@ extern "C" amr_status amr_read_timing(amr_handle h, int n, double *ms, int64_t *
     if (launches) launches[t] = h->kernel_n[t];
   }
   return AMR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FMA rate of this GPU (the denominator of the arithmetic-bound rooflines)
+// ---------------------------------------------------------------------------
+// Every thread runs 8 independent chains of a <- a x + y for `iters` steps
+// (enough independent work per warp to hide the pipe latency); x and y come
+// from the arguments, so nothing folds.  One thread writes the sum.
+template <class T>
+__global__ void k_fma_chains(T x, T y, int iters, T *out) {
+  T a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = T(threadIdx.x + q);
+  for (int t = 0; t < iters; ++t)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = fma(a[q], x, y);
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += a[q];
+  if (s == T(-1.2345)) *out = s;  // never true for these inputs; keeps the chains
+}
+
+template <class T>
+static amr_status fma_rate(int device, int iters, double *flops) {
+  CUDA_TRY(cudaSetDevice(device));
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  cudaStream_t s;
+  CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  T *out = nullptr;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaMallocAsync(&out, sizeof(T), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const dim3 grid(unsigned(8 * sms)), block(256);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, s);
+    k_fma_chains<T><<<grid, block, 0, s>>>(T(0.999999), T(1e-7), iters, out);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;  // the first launch warms up
+  }
+  cudaFreeAsync(out, s);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return fail(AMR_ECUDA, "amr_fma_rate: %s", cudaGetErrorString(e));
+  *flops = 2.0 * 8.0 * double(iters) * double(grid.x) * double(block.x) / (double(best) * 1e-3);
+  return AMR_OK;
+}
+
+extern "C" amr_status amr_fma_rate(int device, int precision, double *flops) {
+  if (!flops) return fail(AMR_EINVAL, "amr_fma_rate: NULL argument");
+  if (precision == 8) return fma_rate<double>(device, 2048, flops);
+  if (precision == 4) return fma_rate<float>(device, 65536, flops);
+  return fail(AMR_EINVAL, "amr_fma_rate: precision must be 4 or 8");
 }

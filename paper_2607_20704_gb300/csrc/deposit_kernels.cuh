@@ -52,6 +52,70 @@ __global__ void k_deposit_level(HashView hv, int member, int l, int N, const T *
   }
 }
 
+// the base level is complete: a table from oct coordinates to oct index
+// replaces the hash probes there
+__global__ void k_base_table(const uint64_t *__restrict__ key, int lo, int64_t nb, int lmin, int32_t *btab) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nb) return;
+  const int o = lo + int(t);
+  const uint64_t k = key[o];
+  const int64_t side = int64_t(1) << (lmin - 1);
+  btab[(int64_t(ikey_x(k)) * side + ikey_y(k)) * side + ikey_z(k)] = o;
+}
+
+// deposit of every particle at the base level l (the list of the base level
+// holds all particles; every stencil cell exists): the arithmetic of
+// k_deposit_level, the oct found in the base table
+template <class T>
+__global__ void k_deposit_base(const int32_t *__restrict__ btab, int l, int64_t np, const T *__restrict__ px,
+                               const T *__restrict__ py, const T *__restrict__ pz, const T *__restrict__ pm,
+                               T *rho) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p >= np) return;
+  const T n = T(int64_t(1) << l);
+  const uint32_t mask = uint32_t((int64_t(1) << l) - 1);
+  const int64_t side = int64_t(1) << (l - 1);
+  int64_t i0[3];
+  T w[3][2];
+  const T pos[3] = {px[p], py[p], pz[p]};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T s = pos[d] * n - T(0.5);
+    const T fl = floor(s);
+    const T f = s - fl;
+    i0[d] = int64_t(fl);
+    w[d][0] = T(1) - f;
+    w[d][1] = f;
+  }
+  const T mm = pm[p];
+  const T scale = T(ldexp(1.0, 3 * l));  // 1 / dx^3, exact
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+    const uint32_t X = uint32_t(i0[0] + cx) & mask, Y = uint32_t(i0[1] + cy) & mask,
+                   Z = uint32_t(i0[2] + cz) & mask;
+    const int32_t o = __ldg(btab + (int64_t(X >> 1) * side + (Y >> 1)) * side + (Z >> 1));
+    const int cc = int((X & 1) + 2 * (Y & 1) + 4 * (Z & 1));
+    atomicAdd(rho + 8 * int64_t(o) + cc, (mm * ((w[0][cx] * w[1][cy]) * w[2][cz])) * scale);
+  }
+}
+
+// flag[p] = 1 if particle p's host cell at the base level is split
+template <class T>
+__global__ void k_split_base(const int32_t *__restrict__ btab, int l, const uint32_t *__restrict__ son,
+                             const T *__restrict__ px, const T *__restrict__ py, const T *__restrict__ pz,
+                             int64_t np, uint32_t *flag) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p >= np) return;
+  const T n = T(int64_t(1) << l);
+  const uint32_t mask = uint32_t((int64_t(1) << l) - 1);
+  const int64_t side = int64_t(1) << (l - 1);
+  const uint32_t X = uint32_t(int64_t(floor(px[p] * n))) & mask, Y = uint32_t(int64_t(floor(py[p] * n))) & mask,
+                 Z = uint32_t(int64_t(floor(pz[p] * n))) & mask;
+  const int32_t o = __ldg(btab + (int64_t(X >> 1) * side + (Y >> 1)) * side + (Z >> 1));
+  flag[p] = (__ldg(son + o) >> ((X & 1) + 2 * (Y & 1) + 4 * (Z & 1))) & 1u;
+}
+
 // flag[t] = 1 if particle list[t]'s host cell at level l exists and is split;
 // 0 past the end of the list (the prefix sum runs over the list's capacity)
 template <class T>

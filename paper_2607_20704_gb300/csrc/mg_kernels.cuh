@@ -202,12 +202,15 @@ __global__ void k_mgl_bsum(int64_t n, const int32_t *__restrict__ fatherg, const
   bsum[t] = bs;
 }
 
+// source fourpiG (rho - rho_bar); rho_bar from the device when rho_bar_dev is
+// set (the base level's mean, without a host round trip)
 template <class T>
 __global__ void k_mgl_source(int64_t n, const int32_t *__restrict__ g0, const T *__restrict__ rho, double fourpiG,
-                             double rho_bar, double *__restrict__ f) {
+                             double rho_bar, const double *__restrict__ rho_bar_dev, double *__restrict__ f) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= n) return;
-  f[t] = __dmul_rn(fourpiG, __dsub_rn(double(rho[g0[t]]), rho_bar));
+  const double rb = rho_bar_dev ? *rho_bar_dev : rho_bar;
+  f[t] = __dmul_rn(fourpiG, __dsub_rn(double(rho[g0[t]]), rb));
 }
 
 __global__ void k_mgl_gather(int64_t n, const int32_t *__restrict__ g0, const double *__restrict__ phil,

@@ -38,6 +38,11 @@ struct RegridArgs {
   const double *mgamma, *msmallr, *msmallp;
   double grad_rho, grad_p, mass;
   int expand;
+  // the criteria's switches and FP32 thresholds, decided on the host
+  // (conversions and FP64 compares run on GB300's slow FP64 pipe)
+  int test_r, test_p, test_mass, use32;
+  float thr_r32, thr_p32;
+  const float *mflag32;  // [3 M]: gamma - 1, smallr, smallp in FP32
   uint32_t *raw;   // [N] criterion masks
   uint32_t *flag;  // [N] final masks
   int *err;
@@ -80,22 +85,32 @@ __device__ __forceinline__ void load_cell(const T *U, int64_t S, int64_t g, doub
 // decision for every cell; GB300's FP64 rate (1/64 of FP32) made the plain
 // FP64 tests the regrid's largest kernel.
 //
-// Error model of the FP32 images (u = 2^-24, round to nearest): every state
-// component converts with relative error u; rho = max(rho, smallr) is
-// 1-Lipschitz, so it keeps error u rho; m.m/2/rho carries at most about
-// 6u of itself (conversions, squares, sum, approximate division); p =
-// (gamma-1)(E - ek) then errs by at most (gamma-1)(2u |E| + 7u ek) plus its
-// own roundings.  The bound stored is (gamma-1) 2^-17 (|E| + ek) (eight
-// times that), and 2^-21 p for the floor rho smallp (max is 1-Lipschitz).
-// A cell whose values leave [2^-60, 2^60] gets the bound +inf: its tests
-// always run in FP64.
+// Error model of the FP32 images (u = 2^-24): every state component
+// converts with relative error below 2u (truncation; exact for an FP32
+// state), the parameters with u; rho = max(rho, smallr) is 1-Lipschitz, so
+// it keeps error 2u rho (the tests allow 8u); m.m/2/rho carries at most
+// about 10u of itself (conversions, squares, sum, approximate division); p =
+// (gamma-1)(E - ek) then errs by at most (gamma-1)(3u |E| + 11u ek) plus its
+// own roundings.  The bound stored is (gamma-1) 2^-17 (|E| + ek) (128u:
+// about ten times that), and 2^-21 p for the floor rho smallp (max is
+// 1-Lipschitz).  A cell whose values leave [2^-60, 2^60] gets the bound
+// +inf: its tests always run in FP64.
+// FP32 image of a state component: exact for an FP32 state; for FP64 the
+// bits are truncated on the integer pipes (relative error below 2^-23, no
+// conversion instruction: those run on the FP64 pipe), magnitudes below
+// 2^-126 give 0 and above 2^128 infinity
 template <class T>
 __device__ __forceinline__ float to_f32(T x) {
   return float(x);
 }
 template <>
 __device__ __forceinline__ float to_f32<double>(double x) {
-  return __double2float_rn(x);
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  const uint32_t sign = uint32_t(b >> 32) & 0x80000000u;
+  const int e = int((b >> 52) & 0x7FF);
+  if (e < 1023 - 126) return __uint_as_float(sign);
+  if (e > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | (uint32_t(e - 896) << 23) | uint32_t((b >> 29) & 0x7FFFFFu));
 }
 
 __device__ __forceinline__ bool in_range32(float x) { return x >= 0x1p-60f && x <= 0x1p60f; }
@@ -109,8 +124,7 @@ __global__ void k_flag_rp(RegridArgs a, const T *__restrict__ U, float *__restri
   float u[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) u[v] = to_f32(U[v * a.S + g]);
-  const float gm1 = __double2float_rn(a.mgamma[m] - 1.0);
-  const float smallr = __double2float_rn(a.msmallr[m]), smallp = __double2float_rn(a.msmallp[m]);
+  const float gm1 = a.mflag32[3 * m], smallr = a.mflag32[3 * m + 1], smallp = a.mflag32[3 * m + 2];
   const float r = fmaxf(u[0], smallr);
   const float m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   const float ek = __fdividef(0.5f * m2, r);
@@ -156,54 +170,63 @@ __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const float *_
     const uint64_t key = a.key[o];
     const int m = ikey_member(key), l = ikey_lev(key);
     if (l < a.mlmax[m]) {
-      // the criteria's switches, decided once (FP64 compares use the slow pipe)
-      const bool test_r = a.grad_rho > 0.0, test_p = a.grad_p > 0.0;
-      f = a.mass > 0.0 && ldexp(double(U[gc]), -3 * l) > a.mass;
-      const float thr_r = __double2float_rn(a.grad_rho), thr_p = __double2float_rn(a.grad_p);
-      const bool use32 = (!test_r || (thr_r >= 0x1p-60f && thr_r <= 0x1p60f)) &&
-                         (!test_p || (thr_p >= 0x1p-60f && thr_p <= 0x1p60f));
+      const bool test_r = a.test_r, test_p = a.test_p, use32 = a.use32;
+      const float thr_r = a.thr_r32, thr_p = a.thr_p32;
+      f = a.test_mass && ldexp(double(U[gc]), -3 * l) > a.mass;
       const float rc = rp[gc], pc = rp[N8 + gc], ec = rp[2 * N8 + gc];
+      // the six face neighbours (same oct, a real oct, or the covering
+      // coarser cell of a ghost oct), then their FP32 images, all loads
+      // issued before the tests
+      int64_t gnb[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int d = k >> 1, plus = k & 1, bit = 1 << d;
+        if (((c >> d) & 1) != plus) {
+          gnb[k] = 8 * int64_t(o) + (c ^ bit);
+        } else {
+          const int32_t ne = a.fnb[k * int64_t(a.NE) + o];
+          gnb[k] = ne < 0 ? -1
+                          : (ne < a.N ? 8 * int64_t(ne) + (c ^ bit)
+                                      : checked(a.csrc[checked(ne - a.N, 0, a.NC, a.err)], 0, N8, a.err));
+        }
+      }
+      float rn[6], pn[6], en[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int64_t q = gnb[k] < 0 ? gc : gnb[k];
+        rn[k] = rp[q];
+        pn[k] = rp[N8 + q];
+        en[k] = rp[2 * N8 + q];
+      }
       double rc64 = 0.0, pc64 = 0.0;
       bool have64 = false;
-      for (int d = 0; d < 3 && !f; ++d)
-        for (int plus = 0; plus < 2 && !f; ++plus) {
-          // face neighbour: same oct, a real oct, or a ghost oct whose
-          // father cell is the covering coarser cell
-          const int bit = 1 << d;
-          int64_t gn;
-          if (((c >> d) & 1) != plus) {
-            gn = 8 * int64_t(o) + (c ^ bit);
-          } else {
-            const int32_t ne = a.fnb[(2 * d + plus) * int64_t(a.NE) + o];
-            if (ne < 0) continue;
-            gn = ne < a.N ? 8 * int64_t(ne) + (c ^ bit)
-                          : checked(a.csrc[checked(ne - a.N, 0, a.NC, a.err)], 0, N8, a.err);
-          }
-          const float en = rp[2 * N8 + gn];
-          int dr = test_r ? -1 : 0, dp = test_p ? -1 : 0;
-          if (use32) {
-            if (dr) dr = jump_exceeds32(rp[gn], rc, 0x1p-23f * rp[gn], 0x1p-23f * rc, thr_r);
-            if (dp && dr != 1) dp = jump_exceeds32(rp[N8 + gn], pc, en, ec, thr_p);
-          }
-          if (dr == 1 || dp == 1) {
-            f = true;
-            continue;
-          }
-          if (dr == 0 && dp == 0) continue;
-          // undecided in FP32: the FP64 test on the FP64 density and pressure
-          if (!have64) {
-            double u[5];
-            load_cell(U, a.S, gc, u);
-            flag_rho_p(u, a.mgamma[m], a.msmallr[m], a.msmallp[m], rc64, pc64);
-            have64 = true;
-          }
-          double u[5], rn64, pn64;
-          load_cell(U, a.S, gn, u);
-          const int mn = ikey_member(a.key[gn >> 3]);
-          flag_rho_p(u, a.mgamma[mn], a.msmallr[mn], a.msmallp[mn], rn64, pn64);
-          if (dr && jump_exceeds(rn64, rc64, a.grad_rho)) f = true;
-          if (dp && jump_exceeds(pn64, pc64, a.grad_p)) f = true;
+      for (int k = 0; k < 6 && !f; ++k) {
+        const int64_t gn = gnb[k];
+        if (gn < 0) continue;
+        int dr = test_r ? -1 : 0, dp = test_p ? -1 : 0;
+        if (use32) {
+          if (dr) dr = jump_exceeds32(rn[k], rc, 0x1p-21f * rn[k], 0x1p-21f * rc, thr_r);
+          if (dp && dr != 1) dp = jump_exceeds32(pn[k], pc, en[k], ec, thr_p);
         }
+        if (dr == 1 || dp == 1) {
+          f = true;
+          continue;
+        }
+        if (dr == 0 && dp == 0) continue;
+        // undecided in FP32: the FP64 test on the FP64 density and pressure
+        if (!have64) {
+          double u[5];
+          load_cell(U, a.S, gc, u);
+          flag_rho_p(u, a.mgamma[m], a.msmallr[m], a.msmallp[m], rc64, pc64);
+          have64 = true;
+        }
+        double u[5], rn64, pn64;
+        load_cell(U, a.S, gn, u);
+        const int mn = ikey_member(a.key[gn >> 3]);
+        flag_rho_p(u, a.mgamma[mn], a.msmallr[mn], a.msmallp[mn], rn64, pn64);
+        if (dr && jump_exceeds(rn64, rc64, a.grad_rho)) f = true;
+        if (dp && jump_exceeds(pn64, pc64, a.grad_p)) f = true;
+      }
     }
   }
   const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
@@ -259,7 +282,12 @@ __global__ void k_flag_expand(RegridArgs a) {
 }
 
 // grading closure from the octs [lo, hi) of one level l > levelmin: every
-// flagged cell flags the level-(l-1) cells covering its 27 neighbours
+// flagged cell flags the level-(l-1) cells covering its 27 neighbours.  Per
+// axis those are, for a cell with bit 0, the father cell's coordinate minus
+// one and itself, for bit 1 itself and plus one, so the cells covered for
+// the whole oct form a subset of the 3^3 level-(l-1) cells around the father
+// cell: collected as a 27-bit set, then one atomic OR per level-(l-1) oct
+// (at most 8) instead of one per covered cell.
 __global__ void k_flag_grade(RegridArgs a, int lo, int hi) {
   const int o = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= hi) return;
@@ -269,36 +297,54 @@ __global__ void k_flag_grade(RegridArgs a, int lo, int hi) {
   const int l = ikey_lev(key);
   const int fo = a.father[o];
   if (fo < 0) return;
-  const int64_t side = int64_t(1) << l;              // cells per axis at level l
-  const int64_t oside = int64_t(1) << (l - 2 > 0 ? l - 2 : 0);  // octs per axis at l-1
-  const uint32_t oi = ikey_x(key), oj = ikey_y(key), okk = ikey_z(key);
+  uint32_t set27 = 0;  // bit (dz+1)*9 + (dy+1)*3 + (dx+1)
+#pragma unroll
   for (int c = 0; c < 8; ++c) {
     if (!((mask >> c) & 1u)) continue;
-    const int64_t x = 2 * int64_t(oi) + (c & 1), y = 2 * int64_t(oj) + ((c >> 1) & 1),
-                  z = 2 * int64_t(okk) + ((c >> 2) & 1);
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          // periodic wrap (side is a power of two)
-          const int64_t X = (x + dx) & (side - 1), Y = (y + dy) & (side - 1), Z = (z + dz) & (side - 1);
-          const int64_t px = X >> 1, py = Y >> 1, pz = Z >> 1;  // covering level-(l-1) cell
-          // its oct, relative to the father cell's oct (oi>>1, oj>>1, ok>>1)
-          int rel[3];
-          const int64_t d3[3] = {(px >> 1) - int64_t(oi >> 1), (py >> 1) - int64_t(oj >> 1),
-                                 (pz >> 1) - int64_t(okk >> 1)};
-          for (int q = 0; q < 3; ++q) {
-            const int64_t dd = d3[q] & (oside - 1);  // oside is a power of two
-            rel[q] = dd == 0 ? 0 : (dd == 1 ? 1 : -1);
-          }
-          const int32_t e = a.nbr27[((rel[2] + 1) * 9 + (rel[1] + 1) * 3 + (rel[0] + 1)) * int64_t(a.N) + fo];
-          if (e < 0 || e >= a.N) {
-            atomicOr(a.err, kErrGrading);
-            continue;
-          }
-          const int cc = int(px & 1) | (int(py & 1) << 1) | (int(pz & 1) << 2);
-          atomicOr(a.flag + e, 1u << cc);
-        }
+    const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int dx = (q & 1) - 1 + bx, dy = ((q >> 1) & 1) - 1 + by, dz = ((q >> 2) & 1) - 1 + bz;
+      set27 |= 1u << ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+    }
   }
+  const int64_t cside = int64_t(1) << (l - 1);                  // cells per axis at level l-1
+  const int64_t oside = int64_t(1) << (l - 2 > 0 ? l - 2 : 0);  // octs per axis at l-1
+  const uint32_t oi = ikey_x(key), oj = ikey_y(key), okk = ikey_z(key);  // the father cell at l-1
+  int32_t octs[8];
+  uint32_t bits[8];
+  int n = 0;
+  for (int k = 0; k < 27; ++k) {
+    if (!((set27 >> k) & 1u)) continue;
+    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    // the covered level-(l-1) cell, periodic (cside is a power of two)
+    const int64_t px = (int64_t(oi) + dx) & (cside - 1), py = (int64_t(oj) + dy) & (cside - 1),
+                  pz = (int64_t(okk) + dz) & (cside - 1);
+    // its oct, relative to the father cell's oct (oi>>1, oj>>1, ok>>1)
+    int rel[3];
+    const int64_t d3[3] = {(px >> 1) - int64_t(oi >> 1), (py >> 1) - int64_t(oj >> 1),
+                           (pz >> 1) - int64_t(okk >> 1)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int64_t dd = d3[q] & (oside - 1);  // oside is a power of two
+      rel[q] = dd == 0 ? 0 : (dd == 1 ? 1 : -1);
+    }
+    const int32_t e = a.nbr27[((rel[2] + 1) * 9 + (rel[1] + 1) * 3 + (rel[0] + 1)) * int64_t(a.N) + fo];
+    if (e < 0 || e >= a.N) {
+      atomicOr(a.err, kErrGrading);
+      continue;
+    }
+    const uint32_t cc = uint32_t(px & 1) | (uint32_t(py & 1) << 1) | (uint32_t(pz & 1) << 2);
+    int t = 0;
+    while (t < n && octs[t] != e) ++t;
+    if (t == n) {
+      octs[n] = e;
+      bits[n] = 0;
+      ++n;
+    }
+    bits[t] |= 1u << cc;
+  }
+  for (int t = 0; t < n; ++t) atomicOr(a.flag + octs[t], bits[t]);
 }
 
 // per oct: 1 if it stays (its father cell is flagged, or it is a base oct),
