@@ -302,8 +302,10 @@ amr_status amr_read_phi(amr_handle h, double *phi, int64_t cap);
  * oct of every member, zero after amr_create and after every regrid): the
  * values of level L-1 are the boundary data, those of level L the initial
  * guess, and level L receives the result (amr_write_phi / amr_read_phi_level
- * move them).  The tables of the level are built on the host on the first
- * call for a (member, level) and kept until the mesh changes.  resid (may be
+ * move them).  The tables of the level (its cells and their ancestors,
+ * sorted, with neighbours, colours, children and prolongation stencils) are
+ * built on the device on the first call for a (member, level) and kept
+ * until the mesh changes.  resid (may be
  * NULL) receives the L2 norm of the level's residual after each V-cycle.
  * FP64 whatever the precision of the state.  Synchronous.  Errors:
  * AMR_EINVAL (level not a populated level above levelmin, n_vcycles outside

@@ -462,19 +462,22 @@ static int64_t scan_tmp_size(int64_t n) {
 // Stable LSD sort of (keys, vals) by the given digits; returns the buffers
 // that hold the result in (*k, *v).
 static void radix_sort(amr_mesh *h, uint64_t **k, uint32_t **v, uint64_t *k_alt, uint32_t *v_alt,
-                       int64_t n, const std::vector<std::pair<int, int>> &digits) {
+                       int64_t n, const std::vector<std::pair<int, int>> &digits,
+                       uint32_t *table = nullptr, uint32_t *scan_tmp = nullptr) {
   if (n <= 0) return;
+  if (!table) table = h->table;
+  if (!scan_tmp) scan_tmp = h->scan_tmp;
   const int64_t ntiles = (n + kRadixTile - 1) / kRadixTile;
   uint64_t *ka = *k, *kb = k_alt;
   uint32_t *va = *v, *vb = v_alt;
   for (auto &dg : digits) {
     const int shift = dg.first, nbits = dg.second;
     launch(h, K_RADIX_HIST, k_radix_hist, dim3(unsigned(ntiles)), dim3(kRadixTile),
-           (const uint64_t *)ka, n, shift, nbits, h->table, ntiles);
-    scan_exclusive(h, h->table, (int64_t(1) << nbits) * ntiles, h->scan_tmp);
+           (const uint64_t *)ka, n, shift, nbits, table, ntiles);
+    scan_exclusive(h, table, (int64_t(1) << nbits) * ntiles, scan_tmp);
     launch(h, K_RADIX_SCATTER, k_radix_scatter, dim3(unsigned(ntiles)), dim3(kRadixTile),
            (const uint64_t *)ka, (const uint32_t *)va, kb, vb, n, shift, nbits,
-           (const uint32_t *)h->table, ntiles);
+           (const uint32_t *)table, ntiles);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
@@ -2222,10 +2225,6 @@ static amr_status ensure_phil(amr_mesh *h) {
 
 static bool level_ok(int level) { return level >= 0 && level <= kMaxLev; }
 
-static inline uint64_t mgl_code(int64_t x, int64_t y, int64_t z) {
-  return (uint64_t(x) << 42) | (uint64_t(y) << 21) | uint64_t(z);
-}
-
 static void mgl_free_set(amr_mesh *h, amr_mesh::MGLSet &S) {
   for (auto &t : S.tab)
     for (void *b : {(void *)t.nb, (void *)t.nbnd, (void *)t.col, (void *)t.child, (void *)t.pro, (void *)t.e,
@@ -2245,160 +2244,125 @@ static void mgl_free(amr_mesh *h) {
   h->mgl_part = h->mgl_scalar = nullptr;
 }
 
-// The MG hierarchy of level L of the selected member: level 0 = the cells of
-// the level-L octs, level k = the level-(L-k) ancestors of level k-1, down to
-// levelmin; every table in sorted (x, y, z) order of the cells.
+// The MG hierarchy of level L of the selected member, built on the device:
+// MG level 0 = the cells of the level-L octs, MG level k = the level-(L-k)
+// parents of MG level k-1, down to levelmin; every table in sorted (x, y, z)
+// order of the cells (keys with L-k bits per axis).  The cell counts of the
+// levels are read back to size them; nothing else leaves the device.
 static amr_status mgl_build(amr_mesh *h, int L, amr_mesh::MGLSet &S) {
   const Member &mb = h->mem[h->sel];
   const int lmin = mb.lmin, K = L - lmin;
-  const int64_t olo = mb.oct_base + mb.lo[L - 1], ohi = mb.oct_base + mb.lo[L + 1];
-  std::vector<uint64_t> key(size_t(ohi - olo));
-  CUDA_TRY(cudaMemcpyAsync(key.data(), h->key + olo, 8 * key.size(), cudaMemcpyDeviceToHost, h->s));
-  CUDA_TRY(cudaStreamSynchronize(h->s));
-  auto cell_code = [&](uint64_t k, int c) {
-    return mgl_code(2 * int64_t(ikey_x(k)) + (c & 1), 2 * int64_t(ikey_y(k)) + ((c >> 1) & 1),
-                    2 * int64_t(ikey_z(k)) + ((c >> 2) & 1));
+  const int lo = int(mb.oct_base + mb.lo[L]);
+  const int64_t nl = mb.lo[L + 1] - mb.lo[L], n0 = 8 * nl;
+  // scratch of the build: keys and values (two copies each for the sort),
+  // the sort's digit table and scan space, flags and positions
+  const int64_t ntiles = (n0 + kRadixTile - 1) / kRadixTile;
+  const int64_t tcap = 256 * ntiles + 256;
+  uint64_t *ka = nullptr, *kb = nullptr;
+  uint32_t *va = nullptr, *vb = nullptr, *table = nullptr, *stmp = nullptr, *flag = nullptr, *pos = nullptr;
+  int64_t *cnt = nullptr;
+  std::vector<uint64_t *> keys(size_t(K + 1), nullptr);
+  auto release = [&] {
+    for (void *b : {(void *)ka, (void *)kb, (void *)va, (void *)vb, (void *)table, (void *)stmp, (void *)flag,
+                    (void *)pos, (void *)cnt})
+      dev_free(h, b);
+    for (uint64_t *b : keys) dev_free(h, b);
   };
-  // cells of level L: (code, global cell index); octs of level L-1: (code,
-  // global oct index); both sorted
-  std::vector<std::pair<uint64_t, int32_t>> cL, oL1;
-  for (int64_t o = olo; o < ohi; ++o) {
-    const uint64_t k = key[size_t(o - olo)];
-    if (ikey_lev(k) == L)
-      for (int c = 0; c < 8; ++c) cL.push_back({cell_code(k, c), int32_t(8 * o + c)});
-    else
-      oL1.push_back({mgl_code(ikey_x(k), ikey_y(k), ikey_z(k)), int32_t(o)});
-  }
-  std::sort(cL.begin(), cL.end());
-  std::sort(oL1.begin(), oL1.end());
-  auto find_in = [](const std::vector<uint64_t> &v, uint64_t c) -> int32_t {
-    auto it = std::lower_bound(v.begin(), v.end(), c);
-    return (it != v.end() && *it == c) ? int32_t(it - v.begin()) : -1;
-  };
-  // global index of the level-(L-1) cell with the given code, or -1
-  auto find_L1 = [&](uint64_t c) -> int32_t {
-    const int64_t X = int64_t(c >> 42), Y = int64_t((c >> 21) & 0x1FFFFF), Z = int64_t(c & 0x1FFFFF);
-    const uint64_t oc = mgl_code(X >> 1, Y >> 1, Z >> 1);
-    auto it = std::lower_bound(oL1.begin(), oL1.end(), std::make_pair(oc, int32_t(-1)));
-    if (it == oL1.end() || it->first != oc) return -1;
-    return 8 * it->second + int32_t((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2));
-  };
-  std::vector<std::vector<uint64_t>> codes(size_t(K + 1));
-  for (auto &pr : cL) codes[0].push_back(pr.first);
-  for (int k = 1; k <= K; ++k) {
-    for (uint64_t c : codes[size_t(k - 1)])
-      codes[size_t(k)].push_back(mgl_code(int64_t(c >> 42) >> 1, int64_t((c >> 21) & 0x1FFFFF) >> 1,
-                                          int64_t(c & 0x1FFFFF) >> 1));
-    std::sort(codes[size_t(k)].begin(), codes[size_t(k)].end());
-    codes[size_t(k)].erase(std::unique(codes[size_t(k)].begin(), codes[size_t(k)].end()), codes[size_t(k)].end());
-  }
-  auto xyz = [](uint64_t c, int64_t &x, int64_t &y, int64_t &z) {
-    x = int64_t(c >> 42);
-    y = int64_t((c >> 21) & 0x1FFFFF);
-    z = int64_t(c & 0x1FFFFF);
-  };
+  amr_status st = AMR_OK;
+#define MGL_TRY(x)      \
+  do {                  \
+    st = (x);           \
+    if (st != AMR_OK) { \
+      release();        \
+      return st;        \
+    }                   \
+  } while (0)
+  MGL_TRY(alloc_n(h, &ka, n0));
+  MGL_TRY(alloc_n(h, &kb, n0));
+  MGL_TRY(alloc_n(h, &va, n0));
+  MGL_TRY(alloc_n(h, &vb, n0));
+  MGL_TRY(alloc_n(h, &table, tcap));
+  MGL_TRY(alloc_n(h, &stmp, scan_tmp_size(std::max(tcap, n0))));
+  MGL_TRY(alloc_n(h, &flag, n0));
+  MGL_TRY(alloc_n(h, &pos, n0));
+  MGL_TRY(alloc_n(h, &cnt, 2));
   S.tab.resize(size_t(K + 1));
-  for (int k = 0; k <= K; ++k) {
-    const std::vector<uint64_t> &cd = codes[size_t(k)];
-    const int64_t n = int64_t(cd.size());
-    const int64_t side = int64_t(1) << (L - k);
-    std::vector<int32_t> nb(6 * size_t(n)), nbnd(size_t(n), 0), col;
-    std::vector<int32_t> c1;
-    for (int64_t t = 0; t < n; ++t) {
-      int64_t x, y, z;
-      xyz(cd[size_t(t)], x, y, z);
-      for (int d = 0; d < 3; ++d)
-        for (int sg = 0; sg < 2; ++sg) {
-          const int64_t dd = sg ? 1 : -1;
-          const int64_t X = (x + (d == 0) * dd) & (side - 1), Y = (y + (d == 1) * dd) & (side - 1),
-                        Z = (z + (d == 2) * dd) & (side - 1);
-          const int32_t q = find_in(cd, mgl_code(X, Y, Z));
-          nb[size_t((2 * d + sg) * n + t)] = q;
-          if (q < 0) nbnd[size_t(t)] += 1;
-        }
-      ((x + y + z) & 1 ? c1 : col).push_back(int32_t(t));
-    }
-    amr_mesh::MGLTab &T = S.tab[size_t(k)];
-    T.L = L - k;
-    T.n = n;
-    T.nc0 = int64_t(col.size());
-    T.nc1 = int64_t(c1.size());
-    col.insert(col.end(), c1.begin(), c1.end());
-    AMR_TRY(upload(h, &T.nb, nb));
-    AMR_TRY(upload(h, &T.nbnd, nbnd));
-    AMR_TRY(upload(h, &T.col, col));
-    AMR_TRY(alloc_n(h, &T.e, n));
-    AMR_TRY(alloc_n(h, &T.f, n));
-    AMR_TRY(alloc_n(h, &T.r, n));
-    if (k >= 1) {
-      // children in MG level k-1 (cx, cy, cz; cz fastest); the trilinear
-      // stencils of level k-1's cells in this level
-      const std::vector<uint64_t> &fine = codes[size_t(k - 1)];
-      const int64_t nf = int64_t(fine.size());
-      std::vector<int32_t> child(8 * size_t(n)), pro(8 * size_t(nf));
-      for (int64_t t = 0; t < n; ++t) {
-        int64_t x, y, z;
-        xyz(cd[size_t(t)], x, y, z);
-        int j = 0;
-        for (int cx = 0; cx < 2; ++cx)
-          for (int cy = 0; cy < 2; ++cy)
-            for (int cz = 0; cz < 2; ++cz, ++j)
-              child[size_t(j * n + t)] = find_in(fine, mgl_code(2 * x + cx, 2 * y + cy, 2 * z + cz));
-      }
-      for (int64_t t = 0; t < nf; ++t) {
-        int64_t x, y, z;
-        xyz(fine[size_t(t)], x, y, z);
-        const int64_t X = x >> 1, Y = y >> 1, Z = z >> 1;
-        const int64_t sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
-        for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b)
-            for (int d = 0; d < 2; ++d)
-              pro[size_t((4 * a + 2 * b + d) * nf + t)] =
-                  find_in(cd, mgl_code((X + a * sx) & (side - 1), (Y + b * sy) & (side - 1), (Z + d * sz) & (side - 1)));
-      }
-      AMR_TRY(upload(h, &T.child, child));
-      AMR_TRY(upload(h, &S.tab[size_t(k - 1)].pro, pro));
-    }
-  }
-  // level 0: global cells, fathers, coarse cells across boundary faces
+  // MG level 0: the level's cells, sorted; their global indices are g0
+  launch(h, K_MG_OTHER, k_mgl_cells, dim3(nblocks(n0)), dim3(256), (const uint64_t *)h->key, lo, nl, L, ka, va);
   {
-    const int64_t n = S.tab[0].n;
-    const int64_t side = int64_t(1) << L, cside = side >> 1;
-    const size_t nn = size_t(n);
-    std::vector<int32_t> g0(nn), fg(nn), ag(6 * nn, -1);
-    for (int64_t t = 0; t < n; ++t) {
-      g0[size_t(t)] = cL[size_t(t)].second;
-      int64_t x, y, z;
-      xyz(codes[0][size_t(t)], x, y, z);
-      fg[size_t(t)] = find_L1(mgl_code(x >> 1, y >> 1, z >> 1));
-    }
-    // boundary faces: read back the neighbour table of level 0
-    std::vector<int32_t> nb(6 * size_t(n));
-    CUDA_TRY(cudaMemcpyAsync(nb.data(), S.tab[0].nb, 4 * nb.size(), cudaMemcpyDeviceToHost, h->s));
-    CUDA_TRY(cudaStreamSynchronize(h->s));
-    for (int64_t t = 0; t < n; ++t) {
-      int64_t x, y, z;
-      xyz(codes[0][size_t(t)], x, y, z);
-      for (int d = 0; d < 3; ++d)
-        for (int sg = 0; sg < 2; ++sg) {
-          const int k6 = 2 * d + sg;
-          if (nb[size_t(k6 * n + t)] >= 0) continue;
-          const int64_t dd = sg ? 1 : -1;
-          const int64_t X = (x + (d == 0) * dd) & (side - 1), Y = (y + (d == 1) * dd) & (side - 1),
-                        Z = (z + (d == 2) * dd) & (side - 1);
-          ag[size_t(k6 * n + t)] = find_L1(mgl_code((X >> 1) & (cside - 1), (Y >> 1) & (cside - 1), (Z >> 1) & (cside - 1)));
-          if (ag[size_t(k6 * n + t)] < 0)
-            return fail(AMR_EGRADING, "amr_poisson_level: a boundary face of level %d has no coarse cell across", L);
-        }
-    }
-    for (int32_t v : fg)
-      if (v < 0) return fail(AMR_EGRADING, "amr_poisson_level: a cell of level %d has no father", L);
-    AMR_TRY(upload(h, &S.g0, g0));
-    AMR_TRY(upload(h, &S.fatherg, fg));
-    AMR_TRY(upload(h, &S.acrossg, ag));
-    AMR_TRY(alloc_n(h, &S.bsum, n));
+    uint64_t *k = ka;
+    uint32_t *v = va;
+    radix_sort(h, &k, &v, kb, vb, n0, digits_for(0, 3 * L), table, stmp);
+    MGL_TRY(alloc_n(h, &keys[0], n0));
+    CUDA_TRY(cudaMemcpyAsync(keys[0], k, 8 * size_t(n0), cudaMemcpyDeviceToDevice, h->s));
+    MGL_TRY(alloc_n(h, &S.g0, n0));
+    CUDA_TRY(cudaMemcpyAsync(S.g0, v, 4 * size_t(n0), cudaMemcpyDeviceToDevice, h->s));
   }
-  return AMR_OK;
+  std::vector<int64_t> n(size_t(K + 1), 0);
+  n[0] = n0;
+  for (int k = 1; k <= K; ++k) {
+    const int b = L - k;
+    const int64_t m = n[size_t(k - 1)];
+    launch(h, K_MG_OTHER, k_mgl_parents, dim3(nblocks(m)), dim3(256), (const uint64_t *)keys[size_t(k - 1)], m, b,
+           ka, va);
+    uint64_t *kk = ka;
+    uint32_t *vv = va;
+    radix_sort(h, &kk, &vv, kb, vb, m, digits_for(0, 3 * b), table, stmp);
+    launch(h, K_MG_OTHER, k_mgl_heads, dim3(nblocks(m)), dim3(256), (const uint64_t *)kk, m, flag);
+    CUDA_TRY(cudaMemcpyAsync(pos, flag, 4 * size_t(m), cudaMemcpyDeviceToDevice, h->s));
+    scan_exclusive(h, pos, m, stmp);
+    MGL_TRY(alloc_n(h, &keys[size_t(k)], m));
+    launch(h, K_MG_OTHER, k_mgl_unique, dim3(nblocks(m)), dim3(256), (const uint64_t *)kk, (const uint32_t *)flag,
+           (const uint32_t *)pos, m, keys[size_t(k)], cnt);
+    int64_t c = 0;
+    CUDA_TRY(cudaMemcpyAsync(&c, cnt, sizeof c, cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+    n[size_t(k)] = c;
+  }
+  // per MG level: neighbours, colours, children and stencils
+  for (int k = 0; k <= K; ++k) {
+    const int b = L - k;
+    const int64_t m = n[size_t(k)];
+    amr_mesh::MGLTab &T = S.tab[size_t(k)];
+    T.L = b;
+    T.n = m;
+    MGL_TRY(alloc_n(h, &T.nb, 6 * m));
+    MGL_TRY(alloc_n(h, &T.nbnd, m));
+    MGL_TRY(alloc_n(h, &T.col, m));
+    MGL_TRY(alloc_n(h, &T.e, m));
+    MGL_TRY(alloc_n(h, &T.f, m));
+    MGL_TRY(alloc_n(h, &T.r, m));
+    launch(h, K_MG_OTHER, k_mgl_faces, dim3(nblocks(m)), dim3(256), (const uint64_t *)keys[size_t(k)], m, b, T.nb,
+           T.nbnd, flag);
+    CUDA_TRY(cudaMemcpyAsync(pos, flag, 4 * size_t(m), cudaMemcpyDeviceToDevice, h->s));
+    scan_exclusive(h, pos, m, stmp);
+    launch(h, K_MG_OTHER, k_mgl_colours, dim3(nblocks(m)), dim3(256), (const uint32_t *)flag,
+           (const uint32_t *)pos, m, T.col, cnt + 1);
+    int64_t c0 = 0;
+    CUDA_TRY(cudaMemcpyAsync(&c0, cnt + 1, sizeof c0, cudaMemcpyDeviceToHost, h->s));
+    CUDA_TRY(cudaStreamSynchronize(h->s));
+    T.nc0 = c0;
+    T.nc1 = m - c0;
+    if (k >= 1) {
+      const int64_t mf = n[size_t(k - 1)];
+      MGL_TRY(alloc_n(h, &T.child, 8 * m));
+      MGL_TRY(alloc_n(h, &S.tab[size_t(k - 1)].pro, 8 * mf));
+      launch(h, K_MG_OTHER, k_mgl_children, dim3(nblocks(m)), dim3(256), (const uint64_t *)keys[size_t(k)], m, b,
+             (const uint64_t *)keys[size_t(k - 1)], mf, T.child);
+      launch(h, K_MG_OTHER, k_mgl_stencils, dim3(nblocks(mf)), dim3(256), (const uint64_t *)keys[size_t(k - 1)], mf,
+             b, (const uint64_t *)keys[size_t(k)], m, S.tab[size_t(k - 1)].pro);
+    }
+  }
+  // MG level 0: father cells and the coarse cells across its boundary
+  MGL_TRY(alloc_n(h, &S.fatherg, n0));
+  MGL_TRY(alloc_n(h, &S.acrossg, 6 * n0));
+  MGL_TRY(alloc_n(h, &S.bsum, n0));
+  launch(h, K_MG_OTHER, k_mgl_coarse, dim3(nblocks(n0)), dim3(256), h->hash, h->sel, L, int(h->N),
+         (const uint64_t *)keys[0], n0, (const int32_t *)S.tab[0].nb, S.fatherg, S.acrossg, h->err);
+  st = check_device(h, "amr_poisson_level");
+  release();
+#undef MGL_TRY
+  return st;
 }
 
 // the hierarchy of level L of the selected member, built on first use and

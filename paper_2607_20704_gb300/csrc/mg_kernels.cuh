@@ -314,4 +314,173 @@ __global__ void k_mgl_norm(const double *__restrict__ part, int nparts, double *
   *out = sqrt(s);
 }
 
+// ---------------------------------------------------------------------------
+// the tables of a refined level's hierarchy, built on the device: cells are
+// keyed by (x << 2b) | (y << b) | z with b bits per axis (lexicographic in
+// x, y, z, the sorted order of every table); neighbours, children and
+// prolongation stencils are found by binary search in the sorted keys
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mgl_key(int64_t x, int64_t y, int64_t z, int b) {
+  return (uint64_t(x) << (2 * b)) | (uint64_t(y) << b) | uint64_t(z);
+}
+__device__ __forceinline__ void mgl_unkey(uint64_t k, int b, int64_t &x, int64_t &y, int64_t &z) {
+  const uint64_t m = (uint64_t(1) << b) - 1;
+  x = int64_t(k >> (2 * b));
+  y = int64_t((k >> b) & m);
+  z = int64_t(k & m);
+}
+// index of key c in the sorted keys[0..n), or -1 (at most log2(n) + 1 steps)
+__device__ __forceinline__ int32_t mgl_find(const uint64_t *__restrict__ keys, int64_t n, uint64_t c) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (keys[mid] < c) lo = mid + 1; else hi = mid;
+  }
+  return (lo < n && keys[lo] == c) ? int32_t(lo) : -1;
+}
+
+// the cells of the level-L octs [lo, lo + nl): key and global cell index
+__global__ void k_mgl_cells(const uint64_t *__restrict__ key, int lo, int64_t nl, int L, uint64_t *__restrict__ ck,
+                            uint32_t *__restrict__ cv) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= 8 * nl) return;
+  const int o = lo + int(t >> 3), c = int(t & 7);
+  const uint64_t k = key[o];
+  ck[t] = mgl_key(2 * int64_t(ikey_x(k)) + (c & 1), 2 * int64_t(ikey_y(k)) + ((c >> 1) & 1),
+                  2 * int64_t(ikey_z(k)) + ((c >> 2) & 1), L);
+  cv[t] = uint32_t(8 * int64_t(o) + c);
+}
+
+// parent keys (b bits per axis) of sorted child keys (b + 1 bits)
+__global__ void k_mgl_parents(const uint64_t *__restrict__ ck, int64_t n, int b, uint64_t *__restrict__ pk,
+                              uint32_t *__restrict__ pv) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  int64_t x, y, z;
+  mgl_unkey(ck[t], b + 1, x, y, z);
+  pk[t] = mgl_key(x >> 1, y >> 1, z >> 1, b);
+  pv[t] = uint32_t(t);
+}
+
+// head flags of runs of equal keys in a sorted array
+__global__ void k_mgl_heads(const uint64_t *__restrict__ k, int64_t n, uint32_t *__restrict__ head) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < n) head[t] = (t == 0 || k[t] != k[t - 1]) ? 1u : 0u;
+}
+
+// the unique keys (pos = exclusive scan of head) and their count
+__global__ void k_mgl_unique(const uint64_t *__restrict__ k, const uint32_t *__restrict__ head,
+                             const uint32_t *__restrict__ pos, int64_t n, uint64_t *__restrict__ out,
+                             int64_t *__restrict__ count) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  if (head[t]) out[pos[t]] = k[t];
+  if (t == n - 1) *count = int64_t(pos[t] + head[t]);
+}
+
+// the six face neighbours in the MG level (-1 outside it), the count of
+// faces to the outside, and the even-colour flag (parity of x + y + z)
+__global__ void k_mgl_faces(const uint64_t *__restrict__ keys, int64_t n, int b, int32_t *__restrict__ nb,
+                            int32_t *__restrict__ nbnd, uint32_t *__restrict__ even) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  int64_t x, y, z;
+  mgl_unkey(keys[t], b, x, y, z);
+  const int64_t m = (int64_t(1) << b) - 1;
+  int nout = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const int64_t dd = sg ? 1 : -1;
+      const int32_t q = mgl_find(keys, n, mgl_key((x + (d == 0) * dd) & m, (y + (d == 1) * dd) & m,
+                                                  (z + (d == 2) * dd) & m, b));
+      nb[(2 * d + sg) * n + t] = q;
+      nout += q < 0;
+    }
+  nbnd[t] = nout;
+  even[t] = ((x + y + z) & 1) ? 0u : 1u;
+}
+
+// colour lists: even cells first, then odd, each in key order (pos = the
+// exclusive scan of even; nc0 = the number of even cells)
+__global__ void k_mgl_colours(const uint32_t *__restrict__ even, const uint32_t *__restrict__ pos, int64_t n,
+                              int32_t *__restrict__ col, int64_t *__restrict__ nc0) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const int64_t n0 = int64_t(pos[n - 1] + even[n - 1]);
+  col[even[t] ? int64_t(pos[t]) : n0 + (t - int64_t(pos[t]))] = int32_t(t);
+  if (t == 0) *nc0 = n0;
+}
+
+// children of coarse cell t (b bits) in the finer MG level (b + 1 bits),
+// order (cx, cy, cz) with cz fastest
+__global__ void k_mgl_children(const uint64_t *__restrict__ keys, int64_t n, int b,
+                               const uint64_t *__restrict__ fkeys, int64_t nf, int32_t *__restrict__ child) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  int64_t x, y, z;
+  mgl_unkey(keys[t], b, x, y, z);
+  int j = 0;
+  for (int cx = 0; cx < 2; ++cx)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cz = 0; cz < 2; ++cz, ++j)
+        child[j * n + t] = mgl_find(fkeys, nf, mgl_key(2 * x + cx, 2 * y + cy, 2 * z + cz, b + 1));
+}
+
+// trilinear stencil of fine cell t (b + 1 bits) in the coarse MG level (b
+// bits): entry 4a + 2b' + d for the coarse cells (X + a sx, Y + b' sy, Z + d sz)
+__global__ void k_mgl_stencils(const uint64_t *__restrict__ fkeys, int64_t nf, int b,
+                               const uint64_t *__restrict__ keys, int64_t n, int32_t *__restrict__ pro) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nf) return;
+  int64_t x, y, z;
+  mgl_unkey(fkeys[t], b + 1, x, y, z);
+  const int64_t X = x >> 1, Y = y >> 1, Z = z >> 1, m = (int64_t(1) << b) - 1;
+  const int64_t sx = (x & 1) ? 1 : -1, sy = (y & 1) ? 1 : -1, sz = (z & 1) ? 1 : -1;
+  for (int a = 0; a < 2; ++a)
+    for (int bb = 0; bb < 2; ++bb)
+      for (int d = 0; d < 2; ++d)
+        pro[(4 * a + 2 * bb + d) * nf + t] =
+            mgl_find(keys, n, mgl_key((X + a * sx) & m, (Y + bb * sy) & m, (Z + d * sz) & m, b));
+}
+
+// global index of the level-(L-1) cell (X, Y, Z), or -1 (no such oct)
+__device__ __forceinline__ int32_t mgl_coarse_cell(HashView hv, int member, int Lc, int64_t X, int64_t Y,
+                                                   int64_t Z, int N) {
+  const int32_t v = hash_probe1(hv, ikey(member, Lc, uint32_t(X >> 1), uint32_t(Y >> 1), uint32_t(Z >> 1)));
+  if (v < 1 || v > N) return -1;
+  return 8 * (v - 1) + int32_t((X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2));
+}
+
+// MG level 0: the father cell of every cell and the level-(L-1) cell across
+// every face that leaves the level (-1 for the others)
+__global__ void k_mgl_coarse(HashView hv, int member, int L, int N, const uint64_t *__restrict__ keys, int64_t n,
+                             const int32_t *__restrict__ nb, int32_t *__restrict__ fatherg,
+                             int32_t *__restrict__ acrossg, int *err) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  int64_t x, y, z;
+  mgl_unkey(keys[t], L, x, y, z);
+  const int64_t m = (int64_t(1) << L) - 1, mc = (int64_t(1) << (L - 1)) - 1;
+  const int32_t f = mgl_coarse_cell(hv, member, L - 1, x >> 1, y >> 1, z >> 1, N);
+  if (f < 0) atomicOr(err, kErrGrading);
+  fatherg[t] = f < 0 ? 0 : f;
+  for (int d = 0; d < 3; ++d)
+    for (int sg = 0; sg < 2; ++sg) {
+      const int k6 = 2 * d + sg;
+      int32_t q = -1;
+      if (nb[k6 * n + t] < 0) {
+        const int64_t dd = sg ? 1 : -1;
+        const int64_t X = (x + (d == 0) * dd) & m, Y = (y + (d == 1) * dd) & m, Z = (z + (d == 2) * dd) & m;
+        q = mgl_coarse_cell(hv, member, L - 1, (X >> 1) & mc, (Y >> 1) & mc, (Z >> 1) & mc, N);
+        if (q < 0) {
+          atomicOr(err, kErrGrading);
+          q = 0;
+        }
+      }
+      acrossg[k6 * n + t] = q;
+    }
+}
+
 }  // namespace amr
