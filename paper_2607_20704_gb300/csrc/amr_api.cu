@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -110,6 +111,17 @@ struct DevBuf {
   size_t bytes;
 };
 
+// Buffers a regrid's retired mesh leaves for the next regrid: shared by the
+// handle and the shells it builds new meshes in, so the next mesh takes its
+// arrays from here instead of the allocator (a regrid allocates and frees
+// about 60 arrays).  Holds at most `cap` bytes (the live mesh's size, set by
+// the regrid; 0 otherwise, when frees go to the allocator).  Handles with a
+// device budget do not keep one.
+struct BufCache {
+  std::vector<DevBuf> v;
+  size_t bytes = 0, cap = 0;
+};
+
 // level-step launch domains of a segment
 enum Dom {
   DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_BLOCKS = 4, DOM_COMMIT = 5, DOM_COUNT = 6
@@ -145,6 +157,7 @@ struct amr_mesh {
   int device = 0, sm_count = 152;
   size_t bytes = 0;
   std::vector<DevBuf> bufs;
+  std::shared_ptr<BufCache> cache;
 
   int M = 1, sel = 0, lmax_all = 1;
   std::vector<Member> mem;
@@ -284,6 +297,22 @@ static amr_status dev_alloc(amr_mesh *h, void **out, size_t bytes) {
     return fail(AMR_ENOMEM, "device allocation of %zu bytes exceeds the budget (%zu of %zu held)",
                 bytes, h->bytes, h->p.hbm_budget_bytes);
   void *ptr = nullptr;
+  if (h->cache && !h->cache->v.empty()) {  // the smallest cached array that fits, within 2x
+    std::vector<DevBuf> &v = h->cache->v;
+    size_t best = v.size();
+    for (size_t t = 0; t < v.size(); ++t)
+      if (v[t].bytes >= bytes && v[t].bytes <= 2 * bytes && (best == v.size() || v[t].bytes < v[best].bytes))
+        best = t;
+    if (best < v.size()) {
+      const DevBuf b = v[best];
+      v.erase(v.begin() + best);
+      h->cache->bytes -= b.bytes;
+      h->bufs.push_back(b);
+      h->bytes += b.bytes;
+      *out = b.p;
+      return AMR_OK;
+    }
+  }
   if (h->p.alloc) {
     ptr = h->p.alloc(bytes, (void *)h->s, h->p.alloc_user);
     if (!ptr) return fail(AMR_ENOMEM, "caller allocator refused %zu bytes", bytes);
@@ -300,16 +329,26 @@ static amr_status dev_alloc(amr_mesh *h, void **out, size_t bytes) {
   return AMR_OK;
 }
 
+static void real_free(amr_mesh *h, void *ptr, size_t bytes) {
+  if (h->p.free)
+    h->p.free(ptr, bytes, (void *)h->s, h->p.alloc_user);
+  else
+    cudaFreeAsync(ptr, h->s);
+}
+
 static void dev_free(amr_mesh *h, void *ptr) {
   if (!ptr) return;
   for (size_t t = 0; t < h->bufs.size(); ++t) {
     if (h->bufs[t].p == ptr) {
-      if (h->p.free)
-        h->p.free(ptr, h->bufs[t].bytes, (void *)h->s, h->p.alloc_user);
-      else
-        cudaFreeAsync(ptr, h->s);
-      h->bytes -= h->bufs[t].bytes;
+      const DevBuf b = h->bufs[t];
+      h->bytes -= b.bytes;
       h->bufs.erase(h->bufs.begin() + t);
+      if (h->cache && h->cache->bytes + b.bytes <= h->cache->cap) {
+        h->cache->v.push_back(b);  // reused in stream order: every use is on h->s
+        h->cache->bytes += b.bytes;
+      } else {
+        real_free(h, b.p, b.bytes);
+      }
       return;
     }
   }
@@ -922,7 +961,14 @@ static void destroy_all(amr_mesh *h) {
     cudaEventDestroy(t.e1);
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
+  const bool last = h->cache && h->cache.use_count() == 1;
+  if (last) h->cache->cap = 0;
   while (!h->bufs.empty()) dev_free(h, h->bufs.back().p);
+  if (last) {
+    for (const DevBuf &b : h->cache->v) real_free(h, b.p, b.bytes);
+    h->cache->v.clear();
+    h->cache->bytes = 0;
+  }
   if (h->s) cudaStreamSynchronize(h->s);
   if (h->own_stream && h->s) cudaStreamDestroy(h->s);
   delete h;
@@ -1380,6 +1426,7 @@ extern "C" amr_status amr_create_batch(const amr_params *p, int n_members,
   amr_mesh *h = new amr_mesh();
   h->p = *p;
   h->M = n_members;
+  if (!p->hbm_budget_bytes) h->cache = std::make_shared<BufCache>();
   h->mem.resize(n_members);
   if (p->tile != 0 && p->tile != 64 && p->tile != 128 && p->tile != 256 && p->tile != 512) {
     delete h;
@@ -1919,6 +1966,7 @@ static amr_mesh *regrid_shell(amr_mesh *h) {
   amr_mesh *nh = new amr_mesh();
   nh->p = h->p;
   nh->s = h->s;
+  nh->cache = h->cache;
   nh->own_stream = false;
   nh->device = h->device;
   nh->sm_count = h->sm_count;
@@ -2082,6 +2130,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
     h->graph = nullptr;
   }
   std::swap(*h, *nh);
+  if (h->cache) h->cache->cap = h->bytes;  // the old mesh's arrays serve the next regrid
   destroy_all(nh);
   return check_device(h, "amr_regrid");
 #undef REGRID_TRY
