@@ -383,8 +383,10 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   constexpr int in = 1 + D, t1 = D == 0 ? 2 : 1, t2 = D == 2 ? 2 : 3;
   const T rl = qL[0], ul = qL[in], pl = qL[4];
   const T rr = qR[0], ur = qR[in], pr = qR[4];
-  const T el = pl * igm1 + T(0.5) * rl * ((qL[1] * qL[1] + qL[2] * qL[2]) + qL[3] * qL[3]);
-  const T er = pr * igm1 + T(0.5) * rr * ((qR[1] * qR[1] + qR[2] * qR[2]) + qR[3] * qR[3]);
+  // total energy of a side (computed for the sampled side only)
+  auto energy = [igm1](const T(&q)[5]) {
+    return q[4] * igm1 + T(0.5) * q[0] * ((q[1] * q[1] + q[2] * q[2]) + q[3] * q[3]);
+  };
   const T cmax = max_sound_speed(g * pl, rl, g * pr, rr);
   const T sl = vmin(ul, ur) - cmax;
   const T sr = vmax(ul, ur) + cmax;
@@ -392,18 +394,22 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
   const T irc = rcp(rcl + rcr);
   const T us = ((rcr * ur + rcl * ul) + (pl - pr)) * irc;
   const T ps = ((rcr * pl + rcl * pr) + rcl * rcr * (ul - ur)) * irc;
+  // The sampled side K is the left one when S_L > 0 or u* > 0; its star
+  // state is taken when S_L <= 0 (left) or S_R > 0 (right).  Selected
+  // without divergent branches: the side's state and energy, then one star
+  // state (unused in the supersonic cases) with the arithmetic of Toro's
+  // four cases.
   T ro, uo, po, eo, v1, v2;
-  if constexpr (sizeof(T) == 4) {
-    // FP32: the same four cases without divergent branches.  The sampled
-    // side K is the left one when S_L > 0 or u* > 0; its star state is taken
-    // when S_L <= 0 (left) or S_R > 0 (right), with the same arithmetic as
-    // the branches below.
+  {
     const bool left = pos(sl) || pos(us);
     const bool star = left ? !pos(sl) : pos(sr);
-    const T rk = left ? rl : rr, uk = left ? ul : ur, pk = left ? pl : pr, ek = left ? el : er;
+    T qk[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qk[v] = left ? qL[v] : qR[v];
+    const T rk = qk[0], uk = qk[in], pk = qk[4], ek = energy(qk);
     const T sk = left ? sl : sr;
-    v1 = left ? qL[t1] : qR[t1];
-    v2 = left ? qL[t2] : qR[t2];
+    v1 = qk[t1];
+    v2 = qk[t2];
     const T id = rcp(sk - us);
     const T rs = rk * (sk - uk) * id;
     const T es = ((sk - uk) * ek - pk * uk + ps * us) * id;
@@ -411,20 +417,6 @@ __device__ __forceinline__ void hllc(const T (&qL)[5], const T (&qR)[5], T g, T 
     eo = star ? es : ek;
     uo = star ? us : uk;
     po = star ? ps : pk;
-  } else if (pos(sl)) {
-    ro = rl; uo = ul; po = pl; eo = el; v1 = qL[t1]; v2 = qL[t2];
-  } else if (pos(us)) {
-    const T id = rcp(sl - us);
-    ro = rl * (sl - ul) * id;
-    eo = ((sl - ul) * el - pl * ul + ps * us) * id;
-    uo = us; po = ps; v1 = qL[t1]; v2 = qL[t2];
-  } else if (pos(sr)) {
-    const T id = rcp(sr - us);
-    ro = rr * (sr - ur) * id;
-    eo = ((sr - ur) * er - pr * ur + ps * us) * id;
-    uo = us; po = ps; v1 = qR[t1]; v2 = qR[t2];
-  } else {
-    ro = rr; uo = ur; po = pr; eo = er; v1 = qR[t1]; v2 = qR[t2];
   }
   const T mf = ro * uo;
   F[0] = mf;
