@@ -32,9 +32,10 @@ namespace amr {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double minmod(double a, double b) {
   // 0 for opposite signs or a zero argument, else the argument of smaller
-  // magnitude; decided on the bit patterns (integer pipes, no FP64 issue)
+  // magnitude; decided on the bit patterns (integer pipes, no FP64 issue):
+  // the bits shifted left by one drop the sign and order the magnitudes
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
-  const long long ma = ia & 0x7FFFFFFFFFFFFFFFll, mb = ib & 0x7FFFFFFFFFFFFFFFll;
+  const unsigned long long ma = (unsigned long long)ia << 1, mb = (unsigned long long)ib << 1;
   if (((ia ^ ib) < 0) | (ma == 0) | (mb == 0)) return 0.0;
   return ma < mb ? a : b;
 }
