@@ -237,6 +237,9 @@ struct amr_mesh {
   // a mesh built from flags that went through the grading closure skips the
   // (27-probe per oct) grading check, except in the bounds-checked build
   bool graded_by_construction = false;
+  // launches of the level-step and time-step kernels (which wait on their
+  // predecessors themselves) use programmatic stream serialization
+  bool pdl = false;
   // Poisson on a refined level: per MG level the tables of k_mgl_*, the
   // level's cells (g0: global cell index), their fathers and the coarse cells
   // across boundary faces; the potential of every cell (mesh order)
@@ -394,6 +397,36 @@ static cudaEvent_t take_event(amr_mesh *h) {
   return e;
 }
 
+// one launch on the handle's stream; with h->pdl the kernel may be scheduled
+// while its predecessor drains (it waits for it with griddepcontrol.wait)
+template <typename... KArgs, typename... Args>
+static void launch_on(amr_mesh *h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                      Args &&...args) {
+  if (!h->pdl) {
+    kern<<<grid, block, smem, h->s>>>(std::forward<Args>(args)...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h->s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// kernels launched inside this scope start with grid_dep_wait()
+struct PdlScope {
+  amr_mesh *h;
+  bool old;
+  explicit PdlScope(amr_mesh *hh) : h(hh), old(hh->pdl) { h->pdl = true; }
+  ~PdlScope() { h->pdl = old; }
+};
+
 template <typename... KArgs, typename... Args>
 static void launch(amr_mesh *h, int kid, void (*kern)(KArgs...), dim3 grid, dim3 block,
                    Args &&...args) {
@@ -404,7 +437,7 @@ static void launch(amr_mesh *h, int kid, void (*kern)(KArgs...), dim3 grid, dim3
     e0 = take_event(h);
     cudaEventRecord(e0, h->s);
   }
-  kern<<<grid, block, 0, h->s>>>(std::forward<Args>(args)...);
+  launch_on(h, kern, grid, block, 0, std::forward<Args>(args)...);
   const cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess && h->launch_err == cudaSuccess) {
     h->launch_err = le;
@@ -432,7 +465,7 @@ static void launch_smem(amr_mesh *h, int kid, void (*kern)(KArgs...), dim3 grid,
     e0 = take_event(h);
     cudaEventRecord(e0, h->s);
   }
-  kern<<<grid, block, smem, h->s>>>(std::forward<Args>(args)...);
+  launch_on(h, kern, grid, block, smem, std::forward<Args>(args)...);
   const cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess && h->launch_err == cudaSuccess) {
     h->launch_err = le;
@@ -720,6 +753,7 @@ static void run_list(amr_mesh *h, int kid, void (*kern)(StepArgs<T>), StepArgs<T
     }
     grid = std::min(a.ntiles, per_sm * h->sm_count);
   }
+  PdlScope pdl(h);  // every kernel of the work lists begins with grid_dep_wait()
   launch(h, kid, kern, dim3(unsigned(grid)), dim3(unsigned(h->tile_size)), a);
 }
 
@@ -743,6 +777,7 @@ static void run_rock_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
     h->occ.push_back({(const void *)kern, per_sm});
   }
   const int grid = h->persistent ? std::min(a.ntiles, per_sm * h->sm_count) : a.ntiles;
+  PdlScope pdl(h);
   launch_smem(h, K_ROCK, kern, dim3(unsigned(grid)), dim3(unsigned(Rock<NS>::THREADS)), smem, a,
               (const int32_t *)h->blk);
 }
@@ -766,6 +801,7 @@ static void run_sweep_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
     h->occ.push_back({(const void *)kern, per_sm});
   }
   const int grid = h->persistent ? std::min(a.ntiles, per_sm * h->sm_count) : a.ntiles;
+  PdlScope pdl(h);
   launch_smem(h, K_SWEEP, kern, dim3(unsigned(grid)), dim3(unsigned(Sweep<NS>::THREADS)), smem, a,
               (const int32_t *)h->blk);
 }
@@ -833,6 +869,9 @@ static CflArgs cfl_args(amr_mesh *h) {
   a.msmallr = h->msmallr_d;
   a.msmallp = h->msmallp_d;
   a.mcfl = h->mcfl_d;
+  a.mgamma_t = h->mgamma_t;
+  a.msmallr_t = h->msmallr_t;
+  a.msmallp_t = h->msmallp_t;
   a.mlmin = h->mlmin;
   a.nmembers = h->M;
   a.smax = h->smax;
@@ -847,6 +886,7 @@ static CflArgs cfl_args(amr_mesh *h) {
 }
 
 static void cfl_device(amr_mesh *h, int consume) {
+  PdlScope pdl(h);  // k_cfl and k_dt begin with grid_dep_wait()
   CflArgs a = cfl_args(h);
   a.consume = consume;
   const unsigned grid = unsigned(std::min(a.ntiles, 4 * h->sm_count));

@@ -88,6 +88,7 @@ struct CflArgs {
   int64_t S;
   const uint32_t *son;
   const double *mgamma, *msmallr, *msmallp, *mcfl;
+  const void *mgamma_t, *msmallr_t, *msmallp_t;  // the same in the state's type
   const int *mlmin;
   int nmembers;
   unsigned long long *smax;  // [16 * members] bit patterns of per-level maxima

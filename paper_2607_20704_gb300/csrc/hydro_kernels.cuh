@@ -71,6 +71,7 @@ __device__ __forceinline__ bool finite_bits(float x) {
 __device__ __forceinline__ bool gt_nonneg(double a, double b) {
   return __double_as_longlong(a) > __double_as_longlong(b);
 }
+__device__ __forceinline__ bool gt_nonneg(float a, float b) { return __float_as_int(a) > __float_as_int(b); }
 __device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
 
@@ -152,6 +153,7 @@ __device__ __forceinline__ SegCtx<T> seg_ctx(const StepArgs<T> &a, int seg) {
 // the tile that lies inside the segment's domain of `size(ctx)` items
 template <class T, class Size, class Body>
 __device__ __forceinline__ void tile_loop(const StepArgs<T> &a, Size size, Body body) {
+  grid_dep_wait();
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
     const Tile td = tile_at(a.tpre, a.tseg0, a.tnseg, a.tstep, ti);
     if (a.mact && !__ldg(a.mact + a.segs[td.seg].member)) continue;  // finished member
@@ -668,24 +670,30 @@ __device__ __forceinline__ void cfl_flush(const CflArgs &a, double s, int seg, d
 
 // Each block keeps a running maximum per thread while its tiles stay in one
 // segment and reduces it (one atomicMax) when the segment changes.
+// The running maximum is kept in the state's type (float to double is exact
+// and monotonic, so converting once per flush gives the same maximum) and
+// the parameters are read in that type: no conversions per cell, which would
+// run on the FP64 pipe.
 template <class T>
 __global__ void k_cfl(CflArgs a, const T *U) {
+  grid_dep_wait();
   __shared__ double wmax[32];
-  double s = 0.0;
+  T s = T(0);
   int cur = -1;
+  const T *mgamma = static_cast<const T *>(a.mgamma_t), *msmallr = static_cast<const T *>(a.msmallr_t),
+          *msmallp = static_cast<const T *>(a.msmallp_t);
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
     const Tile td = tile_at(a.tpre, a.tseg0, a.tnseg, a.tstep, ti);
     if (td.seg != cur) {
-      if (cur >= 0) cfl_flush<T>(a, s, cur, wmax);
-      s = 0.0;
+      if (cur >= 0) cfl_flush<T>(a, double(s), cur, wmax);
+      s = T(0);
       cur = td.seg;
     }
     const Seg sg = a.segs[td.seg];
     const int t = td.start + threadIdx.x;
     if (t < 8 * sg.nl && a.mrem[sg.member] != 0 &&
         !((__ldg(a.son + sg.lo + (t >> 3)) >> (t & 7)) & 1u)) {
-      const T g = T(a.mgamma[sg.member]), smallr = T(a.msmallr[sg.member]),
-              smallp = T(a.msmallp[sg.member]);
+      const T g = mgamma[sg.member], smallr = msmallr[sg.member], smallp = msmallp[sg.member];
       const int64_t gi = 8 * int64_t(sg.lo) + t;
       const T u0 = U[gi], u1 = U[a.S + gi], u2 = U[2 * a.S + gi], u3 = U[3 * a.S + gi],
               u4 = U[4 * a.S + gi];
@@ -700,15 +708,16 @@ __global__ void k_cfl(CflArgs a, const T *U) {
                                 finite_bits(u3) && finite_bits(u4))) {
         atomicOr(a.err, kErrNaN);
         atomicOr(a.merr + sg.member, kErrNaN);
-      } else if (gt_nonneg(double(st), s)) {
-        s = double(st);
+      } else if (gt_nonneg(st, s)) {
+        s = st;
       }
     }
   }
-  if (cur >= 0) cfl_flush<T>(a, s, cur, wmax);
+  if (cur >= 0) cfl_flush<T>(a, double(s), cur, wmax);
 }
 
 __global__ void k_dt(CflArgs a) {
+  grid_dep_wait();
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= a.nmembers) return;
   const int lmin = a.mlmin[m];
