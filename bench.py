@@ -204,8 +204,8 @@ def kernel_traffic(info, levelmin, w, fused):
 # faces), and DRAM bytes per cell of the flux kernels, from one ncu capture
 # of the level-7 launch of the benchmark mesh (ncu: FP64 instruction counts,
 # dram__bytes_read.sum + dram__bytes_write.sum)
-FLUX_FP64_FLOPS_PER_CELL = 310.7
-FLUX_DRAM_BYTES_PER_CELL = {8: 272.8, 4: 126.9}
+FLUX_FP64_FLOPS_PER_CELL = 289.8
+FLUX_DRAM_BYTES_PER_CELL = {8: 272.7, 4: 125.8}
 
 
 def load_peaks():
