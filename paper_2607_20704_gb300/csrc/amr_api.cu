@@ -237,9 +237,6 @@ struct amr_mesh {
   // a mesh built from flags that went through the grading closure skips the
   // (27-probe per oct) grading check, except in the bounds-checked build
   bool graded_by_construction = false;
-  // launches of the level-step and time-step kernels (which wait on their
-  // predecessors themselves) use programmatic stream serialization
-  bool pdl = false;
   // Poisson on a refined level: per MG level the tables of k_mgl_*, the
   // level's cells (g0: global cell index), their fathers and the coarse cells
   // across boundary faces; the potential of every cell (mesh order)
@@ -397,35 +394,12 @@ static cudaEvent_t take_event(amr_mesh *h) {
   return e;
 }
 
-// one launch on the handle's stream; with h->pdl the kernel may be scheduled
-// while its predecessor drains (it waits for it with griddepcontrol.wait)
+// one launch on the handle's stream
 template <typename... KArgs, typename... Args>
 static void launch_on(amr_mesh *h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                       Args &&...args) {
-  if (!h->pdl) {
-    kern<<<grid, block, smem, h->s>>>(std::forward<Args>(args)...);
-    return;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = h->s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  kern<<<grid, block, smem, h->s>>>(std::forward<Args>(args)...);
 }
-
-// kernels launched inside this scope start with grid_dep_wait()
-struct PdlScope {
-  amr_mesh *h;
-  bool old;
-  explicit PdlScope(amr_mesh *hh) : h(hh), old(hh->pdl) { h->pdl = true; }
-  ~PdlScope() { h->pdl = old; }
-};
 
 template <typename... KArgs, typename... Args>
 static void launch(amr_mesh *h, int kid, void (*kern)(KArgs...), dim3 grid, dim3 block,
@@ -753,7 +727,6 @@ static void run_list(amr_mesh *h, int kid, void (*kern)(StepArgs<T>), StepArgs<T
     }
     grid = std::min(a.ntiles, per_sm * h->sm_count);
   }
-  PdlScope pdl(h);  // every kernel of the work lists begins with grid_dep_wait()
   launch(h, kid, kern, dim3(unsigned(grid)), dim3(unsigned(h->tile_size)), a);
 }
 
@@ -777,7 +750,6 @@ static void run_rock_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
     h->occ.push_back({(const void *)kern, per_sm});
   }
   const int grid = h->persistent ? std::min(a.ntiles, per_sm * h->sm_count) : a.ntiles;
-  PdlScope pdl(h);
   launch_smem(h, K_ROCK, kern, dim3(unsigned(grid)), dim3(unsigned(Rock<NS>::THREADS)), smem, a,
               (const int32_t *)h->blk);
 }
@@ -801,7 +773,6 @@ static void run_sweep_ns(amr_mesh *h, StepArgs<T> a, const SegList &L) {
     h->occ.push_back({(const void *)kern, per_sm});
   }
   const int grid = h->persistent ? std::min(a.ntiles, per_sm * h->sm_count) : a.ntiles;
-  PdlScope pdl(h);
   launch_smem(h, K_SWEEP, kern, dim3(unsigned(grid)), dim3(unsigned(Sweep<NS>::THREADS)), smem, a,
               (const int32_t *)h->blk);
 }
@@ -886,7 +857,6 @@ static CflArgs cfl_args(amr_mesh *h) {
 }
 
 static void cfl_device(amr_mesh *h, int consume) {
-  PdlScope pdl(h);  // k_cfl and k_dt begin with grid_dep_wait()
   CflArgs a = cfl_args(h);
   a.consume = consume;
   const unsigned grid = unsigned(std::min(a.ntiles, 4 * h->sm_count));

@@ -201,14 +201,6 @@ __device__ __forceinline__ int32_t hash_probe8(HashView h, uint64_t key) {
 }
 
 // Single-thread lookup (for sparse use inside other kernels).
-// Wait until the grids this one depends on have completed and their writes
-// are visible.  The level-step kernels are launched with programmatic
-// stream serialization, so a kernel's blocks may be scheduled while the
-// previous kernel drains (hiding the launch gap between dependent kernels);
-// each such kernel calls this before touching any data.  A no-op for a
-// normal launch.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 __device__ __forceinline__ int32_t hash_probe1(HashView h, uint64_t key) {
   uint64_t s = fnv1a64(key) & h.mask;
   for (uint64_t n = 0; n <= h.mask; ++n) {

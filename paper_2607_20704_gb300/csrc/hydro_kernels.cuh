@@ -153,7 +153,6 @@ __device__ __forceinline__ SegCtx<T> seg_ctx(const StepArgs<T> &a, int seg) {
 // the tile that lies inside the segment's domain of `size(ctx)` items
 template <class T, class Size, class Body>
 __device__ __forceinline__ void tile_loop(const StepArgs<T> &a, Size size, Body body) {
-  grid_dep_wait();
   for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
     const Tile td = tile_at(a.tpre, a.tseg0, a.tnseg, a.tstep, ti);
     if (a.mact && !__ldg(a.mact + a.segs[td.seg].member)) continue;  // finished member
@@ -676,7 +675,6 @@ __device__ __forceinline__ void cfl_flush(const CflArgs &a, double s, int seg, d
 // run on the FP64 pipe.
 template <class T>
 __global__ void k_cfl(CflArgs a, const T *U) {
-  grid_dep_wait();
   __shared__ double wmax[32];
   T s = T(0);
   int cur = -1;
@@ -717,7 +715,6 @@ __global__ void k_cfl(CflArgs a, const T *U) {
 }
 
 __global__ void k_dt(CflArgs a) {
-  grid_dep_wait();
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= a.nmembers) return;
   const int lmin = a.mlmin[m];

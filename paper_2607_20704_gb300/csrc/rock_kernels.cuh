@@ -217,7 +217,6 @@ __global__ void __launch_bounds__(Rock<NS>::THREADS, Rock<NS>::template min_bloc
   constexpr int E = R::E, C = R::C, NO = R::NO, NOC = R::NOC, NB = R::NB, IN = R::IN, IC = R::IC,
                 RC = R::RC, FS = R::FS, TH = R::THREADS;
   constexpr int LIN = NS == 4 ? 3 : NS == 2 ? 2 : 1;  // log2(IN)
-  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char rock_smem[];
   T *sP = reinterpret_cast<T *>(rock_smem);  // [5][C]: primitives of the cube
   T *sF = sP;                                // [3][5][FS]: fluxes (phase D on)
@@ -551,7 +550,6 @@ struct Sweep {
 
 template <class T, int NS>
 __global__ void __launch_bounds__(Sweep<NS>::THREADS) k_sweep(StepArgs<T> a, const int32_t *__restrict__ blk) {
-  grid_dep_wait();
   using R = Sweep<NS>;
   extern __shared__ __align__(16) unsigned char sweep_smem[];
   T *sW = reinterpret_cast<T *>(sweep_smem);  // [3][5][P]: primitives, plane z at slot z % 3
