@@ -47,6 +47,14 @@ __global__ void k_make_sort_keys(const uint8_t *__restrict__ lvl, const uint32_t
 constexpr int kRadixTile = 256;
 constexpr int kTile = kRadixTile;
 
+// counter[key] += 1 for every calling lane, one atomic per distinct key in
+// the warp (sorted inputs give one key per warp: the per-lane atomics on a
+// handful of counters serialised at the memory system)
+__device__ __forceinline__ void warp_count(uint32_t *counter, int key) {
+  const unsigned peers = __match_any_sync(__activemask(), key);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(counter + key, uint32_t(__popc(peers)));
+}
+
 __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int shift, int nbits,
                              uint32_t *__restrict__ table, int64_t ntiles) {
   __shared__ uint32_t hist[256];
@@ -54,7 +62,7 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int s
   for (int d = threadIdx.x; d < ndig; d += blockDim.x) hist[d] = 0;
   __syncthreads();
   const int64_t t = blockIdx.x * int64_t(kTile) + threadIdx.x;
-  if (t < n) atomicAdd(&hist[(keys[t] >> shift) & uint64_t(ndig - 1)], 1u);
+  if (t < n) warp_count(hist, int((keys[t] >> shift) & uint64_t(ndig - 1)));
   __syncthreads();
   for (int d = threadIdx.x; d < ndig; d += blockDim.x) table[int64_t(d) * ntiles + blockIdx.x] = hist[d];
 }
@@ -106,7 +114,7 @@ __global__ void k_gather_octs(const uint32_t *__restrict__ perm, const uint8_t *
   if (t >= n) return;
   const uint32_t s = perm[t];
   key[t] = ikey(mem[s], lvl[s], ci[s], cj[s], ck[s]);
-  if (seg_count) atomicAdd(seg_count + 16 * int(mem[s]) + lvl[s], 1u);
+  if (seg_count) warp_count(seg_count, 16 * int(mem[s]) + lvl[s]);
   if (!U) return;
   for (int v = 0; v < kNV; ++v)
 #pragma unroll
@@ -206,7 +214,13 @@ __global__ void k_neighbours(HashView h, const uint64_t *__restrict__ key, int64
   const uint64_t s = hash_insert(h, nk, &ins, err);
   if (ins && s != ~0ull) {
     h.val[s] = kPending;
-    const uint32_t slot = atomicAdd(claim_count, 1u);
+    // one atomic per warp for its new claims (their order is sorted away)
+    const unsigned grp = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(claim_count, uint32_t(__popc(grp)));
+    base = __shfl_sync(grp, base, leader);
+    const uint32_t slot = base + uint32_t(__popc(grp & ((1u << lane) - 1u)));
     if (int64_t(slot) < claim_cap)
       claim[slot] = nk;
     else
@@ -236,7 +250,7 @@ __global__ void k_cache_finalize(HashView h, const uint64_t *__restrict__ comp, 
   const int m = int(c >> (4 + 3 * B));
   const uint64_t k = ikey(m, l, uint32_t((c >> (2 * B)) & msk), uint32_t((c >> B) & msk), uint32_t(c & msk));
   ckey[s] = k;
-  if (seg_count) atomicAdd(seg_count + 16 * m + l, 1u);
+  if (seg_count) warp_count(seg_count, 16 * m + l);
   uint64_t p = fnv1a64(k) & h.mask;
   for (uint64_t r = 0; r <= h.mask; ++r) {
     if (h.key[p] == k) {
