@@ -535,6 +535,8 @@ typedef struct {
   int tile, schedule;         /* work-tile size and schedule in use */
   int nsubgrid;               /* level-step kernel in use (amr_params.nsubgrid) */
   int planar;                 /* 1: the fused kernel sweeps planes (amr_params.planar) */
+  int64_t cached_bytes;       /* device arrays a regrid retired, kept for the next one
+                                 (at most the live mesh's size; 0 with a device budget) */
 } amr_info;
 
 /* Counts of the mesh and of the work done so far. */

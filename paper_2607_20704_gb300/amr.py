@@ -52,7 +52,7 @@ class amr_info(C.Structure):
                 ("work_per_step", C.c_int64),
                 ("precision", C.c_int), ("n_members", C.c_int), ("member", C.c_int),
                 ("phases", C.c_int), ("tile", C.c_int), ("schedule", C.c_int),
-                ("nsubgrid", C.c_int), ("planar", C.c_int)]
+                ("nsubgrid", C.c_int), ("planar", C.c_int), ("cached_bytes", C.c_int64)]
 
 
 class amr_member(C.Structure):
@@ -674,6 +674,7 @@ class Mesh:
             "work_per_step": inf.work_per_step, "n_members": inf.n_members,
             "member": inf.member, "phases": inf.phases, "tile": inf.tile,
             "schedule": inf.schedule, "nsubgrid": inf.nsubgrid, "planar": inf.planar,
+            "cached_bytes": inf.cached_bytes,
         }
 
     def set_timing(self, on: bool):

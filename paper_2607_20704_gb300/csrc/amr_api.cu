@@ -3199,6 +3199,7 @@ extern "C" amr_status amr_get_info(amr_handle h, amr_info *info) {
     info->level_leaf_cells[l] = m.leaf[l];
   }
   info->device_bytes = int64_t(h->bytes);
+  info->cached_bytes = h->cache ? int64_t(h->cache->bytes) : 0;
   info->kernel_launches = h->launches;
   info->graph_launches = h->graph_launches;
   info->hash_capacity = int64_t(h->hcap);

@@ -277,6 +277,32 @@ def test_batched_regrid_equals_each_member_alone(precision):
     b.close()
 
 
+def test_regrids_reuse_retired_arrays_within_the_live_size():
+    """A regrid's new mesh takes its arrays from those the previous regrid
+    retired; the kept arrays never exceed the live mesh's size, results are
+    the same as without the cache (a handle with a device budget keeps none),
+    and after many regrids the device holds at most twice the live mesh."""
+    from paper_2607_20704_gb300 import amr
+    prob = inputs.sedov(4, 6, radii={5: 0.15, 6: 0.08})
+    kw = dict(refine_grad_rho=0.1, refine_grad_p=0.1)
+    a = amr.Mesh(*prob.mesh_args(), **prob.params(), **kw)
+    b = amr.Mesh(*prob.mesh_args(), **prob.params(), hbm_budget_bytes=8 << 30, **kw)
+    for _ in range(8):
+        assert a.regrid() == b.regrid()
+        a.advance(1)
+        b.advance(1)
+        ia, ib = a.info(), b.info()
+        assert ia["cached_bytes"] <= ia["device_bytes"], ia
+        assert ib["cached_bytes"] == 0, ib
+    assert a.levels() == b.levels()
+    for l in a.levels():
+        ka, Ua = a.read(l)
+        kb, Ub = b.read(l)
+        assert np.array_equal(ka, kb) and np.array_equal(Ua, Ub), l
+    a.close()
+    b.close()
+
+
 def test_zz_report_near_threshold_cells():
     """The number of near-threshold decisions the tests above met (every
     other cell's flag was compared bit for bit)."""
