@@ -48,8 +48,9 @@ constexpr int kRadixTile = 256;
 constexpr int kTile = kRadixTile;
 
 // counter[key] += 1 for every calling lane, one atomic per distinct key in
-// the warp (sorted inputs give one key per warp: the per-lane atomics on a
-// handful of counters serialised at the memory system)
+// the warp (sorted inputs give one key per warp: per-lane global atomics on a
+// handful of counters serialised at the memory system; shared-memory
+// histograms keep per-lane atomics, which are faster there than the match)
 __device__ __forceinline__ void warp_count(uint32_t *counter, int key) {
   const unsigned peers = __match_any_sync(__activemask(), key);
   if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(counter + key, uint32_t(__popc(peers)));
@@ -62,7 +63,7 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t n, int s
   for (int d = threadIdx.x; d < ndig; d += blockDim.x) hist[d] = 0;
   __syncthreads();
   const int64_t t = blockIdx.x * int64_t(kTile) + threadIdx.x;
-  if (t < n) warp_count(hist, int((keys[t] >> shift) & uint64_t(ndig - 1)));
+  if (t < n) atomicAdd(&hist[(keys[t] >> shift) & uint64_t(ndig - 1)], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < ndig; d += blockDim.x) table[int64_t(d) * ntiles + blockIdx.x] = hist[d];
 }
