@@ -1194,7 +1194,9 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
          (const uint32_t *)d_i, (const uint32_t *)d_j, (const uint32_t *)d_k,
          (const uint16_t *)d_mem, (const uint64_t *)d_hk, n, (const int *)h->mlmin,
          (const int *)h->mlmax, comp, perm, h->err);
-  AMR_TRY(check_device(h, "amr_create"));
+  // a caller's oct list is validated before it is sorted; a regrid's (d_new
+  // set) comes from a checked mesh and is checked with the rest below
+  if (!d_new) AMR_TRY(check_device(h, "amr_create"));
   const int hbits = have_hk ? kHilbertBits : 3 * (h->lmax_all - 1);
   std::vector<std::pair<int, int>> digits = digits_for(0, hbits);
   digits.push_back({kHilbertBits, 4});  // level bucket sort
@@ -1402,8 +1404,7 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   dev_free(h, perm_alt);
   dev_free(h, comp);
   dev_free(h, comp_alt);
-  CUDA_TRY(cudaStreamSynchronize(h->s));
-  return AMR_OK;
+  return AMR_OK;  // the frees are stream-ordered
 }
 
 static amr_status check_member(const amr_member &a, int q) {
