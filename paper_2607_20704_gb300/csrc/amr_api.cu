@@ -1811,10 +1811,9 @@ extern "C" amr_status amr_load_state_async(amr_handle h, const double *U, int64_
   CUDA_TRY(cudaEventRecord(h->ev_in_ready, h->cs));
   // compute stream: after the work already queued, take the input into U
   CUDA_TRY(cudaStreamWaitEvent(h->s, h->ev_in_ready, 0));
-  if (h->p.precision == 8) {
-    for (int v = 0; v < 5; ++v)
-      CUDA_TRY(cudaMemcpyAsync(static_cast<double *>(h->U) + v * h->S + first, h->st_in + v * count,
-                               sizeof(double) * count, cudaMemcpyDeviceToDevice, h->s));
+  if (h->p.precision == 8) {  // one copy kernel for the five rows (copy engines ran at about 2.3 TB/s)
+    launch(h, K_CONVERT, k_rows_copy, dim3(nblocks(5 * count / 2)), dim3(256), (const double2 *)h->st_in,
+           count / 2, count / 2, reinterpret_cast<double2 *>(static_cast<double *>(h->U) + first), h->S / 2);
   } else {
     launch(h, K_CONVERT, k_from_double<float>, dim3(nblocks(5 * count)), dim3(256), (const double *)h->st_in,
            count, static_cast<float *>(h->U) + first, h->S);
@@ -1834,9 +1833,9 @@ extern "C" amr_status amr_store_state_async(amr_handle h, double *U, int64_t cap
   // compute stream: once the previous output has left, snapshot U
   CUDA_TRY(cudaStreamWaitEvent(h->s, h->ev_out_free, 0));
   if (h->p.precision == 8) {
-    for (int v = 0; v < 5; ++v)
-      CUDA_TRY(cudaMemcpyAsync(h->st_out + v * count, static_cast<const double *>(h->U) + v * h->S + first,
-                               sizeof(double) * count, cudaMemcpyDeviceToDevice, h->s));
+    launch(h, K_CONVERT, k_rows_copy, dim3(nblocks(5 * count / 2)), dim3(256),
+           reinterpret_cast<const double2 *>(static_cast<const double *>(h->U) + first), h->S / 2, count / 2,
+           reinterpret_cast<double2 *>(h->st_out), count / 2);
   } else {
     launch(h, K_CONVERT, k_to_double<float>, dim3(nblocks(5 * count)), dim3(256),
            static_cast<const float *>(h->U) + first, h->S, count, h->st_out);

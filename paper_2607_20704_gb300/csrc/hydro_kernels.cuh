@@ -801,6 +801,17 @@ __global__ void k_to_double(const T *src, int64_t src_stride, int64_t count, dou
   const int v = int(q / count);
   dst[q] = double(src[v * src_stride + q % count]);
 }
+// five rows of `count` doubles from src (row stride src_stride) to dst (row
+// stride dst_stride), 16 bytes per thread; count and both strides even, both
+// bases 16-byte aligned (the state's rows start at multiples of 8 cells)
+__global__ void k_rows_copy(const double2 *__restrict__ src, int64_t src_stride2, int64_t count2,
+                            double2 *__restrict__ dst, int64_t dst_stride2) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= 5 * count2) return;
+  const int64_t v = q / count2, j = q - v * count2;
+  dst[v * dst_stride2 + j] = __ldg(src + v * src_stride2 + j);
+}
+
 template <class T>
 __global__ void k_from_double(const double *src, int64_t count, T *dst, int64_t dst_stride) {
   const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
