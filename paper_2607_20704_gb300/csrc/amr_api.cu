@@ -237,6 +237,9 @@ struct amr_mesh {
   // a mesh built from flags that went through the grading closure skips the
   // (27-probe per oct) grading check, except in the bounds-checked build
   bool graded_by_construction = false;
+  // the octs' order came from keys computed here (not from the caller's
+  // Hilbert keys), so a regrid's kept octs are already in sorted order
+  bool order_computed = false;
   // Poisson on a refined level: per MG level the tables of k_mgl_*, the
   // level's cells (g0: global cell index), their fathers and the coarse cells
   // across boundary faces; the potential of every cell (mesh order)
@@ -1095,7 +1098,7 @@ static amr_status build_blocks(amr_mesh *h);
 
 static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
                              uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
-                             double *d_U, uint8_t *d_new);
+                             double *d_U, uint8_t *d_new, int64_t sorted_prefix = 0);
 
 static amr_status create_impl(amr_mesh *h, const amr_member *members) {
   const int M = h->M;
@@ -1166,7 +1169,7 @@ static void mgl_free(amr_mesh *h);
 // restriction.  Frees the inputs.
 static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
                              uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
-                             double *d_U, uint8_t *d_new) {
+                             double *d_U, uint8_t *d_new, int64_t sorted_prefix) {
   const amr_params &p = h->p;
   const int M = h->M;
   // a new set of octs: the refined-level potential and its tables go
@@ -1203,7 +1206,26 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   for (auto &d : digits_for(kHilbertBits + 4, bits_for(M))) digits.push_back(d);
   uint64_t *kk = comp;
   uint32_t *vv = perm;
-  radix_sort(h, &kk, &vv, comp_alt, perm_alt, n, digits);
+  const int64_t n_new = n - sorted_prefix;
+  if (sorted_prefix > 0 && n_new >= 0 && n_new <= kSmallSort) {
+    // a regrid: the kept octs [0, sorted_prefix) are in order; sort the new
+    // ones in one block and merge the two runs by rank
+    if (n_new > 0) {
+      launch(h, K_SORT_KEYS, k_sort_small, dim3(1), dim3(1024), comp + sorted_prefix, perm + sorted_prefix,
+             int(n_new));
+      launch(h, K_SORT_KEYS, k_merge_rank, dim3(nblocks(sorted_prefix)), dim3(256), (const uint64_t *)comp,
+             (const uint32_t *)perm, sorted_prefix, (const uint64_t *)(comp + sorted_prefix), n_new, comp_alt,
+             perm_alt);
+      launch(h, K_SORT_KEYS, k_merge_rank, dim3(nblocks(n_new)), dim3(256),
+             (const uint64_t *)(comp + sorted_prefix), (const uint32_t *)(perm + sorted_prefix), n_new,
+             (const uint64_t *)comp, sorted_prefix, comp_alt, perm_alt);
+      kk = comp_alt;
+      vv = perm_alt;
+    }
+  } else {
+    radix_sort(h, &kk, &vv, comp_alt, perm_alt, n, digits);
+  }
+  h->order_computed = !have_hk;
 
   // --- keys in mesh order, (member, level) offsets ----------------------------------
   AMR_TRY(alloc_n(h, &h->key, n));
@@ -2119,7 +2141,8 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   nh->cs_cap = h->cs_cap;
   h->W = h->Q = h->F = h->C = nullptr;
   h->ls_cap = h->cs_cap = 0;
-  if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, d_U, d_new)) != AMR_OK)
+  if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, d_U, d_new,
+                       h->order_computed ? K : 0)) != AMR_OK)
     return abandon(st);
   // carry the per-member step counters and last time steps over
   cudaMemcpyAsync(nh->mrem, h->mrem, sizeof(int) * h->M, cudaMemcpyDeviceToDevice, h->s);

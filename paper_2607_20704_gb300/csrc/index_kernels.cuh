@@ -40,6 +40,71 @@ __global__ void k_make_sort_keys(const uint8_t *__restrict__ lvl, const uint32_t
 }
 
 // ---------------------------------------------------------------------------
+// a regrid's new oct list: the kept octs in their old (sorted) order, then the
+// new octs.  When the new ones are few, they are sorted by one block and
+// merged by rank instead of radix-sorting the whole list (same order: the
+// keys are unique)
+// ---------------------------------------------------------------------------
+constexpr int kSmallSort = 2048;
+
+// ascending bitonic sort of n <= kSmallSort (key, value) pairs in place; one
+// block of 1024 threads, padded with the largest key
+__global__ void __launch_bounds__(1024) k_sort_small(uint64_t *__restrict__ key, uint32_t *__restrict__ val,
+                                                     int n) {
+  __shared__ uint64_t sk[kSmallSort];
+  __shared__ uint32_t sv[kSmallSort];
+  for (int t = threadIdx.x; t < kSmallSort; t += blockDim.x) {
+    sk[t] = t < n ? key[t] : ~0ull;
+    sv[t] = t < n ? val[t] : 0u;
+  }
+  __syncthreads();
+  for (int size = 2; size <= kSmallSort; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < kSmallSort / 2; t += blockDim.x) {
+        const int lo = 2 * t - (t & (stride - 1));  // first index of the pair
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        if ((sk[lo] > sk[hi]) == up) {
+          const uint64_t k = sk[lo];
+          sk[lo] = sk[hi];
+          sk[hi] = k;
+          const uint32_t v = sv[lo];
+          sv[lo] = sv[hi];
+          sv[hi] = v;
+        }
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    key[t] = sk[t];
+    val[t] = sv[t];
+  }
+}
+
+// number of keys of the sorted a[0..n) below x
+__device__ __forceinline__ int64_t count_below(const uint64_t *__restrict__ a, int64_t n, uint64_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// place every item of the sorted run a (na items) at its rank in the merge
+// with the sorted run b (nb items)
+__global__ void k_merge_rank(const uint64_t *__restrict__ ak, const uint32_t *__restrict__ av, int64_t na,
+                             const uint64_t *__restrict__ bk, int64_t nb, uint64_t *__restrict__ ok,
+                             uint32_t *__restrict__ ov) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= na) return;
+  const uint64_t k = ak[i];
+  const int64_t r = i + count_below(bk, nb, k);
+  ok[r] = k;
+  ov[r] = av[i];
+}
+
+// ---------------------------------------------------------------------------
 // stable LSD radix sort of (u64 key, u32 value) pairs, one item per thread,
 // 256-item tiles: tile histograms -> exclusive scan (digit-major) -> scatter
 // with warp-level ranks (one ballot per digit bit) and a warp-ordered prefix.
