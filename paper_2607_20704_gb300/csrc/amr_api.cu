@@ -316,6 +316,13 @@ static amr_status dev_alloc(amr_mesh *h, void **out, size_t bytes) {
       return AMR_OK;
     }
   }
+  // a handle that regrids asks for arrays a little larger each time a mesh
+  // grows: a fresh large array gets 1/8 headroom, so that the next mesh's
+  // request still fits the cached array instead of a new allocation
+  if (h->cache && bytes >= (size_t(1) << 20)) {
+    const size_t wide = (bytes + bytes / 8 + 65535) & ~size_t(65535);
+    if (!h->p.hbm_budget_bytes || h->bytes + wide <= h->p.hbm_budget_bytes) bytes = wide;
+  }
   if (h->p.alloc) {
     ptr = h->p.alloc(bytes, (void *)h->s, h->p.alloc_user);
     if (!ptr) return fail(AMR_ENOMEM, "caller allocator refused %zu bytes", bytes);
