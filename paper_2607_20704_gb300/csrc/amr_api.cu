@@ -122,6 +122,17 @@ struct BufCache {
   size_t bytes = 0, cap = 0;
 };
 
+// page-locked words for small device-to-host reads: several reads queued on
+// the stream complete with one synchronisation (a read into pageable memory
+// waits for the stream on its own)
+struct HostPin {
+  uint32_t *w = nullptr;  // w[0]: the device error word; w[1..cap): data
+  size_t cap = 0;
+  ~HostPin() {
+    if (w) cudaFreeHost(w);
+  }
+};
+
 // level-step launch domains of a segment
 enum Dom {
   DOM_CELLS = 0, DOM_REAL = 1, DOM_GHOST5 = 2, DOM_POST = 3, DOM_BLOCKS = 4, DOM_COMMIT = 5, DOM_COUNT = 6
@@ -158,6 +169,7 @@ struct amr_mesh {
   size_t bytes = 0;
   std::vector<DevBuf> bufs;
   std::shared_ptr<BufCache> cache;
+  std::shared_ptr<HostPin> pin;  // shared with the handle's regrid shells
 
   int M = 1, sel = 0, lmax_all = 1;
   std::vector<Member> mem;
@@ -468,8 +480,9 @@ static void launch_smem(amr_mesh *h, int kid, void (*kern)(KArgs...), dim3 grid,
 
 static inline unsigned nblocks(int64_t n, int b = 256) { return unsigned((n + b - 1) / b); }
 
-// device error word -> status
-static amr_status check_device(amr_mesh *h, const char *where) {
+// check_device without a synchronisation: launch errors only (the device
+// error word is read at the next check_device)
+static amr_status check_launches(amr_mesh *h, const char *where) {
   if (h->launch_err != cudaSuccess) {
     const cudaError_t le = h->launch_err;
     h->launch_err = cudaSuccess;
@@ -478,6 +491,12 @@ static amr_status check_device(amr_mesh *h, const char *where) {
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(AMR_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+  return AMR_OK;
+}
+
+// device error word -> status
+static amr_status check_device(amr_mesh *h, const char *where) {
+  AMR_TRY(check_launches(h, where));
   int err = 0;
   CUDA_TRY(cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   CUDA_TRY(cudaStreamSynchronize(h->s));
@@ -492,6 +511,50 @@ static amr_status check_device(amr_mesh *h, const char *where) {
   if (err & kErrIndex)
     return fail(AMR_ECUDA, "%s: an index-table entry out of range (bounds-checked build)", where);
   return fail(AMR_ECUDA, "%s: internal index error (bits 0x%x)", where, err);
+}
+
+// the handle's page-locked read-back words, room for n data words (grown at
+// need; w[0] is kept for the device error word)
+static amr_status pinned_words(amr_mesh *h, size_t n, uint32_t **out) {
+  if (!h->pin) h->pin = std::make_shared<HostPin>();
+  HostPin &P = *h->pin;
+  if (P.cap < n + 1) {
+    if (P.w) {
+      CUDA_TRY(cudaStreamSynchronize(h->s));  // no read in flight into the old words
+      cudaFreeHost(P.w);
+      P.w = nullptr;
+      P.cap = 0;
+    }
+    const size_t cap = std::max<size_t>(1024, n + 1);
+    void *p = nullptr;
+    CUDA_TRY(cudaMallocHost(&p, sizeof(uint32_t) * cap));
+    P.w = static_cast<uint32_t *>(p);
+    P.cap = cap;
+  }
+  *out = P.w + 1;
+  return AMR_OK;
+}
+
+// queue a read of n device words into the data words [at, at + n), within
+// the room a pinned_words call made before the first read of the batch
+static amr_status read_words(amr_mesh *h, size_t at, const void *src, size_t n) {
+  if (!h->pin || !h->pin->w || at + n + 1 > h->pin->cap)
+    return fail(AMR_ECUDA, "internal: read-back of %zu words beyond the page-locked room", at + n);
+  uint32_t *w = h->pin->w + 1;
+  CUDA_TRY(cudaMemcpyAsync(w + at, src, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->s));
+  return AMR_OK;
+}
+
+// check_device with further page-locked reads queued before it: one
+// synchronisation for the error word and the reads
+static amr_status check_device_after_reads(amr_mesh *h, const char *where) {
+  AMR_TRY(check_launches(h, where));
+  uint32_t *w = nullptr;
+  AMR_TRY(pinned_words(h, 0, &w));
+  CUDA_TRY(cudaMemcpyAsync(w - 1, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CUDA_TRY(cudaStreamSynchronize(h->s));
+  if (!w[-1]) return AMR_OK;
+  return check_device(h, where);  // decodes (and clears) the error word
 }
 
 // ---------------------------------------------------------------------------
@@ -903,11 +966,11 @@ static amr_status build_index(amr_mesh *h, bool first) {
   launch(h, K_NEIGHBOURS, k_neighbours, dim3(nblocks(27 * N)), dim3(256), h->hash,
          (const uint64_t *)h->key, N, h->nbr27, h->claim, h->counters, h->claim_cap, h->err);
   if (first) {  // create: stop after the claims; the caller sizes the ghost buffers
-    AMR_TRY(check_device(h, "amr_create"));
-    uint32_t nc = 0;
-    CUDA_TRY(cudaMemcpyAsync(&nc, h->counters, sizeof nc, cudaMemcpyDeviceToHost, h->s));
-    CUDA_TRY(cudaStreamSynchronize(h->s));
-    h->NC = nc;
+    uint32_t *w = nullptr;
+    AMR_TRY(pinned_words(h, 1, &w));
+    AMR_TRY(read_words(h, 0, h->counters, 1));
+    AMR_TRY(check_device_after_reads(h, "amr_create"));
+    h->NC = w[0];
     return AMR_OK;
   }
   if (h->NC > 0) {
@@ -1244,8 +1307,13 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
          (const uint32_t *)d_k, (const uint16_t *)d_mem, (const double *)nullptr, n, h->key,
          (double *)nullptr, int64_t(0), h->seg_count);
   std::vector<uint32_t> counts(16 * size_t(M));
-  CUDA_TRY(cudaMemcpyAsync(counts.data(), h->seg_count, 4 * counts.size(), cudaMemcpyDeviceToHost, h->s));
-  CUDA_TRY(cudaStreamSynchronize(h->s));
+  {
+    uint32_t *w = nullptr;
+    AMR_TRY(pinned_words(h, counts.size(), &w));
+    AMR_TRY(read_words(h, 0, h->seg_count, counts.size()));
+    AMR_TRY(check_device_after_reads(h, "amr_create"));
+    std::memcpy(counts.data(), w, 4 * counts.size());
+  }
   {
     int64_t base = 0;
     for (int q = 0; q < M; ++q) {
@@ -1319,8 +1387,13 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
     launch(h, K_NBR_FIX, k_neighbours_fix, dim3(nblocks(27 * n)), dim3(256), h->hash,
            (const uint64_t *)h->key, n, h->nbr27, h->err);
   }
-  CUDA_TRY(cudaMemcpyAsync(counts.data(), h->seg_count, 4 * counts.size(), cudaMemcpyDeviceToHost, h->s));
-  AMR_TRY(check_device(h, "amr_create"));
+  {
+    uint32_t *w = nullptr;
+    AMR_TRY(pinned_words(h, counts.size(), &w));
+    AMR_TRY(read_words(h, 0, h->seg_count, counts.size()));
+    AMR_TRY(check_device_after_reads(h, "amr_create"));
+    std::memcpy(counts.data(), w, 4 * counts.size());
+  }
   {
     int64_t base = 0;
     for (int q = 0; q < M; ++q) {
@@ -1345,7 +1418,9 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   AMR_TRY(alloc_n(h, &h->csrc, 7 * (NC > 0 ? NC : 1)));
   AMR_TRY(alloc_n(h, &h->rslot, 8 * n));
   build_faces_and_sources(h);
-  AMR_TRY(check_device(h, "amr_create"));
+  // a caller's mesh is checked here; a regrid's, graded by construction, with
+  // its states below
+  AMR_TRY(d_new ? check_launches(h, "amr_create") : check_device(h, "amr_create"));
 
   // --- state in mesh order ---------------------------------------------------------
   const size_t es = h->elem();
@@ -1952,7 +2027,8 @@ static RegridArgs regrid_args(amr_mesh *h, uint32_t *raw, uint32_t *flag) {
 }
 
 // flag, expand and grade: final masks in flag[N]
-static amr_status compute_flags(amr_mesh *h, uint32_t *raw, uint32_t *flag, const char *where) {
+static amr_status compute_flags(amr_mesh *h, uint32_t *raw, uint32_t *flag, const char *where,
+                                bool sync = true) {
   const RegridArgs a = regrid_args(h, raw, flag);
   const unsigned g = nblocks(h->N);
   float *rp = nullptr;  // FP32 rho, p and the pressure's error bound per cell
@@ -1974,7 +2050,7 @@ static amr_status compute_flags(amr_mesh *h, uint32_t *raw, uint32_t *flag, cons
       const int lo = int(m.oct_base + m.lo[l]), hi = int(m.oct_base + m.lo[l + 1]);
       if (hi > lo) launch(h, K_FLAG_GRADE, k_flag_grade, dim3(nblocks(hi - lo)), dim3(256), a, lo, hi);
     }
-  return check_device(h, where);
+  return sync ? check_device(h, where) : check_launches(h, where);
 }
 
 extern "C" amr_status amr_flag(amr_handle h, int level, uint8_t *flags, int64_t cap) {
@@ -2006,6 +2082,7 @@ static amr_mesh *regrid_shell(amr_mesh *h) {
   nh->p = h->p;
   nh->s = h->s;
   nh->cache = h->cache;
+  nh->pin = h->pin;
   nh->own_stream = false;
   nh->device = h->device;
   nh->sm_count = h->sm_count;
@@ -2066,7 +2143,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     if (e != cudaSuccess) REGRID_TRY(fail(AMR_ECUDA, "amr_regrid_flags: %s", cudaGetErrorString(e)));
   } else {
-    REGRID_TRY(compute_flags(h, raw, flag, "amr_regrid"));
+    REGRID_TRY(compute_flags(h, raw, flag, "amr_regrid", false));  // checked with the counts
   }
   const RegridArgs a = regrid_args(h, raw, flag);
   launch(h, K_REGRID, k_regrid_count, dim3(nblocks(N)), dim3(256), a, keep, nnew);
@@ -2074,12 +2151,13 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   cudaMemcpyAsync(npos, nnew, 4 * N, cudaMemcpyDeviceToDevice, h->s);
   scan_exclusive(h, kpos, N, tmp);
   scan_exclusive(h, npos, N, tmp);
-  uint32_t tail[4] = {0, 0, 0, 0};
-  cudaMemcpyAsync(tail + 0, kpos + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
-  cudaMemcpyAsync(tail + 1, keep + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
-  cudaMemcpyAsync(tail + 2, npos + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
-  cudaMemcpyAsync(tail + 3, nnew + N - 1, 4, cudaMemcpyDeviceToHost, h->s);
-  REGRID_TRY(check_device(h, "amr_regrid"));
+  uint32_t *tail = nullptr;
+  REGRID_TRY(pinned_words(h, 4, &tail));
+  REGRID_TRY(read_words(h, 0, kpos + N - 1, 1));
+  REGRID_TRY(read_words(h, 1, keep + N - 1, 1));
+  REGRID_TRY(read_words(h, 2, npos + N - 1, 1));
+  REGRID_TRY(read_words(h, 3, nnew + N - 1, 1));
+  REGRID_TRY(check_device_after_reads(h, "amr_regrid"));
   const int64_t K = int64_t(tail[0]) + tail[1], NN = int64_t(tail[2]) + tail[3];
   if (created) *created = NN;
   if (removed) *removed = N - K;
@@ -2136,7 +2214,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
     launch(h, K_REGRID, k_regrid_emit<double>, dim3(nblocks(N)), dim3(256), a, (const double *)h->U,
            (const uint32_t *)kpos, (const uint32_t *)keep, (const uint32_t *)npos, K, n_out, d_lvl,
            d_mem, d_i, d_j, d_k, d_U, d_new);
-  if ((st = check_device(h, "amr_regrid")) != AMR_OK) return abandon(st);
+  if ((st = check_launches(h, "amr_regrid")) != AMR_OK) return abandon(st);
   release();
   // the level-step scratch goes over to the new mesh (reused if large enough)
   for (void **b : {&h->W, &h->Q, &h->F, &h->C}) move_buf(nh, h, *b);
@@ -2172,7 +2250,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   std::swap(*h, *nh);
   if (h->cache) h->cache->cap = h->bytes;  // the old mesh's arrays serve the next regrid
   destroy_all(nh);
-  return check_device(h, "amr_regrid");
+  return check_launches(h, "amr_regrid");  // the new mesh's error word was read after its build
 #undef REGRID_TRY
 }
 
