@@ -530,13 +530,16 @@ def run_adaptive(prob, precision, steps, torch, device):
         t2 = time.perf_counter()
         t_regrid.append(1e3 * (t1 - t0))
         t_step.append(1e3 * (t2 - t1))
-    # kernel time inside regrids (CUDA events around every launch)
-    m.set_timing(True)
+    # kernel time inside regrids that change the mesh (CUDA events around
+    # every launch of the regrid, none in the steps between them)
     for _ in range(3):
+        m.set_timing(True)
         m.regrid()
+        m.sync()
+        m.set_timing(False)
+        m.advance(1)
     m.sync()
     kt = m.read_timing()
-    m.set_timing(False)
     ktot = sum(v[0] for v in kt.values()) or 1.0
     regrid_kernels = {k: {"ms_per_regrid": round(v[0] / 3, 4), "share": round(v[0] / ktot, 4)}
                       for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])[:8]}

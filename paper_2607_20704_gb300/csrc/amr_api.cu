@@ -1166,9 +1166,18 @@ static amr_status clone_members(amr_mesh *nh, const amr_mesh *h) {
 
 static amr_status build_blocks(amr_mesh *h);
 
+// a regrid's state source: the old mesh's state (the handle's precision,
+// variable stride S) and, per entry of the new oct list, the old oct it keeps
+// (~0 for a new oct)
+struct StateSource {
+  const void *U = nullptr;
+  int64_t S = 0;
+  uint32_t *src = nullptr;
+};
 static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
                              uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
-                             double *d_U, uint8_t *d_new, int64_t sorted_prefix = 0);
+                             double *d_U, uint8_t *d_new, int64_t sorted_prefix = 0,
+                             const StateSource *from = nullptr);
 
 static amr_status create_impl(amr_mesh *h, const amr_member *members) {
   const int M = h->M;
@@ -1234,12 +1243,14 @@ static amr_status create_impl(amr_mesh *h, const amr_member *members) {
 static void mgl_free(amr_mesh *h);
 
 // The mesh from device-resident inputs in any order (create and regrid):
-// order, hash, index, ghost cache, state, lists, scratch; d_new marks octs
-// whose state is to be prolonged from their father (regrid), before the
-// restriction.  Frees the inputs.
+// order, hash, index, ghost cache, state, lists, scratch; the state comes
+// from d_U (FP64, variable stride 8 n) or, in a regrid, from the old mesh
+// (from); d_new marks octs whose state is to be prolonged from their father
+// (regrid), before the restriction.  Frees the inputs.
 static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
                              uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
-                             double *d_U, uint8_t *d_new, int64_t sorted_prefix) {
+                             double *d_U, uint8_t *d_new, int64_t sorted_prefix,
+                             const StateSource *from) {
   const amr_params &p = h->p;
   const int M = h->M;
   // a new set of octs: the refined-level potential and its tables go
@@ -1302,10 +1313,9 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   AMR_TRY(alloc_n(h, &h->counters, 4));
   AMR_TRY(alloc_n(h, &h->seg_count, 16 * int64_t(M)));
   CUDA_TRY(cudaMemsetAsync(h->seg_count, 0, sizeof(uint32_t) * 16 * M, h->s));
-  launch(h, K_GATHER, k_gather_octs<double>, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
+  launch(h, K_GATHER, k_gather_octs, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
          (const uint8_t *)d_lvl, (const uint32_t *)d_i, (const uint32_t *)d_j,
-         (const uint32_t *)d_k, (const uint16_t *)d_mem, (const double *)nullptr, n, h->key,
-         (double *)nullptr, int64_t(0), h->seg_count);
+         (const uint32_t *)d_k, (const uint16_t *)d_mem, n, h->key, h->seg_count);
   std::vector<uint32_t> counts(16 * size_t(M));
   {
     uint32_t *w = nullptr;
@@ -1428,16 +1438,20 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   AMR_TRY(dev_alloc(h, &h->Rc, es * 5 * size_t(NC > 0 ? NC : 1)));
   CUDA_TRY(cudaMemsetAsync(h->U, 0, es * 5 * size_t(h->S), h->s));
   CUDA_TRY(cudaMemsetAsync(h->Rc, 0, es * 5 * size_t(NC > 0 ? NC : 1), h->s));
-  if (p.precision == 4)
-    launch(h, K_GATHER, k_gather_octs<float>, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
-           (const uint8_t *)d_lvl, (const uint32_t *)d_i, (const uint32_t *)d_j,
-           (const uint32_t *)d_k, (const uint16_t *)d_mem, (const double *)d_U, n, h->key,
-           (float *)h->U, h->S, (uint32_t *)nullptr);
-  else
-    launch(h, K_GATHER, k_gather_octs<double>, dim3(nblocks(n)), dim3(256), (const uint32_t *)vv,
-           (const uint8_t *)d_lvl, (const uint32_t *)d_i, (const uint32_t *)d_j,
-           (const uint32_t *)d_k, (const uint16_t *)d_mem, (const double *)d_U, n, h->key,
-           (double *)h->U, h->S, (uint32_t *)nullptr);
+  const unsigned gc = nblocks(8 * n);
+  const uint32_t *srcp = from ? (const uint32_t *)from->src : nullptr;
+  if (p.precision == 4) {
+    if (from)
+      launch(h, K_GATHER, k_gather_cells<float, float>, dim3(gc), dim3(256), (const uint32_t *)vv, srcp,
+             (const float *)from->U, from->S, n, (float *)h->U, h->S);
+    else
+      launch(h, K_GATHER, k_gather_cells<double, float>, dim3(gc), dim3(256), (const uint32_t *)vv, srcp,
+             (const double *)d_U, 8 * n, n, (float *)h->U, h->S);
+  } else {
+    launch(h, K_GATHER, k_gather_cells<double, double>, dim3(gc), dim3(256), (const uint32_t *)vv, srcp,
+           from ? (const double *)from->U : (const double *)d_U, from ? from->S : 8 * n, n, (double *)h->U,
+           h->S);
+  }
 
   // leaf counts: each oct above a member's levelmin splits one cell below
   for (auto &m : h->mem) {
@@ -1503,6 +1517,7 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   dev_free(h, d_j);
   dev_free(h, d_k);
   dev_free(h, d_U);
+  if (from) dev_free(h, from->src);
   if (d_hk) dev_free(h, d_hk);
   dev_free(h, perm);
   dev_free(h, perm_alt);
@@ -2076,6 +2091,27 @@ extern "C" amr_status amr_flag(amr_handle h, int level, uint8_t *flags, int64_t 
   return st;
 }
 
+// The new mesh nh takes over h's stream ownership, events, pending timed
+// launches and counters (its own launches, made while it was built, add to
+// them); h's captured graph is dropped.
+static void take_over(amr_mesh *nh, amr_mesh *h) {
+  nh->own_stream = h->own_stream;
+  h->own_stream = false;
+  nh->event_pool.insert(nh->event_pool.end(), h->event_pool.begin(), h->event_pool.end());
+  h->event_pool.clear();
+  nh->pending.insert(nh->pending.begin(), h->pending.begin(), h->pending.end());
+  h->pending.clear();
+  nh->timing = h->timing;
+  nh->launches += h->launches;
+  nh->graph_launches += h->graph_launches;
+  std::memcpy(nh->kernel_ms, h->kernel_ms, sizeof h->kernel_ms);
+  std::memcpy(nh->kernel_n, h->kernel_n, sizeof h->kernel_n);
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+}
+
 // A fresh handle shell that shares h's stream, parameters and members.
 static amr_mesh *regrid_shell(amr_mesh *h) {
   amr_mesh *nh = new amr_mesh();
@@ -2083,6 +2119,7 @@ static amr_mesh *regrid_shell(amr_mesh *h) {
   nh->s = h->s;
   nh->cache = h->cache;
   nh->pin = h->pin;
+  nh->timing = h->timing;  // the new mesh's build is timed with the call that makes it
   nh->own_stream = false;
   nh->device = h->device;
   nh->sm_count = h->sm_count;
@@ -2175,8 +2212,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   nh->graded_by_construction = hflags == nullptr;  // caller's flags are checked
   uint8_t *d_lvl = nullptr, *d_new = nullptr;
   uint16_t *d_mem = nullptr;
-  uint32_t *d_i = nullptr, *d_j = nullptr, *d_k = nullptr;
-  double *d_U = nullptr;
+  uint32_t *d_i = nullptr, *d_j = nullptr, *d_k = nullptr, *d_src = nullptr;
   auto abandon = [&](amr_status e) {
     std::string msg = g_last_error;
     cudaStreamSynchronize(h->s);
@@ -2204,16 +2240,10 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   if ((st = clone_members(nh, h)) != AMR_OK || (st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_new, n_out)) != AMR_OK || (st = alloc_n(nh, &d_mem, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_i, n_out)) != AMR_OK || (st = alloc_n(nh, &d_j, n_out)) != AMR_OK ||
-      (st = alloc_n(nh, &d_k, n_out)) != AMR_OK || (st = alloc_n(nh, &d_U, 40 * n_out)) != AMR_OK)
+      (st = alloc_n(nh, &d_k, n_out)) != AMR_OK || (st = alloc_n(nh, &d_src, n_out)) != AMR_OK)
     return abandon(st);
-  if (h->p.precision == 4)
-    launch(h, K_REGRID, k_regrid_emit<float>, dim3(nblocks(N)), dim3(256), a, (const float *)h->U,
-           (const uint32_t *)kpos, (const uint32_t *)keep, (const uint32_t *)npos, K, n_out, d_lvl,
-           d_mem, d_i, d_j, d_k, d_U, d_new);
-  else
-    launch(h, K_REGRID, k_regrid_emit<double>, dim3(nblocks(N)), dim3(256), a, (const double *)h->U,
-           (const uint32_t *)kpos, (const uint32_t *)keep, (const uint32_t *)npos, K, n_out, d_lvl,
-           d_mem, d_i, d_j, d_k, d_U, d_new);
+  launch(h, K_REGRID, k_regrid_emit, dim3(nblocks(N)), dim3(256), a, (const uint32_t *)kpos,
+         (const uint32_t *)keep, (const uint32_t *)npos, K, d_lvl, d_mem, d_i, d_j, d_k, d_src, d_new);
   if ((st = check_launches(h, "amr_regrid")) != AMR_OK) return abandon(st);
   release();
   // the level-step scratch goes over to the new mesh (reused if large enough)
@@ -2226,27 +2256,16 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   nh->cs_cap = h->cs_cap;
   h->W = h->Q = h->F = h->C = nullptr;
   h->ls_cap = h->cs_cap = 0;
-  if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, d_U, d_new,
-                       h->order_computed ? K : 0)) != AMR_OK)
+  const StateSource from{h->U, h->S, d_src};  // the old mesh lives until the swap below
+  if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, nullptr, d_new,
+                       h->order_computed ? K : 0, &from)) != AMR_OK)
     return abandon(st);
   // carry the per-member step counters and last time steps over
   cudaMemcpyAsync(nh->mrem, h->mrem, sizeof(int) * h->M, cudaMemcpyDeviceToDevice, h->s);
   cudaMemcpyAsync(nh->dt_dev, h->dt_dev, sizeof(double) * h->M, cudaMemcpyDeviceToDevice, h->s);
   cudaMemcpyAsync(nh->merr, h->merr, sizeof(int) * h->M, cudaMemcpyDeviceToDevice, h->s);
   // the handle takes the new mesh; the old one is freed
-  nh->own_stream = h->own_stream;
-  h->own_stream = false;
-  nh->event_pool.swap(h->event_pool);
-  nh->pending.swap(h->pending);
-  nh->timing = h->timing;
-  nh->launches = h->launches;
-  nh->graph_launches = h->graph_launches;
-  std::memcpy(nh->kernel_ms, h->kernel_ms, sizeof h->kernel_ms);
-  std::memcpy(nh->kernel_n, h->kernel_n, sizeof h->kernel_n);
-  if (h->graph) {
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-  }
+  take_over(nh, h);
   std::swap(*h, *nh);
   if (h->cache) h->cache->cap = h->bytes;  // the old mesh's arrays serve the next regrid
   destroy_all(nh);
@@ -2948,19 +2967,7 @@ extern "C" amr_status amr_batch_repack(amr_handle h, int n_keep, const int32_t *
     if (e != cudaSuccess) return abandon(fail(AMR_ECUDA, "amr_batch_repack: %s", cudaGetErrorString(e)));
   }
   // the handle takes the new mesh; the old one is freed
-  nh->own_stream = h->own_stream;
-  h->own_stream = false;
-  nh->event_pool.swap(h->event_pool);
-  nh->pending.swap(h->pending);
-  nh->timing = h->timing;
-  nh->launches = h->launches;
-  nh->graph_launches = h->graph_launches;
-  std::memcpy(nh->kernel_ms, h->kernel_ms, sizeof h->kernel_ms);
-  std::memcpy(nh->kernel_n, h->kernel_n, sizeof h->kernel_n);
-  if (h->graph) {
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-  }
+  take_over(nh, h);
   std::swap(*h, *nh);
   destroy_all(nh);
   return check_device(h, "amr_batch_repack");

@@ -170,21 +170,34 @@ __global__ void k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t
 // ---------------------------------------------------------------------------
 // gather octs and state into mesh order; counts octs per (member, level)
 // ---------------------------------------------------------------------------
-template <class T>
 __global__ void k_gather_octs(const uint32_t *__restrict__ perm, const uint8_t *__restrict__ lvl,
                               const uint32_t *__restrict__ ci, const uint32_t *__restrict__ cj,
                               const uint32_t *__restrict__ ck, const uint16_t *__restrict__ mem,
-                              const double *__restrict__ Uin, int64_t n, uint64_t *__restrict__ key,
-                              T *__restrict__ U, int64_t S, uint32_t *__restrict__ seg_count) {
+                              int64_t n, uint64_t *__restrict__ key, uint32_t *__restrict__ seg_count) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= n) return;
   const uint32_t s = perm[t];
   key[t] = ikey(mem[s], lvl[s], ci[s], cj[s], ck[s]);
   if (seg_count) warp_count(seg_count, 16 * int(mem[s]) + lvl[s]);
-  if (!U) return;
-  for (int v = 0; v < kNV; ++v)
+}
+
+// the state into mesh order, one thread per cell (the 8 cells of an oct in
+// consecutive lanes): oct t of the sorted list takes source oct
+// src[perm[t]] (or perm[t] when src is null) of Uin, whose variable v of
+// cell 8 q + c sits at v * Sin + 8 q + c; a source of ~0 (a new oct) is left
+// as it is (zero)
+template <class Tin, class T>
+__global__ void k_gather_cells(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ src,
+                               const Tin *__restrict__ Uin, int64_t Sin, int64_t n, T *__restrict__ U,
+                               int64_t S) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= 8 * n) return;
+  const uint32_t s = perm[g >> 3];
+  const uint32_t q = src ? src[s] : s;
+  if (q == ~0u) return;
+  const int64_t from = 8 * int64_t(q) + (g & 7);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) U[v * S + 8 * t + c] = T(Uin[v * 8 * n + 8 * int64_t(s) + c]);
+  for (int v = 0; v < kNV; ++v) U[v * S + g] = T(Uin[v * Sin + from]);
 }
 
 // ---------------------------------------------------------------------------

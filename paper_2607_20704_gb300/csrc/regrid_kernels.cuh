@@ -364,12 +364,12 @@ __global__ void k_regrid_count(RegridArgs a, uint32_t *keep, uint32_t *nnew) {
 }
 
 // the new oct list: kept octs at keep[o] (exclusive scan), new child octs
-// after all kept ones, at K + nnew[o] (exclusive scan) in cell order
-template <class T>
-__global__ void k_regrid_emit(RegridArgs a, const T *__restrict__ U, const uint32_t *keep_pos,
-                              const uint32_t *keep, const uint32_t *new_pos, int64_t K,
-                              int64_t n_out, uint8_t *lvl, uint16_t *mem, uint32_t *oi,
-                              uint32_t *oj, uint32_t *ok, double *Uout, uint8_t *is_new) {
+// after all kept ones, at K + nnew[o] (exclusive scan) in cell order; src
+// names the old oct whose state an entry keeps (~0 for a new oct)
+__global__ void k_regrid_emit(RegridArgs a, const uint32_t *keep_pos, const uint32_t *keep,
+                              const uint32_t *new_pos, int64_t K, uint8_t *lvl, uint16_t *mem,
+                              uint32_t *oi, uint32_t *oj, uint32_t *ok, uint32_t *src,
+                              uint8_t *is_new) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= a.N) return;
   const uint64_t key = a.key[o];
@@ -383,10 +383,7 @@ __global__ void k_regrid_emit(RegridArgs a, const T *__restrict__ U, const uint3
     oj[t] = y;
     ok[t] = z;
     is_new[t] = 0;
-#pragma unroll
-    for (int v = 0; v < 5; ++v)
-#pragma unroll
-      for (int c = 0; c < 8; ++c) Uout[v * 8 * n_out + 8 * t + c] = double(U[v * a.S + 8 * int64_t(o) + c]);
+    src[t] = uint32_t(o);
   }
   const uint32_t nm = a.flag[o] & ~a.son[o];
   int64_t t = K + new_pos[o];
@@ -398,10 +395,7 @@ __global__ void k_regrid_emit(RegridArgs a, const T *__restrict__ U, const uint3
     oj[t] = 2 * y + ((c >> 1) & 1);
     ok[t] = 2 * z + ((c >> 2) & 1);
     is_new[t] = 1;
-#pragma unroll
-    for (int v = 0; v < 5; ++v)
-#pragma unroll
-      for (int q = 0; q < 8; ++q) Uout[v * 8 * n_out + 8 * t + q] = 0.0;
+    src[t] = ~0u;
     ++t;
   }
 }
