@@ -87,7 +87,7 @@ enum Kid {
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
   K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_COMMIT, K_SWEEP, K_TOTALS,
-  K_FNV, K_DEPOSIT, K_SPLIT, K_COUNT
+  K_FNV, K_DEPOSIT, K_SPLIT, K_SORT_SMALL, K_MERGE, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
@@ -95,7 +95,8 @@ static const char *kKernelNames[K_COUNT] = {
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
     "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
-    "rock", "commit", "sweep", "totals", "fnv", "deposit_level", "split_level"};
+    "rock", "commit", "sweep", "totals", "fnv", "deposit_level", "split_level", "sort_small",
+    "merge_rank"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -1168,11 +1169,14 @@ static amr_status build_blocks(amr_mesh *h);
 
 // a regrid's state source: the old mesh's state (the handle's precision,
 // variable stride S) and, per entry of the new oct list, the old oct it keeps
-// (~0 for a new oct)
+// (~0 for a new oct); pos is the emit pass's scanned counts over the n_old
+// old octs (the new octs of old oct o at [pos[n_old + o], pos[n_old + o + 1]))
 struct StateSource {
   const void *U = nullptr;
   int64_t S = 0;
   uint32_t *src = nullptr;
+  const uint32_t *pos = nullptr;
+  int64_t n_old = 0;
 };
 static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lvl, uint16_t *d_mem,
                              uint32_t *d_i, uint32_t *d_j, uint32_t *d_k, uint64_t *d_hk,
@@ -1288,16 +1292,22 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   uint64_t *kk = comp;
   uint32_t *vv = perm;
   const int64_t n_new = n - sorted_prefix;
-  if (sorted_prefix > 0 && n_new >= 0 && n_new <= kSmallSort) {
+  const bool grouped = from && from->pos;  // new octs sorted but within each father's group
+  if (sorted_prefix > 0 && n_new >= 0 && (grouped || n_new <= kSmallSort)) {
     // a regrid: the kept octs [0, sorted_prefix) are in order; sort the new
-    // ones in one block and merge the two runs by rank
+    // ones (within their fathers' groups, or in one block) and merge the two
+    // runs by rank
     if (n_new > 0) {
-      launch(h, K_SORT_KEYS, k_sort_small, dim3(1), dim3(1024), comp + sorted_prefix, perm + sorted_prefix,
-             int(n_new));
-      launch(h, K_SORT_KEYS, k_merge_rank, dim3(nblocks(sorted_prefix)), dim3(256), (const uint64_t *)comp,
+      if (grouped)
+        launch(h, K_SORT_SMALL, k_sort_groups, dim3(nblocks(from->n_old)), dim3(256), from->pos, from->n_old,
+               comp, perm);
+      else
+        launch(h, K_SORT_SMALL, k_sort_small, dim3(1), dim3(1024), comp + sorted_prefix,
+               perm + sorted_prefix, int(n_new));
+      launch(h, K_MERGE, k_merge_rank, dim3(nblocks(sorted_prefix)), dim3(256), (const uint64_t *)comp,
              (const uint32_t *)perm, sorted_prefix, (const uint64_t *)(comp + sorted_prefix), n_new, comp_alt,
              perm_alt);
-      launch(h, K_SORT_KEYS, k_merge_rank, dim3(nblocks(n_new)), dim3(256),
+      launch(h, K_MERGE, k_merge_rank, dim3(nblocks(n_new)), dim3(256),
              (const uint64_t *)(comp + sorted_prefix), (const uint32_t *)(perm + sorted_prefix), n_new,
              (const uint64_t *)comp, sorted_prefix, comp_alt, perm_alt);
       kk = comp_alt;
@@ -2144,10 +2154,9 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   if (created) *created = 0;
   if (removed) *removed = 0;
   const int64_t N = h->N;
-  uint32_t *raw = nullptr, *flag = nullptr, *keep = nullptr, *nnew = nullptr, *kpos = nullptr,
-           *npos = nullptr, *tmp = nullptr;
+  uint32_t *raw = nullptr, *flag = nullptr, *pos = nullptr, *tmp = nullptr;
   auto release = [&] {
-    for (uint32_t **q : {&raw, &flag, &keep, &nnew, &kpos, &npos, &tmp})
+    for (uint32_t **q : {&raw, &flag, &pos, &tmp})
       if (*q) {
         dev_free(h, *q);
         *q = nullptr;
@@ -2164,11 +2173,8 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   } while (0)
   REGRID_TRY(alloc_n(h, &raw, N));
   REGRID_TRY(alloc_n(h, &flag, N));
-  REGRID_TRY(alloc_n(h, &keep, N));
-  REGRID_TRY(alloc_n(h, &nnew, N));
-  REGRID_TRY(alloc_n(h, &kpos, N));
-  REGRID_TRY(alloc_n(h, &npos, N));
-  REGRID_TRY(alloc_n(h, &tmp, scan_tmp_size(N)));
+  REGRID_TRY(alloc_n(h, &pos, 2 * N + 1));
+  REGRID_TRY(alloc_n(h, &tmp, scan_tmp_size(2 * N + 1)));
   if (hflags) {
     std::vector<uint32_t> mk(N);
     for (int64_t q = 0; q < N; ++q) {
@@ -2183,19 +2189,14 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
     REGRID_TRY(compute_flags(h, raw, flag, "amr_regrid", false));  // checked with the counts
   }
   const RegridArgs a = regrid_args(h, raw, flag);
-  launch(h, K_REGRID, k_regrid_count, dim3(nblocks(N)), dim3(256), a, keep, nnew);
-  cudaMemcpyAsync(kpos, keep, 4 * N, cudaMemcpyDeviceToDevice, h->s);
-  cudaMemcpyAsync(npos, nnew, 4 * N, cudaMemcpyDeviceToDevice, h->s);
-  scan_exclusive(h, kpos, N, tmp);
-  scan_exclusive(h, npos, N, tmp);
+  launch(h, K_REGRID, k_regrid_count, dim3(nblocks(N)), dim3(256), a, pos);
+  scan_exclusive(h, pos, 2 * N + 1, tmp);
   uint32_t *tail = nullptr;
-  REGRID_TRY(pinned_words(h, 4, &tail));
-  REGRID_TRY(read_words(h, 0, kpos + N - 1, 1));
-  REGRID_TRY(read_words(h, 1, keep + N - 1, 1));
-  REGRID_TRY(read_words(h, 2, npos + N - 1, 1));
-  REGRID_TRY(read_words(h, 3, nnew + N - 1, 1));
+  REGRID_TRY(pinned_words(h, 2, &tail));
+  REGRID_TRY(read_words(h, 0, pos + N, 1));      // kept octs
+  REGRID_TRY(read_words(h, 1, pos + 2 * N, 1));  // kept + new octs
   REGRID_TRY(check_device_after_reads(h, "amr_regrid"));
-  const int64_t K = int64_t(tail[0]) + tail[1], NN = int64_t(tail[2]) + tail[3];
+  const int64_t K = tail[0], NN = int64_t(tail[1]) - tail[0];
   if (created) *created = NN;
   if (removed) *removed = N - K;
   if (NN == 0 && K == N) {  // nothing changes
@@ -2242,10 +2243,13 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
       (st = alloc_n(nh, &d_i, n_out)) != AMR_OK || (st = alloc_n(nh, &d_j, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_k, n_out)) != AMR_OK || (st = alloc_n(nh, &d_src, n_out)) != AMR_OK)
     return abandon(st);
-  launch(h, K_REGRID, k_regrid_emit, dim3(nblocks(N)), dim3(256), a, (const uint32_t *)kpos,
-         (const uint32_t *)keep, (const uint32_t *)npos, K, d_lvl, d_mem, d_i, d_j, d_k, d_src, d_new);
+  launch(h, K_REGRID, k_regrid_emit, dim3(nblocks(N)), dim3(256), a, (const uint32_t *)pos, d_lvl, d_mem,
+         d_i, d_j, d_k, d_src, d_new);
   if ((st = check_launches(h, "amr_regrid")) != AMR_OK) return abandon(st);
-  release();
+  for (uint32_t **q : {&raw, &flag, &tmp}) {  // pos serves the new mesh's build
+    dev_free(h, *q);
+    *q = nullptr;
+  }
   // the level-step scratch goes over to the new mesh (reused if large enough)
   for (void **b : {&h->W, &h->Q, &h->F, &h->C}) move_buf(nh, h, *b);
   nh->W = h->W;
@@ -2256,7 +2260,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   nh->cs_cap = h->cs_cap;
   h->W = h->Q = h->F = h->C = nullptr;
   h->ls_cap = h->cs_cap = 0;
-  const StateSource from{h->U, h->S, d_src};  // the old mesh lives until the swap below
+  const StateSource from{h->U, h->S, d_src, pos, N};  // the old mesh lives until the swap below
   if ((st = build_mesh(nh, n_out, false, d_lvl, d_mem, d_i, d_j, d_k, nullptr, nullptr, d_new,
                        h->order_computed ? K : 0, &from)) != AMR_OK)
     return abandon(st);

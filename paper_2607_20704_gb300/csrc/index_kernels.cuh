@@ -81,6 +81,38 @@ __global__ void __launch_bounds__(1024) k_sort_small(uint64_t *__restrict__ key,
   }
 }
 
+// a regrid's new octs in the order the emit pass wrote them: by old oct
+// (which is the sorted order of their fathers), then by cell of the father.
+// The Hilbert index of an oct is its father's index followed by one octal
+// digit, so the list is sorted once each father's group (at most 8 entries,
+// at [pos[N + o], pos[N + o + 1]) for old oct o) is sorted; one thread per
+// old oct, insertion sort of its group by key
+__global__ void k_sort_groups(const uint32_t *__restrict__ pos, int64_t N, uint64_t *__restrict__ key,
+                              uint32_t *__restrict__ val) {
+  const int64_t o = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (o >= N) return;
+  const int64_t a = pos[N + o], b = pos[N + o + 1];
+  if (b - a < 2) return;
+  uint64_t k[8];
+  uint32_t v[8];
+  const int m = int(b - a);  // <= 8: one new oct per flagged leaf cell
+  for (int t = 0; t < m; ++t) {
+    uint64_t kt = key[a + t];
+    uint32_t vt = val[a + t];
+    int u = t;
+    for (; u > 0 && k[u - 1] > kt; --u) {
+      k[u] = k[u - 1];
+      v[u] = v[u - 1];
+    }
+    k[u] = kt;
+    v[u] = vt;
+  }
+  for (int t = 0; t < m; ++t) {
+    key[a + t] = k[t];
+    val[a + t] = v[t];
+  }
+}
+
 // number of keys of the sorted a[0..n) below x
 __device__ __forceinline__ int64_t count_below(const uint64_t *__restrict__ a, int64_t n, uint64_t x) {
   int64_t lo = 0, hi = n;

@@ -347,10 +347,14 @@ __global__ void k_flag_grade(RegridArgs a, int lo, int hi) {
   for (int t = 0; t < n; ++t) atomicOr(a.flag + octs[t], bits[t]);
 }
 
-// per oct: 1 if it stays (its father cell is flagged, or it is a base oct),
-// and the number of new child octs (flagged leaf cells)
-__global__ void k_regrid_count(RegridArgs a, uint32_t *keep, uint32_t *nnew) {
+// per oct: 1 if it stays (its father cell is flagged, or it is a base oct)
+// at cnt[o], and the number of new child octs (flagged leaf cells) at
+// cnt[N + o]; cnt[2 N] = 0, so that one exclusive scan of the 2 N + 1 words
+// gives the kept octs' places, the new octs' places (after the kept octs)
+// and, at 2 N, the size of the new list
+__global__ void k_regrid_count(RegridArgs a, uint32_t *cnt) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o == 0) cnt[2 * int64_t(a.N)] = 0u;
   if (o >= a.N) return;
   const uint64_t key = a.key[o];
   const int fo = a.father[o];
@@ -359,15 +363,14 @@ __global__ void k_regrid_count(RegridArgs a, uint32_t *keep, uint32_t *nnew) {
     const int fc = int(ikey_x(key) & 1) | (int(ikey_y(key) & 1) << 1) | (int(ikey_z(key) & 1) << 2);
     k = (a.flag[fo] >> fc) & 1u;
   }
-  keep[o] = k;
-  nnew[o] = __popc(a.flag[o] & ~a.son[o]);
+  cnt[o] = k;
+  cnt[a.N + o] = __popc(a.flag[o] & ~a.son[o]);
 }
 
-// the new oct list: kept octs at keep[o] (exclusive scan), new child octs
-// after all kept ones, at K + nnew[o] (exclusive scan) in cell order; src
-// names the old oct whose state an entry keeps (~0 for a new oct)
-__global__ void k_regrid_emit(RegridArgs a, const uint32_t *keep_pos, const uint32_t *keep,
-                              const uint32_t *new_pos, int64_t K, uint8_t *lvl, uint16_t *mem,
+// the new oct list from the scanned counts pos (k_regrid_count): kept octs
+// at pos[o], new child octs after all K kept ones, at pos[N + o] in cell
+// order; src names the old oct whose state an entry keeps (~0 for a new oct)
+__global__ void k_regrid_emit(RegridArgs a, const uint32_t *pos, uint8_t *lvl, uint16_t *mem,
                               uint32_t *oi, uint32_t *oj, uint32_t *ok, uint32_t *src,
                               uint8_t *is_new) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -375,8 +378,8 @@ __global__ void k_regrid_emit(RegridArgs a, const uint32_t *keep_pos, const uint
   const uint64_t key = a.key[o];
   const int l = ikey_lev(key);
   const uint32_t x = ikey_x(key), y = ikey_y(key), z = ikey_z(key);
-  if (keep[o]) {
-    const int64_t t = keep_pos[o];
+  if (pos[o + 1] != pos[o]) {  // kept (pos[N] is the number of kept octs)
+    const int64_t t = pos[o];
     lvl[t] = uint8_t(l);
     mem[t] = uint16_t(ikey_member(key));
     oi[t] = x;
@@ -386,7 +389,7 @@ __global__ void k_regrid_emit(RegridArgs a, const uint32_t *keep_pos, const uint
     src[t] = uint32_t(o);
   }
   const uint32_t nm = a.flag[o] & ~a.son[o];
-  int64_t t = K + new_pos[o];
+  int64_t t = pos[a.N + o];
   for (int c = 0; c < 8; ++c) {
     if (!((nm >> c) & 1u)) continue;
     lvl[t] = uint8_t(l + 1);
