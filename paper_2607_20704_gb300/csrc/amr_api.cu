@@ -87,7 +87,7 @@ enum Kid {
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
   K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_COMMIT, K_SWEEP, K_TOTALS,
-  K_FNV, K_DEPOSIT, K_SPLIT, K_SORT_SMALL, K_MERGE, K_COUNT
+  K_FNV, K_DEPOSIT, K_SPLIT, K_SORT_SMALL, K_MERGE, K_FLAG_EXACT, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
@@ -96,7 +96,7 @@ static const char *kKernelNames[K_COUNT] = {
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
     "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
     "rock", "commit", "sweep", "totals", "fnv", "deposit_level", "split_level", "sort_small",
-    "merge_rank"};
+    "merge_rank", "flag_exact"};
 
 extern "C" const char *amr_kernel_name(int t) {
   return (t >= 0 && t < K_COUNT) ? kKernelNames[t] : nullptr;
@@ -2057,18 +2057,29 @@ static amr_status compute_flags(amr_mesh *h, uint32_t *raw, uint32_t *flag, cons
   const RegridArgs a = regrid_args(h, raw, flag);
   const unsigned g = nblocks(h->N);
   float *rp = nullptr;  // FP32 rho, p and the pressure's error bound per cell
+  uint32_t *und = nullptr, *n_und = nullptr;  // cells left to the FP64 tests
   AMR_TRY(alloc_n(h, &rp, 24 * h->N));
+  AMR_TRY(alloc_n(h, &und, 8 * h->N));
+  AMR_TRY(alloc_n(h, &n_und, 1));
+  CUDA_TRY(cudaMemsetAsync(n_und, 0, sizeof(uint32_t), h->s));
   const unsigned g8 = nblocks(8 * h->N);  // 256-thread blocks: whole octs per warp
+  const unsigned gx = unsigned(std::max(1, 2 * h->sm_count));
   if (h->p.precision == 4) {
     launch(h, K_FLAG_RP, k_flag_rp<float>, dim3(g8), dim3(256), a, (const float *)h->U, rp);
     launch(h, K_FLAG, k_flag_raw<float>, dim3(g8), dim3(256), a, (const float *)h->U,
-           (const float *)rp);
+           (const float *)rp, und, n_und);
+    launch(h, K_FLAG_EXACT, k_flag_exact<float>, dim3(gx), dim3(256), a, (const float *)h->U,
+           (const float *)rp, (const uint32_t *)und, (const uint32_t *)n_und);
   } else {
     launch(h, K_FLAG_RP, k_flag_rp<double>, dim3(g8), dim3(256), a, (const double *)h->U, rp);
     launch(h, K_FLAG, k_flag_raw<double>, dim3(g8), dim3(256), a, (const double *)h->U,
-           (const float *)rp);
+           (const float *)rp, und, n_und);
+    launch(h, K_FLAG_EXACT, k_flag_exact<double>, dim3(gx), dim3(256), a, (const double *)h->U,
+           (const float *)rp, (const uint32_t *)und, (const uint32_t *)n_und);
   }
   dev_free(h, rp);
+  dev_free(h, und);
+  dev_free(h, n_und);
   launch(h, K_FLAG_EXPAND, k_flag_expand, dim3(g), dim3(256), a);
   for (auto &m : h->mem)
     for (int l = m.lmax - 1; l > m.lmin; --l) {

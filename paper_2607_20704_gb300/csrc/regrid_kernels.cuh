@@ -157,39 +157,61 @@ __device__ __forceinline__ int jump_exceeds32(float a, float b, float ea, float 
   return -1;
 }
 
-// criterion masks: one thread per real cell, the 8 cells of an oct in
-// consecutive lanes; a ballot assembles the oct's mask
+// the six face neighbours of cell c of oct o (same oct, a real oct, or the
+// covering coarser cell of a ghost oct), as cell indices; -1 where there is
+// none
+__device__ __forceinline__ void flag_neighbours(const RegridArgs &a, int o, int c, int32_t (&gnb)[6]) {
+  const int64_t N8 = 8 * int64_t(a.N);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int d = k >> 1, plus = k & 1, bit = 1 << d;
+    if (((c >> d) & 1) != plus) {
+      gnb[k] = 8 * o + (c ^ bit);
+    } else {
+      const int32_t ne = a.fnb[k * int64_t(a.NE) + o];
+      gnb[k] = ne < 0 ? -1
+                      : (ne < a.N ? 8 * ne + (c ^ bit)
+                                  : int32_t(checked(a.csrc[checked(ne - a.N, 0, a.NC, a.err)], 0, N8, a.err)));
+    }
+  }
+}
+
+// the FP32 screen of one neighbour pair (k_flag_rp's images): dr, dp = 1 the
+// jump of rho (p) exceeds its threshold, 0 it does not, -1 FP32 cannot tell
+// (0 also for a test that is off)
+__device__ __forceinline__ void flag_screen(const RegridArgs &a, float rn, float pn, float en, float rc,
+                                            float pc, float ec, int &dr, int &dp) {
+  dr = a.test_r ? -1 : 0;
+  dp = a.test_p ? -1 : 0;
+  if (a.use32) {
+    if (dr) dr = jump_exceeds32(rn, rc, 0x1p-21f * rn, 0x1p-21f * rc, a.thr_r32);
+    if (dp && dr != 1) dp = jump_exceeds32(pn, pc, en, ec, a.thr_p32);
+  }
+}
+
+// criterion masks, FP32 pass: one thread per real cell, the 8 cells of an
+// oct in consecutive lanes; a ballot assembles the oct's mask.  A cell whose
+// neighbours FP32 flags none of but leaves a test undecided goes on the list
+// `undecided` (count at n_undecided) for k_flag_exact.
 template <class T>
-__global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const float *__restrict__ rp) {
+__global__ void __launch_bounds__(256) k_flag_raw(RegridArgs a, const T *__restrict__ U,
+                                                  const float *__restrict__ rp,
+                                                  uint32_t *__restrict__ undecided,
+                                                  uint32_t *__restrict__ n_undecided) {
   const int64_t gc = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t N8 = 8 * int64_t(a.N);
   const bool in = gc < N8;
   const int o = int(gc >> 3), c = int(gc & 7);
-  bool f = false;
+  bool f = false, undec = false;
   if (in) {
     const uint64_t key = a.key[o];
     const int m = ikey_member(key), l = ikey_lev(key);
     if (l < a.mlmax[m]) {
-      const bool test_r = a.test_r, test_p = a.test_p, use32 = a.use32;
-      const float thr_r = a.thr_r32, thr_p = a.thr_p32;
       f = a.test_mass && ldexp(double(U[gc]), -3 * l) > a.mass;
       const float rc = rp[gc], pc = rp[N8 + gc], ec = rp[2 * N8 + gc];
-      // the six face neighbours (same oct, a real oct, or the covering
-      // coarser cell of a ghost oct), then their FP32 images, all loads
-      // issued before the tests
-      int64_t gnb[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const int d = k >> 1, plus = k & 1, bit = 1 << d;
-        if (((c >> d) & 1) != plus) {
-          gnb[k] = 8 * int64_t(o) + (c ^ bit);
-        } else {
-          const int32_t ne = a.fnb[k * int64_t(a.NE) + o];
-          gnb[k] = ne < 0 ? -1
-                          : (ne < a.N ? 8 * int64_t(ne) + (c ^ bit)
-                                      : checked(a.csrc[checked(ne - a.N, 0, a.NC, a.err)], 0, N8, a.err));
-        }
-      }
+      int32_t gnb[6];
+      flag_neighbours(a, o, c, gnb);
+      // all loads issued before the tests
       float rn[6], pn[6], en[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
@@ -198,39 +220,63 @@ __global__ void k_flag_raw(RegridArgs a, const T *__restrict__ U, const float *_
         pn[k] = rp[N8 + q];
         en[k] = rp[2 * N8 + q];
       }
-      double rc64 = 0.0, pc64 = 0.0;
-      bool have64 = false;
-      for (int k = 0; k < 6 && !f; ++k) {
-        const int64_t gn = gnb[k];
-        if (gn < 0) continue;
-        int dr = test_r ? -1 : 0, dp = test_p ? -1 : 0;
-        if (use32) {
-          if (dr) dr = jump_exceeds32(rn[k], rc, 0x1p-21f * rn[k], 0x1p-21f * rc, thr_r);
-          if (dp && dr != 1) dp = jump_exceeds32(pn[k], pc, en[k], ec, thr_p);
-        }
-        if (dr == 1 || dp == 1) {
-          f = true;
-          continue;
-        }
-        if (dr == 0 && dp == 0) continue;
-        // undecided in FP32: the FP64 test on the FP64 density and pressure
-        if (!have64) {
-          double u[5];
-          load_cell(U, a.S, gc, u);
-          flag_rho_p(u, a.mgamma[m], a.msmallr[m], a.msmallp[m], rc64, pc64);
-          have64 = true;
-        }
-        double u[5], rn64, pn64;
-        load_cell(U, a.S, gn, u);
-        const int mn = ikey_member(a.key[gn >> 3]);
-        flag_rho_p(u, a.mgamma[mn], a.msmallr[mn], a.msmallp[mn], rn64, pn64);
-        if (dr && jump_exceeds(rn64, rc64, a.grad_rho)) f = true;
-        if (dp && jump_exceeds(pn64, pc64, a.grad_p)) f = true;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        if (gnb[k] < 0) continue;
+        int dr, dp;
+        flag_screen(a, rn[k], pn[k], en[k], rc, pc, ec, dr, dp);
+        if (dr == 1 || dp == 1) f = true;
+        else if (dr || dp) undec = true;
       }
     }
   }
   const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
   if (in && c == 0) a.raw[o] = (b >> (threadIdx.x & 24)) & 0xFFu;
+  // the list, one atomic per warp
+  const unsigned lst = __ballot_sync(0xFFFFFFFFu, undec && !f);
+  if (lst) {
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(lst) - 1) base = atomicAdd(n_undecided, uint32_t(__popc(lst)));
+    base = __shfl_sync(0xFFFFFFFFu, base, __ffs(lst) - 1);
+    if ((lst >> lane) & 1u) undecided[base + __popc(lst & ((1u << lane) - 1u))] = uint32_t(gc);
+  }
+}
+
+// criterion masks, FP64 pass: the listed cells' undecided tests in FP64 (the
+// decision as defined, bit for bit); a cell that one of them flags sets its
+// bit with an atomic OR.  Grid-stride over the list.
+template <class T>
+__global__ void k_flag_exact(RegridArgs a, const T *__restrict__ U, const float *__restrict__ rp,
+                             const uint32_t *__restrict__ undecided, const uint32_t *__restrict__ n_undecided) {
+  const int64_t N8 = 8 * int64_t(a.N);
+  const uint32_t n = *n_undecided;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int64_t gc = undecided[t];
+    const int o = int(gc >> 3), c = int(gc & 7);
+    const int m = ikey_member(a.key[o]);
+    const float rc = rp[gc], pc = rp[N8 + gc], ec = rp[2 * N8 + gc];
+    int32_t gnb[6];
+    flag_neighbours(a, o, c, gnb);
+    double u[5], rc64, pc64;
+    load_cell(U, a.S, gc, u);
+    flag_rho_p(u, a.mgamma[m], a.msmallr[m], a.msmallp[m], rc64, pc64);
+    bool f = false;
+    for (int k = 0; k < 6 && !f; ++k) {
+      const int64_t gn = gnb[k];
+      if (gn < 0) continue;
+      int dr, dp;
+      flag_screen(a, rp[gn], rp[N8 + gn], rp[2 * N8 + gn], rc, pc, ec, dr, dp);
+      if (dr == 0 && dp == 0) continue;
+      double rn64, pn64;
+      load_cell(U, a.S, gn, u);
+      const int mn = ikey_member(a.key[gn >> 3]);
+      flag_rho_p(u, a.mgamma[mn], a.msmallr[mn], a.msmallp[mn], rn64, pn64);
+      if (dr && jump_exceeds(rn64, rc64, a.grad_rho)) f = true;
+      if (dp && jump_exceeds(pn64, pc64, a.grad_p)) f = true;
+    }
+    if (f) atomicOr(a.raw + o, 1u << c);
+  }
 }
 
 // expansion over the 3x3x3 same-level block (or a copy when expand = 0); one
@@ -286,8 +332,12 @@ __global__ void k_flag_expand(RegridArgs a) {
 // axis those are, for a cell with bit 0, the father cell's coordinate minus
 // one and itself, for bit 1 itself and plus one, so the cells covered for
 // the whole oct form a subset of the 3^3 level-(l-1) cells around the father
-// cell: collected as a 27-bit set, then one atomic OR per level-(l-1) oct
-// (at most 8) instead of one per covered cell.
+// cell.  Per axis, offset 0 and the offset away from the father oct's centre
+// stay in the father oct, and the offset towards it lands in the
+// neighbouring oct on that side (the father oct itself when the level has
+// one oct per axis): the covered cells fall into at most 2^3 octs, whose
+// cell masks are collected in one 64-bit word (byte = oct), then one atomic
+// OR per oct instead of one per covered cell.
 __global__ void k_flag_grade(RegridArgs a, int lo, int hi) {
   const int o = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= hi) return;
@@ -310,41 +360,42 @@ __global__ void k_flag_grade(RegridArgs a, int lo, int hi) {
   }
   const int64_t cside = int64_t(1) << (l - 1);                  // cells per axis at level l-1
   const int64_t oside = int64_t(1) << (l - 2 > 0 ? l - 2 : 0);  // octs per axis at l-1
-  const uint32_t oi = ikey_x(key), oj = ikey_y(key), okk = ikey_z(key);  // the father cell at l-1
-  int32_t octs[8];
-  uint32_t bits[8];
-  int n = 0;
+  const int64_t fc[3] = {int64_t(ikey_x(key)), int64_t(ikey_y(key)), int64_t(ikey_z(key))};  // father cell
+  // per axis: the offset towards the neighbouring oct, and that oct's place
+  // (-1, 0 or +1) relative to the father oct, periodic
+  int toward[3], rel_t[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    toward[q] = (fc[q] & 1) ? 1 : -1;
+    const int64_t p = (fc[q] + toward[q]) & (cside - 1);
+    const int64_t dd = ((p >> 1) - (fc[q] >> 1)) & (oside - 1);  // oside is a power of two
+    rel_t[q] = dd == 0 ? 0 : (dd == 1 ? 1 : -1);
+  }
+  uint64_t acc = 0;  // byte sx + 2 sy + 4 sz: the cells of the oct on the toward side of the axes s = 1
+#pragma unroll
   for (int k = 0; k < 27; ++k) {
     if (!((set27 >> k) & 1u)) continue;
-    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-    // the covered level-(l-1) cell, periodic (cside is a power of two)
-    const int64_t px = (int64_t(oi) + dx) & (cside - 1), py = (int64_t(oj) + dy) & (cside - 1),
-                  pz = (int64_t(okk) + dz) & (cside - 1);
-    // its oct, relative to the father cell's oct (oi>>1, oj>>1, ok>>1)
-    int rel[3];
-    const int64_t d3[3] = {(px >> 1) - int64_t(oi >> 1), (py >> 1) - int64_t(oj >> 1),
-                           (pz >> 1) - int64_t(okk >> 1)};
+    const int d[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
+    int slot = 0, cc = 0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const int64_t dd = d3[q] & (oside - 1);  // oside is a power of two
-      rel[q] = dd == 0 ? 0 : (dd == 1 ? 1 : -1);
+      if (d[q] == toward[q] && rel_t[q] != 0) slot |= 1 << q;
+      cc |= int(((fc[q] + d[q]) & (cside - 1)) & 1) << q;
     }
-    const int32_t e = a.nbr27[((rel[2] + 1) * 9 + (rel[1] + 1) * 3 + (rel[0] + 1)) * int64_t(a.N) + fo];
+    acc |= uint64_t(1) << (8 * slot + cc);
+  }
+#pragma unroll
+  for (int slot = 0; slot < 8; ++slot) {
+    const uint32_t bits = uint32_t(acc >> (8 * slot)) & 0xFFu;
+    if (!bits) continue;
+    const int rx = (slot & 1) ? rel_t[0] : 0, ry = (slot & 2) ? rel_t[1] : 0, rz = (slot & 4) ? rel_t[2] : 0;
+    const int32_t e = a.nbr27[((rz + 1) * 9 + (ry + 1) * 3 + (rx + 1)) * int64_t(a.N) + fo];
     if (e < 0 || e >= a.N) {
       atomicOr(a.err, kErrGrading);
       continue;
     }
-    const uint32_t cc = uint32_t(px & 1) | (uint32_t(py & 1) << 1) | (uint32_t(pz & 1) << 2);
-    int t = 0;
-    while (t < n && octs[t] != e) ++t;
-    if (t == n) {
-      octs[n] = e;
-      bits[n] = 0;
-      ++n;
-    }
-    bits[t] |= 1u << cc;
+    atomicOr(a.flag + e, bits);
   }
-  for (int t = 0; t < n; ++t) atomicOr(a.flag + octs[t], bits[t]);
 }
 
 // per oct: 1 if it stays (its father cell is flagged, or it is a base oct)
