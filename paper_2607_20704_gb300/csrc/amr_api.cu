@@ -292,6 +292,7 @@ struct amr_mesh {
   int64_t launches = 0, graph_launches = 0;
   bool capturing = false;
   int64_t capture_kernels = 0;
+  int64_t steps_on_mesh = 0;  // coarse steps since this mesh was built
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;
   bool timing = false;
@@ -313,11 +314,12 @@ static amr_status dev_alloc(amr_mesh *h, void **out, size_t bytes) {
     return fail(AMR_ENOMEM, "device allocation of %zu bytes exceeds the budget (%zu of %zu held)",
                 bytes, h->bytes, h->p.hbm_budget_bytes);
   void *ptr = nullptr;
-  if (h->cache && !h->cache->v.empty()) {  // the smallest cached array that fits, within 2x
+  if (h->cache && !h->cache->v.empty()) {  // the smallest cached array that fits, within 2x (or 8 KB)
     std::vector<DevBuf> &v = h->cache->v;
     size_t best = v.size();
     for (size_t t = 0; t < v.size(); ++t)
-      if (v[t].bytes >= bytes && v[t].bytes <= 2 * bytes && (best == v.size() || v[t].bytes < v[best].bytes))
+      if (v[t].bytes >= bytes && v[t].bytes <= std::max(2 * bytes, size_t(8192)) &&
+          (best == v.size() || v[t].bytes < v[best].bytes))
         best = t;
     if (best < v.size()) {
       const DevBuf b = v[best];
@@ -330,10 +332,10 @@ static amr_status dev_alloc(amr_mesh *h, void **out, size_t bytes) {
     }
   }
   // a handle that regrids asks for arrays a little larger each time a mesh
-  // grows: a fresh large array gets 1/8 headroom, so that the next mesh's
-  // request still fits the cached array instead of a new allocation
-  if (h->cache && bytes >= (size_t(1) << 20)) {
-    const size_t wide = (bytes + bytes / 8 + 65535) & ~size_t(65535);
+  // grows: a fresh array gets 1/8 headroom, so that the next mesh's request
+  // still fits the cached array instead of a new allocation
+  if (h->cache) {
+    const size_t wide = (bytes + bytes / 8 + 4095) & ~size_t(4095);
     if (!h->p.hbm_budget_bytes || h->bytes + wide <= h->p.hbm_budget_bytes) bytes = wide;
   }
   if (h->p.alloc) {
@@ -1861,17 +1863,21 @@ extern "C" amr_status amr_advance(amr_handle h, int n, double *dt_last) {
   const bool graphs = h->p.use_graphs && !h->timing;
   for (int t = 0; t < n; ++t) {
     if (h->p.regrid_every_step) AMR_TRY(amr_regrid(h, nullptr, nullptr));
-    if (graphs && !h->graph) {
+    // a mesh's first coarse step runs its launches directly (the device
+    // starts at the first one); the graph is captured for the second: a mesh
+    // that is regridded before every coarse step never pays for a capture
+    if (graphs && !h->graph && h->steps_on_mesh >= 1) {
       AMR_TRY(capture_coarse_step(h, &h->graph));
       h->graph_kernels = h->capture_kernels;
     }
-    if (graphs) {
+    if (graphs && h->graph) {
       CUDA_TRY(cudaGraphLaunch(h->graph, h->s));
       h->graph_launches++;
       h->launches += h->graph_kernels;
     } else {
       coarse_step(h);
     }
+    ++h->steps_on_mesh;
   }
   if (h->launch_err != cudaSuccess) return check_device(h, "amr_advance");
   cudaError_t e = cudaGetLastError();
