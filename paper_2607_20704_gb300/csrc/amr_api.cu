@@ -566,7 +566,9 @@ static amr_status check_device_after_reads(amr_mesh *h, const char *where) {
 static void scan_exclusive(amr_mesh *h, uint32_t *data, int64_t n, uint32_t *tmp) {
   const int64_t nb = (n + kScanItems - 1) / kScanItems;
   launch(h, K_SCAN, k_scan_block, dim3(unsigned(nb)), dim3(256), data, n, tmp);
-  if (nb > 1) {
+  if (nb > 1 && nb <= kScanFlat) {
+    launch(h, K_SCAN, k_scan_add_flat, dim3(unsigned(nb - 1)), dim3(256), data, n, (const uint32_t *)tmp);
+  } else if (nb > 1) {
     scan_exclusive(h, tmp, nb, tmp + ((nb + 255) & ~int64_t(255)));
     launch(h, K_SCAN, k_scan_add, dim3(nblocks(n)), dim3(256), data, n, (const uint32_t *)tmp);
   }
@@ -1146,25 +1148,28 @@ static amr_status dup_n(amr_mesh *nh, P **dst, const P *src, int64_t n) {
   return AMR_OK;
 }
 
-// the member arrays of a new handle with the same members as h (a regrid):
-// device-to-device copies on the shared stream, no host round trip
-static amr_status clone_members(amr_mesh *nh, const amr_mesh *h) {
-  const int64_t M = h->M;
-  AMR_TRY(dup_n(nh, &nh->mlmin, (const int *)h->mlmin, M));
-  AMR_TRY(dup_n(nh, &nh->mlmax, (const int *)h->mlmax, M));
-  AMR_TRY(dup_n(nh, &nh->mgamma_d, (const double *)h->mgamma_d, M));
-  AMR_TRY(dup_n(nh, &nh->mcfl_d, (const double *)h->mcfl_d, M));
-  AMR_TRY(dup_n(nh, &nh->msmallr_d, (const double *)h->msmallr_d, M));
-  AMR_TRY(dup_n(nh, &nh->msmallp_d, (const double *)h->msmallp_d, M));
-  AMR_TRY(dup_n(nh, &nh->mflag32, (const float *)h->mflag32, 3 * M));
-  const size_t bytes = h->elem() * size_t(M);
-  void **dst[4] = {&nh->mgamma_t, &nh->migm1_t, &nh->msmallr_t, &nh->msmallp_t};
-  const void *src[4] = {h->mgamma_t, h->migm1_t, h->msmallr_t, h->msmallp_t};
-  for (int t = 0; t < 4; ++t) {
-    AMR_TRY(dev_alloc(nh, dst[t], bytes));
-    CUDA_TRY(cudaMemcpyAsync(*dst[t], src[t], bytes, cudaMemcpyDeviceToDevice, nh->s));
-  }
-  return AMR_OK;
+// a regrid's new mesh nh reads h's member arrays (levels, parameters: fixed
+// for a member's life) as they are; h still owns them
+static void share_members(amr_mesh *nh, const amr_mesh *h) {
+  nh->mlmin = h->mlmin;
+  nh->mlmax = h->mlmax;
+  nh->mgamma_d = h->mgamma_d;
+  nh->mcfl_d = h->mcfl_d;
+  nh->msmallr_d = h->msmallr_d;
+  nh->msmallp_d = h->msmallp_d;
+  nh->mflag32 = h->mflag32;
+  nh->mgamma_t = h->mgamma_t;
+  nh->migm1_t = h->migm1_t;
+  nh->msmallr_t = h->msmallr_t;
+  nh->msmallp_t = h->msmallp_t;
+}
+
+// after the swap: the new mesh h takes the member arrays over from the old
+// mesh old, which then no longer frees them
+static void own_members(amr_mesh *h, amr_mesh *old) {
+  const void *arrays[] = {h->mlmin,     h->mlmax,   h->mgamma_d, h->mcfl_d,    h->msmallr_d, h->msmallp_d,
+                          h->mflag32,   h->mgamma_t, h->migm1_t, h->msmallr_t, h->msmallp_t};
+  for (const void *a : arrays) move_buf(h, old, const_cast<void *>(a));
 }
 
 static amr_status build_blocks(amr_mesh *h);
@@ -2255,7 +2260,8 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
     g_last_error = msg;
     return se != AMR_OK ? se : e;
   };
-  if ((st = clone_members(nh, h)) != AMR_OK || (st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
+  share_members(nh, h);
+  if ((st = alloc_n(nh, &d_lvl, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_new, n_out)) != AMR_OK || (st = alloc_n(nh, &d_mem, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_i, n_out)) != AMR_OK || (st = alloc_n(nh, &d_j, n_out)) != AMR_OK ||
       (st = alloc_n(nh, &d_k, n_out)) != AMR_OK || (st = alloc_n(nh, &d_src, n_out)) != AMR_OK)
@@ -2288,6 +2294,7 @@ static amr_status regrid_impl(amr_mesh *h, const uint8_t *hflags, int64_t *creat
   // the handle takes the new mesh; the old one is freed
   take_over(nh, h);
   std::swap(*h, *nh);
+  own_members(h, nh);
   if (h->cache) h->cache->cap = h->bytes;  // the old mesh's arrays serve the next regrid
   destroy_all(nh);
   return check_launches(h, "amr_regrid");  // the new mesh's error word was read after its build

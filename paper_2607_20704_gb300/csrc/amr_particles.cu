@@ -170,7 +170,9 @@ int64_t scan_tmp_len(int64_t n) {
 void scan_exclusive(amr_particles *h, int kid, uint32_t *data, int64_t n, uint32_t *tmp) {
   const int64_t nb = (n + kScanItems - 1) / kScanItems;
   launch(h, kid, k_scan_block, dim3(unsigned(nb)), dim3(256), data, n, tmp);
-  if (nb > 1) {
+  if (nb > 1 && nb <= kScanFlat) {
+    launch(h, kid, k_scan_add_flat, dim3(unsigned(nb - 1)), dim3(256), data, n, (const uint32_t *)tmp);
+  } else if (nb > 1) {
     scan_exclusive(h, kid, tmp, nb, tmp + ((nb + 255) & ~int64_t(255)));
     launch(h, kid, k_scan_add, dim3(nblocks(n)), dim3(256), data, n, (const uint32_t *)tmp);
   }

@@ -51,5 +51,28 @@ __global__ void k_scan_add(uint32_t *__restrict__ data, int64_t n, const uint32_
   if (t < n) data[t] += sums[t / kScanBlock];
 }
 
+// the second pass when there are at most kScanFlat blocks: block b + 1 adds
+// the sum of the block totals before it, which it forms itself (no scan of
+// the totals, one launch less)
+constexpr int64_t kScanFlat = 4096;
+__global__ void k_scan_add_flat(uint32_t *__restrict__ data, int64_t n, const uint32_t *__restrict__ sums) {
+  const int64_t b = blockIdx.x + 1;
+  uint32_t acc = 0;
+  for (int64_t q = threadIdx.x; q < b; q += blockDim.x) acc += sums[q];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+  __shared__ uint32_t part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  uint32_t off = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) off += part[w];
+  const int64_t base = b * int64_t(kScanBlock);
+  for (int q = threadIdx.x; q < kScanBlock; q += blockDim.x) {
+    const int64_t t = base + q;
+    if (t < n) data[t] += off;
+  }
+}
+
 }  // namespace
 }  // namespace amr
