@@ -1507,11 +1507,11 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
         const int lo = int(m.oct_base + m.lo[l]), hi = int(m.oct_base + m.lo[l + 1]);
         if (hi <= lo) continue;
         if (p.precision == 4)
-          launch(h, K_PROLONG_NEW, k_prolong_new<float>, dim3(nblocks(hi - lo)), dim3(256), int(n),
+          launch(h, K_PROLONG_NEW, k_prolong_new<float>, dim3(nblocks(5 * int64_t(hi - lo))), dim3(256), int(n),
                  int(h->NE), h->S, (const uint64_t *)h->key, (const int32_t *)h->father,
                  (const int32_t *)h->fnb, (const uint8_t *)isnew, (float *)h->U, lo, hi, h->err);
         else
-          launch(h, K_PROLONG_NEW, k_prolong_new<double>, dim3(nblocks(hi - lo)), dim3(256), int(n),
+          launch(h, K_PROLONG_NEW, k_prolong_new<double>, dim3(nblocks(5 * int64_t(hi - lo))), dim3(256), int(n),
                  int(h->NE), h->S, (const uint64_t *)h->key, (const int32_t *)h->father,
                  (const int32_t *)h->fnb, (const uint8_t *)isnew, (double *)h->U, lo, hi, h->err);
       }

@@ -483,12 +483,14 @@ __global__ void k_repack_emit(int64_t N, int64_t S, const uint64_t *__restrict__
 }
 
 // new octs of [lo, hi) (one level) take the minmod prolongation of their
-// father cell from the father's face neighbours (all real after grading)
+// father cell from the father's face neighbours (all real after grading);
+// one thread per (oct, variable), 5 (hi - lo) threads
 template <class T>
 __global__ void k_prolong_new(int N, int NE, int64_t S, const uint64_t *__restrict__ key,
                               const int32_t *__restrict__ father, const int32_t *__restrict__ fnb,
                               const uint8_t *__restrict__ is_new, T *U, int lo, int hi, int *err) {
-  const int o = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int o = lo + int(tid / 5), v = int(tid % 5);
   if (o >= hi || !is_new[o]) return;
   const int fo = father[o];
   const uint64_t k = key[o];
@@ -512,19 +514,17 @@ __global__ void k_prolong_new(int N, int NE, int64_t S, const uint64_t *__restri
     }
   }
   const int64_t gc = 8 * int64_t(fo) + fc;
-  for (int v = 0; v < 5; ++v) {
-    const T *Uv = U + v * S;
-    const T uc = Uv[gc];
-    const T sx = minmod(Uv[gp[0]] - uc, uc - Uv[gm[0]]);
-    const T sy = minmod(Uv[gp[1]] - uc, uc - Uv[gm[1]]);
-    const T sz = minmod(Uv[gp[2]] - uc, uc - Uv[gm[2]]);
-    T *dst = U + v * S + 8 * int64_t(o);
-    const T h = T(0.25);
+  const T *Uv = U + v * S;
+  const T uc = Uv[gc];
+  const T sx = minmod(Uv[gp[0]] - uc, uc - Uv[gm[0]]);
+  const T sy = minmod(Uv[gp[1]] - uc, uc - Uv[gm[1]]);
+  const T sz = minmod(Uv[gp[2]] - uc, uc - Uv[gm[2]]);
+  T *dst = U + v * S + 8 * int64_t(o);
+  const T h = T(0.25);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const T hx = (c & 1) ? h : -h, hy = (c & 2) ? h : -h, hz = (c & 4) ? h : -h;
-      dst[c] = ((uc + hx * sx) + hy * sy) + hz * sz;
-    }
+  for (int c = 0; c < 8; ++c) {
+    const T hx = (c & 1) ? h : -h, hy = (c & 2) ? h : -h, hz = (c & 4) ? h : -h;
+    dst[c] = ((uc + hx * sx) + hy * sy) + hz * sz;
   }
 }
 

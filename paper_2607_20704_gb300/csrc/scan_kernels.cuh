@@ -14,31 +14,34 @@ constexpr int kScanBlock = kScanItems;
 
 __global__ void k_scan_block(uint32_t *__restrict__ data, int64_t n, uint32_t *__restrict__ sums) {
   __shared__ uint32_t s[kScanBlock];
+  __shared__ uint32_t wsum[8];
   const int64_t base = blockIdx.x * int64_t(kScanBlock);
   for (int q = threadIdx.x; q < kScanBlock; q += blockDim.x) {
     const int64_t t = base + q;
     s[q] = t < n ? data[t] : 0u;
   }
   __syncthreads();
-  // each of the 256 threads owns 4 items; Hillis-Steele over the thread sums
-  const int q0 = threadIdx.x * 4;
-  uint32_t a0 = s[q0], a1 = s[q0 + 1], a2 = s[q0 + 2], a3 = s[q0 + 3];
+  // each of the 256 threads owns 4 items; warp scans of the thread sums by
+  // shuffles, then the 8 warp totals
+  const int q0 = threadIdx.x * 4, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t a0 = s[q0], a1 = s[q0 + 1], a2 = s[q0 + 2], a3 = s[q0 + 3];
   const uint32_t tot = a0 + a1 + a2 + a3;
-  __shared__ uint32_t part[256];
-  part[threadIdx.x] = tot;
-  __syncthreads();
-  for (int off = 1; off < 256; off <<= 1) {
-    const uint32_t x = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += x;
-    __syncthreads();
+  uint32_t x = tot;  // inclusive within the warp
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
   }
-  const uint32_t excl = part[threadIdx.x] - tot;
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+  for (int k = 0; k < w; ++k) wpre += wsum[k];
+  const uint32_t excl = wpre + x - tot;
   s[q0] = excl;
   s[q0 + 1] = excl + a0;
   s[q0 + 2] = excl + a0 + a1;
   s[q0 + 3] = excl + a0 + a1 + a2;
-  if (threadIdx.x == 255) sums[blockIdx.x] = part[255];
+  if (threadIdx.x == 255) sums[blockIdx.x] = wpre + x;
   __syncthreads();
   for (int q = threadIdx.x; q < kScanBlock; q += blockDim.x) {
     const int64_t t = base + q;
