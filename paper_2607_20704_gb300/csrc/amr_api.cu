@@ -2051,6 +2051,17 @@ static RegridArgs regrid_args(amr_mesh *h, uint32_t *raw, uint32_t *flag) {
   a.test_r = a.grad_rho > 0.0;
   a.test_p = a.grad_p > 0.0;
   a.test_mass = a.mass > 0.0;
+  for (int l = 0; l < 16; ++l) {
+    const double t = a.test_mass ? std::ldexp(a.mass, 3 * l) : 0.0;  // +inf past the range
+    int64_t b64;
+    std::memcpy(&b64, &t, 8);
+    a.mass_bits64[l] = b64;
+    float f = float(t);  // rounded down to an FP32 value: rho32 > t  <=>  rho32 > f
+    if (double(f) > t) f = std::nextafter(f, -INFINITY);
+    int32_t b32;
+    std::memcpy(&b32, &f, 4);
+    a.mass_bits32[l] = b32;
+  }
   a.thr_r32 = float(a.grad_rho);
   a.thr_p32 = float(a.grad_p);
   auto thr_ok = [](float t) { return t >= 0x1p-60f && t <= 0x1p60f; };

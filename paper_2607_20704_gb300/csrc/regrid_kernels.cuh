@@ -43,6 +43,11 @@ struct RegridArgs {
   int test_r, test_p, test_mass, use32;
   float thr_r32, thr_p32;
   const float *mflag32;  // [3 M]: gamma - 1, smallr, smallp in FP32
+  // the mass criterion rho 2^(-3 l) > mass as rho > mass 2^(3 l): per level
+  // the bits of mass 2^(3 l) (FP64, +inf past the range) and of its FP32
+  // image rounded down, so that both states compare as integers
+  int64_t mass_bits64[16];
+  int32_t mass_bits32[16];
   uint32_t *raw;   // [N] criterion masks
   uint32_t *flag;  // [N] final masks
   int *err;
@@ -176,6 +181,19 @@ __device__ __forceinline__ void flag_neighbours(const RegridArgs &a, int o, int 
   }
 }
 
+// rho 2^(-3 l) > mass, exactly (the scaling is exact wherever the product is
+// a normal number; where it is not, both forms are false), compared as the
+// integers of the bits: positive values order as their bits, a negative one
+// is below every threshold, and a NaN is excluded
+__device__ __forceinline__ bool mass_exceeds(double rho, const RegridArgs &a, int l) {
+  const int64_t b = __double_as_longlong(rho);
+  return b > a.mass_bits64[l] && b <= 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ bool mass_exceeds(float rho, const RegridArgs &a, int l) {
+  const int32_t b = __float_as_int(rho);
+  return b > a.mass_bits32[l] && b <= 0x7F800000;
+}
+
 // the FP32 screen of one neighbour pair (k_flag_rp's images): dr, dp = 1 the
 // jump of rho (p) exceeds its threshold, 0 it does not, -1 FP32 cannot tell
 // (0 also for a test that is off)
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(256) k_flag_raw(RegridArgs a, const T *__restr
     const uint64_t key = a.key[o];
     const int m = ikey_member(key), l = ikey_lev(key);
     if (l < a.mlmax[m]) {
-      f = a.test_mass && ldexp(double(U[gc]), -3 * l) > a.mass;
+      if (a.test_mass) f = mass_exceeds(U[gc], a, l);
       const float rc = rp[gc], pc = rp[N8 + gc], ec = rp[2 * N8 + gc];
       int32_t gnb[6];
       flag_neighbours(a, o, c, gnb);
