@@ -76,3 +76,16 @@ def test_hilbert_octants_are_contiguous(orc):
         blocks.setdefault(h // 64, set()).add((x >> 2, y >> 2, z >> 2))
     assert all(len(v) == 1 for v in blocks.values())
     assert len({next(iter(v)) for v in blocks.values()}) == 8
+
+
+@pytest.mark.parametrize("bits", [1, 2, 5, 9, 14])
+def test_hilbert_index_extends_the_parents(orc, bits):
+    """The index of a cell at bits + 1 is its parent's index (coordinates
+    halved, at bits) followed by one octal digit: octs whose fathers are in
+    curve order are in curve order once the children of each father are
+    sorted (the order a regrid builds for its new octs)."""
+    rng = np.random.default_rng(bits)
+    side = 1 << (bits + 1)
+    for x, y, z in rng.integers(0, side, size=(2000, 3)):
+        child = orc.hilbert3(x, y, z, bits + 1)
+        assert child >> 3 == orc.hilbert3(x >> 1, y >> 1, z >> 1, bits), (x, y, z, bits)
