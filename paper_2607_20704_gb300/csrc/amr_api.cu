@@ -87,7 +87,7 @@ enum Kid {
   K_LOOKUP, K_PROLONG, K_PRIM, K_PREDICT, K_FLUX, K_UPDATE, K_REFLUX, K_RESTRICT, K_CFL, K_DT,
   K_CONVERT, K_FLAG, K_REGRID, K_PROLONG_NEW, K_FLAG_RP, K_FLAG_EXPAND, K_FLAG_GRADE,
   K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_OTHER, K_ROCK, K_COMMIT, K_SWEEP, K_TOTALS,
-  K_FNV, K_DEPOSIT, K_SPLIT, K_SORT_SMALL, K_MERGE, K_FLAG_EXACT, K_COUNT
+  K_FNV, K_DEPOSIT, K_SPLIT, K_SORT_GROUPS, K_MERGE, K_FLAG_EXACT, K_COUNT
 };
 static const char *kKernelNames[K_COUNT] = {
     "sort_keys", "radix_hist", "radix_scatter", "scan", "gather_octs", "hash_insert",
@@ -95,7 +95,7 @@ static const char *kKernelNames[K_COUNT] = {
     "faces", "cache_sources", "lookup", "prolong", "prim", "predict", "flux", "update",
     "reflux", "reflux_restrict", "cfl", "dt", "convert", "flag", "regrid", "prolong_new",
     "flag_rp", "flag_expand", "flag_grade", "mg_smooth", "mg_restrict", "mg_prolong", "mg_other",
-    "rock", "commit", "sweep", "totals", "fnv", "deposit_level", "split_level", "sort_small",
+    "rock", "commit", "sweep", "totals", "fnv", "deposit_level", "split_level", "sort_groups",
     "merge_rank", "flag_exact"};
 
 extern "C" const char *amr_kernel_name(int t) {
@@ -1299,18 +1299,12 @@ static amr_status build_mesh(amr_mesh *h, int64_t n, bool have_hk, uint8_t *d_lv
   uint64_t *kk = comp;
   uint32_t *vv = perm;
   const int64_t n_new = n - sorted_prefix;
-  const bool grouped = from && from->pos;  // new octs sorted but within each father's group
-  if (sorted_prefix > 0 && n_new >= 0 && (grouped || n_new <= kSmallSort)) {
-    // a regrid: the kept octs [0, sorted_prefix) are in order; sort the new
-    // ones (within their fathers' groups, or in one block) and merge the two
-    // runs by rank
+  if (sorted_prefix > 0 && n_new >= 0 && from && from->pos) {
+    // a regrid: the kept octs [0, sorted_prefix) are in order, the new ones
+    // are once each father's group is sorted; then the two runs merge by rank
     if (n_new > 0) {
-      if (grouped)
-        launch(h, K_SORT_SMALL, k_sort_groups, dim3(nblocks(from->n_old)), dim3(256), from->pos, from->n_old,
-               comp, perm);
-      else
-        launch(h, K_SORT_SMALL, k_sort_small, dim3(1), dim3(1024), comp + sorted_prefix,
-               perm + sorted_prefix, int(n_new));
+      launch(h, K_SORT_GROUPS, k_sort_groups, dim3(nblocks(from->n_old)), dim3(256), from->pos, from->n_old,
+             comp, perm);
       launch(h, K_MERGE, k_merge_rank, dim3(nblocks(sorted_prefix)), dim3(256), (const uint64_t *)comp,
              (const uint32_t *)perm, sorted_prefix, (const uint64_t *)(comp + sorted_prefix), n_new, comp_alt,
              perm_alt);

@@ -41,45 +41,10 @@ __global__ void k_make_sort_keys(const uint8_t *__restrict__ lvl, const uint32_t
 
 // ---------------------------------------------------------------------------
 // a regrid's new oct list: the kept octs in their old (sorted) order, then the
-// new octs.  When the new ones are few, they are sorted by one block and
-// merged by rank instead of radix-sorting the whole list (same order: the
-// keys are unique)
+// new octs; the new ones are put in order (below) and the two runs merged by
+// rank instead of radix-sorting the whole list (same order: the keys are
+// unique)
 // ---------------------------------------------------------------------------
-constexpr int kSmallSort = 2048;
-
-// ascending bitonic sort of n <= kSmallSort (key, value) pairs in place; one
-// block of 1024 threads, padded with the largest key
-__global__ void __launch_bounds__(1024) k_sort_small(uint64_t *__restrict__ key, uint32_t *__restrict__ val,
-                                                     int n) {
-  __shared__ uint64_t sk[kSmallSort];
-  __shared__ uint32_t sv[kSmallSort];
-  for (int t = threadIdx.x; t < kSmallSort; t += blockDim.x) {
-    sk[t] = t < n ? key[t] : ~0ull;
-    sv[t] = t < n ? val[t] : 0u;
-  }
-  __syncthreads();
-  for (int size = 2; size <= kSmallSort; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < kSmallSort / 2; t += blockDim.x) {
-        const int lo = 2 * t - (t & (stride - 1));  // first index of the pair
-        const int hi = lo + stride;
-        const bool up = (lo & size) == 0;
-        if ((sk[lo] > sk[hi]) == up) {
-          const uint64_t k = sk[lo];
-          sk[lo] = sk[hi];
-          sk[hi] = k;
-          const uint32_t v = sv[lo];
-          sv[lo] = sv[hi];
-          sv[hi] = v;
-        }
-      }
-      __syncthreads();
-    }
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    key[t] = sk[t];
-    val[t] = sv[t];
-  }
-}
 
 // a regrid's new octs in the order the emit pass wrote them: by old oct
 // (which is the sorted order of their fathers), then by cell of the father.
