@@ -83,6 +83,46 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.amr_destroy(None) == amr.AMR_OK
 
 
+HANDLES = ("amr_handle", "amr_server_t", "amr_part_handle")
+
+
+def _handle_entry_points():
+    """(name, parameter types) of every call in the headers that takes a
+    handle (mesh, server or particle set) first, read from the header text."""
+    out = []
+    for header in ("amr.h", "amr_particles.h"):
+        text = open(os.path.join(ROOT, "include", header)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for name, args in re.findall(r"\bamr_status\s+(amr_\w+)\s*\(([^;{]*?)\)\s*;", text, re.S):
+            params = [" ".join(p.split()) for p in args.split(",")]
+            if not params[0].split()[0] in HANDLES:
+                continue
+            out.append((name, [p if p.endswith("*") or "*" in p.split()[-1] else re.sub(r"\s*\b\w+$", "", p)
+                               for p in params[1:]]))
+    return out
+
+
+def test_every_handle_call_refuses_a_null_handle(lib):
+    """Every call that takes a handle returns AMR_EINVAL for NULL (the destroy
+    calls: AMR_OK) before it touches any other argument or the device."""
+    from paper_2607_20704_gb300 import amr
+    scalar = {"int": C.c_int, "int64_t": C.c_int64, "double": C.c_double}
+    calls = _handle_entry_points()
+    assert len(calls) >= 50
+    own = C.CDLL(amr.LIB)  # prototypes set here stay off the binding's functions
+    own.amr_last_error.restype = C.c_char_p
+    for name, params in calls:
+        fn = getattr(own, name)
+        types = [C.c_void_p] + [C.c_void_p if "*" in t else scalar[t] for t in params]
+        fn.argtypes = types
+        fn.restype = C.c_int
+        args = [None] + [None if t is C.c_void_p else t(0) for t in types[1:]]
+        want = amr.AMR_OK if name.endswith("_destroy") else amr.AMR_EINVAL
+        assert fn(*args) == want, name
+        if want == amr.AMR_EINVAL:
+            assert own.amr_last_error().decode(), name
+
+
 def test_particle_calls_check_their_arguments_on_the_host(lib):
     from paper_2607_20704_gb300 import amr
     import numpy as np
