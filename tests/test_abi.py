@@ -179,3 +179,28 @@ def test_create_refuses_oversize_meshes_on_the_host(lib):
     rc = lib.amr_create_batch(C.byref(p), 2, members, C.byref(h))
     assert rc == amr.AMR_EINVAL and not h.value
     assert "2^26" in lib.amr_last_error().decode()
+
+
+def test_static_cfl_refuses_bad_arguments_on_the_host(lib):
+    """amr_cfl_dt_static checks its pointers, sizes and parameters before any
+    CUDA call (the device pointers given here are never dereferenced: every
+    case is refused first)."""
+    from paper_2607_20704_gb300 import amr
+    own = C.CDLL(amr.LIB)
+    fn = own.amr_cfl_dt_static
+    fn.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_double,
+                   C.c_double, C.c_void_p, C.c_void_p]
+    fn.restype = C.c_int
+    own.amr_last_error.restype = C.c_char_p
+    fake = 0x1000  # stands for a device address; none of the cases below reaches it
+    good = dict(U=fake, n=1024, stride=1024, level=5, gamma=1.4, cfl=0.8, smallr=1e-10, smallc=1e-10,
+                dt=fake)
+    cases = [dict(U=None), dict(dt=None), dict(n=0), dict(n=(65536 * 256) + 1), dict(stride=1023),
+             dict(level=-1), dict(level=31), dict(gamma=1.0), dict(cfl=0.0), dict(smallr=0.0),
+             dict(smallc=-1.0), dict(gamma=float("nan"))]
+    for bad in cases:
+        a = {**good, **bad}
+        rc = fn(a["U"], a["n"], a["stride"], a["level"], a["gamma"], a["cfl"], a["smallr"], a["smallc"],
+                a["dt"], None)
+        assert rc == amr.AMR_EINVAL, bad
+        assert own.amr_last_error().decode().startswith("amr_cfl_dt_static"), bad
