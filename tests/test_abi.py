@@ -204,3 +204,42 @@ def test_static_cfl_refuses_bad_arguments_on_the_host(lib):
                 a["dt"], None)
         assert rc == amr.AMR_EINVAL, bad
         assert own.amr_last_error().decode().startswith("amr_cfl_dt_static"), bad
+
+
+def test_batch_members_are_checked_on_the_host(lib):
+    """A member with a NULL array, bad levels or parameters, or no octs, and
+    launch parameters outside their sets, are refused before any device work
+    (this runs without a GPU; the arrays are never read)."""
+    from paper_2607_20704_gb300 import amr
+    import numpy as np
+    one = np.ones(1, np.uint8)
+    z = np.zeros(1, np.uint32)
+    U = np.ones((5, 8))
+
+    def member(**kw):
+        m = amr.amr_member()
+        m.levelmin, m.levelmax, m.gamma, m.cfl, m.smallr, m.smallc, m.n_oct = 3, 4, 1.4, 0.8, 1e-10, 1e-10, 1
+        m.level, m.i, m.j, m.k, m.U = one.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data, U.ctypes.data
+        for key, v in kw.items():
+            setattr(m, key, v)
+        return m
+
+    bad_members = [dict(level=None), dict(i=None), dict(U=None), dict(levelmin=0), dict(levelmax=16),
+                   dict(levelmin=5, levelmax=4), dict(gamma=1.0), dict(cfl=0.0), dict(smallr=0.0),
+                   dict(smallc=0.0), dict(n_oct=0)]
+    p = amr.amr_params()
+    lib.amr_params_default(C.byref(p))
+    h = C.c_void_p()
+    for bad in bad_members:
+        members = (amr.amr_member * 2)(member(), member(**bad))
+        assert lib.amr_create_batch(C.byref(p), 2, members, C.byref(h)) == amr.AMR_EINVAL, bad
+        assert not h.value and lib.amr_last_error().decode(), bad
+    members = (amr.amr_member * 1)(member())
+    assert lib.amr_create_batch(C.byref(p), 0, members, C.byref(h)) == amr.AMR_EINVAL
+    assert lib.amr_create_batch(C.byref(p), 1, None, C.byref(h)) == amr.AMR_EINVAL
+    for field, value in (("tile", 100), ("nsubgrid", 3), ("planar", 2), ("precision", 16)):
+        q = amr.amr_params()
+        lib.amr_params_default(C.byref(q))
+        setattr(q, field, value)
+        assert lib.amr_create_batch(C.byref(q), 1, members, C.byref(h)) == amr.AMR_EINVAL, field
+        assert not h.value
