@@ -241,3 +241,62 @@ def test_new_children_interpolate_linear_data():
     assert interior.sum() > 0
     want = 1.0 + 0.1 * xc[interior]
     assert np.max(np.abs(U[0, interior] - want)) <= 1e-14
+
+
+@pytest.mark.parametrize("seed,pre,thr", [(3, None, 0.05), (4, None, 0.05), (5, 0.05, 0.3), (7, 0.03, 0.3)])
+def test_new_order_from_the_old_one(seed, pre, thr):
+    """The regridded mesh's order (level, then Hilbert index) is the old order
+    of the kept octs merged by rank with the new octs taken by father (in the
+    old order) and sorted within each father's group, because an oct's
+    Hilbert index is its father's followed by one octal digit.  The kept and
+    new octs are derived here from the oracle's flags and split masks; the
+    merge is compared with the order of the oracle's regridded mesh."""
+    import bisect
+    prob = inputs.random_mesh(3, 6, seed=seed)
+    o = _mesh(prob)
+    if pre is not None:  # a refined mesh first, so that this regrid also removes octs
+        o.regrid(grad_rho=pre, grad_p=pre)
+    crit = dict(grad_rho=thr, grad_p=thr)
+    F = o.flags(**crit)
+
+    def coords(k):
+        k = int(k)
+        return (k >> 40) & 0xFFFFF, (k >> 20) & 0xFFFFF, k & 0xFFFFF
+
+    def hkey(l, x, y, z):
+        return l, oracle.hilbert3(x, y, z, l - 1)
+
+    old = []  # (level, x, y, z, flags[8], split[8]) in mesh order
+    for l in o.levels():
+        keys, _ = o.read(l)
+        off = o.level_offset(l)
+        fl = F[8 * off: 8 * (off + len(keys))].reshape(-1, 8)
+        sp = o.read_split(l).reshape(-1, 8)
+        old += [(l, *coords(k), fl[q], sp[q]) for q, k in enumerate(keys)]
+    where = {(l, x, y, z): q for q, (l, x, y, z, _, _) in enumerate(old)}
+    kept, groups = [], []
+    for l, x, y, z, fl, sp in old:
+        if l == o.levelmin:
+            keep = True
+        else:
+            father = old[where[(l - 1, x >> 1, y >> 1, z >> 1)]]
+            keep = bool(father[4][(x & 1) | ((y & 1) << 1) | ((z & 1) << 2)])
+        if keep:
+            kept.append(hkey(l, x, y, z))
+        groups.append(sorted(hkey(l + 1, 2 * x + (c & 1), 2 * y + ((c >> 1) & 1), 2 * z + ((c >> 2) & 1))
+                             for c in range(8) if fl[c] and not sp[c]))
+    new = [k for g in groups for k in g]
+    assert new == sorted(new) and kept == sorted(kept)
+    merged = [None] * (len(kept) + len(new))
+    for i, k in enumerate(kept):
+        merged[i + bisect.bisect_left(new, k)] = k
+    for i, k in enumerate(new):
+        merged[i + bisect.bisect_left(kept, k)] = k
+    created, removed = o.regrid(**crit)
+    assert (created, removed) == (len(new), len(old) - len(kept))
+    assert created > 0 and (pre is None or removed > 0), (created, removed)
+    want = []
+    for l in o.levels():
+        keys, _ = o.read(l)
+        want += [hkey(l, *coords(k)) for k in keys]
+    assert merged == want
