@@ -5,6 +5,7 @@ comparisons, checked against the comparisons as defined (CPU, numpy).
   (signed 64-bit integers; NaN excluded), and for an FP32 state as
   bits32(rho) > bits32(RD32(mass 2^(3 l))), RD32 = rounding down to FP32.
 - Jumps: two non-negative doubles compare as the integers of their bits.
+- FP32 images of an FP64 state: the bits truncated on the integer pipes.
 """
 import math
 
@@ -74,3 +75,37 @@ def test_non_negative_doubles_order_as_their_bits(seed):
     ia, ib = a.view(np.int64), b.view(np.int64)
     assert np.array_equal(ia > ib, a > b)
     assert np.array_equal(ia == ib, a == b)
+
+
+def _to_f32_bits(x):
+    """The flag kernels' FP32 image of an FP64 value, on the integer pipes:
+    sign, exponent rebiased, mantissa truncated; below 2^-126 zero, above the
+    FP32 range infinity."""
+    b = int(np.array([x], np.float64).view(np.uint64)[0])
+    sign = (b >> 32) & 0x80000000
+    e = (b >> 52) & 0x7FF
+    if e < 1023 - 126:
+        bits = sign
+    elif e > 1023 + 127:
+        bits = sign | 0x7F800000
+    else:
+        bits = sign | ((e - 896) << 23) | ((b >> 29) & 0x7FFFFF)
+    return float(np.array([bits], np.uint32).view(np.float32)[0])
+
+
+def test_fp32_images_truncate_within_their_bound():
+    """Within the normal FP32 range the image is x rounded toward zero to
+    FP32 (relative error below 2^-23, the bound the screen assumes), and an
+    FP32 value maps to itself."""
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([np.exp(rng.uniform(-80, 80, 3000)) * rng.choice([-1, 1], 3000),
+                         [1.0, -1.0, 1.5, 2.0 ** -126, 3.4e38]])
+    for x in xs:
+        f = _to_f32_bits(x)
+        r = np.float32(x)
+        if abs(float(r)) > abs(x):
+            r = np.nextafter(r, np.float32(0))
+        assert f == float(r), x
+        assert abs(f - x) <= 2.0 ** -23 * abs(x), x
+        assert _to_f32_bits(float(np.float32(x))) == float(np.float32(x))
+    assert _to_f32_bits(1e-300) == 0.0 and _to_f32_bits(1e300) == np.inf and _to_f32_bits(-1e300) == -np.inf
