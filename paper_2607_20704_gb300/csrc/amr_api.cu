@@ -1141,13 +1141,6 @@ static amr_status upload_members(amr_mesh *h) {
   return upload_member_params<double>(h);
 }
 
-template <class P>
-static amr_status dup_n(amr_mesh *nh, P **dst, const P *src, int64_t n) {
-  AMR_TRY(alloc_n(nh, dst, n));
-  CUDA_TRY(cudaMemcpyAsync(*dst, src, sizeof(P) * size_t(n), cudaMemcpyDeviceToDevice, nh->s));
-  return AMR_OK;
-}
-
 // a regrid's new mesh nh reads h's member arrays (levels, parameters: fixed
 // for a member's life) as they are; h still owns them
 static void share_members(amr_mesh *nh, const amr_mesh *h) {
